@@ -1,0 +1,247 @@
+"""FP64 CPU oracle of the differentiable splat rasterizer (ctypes wrapper).
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the tests, the smoke check and the
+benchmark's CPU-baseline leg may import this package.  It loads
+oracle/_build/liboracle.so (built from gs_oracle.cpp by oracle/build.py) and
+shares nothing with the CUDA path.  Every function takes scenes and cameras in
+natural layout (paper_2607_14481_b300.synth.Scene / Camera) and upcasts them to
+float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        d = C.POINTER(C.c_double)
+        i32 = C.POINTER(C.c_int32)
+        u8 = C.POINTER(C.c_uint8)
+        u32 = C.POINTER(C.c_uint32)
+        u64 = C.POINTER(C.c_uint64)
+        L.orc_sh_basis.argtypes = [C.c_int, C.c_int64, d, d]
+        L.orc_render.argtypes = [C.c_int64, C.c_int, d, d, d, d, d, C.c_int, d, d, i32, C.c_double,
+                                 C.c_int, C.c_int, d, C.c_int, d, d, d, u8, d]
+        L.orc_render_dual.argtypes = [C.c_int64, C.c_int, d, d, d, d, d, d, d, d, d, d, C.c_int, d, d,
+                                      d, i32, C.c_double, C.c_int, C.c_int, d, C.c_int, d, d, d]
+        L.orc_backward.argtypes = [C.c_int64, C.c_int, d, d, d, d, d, C.c_int, d, d, i32, C.c_double,
+                                   C.c_int, C.c_int, d, C.c_int, d, d, d, d, d, d, d, d]
+        L.orc_bin.argtypes = [C.c_int, C.c_int64, u32, i32, i32, C.c_int64, u64, u32, u32]
+        L.orc_bin.restype = C.c_int64
+        L.orc_adam.argtypes = [C.c_int64, d, d, d, d, d, C.c_double, C.c_double, C.c_double, C.c_int]
+        L.orc_pose_adam.argtypes = [C.c_int, d, d, d, d, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, C.c_int]
+        L.orc_se3_exp.argtypes = [d, d, d]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ct=C.c_double):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+PROJ_FIELDS = ("vis", "mx", "my", "A", "B", "C", "opacity", "r", "g", "b", "depth", "radius",
+               "xlo", "ylo", "xhi", "yhi", "clamp", "img_amb", "grad_amb", "bin_amb")
+
+
+class _Inputs:
+    def __init__(self, scene, cams, znear, tile, bg, clamp_j):
+        self.N = scene.n
+        self.deg = scene.sh_degree
+        self.means = _f64(scene.means)
+        self.lsc = _f64(scene.log_scales)
+        self.quat = _f64(scene.quats)
+        self.opl = _f64(scene.opa_logits)
+        self.sh = _f64(scene.sh)
+        self.V = len(cams)
+        self.poses = _f64(np.stack([c.pose12() for c in cams]))
+        self.intr = _f64([[c.fx, c.fy, c.cx, c.cy] for c in cams])
+        self.wh = np.ascontiguousarray(np.array([[c.width, c.height] for c in cams], np.int32))
+        self.znear = float(znear)
+        self.tw, self.th = int(tile[0]), int(tile[1])
+        self.bg = _f64(bg)
+        self.clamp_j = int(bool(clamp_j))
+        self.cams = cams
+
+    def scene_args(self):
+        return (self.N, self.deg, _p(self.means), _p(self.lsc), _p(self.quat), _p(self.opl), _p(self.sh))
+
+    def split_views(self, flat: np.ndarray, per_pixel: int) -> List[np.ndarray]:
+        out, off = [], 0
+        for c in self.cams:
+            n = per_pixel * c.width * c.height
+            a = flat[off:off + n]
+            out.append(a.reshape((per_pixel, c.height, c.width)) if per_pixel > 1
+                       else a.reshape((c.height, c.width)))
+            off += n
+        return out
+
+
+def _npix(cams) -> int:
+    return int(sum(c.width * c.height for c in cams))
+
+
+def sh_basis(degree: int, dirs) -> np.ndarray:
+    """Real SH basis values [n, (degree+1)^2] at unit directions [n,3]."""
+    d = _f64(dirs).reshape(-1, 3)
+    nc = (degree + 1) ** 2
+    out = np.zeros((d.shape[0], nc))
+    rc = lib().orc_sh_basis(int(degree), d.shape[0], _p(d), _p(out))
+    assert rc == 0
+    return out
+
+
+def render(scene, cams, znear=0.2, tile=(16, 16), bg=(0.0, 0.0, 0.0), clamp_j=True,
+           margins: Optional[Sequence[float]] = None, want_proj=False) -> Dict:
+    """Forward render.  Returns image (list of [3,H,W]), alpha (list of [H,W]),
+    flags (list of [H,W] uint8: bit 0 = the image value depends on a decision
+    within margin, bit 1 = its derivative does) and optionally proj
+    [V,N,len(PROJ_FIELDS)]."""
+    a = _Inputs(scene, cams, znear, tile, bg, clamp_j)
+    P = _npix(cams)
+    img = np.zeros(3 * P)
+    alpha = np.zeros(P)
+    flags = np.zeros(P, np.uint8)
+    proj = np.zeros((a.V, a.N, len(PROJ_FIELDS))) if want_proj else None
+    mg = _f64(margins) if margins is not None else None
+    rc = lib().orc_render(*a.scene_args(), a.V, _p(a.poses), _p(a.intr), _p(a.wh, C.c_int32), a.znear,
+                          a.tw, a.th, _p(a.bg), a.clamp_j, _p(mg) if mg is not None else None,
+                          _p(img), _p(alpha), _p(flags, C.c_uint8),
+                          _p(proj) if proj is not None else None)
+    assert rc == 0
+    out = {"image": a.split_views(img, 3), "alpha": a.split_views(alpha, 1),
+           "flags": a.split_views(flags, 1)}
+    if proj is not None:
+        out["proj"] = proj
+    return out
+
+
+def backward(scene, cams, dimage: Sequence[np.ndarray], dalpha: Optional[Sequence[np.ndarray]] = None,
+             znear=0.2, tile=(16, 16), bg=(0.0, 0.0, 0.0), clamp_j=True) -> Dict:
+    """Analytic FP64 gradients of sum(dimage * image) + sum(dalpha * alpha)
+    w.r.t. every parameter (natural layout) and every pose ([V,6], (v, omega)
+    of the left perturbation T <- Exp(xi) T)."""
+    a = _Inputs(scene, cams, znear, tile, bg, clamp_j)
+    di = _f64(np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in dimage]))
+    da = (_f64(np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in dalpha]))
+          if dalpha is not None else None)
+    N, nc = a.N, (a.deg + 1) ** 2
+    g = {"means": np.zeros((N, 3)), "log_scales": np.zeros((N, 3)), "quats": np.zeros((N, 4)),
+         "opa_logits": np.zeros(N), "sh": np.zeros((N, 3, nc)), "pose": np.zeros((a.V, 6))}
+    rc = lib().orc_backward(*a.scene_args(), a.V, _p(a.poses), _p(a.intr), _p(a.wh, C.c_int32), a.znear,
+                            a.tw, a.th, _p(a.bg), a.clamp_j, _p(di), _p(da) if da is not None else None,
+                            _p(g["means"]), _p(g["log_scales"]), _p(g["quats"]), _p(g["opa_logits"]),
+                            _p(g["sh"]), _p(g["pose"]))
+    assert rc == 0
+    return g
+
+
+def render_dual(scene, tangent: Dict[str, np.ndarray], pose_tangent: np.ndarray, cams, znear=0.2,
+                tile=(16, 16), bg=(0.0, 0.0, 0.0), clamp_j=True) -> Dict:
+    """Forward render on dual numbers.  `tangent` holds arrays shaped like the
+    scene's (keys means, log_scales, quats, opa_logits, sh); pose_tangent is
+    [V,6] (v, omega).  Returns image values and their exact directional
+    derivatives (lists of [3,H,W]) and the alpha derivative."""
+    a = _Inputs(scene, cams, znear, tile, bg, clamp_j)
+    t = {k: _f64(tangent[k]) for k in ("means", "log_scales", "quats", "opa_logits", "sh")}
+    tp = _f64(pose_tangent).reshape(a.V, 6)
+    P = _npix(cams)
+    img = np.zeros(3 * P)
+    img_t = np.zeros(3 * P)
+    al_t = np.zeros(P)
+    rc = lib().orc_render_dual(*a.scene_args(), _p(t["means"]), _p(t["log_scales"]), _p(t["quats"]),
+                               _p(t["opa_logits"]), _p(t["sh"]), a.V, _p(a.poses), _p(tp), _p(a.intr),
+                               _p(a.wh, C.c_int32), a.znear, a.tw, a.th, _p(a.bg), a.clamp_j,
+                               _p(img), _p(img_t), _p(al_t))
+    assert rc == 0
+    return {"image": a.split_views(img, 3), "image_tan": a.split_views(img_t, 3),
+            "alpha_tan": a.split_views(al_t, 1)}
+
+
+def bin_records(depth: np.ndarray, rect: np.ndarray, tiles: Sequence[tuple]):
+    """Reference binning of given records: depth [V,N] float32 (positive),
+    rect [V,N,4] int (xlo, ylo, xhi, yhi; xlo > xhi = culled), tiles [(TX,TY)].
+    Returns (keys uint64 [K], vals uint32 [K], ranges uint32 [G,2])."""
+    depth = np.ascontiguousarray(depth, np.float32)
+    bits = np.ascontiguousarray(depth.view(np.uint32))
+    rect = np.ascontiguousarray(rect, np.int32)
+    V, N = depth.shape
+    tl = np.ascontiguousarray(np.array(tiles, np.int32).reshape(V, 2))
+    G = int(sum(int(tx) * int(ty) for tx, ty in tl))
+    cap = 0
+    for v in range(V):
+        r = rect[v]
+        ok = (r[:, 0] <= r[:, 2]) & (r[:, 1] <= r[:, 3])
+        cap += int(((r[:, 2] - r[:, 0] + 1) * (r[:, 3] - r[:, 1] + 1) * ok).sum())
+    keys = np.zeros(max(cap, 1), np.uint64)
+    vals = np.zeros(max(cap, 1), np.uint32)
+    ranges = np.zeros((G, 2), np.uint32)
+    K = lib().orc_bin(V, N, _p(bits, C.c_uint32), _p(rect, C.c_int32), _p(tl, C.c_int32), cap,
+                      _p(keys, C.c_uint64), _p(vals, C.c_uint32), _p(ranges, C.c_uint32))
+    assert K == cap
+    return keys[:K], vals[:K], ranges
+
+
+def adam(p, g, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15):
+    """In-place bias-corrected Adam on float64 arrays; lr scalar or per element."""
+    n = p.size
+    lr_a = _f64(np.broadcast_to(np.asarray(lr, np.float64), (n,)))
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    gg = _f64(g)
+    rc = lib().orc_adam(n, _p(p), _p(gg), _p(m), _p(v), _p(lr_a), b1, b2, eps, int(step))
+    assert rc == 0
+
+
+def pose_adam(poses, gpose, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15):
+    """In-place pose step on float64 arrays: Adam on xi, then T <- Exp(xi) T.
+    poses [V,12] ([R | t] row-major), gpose/m/v [V,6]."""
+    for a in (poses, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    gg = _f64(gpose)
+    rc = lib().orc_pose_adam(poses.shape[0], _p(poses), _p(gg), _p(m), _p(v), lr, b1, b2, eps, int(step))
+    assert rc == 0
+
+
+def se3_exp(xi) -> tuple:
+    """SE(3) exponential of xi = (v, omega): returns (R [3,3], t [3])."""
+    x = _f64(xi).reshape(6)
+    R = np.zeros(9)
+    t = np.zeros(3)
+    lib().orc_se3_exp(_p(x), _p(R), _p(t))
+    return R.reshape(3, 3), t
+
+
+# ---------------------------------------------------------------------------
+# Losses (outside the renderer, which consumes dL/dimage)
+# ---------------------------------------------------------------------------
+
+def l1_loss(images: Sequence[np.ndarray], targets: Sequence[np.ndarray]):
+    """Mean absolute error over all views' pixels and channels; returns
+    (loss, [dL/dimage per view])."""
+    n = sum(t.size for t in targets)
+    loss = sum(np.abs(np.asarray(i, np.float64) - t).sum() for i, t in zip(images, targets)) / n
+    grads = [np.sign(np.asarray(i, np.float64) - t) / n for i, t in zip(images, targets)]
+    return loss, grads
+
+
+def mse_loss(images: Sequence[np.ndarray], targets: Sequence[np.ndarray]):
+    """Mean squared error over all views' pixels and channels."""
+    n = sum(t.size for t in targets)
+    d = [np.asarray(i, np.float64) - t for i, t in zip(images, targets)]
+    loss = sum((x * x).sum() for x in d) / n
+    return loss, [2.0 * x / n for x in d]

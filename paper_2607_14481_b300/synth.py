@@ -1,0 +1,231 @@
+"""Seeded synthetic scenes, cameras and trajectories.
+
+The paper's captures (MipNeRF360, TUM, StaticHikes, CityWalk ...) are not
+available, so every input is drawn here with the shapes of those captures:
+Gaussian counts of 0.5-2M for medium scenes (the paper's hierarchy memory
+evaluation reports 1.3-2.1M), 720p-1080p views, forward-moving or
+inward-facing trajectories.
+
+This module holds random draws and camera placement only.  It contains none of
+the renderer's arithmetic, so it can feed both the CUDA path and the CPU oracle.
+All arrays are float32 (the precision the renderer consumes); the oracle upcasts
+the same values to float64.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Sequence
+
+import numpy as np
+
+
+@dataclass
+class Scene:
+    """Gaussian primitives in natural layout (Sec. 7: position, opacity,
+    rotation, scale and SH coefficients per primitive)."""
+    means: np.ndarray        # [N,3]
+    log_scales: np.ndarray   # [N,3]
+    quats: np.ndarray        # [N,4] (w,x,y,z), not normalised
+    opa_logits: np.ndarray   # [N]
+    sh: np.ndarray           # [N,3,C], C = (degree+1)^2
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @property
+    def sh_degree(self) -> int:
+        return int(round(np.sqrt(self.sh.shape[2]))) - 1
+
+    def copy(self) -> "Scene":
+        return Scene(self.means.copy(), self.log_scales.copy(), self.quats.copy(),
+                     self.opa_logits.copy(), self.sh.copy())
+
+    def subset(self, idx) -> "Scene":
+        return Scene(self.means[idx], self.log_scales[idx], self.quats[idx],
+                     self.opa_logits[idx], self.sh[idx])
+
+
+@dataclass
+class Camera:
+    """Pinhole camera, OpenCV axes (x right, y down, z forward).
+    R, t map world to camera: x_cam = R x_world + t."""
+    R: np.ndarray            # [3,3] float32
+    t: np.ndarray            # [3]   float32
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+
+    def pose12(self) -> np.ndarray:
+        """[R | t] as 12 values, row-major 3x4, in the dtype R and t carry."""
+        R = np.asarray(self.R)
+        t = np.asarray(self.t)
+        return np.concatenate([R, t[:, None]], axis=1).reshape(12)
+
+    @property
+    def pixels(self) -> int:
+        return self.width * self.height
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(seed)
+
+
+def random_scene(n: int, seed: int, sh_degree: int, mean_lo: Sequence[float],
+                 mean_hi: Sequence[float], log_scale_mu: float, log_scale_sigma: float,
+                 sh_rest_sigma: float = 0.05) -> Scene:
+    """Means uniform in a box, log-scales N(mu, sigma^2) per axis, quaternions
+    N(0, I4) (normalised by the renderer), opacity logits N(0,1) (so the
+    opacity is sigmoid of a standard normal), SH DC uniform in [0,1], higher
+    bands N(0, sh_rest_sigma^2)."""
+    g = _rng(seed)
+    lo = np.asarray(mean_lo, np.float64)
+    hi = np.asarray(mean_hi, np.float64)
+    means = (lo + (hi - lo) * g.random((n, 3))).astype(np.float32)
+    log_scales = g.normal(log_scale_mu, log_scale_sigma, (n, 3)).astype(np.float32)
+    quats = g.normal(0.0, 1.0, (n, 4)).astype(np.float32)
+    # keep quaternions away from zero norm (a measure-zero event, redrawn)
+    bad = np.linalg.norm(quats, axis=1) < 1e-3
+    while bad.any():
+        quats[bad] = g.normal(0.0, 1.0, (int(bad.sum()), 4)).astype(np.float32)
+        bad = np.linalg.norm(quats, axis=1) < 1e-3
+    opa_logits = g.normal(0.0, 1.0, n).astype(np.float32)
+    nc = (sh_degree + 1) ** 2
+    sh = np.zeros((n, 3, nc), np.float32)
+    sh[:, :, 0] = g.random((n, 3)).astype(np.float32)
+    if nc > 1:
+        sh[:, :, 1:] = g.normal(0.0, sh_rest_sigma, (n, 3, nc - 1)).astype(np.float32)
+    return Scene(means, log_scales, quats, opa_logits, sh)
+
+
+def look_at(eye, target, fx, fy, cx, cy, width, height, up=(0.0, -1.0, 0.0)) -> Camera:
+    """Camera at `eye` looking at `target`; world 'up' is -y (image y grows down)."""
+    eye = np.asarray(eye, np.float64)
+    z = np.asarray(target, np.float64) - eye
+    z /= np.linalg.norm(z)
+    x = np.cross(z, np.asarray(up, np.float64))
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    R = np.stack([x, y, z])
+    t = -R @ eye
+    return Camera(R.astype(np.float32), t.astype(np.float32), float(fx), float(fy),
+                  float(cx), float(cy), int(width), int(height))
+
+
+def _small_rotation(g: np.random.Generator, sigma_deg: float) -> np.ndarray:
+    a = np.deg2rad(g.normal(0.0, sigma_deg, 3))
+    cx, sx, cy, sy, cz, sz = np.cos(a[0]), np.sin(a[0]), np.cos(a[1]), np.sin(a[1]), np.cos(a[2]), np.sin(a[2])
+    Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+    return Rx @ Ry @ Rz
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+def plain_small(seed: int = 7):
+    """4,096 Gaussians in [-1,1]^3, log-scales N(-3.5, 0.4^2), SH degree 0;
+    one 128x128 camera with f = 120 at distance 3 looking at the origin
+    (R = I, t = (0,0,3)); a seeded U[0,1] target image."""
+    sc = random_scene(4096, seed, 0, (-1, -1, -1), (1, 1, 1), -3.5, 0.4)
+    cam = Camera(np.eye(3, dtype=np.float32), np.array([0, 0, 3], np.float32),
+                 120.0, 120.0, 64.0, 64.0, 128, 128)
+    target = _rng(seed + 1).random((3, 128, 128)).astype(np.float32)
+    return sc, [cam], [target]
+
+
+def box_scene(n: int, seed: int, sh_degree: int = 3) -> Scene:
+    """Gaussians in a 20 x 5 x 20 m box (y is the 5 m vertical), log-scales
+    N(-4, 0.5^2), SH degree 3 with higher bands N(0, 0.05^2)."""
+    return random_scene(n, seed, sh_degree, (-10, -2.5, -10), (10, 2.5, 10), -4.0, 0.5)
+
+
+def forward_trajectory(n_poses: int, seed: int, width: int = 1280, height: int = 720,
+                       f: float = 1000.0) -> List[Camera]:
+    """Poses moving along +z from z = -9 to z = +9 looking +z, jittered by
+    N(0, 0.02 m) in position and N(0, 0.5 deg) per rotation axis."""
+    g = _rng(seed)
+    cams = []
+    zs = np.linspace(-9.0, 9.0, n_poses) if n_poses > 1 else np.array([-9.0])
+    for z in zs:
+        eye = np.array([0.0, 0.0, z]) + g.normal(0.0, 0.02, 3)
+        R = _small_rotation(g, 0.5)
+        t = -R @ eye
+        cams.append(Camera(R.astype(np.float32), t.astype(np.float32), f, f,
+                           width / 2.0, height / 2.0, width, height))
+    return cams
+
+
+def diffcheck(seed: int = 2007):
+    """256 Gaussians in [-0.5,0.5]^3, log-scales N(-2.5, 0.3^2), SH degree 3;
+    three 64x64 views, f = 60, on a 30 degree arc at distance 2.5 looking at
+    the origin; a seeded U[0,1] target per view."""
+    sc = random_scene(256, seed, 3, (-0.5, -0.5, -0.5), (0.5, 0.5, 0.5), -2.5, 0.3)
+    cams = []
+    for a in np.deg2rad([-15.0, 0.0, 15.0]):
+        eye = (2.5 * np.sin(a), 0.0, -2.5 * np.cos(a))
+        cams.append(look_at(eye, (0, 0, 0), 60.0, 60.0, 32.0, 32.0, 64, 64))
+    g = _rng(seed + 1)
+    targets = [g.random((3, 64, 64)).astype(np.float32) for _ in cams]
+    return sc, cams, targets
+
+
+RESOLUTIONS = ((960, 540), (1280, 720), (1600, 900), (1920, 1080))
+
+
+def loop_views(n_views: int, seed: int, radius: float = 12.0, height: float = -1.5):
+    """Inward-facing loop of radius 12 m at height 1.5 m (y = -1.5, y points
+    down) looking at the centre; each view's resolution drawn from 540p-1080p,
+    f = 0.78 W."""
+    g = _rng(seed)
+    cams = []
+    for k in range(n_views):
+        a = 2.0 * np.pi * k / n_views
+        w, h = RESOLUTIONS[int(g.integers(0, len(RESOLUTIONS)))]
+        eye = (radius * np.sin(a), height, -radius * np.cos(a))
+        f = 0.78 * w
+        cams.append(look_at(eye, (0, 0, 0), f, f, w / 2.0, h / 2.0, w, h))
+    return cams
+
+
+def perturbed(sc: Scene, seed: int, sigma: float = 0.01) -> Scene:
+    """Copy of a scene with means moved by N(0, sigma^2): used to render
+    targets that carry structure."""
+    out = sc.copy()
+    out.means = (out.means + _rng(seed).normal(0.0, sigma, out.means.shape)).astype(np.float32)
+    return out
+
+
+def random_records(views: Sequence[tuple], n: int, seed: int, tie_levels: int = 0):
+    """Synthetic per-(view, Gaussian) bin inputs for the binning stage alone:
+    positive depths (as float32), tile rects inside each view's tile grid and a
+    culled share.  `views` holds (tiles_x, tiles_y).  With tie_levels > 0 the
+    depths take only that many distinct values, forcing key ties."""
+    g = _rng(seed)
+    V = len(views)
+    depth = np.zeros((V, n), np.float32)
+    rect = np.zeros((V, n, 4), np.int32)
+    for v, (tx, ty) in enumerate(views):
+        if tie_levels > 0:
+            levels = (0.2 + 50.0 * g.random(tie_levels)).astype(np.float32)
+            depth[v] = levels[g.integers(0, tie_levels, n)]
+        else:
+            depth[v] = (0.2 + 50.0 * g.random(n) ** 2).astype(np.float32)
+        # footprints: mostly 1-3 tiles wide, a heavy tail of large ones
+        wx = np.minimum(tx, g.geometric(0.55, n) + (g.random(n) < 0.01) * g.integers(0, tx, n))
+        wy = np.minimum(ty, g.geometric(0.55, n) + (g.random(n) < 0.01) * g.integers(0, ty, n))
+        x0 = g.integers(0, tx, n)
+        y0 = g.integers(0, ty, n)
+        x1 = np.minimum(tx - 1, x0 + wx - 1)
+        y1 = np.minimum(ty - 1, y0 + wy - 1)
+        culled = g.random(n) < 0.3
+        rect[v, :, 0] = np.where(culled, 1, x0)
+        rect[v, :, 1] = np.where(culled, 1, y0)
+        rect[v, :, 2] = np.where(culled, 0, x1)
+        rect[v, :, 3] = np.where(culled, 0, y1)
+    return depth, rect
