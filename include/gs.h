@@ -1,0 +1,300 @@
+/*
+ * gs.h -- C ABI of the B300 differentiable 3D Gaussian-splat rasterizer.
+ *
+ * The operation is the renderer that the paper's joint optimisation runs every
+ * iteration (Sec. 5.2: the Gaussian model is trained for 30 iterations per
+ * keyframe with a custom differentiable splat renderer, render -> loss ->
+ * optimise), split into the calls a training step makes:
+ *
+ *   gs_project     EWA projection + SH colour of every (view, Gaussian)
+ *   gs_bin_sort    per-tile duplication and (tile, depth) sort, tile ranges
+ *   gs_render_fwd  front-to-back alpha compositing per 16x16 tile
+ *   gs_render_bwd  analytic backward to all parameters and the camera poses
+ *   gs_adam_step   fused Adam over the parameter arena (+ optional pose step)
+ *
+ * The primitive (Sec. 7: position, opacity, rotation, scale, SH coefficients)
+ * and the renderer's fixed rules are those of the standard 3DGS rasterizer:
+ * 2D covariance dilated by 0.3 px^2, alpha = min(0.99, o exp(power)), splats
+ * with alpha < 1/255 skipped, compositing stopped before the splat that would
+ * bring transmittance below 1e-4.  Readings where the paper is silent:
+ *   - OpenCV camera axes; pose = world->camera [R | t]; centre = -R^T t;
+ *   - pixel (u,v) has centre (u+1/2, v+1/2), principal point in the same units;
+ *   - culled when t_z <= znear;
+ *   - support half-width r = ceil(3 sqrt(lambda_max)); a splat touches a pixel
+ *     only when the pixel centre lies in [m-r, m+r]^2, so the image does not
+ *     depend on the tile shape;
+ *   - real SH without Condon-Shortley phase, k = l^2 + l + m,
+ *     rgb = max(0, sum_k c_k Y_k(dir) + 1/2), dir from the camera centre;
+ *   - quaternion (w,x,y,z), normalised inside the forward;
+ *   - pose gradient for the left perturbation T <- Exp(xi) T, xi = (v, omega);
+ *   - equal (tile, depth) keys keep Gaussian-id order.
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev or documented as device memory are device pointers
+ *     owned by the caller; the library never frees them.  Host pointers are
+ *     read during the call only.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream); no call synchronises the stream.
+ *   - A call returns GS_OK once its kernels are enqueued.  Argument errors
+ *     return GS_ERR_INVALID and enqueue nothing; a failing CUDA call returns
+ *     GS_ERR_CUDA.  gs_last_error() gives the message of the calling thread's
+ *     last failure.
+ *   - Conditions only the device can see (pair capacity exceeded, non-finite
+ *     gradient) are recorded in the caller's status words (gs_bins.counts and
+ *     gs_adam_cfg.status), read by the caller after the stream completes.
+ *   - Float arithmetic is IEEE single precision except where stated.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+typedef int gs_status;
+#define GS_OK 0
+#define GS_ERR_INVALID 1  /* bad argument: nothing was enqueued */
+#define GS_ERR_OOM 2      /* workspace smaller than the size query returned */
+#define GS_ERR_CUDA 3     /* a CUDA runtime call failed */
+#define GS_ERR_TIMEOUT 4  /* a bounded device wait expired */
+#define GS_ERR_NONFINITE 5
+#define GS_ERR_BUSY 6
+
+#define GS_MAX_VIEWS 64   /* views per call */
+#define GS_TILE 16        /* tile edge in pixels (16x16 tiles) */
+
+typedef void* gs_stream;  /* cudaStream_t */
+
+/* Gaussian parameters, device memory, structure of arrays:
+ *   means4    [n][4]  x, y, z, (ignored)
+ *   scale_opa [n][4]  log-scale x, y, z, opacity logit (opacity = sigmoid)
+ *   quat      [n][4]  w, x, y, z (any non-zero norm; normalised inside)
+ *   sh        [3*nc][n] planar: plane (channel*nc + k) holds coefficient k of
+ *             that colour channel for every Gaussian; nc = (sh_degree+1)^2
+ * All four base pointers must be 16-byte aligned. */
+typedef struct {
+  const float* means4;
+  const float* scale_opa;
+  const float* quat;
+  const float* sh;
+  int64_t n;
+  int32_t sh_degree; /* 0..3 */
+} gs_params;
+
+/* Gradients in exactly the layout of gs_params (the ignored 4th component of
+ * means4 receives 0). */
+typedef struct {
+  float* means4;
+  float* scale_opa;
+  float* quat;
+  float* sh;
+  int64_t n;
+  int32_t sh_degree;
+} gs_grads;
+
+/* Intrinsics and image size of one view, host memory. */
+typedef struct {
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} gs_camera;
+
+typedef struct {
+  int32_t tile_w, tile_h; /* must be GS_TILE x GS_TILE */
+  float bg[3];            /* background colour behind the last splat */
+  float znear;            /* near plane (> 0) */
+  int32_t clamp_jacobian; /* 1: guard t_x/t_z, t_y/t_z at +-1.3 (W/2)/fx, (H/2)/fy */
+} gs_raster_cfg;
+
+/* Projected splats of V views, device memory, each array [V][n] (view-major):
+ *   xy       float4  m = (x_int + x_frac, y_int + y_frac): the pixel-space
+ *                    mean split into an integer part and a fraction in [0,1),
+ *                    computed in double-single arithmetic so that it is
+ *                    accurate to ~1e-6 px at any image size
+ *   conic    float4  A, B, C of the inverse 2D covariance, opacity
+ *   rgb      float4  r, g, b, support half-width r (integer valued)
+ *   depth    float   camera-space z, correctly rounded (the sort key)
+ *   rect     uint2   (x_lo | y_lo << 16, x_hi | y_hi << 16): inclusive tiles
+ *   touched  uint32  tiles in rect; 0 = culled
+ *   aux      uint32  bits 0-2: rgb channel clamped at 0; bit 3/4: Jacobian
+ *                    guard active in x/y
+ * Size in bytes of all arrays together: gs_splats_bytes(). */
+typedef struct {
+  float* xy;
+  float* conic;
+  float* rgb;
+  float* depth;
+  uint32_t* rect;
+  uint32_t* touched;
+  uint32_t* aux;
+  int64_t n;
+  int32_t views;
+} gs_splats;
+
+/* Sorted tile lists, device memory:
+ *   vals      [capacity] Gaussian id of each (tile, Gaussian) pair, ordered by
+ *             (global tile, depth, Gaussian id)
+ *   ranges    [num_tiles][2] [start, end) of each global tile in vals; global
+ *             tile = sum of the tile counts of earlier views + ty*TX + tx
+ *   pair_off  [V][n] position of the first pair of each (view, Gaussian) in
+ *             emission order (pairs of one Gaussian are contiguous there)
+ *   keys      optional [capacity] (global tile << 32 | depth bits), sorted;
+ *             NULL = not written
+ *   counts    [4] status words written by the device: [0] visible
+ *             (view, Gaussian) items, [1] pairs K, [2] 1 if K > capacity (the
+ *             lists are then truncated and must not be rendered), [3]
+ *             min(K, capacity) */
+typedef struct {
+  uint32_t* vals;
+  uint32_t* ranges;
+  uint32_t* pair_off;
+  uint64_t* keys;
+  uint32_t* counts;
+  int64_t capacity;
+  int64_t num_tiles;
+} gs_bins;
+
+/* One Adam parameter group: elements [begin, end) of the arena; element e
+ * uses learning rate lr[(e - begin) & 3] (so one float4 group can give its
+ * four lanes different rates, e.g. log-scales and the opacity logit). */
+typedef struct {
+  int64_t begin, end;
+  float lr[4];
+} gs_adam_group;
+
+#define GS_MAX_ADAM_GROUPS 16
+
+typedef struct {
+  const gs_adam_group* groups; /* host array */
+  int32_t num_groups;          /* 1..GS_MAX_ADAM_GROUPS */
+  float beta1, beta2, eps;
+  uint32_t* status;            /* optional device word: set to 1 when a
+                                  non-finite gradient or moment is met */
+  /* optional pose step (pose == NULL: skipped): Adam on the twist xi of each
+   * view, then pose <- Exp(xi) pose */
+  float* pose;                 /* [V][12] device, [R | t] row-major */
+  const float* dpose;          /* [V][6] device, (v, omega) */
+  float* pose_m;               /* [V][6] device */
+  float* pose_v;               /* [V][6] device */
+  int32_t views;
+  float pose_lr;
+  int32_t pose_step;           /* bias-correction step of the pose moments
+                                  (0 = the parameters' step) */
+} gs_adam_cfg;
+
+/* ---------------------------------------------------------------------- */
+
+/* Message of the calling thread's last failing call ("" if none).  Copies at
+ * most len-1 bytes and a terminating NUL into buf; returns the full length. */
+GS_API size_t gs_last_error(char* buf, size_t len);
+
+/* Library version and the compute capability it was built for. */
+GS_API int32_t gs_version(void);
+GS_API int32_t gs_built_arch(void);
+
+/* Bytes of the gs_splats arrays for n Gaussians and V views, laid out by
+ * gs_splats_carve in one allocation (every array 256-byte aligned). */
+GS_API size_t gs_splats_bytes(int64_t n, int32_t views);
+/* Fill `out` with pointers into `base` (device, >= gs_splats_bytes, 256-byte
+ * aligned). */
+GS_API gs_status gs_splats_carve(void* base, int64_t n, int32_t views, gs_splats* out);
+
+/* EWA projection (Sec. 5.2's renderer, per-Gaussian stage) of n Gaussians into
+ * V views.  poses_dev [V][12] device ([R | t], world->camera); cams host [V].
+ * Per (view, Gaussian): t = R mu + t_cam (double-single); culled if
+ * t_z <= znear; Sigma = Rq diag(e^{2s}) Rq^T; 2D covariance
+ * J R Sigma R^T J^T + 0.3 I; conic = its inverse; r = ceil(3 sqrt(lambda_max));
+ * tile rect of [m-r, m+r]^2; colour from SH at dir = normalise(mu - centre).
+ * Writes every field of `out` for every (view, Gaussian). */
+GS_API gs_status gs_project(const gs_params* params, const float* poses_dev, const gs_camera* cams,
+                     int32_t views, const gs_raster_cfg* cfg, gs_splats* out, gs_stream stream);
+
+/* Workspace bytes of gs_bin_sort. */
+GS_API size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity);
+
+/* Tile binning: every visible (view, Gaussian) emits one pair per tile of its
+ * rect; pairs are sorted by (global tile, depth bits) with equal keys in
+ * Gaussian-id order, and each tile's [start, end) range is written.  The sort
+ * is two stable LSD radix sorts written for this library: depth keys of the
+ * visible items (32 bits), then the emitted pairs by global tile (only the
+ * significant tile bits).  No host synchronisation: K stays on the device
+ * (counts).  ws: device, >= gs_bin_sort_workspace bytes, 256-byte aligned. */
+GS_API gs_status gs_bin_sort(const gs_splats* splats, const gs_camera* cams, int32_t views,
+                      const gs_raster_cfg* cfg, gs_bins* out, void* ws, size_t ws_bytes,
+                      gs_stream stream);
+
+/* Forward compositing, one CTA per 16x16 tile: per pixel, splats in list
+ * order; skip when the centre is outside [m-r, m+r]^2, power > 0 or
+ * alpha < 1/255; stop before a splat that would make T < 1e-4;
+ * C += rgb alpha T; image = C + T bg.
+ * image: device, views concatenated, each [3][H][W]; alpha (optional):
+ * device, each [H][W], 1 - final transmittance. */
+GS_API gs_status gs_render_fwd(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
+                        int32_t views, const gs_raster_cfg* cfg, float* image, float* alpha,
+                        gs_stream stream);
+
+/* Workspace bytes of gs_render_bwd. */
+GS_API size_t gs_render_bwd_workspace(int64_t n, int32_t views, int64_t capacity);
+
+/* Backward of gs_project + gs_render_fwd for the loss gradients dL_dimage
+ * (layout of image) and optional dL_dalpha (layout of alpha).  Per pixel the
+ * forward pass is replayed to recover the final transmittance and the last
+ * blended splat (no per-pixel state is stored), then splats are walked back to
+ * front recovering T_i = T_{i+1} / (1 - alpha_i).  Per (tile, splat) the
+ * gradients of m, conic, opacity and rgb are reduced over the tile's pixels by
+ * warp shuffles and shared memory (no global atomics) and stored per pair;
+ * a per-Gaussian pass sums its pairs in a fixed order and applies the chain
+ * rule to every parameter and the camera pose.  Deterministic: equal inputs
+ * give bit-identical outputs.  grads: overwritten (all n Gaussians).
+ * dL_dpose (optional): [V][6] device, (v, omega), overwritten. */
+GS_API gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const gs_camera* cams,
+                        int32_t views, const gs_splats* splats, const gs_bins* bins,
+                        const gs_raster_cfg* cfg, const float* dL_dimage, const float* dL_dalpha,
+                        gs_grads* grads, float* dL_dpose, void* ws, size_t ws_bytes,
+                        gs_stream stream);
+
+/* The two halves of gs_render_bwd, for callers that time or overlap them:
+ * gs_render_bwd_pixels runs the per-tile pass and leaves the per-pair
+ * gradients in ws; gs_render_bwd_gaussians then applies the per-Gaussian
+ * pass.  Calling them in this order with the same arguments is exactly
+ * gs_render_bwd. */
+GS_API gs_status gs_render_bwd_pixels(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
+                                      int32_t views, const gs_raster_cfg* cfg, const float* dL_dimage,
+                                      const float* dL_dalpha, int64_t n, void* ws, size_t ws_bytes,
+                                      gs_stream stream);
+GS_API gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_dev,
+                                         const gs_camera* cams, int32_t views, const gs_splats* splats,
+                                         const gs_bins* bins, const gs_raster_cfg* cfg, gs_grads* grads,
+                                         float* dL_dpose, void* ws, size_t ws_bytes, gs_stream stream);
+
+/* Fused Adam over one flat float arena of n elements (parameters p, gradients
+ * g, moments m, v; all device, 16-byte aligned):
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps)
+ * Elements outside every group are left unchanged.  step >= 1. */
+GS_API gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
+                       const gs_adam_cfg* cfg, int32_t step, gs_stream stream);
+
+/* Image loss of a training step over `count` floats (all views' images):
+ * kind 0 = L1, mean |image - target|; kind 1 = mean squared error.  The paper
+ * names its rendering loss without defining it; these are the two readings
+ * offered.  Writes the loss to *loss_dev (device float) and, if dL_dimage is
+ * not NULL, its gradient (same layout as image).  ws: device, >=
+ * gs_image_loss_workspace() bytes, 256-byte aligned.  Deterministic. */
+GS_API size_t gs_image_loss_workspace(void);
+GS_API gs_status gs_image_loss(const float* image, const float* target, int64_t count, int32_t kind,
+                               float* dL_dimage, float* loss_dev, void* ws, size_t ws_bytes,
+                               gs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

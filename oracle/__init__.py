@@ -30,11 +30,11 @@ def lib():
         u32 = C.POINTER(C.c_uint32)
         u64 = C.POINTER(C.c_uint64)
         L.orc_sh_basis.argtypes = [C.c_int, C.c_int64, d, d]
-        L.orc_render.argtypes = [C.c_int64, C.c_int, d, d, d, d, d, C.c_int, d, d, i32, C.c_double,
+        L.orc_render.argtypes = [C.c_int64, C.c_int, d, d, d, d, d, C.c_int, d, d, i32, i32, C.c_double,
                                  C.c_int, C.c_int, d, C.c_int, d, d, d, u8, d]
         L.orc_render_dual.argtypes = [C.c_int64, C.c_int, d, d, d, d, d, d, d, d, d, d, C.c_int, d, d,
-                                      d, i32, C.c_double, C.c_int, C.c_int, d, C.c_int, d, d, d]
-        L.orc_backward.argtypes = [C.c_int64, C.c_int, d, d, d, d, d, C.c_int, d, d, i32, C.c_double,
+                                      d, i32, i32, C.c_double, C.c_int, C.c_int, d, C.c_int, d, d, d]
+        L.orc_backward.argtypes = [C.c_int64, C.c_int, d, d, d, d, d, C.c_int, d, d, i32, i32, C.c_double,
                                    C.c_int, C.c_int, d, C.c_int, d, d, d, d, d, d, d, d]
         L.orc_bin.argtypes = [C.c_int, C.c_int64, u32, i32, i32, C.c_int64, u64, u32, u32]
         L.orc_bin.restype = C.c_int64
@@ -59,7 +59,7 @@ PROJ_FIELDS = ("vis", "mx", "my", "A", "B", "C", "opacity", "r", "g", "b", "dept
 
 
 class _Inputs:
-    def __init__(self, scene, cams, znear, tile, bg, clamp_j):
+    def __init__(self, scene, cams, znear, tile, bg, clamp_j, windows=None):
         self.N = scene.n
         self.deg = scene.sh_degree
         self.means = _f64(scene.means)
@@ -76,23 +76,33 @@ class _Inputs:
         self.bg = _f64(bg)
         self.clamp_j = int(bool(clamp_j))
         self.cams = cams
+        if windows is None:
+            self.win = None
+            self.sizes = [(c.width, c.height) for c in cams]
+        else:
+            self.win = np.ascontiguousarray(np.array(windows, np.int32).reshape(self.V, 4))
+            for c, w in zip(cams, self.win):
+                assert 0 <= w[0] and 0 <= w[1] and w[2] > 0 and w[3] > 0
+                assert w[0] + w[2] <= c.width and w[1] + w[3] <= c.height
+            self.sizes = [(int(w[2]), int(w[3])) for w in self.win]
+
+    def win_ptr(self):
+        return _p(self.win, C.c_int32) if self.win is not None else None
+
+    def npix(self) -> int:
+        return int(sum(w * h for w, h in self.sizes))
 
     def scene_args(self):
         return (self.N, self.deg, _p(self.means), _p(self.lsc), _p(self.quat), _p(self.opl), _p(self.sh))
 
     def split_views(self, flat: np.ndarray, per_pixel: int) -> List[np.ndarray]:
         out, off = [], 0
-        for c in self.cams:
-            n = per_pixel * c.width * c.height
+        for w, h in self.sizes:
+            n = per_pixel * w * h
             a = flat[off:off + n]
-            out.append(a.reshape((per_pixel, c.height, c.width)) if per_pixel > 1
-                       else a.reshape((c.height, c.width)))
+            out.append(a.reshape((per_pixel, h, w)) if per_pixel > 1 else a.reshape((h, w)))
             off += n
         return out
-
-
-def _npix(cams) -> int:
-    return int(sum(c.width * c.height for c in cams))
 
 
 def sh_basis(degree: int, dirs) -> np.ndarray:
@@ -106,20 +116,21 @@ def sh_basis(degree: int, dirs) -> np.ndarray:
 
 
 def render(scene, cams, znear=0.2, tile=(16, 16), bg=(0.0, 0.0, 0.0), clamp_j=True,
-           margins: Optional[Sequence[float]] = None, want_proj=False) -> Dict:
+           margins: Optional[Sequence[float]] = None, want_proj=False, windows=None) -> Dict:
     """Forward render.  Returns image (list of [3,H,W]), alpha (list of [H,W]),
     flags (list of [H,W] uint8: bit 0 = the image value depends on a decision
     within margin, bit 1 = its derivative does) and optionally proj
-    [V,N,len(PROJ_FIELDS)]."""
-    a = _Inputs(scene, cams, znear, tile, bg, clamp_j)
-    P = _npix(cams)
+    [V,N,len(PROJ_FIELDS)].  windows: optional per-view (x0, y0, w, h) pixel
+    windows; the outputs then cover the windows only."""
+    a = _Inputs(scene, cams, znear, tile, bg, clamp_j, windows)
+    P = a.npix()
     img = np.zeros(3 * P)
     alpha = np.zeros(P)
     flags = np.zeros(P, np.uint8)
     proj = np.zeros((a.V, a.N, len(PROJ_FIELDS))) if want_proj else None
     mg = _f64(margins) if margins is not None else None
-    rc = lib().orc_render(*a.scene_args(), a.V, _p(a.poses), _p(a.intr), _p(a.wh, C.c_int32), a.znear,
-                          a.tw, a.th, _p(a.bg), a.clamp_j, _p(mg) if mg is not None else None,
+    rc = lib().orc_render(*a.scene_args(), a.V, _p(a.poses), _p(a.intr), _p(a.wh, C.c_int32), a.win_ptr(),
+                          a.znear, a.tw, a.th, _p(a.bg), a.clamp_j, _p(mg) if mg is not None else None,
                           _p(img), _p(alpha), _p(flags, C.c_uint8),
                           _p(proj) if proj is not None else None)
     assert rc == 0
@@ -131,19 +142,20 @@ def render(scene, cams, znear=0.2, tile=(16, 16), bg=(0.0, 0.0, 0.0), clamp_j=Tr
 
 
 def backward(scene, cams, dimage: Sequence[np.ndarray], dalpha: Optional[Sequence[np.ndarray]] = None,
-             znear=0.2, tile=(16, 16), bg=(0.0, 0.0, 0.0), clamp_j=True) -> Dict:
+             znear=0.2, tile=(16, 16), bg=(0.0, 0.0, 0.0), clamp_j=True, windows=None) -> Dict:
     """Analytic FP64 gradients of sum(dimage * image) + sum(dalpha * alpha)
     w.r.t. every parameter (natural layout) and every pose ([V,6], (v, omega)
-    of the left perturbation T <- Exp(xi) T)."""
-    a = _Inputs(scene, cams, znear, tile, bg, clamp_j)
+    of the left perturbation T <- Exp(xi) T).  With windows, dimage/dalpha
+    cover the windows and the loss gradient is zero outside them."""
+    a = _Inputs(scene, cams, znear, tile, bg, clamp_j, windows)
     di = _f64(np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in dimage]))
     da = (_f64(np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in dalpha]))
           if dalpha is not None else None)
     N, nc = a.N, (a.deg + 1) ** 2
     g = {"means": np.zeros((N, 3)), "log_scales": np.zeros((N, 3)), "quats": np.zeros((N, 4)),
          "opa_logits": np.zeros(N), "sh": np.zeros((N, 3, nc)), "pose": np.zeros((a.V, 6))}
-    rc = lib().orc_backward(*a.scene_args(), a.V, _p(a.poses), _p(a.intr), _p(a.wh, C.c_int32), a.znear,
-                            a.tw, a.th, _p(a.bg), a.clamp_j, _p(di), _p(da) if da is not None else None,
+    rc = lib().orc_backward(*a.scene_args(), a.V, _p(a.poses), _p(a.intr), _p(a.wh, C.c_int32), a.win_ptr(),
+                            a.znear, a.tw, a.th, _p(a.bg), a.clamp_j, _p(di), _p(da) if da is not None else None,
                             _p(g["means"]), _p(g["log_scales"]), _p(g["quats"]), _p(g["opa_logits"]),
                             _p(g["sh"]), _p(g["pose"]))
     assert rc == 0
@@ -151,21 +163,21 @@ def backward(scene, cams, dimage: Sequence[np.ndarray], dalpha: Optional[Sequenc
 
 
 def render_dual(scene, tangent: Dict[str, np.ndarray], pose_tangent: np.ndarray, cams, znear=0.2,
-                tile=(16, 16), bg=(0.0, 0.0, 0.0), clamp_j=True) -> Dict:
+                tile=(16, 16), bg=(0.0, 0.0, 0.0), clamp_j=True, windows=None) -> Dict:
     """Forward render on dual numbers.  `tangent` holds arrays shaped like the
     scene's (keys means, log_scales, quats, opa_logits, sh); pose_tangent is
     [V,6] (v, omega).  Returns image values and their exact directional
     derivatives (lists of [3,H,W]) and the alpha derivative."""
-    a = _Inputs(scene, cams, znear, tile, bg, clamp_j)
+    a = _Inputs(scene, cams, znear, tile, bg, clamp_j, windows)
     t = {k: _f64(tangent[k]) for k in ("means", "log_scales", "quats", "opa_logits", "sh")}
     tp = _f64(pose_tangent).reshape(a.V, 6)
-    P = _npix(cams)
+    P = a.npix()
     img = np.zeros(3 * P)
     img_t = np.zeros(3 * P)
     al_t = np.zeros(P)
     rc = lib().orc_render_dual(*a.scene_args(), _p(t["means"]), _p(t["log_scales"]), _p(t["quats"]),
                                _p(t["opa_logits"]), _p(t["sh"]), a.V, _p(a.poses), _p(tp), _p(a.intr),
-                               _p(a.wh, C.c_int32), a.znear, a.tw, a.th, _p(a.bg), a.clamp_j,
+                               _p(a.wh, C.c_int32), a.win_ptr(), a.znear, a.tw, a.th, _p(a.bg), a.clamp_j,
                                _p(img), _p(img_t), _p(al_t))
     assert rc == 0
     return {"image": a.split_views(img, 3), "image_tan": a.split_views(img_t, 3),

@@ -141,6 +141,7 @@ struct View {
   double fx, fy, cx, cy;
   int W, H;
   int TX, TY;    // tiles
+  int wx0, wy0, ww, wh;  // composited pixel window (the whole image by default)
 };
 
 struct Cfg {
@@ -367,9 +368,9 @@ struct Blended {
 
 template <class S>
 struct ViewOut {
-  S* image;        // [3][H][W]
-  S* alpha;        // [H][W]
-  uint8_t* flags;  // [H][W] or null
+  S* image;        // [3][wh][ww] (the view's pixel window)
+  S* alpha;        // [wh][ww]
+  uint8_t* flags;  // [wh][ww] or null
 };
 
 // One view: project, bin (by FP64 depth), composite.
@@ -402,11 +403,12 @@ void render_view(const Scene& sc, const Scene* tg, const View<S>& vw, const Cfg&
   const double a_min = 1.0 / 255.0, t_min = 1e-4;
   std::vector<Blended> bl;
 
+  const int wx1 = vw.wx0 + vw.ww, wy1 = vw.wy0 + vw.wh;
   for (int ty = 0; ty < vw.TY; ++ty)
     for (int tx = 0; tx < vw.TX; ++tx) {
       const std::vector<int64_t>& lst = tiles[(size_t)ty * vw.TX + tx];
-      for (int py = ty * cf.th; py < std::min(vw.H, (ty + 1) * cf.th); ++py)
-        for (int px = tx * cf.tw; px < std::min(vw.W, (tx + 1) * cf.tw); ++px) {
+      for (int py = std::max(vw.wy0, ty * cf.th); py < std::min(wy1, (ty + 1) * cf.th); ++py)
+        for (int px = std::max(vw.wx0, tx * cf.tw); px < std::min(wx1, (tx + 1) * cf.tw); ++px) {
           const double pcx = px + 0.5, pcy = py + 0.5;
           S T = S(1.0);
           S Cc[3] = {S(0.0), S(0.0), S(0.0)};
@@ -446,8 +448,8 @@ void render_view(const Scene& sc, const Scene* tg, const View<S>& vw, const Cfg&
             if (record) bl.push_back({i, val(al), val(T), val(ex), val(dx), val(dy), clamped});
             T = Tn;
           }
-          const size_t pix = (size_t)py * vw.W + px;
-          for (int ch = 0; ch < 3; ++ch) out.image[(size_t)ch * vw.W * vw.H + pix] = Cc[ch] + T * S(cf.bg[ch]);
+          const size_t pix = (size_t)(py - vw.wy0) * vw.ww + (px - vw.wx0);
+          for (int ch = 0; ch < 3; ++ch) out.image[(size_t)ch * vw.ww * vw.wh + pix] = Cc[ch] + T * S(cf.bg[ch]);
           if (out.alpha) out.alpha[pix] = S(1.0) - T;
           if (out.flags) out.flags[pix] = fl;
           if (record) on_pixel(pix, bl, val(T));
@@ -455,13 +457,10 @@ void render_view(const Scene& sc, const Scene* tg, const View<S>& vw, const Cfg&
     }
 }
 
-template <class S>
-void load_views(int V, const double* poses, const double* tposes, const double* intr,
-                const int32_t* wh, const Cfg& cf, std::vector<View<S>>& views);
-
-template <>
-void load_views<double>(int V, const double* poses, const double*, const double* intr,
-                        const int32_t* wh, const Cfg& cf, std::vector<View<double>>& views) {
+// Views from [V][12] poses, [V][4] intrinsics, [V][2] sizes and optional
+// [V][4] pixel windows (x0, y0, w, h).
+void load_views(int V, const double* poses, const double* intr, const int32_t* wh,
+                const int32_t* win, const Cfg& cf, std::vector<View<double>>& views) {
   views.resize(V);
   for (int v = 0; v < V; ++v) {
     View<double>& w = views[v];
@@ -472,17 +471,22 @@ void load_views<double>(int V, const double* poses, const double*, const double*
     w.fx = intr[4 * v]; w.fy = intr[4 * v + 1]; w.cx = intr[4 * v + 2]; w.cy = intr[4 * v + 3];
     w.W = wh[2 * v]; w.H = wh[2 * v + 1];
     w.TX = (w.W + cf.tw - 1) / cf.tw; w.TY = (w.H + cf.th - 1) / cf.th;
+    if (win) {
+      w.wx0 = win[4 * v]; w.wy0 = win[4 * v + 1]; w.ww = win[4 * v + 2]; w.wh = win[4 * v + 3];
+    } else {
+      w.wx0 = 0; w.wy0 = 0; w.ww = w.W; w.wh = w.H;
+    }
   }
 }
 
 // Dual views: the pose moves along T(eps) = Exp(eps xi) T, xi = (v, omega) given
 // per view in `tposes` [V][6].  To first order R(eps) = R + eps [omega]x R and
 // tau(eps) = tau + eps ([omega]x tau + v), which is exact for dual numbers.
-template <>
-void load_views<Dual>(int V, const double* poses, const double* tposes, const double* intr,
-                      const int32_t* wh, const Cfg& cf, std::vector<View<Dual>>& views) {
+void load_dual_views(int V, const double* poses, const double* tposes, const double* intr,
+                     const int32_t* wh, const int32_t* win, const Cfg& cf,
+                     std::vector<View<Dual>>& views) {
   std::vector<View<double>> base;
-  load_views<double>(V, poses, nullptr, intr, wh, cf, base);
+  load_views(V, poses, intr, wh, win, cf, base);
   views.resize(V);
   for (int v = 0; v < V; ++v) {
     const double* xi = tposes + 6 * v;
@@ -501,6 +505,7 @@ void load_views<Dual>(int V, const double* poses, const double* tposes, const do
       w.tau[r] = Dual(b.tau[r], d);
     }
     w.fx = b.fx; w.fy = b.fy; w.cx = b.cx; w.cy = b.cy; w.W = b.W; w.H = b.H; w.TX = b.TX; w.TY = b.TY;
+    w.wx0 = b.wx0; w.wy0 = b.wy0; w.ww = b.ww; w.wh = b.wh;
   }
 }
 
@@ -768,27 +773,30 @@ static void write_proj(const Proj<double>& p, double* o) {
   o[16] = p.clampbits; o[17] = p.img_amb; o[18] = p.grad_amb; o[19] = p.bin_amb;
 }
 
-// Forward render of V views.  image: views concatenated, each [3][H][W];
-// alpha: each [H][W]; flags (optional): each [H][W], bit 0 = the image value at
+// Forward render of V views.  windows (optional): [V][4] pixel windows
+// (x0, y0, w, h) to composite; the projection and binning always cover the
+// whole view.  image: windows concatenated, each [3][h][w]; alpha: each [h][w];
+// flags (optional): each [h][w], bit 0 = the image value at
 // this pixel hangs on a decision within margin, bit 1 = its derivative does.
 // proj (optional): [V][N][PROJ_STRIDE].
 int orc_render(int64_t N, int deg, const double* means, const double* lsc, const double* quat,
                const double* opl, const double* sh, int V, const double* poses, const double* intr,
-               const int32_t* wh, double znear, int tw, int th, const double* bg, int clamp_j,
-               const double* margins, double* image, double* alpha, uint8_t* flags, double* proj) {
+               const int32_t* wh, const int32_t* windows, double znear, int tw, int th,
+               const double* bg, int clamp_j, const double* margins, double* image, double* alpha,
+               uint8_t* flags, double* proj) {
   if (N < 0 || deg < 0 || deg > 3 || V <= 0 || tw <= 0 || th <= 0) return 1;
   Scene sc = make_scene(N, deg, means, lsc, quat, opl, sh);
   Cfg cf = make_cfg(znear, tw, th, bg, clamp_j, margins);
   std::vector<View<double>> views;
-  load_views<double>(V, poses, nullptr, intr, wh, cf, views);
+  load_views(V, poses, intr, wh, windows, cf, views);
   size_t off_img = 0, off_px = 0;
   std::vector<Proj<double>> pj;
   for (int v = 0; v < V; ++v) {
     ViewOut<double> o{image + off_img, alpha ? alpha + off_px : nullptr, flags ? flags + off_px : nullptr};
     render_view<double>(sc, nullptr, views[v], cf, pj, o, false, NoPixel());
     if (proj) for (int64_t i = 0; i < N; ++i) write_proj(pj[i], proj + PROJ_STRIDE * (v * N + i));
-    off_img += (size_t)3 * views[v].W * views[v].H;
-    off_px += (size_t)views[v].W * views[v].H;
+    off_img += (size_t)3 * views[v].ww * views[v].wh;
+    off_px += (size_t)views[v].ww * views[v].wh;
   }
   return 0;
 }
@@ -800,18 +808,18 @@ int orc_render_dual(int64_t N, int deg, const double* means, const double* lsc, 
                     const double* opl, const double* sh, const double* t_means, const double* t_lsc,
                     const double* t_quat, const double* t_opl, const double* t_sh, int V,
                     const double* poses, const double* t_pose, const double* intr, const int32_t* wh,
-                    double znear, int tw, int th, const double* bg, int clamp_j, double* image,
-                    double* image_tan, double* alpha_tan) {
+                    const int32_t* windows, double znear, int tw, int th, const double* bg,
+                    int clamp_j, double* image, double* image_tan, double* alpha_tan) {
   if (N < 0 || deg < 0 || deg > 3 || V <= 0) return 1;
   Scene sc = make_scene(N, deg, means, lsc, quat, opl, sh);
   Scene tg = make_scene(N, deg, t_means, t_lsc, t_quat, t_opl, t_sh);
   Cfg cf = make_cfg(znear, tw, th, bg, clamp_j, nullptr);
   std::vector<View<Dual>> views;
-  load_views<Dual>(V, poses, t_pose, intr, wh, cf, views);
+  load_dual_views(V, poses, t_pose, intr, wh, windows, cf, views);
   size_t off_img = 0, off_px = 0;
   std::vector<Proj<Dual>> pj;
   for (int v = 0; v < V; ++v) {
-    size_t np = (size_t)views[v].W * views[v].H;
+    size_t np = (size_t)views[v].ww * views[v].wh;
     std::vector<Dual> img(3 * np), al(np);
     ViewOut<Dual> o{img.data(), al.data(), nullptr};
     render_view<Dual>(sc, &tg, views[v], cf, pj, o, false, NoPixel());
@@ -825,17 +833,19 @@ int orc_render_dual(int64_t N, int deg, const double* means, const double* lsc, 
 
 // Analytic backward: given dL/dimage (same layout as image) and optionally
 // dL/dalpha, accumulate dL/dparams (natural layouts) and dL/dpose [V][6]
-// (v, omega).  Gradient arrays are overwritten.
+// (v, omega).  With windows, dL/dimage covers the windows only (the loss
+// gradient is zero elsewhere).  Gradient arrays are overwritten.
 int orc_backward(int64_t N, int deg, const double* means, const double* lsc, const double* quat,
                  const double* opl, const double* sh, int V, const double* poses, const double* intr,
-                 const int32_t* wh, double znear, int tw, int th, const double* bg, int clamp_j,
-                 const double* dimage, const double* dalpha, double* gmeans, double* glsc,
+                 const int32_t* wh, const int32_t* windows, double znear, int tw, int th,
+                 const double* bg, int clamp_j, const double* dimage, const double* dalpha,
+                 double* gmeans, double* glsc,
                  double* gquat, double* gopl, double* gsh, double* gpose) {
   if (N < 0 || deg < 0 || deg > 3 || V <= 0) return 1;
   Scene sc = make_scene(N, deg, means, lsc, quat, opl, sh);
   Cfg cf = make_cfg(znear, tw, th, bg, clamp_j, nullptr);
   std::vector<View<double>> views;
-  load_views<double>(V, poses, nullptr, intr, wh, cf, views);
+  load_views(V, poses, intr, wh, windows, cf, views);
   const int nc = sc.nc;
   std::memset(gmeans, 0, sizeof(double) * 3 * N);
   std::memset(glsc, 0, sizeof(double) * 3 * N);
@@ -847,7 +857,7 @@ int orc_backward(int64_t N, int deg, const double* means, const double* lsc, con
   std::vector<Proj<double>> pj;
   for (int v = 0; v < V; ++v) {
     const View<double>& vw = views[v];
-    size_t np = (size_t)vw.W * vw.H;
+    size_t np = (size_t)vw.ww * vw.wh;
     std::vector<double> img(3 * np), al(np);
     std::vector<Grad2D> g2(N);
     std::memset(g2.data(), 0, sizeof(Grad2D) * N);

@@ -1,0 +1,130 @@
+"""ctypes binding of include/gs.h (argument marshalling only).
+
+Loads paper_2607_14481_b300/_build/libgs.so.  A missing or unloadable library
+raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgs.so")
+
+GS_OK, GS_ERR_INVALID, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NONFINITE, GS_ERR_BUSY = range(7)
+GS_MAX_VIEWS = 64
+GS_TILE = 16
+GS_MAX_ADAM_GROUPS = 16
+
+EXPORTED = (
+    "gs_last_error", "gs_version", "gs_built_arch", "gs_splats_bytes", "gs_splats_carve",
+    "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_render_fwd",
+    "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
+    "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss",
+)
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, what: str, msg: str):
+        super().__init__(f"{what} failed with status {status}: {msg}")
+        self.status = status
+
+
+class GsParams(C.Structure):
+    _fields_ = [("means4", C.c_void_p), ("scale_opa", C.c_void_p), ("quat", C.c_void_p),
+                ("sh", C.c_void_p), ("n", C.c_int64), ("sh_degree", C.c_int32)]
+
+
+GsGrads = GsParams  # same layout (non-const pointers)
+
+
+class GsCamera(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class GsRasterCfg(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("bg", C.c_float * 3),
+                ("znear", C.c_float), ("clamp_jacobian", C.c_int32)]
+
+
+class GsSplats(C.Structure):
+    _fields_ = [("xy", C.c_void_p), ("conic", C.c_void_p), ("rgb", C.c_void_p), ("depth", C.c_void_p),
+                ("rect", C.c_void_p), ("touched", C.c_void_p), ("aux", C.c_void_p),
+                ("n", C.c_int64), ("views", C.c_int32)]
+
+
+class GsBins(C.Structure):
+    _fields_ = [("vals", C.c_void_p), ("ranges", C.c_void_p), ("pair_off", C.c_void_p),
+                ("keys", C.c_void_p), ("counts", C.c_void_p), ("capacity", C.c_int64),
+                ("num_tiles", C.c_int64)]
+
+
+class GsAdamGroup(C.Structure):
+    _fields_ = [("begin", C.c_int64), ("end", C.c_int64), ("lr", C.c_float * 4)]
+
+
+class GsAdamCfg(C.Structure):
+    _fields_ = [("groups", C.POINTER(GsAdamGroup)), ("num_groups", C.c_int32), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("status", C.c_void_p), ("pose", C.c_void_p),
+                ("dpose", C.c_void_p), ("pose_m", C.c_void_p), ("pose_v", C.c_void_p),
+                ("views", C.c_int32), ("pose_lr", C.c_float), ("pose_step", C.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libgs.so; raises if it is absent or lacks a declared symbol."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgs.so not found at {path}: build it with paper_2607_14481_b300/build.py")
+    L = C.CDLL(path)
+    for name in EXPORTED:
+        if not hasattr(L, name):
+            raise RuntimeError(f"libgs.so lacks symbol {name}")
+    vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+    P = C.POINTER
+    L.gs_last_error.argtypes = [C.c_char_p, sz]
+    L.gs_last_error.restype = sz
+    L.gs_version.restype = i32
+    L.gs_built_arch.restype = i32
+    L.gs_splats_bytes.argtypes = [i64, i32]
+    L.gs_splats_bytes.restype = sz
+    L.gs_splats_carve.argtypes = [vp, i64, i32, P(GsSplats)]
+    L.gs_project.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsRasterCfg), P(GsSplats), vp]
+    L.gs_bin_sort_workspace.argtypes = [i64, i32, i64]
+    L.gs_bin_sort_workspace.restype = sz
+    L.gs_bin_sort.argtypes = [P(GsSplats), P(GsCamera), i32, P(GsRasterCfg), P(GsBins), vp, sz, vp]
+    L.gs_render_fwd.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp, vp]
+    L.gs_render_bwd_workspace.argtypes = [i64, i32, i64]
+    L.gs_render_bwd_workspace.restype = sz
+    L.gs_render_bwd.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsSplats), P(GsBins),
+                                P(GsRasterCfg), vp, vp, P(GsGrads), vp, vp, sz, vp]
+    L.gs_render_bwd_pixels.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp, i64,
+                                       vp, sz, vp]
+    L.gs_render_bwd_gaussians.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsSplats), P(GsBins),
+                                          P(GsRasterCfg), P(GsGrads), vp, vp, sz, vp]
+    L.gs_adam_step.argtypes = [vp, vp, vp, vp, i64, P(GsAdamCfg), i32, vp]
+    L.gs_image_loss_workspace.argtypes = []
+    L.gs_image_loss_workspace.restype = sz
+    L.gs_image_loss.argtypes = [vp, vp, i64, i32, vp, vp, vp, sz, vp]
+    for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
+                 "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    L = load()
+    buf = C.create_string_buffer(1024)
+    L.gs_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def check(status: int, what: str) -> None:
+    if status != GS_OK:
+        raise GsError(status, what, last_error())

@@ -1,0 +1,357 @@
+// C entry points of include/gs.h: argument validation, workspace carving,
+// error reporting.  No entry point allocates device memory or synchronises.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+static thread_local std::string t_last_error;
+
+gs_status fail(gs_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return st;
+}
+
+gs_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return GS_OK;
+}
+
+bool make_view_table(const gs_camera* cams, int views, ViewTable* vt) {
+  if (!cams || views <= 0 || views > GS_MAX_VIEWS) {
+    fail(GS_ERR_INVALID, "views must be in [1, %d] with a camera array", GS_MAX_VIEWS);
+    return false;
+  }
+  std::memset(vt, 0, sizeof(*vt));
+  vt->views = views;
+  int64_t tiles = 0, pix = 0;
+  for (int v = 0; v < views; ++v) {
+    const gs_camera& c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || c.width > 16 * 4096 || c.height > 16 * 4096 ||
+        !(c.fx > 0.f) || !(c.fy > 0.f) || !std::isfinite(c.cx) || !std::isfinite(c.cy)) {
+      fail(GS_ERR_INVALID, "camera %d: bad intrinsics or size", v);
+      return false;
+    }
+    ViewInfo& vi = vt->v[v];
+    vi.fx = c.fx; vi.fy = c.fy; vi.cx = c.cx; vi.cy = c.cy;
+    vi.W = c.width; vi.H = c.height;
+    vi.TX = (c.width + kTile - 1) / kTile;
+    vi.TY = (c.height + kTile - 1) / kTile;
+    vi.tile_base = (int32_t)tiles;
+    vi.pix_base = pix;
+    tiles += (int64_t)vi.TX * vi.TY;
+    pix += (int64_t)c.width * c.height;
+  }
+  if (tiles >= (1ll << 30)) {
+    fail(GS_ERR_INVALID, "too many tiles (%lld)", (long long)tiles);
+    return false;
+  }
+  vt->total_tiles = (int32_t)tiles;
+  return true;
+}
+
+size_t bin_sort_workspace_bytes(int64_t m, int64_t cap);
+gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bins& bins, void* ws,
+                          cudaStream_t s);
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static gs_status check_cfg(const gs_raster_cfg* cfg) {
+  if (!cfg) return fail(GS_ERR_INVALID, "cfg is NULL");
+  if (cfg->tile_w != kTile || cfg->tile_h != kTile)
+    return fail(GS_ERR_INVALID, "tile must be %dx%d (got %dx%d)", kTile, kTile, cfg->tile_w, cfg->tile_h);
+  if (!(cfg->znear > 0.f)) return fail(GS_ERR_INVALID, "znear must be > 0");
+  return GS_OK;
+}
+
+static gs_status check_params(const gs_params* p) {
+  if (!p) return fail(GS_ERR_INVALID, "params is NULL");
+  if (p->n < 0 || p->n >= (1ll << 31)) return fail(GS_ERR_INVALID, "n out of range");
+  if (p->sh_degree < 0 || p->sh_degree > 3) return fail(GS_ERR_INVALID, "sh_degree must be 0..3");
+  if (p->n > 0 && (!p->means4 || !p->scale_opa || !p->quat || !p->sh))
+    return fail(GS_ERR_INVALID, "NULL parameter array");
+  if (!aligned(p->means4, 16) || !aligned(p->scale_opa, 16) || !aligned(p->quat, 16))
+    return fail(GS_ERR_INVALID, "parameter arrays must be 16-byte aligned");
+  return GS_OK;
+}
+
+static gs_status check_splats(const gs_splats* sp, int64_t n, int views) {
+  if (!sp) return fail(GS_ERR_INVALID, "splats is NULL");
+  if (sp->n != n || sp->views != views) return fail(GS_ERR_INVALID, "splats sized for another n/views");
+  if (n > 0 && (!sp->xy || !sp->conic || !sp->rgb || !sp->depth || !sp->rect || !sp->touched || !sp->aux))
+    return fail(GS_ERR_INVALID, "NULL splat array");
+  if (!aligned(sp->xy, 16) || !aligned(sp->conic, 16) || !aligned(sp->rgb, 16) || !aligned(sp->rect, 8))
+    return fail(GS_ERR_INVALID, "splat arrays misaligned");
+  if ((uint64_t)n * (uint64_t)views >= (1ull << 32))
+    return fail(GS_ERR_INVALID, "n * views must be < 2^32");
+  return GS_OK;
+}
+
+static gs_status check_bins(const gs_bins* b, const ViewTable& vt, int64_t n) {
+  if (!b) return fail(GS_ERR_INVALID, "bins is NULL");
+  if (!b->vals || !b->ranges || !b->pair_off || !b->counts) return fail(GS_ERR_INVALID, "NULL bins array");
+  if (b->capacity < 0 || b->capacity >= (1ll << 32) - 1) return fail(GS_ERR_INVALID, "capacity out of range");
+  if (b->num_tiles != vt.total_tiles)
+    return fail(GS_ERR_INVALID, "bins.num_tiles (%lld) != tiles of the views (%d)", (long long)b->num_tiles,
+                vt.total_tiles);
+  (void)n;
+  return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+size_t gs_last_error(char* buf, size_t len) {
+  const std::string& e = t_last_error;
+  if (buf && len > 0) {
+    size_t k = std::min(len - 1, e.size());
+    std::memcpy(buf, e.data(), k);
+    buf[k] = '\0';
+  }
+  return e.size();
+}
+
+int32_t gs_version(void) { return 1; }
+
+int32_t gs_built_arch(void) {
+#ifdef GS_BUILT_ARCH
+  return GS_BUILT_ARCH;
+#else
+  return 0;
+#endif
+}
+
+static size_t splat_layout(int64_t n, int32_t views, char* base, gs_splats* out) {
+  const size_t m = (size_t)std::max<int64_t>(0, n) * (size_t)std::max(0, views);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += align_up(std::max<size_t>(bytes, 1), 256);
+    return p;
+  };
+  float* xy = (float*)take(16 * m);
+  float* conic = (float*)take(16 * m);
+  float* rgb = (float*)take(16 * m);
+  float* depth = (float*)take(4 * m);
+  uint32_t* rect = (uint32_t*)take(8 * m);
+  uint32_t* touched = (uint32_t*)take(4 * m);
+  uint32_t* aux = (uint32_t*)take(4 * m);
+  if (out) {
+    out->xy = xy; out->conic = conic; out->rgb = rgb; out->depth = depth;
+    out->rect = rect; out->touched = touched; out->aux = aux;
+    out->n = n; out->views = views;
+  }
+  return off;
+}
+
+size_t gs_splats_bytes(int64_t n, int32_t views) { return splat_layout(n, views, nullptr, nullptr); }
+
+gs_status gs_splats_carve(void* base, int64_t n, int32_t views, gs_splats* out) {
+  if (!base || !out) return fail(GS_ERR_INVALID, "NULL base or out");
+  if (n < 0 || views <= 0 || views > GS_MAX_VIEWS) return fail(GS_ERR_INVALID, "bad n or views");
+  if (reinterpret_cast<uintptr_t>(base) % 256) return fail(GS_ERR_INVALID, "base must be 256-byte aligned");
+  splat_layout(n, views, static_cast<char*>(base), out);
+  return GS_OK;
+}
+
+gs_status gs_project(const gs_params* params, const float* poses_dev, const gs_camera* cams,
+                     int32_t views, const gs_raster_cfg* cfg, gs_splats* out, gs_stream stream) {
+  gs_status st;
+  if ((st = check_params(params)) != GS_OK) return st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
+  if ((st = check_splats(out, params->n, views)) != GS_OK) return st;
+  return launch_project(*params, poses_dev, vt, *cfg, *out, (cudaStream_t)stream);
+}
+
+size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity) {
+  return bin_sort_workspace_bytes(std::max<int64_t>(0, n) * std::max(0, views), std::max<int64_t>(0, capacity));
+}
+
+gs_status gs_bin_sort(const gs_splats* splats, const gs_camera* cams, int32_t views,
+                      const gs_raster_cfg* cfg, gs_bins* out, void* ws, size_t ws_bytes,
+                      gs_stream stream) {
+  gs_status st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!splats) return fail(GS_ERR_INVALID, "splats is NULL");
+  if ((st = check_splats(splats, splats->n, views)) != GS_OK) return st;
+  if ((st = check_bins(out, vt, splats->n)) != GS_OK) return st;
+  const size_t need = gs_bin_sort_workspace(splats->n, views, out->capacity);
+  if (!ws || ws_bytes < need)
+    return fail(GS_ERR_OOM, "bin_sort workspace: need %zu bytes, got %zu", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+  return launch_bin_sort(*splats, vt, *out, ws, (cudaStream_t)stream);
+}
+
+gs_status gs_render_fwd(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
+                        int32_t views, const gs_raster_cfg* cfg, float* image, float* alpha,
+                        gs_stream stream) {
+  gs_status st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!splats) return fail(GS_ERR_INVALID, "splats is NULL");
+  if ((st = check_splats(splats, splats->n, views)) != GS_OK) return st;
+  if ((st = check_bins(bins, vt, splats->n)) != GS_OK) return st;
+  if (!image) return fail(GS_ERR_INVALID, "image is NULL");
+  return launch_render_fwd(*splats, *bins, vt, *cfg, image, alpha, (cudaStream_t)stream);
+}
+
+static size_t bwd_layout(int64_t n, int32_t views, int64_t capacity, char* base, float** partials,
+                         float** pose_partials, int* pose_blocks) {
+  const int blocks = (int)std::max<int64_t>(1, (n + kGradBlock - 1) / kGradBlock);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += align_up(std::max<size_t>(bytes, 1), 256);
+    return p;
+  };
+  float* pa = (float*)take(sizeof(float) * kPartialStride * (size_t)std::max<int64_t>(0, capacity));
+  float* pp = (float*)take(sizeof(float) * 6 * (size_t)blocks * (size_t)std::max(1, views));
+  if (partials) *partials = pa;
+  if (pose_partials) *pose_partials = pp;
+  if (pose_blocks) *pose_blocks = blocks;
+  return off;
+}
+
+size_t gs_render_bwd_workspace(int64_t n, int32_t views, int64_t capacity) {
+  return bwd_layout(n, views, capacity, nullptr, nullptr, nullptr, nullptr);
+}
+
+gs_status gs_render_bwd_pixels(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
+                               int32_t views, const gs_raster_cfg* cfg, const float* dL_dimage,
+                               const float* dL_dalpha, int64_t n, void* ws, size_t ws_bytes,
+                               gs_stream stream) {
+  gs_status st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if ((st = check_splats(splats, n, views)) != GS_OK) return st;
+  if ((st = check_bins(bins, vt, n)) != GS_OK) return st;
+  if (!dL_dimage) return fail(GS_ERR_INVALID, "dL_dimage is NULL");
+  const size_t need = gs_render_bwd_workspace(n, views, bins->capacity);
+  if (!ws || ws_bytes < need)
+    return fail(GS_ERR_OOM, "render_bwd workspace: need %zu bytes, got %zu", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+  float *partials, *pose_partials;
+  int pose_blocks;
+  bwd_layout(n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks);
+  return launch_render_bwd(*splats, *bins, vt, *cfg, dL_dimage, dL_dalpha, partials, (cudaStream_t)stream);
+}
+
+gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_dev, const gs_camera* cams,
+                                  int32_t views, const gs_splats* splats, const gs_bins* bins,
+                                  const gs_raster_cfg* cfg, gs_grads* grads, float* dL_dpose, void* ws,
+                                  size_t ws_bytes, gs_stream stream) {
+  gs_status st;
+  if ((st = check_params(params)) != GS_OK) return st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
+  if ((st = check_splats(splats, params->n, views)) != GS_OK) return st;
+  if ((st = check_bins(bins, vt, params->n)) != GS_OK) return st;
+  if (!grads || grads->n != params->n || grads->sh_degree != params->sh_degree)
+    return fail(GS_ERR_INVALID, "grads must match params");
+  if (params->n > 0 && (!grads->means4 || !grads->scale_opa || !grads->quat || !grads->sh))
+    return fail(GS_ERR_INVALID, "NULL gradient array");
+  if (!aligned(grads->means4, 16) || !aligned(grads->scale_opa, 16) || !aligned(grads->quat, 16))
+    return fail(GS_ERR_INVALID, "gradient arrays must be 16-byte aligned");
+  const size_t need = gs_render_bwd_workspace(params->n, views, bins->capacity);
+  if (!ws || ws_bytes < need)
+    return fail(GS_ERR_OOM, "render_bwd workspace: need %zu bytes, got %zu", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+  float *partials, *pose_partials;
+  int pose_blocks;
+  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks);
+  return launch_project_bwd(*params, poses_dev, vt, *cfg, *splats, *bins, partials, *grads, pose_partials,
+                            pose_blocks, dL_dpose, (cudaStream_t)stream);
+}
+
+gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const gs_camera* cams,
+                        int32_t views, const gs_splats* splats, const gs_bins* bins,
+                        const gs_raster_cfg* cfg, const float* dL_dimage, const float* dL_dalpha,
+                        gs_grads* grads, float* dL_dpose, void* ws, size_t ws_bytes,
+                        gs_stream stream) {
+  gs_status st;
+  if ((st = check_params(params)) != GS_OK) return st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
+  if ((st = check_splats(splats, params->n, views)) != GS_OK) return st;
+  if ((st = check_bins(bins, vt, params->n)) != GS_OK) return st;
+  if (!dL_dimage) return fail(GS_ERR_INVALID, "dL_dimage is NULL");
+  if (!grads || grads->n != params->n || grads->sh_degree != params->sh_degree)
+    return fail(GS_ERR_INVALID, "grads must match params");
+  if (params->n > 0 && (!grads->means4 || !grads->scale_opa || !grads->quat || !grads->sh))
+    return fail(GS_ERR_INVALID, "NULL gradient array");
+  if (!aligned(grads->means4, 16) || !aligned(grads->scale_opa, 16) || !aligned(grads->quat, 16))
+    return fail(GS_ERR_INVALID, "gradient arrays must be 16-byte aligned");
+  const size_t need = gs_render_bwd_workspace(params->n, views, bins->capacity);
+  if (!ws || ws_bytes < need)
+    return fail(GS_ERR_OOM, "render_bwd workspace: need %zu bytes, got %zu", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+  float *partials, *pose_partials;
+  int pose_blocks;
+  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks);
+  cudaStream_t s = (cudaStream_t)stream;
+  st = launch_render_bwd(*splats, *bins, vt, *cfg, dL_dimage, dL_dalpha, partials, s);
+  if (st != GS_OK) return st;
+  return launch_project_bwd(*params, poses_dev, vt, *cfg, *splats, *bins, partials, *grads, pose_partials,
+                            pose_blocks, dL_dpose, s);
+}
+
+gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
+                       const gs_adam_cfg* cfg, int32_t step, gs_stream stream) {
+  if (!cfg) return fail(GS_ERR_INVALID, "cfg is NULL");
+  if (n < 0) return fail(GS_ERR_INVALID, "n < 0");
+  if (step < 1) return fail(GS_ERR_INVALID, "step must be >= 1");
+  if (n > 0 && (!p || !g || !m || !v)) return fail(GS_ERR_INVALID, "NULL arena");
+  if (!aligned(p, 16) || !aligned(g, 16) || !aligned(m, 16) || !aligned(v, 16))
+    return fail(GS_ERR_INVALID, "arenas must be 16-byte aligned");
+  if (cfg->num_groups < 1 || cfg->num_groups > GS_MAX_ADAM_GROUPS || !cfg->groups)
+    return fail(GS_ERR_INVALID, "num_groups must be 1..%d", GS_MAX_ADAM_GROUPS);
+  for (int k = 0; k < cfg->num_groups; ++k) {
+    const gs_adam_group& G = cfg->groups[k];
+    if (G.begin < 0 || G.end < G.begin || G.end > n) return fail(GS_ERR_INVALID, "group %d out of range", k);
+  }
+  if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f))
+    return fail(GS_ERR_INVALID, "bad Adam hyper-parameters");
+  if (cfg->pose && (cfg->views < 1 || !cfg->dpose || !cfg->pose_m || !cfg->pose_v))
+    return fail(GS_ERR_INVALID, "pose step needs views, dpose, pose_m, pose_v");
+  return launch_adam(p, g, m, v, n, *cfg, step, (cudaStream_t)stream);
+}
+
+size_t gs_image_loss_workspace(void) { return loss_workspace_bytes(); }
+
+gs_status gs_image_loss(const float* image, const float* target, int64_t count, int32_t kind,
+                        float* dL_dimage, float* loss_dev, void* ws, size_t ws_bytes, gs_stream stream) {
+  if (count <= 0) return fail(GS_ERR_INVALID, "count must be > 0");
+  if (!image || !target || !loss_dev) return fail(GS_ERR_INVALID, "NULL image, target or loss");
+  if (kind != 0 && kind != 1) return fail(GS_ERR_INVALID, "kind must be 0 (L1) or 1 (MSE)");
+  if (!ws || ws_bytes < loss_workspace_bytes())
+    return fail(GS_ERR_OOM, "image_loss workspace: need %zu bytes, got %zu", loss_workspace_bytes(), ws_bytes);
+  return launch_loss(image, target, count, kind, dL_dimage, loss_dev, ws, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,354 @@
+// Per-Gaussian backward: sums each (view, Gaussian)'s per-tile partial
+// gradients in a fixed order, then applies the chain rule of the projection
+// (pixel-space mean, conic, opacity, SH colour) to the parameters (means,
+// log-scales, quaternion, opacity logit, SH) and to each view's pose for the
+// left perturbation T <- Exp(xi) T, xi = (v, omega).  One thread per
+// Gaussian, all views in one fixed-order loop; pose gradients are reduced per
+// block (fixed tree) and then over blocks (fixed order): the result is
+// deterministic without atomics.
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+struct GradArgs {
+  const float4* means4;
+  const float4* scale_opa;
+  const float4* quat;
+  const float* sh;
+  int64_t n;
+  const float* poses;
+  int clamp_j;
+  const uint32_t* touched;
+  const uint32_t* aux;
+  const uint32_t* pair_off;
+  const uint32_t* counts;  // [3] = pairs in the lists (min(K, capacity))
+  const float* partials;
+  float4* g_means4;
+  float4* g_scale_opa;
+  float4* g_quat;
+  float* g_sh;
+  float* pose_partials;  // [V][gridDim.x][6]
+};
+
+// Deterministic 256-thread sum of 6 values per thread into out[6] (thread 0).
+__device__ __forceinline__ void block_sum6(float (&x)[6], float* s_tmp /*[8][6]*/, float* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x[c] += __shfl_xor_sync(0xffffffffu, x[c], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s_tmp[warp * 6 + c] = x[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float s = 0.f;
+    for (int w = 0; w < kGradBlock / 32; ++w) s += s_tmp[w * 6 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, const ViewTable vt) {
+  constexpr int NC = (DEG + 1) * (DEG + 1);
+  __shared__ float s_tmp[(kGradBlock / 32) * 6];
+  const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
+  const bool valid = i < a.n;
+
+  float4 mu = make_float4(0.f, 0.f, 0.f, 0.f), so = mu, q4 = mu;
+  if (valid) { mu = a.means4[i]; so = a.scale_opa[i]; q4 = a.quat[i]; }
+  // quaternion, rotation, scales (view independent)
+  const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+  const float qi = valid ? 1.0f / qn : 0.f;
+  const float qw = q4.x * qi, qx = q4.y * qi, qy = q4.z * qi, qz = q4.w * qi;
+  float Rq[9];
+  quat_rot(qw, qx, qy, qz, Rq);
+  const float s[3] = {expf(so.x), expf(so.y), expf(so.z)};
+  float M[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * s[c];
+  const float opa = 1.0f / (1.0f + expf(-so.w));
+
+  float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+  float gol = 0.f;
+  float gsh[3][NC];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
+  // gradient w.r.t. the rotation matrix entries, accumulated over views
+  float gRq[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) gRq[k] = 0.f;
+  float gs_[3] = {0.f, 0.f, 0.f};
+
+  const uint32_t kpairs = a.counts[3];
+  for (int v = 0; v < vt.views; ++v) {
+    float pv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int64_t o = (int64_t)v * a.n + i;
+    uint32_t tch = valid ? a.touched[o] : 0u;
+    // pairs cut off by a capacity overflow were never rendered: skip them
+    if (tch > 0 && (uint64_t)a.pair_off[o] + tch > kpairs) tch = 0;
+    if (tch > 0) {
+      const ViewInfo vi = vt.v[v];
+      // ---- sum of this (view, Gaussian)'s per-tile partials, fixed order
+      float G[kPartialStride];
+#pragma unroll
+      for (int c = 0; c < kPartialStride; ++c) G[c] = 0.f;
+      const float* pp = a.partials + (int64_t)a.pair_off[o] * kPartialStride;
+      for (uint32_t k = 0; k < tch; ++k) {
+#pragma unroll
+        for (int c = 0; c < kPartialStride; ++c) G[c] += pp[k * kPartialStride + c];
+      }
+      const uint32_t auxb = a.aux[o];
+      const float* P = a.poses + 12 * v;
+      const float R[9] = {P[0], P[1], P[2], P[4], P[5], P[6], P[8], P[9], P[10]};
+      const float tc[3] = {P[3], P[7], P[11]};
+      float t[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) t[r] = R[3 * r] * mu.x + R[3 * r + 1] * mu.y + R[3 * r + 2] * mu.z + tc[r];
+      const float iz = 1.0f / t[2], iz2 = iz * iz;
+      float dt[3] = {0.f, 0.f, 0.f};
+
+      // ---- colour (SH) and the view direction
+      {
+        const float oc0 = -(R[0] * tc[0] + R[3] * tc[1] + R[6] * tc[2]);
+        const float oc1 = -(R[1] * tc[0] + R[4] * tc[1] + R[7] * tc[2]);
+        const float oc2 = -(R[2] * tc[0] + R[5] * tc[1] + R[8] * tc[2]);
+        float wx = mu.x - oc0, wy = mu.y - oc1, wz = mu.z - oc2;
+        const float wn = sqrtf(wx * wx + wy * wy + wz * wz), inv = 1.0f / wn;
+        const float dx = wx * inv, dy = wy * inv, dz = wz * inv;
+        float Y[NC];
+        sh_basis<DEG>(dx, dy, dz, Y);
+        float dY[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) dY[k] = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          if (auxb & (1u << ch)) continue;
+          const float gc = G[6 + ch];
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            gsh[ch][k] += gc * Y[k];
+            dY[k] += gc * a.sh[(int64_t)(ch * NC + k) * a.n + i];
+          }
+        }
+        float ddx, ddy, ddz;
+        sh_basis_grad<DEG>(dx, dy, dz, dY, ddx, ddy, ddz);
+        const float pr = dx * ddx + dy * ddy + dz * ddz;
+        const float dwx = (ddx - dx * pr) * inv, dwy = (ddy - dy * pr) * inv, dwz = (ddz - dz * pr) * inv;
+        gmu[0] += dwx; gmu[1] += dwy; gmu[2] += dwz;
+        // mu - centre moves by R^T v under the pose perturbation
+        pv[0] += R[0] * dwx + R[1] * dwy + R[2] * dwz;
+        pv[1] += R[3] * dwx + R[4] * dwy + R[5] * dwz;
+        pv[2] += R[6] * dwx + R[7] * dwy + R[8] * dwz;
+      }
+
+      // ---- opacity
+      gol += G[5] * opa * (1.f - opa);
+
+      // ---- pixel-space mean m = f t_xy / t_z + c
+      dt[0] += G[0] * vi.fx * iz;
+      dt[1] += G[1] * vi.fy * iz;
+      dt[2] -= (G[0] * vi.fx * t[0] + G[1] * vi.fy * t[1]) * iz2;
+
+      // ---- conic -> 2D covariance -> (J, R, Rq, s)
+      float u = t[0] * iz, w = t[1] * iz;
+      const bool cx = (auxb & 8u) != 0, cy = (auxb & 16u) != 0;
+      if (a.clamp_j) {
+        const float limx = kGuard * 0.5f * (float)vi.W / vi.fx;
+        const float limy = kGuard * 0.5f * (float)vi.H / vi.fy;
+        if (cx) u = u > 0.f ? limx : -limx;
+        if (cy) w = w > 0.f ? limy : -limy;
+      }
+      const float J00 = vi.fx * iz, J02 = -vi.fx * u * iz;
+      const float J11 = vi.fy * iz, J12 = -vi.fy * w * iz;
+      const float T0[3] = {J00 * R[0] + J02 * R[6], J00 * R[1] + J02 * R[7], J00 * R[2] + J02 * R[8]};
+      const float T1[3] = {J11 * R[3] + J12 * R[6], J11 * R[4] + J12 * R[7], J11 * R[5] + J12 * R[8]};
+      float P0[3], P1[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        P0[c] = T0[0] * M[c] + T0[1] * M[3 + c] + T0[2] * M[6 + c];
+        P1[c] = T1[0] * M[c] + T1[1] * M[3 + c] + T1[2] * M[6 + c];
+      }
+      const float ca = P0[0] * P0[0] + P0[1] * P0[1] + P0[2] * P0[2] + kDilation;
+      const float cb = P0[0] * P1[0] + P0[1] * P1[1] + P0[2] * P1[2];
+      const float cc = P1[0] * P1[0] + P1[1] * P1[1] + P1[2] * P1[2] + kDilation;
+      const float det = ca * cc - cb * cb;
+      const float id = 1.0f / det, id2 = id * id;
+      const float gA = G[2], gB = G[3], gC = G[4];
+      const float ga = (-cc * cc * gA + cb * cc * gB - cb * cb * gC) * id2;
+      const float gb = (2.f * cb * cc * gA - (ca * cc + cb * cb) * gB + 2.f * ca * cb * gC) * id2;
+      const float gc = (-cb * cb * gA + ca * cb * gB - ca * ca * gC) * id2;
+      float dP0[3], dP1[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dP0[c] = 2.f * ga * P0[c] + gb * P1[c];
+        dP1[c] = gb * P0[c] + 2.f * gc * P1[c];
+      }
+      // P = T M:  dT = dP M^T,  dM = T^T dP
+      float dT0[3], dT1[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        dT0[r] = dP0[0] * M[3 * r] + dP0[1] * M[3 * r + 1] + dP0[2] * M[3 * r + 2];
+        dT1[r] = dP1[0] * M[3 * r] + dP1[1] * M[3 * r + 1] + dP1[2] * M[3 * r + 2];
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float dm = T0[r] * dP0[c] + T1[r] * dP1[c];
+          gs_[c] += dm * Rq[3 * r + c];
+          gRq[3 * r + c] += dm * s[c];
+        }
+      // T = J R (rows): dJ and the rotation-matrix gradient of the pose
+      const float dJ00 = dT0[0] * R[0] + dT0[1] * R[1] + dT0[2] * R[2];
+      const float dJ02 = dT0[0] * R[6] + dT0[1] * R[7] + dT0[2] * R[8];
+      const float dJ11 = dT1[0] * R[3] + dT1[1] * R[4] + dT1[2] * R[5];
+      const float dJ12 = dT1[0] * R[6] + dT1[1] * R[7] + dT1[2] * R[8];
+      float dR[9];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dR[c] = J00 * dT0[c];
+        dR[3 + c] = J11 * dT1[c];
+        dR[6 + c] = J02 * dT0[c] + J12 * dT1[c];
+      }
+      // J as a function of t
+      dt[2] -= (dJ00 * vi.fx + dJ11 * vi.fy) * iz2;
+      if (cx) {
+        dt[2] += dJ02 * vi.fx * u * iz2;
+      } else {
+        dt[0] -= dJ02 * vi.fx * iz2;
+        dt[2] += dJ02 * 2.f * vi.fx * t[0] * iz2 * iz;
+      }
+      if (cy) {
+        dt[2] += dJ12 * vi.fy * w * iz2;
+      } else {
+        dt[1] -= dJ12 * vi.fy * iz2;
+        dt[2] += dJ12 * 2.f * vi.fy * t[1] * iz2 * iz;
+      }
+      // t = R mu + t_cam
+      gmu[0] += R[0] * dt[0] + R[3] * dt[1] + R[6] * dt[2];
+      gmu[1] += R[1] * dt[0] + R[4] * dt[1] + R[7] * dt[2];
+      gmu[2] += R[2] * dt[0] + R[5] * dt[1] + R[8] * dt[2];
+      // pose: t -> t + omega x t + v ; R -> R + [omega]x R
+      pv[0] += dt[0]; pv[1] += dt[1]; pv[2] += dt[2];
+      pv[3] += t[1] * dt[2] - t[2] * dt[1];
+      pv[4] += t[2] * dt[0] - t[0] * dt[2];
+      pv[5] += t[0] * dt[1] - t[1] * dt[0];
+      // N = R dR^T; d omega += (N12 - N21, N20 - N02, N01 - N10)
+      float N[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          N[3 * r + c] = R[3 * r] * dR[3 * c] + R[3 * r + 1] * dR[3 * c + 1] + R[3 * r + 2] * dR[3 * c + 2];
+      pv[3] += N[5] - N[7];
+      pv[4] += N[6] - N[2];
+      pv[5] += N[1] - N[3];
+    }
+    float* dst = a.pose_partials + ((int64_t)v * gridDim.x + blockIdx.x) * 6;
+    block_sum6(pv, s_tmp, dst);
+  }
+
+  if (!valid) return;
+  // rotation entries -> unit quaternion -> quaternion
+  const float dqw = gRq[1] * (-2.f * qz) + gRq[2] * (2.f * qy) + gRq[3] * (2.f * qz) +
+                    gRq[5] * (-2.f * qx) + gRq[6] * (-2.f * qy) + gRq[7] * (2.f * qx);
+  const float dqx = gRq[1] * (2.f * qy) + gRq[2] * (2.f * qz) + gRq[3] * (2.f * qy) +
+                    gRq[4] * (-4.f * qx) + gRq[5] * (-2.f * qw) + gRq[6] * (2.f * qz) +
+                    gRq[7] * (2.f * qw) + gRq[8] * (-4.f * qx);
+  const float dqy = gRq[0] * (-4.f * qy) + gRq[1] * (2.f * qx) + gRq[2] * (2.f * qw) +
+                    gRq[3] * (2.f * qx) + gRq[5] * (2.f * qz) + gRq[6] * (-2.f * qw) +
+                    gRq[7] * (2.f * qz) + gRq[8] * (-4.f * qy);
+  const float dqz = gRq[0] * (-4.f * qz) + gRq[1] * (-2.f * qw) + gRq[2] * (2.f * qx) +
+                    gRq[3] * (2.f * qw) + gRq[4] * (-4.f * qz) + gRq[5] * (2.f * qy) +
+                    gRq[6] * (2.f * qx) + gRq[7] * (2.f * qy);
+  const float pr = qw * dqw + qx * dqx + qy * dqy + qz * dqz;
+  gq[0] = (dqw - qw * pr) * qi;
+  gq[1] = (dqx - qx * pr) * qi;
+  gq[2] = (dqy - qy * pr) * qi;
+  gq[3] = (dqz - qz * pr) * qi;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) gls[c] = gs_[c] * s[c];
+
+  a.g_means4[i] = make_float4(gmu[0], gmu[1], gmu[2], 0.f);
+  a.g_scale_opa[i] = make_float4(gls[0], gls[1], gls[2], gol);
+  a.g_quat[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) a.g_sh[(int64_t)(ch * NC + k) * a.n + i] = gsh[ch][k];
+}
+
+// Sum of the per-block pose partials of each view, in a fixed order.
+__global__ void __launch_bounds__(256) k_pose_finalize(const float* __restrict__ partials,
+                                                       int blocks, float* __restrict__ dpose) {
+  __shared__ float s[256][6];
+  const int v = blockIdx.x;
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int b = threadIdx.x; b < blocks; b += 256) {
+    const float* p = partials + ((int64_t)v * blocks + b) * 6;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += p[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s[threadIdx.x][c] = acc[c];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) s[threadIdx.x][c] += s[threadIdx.x + h][c];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) dpose[v * 6 + threadIdx.x] = s[0][threadIdx.x];
+}
+
+}  // namespace
+
+gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewTable& vt,
+                             const gs_raster_cfg& cfg, const gs_splats& sp, const gs_bins& bins,
+                             const float* partials, const gs_grads& g, float* pose_partials,
+                             int pose_blocks, float* dpose, cudaStream_t s) {
+  GradArgs a;
+  a.means4 = reinterpret_cast<const float4*>(p.means4);
+  a.scale_opa = reinterpret_cast<const float4*>(p.scale_opa);
+  a.quat = reinterpret_cast<const float4*>(p.quat);
+  a.sh = p.sh;
+  a.n = p.n;
+  a.poses = poses;
+  a.clamp_j = cfg.clamp_jacobian;
+  a.touched = sp.touched;
+  a.aux = sp.aux;
+  a.pair_off = bins.pair_off;
+  a.counts = bins.counts;
+  a.partials = partials;
+  a.g_means4 = reinterpret_cast<float4*>(g.means4);
+  a.g_scale_opa = reinterpret_cast<float4*>(g.scale_opa);
+  a.g_quat = reinterpret_cast<float4*>(g.quat);
+  a.g_sh = g.sh;
+  a.pose_partials = pose_partials;
+  if (p.n == 0) {
+    if (dpose) cudaMemsetAsync(dpose, 0, sizeof(float) * 6 * vt.views, s);
+    return check_launch("project_bwd");
+  }
+  const unsigned grid = (unsigned)pose_blocks;
+  switch (p.sh_degree) {
+    case 0: k_project_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt); break;
+    case 1: k_project_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt); break;
+    case 2: k_project_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt); break;
+    default: k_project_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt); break;
+  }
+  if (dpose) k_pose_finalize<<<vt.views, 256, 0, s>>>(pose_partials, pose_blocks, dpose);
+  return check_launch("project_bwd");
+}
+
+}  // namespace gs

@@ -1,0 +1,61 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gs.h"
+#include "gs_device.cuh"
+
+namespace gs {
+
+// Record a failure message for gs_last_error (thread-local) and return `st`.
+gs_status fail(gs_status st, const char* fmt, ...);
+// Map the last CUDA error (if any) to GS_ERR_CUDA with a message.
+gs_status check_launch(const char* what);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Fills a ViewTable from host cameras; returns false (with a message) on
+// invalid cameras.
+bool make_view_table(const gs_camera* cams, int views, ViewTable* vt);
+
+// ---- kernels' host launchers (each enqueues on `s`, returns GS_OK or GS_ERR_CUDA)
+gs_status launch_project(const gs_params& p, const float* poses, const ViewTable& vt,
+                         const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s);
+
+// Exclusive scan of n_cap u32 values (in place allowed); the number of valid
+// entries is *n_dev (device); the total goes to *total_dev.
+size_t scan_workspace(int64_t n_cap);
+gs_status launch_scan(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, int64_t n_cap,
+                      uint32_t* total_dev, void* ws, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) u32 pairs on key bits [0, bits);
+// count *n_dev (device) <= n_cap.  keys/vals ping-pong between the *_a and
+// *_b buffers; the result lands in (keys_out, vals_out).
+size_t radix_workspace(int64_t n_cap);
+gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
+                            uint32_t* keys_out, uint32_t* vals_out, const uint32_t* n_dev,
+                            int64_t n_cap, int bits, void* ws, cudaStream_t s);
+
+gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
+                            const gs_raster_cfg& cfg, float* image, float* alpha, cudaStream_t s);
+gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
+                            const gs_raster_cfg& cfg, const float* dimage, const float* dalpha,
+                            float* partials, cudaStream_t s);
+gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewTable& vt,
+                             const gs_raster_cfg& cfg, const gs_splats& sp, const gs_bins& bins,
+                             const float* partials, const gs_grads& g, float* pose_partials,
+                             int pose_blocks, float* dpose, cudaStream_t s);
+gs_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
+                      const gs_adam_cfg& cfg, int step, cudaStream_t s);
+
+size_t loss_workspace_bytes();
+gs_status launch_loss(const float* img, const float* tgt, int64_t count, int kind, float* grad,
+                      float* loss, void* ws, cudaStream_t s);
+
+constexpr int kPartialStride = 9;       // floats per (tile, splat) pair gradient
+constexpr int kGradBlock = 256;         // threads per block of the per-Gaussian backward
+
+}  // namespace gs

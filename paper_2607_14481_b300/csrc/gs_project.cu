@@ -1,0 +1,184 @@
+// EWA projection of every (view, Gaussian): the per-Gaussian stage of the
+// splat renderer (Sec. 5.2).  One thread per (view, Gaussian); the Gaussian's
+// parameters are read as coalesced float4 / planar-SH loads, the splat record
+// is written as float4 structure-of-arrays.  HBM-bound: ~64 B (SH0) / 240 B
+// (SH3) read and 64 B written per (view, Gaussian).
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+struct ProjectArgs {
+  const float4* means4;
+  const float4* scale_opa;
+  const float4* quat;
+  const float* sh;
+  int64_t n;
+  const float* poses;
+  float znear;
+  int clamp_j;
+  float4* xy;
+  float4* conic;
+  float4* rgb;
+  float* depth;
+  uint2* rect;
+  uint32_t* touched;
+  uint32_t* aux;
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const ViewTable vt) {
+  constexpr int NC = (DEG + 1) * (DEG + 1);
+  const int v = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int64_t o = (int64_t)v * a.n + i;
+  const ViewInfo vi = vt.v[v];
+  const float* P = a.poses + 12 * v;
+  const float R[9] = {P[0], P[1], P[2], P[4], P[5], P[6], P[8], P[9], P[10]};
+  const float tc[3] = {P[3], P[7], P[11]};
+
+  const float4 mu = a.means4[i];
+  // camera-space centre in double-single
+  const df tz = df_dot3_add(R[6], mu.x, R[7], mu.y, R[8], mu.z, tc[2]);
+  bool vis = !df_le(tz, a.znear);
+  df tx = {0.f, 0.f}, ty = {0.f, 0.f}, mx = {0.f, 0.f}, my = {0.f, 0.f};
+  if (vis) {
+    tx = df_dot3_add(R[0], mu.x, R[1], mu.y, R[2], mu.z, tc[0]);
+    ty = df_dot3_add(R[3], mu.x, R[4], mu.y, R[5], mu.z, tc[1]);
+    mx = df_add_f(df_mul_f(df_div(tx, tz), vi.fx), vi.cx);
+    my = df_add_f(df_mul_f(df_div(ty, tz), vi.fy), vi.cy);
+    // far off-screen (or non-finite) centres are culled before the split
+    vis = fabsf(mx.hi) < 1e7f && fabsf(my.hi) < 1e7f;
+  }
+  float A = 0.f, B = 0.f, C = 0.f, r = 0.f, opa = 0.f;
+  float mix = 0.f, miy = 0.f, mfx = 0.f, mfy = 0.f;
+  int xlo = 1, ylo = 1, xhi = 0, yhi = 0;
+  uint32_t auxbits = 0;
+  if (vis) {
+    // integer / fraction split of the pixel-space mean
+    mix = floorf(mx.hi);
+    mfx = (mx.hi - mix) + mx.lo;
+    if (mfx < 0.f) { mix -= 1.f; mfx += 1.f; } else if (mfx >= 1.f) { mix += 1.f; mfx -= 1.f; }
+    miy = floorf(my.hi);
+    mfy = (my.hi - miy) + my.lo;
+    if (mfy < 0.f) { miy -= 1.f; mfy += 1.f; } else if (mfy >= 1.f) { miy += 1.f; mfy -= 1.f; }
+
+    const float4 q = a.quat[i];
+    const float qi = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    float Rq[9];
+    quat_rot(q.x * qi, q.y * qi, q.z * qi, q.w * qi, Rq);
+    const float4 so = a.scale_opa[i];
+    const float s[3] = {expf(so.x), expf(so.y), expf(so.z)};
+
+    // perspective Jacobian with the frustum guard
+    const float tzf = tz.hi, iz = 1.0f / tzf;
+    float u = tx.hi * iz, w = ty.hi * iz;
+    if (a.clamp_j) {
+      const float limx = kGuard * 0.5f * (float)vi.W / vi.fx;
+      const float limy = kGuard * 0.5f * (float)vi.H / vi.fy;
+      if (u > limx) { u = limx; auxbits |= 8u; } else if (u < -limx) { u = -limx; auxbits |= 8u; }
+      if (w > limy) { w = limy; auxbits |= 16u; } else if (w < -limy) { w = -limy; auxbits |= 16u; }
+    }
+    const float J00 = vi.fx * iz, J02 = -vi.fx * u * iz;
+    const float J11 = vi.fy * iz, J12 = -vi.fy * w * iz;
+    // T = J R (2x3); P = T Rq diag(s); 2D covariance = P P^T + 0.3 I
+    const float T0[3] = {J00 * R[0] + J02 * R[6], J00 * R[1] + J02 * R[7], J00 * R[2] + J02 * R[8]};
+    const float T1[3] = {J11 * R[3] + J12 * R[6], J11 * R[4] + J12 * R[7], J11 * R[5] + J12 * R[8]};
+    float P0[3], P1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      P0[c] = (T0[0] * Rq[c] + T0[1] * Rq[3 + c] + T0[2] * Rq[6 + c]) * s[c];
+      P1[c] = (T1[0] * Rq[c] + T1[1] * Rq[3 + c] + T1[2] * Rq[6 + c]) * s[c];
+    }
+    const float ca = P0[0] * P0[0] + P0[1] * P0[1] + P0[2] * P0[2] + kDilation;
+    const float cb = P0[0] * P1[0] + P0[1] * P1[1] + P0[2] * P1[2];
+    const float cc = P1[0] * P1[0] + P1[1] * P1[1] + P1[2] * P1[2] + kDilation;
+    const float det = ca * cc - cb * cb;
+    vis = det > 0.f;
+    if (vis) {
+      const float id = 1.0f / det;
+      A = cc * id; B = -cb * id; C = ca * id;
+      const float hd = 0.5f * (ca - cc);
+      const float lam = 0.5f * (ca + cc) + sqrtf(fmaxf(0.f, hd * hd + cb * cb));
+      r = ceilf(3.0f * sqrtf(lam));
+      // tile rect of [m - r, m + r]^2; m = mi + frac with frac in [0,1)
+      xlo = max(0, (int)floorf((mix - r) * (1.0f / kTile)));
+      xhi = min(vi.TX - 1, (int)floorf((mix + r) * (1.0f / kTile)));
+      ylo = max(0, (int)floorf((miy - r) * (1.0f / kTile)));
+      yhi = min(vi.TY - 1, (int)floorf((miy + r) * (1.0f / kTile)));
+      vis = xlo <= xhi && ylo <= yhi;
+      opa = 1.0f / (1.0f + expf(-so.w));
+    }
+  }
+  float3 col = make_float3(0.f, 0.f, 0.f);
+  if (vis) {
+    // SH colour seen from the camera centre -R^T t
+    const float oc0 = -(R[0] * tc[0] + R[3] * tc[1] + R[6] * tc[2]);
+    const float oc1 = -(R[1] * tc[0] + R[4] * tc[1] + R[7] * tc[2]);
+    const float oc2 = -(R[2] * tc[0] + R[5] * tc[1] + R[8] * tc[2]);
+    float dx = mu.x - oc0, dy = mu.y - oc1, dz = mu.z - oc2;
+    const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv; dy *= inv; dz *= inv;
+    float Y[NC];
+    sh_basis<DEG>(dx, dy, dz, Y);
+    float cv[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) acc += a.sh[(int64_t)(ch * NC + k) * a.n + i] * Y[k];
+      acc += 0.5f;
+      if (acc < 0.f) { acc = 0.f; auxbits |= 1u << ch; }
+      cv[ch] = acc;
+    }
+    col = make_float3(cv[0], cv[1], cv[2]);
+  }
+  if (!vis) {
+    A = B = C = opa = r = 0.f;
+    mix = miy = mfx = mfy = 0.f;
+    xlo = ylo = 1; xhi = yhi = 0;
+    auxbits = 0;
+  }
+  a.xy[o] = make_float4(mix, miy, mfx, mfy);
+  a.conic[o] = make_float4(A, B, C, opa);
+  a.rgb[o] = make_float4(col.x, col.y, col.z, r);
+  a.depth[o] = tz.hi;
+  a.rect[o] = make_uint2((uint32_t)xlo | ((uint32_t)ylo << 16), (uint32_t)xhi | ((uint32_t)yhi << 16));
+  a.touched[o] = vis ? (uint32_t)((xhi - xlo + 1) * (yhi - ylo + 1)) : 0u;
+  a.aux[o] = auxbits;
+}
+
+}  // namespace
+
+gs_status launch_project(const gs_params& p, const float* poses, const ViewTable& vt,
+                         const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s) {
+  ProjectArgs a;
+  a.means4 = reinterpret_cast<const float4*>(p.means4);
+  a.scale_opa = reinterpret_cast<const float4*>(p.scale_opa);
+  a.quat = reinterpret_cast<const float4*>(p.quat);
+  a.sh = p.sh;
+  a.n = p.n;
+  a.poses = poses;
+  a.znear = cfg.znear;
+  a.clamp_j = cfg.clamp_jacobian;
+  a.xy = reinterpret_cast<float4*>(out.xy);
+  a.conic = reinterpret_cast<float4*>(out.conic);
+  a.rgb = reinterpret_cast<float4*>(out.rgb);
+  a.depth = out.depth;
+  a.rect = reinterpret_cast<uint2*>(out.rect);
+  a.touched = out.touched;
+  a.aux = out.aux;
+  if (p.n == 0) return GS_OK;
+  dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)vt.views);
+  switch (p.sh_degree) {
+    case 0: k_project<0><<<grid, 256, 0, s>>>(a, vt); break;
+    case 1: k_project<1><<<grid, 256, 0, s>>>(a, vt); break;
+    case 2: k_project<2><<<grid, 256, 0, s>>>(a, vt); break;
+    default: k_project<3><<<grid, 256, 0, s>>>(a, vt); break;
+  }
+  return check_launch("k_project");
+}
+
+}  // namespace gs

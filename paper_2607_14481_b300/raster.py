@@ -1,0 +1,291 @@
+"""Tensor-level API: device buffers held in torch tensors, every step run by
+libgs (include/gs.h).  torch supplies device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from .synth import Camera, Scene
+
+
+def _p(t: Optional[torch.Tensor]):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Arena:
+    """Per-Gaussian float arrays in the library's layout inside one flat
+    float32 buffer: [means4 (4n) | scale_opa (4n) | quat (4n) | sh (3 nc n)],
+    padded to a multiple of 4 floats.  Parameters, gradients and both Adam
+    moments use the same layout, so one fused Adam launch covers them all."""
+
+    def __init__(self, n: int, sh_degree: int, device="cuda", buf: Optional[torch.Tensor] = None):
+        self.n = int(n)
+        self.sh_degree = int(sh_degree)
+        self.nc = (self.sh_degree + 1) ** 2
+        self.size = 12 * self.n + 3 * self.nc * self.n
+        self.padded = (self.size + 3) // 4 * 4
+        if buf is None:
+            buf = torch.zeros(max(self.padded, 4), dtype=torch.float32, device=device)
+        self.buf = buf
+        n4 = 4 * self.n
+        self.means4 = buf[0:n4].view(self.n, 4)
+        self.scale_opa = buf[n4:2 * n4].view(self.n, 4)
+        self.quat = buf[2 * n4:3 * n4].view(self.n, 4)
+        self.sh = buf[3 * n4:3 * n4 + 3 * self.nc * self.n].view(3 * self.nc, self.n)
+
+    @classmethod
+    def from_scene(cls, sc: Scene, device="cuda") -> "Arena":
+        a = cls(sc.n, sc.sh_degree, device)
+        h = np.zeros(a.padded, np.float32)
+        n, nc = a.n, a.nc
+        h[0:4 * n].reshape(n, 4)[:, :3] = sc.means
+        so = h[4 * n:8 * n].reshape(n, 4)
+        so[:, :3] = sc.log_scales
+        so[:, 3] = sc.opa_logits
+        h[8 * n:12 * n] = sc.quats.reshape(-1)
+        h[12 * n:12 * n + 3 * nc * n] = np.ascontiguousarray(sc.sh.reshape(n, 3 * nc).T).reshape(-1)
+        a.buf.copy_(torch.from_numpy(h).to(a.buf.device))
+        return a
+
+    def like(self) -> "Arena":
+        return Arena(self.n, self.sh_degree, self.buf.device)
+
+    def to_natural(self) -> dict:
+        """Host float64 copies in natural layout (means [n,3], log_scales [n,3],
+        quats [n,4], opa_logits [n], sh [n,3,nc])."""
+        h = self.buf.detach().cpu().numpy().astype(np.float64)
+        n, nc = self.n, self.nc
+        m4 = h[0:4 * n].reshape(n, 4)
+        so = h[4 * n:8 * n].reshape(n, 4)
+        return {"means": m4[:, :3].copy(), "means_pad": m4[:, 3].copy(), "log_scales": so[:, :3].copy(),
+                "opa_logits": so[:, 3].copy(), "quats": h[8 * n:12 * n].reshape(n, 4).copy(),
+                "sh": h[12 * n:12 * n + 3 * nc * n].reshape(3 * nc, n).T.reshape(n, 3, nc).copy()}
+
+    def struct(self):
+        return _lib.GsParams(self.means4.data_ptr(), self.scale_opa.data_ptr(), self.quat.data_ptr(),
+                             self.sh.data_ptr(), self.n, self.sh_degree)
+
+    def adam_groups(self, lr_means=1.6e-4, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3,
+                    lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4) -> List[_lib.GsAdamGroup]:
+        """One group per parameter kind; the scale_opa float4 gives its first
+        three lanes the scale rate and its fourth the opacity rate."""
+        n, nc = self.n, self.nc
+        G = _lib.GsAdamGroup
+        f4 = C.c_float * 4
+        groups = [G(0, 4 * n, f4(lr_means, lr_means, lr_means, 0.0)),
+                  G(4 * n, 8 * n, f4(lr_scale, lr_scale, lr_scale, lr_opacity)),
+                  G(8 * n, 12 * n, f4(lr_quat, lr_quat, lr_quat, lr_quat)),
+                  G(12 * n, 12 * n + 3 * n * nc, f4(lr_sh_rest, lr_sh_rest, lr_sh_rest, lr_sh_rest))]
+        # SH DC planes are k = 0 of each channel: planes 0, nc, 2 nc
+        for ch in range(3):
+            b = 12 * n + ch * nc * n
+            groups.append(G(b, b + n, f4(lr_sh_dc, lr_sh_dc, lr_sh_dc, lr_sh_dc)))
+        # first matching group wins: put the DC planes first
+        return groups[4:] + groups[:4]
+
+
+def cameras_struct(cams: Sequence[Camera]):
+    arr = (_lib.GsCamera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = _lib.GsCamera(c.fx, c.fy, c.cx, c.cy, c.width, c.height)
+    return arr
+
+
+def poses_tensor(cams: Sequence[Camera], device="cuda") -> torch.Tensor:
+    return torch.from_numpy(np.stack([c.pose12() for c in cams]).astype(np.float32)).to(device).contiguous()
+
+
+class Rasterizer:
+    """Splat records, tile lists and workspaces for a fixed set of views.
+
+    forward(): gs_project -> gs_bin_sort -> gs_render_fwd
+    backward(): gs_render_bwd
+    The pair capacity grows on overflow when forward(check=True) reads the
+    device counts (one 16-byte copy); with check=False nothing synchronises."""
+
+    def __init__(self, n: int, sh_degree: int, cams: Sequence[Camera], bg=(0.0, 0.0, 0.0), znear=0.2,
+                 clamp_jacobian=True, capacity: Optional[int] = None, device="cuda", keep_keys=False):
+        self.L = _lib.load()
+        self.n, self.sh_degree = int(n), int(sh_degree)
+        self.device = torch.device(device)
+        self.set_cameras(cams)
+        self.cfg = _lib.GsRasterCfg(_lib.GS_TILE, _lib.GS_TILE, (C.c_float * 3)(*bg), float(znear),
+                                    int(bool(clamp_jacobian)))
+        V = self.views
+        self.splat_buf = torch.empty(self.L.gs_splats_bytes(self.n, V), dtype=torch.uint8, device=self.device)
+        self.splats = _lib.GsSplats()
+        _lib.check(self.L.gs_splats_carve(_p(self.splat_buf), self.n, V, C.byref(self.splats)), "gs_splats_carve")
+        self.pair_off = torch.empty(max(1, self.n * V), dtype=torch.int32, device=self.device)
+        self.counts = torch.zeros(4, dtype=torch.int32, device=self.device)
+        self.keep_keys = keep_keys
+        self.capacity = 0
+        self.set_capacity(capacity if capacity is not None else max(4096, 4 * self.n * V))
+
+    def set_cameras(self, cams: Sequence[Camera]) -> None:
+        cams = list(cams)
+        if hasattr(self, "views") and len(cams) != self.views:
+            raise ValueError("number of views is fixed per Rasterizer")
+        self.cams = cams
+        self.views = len(cams)
+        self.cam_struct = cameras_struct(cams)
+        self.num_tiles = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in cams)
+        self.pixels = sum(c.width * c.height for c in cams)
+        if hasattr(self, "ranges") and self.ranges.numel() >= 2 * self.num_tiles:
+            return
+        self.ranges = torch.zeros(max(2, 2 * self.num_tiles), dtype=torch.int32, device=self.device)
+
+    def set_capacity(self, cap: int) -> None:
+        cap = int(cap)
+        if cap == self.capacity:
+            return
+        self.capacity = cap
+        self.vals = torch.empty(max(1, cap), dtype=torch.int32, device=self.device)
+        self.keys = torch.empty(max(1, cap), dtype=torch.int64, device=self.device) if self.keep_keys else None
+        self.ws_bin = torch.empty(self.L.gs_bin_sort_workspace(self.n, self.views, cap), dtype=torch.uint8,
+                                  device=self.device)
+        self.ws_bwd = torch.empty(self.L.gs_render_bwd_workspace(self.n, self.views, cap), dtype=torch.uint8,
+                                  device=self.device)
+
+    def bins_struct(self):
+        return _lib.GsBins(self.vals.data_ptr(), self.ranges.data_ptr(), self.pair_off.data_ptr(),
+                           self.keys.data_ptr() if self.keys is not None else None, self.counts.data_ptr(),
+                           self.capacity, self.num_tiles)
+
+    def new_image(self) -> torch.Tensor:
+        return torch.empty(3 * self.pixels, dtype=torch.float32, device=self.device)
+
+    def new_alpha(self) -> torch.Tensor:
+        return torch.empty(self.pixels, dtype=torch.float32, device=self.device)
+
+    def split(self, flat: torch.Tensor, channels: int) -> List[torch.Tensor]:
+        out, off = [], 0
+        for c in self.cams:
+            k = channels * c.width * c.height
+            t = flat[off:off + k]
+            out.append(t.view(channels, c.height, c.width) if channels > 1 else t.view(c.height, c.width))
+            off += k
+        return out
+
+    # -- stages -----------------------------------------------------------
+    def project(self, params: Arena, poses: torch.Tensor) -> None:
+        assert poses.is_contiguous() and poses.dtype == torch.float32 and poses.numel() == 12 * self.views
+        ps = params.struct()
+        _lib.check(self.L.gs_project(C.byref(ps), _p(poses), self.cam_struct, self.views, C.byref(self.cfg),
+                                     C.byref(self.splats), _stream()), "gs_project")
+
+    def bin_sort(self) -> None:
+        b = self.bins_struct()
+        _lib.check(self.L.gs_bin_sort(C.byref(self.splats), self.cam_struct, self.views, C.byref(self.cfg),
+                                      C.byref(b), _p(self.ws_bin), self.ws_bin.numel(), _stream()), "gs_bin_sort")
+
+    def render_fwd(self, image: torch.Tensor, alpha: Optional[torch.Tensor]) -> None:
+        b = self.bins_struct()
+        _lib.check(self.L.gs_render_fwd(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
+                                        C.byref(self.cfg), _p(image), _p(alpha), _stream()), "gs_render_fwd")
+
+    def read_counts(self) -> np.ndarray:
+        return self.counts.cpu().numpy().view(np.uint32).copy()
+
+    def forward(self, params: Arena, poses: torch.Tensor, image=None, alpha=None, check=True):
+        image = self.new_image() if image is None else image
+        self.project(params, poses)
+        self.bin_sort()
+        if check:
+            cnt = self.read_counts()
+            if cnt[2]:
+                self.set_capacity(int(cnt[1] * 1.25) + 1024)
+                self.bin_sort()
+                assert self.read_counts()[2] == 0
+        self.render_fwd(image, alpha)
+        return image, alpha
+
+    def backward(self, params: Arena, poses: torch.Tensor, dimage: torch.Tensor, dalpha: Optional[torch.Tensor],
+                 grads: Arena, dpose: Optional[torch.Tensor]) -> None:
+        ps = params.struct()
+        gs = grads.struct()
+        b = self.bins_struct()
+        _lib.check(self.L.gs_render_bwd(C.byref(ps), _p(poses), self.cam_struct, self.views, C.byref(self.splats),
+                                        C.byref(b), C.byref(self.cfg), _p(dimage), _p(dalpha), C.byref(gs),
+                                        _p(dpose), _p(self.ws_bwd), self.ws_bwd.numel(), _stream()),
+                   "gs_render_bwd")
+
+    def backward_pixels(self, dimage: torch.Tensor, dalpha: Optional[torch.Tensor] = None) -> None:
+        b = self.bins_struct()
+        _lib.check(self.L.gs_render_bwd_pixels(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
+                                               C.byref(self.cfg), _p(dimage), _p(dalpha), self.n, _p(self.ws_bwd),
+                                               self.ws_bwd.numel(), _stream()), "gs_render_bwd_pixels")
+
+    def backward_gaussians(self, params: Arena, poses: torch.Tensor, grads: Arena,
+                           dpose: Optional[torch.Tensor]) -> None:
+        ps = params.struct()
+        gs = grads.struct()
+        b = self.bins_struct()
+        _lib.check(self.L.gs_render_bwd_gaussians(C.byref(ps), _p(poses), self.cam_struct, self.views,
+                                                  C.byref(self.splats), C.byref(b), C.byref(self.cfg), C.byref(gs),
+                                                  _p(dpose), _p(self.ws_bwd), self.ws_bwd.numel(), _stream()),
+                   "gs_render_bwd_gaussians")
+
+    # -- splat records as tensors (tests, tools) -------------------------------
+    def splat_views(self) -> dict:
+        """Device tensor views of the splat arrays, shaped [V, n, ...]."""
+        m = self.n * self.views
+        sp = self.splats
+        base = self.splat_buf.data_ptr()
+
+        def view(ptr, count, dtype, shape):
+            off = ptr - base
+            nbytes = count * torch.tensor([], dtype=dtype).element_size()
+            return self.splat_buf[off:off + nbytes].view(dtype).view(shape)
+
+        V, n = self.views, self.n
+        return {"xy": view(sp.xy, 4 * m, torch.float32, (V, n, 4)),
+                "conic": view(sp.conic, 4 * m, torch.float32, (V, n, 4)),
+                "rgb": view(sp.rgb, 4 * m, torch.float32, (V, n, 4)),
+                "depth": view(sp.depth, m, torch.float32, (V, n)),
+                "rect": view(sp.rect, 2 * m, torch.int32, (V, n, 2)),
+                "touched": view(sp.touched, m, torch.int32, (V, n)),
+                "aux": view(sp.aux, m, torch.int32, (V, n))}
+
+    def splat_arrays(self) -> dict:
+        """Host copies of the splat arrays (unsigned fields as uint32)."""
+        out = {}
+        for k, t in self.splat_views().items():
+            a = t.cpu().numpy()
+            out[k] = a.view(np.uint32) if a.dtype == np.int32 else a
+        return out
+
+
+def adam_step(params: Arena, grads: Arena, m: Arena, v: Arena, step: int, groups, beta1=0.9, beta2=0.999,
+              eps=1e-15, status: Optional[torch.Tensor] = None, pose: Optional[torch.Tensor] = None,
+              dpose: Optional[torch.Tensor] = None, pose_m: Optional[torch.Tensor] = None,
+              pose_v: Optional[torch.Tensor] = None, pose_lr: float = 1e-4, pose_step: int = 0) -> None:
+    L = _lib.load()
+    garr = (_lib.GsAdamGroup * len(groups))(*groups)
+    cfg = _lib.GsAdamCfg(garr, len(groups), beta1, beta2, eps, _p(status), _p(pose), _p(dpose), _p(pose_m),
+                         _p(pose_v), pose.shape[0] if pose is not None else 0, pose_lr, int(pose_step))
+    _lib.check(L.gs_adam_step(_p(params.buf), _p(grads.buf), _p(m.buf), _p(v.buf), params.padded, C.byref(cfg),
+                              int(step), _stream()), "gs_adam_step")
+
+
+class ImageLoss:
+    """L1 (kind 0) or MSE (kind 1) of images against targets, with dL/dimage."""
+
+    def __init__(self, device="cuda"):
+        self.L = _lib.load()
+        self.ws = torch.empty(self.L.gs_image_loss_workspace(), dtype=torch.uint8, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+
+    def __call__(self, image: torch.Tensor, target: torch.Tensor, grad: Optional[torch.Tensor], kind: int = 0):
+        assert image.numel() == target.numel()
+        _lib.check(self.L.gs_image_loss(_p(image), _p(target), image.numel(), int(kind), _p(grad), _p(self.loss),
+                                        _p(self.ws), self.ws.numel(), _stream()), "gs_image_loss")
+        return self.loss

@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every entry point include/gs.h
+declares; host-side argument checks reject bad calls before any device work
+(no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2607_14481_b300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "gs.h")).read()
+    return sorted(set(re.findall(r"GS_API\s+[\w\s\*]+?\b(gs_\w+)\s*\(", text)))
+
+
+def test_header_declarations_match_binding_list():
+    assert set(_declared()) == set(_lib.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_arch(lib):
+    assert lib.gs_version() == 1
+    assert lib.gs_built_arch() == 1030
+
+
+def test_size_queries(lib):
+    a = lib.gs_splats_bytes(1000, 2)
+    b = lib.gs_splats_bytes(2000, 2)
+    assert 0 < a < b
+    # 3 float4 + depth + rect + touched + aux = 64 B per (view, Gaussian) + alignment
+    assert b >= 64 * 2000 * 2
+    assert lib.gs_bin_sort_workspace(1000, 1, 10_000) > lib.gs_bin_sort_workspace(1000, 1, 1000)
+    assert lib.gs_render_bwd_workspace(1000, 1, 10_000) >= 36 * 10_000
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    cam = (_lib.GsCamera * 1)(_lib.GsCamera(100.0, 100.0, 32.0, 32.0, 64, 64))
+    cfg = _lib.GsRasterCfg(16, 16, (C.c_float * 3)(0, 0, 0), 0.2, 1)
+    sp = _lib.GsSplats()
+    st = lib.gs_project(None, None, cam, 1, C.byref(cfg), C.byref(sp), None)
+    assert st == _lib.GS_ERR_INVALID
+    assert "params" in _lib.last_error()
+    params = _lib.GsParams(None, None, None, None, 0, 5)
+    st = lib.gs_project(C.byref(params), None, cam, 1, C.byref(cfg), C.byref(sp), None)
+    assert st == _lib.GS_ERR_INVALID and "sh_degree" in _lib.last_error()
+    bad = _lib.GsRasterCfg(8, 8, (C.c_float * 3)(0, 0, 0), 0.2, 1)
+    params = _lib.GsParams(None, None, None, None, 0, 0)
+    st = lib.gs_project(C.byref(params), None, cam, 1, C.byref(bad), C.byref(sp), None)
+    assert st == _lib.GS_ERR_INVALID and "tile" in _lib.last_error()
+    st = lib.gs_project(C.byref(params), None, cam, 0, C.byref(cfg), C.byref(sp), None)
+    assert st == _lib.GS_ERR_INVALID
+    grp = (_lib.GsAdamGroup * 1)(_lib.GsAdamGroup(0, 4, (C.c_float * 4)(1, 1, 1, 1)))
+    acfg = _lib.GsAdamCfg(grp, 1, 0.9, 0.999, 1e-15, None, None, None, None, None, 0, 0.0, 0)
+    st = lib.gs_adam_step(None, None, None, None, 0, C.byref(acfg), 0, None)
+    assert st == _lib.GS_ERR_INVALID and "step" in _lib.last_error()
+    st = lib.gs_adam_step(None, None, None, None, 4, C.byref(acfg), 1, None)
+    assert st == _lib.GS_ERR_INVALID
+    # a workspace that is too small is reported as GS_ERR_OOM before any launch
+    bins = _lib.GsBins(16, 16, 16, None, 16, 100, 16)
+    sp = _lib.GsSplats(256, 256, 256, 256, 256, 256, 256, 10, 1)
+    st = lib.gs_bin_sort(C.byref(sp), cam, 1, C.byref(cfg), C.byref(bins), C.c_void_p(256), 16, None)
+    assert st == _lib.GS_ERR_OOM and "workspace" in _lib.last_error()

@@ -193,3 +193,23 @@ def test_projected_covariance_against_fd_jacobian():
         assert np.allclose(proj[i, 1:3], m, rtol=0, atol=1e-9)
         # radius: ceil(3 sqrt(largest eigenvalue))
         assert proj[i, 11] == np.ceil(3 * np.sqrt(np.linalg.eigvalsh(S2).max()))
+
+
+def test_window_equals_crop_of_full_render():
+    # a pixel window composites exactly the same pixels as the full render
+    sc, cams, _ = synth.plain_small(13)
+    full = oracle.render(sc, cams)
+    win = [(37, 21, 50, 30)]
+    part = oracle.render(sc, cams, windows=win)
+    x0, y0, w, h = win[0]
+    assert np.array_equal(part["image"][0], full["image"][0][:, y0:y0 + h, x0:x0 + w])
+    assert np.array_equal(part["alpha"][0], full["alpha"][0][y0:y0 + h, x0:x0 + w])
+    # and the backward of a loss living in the window equals the full
+    # backward with the loss gradient zero outside it
+    g = np.random.default_rng(0).normal(size=(3, h, w))
+    gfull = np.zeros((3, 128, 128))
+    gfull[:, y0:y0 + h, x0:x0 + w] = g
+    a = oracle.backward(sc, cams, [g], windows=win)
+    b = oracle.backward(sc, cams, [gfull])
+    for k in a:
+        assert np.abs(a[k] - b[k]).max() <= 1e-12 * max(1.0, np.abs(b[k]).max())
