@@ -215,7 +215,7 @@ class Workload:
 
     def check_device_status(self):
         cnt = self.rast.read_counts()
-        assert cnt[2] == 0, "pair capacity overflow in the timed loop"
+        assert cnt[2] == 0, f"binning status {cnt[2]} in the timed loop (1 = capacity, 2 = index)"
         return int(self.status.item())
 
 
@@ -246,10 +246,12 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     t0.record()
     for i in range(K):
         wl.step(wl.targets[wl.step_no % N_POSES], evs[i])
     t1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()

@@ -149,8 +149,10 @@ typedef struct {
  *   keys      optional [capacity] (global tile << 32 | depth bits), sorted;
  *             NULL = not written
  *   counts    [4] status words written by the device: [0] visible
- *             (view, Gaussian) items, [1] pairs K, [2] 1 if K > capacity (the
- *             lists are then truncated and must not be rendered), [3]
+ *             (view, Gaussian) items, [1] pairs K, [2] status bits: 1 = K >
+ *             capacity (the lists are then truncated and must not be
+ *             rendered), 2 = an index read from an earlier stage was out of
+ *             range and its access was skipped (an internal error), [3]
  *             min(K, capacity) */
 typedef struct {
   uint32_t* vals;

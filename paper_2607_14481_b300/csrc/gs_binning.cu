@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-    const uint32_t* __restrict__ n_dev, int shift, const uint32_t* __restrict__ hist_scanned) {
+    const uint32_t* __restrict__ n_dev, int shift, const uint32_t* __restrict__ hist_scanned,
+    uint32_t n_cap) {
   __shared__ uint32_t s_wh[kThreads / 32][kRadixDigits];
   __shared__ uint32_t s_bo[kRadixDigits];
   const uint32_t n = *n_dev;
@@ -218,8 +219,10 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
   for (int r = 0; r < kIPT; ++r) {
     if (dig[r] < (uint32_t)kRadixDigits) {
       const uint32_t pos = s_bo[dig[r]] + s_wh[warp][dig[r]] + rank[r];
-      keys_out[pos] = key[r];
-      vals_out[pos] = val[r];
+      if (pos < n_cap) {  // always true for a consistent histogram
+        keys_out[pos] = key[r];
+        vals_out[pos] = val[r];
+      }
     }
   }
 }
@@ -243,20 +246,32 @@ __global__ void k_compact(const uint32_t* __restrict__ touched, const float* __r
   items[o] = (uint32_t)i;
 }
 
+// Status bits written to counts[2]: 1 = pair capacity exceeded, 2 = an index
+// read from an earlier stage was out of range (the access was skipped).
+constexpr uint32_t kStatusCapacity = 1u, kStatusIndex = 2u;
+
 __global__ void k_pair_counts(const uint32_t* __restrict__ items, const uint32_t* __restrict__ touched,
-                              const uint32_t* __restrict__ n_dev, uint32_t* __restrict__ cnt) {
+                              const uint32_t* __restrict__ n_dev, int64_t m, uint32_t* __restrict__ cnt,
+                              uint32_t* __restrict__ counts) {
   uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < *n_dev) cnt[j] = touched[items[j]];
+  if (j >= *n_dev || (int64_t)j >= m) return;
+  const uint32_t it = items[j];
+  if ((int64_t)it >= m) {
+    cnt[j] = 0;
+    atomicOr(&counts[2], kStatusIndex);
+    return;
+  }
+  cnt[j] = touched[it];
 }
 
-__global__ void k_init_counts(uint32_t* counts, uint32_t m) {
-  counts[0] = m;  // live length of the first (item) scan
-  counts[1] = 0; counts[2] = 0; counts[3] = 0;
+__global__ void k_init_counts(uint32_t* counts, uint32_t* m_dev, uint32_t m) {
+  *m_dev = m;  // live length of the first (item) scan; its total goes to counts[0]
+  counts[0] = 0; counts[1] = 0; counts[2] = 0; counts[3] = 0;
 }
 
 __global__ void k_pair_status(uint32_t* counts, int64_t cap) {
   const uint32_t K = counts[1];
-  counts[2] = (int64_t)K > cap ? 1u : 0u;
+  if ((int64_t)K > cap) counts[2] |= kStatusCapacity;
   counts[3] = (int64_t)K > cap ? (uint32_t)cap : K;
 }
 
@@ -274,8 +289,12 @@ struct EmitArgs {
 
 __global__ void __launch_bounds__(256) k_emit(const EmitArgs a, const ViewTable vt) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.counts[0]) return;
+  if (j >= a.counts[0] || (int64_t)j >= a.n * vt.views) return;
   const uint32_t item = a.items[j];
+  if ((int64_t)item >= a.n * vt.views) {
+    atomicOr(const_cast<uint32_t*>(&a.counts[2]), kStatusIndex);
+    return;
+  }
   const int v = (int)(item / (uint64_t)a.n);
   const uint32_t g = (uint32_t)(item - (uint64_t)v * a.n);
   const uint32_t off = a.poff[j];
@@ -283,6 +302,10 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a, const ViewTable 
   const uint2 rc = a.rect[item];
   const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
   const int TX = vt.v[v].TX;
+  if (x1 >= TX || y1 >= vt.v[v].TY) {
+    atomicOr(const_cast<uint32_t*>(&a.counts[2]), kStatusIndex);
+    return;
+  }
   const uint32_t tb = (uint32_t)vt.v[v].tile_base;
   uint64_t k = off;
   for (int ty = y0; ty <= y1; ++ty)
@@ -293,12 +316,16 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a, const ViewTable 
     }
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ counts,
-                         uint2* __restrict__ ranges) {
+__global__ void k_ranges(const uint32_t* __restrict__ tkeys, uint32_t* __restrict__ counts,
+                         uint2* __restrict__ ranges, uint32_t num_tiles) {
   const uint32_t K = counts[3];
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   const uint32_t g = tkeys[k];
+  if (g >= num_tiles) {
+    atomicOr(&counts[2], kStatusIndex);
+    return;
+  }
   if (k == 0 || tkeys[k - 1] != g) ranges[g].x = k;
   if (k == K - 1 || tkeys[k + 1] != g) ranges[g].y = k + 1;
 }
@@ -310,7 +337,8 @@ __global__ void k_full_keys(const uint32_t* __restrict__ tkeys, const uint32_t* 
   if (k >= counts[3]) return;
   const uint32_t g = tkeys[k];
   const int v = view_of_tile(vt, (int)g);
-  keys[k] = ((uint64_t)g << 32) | __float_as_uint(depth[(int64_t)v * n + vals[k]]);
+  const uint32_t gid = vals[k];
+  keys[k] = ((uint64_t)g << 32) | (gid < n ? __float_as_uint(depth[(int64_t)v * n + gid]) : 0u);
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -360,7 +388,8 @@ gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b
     k_radix_hist<<<(unsigned)nb, kThreads, 0, s>>>(ksrc, n_dev, shift, hist, hist_n);
     gs_status st = launch_scan(hist, hist, hist_n, kRadixDigits * nb, hist_total, scan_ws, s);
     if (st != GS_OK) return st;
-    k_radix_scatter<<<(unsigned)nb, kThreads, 0, s>>>(ksrc, vsrc, kdst, vdst, n_dev, shift, hist);
+    k_radix_scatter<<<(unsigned)nb, kThreads, 0, s>>>(ksrc, vsrc, kdst, vdst, n_dev, shift, hist,
+                                                       (uint32_t)n_cap);
     ksrc = kdst;
     vsrc = vdst;
   }
@@ -371,6 +400,7 @@ gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b
 // Workspace of gs_bin_sort: item arrays sized n*V, pair arrays sized capacity.
 // ---------------------------------------------------------------------------
 struct BinWs {
+  uint32_t* scalars;  // [0] = item count m (input length of the first scan)
   uint32_t *offs, *dk_a, *it_a, *dk_b, *it_b, *dk_s, *it_s, *cnt;
   uint32_t *tk_a, *tv_a, *tk_b, *tv_b, *tk_s;
   void* radix;
@@ -388,6 +418,7 @@ static BinWs bin_layout(char* base, int64_t m, int64_t cap) {
   };
   const size_t mi = sizeof(uint32_t) * (size_t)std::max<int64_t>(1, m);
   const size_t ci = sizeof(uint32_t) * (size_t)std::max<int64_t>(1, cap);
+  w.scalars = (uint32_t*)take(16);
   w.offs = (uint32_t*)take(mi);
   w.dk_a = (uint32_t*)take(mi); w.it_a = (uint32_t*)take(mi);
   w.dk_b = (uint32_t*)take(mi); w.it_b = (uint32_t*)take(mi);
@@ -411,20 +442,21 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   BinWs w = bin_layout(static_cast<char*>(ws), m, cap);
   uint32_t* counts = bins.counts;
   const int T = 256;
-  k_init_counts<<<1, 1, 0, s>>>(counts, (uint32_t)m);
+  k_init_counts<<<1, 1, 0, s>>>(counts, w.scalars, (uint32_t)m);
   if (cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)bins.num_tiles, s) != cudaSuccess)
     return check_launch("memset ranges");
   if (m == 0) return check_launch("bin_sort");
   // 1. compact the visible items in (view, id) order with their depth keys
   k_visible_flags<<<grid_for(m, T), T, 0, s>>>(sp.touched, m, w.offs);
-  gs_status st = launch_scan(w.offs, w.offs, counts, m, counts, w.scan, s);
+  // the scan's length (m) and its total (visible items -> counts[0]) must not alias
+  gs_status st = launch_scan(w.offs, w.offs, w.scalars, m, counts, w.scan, s);
   if (st != GS_OK) return st;
   k_compact<<<grid_for(m, T), T, 0, s>>>(sp.touched, sp.depth, w.offs, m, w.dk_a, w.it_a);
   // 2. stable sort of the visible items by depth
   st = launch_radix_sort(w.dk_a, w.it_a, w.dk_b, w.it_b, w.dk_s, w.it_s, counts, m, 32, w.radix, s);
   if (st != GS_OK) return st;
   // 3. pair offsets in depth order, emission, pair count status
-  k_pair_counts<<<grid_for(m, T), T, 0, s>>>(w.it_s, sp.touched, counts, w.cnt);
+  k_pair_counts<<<grid_for(m, T), T, 0, s>>>(w.it_s, sp.touched, counts, m, w.cnt, counts);
   st = launch_scan(w.cnt, w.cnt, counts, m, counts + 1, w.scan, s);
   if (st != GS_OK) return st;
   k_pair_status<<<1, 1, 0, s>>>(counts, cap);
@@ -438,7 +470,8 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
     st = launch_radix_sort(w.tk_a, w.tv_a, w.tk_b, w.tv_b, w.tk_s, bins.vals, counts + 3, cap, bits,
                            w.radix, s);
     if (st != GS_OK) return st;
-    k_ranges<<<grid_for(cap, T), T, 0, s>>>(w.tk_s, counts, reinterpret_cast<uint2*>(bins.ranges));
+    k_ranges<<<grid_for(cap, T), T, 0, s>>>(w.tk_s, counts, reinterpret_cast<uint2*>(bins.ranges),
+                                            (uint32_t)bins.num_tiles);
     if (bins.keys)
       k_full_keys<<<grid_for(cap, T), T, 0, s>>>(w.tk_s, bins.vals, counts, sp.depth, sp.n, bins.keys, vt);
   }

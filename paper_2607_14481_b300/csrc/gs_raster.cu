@@ -34,12 +34,21 @@ __device__ __forceinline__ bool splat_alpha(const float4 m, const float4 co, flo
   return e.alpha >= kAlphaMin;
 }
 
+// A splat that never passes the test (radius -1): stands in for an
+// out-of-range id, which is reported through counts[2] bit 2.
+__device__ __forceinline__ void null_splat(float4& m, float4& co, float4& col) {
+  m = make_float4(0.f, 0.f, 0.f, 0.f);
+  co = make_float4(0.f, 0.f, 0.f, 0.f);
+  col = make_float4(0.f, 0.f, 0.f, -1.f);
+}
+
 struct FwdArgs {
   const float4* xy;
   const float4* conic;
   const float4* rgb;
   const uint32_t* vals;
   const uint2* ranges;
+  uint32_t* counts;
   int64_t n;
   float bg[3];
   float* image;
@@ -66,10 +75,16 @@ __global__ void __launch_bounds__(kTilePixels) k_render_fwd(const FwdArgs a, con
     if (__syncthreads_count(done) == kTilePixels) break;
     const uint32_t j = start + threadIdx.x;
     if (j < rg.y) {
-      const int64_t gi = vbase + a.vals[j];
-      s_xy[threadIdx.x] = a.xy[gi];
-      s_co[threadIdx.x] = a.conic[gi];
-      s_rgb[threadIdx.x] = a.rgb[gi];
+      const uint32_t g = a.vals[j];
+      if (g < a.n) {
+        const int64_t gi = vbase + g;
+        s_xy[threadIdx.x] = a.xy[gi];
+        s_co[threadIdx.x] = a.conic[gi];
+        s_rgb[threadIdx.x] = a.rgb[gi];
+      } else {
+        null_splat(s_xy[threadIdx.x], s_co[threadIdx.x], s_rgb[threadIdx.x]);
+        atomicOr(&a.counts[2], 2u);
+      }
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kFwdBatch, rg.y - start);
@@ -103,7 +118,9 @@ struct BwdArgs {
   const uint32_t* pair_off;
   const uint32_t* vals;
   const uint2* ranges;
+  uint32_t* counts;
   int64_t n;
+  int64_t cap;
   float bg[3];
   const float* dimage;
   const float* dalpha;
@@ -139,10 +156,15 @@ __global__ void __launch_bounds__(kTilePixels) k_render_bwd(const BwdArgs a, con
     if (__syncthreads_count(done) == kTilePixels) break;
     const uint32_t j = start + threadIdx.x;
     if (threadIdx.x < kBwdBatch && j < rg.y) {
-      const int64_t gi = vbase + a.vals[j];
-      s_xy[threadIdx.x] = a.xy[gi];
-      s_co[threadIdx.x] = a.conic[gi];
-      s_rgb[threadIdx.x] = a.rgb[gi];
+      const uint32_t g = a.vals[j];
+      if (g < a.n) {
+        const int64_t gi = vbase + g;
+        s_xy[threadIdx.x] = a.xy[gi];
+        s_co[threadIdx.x] = a.conic[gi];
+        s_rgb[threadIdx.x] = a.rgb[gi];
+      } else {
+        null_splat(s_xy[threadIdx.x], s_co[threadIdx.x], s_rgb[threadIdx.x]);
+      }
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBwdBatch, rg.y - start);
@@ -173,8 +195,14 @@ __global__ void __launch_bounds__(kTilePixels) k_render_bwd(const BwdArgs a, con
 
   // pairs behind every pixel's last blended splat receive zero gradient
   for (uint32_t p = (uint32_t)(maxlast + 1) + threadIdx.x; p < rg.y; p += kTilePixels) {
-    const int64_t gi = vbase + a.vals[p];
+    const uint32_t g = a.vals[p];
+    if (g >= a.n) continue;
+    const int64_t gi = vbase + g;
     const uint32_t pidx = a.pair_off[gi] + rect_index(a.rect[gi], tx, ty);
+    if ((int64_t)pidx >= a.cap) {
+      atomicOr(&a.counts[2], 2u);
+      continue;
+    }
     float* dst = a.partials + (int64_t)pidx * kPartialStride;
 #pragma unroll
     for (int c = 0; c < kPartialStride; ++c) dst[c] = 0.f;
@@ -186,11 +214,18 @@ __global__ void __launch_bounds__(kTilePixels) k_render_bwd(const BwdArgs a, con
     const int cnt = bend - bstart;
     __syncthreads();
     if (threadIdx.x < cnt) {
-      const int64_t gi = vbase + a.vals[bstart + threadIdx.x];
-      s_xy[threadIdx.x] = a.xy[gi];
-      s_co[threadIdx.x] = a.conic[gi];
-      s_rgb[threadIdx.x] = a.rgb[gi];
-      s_pidx[threadIdx.x] = a.pair_off[gi] + rect_index(a.rect[gi], tx, ty);
+      const uint32_t g = a.vals[bstart + threadIdx.x];
+      uint32_t pidx = 0xffffffffu;
+      if (g < a.n) {
+        const int64_t gi = vbase + g;
+        s_xy[threadIdx.x] = a.xy[gi];
+        s_co[threadIdx.x] = a.conic[gi];
+        s_rgb[threadIdx.x] = a.rgb[gi];
+        pidx = a.pair_off[gi] + rect_index(a.rect[gi], tx, ty);
+      } else {
+        null_splat(s_xy[threadIdx.x], s_co[threadIdx.x], s_rgb[threadIdx.x]);
+      }
+      s_pidx[threadIdx.x] = pidx;
     }
     __syncthreads();
     for (int k = cnt - 1; k >= 0; --k) {
@@ -236,7 +271,8 @@ __global__ void __launch_bounds__(kTilePixels) k_render_bwd(const BwdArgs a, con
       }
     }
     __syncthreads();
-    if (threadIdx.x < cnt) {
+    if (threadIdx.x < cnt && (int64_t)s_pidx[threadIdx.x] >= a.cap) atomicOr(&a.counts[2], 2u);
+    if (threadIdx.x < cnt && (int64_t)s_pidx[threadIdx.x] < a.cap) {
       float* dst = a.partials + (int64_t)s_pidx[threadIdx.x] * kPartialStride;
 #pragma unroll
       for (int c = 0; c < kPartialStride; ++c) {
@@ -259,6 +295,7 @@ gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const View
   a.rgb = reinterpret_cast<const float4*>(sp.rgb);
   a.vals = bins.vals;
   a.ranges = reinterpret_cast<const uint2*>(bins.ranges);
+  a.counts = bins.counts;
   a.n = sp.n;
   for (int c = 0; c < 3; ++c) a.bg[c] = cfg.bg[c];
   a.image = image;
@@ -279,7 +316,9 @@ gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const View
   a.pair_off = bins.pair_off;
   a.vals = bins.vals;
   a.ranges = reinterpret_cast<const uint2*>(bins.ranges);
+  a.counts = bins.counts;
   a.n = sp.n;
+  a.cap = bins.capacity;
   for (int c = 0; c < 3; ++c) a.bg[c] = cfg.bg[c];
   a.dimage = dimage;
   a.dalpha = dalpha;

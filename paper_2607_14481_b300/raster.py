@@ -201,10 +201,13 @@ class Rasterizer:
         self.bin_sort()
         if check:
             cnt = self.read_counts()
-            if cnt[2]:
+            if cnt[2] & 2:
+                raise RuntimeError("gs_bin_sort reported an out-of-range index (internal error)")
+            if cnt[2] & 1:
                 self.set_capacity(int(cnt[1] * 1.25) + 1024)
                 self.bin_sort()
-                assert self.read_counts()[2] == 0
+                if self.read_counts()[2] != 0:
+                    raise RuntimeError("pair capacity still exceeded after growing it")
         self.render_fwd(image, alpha)
         return image, alpha
 
