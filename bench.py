@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--n", type=int, default=N_GAUSS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -136,112 +137,113 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-class Workload:
-    def __init__(self, n, device, rank=0):
-        import torch
-        from paper_2607_14481_b300 import raster, synth
-        self.torch = torch
-        self.raster = raster
-        self.n = n
-        self.device = device
-        self.scene = synth.box_scene(n, SEED_SCENE + 100 * rank)
-        self.cams = synth.forward_trajectory(N_POSES, SEED_TRAJ)
-        self.arena = raster.Arena.from_scene(self.scene, device)
-        self.grads = self.arena.like()
-        self.m = self.arena.like()
-        self.v = self.arena.like()
-        self.groups = self.arena.adam_groups(lr_means=1.6e-4 * 10.0)
-        self.poses = raster.poses_tensor(self.cams, device)
-        self.pose_m = torch.zeros((N_POSES, 6), dtype=torch.float32, device=device)
-        self.pose_v = torch.zeros((N_POSES, 6), dtype=torch.float32, device=device)
-        self.dpose = torch.zeros((N_POSES, 6), dtype=torch.float32, device=device)
-        self.pose_uses = [0] * N_POSES
-        self.rast = raster.Rasterizer(n, 3, self.cams[:1], device=device)
-        self.loss = raster.ImageLoss(device)
-        self.img = self.rast.new_image()
-        self.dimg = self.rast.new_image()
-        self.status = torch.zeros(1, dtype=torch.int32, device=device)
-        self.pixels = self.cams[0].width * self.cams[0].height
-        self._make_targets(synth)
-        self.step_no = 0
-
-    def _make_targets(self, synth):
-        torch = self.torch
-        pert = self.raster.Arena.from_scene(synth.perturbed(self.scene, SEED_TARGET), self.device)
-        self.targets = torch.empty((N_POSES, 3 * self.pixels), dtype=torch.float32, device=self.device)
-        kmax = 0
-        for k, c in enumerate(self.cams):
-            self.rast.set_cameras([c])
-            self.rast.forward(pert, self.poses[k:k + 1], self.targets[k], None, check=True)
-            kmax = max(kmax, int(self.rast.read_counts()[1]))
-        for k, c in enumerate(self.cams):  # the trained scene's own pair counts
-            self.rast.set_cameras([c])
-            self.rast.forward(self.arena, self.poses[k:k + 1], self.img, None, check=True)
-            kmax = max(kmax, int(self.rast.read_counts()[1]))
-        # fixed capacity for the timed loop: no host synchronisation inside it
-        self.rast.set_capacity(int(kmax * 1.3) + 4096)
-        self.kmax = kmax
-        self.targets_host = self.targets.cpu().pin_memory()
-        self.target_dev = torch.empty_like(self.targets[0])
-
-    def step(self, target, ev=None):
-        """One training iteration on the next pose.  ev: optional list of 7
-        CUDA events recorded at the stage boundaries."""
-        k = self.step_no % N_POSES
-        self.step_no += 1
-        r = self.rast
-        r.set_cameras([self.cams[k]])
-        pose = self.poses[k:k + 1]
-        rec = (lambda i: ev[i].record()) if ev is not None else (lambda i: None)
-        rec(0)
-        r.project(self.arena, pose)
-        rec(1)
-        r.bin_sort()
-        rec(2)
-        r.render_fwd(self.img, None)
-        rec(3)
-        self.loss(self.img, target, self.dimg, kind=0)
-        rec(4)
-        r.backward_pixels(self.dimg, None)
-        rec(5)
-        r.backward_gaussians(self.arena, pose, self.grads, self.dpose[k:k + 1])
-        rec(6)
-        self.pose_uses[k] += 1
-        self.raster.adam_step(self.arena, self.grads, self.m, self.v, self.step_no, self.groups,
-                              status=self.status, pose=pose, dpose=self.dpose[k:k + 1],
-                              pose_m=self.pose_m[k:k + 1], pose_v=self.pose_v[k:k + 1], pose_lr=1e-4,
-                              pose_step=self.pose_uses[k])
-        rec(7)
-
-    def check_device_status(self):
-        cnt = self.rast.read_counts()
-        assert cnt[2] == 0, f"binning status {cnt[2]} in the timed loop (1 = capacity, 2 = index)"
-        return int(self.status.item())
-
-
 STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd_pixels", "render_bwd_gaussians", "adam")
 
 
-def run_ours(args, ws, rank, local):
-    import torch
-    from paper_2607_14481_b300 import build
-    if rank == 0:
-        build.build()
-    barrier(ws)
-    device = torch.device("cuda", local)
-    torch.cuda.set_device(device)
-    wl = Workload(args.n, device, rank)
-    torch.cuda.synchronize()
-    # warm-up
-    for _ in range(max(3, args.warmup)):
-        wl.step(wl.targets[wl.step_no % N_POSES])
-    torch.cuda.synchronize()
+class Workload:
+    """Scene, optimiser state and per-view training steps for one set of views.
 
-    # ---- timed region: device-resident inputs, stage events on the launching stream
-    K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)]
-    clocks = ClockSampler(local)
-    clocks.start()
+    plain: one view per iteration, cycling through the 100-pose trajectory,
+    one captured CUDA graph per pose.  batched: all views of `cams` in every
+    iteration (one Adam step), one captured graph."""
+
+    def __init__(self, n, device, cams, batched, rank=0, use_graphs=True):
+        import torch
+        from paper_2607_14481_b300 import raster, synth, train
+        self.torch, self.raster = torch, raster
+        self.n, self.device, self.batched = n, device, batched
+        self.cams = list(cams)
+        self.scene = synth.box_scene(n, SEED_SCENE + 100 * rank)
+        self.arena = raster.Arena.from_scene(self.scene, device)
+        self.grads, self.m, self.v = self.arena.like(), self.arena.like(), self.arena.like()
+        self.groups = self.arena.adam_groups(lr_means=1.6e-4 * 10.0)
+        P = len(self.cams)
+        self.poses = raster.poses_tensor(self.cams, device)
+        self.pose_m = torch.zeros((P, 6), dtype=torch.float32, device=device)
+        self.pose_v = torch.zeros((P, 6), dtype=torch.float32, device=device)
+        self.pose_steps = torch.zeros(P, dtype=torch.int32, device=device)
+        self.step_dev = torch.zeros(1, dtype=torch.int32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        views = self.cams if batched else self.cams[:1]
+        self.rast = raster.Rasterizer(n, 3, views, device=device)
+        self.loss = raster.ImageLoss(device)
+        # targets: renders of a perturbed copy of the scene
+        pert = raster.Arena.from_scene(synth.perturbed(self.scene, SEED_TARGET), device)
+        groups = [self.cams] if batched else [[c] for c in self.cams]
+        self.view_pixels = [sum(c.width * c.height for c in g) for g in groups]
+        self.targets = [torch.empty(3 * px, dtype=torch.float32, device=device) for px in self.view_pixels]
+        kmax = 0
+        for k, g in enumerate(groups):
+            self.rast.set_cameras(g)
+            sl = slice(0, P) if batched else slice(k, k + 1)
+            self.rast.forward(pert, self.poses[sl], self.targets[k], None, check=True)
+            kmax = max(kmax, int(self.rast.read_counts()[1]))
+            self.rast.forward(self.arena, self.poses[sl], self.rast.new_image(), None, check=True)
+            kmax = max(kmax, int(self.rast.read_counts()[1]))
+        del pert
+        self.rast.set_capacity(int(kmax * 1.3) + 4096)  # fixed: no host synchronisation per step
+        self.kmax = kmax
+        img = self.rast.new_image() if batched else torch.empty(3 * max(self.view_pixels), device=device)
+        dimg = torch.empty_like(img)
+        self.steps = []
+        for k, g in enumerate(groups):
+            sl = slice(0, P) if batched else slice(k, k + 1)
+            px = self.view_pixels[k]
+            self.steps.append(train.TrainStep(
+                self.arena, self.grads, self.m, self.v, self.groups, self.rast, self.poses[sl], self.targets[k],
+                self.step_dev, pose_m=self.pose_m[sl], pose_v=self.pose_v[sl], pose_steps=self.pose_steps[sl],
+                pose_lr=1e-4, loss_kind=0, status=self.status, image=img[:3 * px], dimage=dimg[:3 * px],
+                loss=self.loss, cams=g))
+        if use_graphs:
+            self.pool = torch.cuda.graph_pool_handle()
+            for st in self.steps:
+                st.capture(pool=self.pool)
+        self.targets_host = [t.cpu().pin_memory() for t in self.targets]
+        self.i = 0
+        self.pixels_per_iter = self.view_pixels[0] if batched else self.cams[0].width * self.cams[0].height
+
+    def step(self):
+        st = self.steps[self.i % len(self.steps)]
+        self.i += 1
+        st.run()
+        return st
+
+    def instrumented_step(self, ev):
+        """The same iteration run eagerly with CUDA events at the stage
+        boundaries (on the launching stream)."""
+        st = self.steps[self.i % len(self.steps)]
+        self.i += 1
+        r = st.rast
+        r.set_cameras(st.cams)
+        ev[0].record()
+        r.project(st.arena, st.poses)
+        ev[1].record()
+        r.bin_sort()
+        ev[2].record()
+        r.render_fwd(st.img, None)
+        ev[3].record()
+        st.loss(st.img, st.targets, st.dimg, st.kind)
+        ev[4].record()
+        r.backward_pixels(st.dimg, None)
+        ev[5].record()
+        r.backward_gaussians(st.arena, st.poses, st.grads, st.dpose)
+        ev[6].record()
+        self.raster.adam_step(st.arena, st.grads, st.m, st.v, 0, st.groups, status=st.status, pose=st.poses,
+                              dpose=st.dpose, pose_m=st.pose_m, pose_v=st.pose_v, pose_lr=st.pose_lr,
+                              step_dev=st.step_dev, pose_steps_dev=st.pose_steps)
+        ev[7].record()
+
+    def check_device_status(self):
+        cnt = self.rast.read_counts()
+        assert cnt[2] == 0, f"binning status {cnt[2]} (1 = capacity, 2 = index)"
+        return int(self.status.item())
+
+
+def timed_loop(wl, K, ws, e2e=False):
+    """K iterations between a barrier + synchronize on both sides; device time
+    from CUDA events on the launching stream, max over ranks."""
+    import torch
+    loss_host = torch.zeros(max(K, 1), dtype=torch.float32).pin_memory() if e2e else None
     barrier(ws)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -249,62 +251,113 @@ def run_ours(args, ws, rank, local):
     torch.cuda.nvtx.range_push("timed")
     t0.record()
     for i in range(K):
-        wl.step(wl.targets[wl.step_no % N_POSES], evs[i])
+        if e2e:
+            k = wl.i % len(wl.steps)
+            wl.steps[k].targets.copy_(wl.targets_host[k], non_blocking=True)
+        st = wl.step()
+        if e2e:
+            loss_host[i:i + 1].copy_(st.loss.loss, non_blocking=True)
     t1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(ws)
-    clk = clocks.stop()
-    elapsed = t0.elapsed_time(t1) / 1e3
-    elapsed_max = allreduce_max(elapsed, ws)
-    stage_ms = {s: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K)]))
-                for j, s in enumerate(STAGES)}
-    bad = wl.check_device_status()
-    value = ws * K / elapsed_max
+    return allreduce_max(t0.elapsed_time(t1) / 1e3, ws)
 
-    # ---- end to end through the public API with host buffers
+
+def stage_times(wl, K):
+    """Per-stage device times (CUDA events on the launching stream) of K eager
+    iterations, and the blend work counts of each iteration's tile lists."""
+    import torch
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)]
+    counts = []
+    torch.cuda.nvtx.range_push("eager")
+    for i in range(K):
+        wl.instrumented_step(evs[i])
+        if i < 8:
+            counts.append(wl.rast.render_stats())
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = {s: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K)]))
+          for j, s in enumerate(STAGES)}
+    work = {k: float(np.mean([c[k] for c in counts])) for k in counts[0]}
+    return ms, work
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2607_14481_b300 import build, synth
+    if rank == 0:
+        build.build()
+    barrier(ws)
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    K = args.steps
+    # ---- plain single-view training (the headline)
+    wl = Workload(args.n, device, synth.forward_trajectory(N_POSES, SEED_TRAJ), batched=False, rank=rank)
+    for _ in range(max(3, args.warmup)):
+        wl.step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    elapsed = timed_loop(wl, K, ws)
+    clk = clocks.stop()
+    bad = wl.check_device_status()
+    value = ws * K / elapsed
     e2e = None
     if not args.no_e2e:
-        loss_host = torch.zeros(K, dtype=torch.float32).pin_memory()
-        barrier(ws)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for i in range(K):
-            k = wl.step_no % N_POSES
-            wl.target_dev.copy_(wl.targets_host[k], non_blocking=True)
-            wl.step(wl.target_dev)
-            loss_host[i:i + 1].copy_(wl.loss.loss, non_blocking=True)
-        e1.record()
-        torch.cuda.synchronize()
-        barrier(ws)
-        e_el = allreduce_max(e0.elapsed_time(e1) / 1e3, ws)
+        e_el = timed_loop(wl, K, ws, e2e=True)
         e2e = {"value": ws * K / e_el, "unit": "iters/s",
-               "h2d_bytes_per_step": int(wl.target_dev.numel() * 4),
-               "d2h_bytes_per_step": 4,
+               "h2d_bytes_per_step": int(wl.targets[0].numel() * 4), "d2h_bytes_per_step": 4,
                "ms_per_step": 1e3 * e_el / K}
         wl.check_device_status()
-
-    # ---- roofline of the dominant stage
+    stage_ms, work = stage_times(wl, min(K, 30))
+    wl.check_device_status()
     peaks = load_peaks()
-    roof = roofline(wl, stage_ms, peaks)
+    roof = roofline(wl, stage_ms, work, peaks)
+    plain_pixels = wl.pixels_per_iter
+    n_launch = launches_per_step(1, wl.rast.num_tiles)
+    del wl
+    torch.cuda.empty_cache()
+
+    # ---- batched: 16 views of uneven size per iteration (one Adam step)
+    batched = None
+    if not args.no_batched:
+        cams16 = synth.loop_views(16, SEED_TRAJ + 1)
+        wb = Workload(args.n, device, cams16, batched=True, rank=rank)
+        for _ in range(max(3, args.warmup)):
+            wb.step()
+        torch.cuda.synchronize()
+        Kb = max(5, K // 8)
+        eb = timed_loop(wb, Kb, ws)
+        wb.check_device_status()
+        sb, wkb = stage_times(wb, min(Kb, 10))
+        batched = {"views_per_iter": 16, "iters_per_s": ws * Kb / eb,
+                   "view_iters_per_s": ws * 16 * Kb / eb,
+                   "mpix_per_s": ws * Kb * wb.pixels_per_iter / eb / 1e6,
+                   "ms_per_iter": 1e3 * eb / Kb, "steps": Kb,
+                   "pixels_per_iter": wb.pixels_per_iter, "pairs_max": wb.kmax,
+                   "resolutions": [[c.width, c.height] for c in cams16], "stage_ms": sb,
+                   "roofline": roofline(wb, sb, wkb, load_peaks()),
+                   "vs_plain_view_iters": (16 * Kb / eb) / (K / elapsed)}
+        del wb
+        torch.cuda.empty_cache()
+
     out = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": K,
-        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / K, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"plain single-view training, {args.n} Gaussians SH3, 1280x720, "
-                               f"100-pose forward trajectory, L1 loss",
+                               f"100-pose forward trajectory, L1 loss, one CUDA graph per pose",
                    "gaussians": args.n, "views_per_iter": 1, "resolution": [1280, 720],
-                   "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (parameter arena "
-                   f"{wl.arena.padded * 4 / 1e6:.0f} MB x4)",
-                   "pairs_max": wl.kmax, "capacity": wl.rast.capacity},
-        "mpix_per_s": value * wl.pixels / 1e6,
+                   "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (parameter arena 240 MB, x4 with gradients and moments)"},
+        "mpix_per_s": value * plain_pixels / 1e6,
         "stage_ms": stage_ms,
         "e2e": e2e,
         "roofline": roof,
+        "batched": batched,
         "clocks": clk,
-        "gpu_launches": launches_per_step() * K,
+        "gpu_launches": n_launch * K,
         "nonfinite_flag": bad,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -312,12 +365,13 @@ def run_ours(args, ws, rank, local):
     return out, rank
 
 
-def launches_per_step():
-    # project 1; bin_sort: init 1 + flags 1 + scan 3 + compact 1 + 4 x (hist 1 + scan 3 + scatter 1) +
-    # pair counts 1 + scan 3 + status 1 + emit 1 + 2 x 5 + ranges 1 (+ memset); fwd 1; loss 2;
-    # bwd pixels 1; bwd gaussians 2; adam 2
-    bin_sort = 1 + 1 + 3 + 1 + 4 * 5 + 1 + 3 + 1 + 1 + 2 * 5 + 1
-    return 1 + bin_sort + 1 + 2 + 1 + 2 + 2
+def launches_per_step(views, num_tiles):
+    """Kernels one training step launches (memsets excluded)."""
+    bits = max(1, int(np.ceil(np.log2(max(2, num_tiles)))))
+    tile_passes = (bits + 7) // 8
+    scan = 3
+    bin_sort = 1 + 1 + scan + 1 + 4 * (2 + scan) + 1 + scan + 1 + 1 + tile_passes * (2 + scan) + 1
+    return 1 + bin_sort + 1 + 2 + 1 + 3 + 3
 
 
 def load_peaks():
@@ -330,24 +384,52 @@ def load_peaks():
         return {"hbm_gbs": 6400.0, "source": "fallback", "sm_max_mhz": 2032.0}
 
 
-def roofline(wl, stage_ms, peaks):
-    """Algorithmic bytes of the HBM-bound stages per launch:
-    adam 28 B per arena element; project 308 B per (view, Gaussian) at SH3
-    (240 B of parameters read, 68 B of splat record written)."""
+# FP32 operations per (pixel, splat) pair, counted from the kernels' source:
+# the splat test (offsets 6, box test 2, quadratic form 7, power test 1,
+# exp 2, opacity product 1, clamp 1, threshold 1) = 21; a forward blend
+# (1 - alpha, transmittance, stop test, weight, 3 colour FMAs) = 7; a backward
+# blend (reciprocal, transmittance, weights, alpha gradient, suffix colour,
+# opacity, quadratic-form and mean gradients) = 50 + 4 replay + 9 reduction adds.
+OPS_TEST, OPS_FWD_BLEND, OPS_BWD_BLEND = 21, 7, 63
+
+
+def roofline(wl, stage_ms, work, peaks):
+    """Achieved fraction of each stage's bound; the dominant stage's object is
+    the JSON line's roofline.  HBM stages count algorithmic bytes per launch,
+    the blend stages FP32 operations per launch (work counts from
+    gs_render_stats) against the FP32 issue rate at the maximum SM clock."""
     n = wl.n
-    algo = {"adam": 28.0 * wl.arena.padded,
-            "project": (16 * 3 + 3 * 16 * 4 + 68.0) * n,
-            "render_bwd_gaussians": None, "render_fwd": None, "render_bwd_pixels": None,
-            "bin_sort": None, "loss": 3 * 4 * 3.0 * wl.pixels}
-    dom = max(stage_ms, key=stage_ms.get)
-    hbm_stages = {k: v for k, v in algo.items() if v is not None}
-    pick = dom if dom in hbm_stages else max(hbm_stages, key=lambda k: stage_ms[k])
-    t = stage_ms[pick] / 1e3
-    ach = hbm_stages[pick] / t / 1e9
-    return {"kernel": pick, "dominant_stage": dom, "bound": "hbm", "achieved": ach,
-            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
-            "peak_source": peaks["source"] + " (copy, burst)", "traffic": None,
-            "algorithmic_bytes": hbm_stages[pick]}
+    V = len(wl.steps[0].cams)
+    nc = 16
+    K = work["listed"]
+    fp32_peak = 148 * 128 * peaks["sm_max_mhz"] * 1e6 / 1e9  # Gop/s
+    per = {
+        "project": ("hbm", (48 + 3 * nc * 4) * n + 68.0 * n * V),
+        "render_bwd_gaussians": ("hbm", (48 + 3 * nc * 4) * n + (48 + 3 * nc * 4) * n + 36.0 * K
+                                 + (12 + 16) * n * V + (16 + 12 + 16) * n * V),
+        "adam": ("hbm", 28.0 * wl.arena.padded),
+        "loss": ("hbm", 3 * 4 * 3.0 * wl.pixels_per_iter),
+        "render_fwd": ("alu", OPS_TEST * work["tested"] + OPS_FWD_BLEND * work["blended"]),
+        "render_bwd_pixels": ("alu", 2 * OPS_TEST * work["tested"] + OPS_BWD_BLEND * work["blended"]),
+    }
+    table = {}
+    for k, (bound, amount) in per.items():
+        t = stage_ms[k] / 1e3
+        if bound == "hbm":
+            ach = amount / t / 1e9
+            table[k] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / peaks["hbm_gbs"], "algorithmic": amount}
+        else:
+            ach = amount / t / 1e9
+            table[k] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "Gop/s",
+                        "frac": ach / fp32_peak, "algorithmic": amount}
+    dom = max(per, key=lambda k: stage_ms[k])
+    out = dict(table[dom])
+    out.update({"kernel": dom, "traffic": None,
+                "peak_source": (f"{peaks['source']} HBM copy (burst)" if out["bound"] == "hbm" else
+                                "148 SMs x 128 FP32 lanes x max SM clock"),
+                "work_counts": work, "per_stage": table})
+    return out
 
 
 # ---------------------------------------------------------------------------

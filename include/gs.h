@@ -166,7 +166,8 @@ typedef struct {
 
 /* One Adam parameter group: elements [begin, end) of the arena; element e
  * uses learning rate lr[(e - begin) & 3] (so one float4 group can give its
- * four lanes different rates, e.g. log-scales and the opacity logit). */
+ * four lanes different rates, e.g. log-scales and the opacity logit).  Groups
+ * must not overlap. */
 typedef struct {
   int64_t begin, end;
   float lr[4];
@@ -190,6 +191,12 @@ typedef struct {
   float pose_lr;
   int32_t pose_step;           /* bias-correction step of the pose moments
                                   (0 = the parameters' step) */
+  /* optional device step counters, for replaying a captured step: when
+   * step_dev is set, the `step` argument is ignored, the update uses
+   * *step_dev + 1 and then increments *step_dev; when pose_steps_dev ([V])
+   * is set, view v's pose update uses pose_steps_dev[v] + 1 and increments it. */
+  int32_t* step_dev;
+  int32_t* pose_steps_dev;
 } gs_adam_cfg;
 
 /* ---------------------------------------------------------------------- */
@@ -278,12 +285,24 @@ GS_API gs_status gs_render_bwd_gaussians(const gs_params* params, const float* p
                                          float* dL_dpose, void* ws, size_t ws_bytes, gs_stream stream);
 
 /* Fused Adam over one flat float arena of n elements (parameters p, gradients
- * g, moments m, v; all device, 16-byte aligned):
+ * g, moments m, v; all device, 16-byte aligned), in one launch for all groups
+ * (the standard Adam update, bias-corrected):
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
  *   p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps)
- * Elements outside every group are left unchanged.  step >= 1. */
+ * Elements outside every group are left unchanged.  step >= 1 (unless
+ * cfg->step_dev is set). */
 GS_API gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
                        const gs_adam_cfg* cfg, int32_t step, gs_stream stream);
+
+/* Work counts of one forward composite (diagnostics for roofline accounting;
+ * no image is written): stats_dev[0] = (pixel, splat) pairs tested, up to and
+ * including the splat that stops a pixel; [1] = pairs blended; [2] = sum over
+ * tiles of the backward's reverse-walk length (list positions up to the last
+ * blended splat of any pixel of the tile); [3] = sum over tiles of the list
+ * length.  stats_dev: device, 4 uint64, 8-byte aligned, overwritten. */
+GS_API gs_status gs_render_stats(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
+                                 int32_t views, const gs_raster_cfg* cfg, uint64_t* stats_dev,
+                                 gs_stream stream);
 
 /* Image loss of a training step over `count` floats (all views' images):
  * kind 0 = L1, mean |image - target|; kind 1 = mean squared error.  The paper

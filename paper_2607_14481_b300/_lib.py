@@ -20,7 +20,7 @@ EXPORTED = (
     "gs_last_error", "gs_version", "gs_built_arch", "gs_splats_bytes", "gs_splats_carve",
     "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_render_fwd",
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
-    "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss",
+    "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
 )
 
 
@@ -68,7 +68,8 @@ class GsAdamCfg(C.Structure):
     _fields_ = [("groups", C.POINTER(GsAdamGroup)), ("num_groups", C.c_int32), ("beta1", C.c_float),
                 ("beta2", C.c_float), ("eps", C.c_float), ("status", C.c_void_p), ("pose", C.c_void_p),
                 ("dpose", C.c_void_p), ("pose_m", C.c_void_p), ("pose_v", C.c_void_p),
-                ("views", C.c_int32), ("pose_lr", C.c_float), ("pose_step", C.c_int32)]
+                ("views", C.c_int32), ("pose_lr", C.c_float), ("pose_step", C.c_int32),
+                ("step_dev", C.c_void_p), ("pose_steps_dev", C.c_void_p)]
 
 
 _lib = None
@@ -108,11 +109,13 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_render_bwd_gaussians.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsSplats), P(GsBins),
                                           P(GsRasterCfg), P(GsGrads), vp, vp, sz, vp]
     L.gs_adam_step.argtypes = [vp, vp, vp, vp, i64, P(GsAdamCfg), i32, vp]
+    L.gs_render_stats.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp]
     L.gs_image_loss_workspace.argtypes = []
     L.gs_image_loss_workspace.restype = sz
     L.gs_image_loss.argtypes = [vp, vp, i64, i32, vp, vp, vp, sz, vp]
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
-                 "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss"):
+                 "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
+                 "gs_render_stats"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

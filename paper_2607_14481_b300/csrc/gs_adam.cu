@@ -9,6 +9,9 @@ namespace gs {
 
 namespace {
 
+constexpr int kAdamThreads = 256;
+constexpr int64_t kAdamChunk = kAdamThreads * 4 * 4;  // elements per block (4 float4 per thread)
+
 struct AdamArgs {
   float* p;
   const float* g;
@@ -19,56 +22,71 @@ struct AdamArgs {
   float bc1, bc2;           // 1 - beta^step
   int num_groups;
   gs_adam_group groups[GS_MAX_ADAM_GROUPS];
+  int32_t block_start[GS_MAX_ADAM_GROUPS + 1];  // first block of each group
   uint32_t* status;
+  const int32_t* step_dev;  // optional: step = *step_dev + 1
 };
 
+// 1 - beta^step in double, rounded once
+__device__ __forceinline__ float bias_corr(float beta, int step) {
+  return (float)(1.0 - pow((double)beta, (double)step));
+}
+
 __device__ __forceinline__ bool adam_elem(float& p, float g, float& m, float& v, float lr,
-                                          const AdamArgs& a) {
+                                          const AdamArgs& a, float bc1, float bc2) {
   m = a.b1 * m + (1.f - a.b1) * g;
   v = a.b2 * v + (1.f - a.b2) * g * g;
-  const float mh = m / a.bc1, vh = v / a.bc2;
+  const float mh = m / bc1, vh = v / bc2;
   p -= lr * mh / (sqrtf(vh) + a.eps);
   return isfinite(g) && isfinite(v);
 }
 
-__device__ __forceinline__ float lr_of(const AdamArgs& a, int64_t e, bool& in_group) {
-  for (int k = 0; k < a.num_groups; ++k) {
-    const gs_adam_group& G = a.groups[k];
-    if (e >= G.begin && e < G.end) { in_group = true; return G.lr[(e - G.begin) & 3]; }
+// Block b updates one chunk of one group: the group is found once per block
+// (no per-element search); the chunk's 16-byte aligned body is processed as
+// float4, its ragged head and tail element by element.
+__global__ void __launch_bounds__(kAdamThreads) k_adam(const AdamArgs a) {
+  __shared__ float s_bc[2];
+  float bc1 = a.bc1, bc2 = a.bc2;
+  if (a.step_dev) {
+    if (threadIdx.x == 0) {
+      const int st = *a.step_dev + 1;
+      s_bc[0] = bias_corr(a.b1, st);
+      s_bc[1] = bias_corr(a.b2, st);
+    }
+    __syncthreads();
+    bc1 = s_bc[0];
+    bc2 = s_bc[1];
   }
-  in_group = false;
-  return 0.f;
-}
-
-// Grid-stride over float4 chunks (the arena is 16-byte aligned); the scalar
-// tail is handled by the first threads.
-__global__ void __launch_bounds__(256) k_adam(const AdamArgs a) {
-  const int64_t n4 = a.n / 4;
+  const int b = blockIdx.x;
+  int gi = 0;
+  while (gi + 1 < a.num_groups && a.block_start[gi + 1] <= b) ++gi;
+  const gs_adam_group G = a.groups[gi];
+  const int64_t r0 = G.begin + (int64_t)(b - a.block_start[gi]) * kAdamChunk;
+  const int64_t r1 = min(G.end, r0 + kAdamChunk);
+  if (r0 >= r1) return;
+  const int64_t a0 = min(r1, (r0 + 3) & ~(int64_t)3);  // first 16-byte aligned element
+  const int64_t a1 = max(a0, r1 & ~(int64_t)3);        // end of the float4 body
   bool bad = false;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n4;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = r0 + threadIdx.x; e < a0; e += kAdamThreads)
+    bad |= !adam_elem(a.p[e], a.g[e], a.m[e], a.v[e], G.lr[(e - G.begin) & 3], a, bc1, bc2);
+  const int rot = (int)((a0 - G.begin) & 3);
+  const float lr4[4] = {G.lr[rot & 3], G.lr[(rot + 1) & 3], G.lr[(rot + 2) & 3], G.lr[(rot + 3) & 3]};
+#pragma unroll 4
+  for (int64_t c = a0 / 4 + threadIdx.x; c < a1 / 4; c += kAdamThreads) {
     float4 p = reinterpret_cast<float4*>(a.p)[c];
     const float4 g = reinterpret_cast<const float4*>(a.g)[c];
     float4 m = reinterpret_cast<float4*>(a.m)[c];
     float4 v = reinterpret_cast<float4*>(a.v)[c];
-    float* pp = &p.x; const float* gg = &g.x; float* mm = &m.x; float* vv = &v.x;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      bool in;
-      const float lr = lr_of(a, 4 * c + k, in);
-      if (in) bad |= !adam_elem(pp[k], gg[k], mm[k], vv[k], lr, a);
-    }
+    bad |= !adam_elem(p.x, g.x, m.x, v.x, lr4[0], a, bc1, bc2);
+    bad |= !adam_elem(p.y, g.y, m.y, v.y, lr4[1], a, bc1, bc2);
+    bad |= !adam_elem(p.z, g.z, m.z, v.z, lr4[2], a, bc1, bc2);
+    bad |= !adam_elem(p.w, g.w, m.w, v.w, lr4[3], a, bc1, bc2);
     reinterpret_cast<float4*>(a.p)[c] = p;
     reinterpret_cast<float4*>(a.m)[c] = m;
     reinterpret_cast<float4*>(a.v)[c] = v;
   }
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t e = 4 * n4 + t;
-  if (t < 4 && e < a.n) {
-    bool in;
-    const float lr = lr_of(a, e, in);
-    if (in) bad |= !adam_elem(a.p[e], a.g[e], a.m[e], a.v[e], lr, a);
-  }
+  for (int64_t e = a1 + threadIdx.x; e < r1; e += kAdamThreads)
+    bad |= !adam_elem(a.p[e], a.g[e], a.m[e], a.v[e], G.lr[(e - G.begin) & 3], a, bc1, bc2);
   if (bad && a.status) atomicOr(a.status, 1u);
 }
 
@@ -80,6 +98,8 @@ struct PoseArgs {
   int views;
   float lr, b1, b2, eps, bc1, bc2;
   uint32_t* status;
+  const int32_t* step_dev;  // optional shared step (*step_dev + 1)
+  int32_t* pose_steps;      // optional per-view steps, incremented here
 };
 
 // Pose step per view: Adam on xi (zero-based tangent), then the SE(3)
@@ -87,6 +107,17 @@ struct PoseArgs {
 __global__ void k_pose_adam(const PoseArgs a) {
   const int vw = blockIdx.x * blockDim.x + threadIdx.x;
   if (vw >= a.views) return;
+  float bc1 = a.bc1, bc2 = a.bc2;
+  if (a.pose_steps) {
+    const int st = a.pose_steps[vw] + 1;
+    a.pose_steps[vw] = st;
+    bc1 = bias_corr(a.b1, st);
+    bc2 = bias_corr(a.b2, st);
+  } else if (a.step_dev) {
+    const int st = *a.step_dev + 1;
+    bc1 = bias_corr(a.b1, st);
+    bc2 = bias_corr(a.b2, st);
+  }
   float xi[6];
   bool bad = false;
   for (int k = 0; k < 6; ++k) {
@@ -95,7 +126,7 @@ __global__ void k_pose_adam(const PoseArgs a) {
     const float m = a.b1 * a.m[j] + (1.f - a.b1) * g;
     const float v = a.b2 * a.v[j] + (1.f - a.b2) * g * g;
     a.m[j] = m; a.v[j] = v;
-    xi[k] = -a.lr * (m / a.bc1) / (sqrtf(v / a.bc2) + a.eps);
+    xi[k] = -a.lr * (m / bc1) / (sqrtf(v / bc2) + a.eps);
     bad |= !isfinite(g);
   }
   const float wx = xi[3], wy = xi[4], wz = xi[5];
@@ -138,6 +169,8 @@ __global__ void k_pose_adam(const PoseArgs a) {
   if (bad && a.status) atomicOr(a.status, 1u);
 }
 
+__global__ void k_step_increment(int32_t* step) { *step += 1; }
+
 }  // namespace
 
 gs_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
@@ -148,17 +181,16 @@ gs_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
   a.bc1 = (float)(1.0 - std::pow((double)cfg.beta1, step));
   a.bc2 = (float)(1.0 - std::pow((double)cfg.beta2, step));
   a.num_groups = cfg.num_groups;
-  for (int k = 0; k < cfg.num_groups; ++k) a.groups[k] = cfg.groups[k];
-  a.status = cfg.status;
-  if (n > 0) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t n4 = std::max<int64_t>(1, n / 4);
-    const int64_t want = (n4 + 255) / 256;
-    const int64_t grid = std::min<int64_t>(want, (int64_t)sms * 8);  // 8 resident CTAs per SM
-    k_adam<<<(unsigned)grid, 256, 0, s>>>(a);
+  int64_t blocks = 0;
+  for (int k = 0; k < cfg.num_groups; ++k) {
+    a.groups[k] = cfg.groups[k];
+    a.block_start[k] = (int32_t)blocks;
+    blocks += (cfg.groups[k].end - cfg.groups[k].begin + kAdamChunk - 1) / kAdamChunk;
   }
+  a.block_start[cfg.num_groups] = (int32_t)blocks;
+  a.status = cfg.status;
+  a.step_dev = cfg.step_dev;
+  if (n > 0 && blocks > 0) k_adam<<<(unsigned)blocks, kAdamThreads, 0, s>>>(a);
   if (cfg.pose && cfg.views > 0) {
     PoseArgs pa;
     pa.pose = cfg.pose; pa.dpose = cfg.dpose; pa.m = cfg.pose_m; pa.v = cfg.pose_v;
@@ -167,8 +199,11 @@ gs_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
     pa.bc1 = (float)(1.0 - std::pow((double)cfg.beta1, ps));
     pa.bc2 = (float)(1.0 - std::pow((double)cfg.beta2, ps));
     pa.status = cfg.status;
+    pa.step_dev = cfg.step_dev;
+    pa.pose_steps = cfg.pose_steps_dev;
     k_pose_adam<<<(cfg.views + 63) / 64, 64, 0, s>>>(pa);
   }
+  if (cfg.step_dev) k_step_increment<<<1, 1, 0, s>>>(cfg.step_dev);
   return check_launch("adam");
 }
 

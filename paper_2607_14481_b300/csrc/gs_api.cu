@@ -217,7 +217,7 @@ gs_status gs_render_fwd(const gs_splats* splats, const gs_bins* bins, const gs_c
 }
 
 static size_t bwd_layout(int64_t n, int32_t views, int64_t capacity, char* base, float** partials,
-                         float** pose_partials, int* pose_blocks) {
+                         float** pose_partials, int* pose_blocks, float** drgb = nullptr) {
   const int blocks = (int)std::max<int64_t>(1, (n + kGradBlock - 1) / kGradBlock);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -227,6 +227,8 @@ static size_t bwd_layout(int64_t n, int32_t views, int64_t capacity, char* base,
   };
   float* pa = (float*)take(sizeof(float) * kPartialStride * (size_t)std::max<int64_t>(0, capacity));
   float* pp = (float*)take(sizeof(float) * 6 * (size_t)blocks * (size_t)std::max(1, views));
+  float* dc = (float*)take(sizeof(float) * 4 * (size_t)std::max<int64_t>(0, n) * (size_t)std::max(1, views));
+  if (drgb) *drgb = dc;
   if (partials) *partials = pa;
   if (pose_partials) *pose_partials = pp;
   if (pose_blocks) *pose_blocks = blocks;
@@ -280,11 +282,12 @@ gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_de
   if (!ws || ws_bytes < need)
     return fail(GS_ERR_OOM, "render_bwd workspace: need %zu bytes, got %zu", need, ws_bytes);
   if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
-  float *partials, *pose_partials;
+  float *partials, *pose_partials, *drgb;
   int pose_blocks;
-  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks);
+  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks,
+             &drgb);
   return launch_project_bwd(*params, poses_dev, vt, *cfg, *splats, *bins, partials, *grads, pose_partials,
-                            pose_blocks, dL_dpose, (cudaStream_t)stream);
+                            pose_blocks, dL_dpose, drgb, (cudaStream_t)stream);
 }
 
 gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const gs_camera* cams,
@@ -311,21 +314,22 @@ gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const g
   if (!ws || ws_bytes < need)
     return fail(GS_ERR_OOM, "render_bwd workspace: need %zu bytes, got %zu", need, ws_bytes);
   if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
-  float *partials, *pose_partials;
+  float *partials, *pose_partials, *drgb;
   int pose_blocks;
-  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks);
+  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks,
+             &drgb);
   cudaStream_t s = (cudaStream_t)stream;
   st = launch_render_bwd(*splats, *bins, vt, *cfg, dL_dimage, dL_dalpha, partials, s);
   if (st != GS_OK) return st;
   return launch_project_bwd(*params, poses_dev, vt, *cfg, *splats, *bins, partials, *grads, pose_partials,
-                            pose_blocks, dL_dpose, s);
+                            pose_blocks, dL_dpose, drgb, s);
 }
 
 gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
                        const gs_adam_cfg* cfg, int32_t step, gs_stream stream) {
   if (!cfg) return fail(GS_ERR_INVALID, "cfg is NULL");
   if (n < 0) return fail(GS_ERR_INVALID, "n < 0");
-  if (step < 1) return fail(GS_ERR_INVALID, "step must be >= 1");
+  if (step < 1 && !cfg->step_dev) return fail(GS_ERR_INVALID, "step must be >= 1");
   if (n > 0 && (!p || !g || !m || !v)) return fail(GS_ERR_INVALID, "NULL arena");
   if (!aligned(p, 16) || !aligned(g, 16) || !aligned(m, 16) || !aligned(v, 16))
     return fail(GS_ERR_INVALID, "arenas must be 16-byte aligned");
@@ -334,12 +338,32 @@ gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
   for (int k = 0; k < cfg->num_groups; ++k) {
     const gs_adam_group& G = cfg->groups[k];
     if (G.begin < 0 || G.end < G.begin || G.end > n) return fail(GS_ERR_INVALID, "group %d out of range", k);
+    for (int j = 0; j < k; ++j) {
+      const gs_adam_group& H = cfg->groups[j];
+      if (G.begin < H.end && H.begin < G.end) return fail(GS_ERR_INVALID, "groups %d and %d overlap", j, k);
+    }
+    if ((G.end - G.begin + (int64_t)(16 * 256) - 1) / (16 * 256) >= (1ll << 30))
+      return fail(GS_ERR_INVALID, "group %d too large", k);
   }
   if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f))
     return fail(GS_ERR_INVALID, "bad Adam hyper-parameters");
   if (cfg->pose && (cfg->views < 1 || !cfg->dpose || !cfg->pose_m || !cfg->pose_v))
     return fail(GS_ERR_INVALID, "pose step needs views, dpose, pose_m, pose_v");
   return launch_adam(p, g, m, v, n, *cfg, step, (cudaStream_t)stream);
+}
+
+gs_status gs_render_stats(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams, int32_t views,
+                          const gs_raster_cfg* cfg, uint64_t* stats_dev, gs_stream stream) {
+  gs_status st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!splats) return fail(GS_ERR_INVALID, "splats is NULL");
+  if ((st = check_splats(splats, splats->n, views)) != GS_OK) return st;
+  if ((st = check_bins(bins, vt, splats->n)) != GS_OK) return st;
+  if (!stats_dev || !aligned(stats_dev, 8)) return fail(GS_ERR_INVALID, "stats must be 8-byte aligned device memory");
+  return launch_render_stats(*splats, *bins, vt, reinterpret_cast<unsigned long long*>(stats_dev),
+                             (cudaStream_t)stream);
 }
 
 size_t gs_image_loss_workspace(void) { return loss_workspace_bytes(); }

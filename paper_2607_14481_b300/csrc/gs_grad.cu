@@ -30,6 +30,7 @@ struct GradArgs {
   float4* g_quat;
   float* g_sh;
   float* pose_partials;  // [V][gridDim.x][6]
+  float4* drgb;          // [V][n] summed colour gradient of each visible (view, Gaussian)
 };
 
 // Deterministic 256-thread sum of 6 values per thread into out[6] (thread 0).
@@ -78,11 +79,6 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
 
   float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   float gol = 0.f;
-  float gsh[3][NC];
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch)
-#pragma unroll
-    for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
   // gradient w.r.t. the rotation matrix entries, accumulated over views
   float gRq[9];
 #pragma unroll
@@ -108,6 +104,7 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
         for (int c = 0; c < kPartialStride; ++c) G[c] += pp[k * kPartialStride + c];
       }
       const uint32_t auxb = a.aux[o];
+      a.drgb[o] = make_float4(G[6], G[7], G[8], 0.f);
       const float* P = a.poses + 12 * v;
       const float R[9] = {P[0], P[1], P[2], P[4], P[5], P[6], P[8], P[9], P[10]};
       const float tc[3] = {P[3], P[7], P[11]};
@@ -125,8 +122,8 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
         float wx = mu.x - oc0, wy = mu.y - oc1, wz = mu.z - oc2;
         const float wn = sqrtf(wx * wx + wy * wy + wz * wz), inv = 1.0f / wn;
         const float dx = wx * inv, dy = wy * inv, dz = wz * inv;
-        float Y[NC];
-        sh_basis<DEG>(dx, dy, dz, Y);
+        // d rgb / d Y_k = c_k for unclamped channels (the SH coefficient
+        // gradients g_c Y_k are accumulated by k_sh_bwd)
         float dY[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) dY[k] = 0.f;
@@ -135,10 +132,7 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
           if (auxb & (1u << ch)) continue;
           const float gc = G[6 + ch];
 #pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            gsh[ch][k] += gc * Y[k];
-            dY[k] += gc * a.sh[(int64_t)(ch * NC + k) * a.n + i];
-          }
+          for (int k = 1; k < NC; ++k) dY[k] += gc * a.sh[(int64_t)(ch * NC + k) * a.n + i];
         }
         float ddx, ddy, ddz;
         sh_basis_grad<DEG>(dx, dy, dz, dY, ddx, ddy, ddz);
@@ -282,6 +276,42 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
   a.g_means4[i] = make_float4(gmu[0], gmu[1], gmu[2], 0.f);
   a.g_scale_opa[i] = make_float4(gls[0], gls[1], gls[2], gol);
   a.g_quat[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+}
+
+// SH coefficient gradients: sum over views (fixed order) of g_c Y_k(dir) for
+// every unclamped channel c, from the colour gradients k_project_bwd stored.
+template <int DEG>
+__global__ void __launch_bounds__(256) k_sh_bwd(const GradArgs a, const ViewTable vt) {
+  constexpr int NC = (DEG + 1) * (DEG + 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const float4 mu = a.means4[i];
+  float gsh[3][NC];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
+  const uint32_t kpairs = a.counts[3];
+  for (int v = 0; v < vt.views; ++v) {
+    const int64_t o = (int64_t)v * a.n + i;
+    const uint32_t tch = a.touched[o];
+    if (tch == 0 || (uint64_t)a.pair_off[o] + tch > kpairs) continue;
+    const float4 g = a.drgb[o];
+    const uint32_t auxb = a.aux[o];
+    const float* P = a.poses + 12 * v;
+    const float oc0 = -(P[0] * P[3] + P[4] * P[7] + P[8] * P[11]);
+    const float oc1 = -(P[1] * P[3] + P[5] * P[7] + P[9] * P[11]);
+    const float oc2 = -(P[2] * P[3] + P[6] * P[7] + P[10] * P[11]);
+    float wx = mu.x - oc0, wy = mu.y - oc1, wz = mu.z - oc2;
+    const float inv = 1.0f / sqrtf(wx * wx + wy * wy + wz * wz);
+    float Y[NC];
+    sh_basis<DEG>(wx * inv, wy * inv, wz * inv, Y);
+    const float gc[3] = {(auxb & 1u) ? 0.f : g.x, (auxb & 2u) ? 0.f : g.y, (auxb & 4u) ? 0.f : g.z};
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) gsh[ch][k] += gc[ch] * Y[k];
+  }
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch)
 #pragma unroll
@@ -317,7 +347,7 @@ __global__ void __launch_bounds__(256) k_pose_finalize(const float* __restrict__
 gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewTable& vt,
                              const gs_raster_cfg& cfg, const gs_splats& sp, const gs_bins& bins,
                              const float* partials, const gs_grads& g, float* pose_partials,
-                             int pose_blocks, float* dpose, cudaStream_t s) {
+                             int pose_blocks, float* dpose, float* drgb, cudaStream_t s) {
   GradArgs a;
   a.means4 = reinterpret_cast<const float4*>(p.means4);
   a.scale_opa = reinterpret_cast<const float4*>(p.scale_opa);
@@ -336,16 +366,30 @@ gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewT
   a.g_quat = reinterpret_cast<float4*>(g.quat);
   a.g_sh = g.sh;
   a.pose_partials = pose_partials;
+  a.drgb = reinterpret_cast<float4*>(drgb);
   if (p.n == 0) {
     if (dpose) cudaMemsetAsync(dpose, 0, sizeof(float) * 6 * vt.views, s);
     return check_launch("project_bwd");
   }
   const unsigned grid = (unsigned)pose_blocks;
+  const unsigned sh_grid = (unsigned)((p.n + 255) / 256);
   switch (p.sh_degree) {
-    case 0: k_project_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt); break;
-    case 1: k_project_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt); break;
-    case 2: k_project_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt); break;
-    default: k_project_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt); break;
+    case 0:
+      k_project_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt);
+      k_sh_bwd<0><<<sh_grid, 256, 0, s>>>(a, vt);
+      break;
+    case 1:
+      k_project_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt);
+      k_sh_bwd<1><<<sh_grid, 256, 0, s>>>(a, vt);
+      break;
+    case 2:
+      k_project_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt);
+      k_sh_bwd<2><<<sh_grid, 256, 0, s>>>(a, vt);
+      break;
+    default:
+      k_project_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt);
+      k_sh_bwd<3><<<sh_grid, 256, 0, s>>>(a, vt);
+      break;
   }
   if (dpose) k_pose_finalize<<<vt.views, 256, 0, s>>>(pose_partials, pose_blocks, dpose);
   return check_launch("project_bwd");

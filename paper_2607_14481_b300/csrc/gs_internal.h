@@ -41,13 +41,15 @@ gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b
 
 gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                             const gs_raster_cfg& cfg, float* image, float* alpha, cudaStream_t s);
+gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
+                              unsigned long long* stats, cudaStream_t s);
 gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                             const gs_raster_cfg& cfg, const float* dimage, const float* dalpha,
                             float* partials, cudaStream_t s);
 gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewTable& vt,
                              const gs_raster_cfg& cfg, const gs_splats& sp, const gs_bins& bins,
                              const float* partials, const gs_grads& g, float* pose_partials,
-                             int pose_blocks, float* dpose, cudaStream_t s);
+                             int pose_blocks, float* dpose, float* drgb, cudaStream_t s);
 gs_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
                       const gs_adam_cfg& cfg, int step, cudaStream_t s);
 

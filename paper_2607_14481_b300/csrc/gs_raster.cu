@@ -16,7 +16,7 @@ namespace gs {
 namespace {
 
 struct Eval {
-  float dx, dy, power, raw, alpha;
+  float dx, dy, power, ex, raw, alpha;
 };
 
 // Alpha of one splat at pixel (px, py): false when the splat is skipped
@@ -29,7 +29,8 @@ __device__ __forceinline__ bool splat_alpha(const float4 m, const float4 co, flo
   const float q = __fmaf_rn(co.x, __fmul_rn(e.dx, e.dx), __fmul_rn(co.z, __fmul_rn(e.dy, e.dy)));
   e.power = __fmaf_rn(-0.5f, q, __fmul_rn(-co.y, __fmul_rn(e.dx, e.dy)));
   if (e.power > 0.f) return false;
-  e.raw = __fmul_rn(co.w, __expf(e.power));
+  e.ex = __expf(e.power);
+  e.raw = __fmul_rn(co.w, e.ex);
   e.alpha = fminf(kAlphaMax, e.raw);
   return e.alpha >= kAlphaMin;
 }
@@ -57,8 +58,17 @@ struct FwdArgs {
 
 constexpr int kFwdBatch = kTilePixels;
 
-__global__ void __launch_bounds__(kTilePixels) k_render_fwd(const FwdArgs a, const ViewTable vt) {
+// COUNT = true is the diagnostic instantiation behind gs_render_stats: the
+// same loop, also counting per pixel the splats tested (up to and including
+// the one that stops it) and blended, and per tile the backward's walk length.
+template <bool COUNT>
+__global__ void __launch_bounds__(kTilePixels) k_render_fwd(const FwdArgs a, const ViewTable vt,
+                                                            unsigned long long* stats) {
   __shared__ float4 s_xy[kFwdBatch], s_co[kFwdBatch], s_rgb[kFwdBatch];
+  __shared__ int s_last;
+  uint32_t n_tested = 0, n_blended = 0;
+  int last = -1;
+  if (COUNT && threadIdx.x == 0) s_last = -1;
   const int gt = blockIdx.x;
   const int v = view_of_tile(vt, gt);
   const ViewInfo& vi = vt.v[v];
@@ -91,13 +101,33 @@ __global__ void __launch_bounds__(kTilePixels) k_render_fwd(const FwdArgs a, con
     for (int k = 0; !done && k < cnt; ++k) {
       const float4 col = s_rgb[k];
       Eval e;
+      if (COUNT) ++n_tested;
       if (!splat_alpha(s_xy[k], s_co[k], col.w, pxf, pyf, e)) continue;
       const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
       if (Tn < kTransMin) { done = true; break; }
       const float w = e.alpha * T;
       c0 += col.x * w; c1 += col.y * w; c2 += col.z * w;
       T = Tn;
+      if (COUNT) { ++n_blended; last = (int)(start + k); }
     }
+  }
+  if (COUNT) {
+    __syncthreads();
+    if (last >= 0) atomicMax(&s_last, last);
+    unsigned long long t = n_tested, b = n_blended;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      t += __shfl_xor_sync(0xffffffffu, t, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats[0], t);
+      atomicAdd(&stats[1], b);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_last >= 0) atomicAdd(&stats[2], (unsigned long long)(s_last + 1 - (int)rg.x));
+    if (threadIdx.x == 0) atomicAdd(&stats[3], (unsigned long long)(rg.y - rg.x));
+    return;
   }
   if (inside) {
     const int64_t np = (int64_t)vi.W * vi.H;
@@ -129,6 +159,42 @@ struct BwdArgs {
 
 constexpr int kBwdBatch = 128;
 constexpr int kWarps = kTilePixels / 32;
+
+// Warp sum of 9 values per lane with 14 shuffles instead of 45: values 0-7
+// are reduced by halving exchanges (each step a lane keeps half of what it
+// carries and sends the other half to its partner), value 8 by a plain
+// butterfly.  On return lane l holds the total of value idx(l) in s8 where
+// idx(l) = 4 [l & 16] + 2 [l & 8] + [l & 4] (lanes 0, 4, ..., 28 cover 0-7),
+// and every lane holds the total of value 8 in t8.
+__device__ __forceinline__ void warp_sum9(const float (&d)[kPartialStride], int lane, float& s8,
+                                          int& idx, float& t8) {
+  const unsigned full = 0xffffffffu;
+  const bool u1 = (lane & 16) != 0, u2 = (lane & 8) != 0, u3 = (lane & 4) != 0;
+  float k4[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = u1 ? d[i] : d[i + 4];
+    const float keep = u1 ? d[i + 4] : d[i];
+    k4[i] = keep + __shfl_xor_sync(full, send, 16);
+  }
+  float k2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = u2 ? k4[i] : k4[i + 2];
+    const float keep = u2 ? k4[i + 2] : k4[i];
+    k2[i] = keep + __shfl_xor_sync(full, send, 8);
+  }
+  const float send = u3 ? k2[0] : k2[1];
+  float k1 = (u3 ? k2[1] : k2[0]) + __shfl_xor_sync(full, send, 4);
+  k1 += __shfl_xor_sync(full, k1, 2);
+  k1 += __shfl_xor_sync(full, k1, 1);
+  s8 = k1;
+  idx = (u1 ? 4 : 0) + (u2 ? 2 : 0) + (u3 ? 1 : 0);
+  float v = d[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+  t8 = v;
+}
 
 __global__ void __launch_bounds__(kTilePixels) k_render_bwd(const BwdArgs a, const ViewTable vt) {
   __shared__ float4 s_xy[kBwdBatch], s_co[kBwdBatch], s_rgb[kBwdBatch];
@@ -238,15 +304,17 @@ __global__ void __launch_bounds__(kTilePixels) k_render_bwd(const BwdArgs a, con
         const float4 co = s_co[k];
         const float4 col = s_rgb[k];
         if (splat_alpha(s_xy[k], co, col.w, pxf, pyf, e)) {
-          const float om = 1.f - e.alpha;
-          const float Tb = T / om;            // transmittance in front of this splat
+          // 1 - alpha >= 0.01: one approximate reciprocal (relative error ~1e-7)
+          // serves the transmittance recovery and the suffix terms
+          const float rom = __fdividef(1.f, 1.f - e.alpha);
+          const float Tb = T * rom;           // transmittance in front of this splat
           const float w = e.alpha * Tb;
           d[6] = g0 * w; d[7] = g1 * w; d[8] = g2 * w;
-          float dal = g0 * (col.x * Tb - acc0 / om) + g1 * (col.y * Tb - acc1 / om) +
-                      g2 * (col.z * Tb - acc2 / om) + ga * Tfinal / om;
+          float dal = g0 * (col.x * Tb - acc0 * rom) + g1 * (col.y * Tb - acc1 * rom) +
+                      g2 * (col.z * Tb - acc2 * rom) + ga * Tfinal * rom;
           acc0 += col.x * w; acc1 += col.y * w; acc2 += col.z * w;
           if (e.raw <= kAlphaMax) {
-            d[5] = dal * (e.alpha / co.w);    // d alpha / d opacity = exp(power)
+            d[5] = dal * e.ex;                // d alpha / d opacity = exp(power)
             const float dp = dal * e.alpha;   // d alpha / d power = alpha
             d[2] = -0.5f * e.dx * e.dx * dp;
             d[3] = -e.dx * e.dy * dp;
@@ -258,17 +326,11 @@ __global__ void __launch_bounds__(kTilePixels) k_render_bwd(const BwdArgs a, con
           contrib = true;
         }
       }
-      if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int c = 0; c < kPartialStride; ++c) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
-        }
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < kPartialStride; ++c) s_red[k][warp][c] = d[c];
-      }
+      float s8 = 0.f, t8 = 0.f;
+      int idx = ((lane & 16) ? 4 : 0) + ((lane & 8) ? 2 : 0) + ((lane & 4) ? 1 : 0);
+      if (__any_sync(0xffffffffu, contrib)) warp_sum9(d, lane, s8, idx, t8);
+      if ((lane & 3) == 0) s_red[k][warp][idx] = s8;
+      if (lane == 0) s_red[k][warp][8] = t8;
     }
     __syncthreads();
     if (threadIdx.x < cnt && (int64_t)s_pidx[threadIdx.x] >= a.cap) atomicOr(&a.counts[2], 2u);
@@ -301,8 +363,27 @@ gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const View
   a.image = image;
   a.alpha = alpha;
   if (vt.total_tiles == 0) return GS_OK;
-  k_render_fwd<<<vt.total_tiles, kTilePixels, 0, s>>>(a, vt);
+  k_render_fwd<false><<<vt.total_tiles, kTilePixels, 0, s>>>(a, vt, nullptr);
   return check_launch("k_render_fwd");
+}
+
+gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
+                              unsigned long long* stats, cudaStream_t s) {
+  FwdArgs a;
+  a.xy = reinterpret_cast<const float4*>(sp.xy);
+  a.conic = reinterpret_cast<const float4*>(sp.conic);
+  a.rgb = reinterpret_cast<const float4*>(sp.rgb);
+  a.vals = bins.vals;
+  a.ranges = reinterpret_cast<const uint2*>(bins.ranges);
+  a.counts = bins.counts;
+  a.n = sp.n;
+  a.bg[0] = a.bg[1] = a.bg[2] = 0.f;
+  a.image = nullptr;
+  a.alpha = nullptr;
+  if (cudaMemsetAsync(stats, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return check_launch("stats");
+  if (vt.total_tiles == 0) return GS_OK;
+  k_render_fwd<true><<<vt.total_tiles, kTilePixels, 0, s>>>(a, vt, stats);
+  return check_launch("k_render_fwd<count>");
 }
 
 gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,

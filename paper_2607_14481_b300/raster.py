@@ -76,21 +76,22 @@ class Arena:
 
     def adam_groups(self, lr_means=1.6e-4, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3,
                     lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4) -> List[_lib.GsAdamGroup]:
-        """One group per parameter kind; the scale_opa float4 gives its first
-        three lanes the scale rate and its fourth the opacity rate."""
+        """Non-overlapping groups, one per parameter kind; the scale_opa float4
+        gives its first three lanes the scale rate and its fourth the opacity
+        rate; per channel the SH DC plane (k = 0) and the higher bands
+        (k = 1 .. nc-1) are separate groups."""
         n, nc = self.n, self.nc
         G = _lib.GsAdamGroup
         f4 = C.c_float * 4
         groups = [G(0, 4 * n, f4(lr_means, lr_means, lr_means, 0.0)),
                   G(4 * n, 8 * n, f4(lr_scale, lr_scale, lr_scale, lr_opacity)),
-                  G(8 * n, 12 * n, f4(lr_quat, lr_quat, lr_quat, lr_quat)),
-                  G(12 * n, 12 * n + 3 * n * nc, f4(lr_sh_rest, lr_sh_rest, lr_sh_rest, lr_sh_rest))]
-        # SH DC planes are k = 0 of each channel: planes 0, nc, 2 nc
+                  G(8 * n, 12 * n, f4(lr_quat, lr_quat, lr_quat, lr_quat))]
         for ch in range(3):
             b = 12 * n + ch * nc * n
             groups.append(G(b, b + n, f4(lr_sh_dc, lr_sh_dc, lr_sh_dc, lr_sh_dc)))
-        # first matching group wins: put the DC planes first
-        return groups[4:] + groups[:4]
+            if nc > 1:
+                groups.append(G(b + n, b + nc * n, f4(lr_sh_rest, lr_sh_rest, lr_sh_rest, lr_sh_rest)))
+        return groups
 
 
 def cameras_struct(cams: Sequence[Camera]):
@@ -192,6 +193,16 @@ class Rasterizer:
         _lib.check(self.L.gs_render_fwd(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
                                         C.byref(self.cfg), _p(image), _p(alpha), _stream()), "gs_render_fwd")
 
+    def render_stats(self) -> dict:
+        """Work counts of the current tile lists (synchronises): pairs tested
+        and blended by the forward, the backward's walk length, list length."""
+        st = torch.zeros(4, dtype=torch.int64, device=self.device)
+        b = self.bins_struct()
+        _lib.check(self.L.gs_render_stats(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
+                                          C.byref(self.cfg), _p(st), _stream()), "gs_render_stats")
+        v = st.cpu().numpy()
+        return {"tested": int(v[0]), "blended": int(v[1]), "walk": int(v[2]), "listed": int(v[3])}
+
     def read_counts(self) -> np.ndarray:
         return self.counts.cpu().numpy().view(np.uint32).copy()
 
@@ -270,11 +281,16 @@ class Rasterizer:
 def adam_step(params: Arena, grads: Arena, m: Arena, v: Arena, step: int, groups, beta1=0.9, beta2=0.999,
               eps=1e-15, status: Optional[torch.Tensor] = None, pose: Optional[torch.Tensor] = None,
               dpose: Optional[torch.Tensor] = None, pose_m: Optional[torch.Tensor] = None,
-              pose_v: Optional[torch.Tensor] = None, pose_lr: float = 1e-4, pose_step: int = 0) -> None:
+              pose_v: Optional[torch.Tensor] = None, pose_lr: float = 1e-4, pose_step: int = 0,
+              step_dev: Optional[torch.Tensor] = None, pose_steps_dev: Optional[torch.Tensor] = None) -> None:
+    """Fused Adam over the whole arena (+ optional pose step).  With step_dev
+    (a device int32 scalar) the step is read and incremented on the device, so
+    the call can be captured in a CUDA graph."""
     L = _lib.load()
     garr = (_lib.GsAdamGroup * len(groups))(*groups)
     cfg = _lib.GsAdamCfg(garr, len(groups), beta1, beta2, eps, _p(status), _p(pose), _p(dpose), _p(pose_m),
-                         _p(pose_v), pose.shape[0] if pose is not None else 0, pose_lr, int(pose_step))
+                         _p(pose_v), pose.shape[0] if pose is not None else 0, pose_lr, int(pose_step),
+                         _p(step_dev), _p(pose_steps_dev))
     _lib.check(L.gs_adam_step(_p(params.buf), _p(grads.buf), _p(m.buf), _p(v.buf), params.padded, C.byref(cfg),
                               int(step), _stream()), "gs_adam_step")
 

@@ -64,7 +64,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     st = lib.gs_project(C.byref(params), None, cam, 0, C.byref(cfg), C.byref(sp), None)
     assert st == _lib.GS_ERR_INVALID
     grp = (_lib.GsAdamGroup * 1)(_lib.GsAdamGroup(0, 4, (C.c_float * 4)(1, 1, 1, 1)))
-    acfg = _lib.GsAdamCfg(grp, 1, 0.9, 0.999, 1e-15, None, None, None, None, None, 0, 0.0, 0)
+    acfg = _lib.GsAdamCfg(grp, 1, 0.9, 0.999, 1e-15, None, None, None, None, None, 0, 0.0, 0, None, None)
     st = lib.gs_adam_step(None, None, None, None, 0, C.byref(acfg), 0, None)
     assert st == _lib.GS_ERR_INVALID and "step" in _lib.last_error()
     st = lib.gs_adam_step(None, None, None, None, 4, C.byref(acfg), 1, None)
