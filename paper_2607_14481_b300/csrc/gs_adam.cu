@@ -71,19 +71,36 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(const AdamArgs a) {
     bad |= !adam_elem(a.p[e], a.g[e], a.m[e], a.v[e], G.lr[(e - G.begin) & 3], a, bc1, bc2);
   const int rot = (int)((a0 - G.begin) & 3);
   const float lr4[4] = {G.lr[rot & 3], G.lr[(rot + 1) & 3], G.lr[(rot + 2) & 3], G.lr[(rot + 3) & 3]};
-#pragma unroll 4
-  for (int64_t c = a0 / 4 + threadIdx.x; c < a1 / 4; c += kAdamThreads) {
-    float4 p = reinterpret_cast<float4*>(a.p)[c];
-    const float4 g = reinterpret_cast<const float4*>(a.g)[c];
-    float4 m = reinterpret_cast<float4*>(a.m)[c];
-    float4 v = reinterpret_cast<float4*>(a.v)[c];
-    bad |= !adam_elem(p.x, g.x, m.x, v.x, lr4[0], a, bc1, bc2);
-    bad |= !adam_elem(p.y, g.y, m.y, v.y, lr4[1], a, bc1, bc2);
-    bad |= !adam_elem(p.z, g.z, m.z, v.z, lr4[2], a, bc1, bc2);
-    bad |= !adam_elem(p.w, g.w, m.w, v.w, lr4[3], a, bc1, bc2);
-    reinterpret_cast<float4*>(a.p)[c] = p;
-    reinterpret_cast<float4*>(a.m)[c] = m;
-    reinterpret_cast<float4*>(a.v)[c] = v;
+  // Each thread owns up to 4 float4 chunks of the block's body: all 16 loads
+  // are issued before any store (the arrays are touched once: streaming hints).
+  float4* __restrict__ P4 = reinterpret_cast<float4*>(a.p);
+  const float4* __restrict__ G4 = reinterpret_cast<const float4*>(a.g);
+  float4* __restrict__ M4 = reinterpret_cast<float4*>(a.m);
+  float4* __restrict__ V4 = reinterpret_cast<float4*>(a.v);
+  const int64_t c0 = a0 / 4 + threadIdx.x, c1 = a1 / 4;
+  float4 p[4], g[4], m[4], v[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t c = c0 + (int64_t)u * kAdamThreads;
+    if (c < c1) {
+      p[u] = __ldcs(P4 + c);
+      g[u] = __ldcs(G4 + c);
+      m[u] = __ldcs(M4 + c);
+      v[u] = __ldcs(V4 + c);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t c = c0 + (int64_t)u * kAdamThreads;
+    if (c < c1) {
+      bad |= !adam_elem(p[u].x, g[u].x, m[u].x, v[u].x, lr4[0], a, bc1, bc2);
+      bad |= !adam_elem(p[u].y, g[u].y, m[u].y, v[u].y, lr4[1], a, bc1, bc2);
+      bad |= !adam_elem(p[u].z, g[u].z, m[u].z, v[u].z, lr4[2], a, bc1, bc2);
+      bad |= !adam_elem(p[u].w, g[u].w, m[u].w, v[u].w, lr4[3], a, bc1, bc2);
+      __stcs(P4 + c, p[u]);
+      __stcs(M4 + c, m[u]);
+      __stcs(V4 + c, v[u]);
+    }
   }
   for (int64_t e = a1 + threadIdx.x; e < r1; e += kAdamThreads)
     bad |= !adam_elem(a.p[e], a.g[e], a.m[e], a.v[e], G.lr[(e - G.begin) & 3], a, bc1, bc2);

@@ -287,33 +287,61 @@ struct EmitArgs {
   uint32_t* tvals;
 };
 
+// Warp-cooperative emission: each warp takes 32 consecutive items (in depth
+// order); lane l loads item l's record, then the warp emits the items one
+// after another with its 32 lanes striding over the item's tiles, so a splat
+// covering hundreds of tiles is written by 32 lanes and consecutive pairs are
+// written by consecutive lanes (coalesced).
 __global__ void __launch_bounds__(256) k_emit(const EmitArgs a, const ViewTable vt) {
-  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.counts[0] || (int64_t)j >= a.n * vt.views) return;
-  const uint32_t item = a.items[j];
-  if ((int64_t)item >= a.n * vt.views) {
-    atomicOr(const_cast<uint32_t*>(&a.counts[2]), kStatusIndex);
-    return;
+  const uint32_t M = a.counts[0];
+  const int lane = threadIdx.x & 31;
+  const uint32_t j0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  if (j0 >= M || (int64_t)j0 >= a.n * vt.views) return;
+  const uint32_t j = j0 + lane;
+  const int64_t total = a.n * vt.views;
+  bool ok = j < M && (int64_t)j < total;
+  uint32_t item = 0, off = 0, rx = 1u, ry = 0u;
+  int v = 0;
+  if (ok) {
+    item = a.items[j];
+    if ((int64_t)item >= total) {
+      atomicOr(const_cast<uint32_t*>(&a.counts[2]), kStatusIndex);
+      ok = false;
+    } else {
+      v = (int)(item / (uint64_t)a.n);
+      off = a.poff[j];
+      a.pair_off[item] = off;
+      const uint2 rc = a.rect[item];
+      rx = rc.x;
+      ry = rc.y;
+      if ((int)(ry & 0xffff) >= vt.v[v].TX || (int)(ry >> 16) >= vt.v[v].TY) {
+        atomicOr(const_cast<uint32_t*>(&a.counts[2]), kStatusIndex);
+        ok = false;
+      }
+    }
   }
-  const int v = (int)(item / (uint64_t)a.n);
-  const uint32_t g = (uint32_t)(item - (uint64_t)v * a.n);
-  const uint32_t off = a.poff[j];
-  a.pair_off[item] = off;
-  const uint2 rc = a.rect[item];
-  const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
-  const int TX = vt.v[v].TX;
-  if (x1 >= TX || y1 >= vt.v[v].TY) {
-    atomicOr(const_cast<uint32_t*>(&a.counts[2]), kStatusIndex);
-    return;
-  }
-  const uint32_t tb = (uint32_t)vt.v[v].tile_base;
-  uint64_t k = off;
-  for (int ty = y0; ty <= y1; ++ty)
-    for (int tx = x0; tx <= x1; ++tx, ++k) {
-      if ((int64_t)k >= a.cap) return;
+  for (int src = 0; src < 32; ++src) {
+    const bool sok = __shfl_sync(0xffffffffu, ok, src);
+    const uint32_t sitem = __shfl_sync(0xffffffffu, item, src);
+    const uint32_t soff = __shfl_sync(0xffffffffu, off, src);
+    const uint32_t sx = __shfl_sync(0xffffffffu, rx, src);
+    const uint32_t sy = __shfl_sync(0xffffffffu, ry, src);
+    const int sv = __shfl_sync(0xffffffffu, v, src);
+    if (!sok) continue;
+    const int x0 = sx & 0xffff, y0 = sx >> 16, x1 = sy & 0xffff, y1 = sy >> 16;
+    const int w = x1 - x0 + 1;
+    const int cnt = w * (y1 - y0 + 1);
+    const int TX = vt.v[sv].TX;
+    const uint32_t tb = (uint32_t)vt.v[sv].tile_base;
+    const uint32_t g = (uint32_t)(sitem - (uint64_t)sv * a.n);
+    for (int t = lane; t < cnt; t += 32) {
+      const uint64_t k = (uint64_t)soff + t;
+      if ((int64_t)k >= a.cap) break;
+      const int ty = y0 + t / w, tx = x0 + t % w;
       a.tkeys[k] = tb + (uint32_t)(ty * TX + tx);
       a.tvals[k] = g;
     }
+  }
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ tkeys, uint32_t* __restrict__ counts,

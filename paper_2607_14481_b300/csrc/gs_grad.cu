@@ -95,13 +95,15 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
     if (tch > 0) {
       const ViewInfo vi = vt.v[v];
       // ---- sum of this (view, Gaussian)'s per-tile partials, fixed order
-      float G[kPartialStride];
+      float G[kPartialValues];
 #pragma unroll
-      for (int c = 0; c < kPartialStride; ++c) G[c] = 0.f;
-      const float* pp = a.partials + (int64_t)a.pair_off[o] * kPartialStride;
+      for (int c = 0; c < kPartialValues; ++c) G[c] = 0.f;
+      const float4* pp = reinterpret_cast<const float4*>(a.partials + (int64_t)a.pair_off[o] * kPartialStride);
       for (uint32_t k = 0; k < tch; ++k) {
-#pragma unroll
-        for (int c = 0; c < kPartialStride; ++c) G[c] += pp[k * kPartialStride + c];
+        const float4 p0 = pp[3 * k], p1 = pp[3 * k + 1], p2 = pp[3 * k + 2];
+        G[0] += p0.x; G[1] += p0.y; G[2] += p0.z; G[3] += p0.w;
+        G[4] += p1.x; G[5] += p1.y; G[6] += p1.z; G[7] += p1.w;
+        G[8] += p2.x;
       }
       const uint32_t auxb = a.aux[o];
       a.drgb[o] = make_float4(G[6], G[7], G[8], 0.f);

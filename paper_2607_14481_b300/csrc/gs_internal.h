@@ -57,7 +57,8 @@ size_t loss_workspace_bytes();
 gs_status launch_loss(const float* img, const float* tgt, int64_t count, int kind, float* grad,
                       float* loss, void* ws, cudaStream_t s);
 
-constexpr int kPartialStride = 9;       // floats per (tile, splat) pair gradient
+constexpr int kPartialValues = 9;       // dmx, dmy, dA, dB, dC, dopacity, dr, dg, db
+constexpr int kPartialStride = 12;      // floats per (tile, splat) pair: 3 float4, last 3 unused
 constexpr int kGradBlock = 256;         // threads per block of the per-Gaussian backward
 
 }  // namespace gs

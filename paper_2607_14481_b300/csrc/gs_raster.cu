@@ -1,10 +1,14 @@
 // Front-to-back alpha compositing per 16x16 tile and its backward (the
-// per-pixel stages of the splat renderer of Sec. 5.2).
+// per-pixel stages of the splat renderer of §5.2).
 //
-// One CTA per (view, tile), one thread per pixel.  Each batch of the tile's
-// sorted splat list is staged in shared memory by the CTA's threads with
-// coalesced float4 loads; the whole CTA leaves the list as soon as every pixel
-// has saturated (__syncthreads_count, the block-wide ballot).
+// One CTA of 128 threads per (view, tile); each thread owns two vertically
+// adjacent pixels, so a warp covers 4 tile rows and every splat fetched from
+// shared memory serves two pixels.  Each batch of the tile's sorted splat list
+// is staged in shared memory by the CTA's threads with coalesced float4 loads,
+// together with the splat's vertical support range; a warp skips a splat whose
+// support misses its 4 rows (a warp-uniform test with one pixel of margin, so
+// it never skips a splat the exact per-pixel test would accept).  The CTA
+// leaves the list as soon as every pixel has saturated (__syncthreads_count).
 //
 // The splat test is written once (splat_alpha) with explicit round-to-nearest
 // intrinsics so that the forward, the backward's replay and the backward's
@@ -14,6 +18,11 @@
 namespace gs {
 
 namespace {
+
+constexpr int kThreads = kTilePixels / 2;   // two pixels per thread
+constexpr int kWarps = kThreads / 32;
+constexpr int kBatch = kThreads;            // splats staged per batch
+constexpr int kRowsPerWarp = 32 / kTile * 2;  // 4
 
 struct Eval {
   float dx, dy, power, ex, raw, alpha;
@@ -35,12 +44,42 @@ __device__ __forceinline__ bool splat_alpha(const float4 m, const float4 co, flo
   return e.alpha >= kAlphaMin;
 }
 
+// Rows a splat can touch, with a margin of one pixel (plus the rounding of
+// the single-precision centre far off screen): [my - r - e, my + r + e].  The
+// exact per-pixel test accepts rows within half a pixel of [my - r, my + r].
+// A negative radius (null splat) gives an empty range.
+__device__ __forceinline__ float2 splat_rows(const float4 m, float r) {
+  if (r < 0.f) return make_float2(1e30f, -1e30f);
+  const float my = m.y + m.w;
+  const float e = 1.f + 1e-6f * fabsf(my) + 1e-6f * r;
+  return make_float2(my - r - e, my + r + e);
+}
+
 // A splat that never passes the test (radius -1): stands in for an
 // out-of-range id, which is reported through counts[2] bit 2.
 __device__ __forceinline__ void null_splat(float4& m, float4& co, float4& col) {
   m = make_float4(0.f, 0.f, 0.f, 0.f);
   co = make_float4(0.f, 0.f, 0.f, 0.f);
   col = make_float4(0.f, 0.f, 0.f, -1.f);
+}
+
+struct TileCoords {
+  int v, tx, ty, px, py0;
+  bool in0, in1;
+};
+
+__device__ __forceinline__ TileCoords tile_coords(const ViewTable& vt, int gt) {
+  TileCoords c;
+  c.v = view_of_tile(vt, gt);
+  const ViewInfo& vi = vt.v[c.v];
+  const int lt = gt - vi.tile_base;
+  c.tx = lt % vi.TX;
+  c.ty = lt / vi.TX;
+  c.px = c.tx * kTile + (threadIdx.x % kTile);
+  c.py0 = c.ty * kTile + 2 * (threadIdx.x / kTile);
+  c.in0 = c.px < vi.W && c.py0 < vi.H;
+  c.in1 = c.px < vi.W && c.py0 + 1 < vi.H;
+  return c;
 }
 
 struct FwdArgs {
@@ -56,59 +95,91 @@ struct FwdArgs {
   float* alpha;
 };
 
-constexpr int kFwdBatch = kTilePixels;
+// Stages splat `j` of the list (or a null splat) in shared memory slot `t`.
+__device__ __forceinline__ void stage_splat(const float4* xy, const float4* conic, const float4* rgb,
+                                            const uint32_t* vals, int64_t n, int64_t vbase, uint32_t j,
+                                            int t, float4* s_xy, float4* s_co, float4* s_rgb,
+                                            float2* s_rows, uint32_t* counts) {
+  const uint32_t g = vals[j];
+  float4 m, co, col;
+  if (g < n) {
+    const int64_t gi = vbase + g;
+    m = xy[gi];
+    co = conic[gi];
+    col = rgb[gi];
+  } else {
+    null_splat(m, co, col);
+    if (counts) atomicOr(&counts[2], 2u);
+  }
+  s_xy[t] = m;
+  s_co[t] = co;
+  s_rgb[t] = col;
+  s_rows[t] = splat_rows(m, col.w);
+}
 
 // COUNT = true is the diagnostic instantiation behind gs_render_stats: the
 // same loop, also counting per pixel the splats tested (up to and including
 // the one that stops it) and blended, and per tile the backward's walk length.
 template <bool COUNT>
-__global__ void __launch_bounds__(kTilePixels) k_render_fwd(const FwdArgs a, const ViewTable vt,
-                                                            unsigned long long* stats) {
-  __shared__ float4 s_xy[kFwdBatch], s_co[kFwdBatch], s_rgb[kFwdBatch];
+__global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const ViewTable vt,
+                                                         unsigned long long* stats) {
+  __shared__ float4 s_xy[kBatch], s_co[kBatch], s_rgb[kBatch];
+  __shared__ float2 s_rows[kBatch];
   __shared__ int s_last;
+  const TileCoords tc = tile_coords(vt, blockIdx.x);
+  const ViewInfo& vi = vt.v[tc.v];
+  const float pxf = (float)tc.px, py0f = (float)tc.py0, py1f = py0f + 1.f;
+  const float wrow_lo = (float)(tc.ty * kTile + (threadIdx.x >> 5) * kRowsPerWarp);
+  const float wrow_hi = wrow_lo + (float)(kRowsPerWarp - 1);
+  const uint2 rg = a.ranges[blockIdx.x];
+  const int64_t vbase = (int64_t)tc.v * a.n;
+  float T0 = 1.f, T1 = 1.f;
+  float c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
+  bool d0 = !tc.in0, d1 = !tc.in1;
   uint32_t n_tested = 0, n_blended = 0;
   int last = -1;
   if (COUNT && threadIdx.x == 0) s_last = -1;
-  const int gt = blockIdx.x;
-  const int v = view_of_tile(vt, gt);
-  const ViewInfo& vi = vt.v[v];
-  const int lt = gt - vi.tile_base;
-  const int tx = lt % vi.TX, ty = lt / vi.TX;
-  const int px = tx * kTile + (threadIdx.x % kTile), py = ty * kTile + (threadIdx.x / kTile);
-  const bool inside = px < vi.W && py < vi.H;
-  const float pxf = (float)px, pyf = (float)py;
-  const uint2 rg = a.ranges[gt];
-  const int64_t vbase = (int64_t)v * a.n;
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  bool done = !inside;
-  for (uint32_t start = rg.x; start < rg.y; start += kFwdBatch) {
-    if (__syncthreads_count(done) == kTilePixels) break;
+  for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
+    if (__syncthreads_count(d0 && d1) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
-    if (j < rg.y) {
-      const uint32_t g = a.vals[j];
-      if (g < a.n) {
-        const int64_t gi = vbase + g;
-        s_xy[threadIdx.x] = a.xy[gi];
-        s_co[threadIdx.x] = a.conic[gi];
-        s_rgb[threadIdx.x] = a.rgb[gi];
-      } else {
-        null_splat(s_xy[threadIdx.x], s_co[threadIdx.x], s_rgb[threadIdx.x]);
-        atomicOr(&a.counts[2], 2u);
-      }
-    }
+    if (j < rg.y)
+      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, s_xy, s_co, s_rgb, s_rows,
+                  COUNT ? nullptr : a.counts);
     __syncthreads();
-    const int cnt = (int)min((uint32_t)kFwdBatch, rg.y - start);
-    for (int k = 0; !done && k < cnt; ++k) {
-      const float4 col = s_rgb[k];
+    const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
+    for (int k = 0; k < cnt && !(d0 && d1); ++k) {
+      const float2 rows = s_rows[k];
+      if (wrow_lo > rows.y || wrow_hi < rows.x) continue;  // warp-uniform
+      const float4 m = s_xy[k], co = s_co[k], col = s_rgb[k];
       Eval e;
-      if (COUNT) ++n_tested;
-      if (!splat_alpha(s_xy[k], s_co[k], col.w, pxf, pyf, e)) continue;
-      const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
-      if (Tn < kTransMin) { done = true; break; }
-      const float w = e.alpha * T;
-      c0 += col.x * w; c1 += col.y * w; c2 += col.z * w;
-      T = Tn;
-      if (COUNT) { ++n_blended; last = (int)(start + k); }
+      if (!d0) {
+        if (COUNT) ++n_tested;
+        if (splat_alpha(m, co, col.w, pxf, py0f, e)) {
+          const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
+          if (Tn < kTransMin) {
+            d0 = true;
+          } else {
+            const float w = e.alpha * T0;
+            c00 += col.x * w; c01 += col.y * w; c02 += col.z * w;
+            T0 = Tn;
+            if (COUNT) { ++n_blended; last = max(last, (int)(start + k)); }
+          }
+        }
+      }
+      if (!d1) {
+        if (COUNT) ++n_tested;
+        if (splat_alpha(m, co, col.w, pxf, py1f, e)) {
+          const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
+          if (Tn < kTransMin) {
+            d1 = true;
+          } else {
+            const float w = e.alpha * T1;
+            c10 += col.x * w; c11 += col.y * w; c12 += col.z * w;
+            T1 = Tn;
+            if (COUNT) { ++n_blended; last = max(last, (int)(start + k)); }
+          }
+        }
+      }
     }
   }
   if (COUNT) {
@@ -129,14 +200,21 @@ __global__ void __launch_bounds__(kTilePixels) k_render_fwd(const FwdArgs a, con
     if (threadIdx.x == 0) atomicAdd(&stats[3], (unsigned long long)(rg.y - rg.x));
     return;
   }
-  if (inside) {
-    const int64_t np = (int64_t)vi.W * vi.H;
-    const int64_t pix = (int64_t)py * vi.W + px;
-    float* img = a.image + 3 * vi.pix_base;
-    img[pix] = c0 + T * a.bg[0];
-    img[np + pix] = c1 + T * a.bg[1];
-    img[2 * np + pix] = c2 + T * a.bg[2];
-    if (a.alpha) a.alpha[vi.pix_base + pix] = 1.f - T;
+  const int64_t np = (int64_t)vi.W * vi.H;
+  float* img = a.image + 3 * vi.pix_base;
+  if (tc.in0) {
+    const int64_t pix = (int64_t)tc.py0 * vi.W + tc.px;
+    img[pix] = c00 + T0 * a.bg[0];
+    img[np + pix] = c01 + T0 * a.bg[1];
+    img[2 * np + pix] = c02 + T0 * a.bg[2];
+    if (a.alpha) a.alpha[vi.pix_base + pix] = 1.f - T0;
+  }
+  if (tc.in1) {
+    const int64_t pix = (int64_t)(tc.py0 + 1) * vi.W + tc.px;
+    img[pix] = c10 + T1 * a.bg[0];
+    img[np + pix] = c11 + T1 * a.bg[1];
+    img[2 * np + pix] = c12 + T1 * a.bg[2];
+    if (a.alpha) a.alpha[vi.pix_base + pix] = 1.f - T1;
   }
 }
 
@@ -154,11 +232,8 @@ struct BwdArgs {
   float bg[3];
   const float* dimage;
   const float* dalpha;
-  float* partials;  // [K][9]: dmx, dmy, dA, dB, dC, dopacity, dr, dg, db
+  float* partials;  // [K][12]: dmx, dmy, dA, dB | dC, dopacity, dr, dg | db, 0, 0, 0
 };
-
-constexpr int kBwdBatch = 128;
-constexpr int kWarps = kTilePixels / 32;
 
 // Warp sum of 9 values per lane with 14 shuffles instead of 45: values 0-7
 // are reduced by halving exchanges (each step a lane keeps half of what it
@@ -166,7 +241,7 @@ constexpr int kWarps = kTilePixels / 32;
 // butterfly.  On return lane l holds the total of value idx(l) in s8 where
 // idx(l) = 4 [l & 16] + 2 [l & 8] + [l & 4] (lanes 0, 4, ..., 28 cover 0-7),
 // and every lane holds the total of value 8 in t8.
-__device__ __forceinline__ void warp_sum9(const float (&d)[kPartialStride], int lane, float& s8,
+__device__ __forceinline__ void warp_sum9(const float (&d)[kPartialValues], int lane, float& s8,
                                           int& idx, float& t8) {
   const unsigned full = 0xffffffffu;
   const bool u1 = (lane & 16) != 0, u2 = (lane & 8) != 0, u3 = (lane & 4) != 0;
@@ -196,152 +271,183 @@ __device__ __forceinline__ void warp_sum9(const float (&d)[kPartialStride], int 
   t8 = v;
 }
 
-__global__ void __launch_bounds__(kTilePixels) k_render_bwd(const BwdArgs a, const ViewTable vt) {
-  __shared__ float4 s_xy[kBwdBatch], s_co[kBwdBatch], s_rgb[kBwdBatch];
-  __shared__ uint32_t s_pidx[kBwdBatch];
-  __shared__ float s_red[kBwdBatch][kWarps][kPartialStride];
+// Gradient contribution of one blended splat at one pixel, walking back to
+// front: T is the transmittance behind the splat on entry and in front of it
+// on return; acc is the colour behind it (background included).
+__device__ __forceinline__ void splat_grad(const Eval& e, const float4 co, const float4 col, float g0,
+                                           float g1, float g2, float ga, float Tfinal, float& T,
+                                           float& acc0, float& acc1, float& acc2,
+                                           float (&d)[kPartialValues]) {
+  // 1 - alpha >= 0.01: one approximate reciprocal (relative error ~1e-7)
+  // serves the transmittance recovery and the suffix terms
+  const float rom = __fdividef(1.f, 1.f - e.alpha);
+  const float Tb = T * rom;
+  const float w = e.alpha * Tb;
+  d[6] += g0 * w; d[7] += g1 * w; d[8] += g2 * w;
+  const float dal = g0 * (col.x * Tb - acc0 * rom) + g1 * (col.y * Tb - acc1 * rom) +
+                    g2 * (col.z * Tb - acc2 * rom) + ga * Tfinal * rom;
+  acc0 += col.x * w; acc1 += col.y * w; acc2 += col.z * w;
+  if (e.raw <= kAlphaMax) {
+    d[5] += dal * e.ex;                  // d alpha / d opacity = exp(power)
+    const float dp = dal * e.alpha;      // d alpha / d power = alpha
+    d[2] -= 0.5f * e.dx * e.dx * dp;
+    d[3] -= e.dx * e.dy * dp;
+    d[4] -= 0.5f * e.dy * e.dy * dp;
+    d[0] -= (co.x * e.dx + co.y * e.dy) * dp;
+    d[1] -= (co.z * e.dy + co.y * e.dx) * dp;
+  }
+  T = Tb;
+}
+
+__global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const ViewTable vt) {
+  __shared__ float4 s_xy[kBatch], s_co[kBatch], s_rgb[kBatch];
+  __shared__ float2 s_rows[kBatch];
+  __shared__ uint32_t s_pidx[kBatch];
+  __shared__ float s_red[kBatch][kWarps][kPartialValues];
+  __shared__ uint8_t s_hit[kBatch][kWarps];
   __shared__ int s_maxlast;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gt = blockIdx.x;
-  const int v = view_of_tile(vt, gt);
-  const ViewInfo& vi = vt.v[v];
-  const int lt = gt - vi.tile_base;
-  const int tx = lt % vi.TX, ty = lt / vi.TX;
-  const int px = tx * kTile + (threadIdx.x % kTile), py = ty * kTile + (threadIdx.x / kTile);
-  const bool inside = px < vi.W && py < vi.H;
-  const float pxf = (float)px, pyf = (float)py;
-  const uint2 rg = a.ranges[gt];
-  const int64_t vbase = (int64_t)v * a.n;
+  const TileCoords tc = tile_coords(vt, blockIdx.x);
+  const ViewInfo& vi = vt.v[tc.v];
+  const float pxf = (float)tc.px, py0f = (float)tc.py0, py1f = py0f + 1.f;
+  const float wrow_lo = (float)(tc.ty * kTile + warp * kRowsPerWarp);
+  const float wrow_hi = wrow_lo + (float)(kRowsPerWarp - 1);
+  const uint2 rg = a.ranges[blockIdx.x];
+  const int64_t vbase = (int64_t)tc.v * a.n;
   if (threadIdx.x == 0) s_maxlast = -1;
 
   // ---- 1. replay the forward: final transmittance and last blended position
-  float T = 1.f;
-  int last = -1;
-  bool done = !inside;
-  for (uint32_t start = rg.x; start < rg.y; start += kBwdBatch) {
-    if (__syncthreads_count(done) == kTilePixels) break;
+  float T0 = 1.f, T1 = 1.f;
+  int last0 = -1, last1 = -1;
+  bool d0 = !tc.in0, d1 = !tc.in1;
+  for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
+    if (__syncthreads_count(d0 && d1) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
-    if (threadIdx.x < kBwdBatch && j < rg.y) {
-      const uint32_t g = a.vals[j];
-      if (g < a.n) {
-        const int64_t gi = vbase + g;
-        s_xy[threadIdx.x] = a.xy[gi];
-        s_co[threadIdx.x] = a.conic[gi];
-        s_rgb[threadIdx.x] = a.rgb[gi];
-      } else {
-        null_splat(s_xy[threadIdx.x], s_co[threadIdx.x], s_rgb[threadIdx.x]);
+    if (j < rg.y)
+      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, s_xy, s_co, s_rgb, s_rows,
+                  nullptr);
+    __syncthreads();
+    const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
+    for (int k = 0; k < cnt && !(d0 && d1); ++k) {
+      const float2 rows = s_rows[k];
+      if (wrow_lo > rows.y || wrow_hi < rows.x) continue;
+      const float4 m = s_xy[k], co = s_co[k];
+      const float r = s_rgb[k].w;
+      Eval e;
+      if (!d0 && splat_alpha(m, co, r, pxf, py0f, e)) {
+        const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
+        if (Tn < kTransMin) d0 = true; else { T0 = Tn; last0 = (int)(start + k); }
+      }
+      if (!d1 && splat_alpha(m, co, r, pxf, py1f, e)) {
+        const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
+        if (Tn < kTransMin) d1 = true; else { T1 = Tn; last1 = (int)(start + k); }
       }
     }
-    __syncthreads();
-    const int cnt = (int)min((uint32_t)kBwdBatch, rg.y - start);
-    for (int k = 0; !done && k < cnt; ++k) {
-      Eval e;
-      if (!splat_alpha(s_xy[k], s_co[k], s_rgb[k].w, pxf, pyf, e)) continue;
-      const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
-      if (Tn < kTransMin) { done = true; break; }
-      T = Tn;
-      last = (int)(start + k);
-    }
   }
   __syncthreads();
-  if (last >= 0) atomicMax(&s_maxlast, last);
+  if (max(last0, last1) >= 0) atomicMax(&s_maxlast, max(last0, last1));
   __syncthreads();
   const int maxlast = s_maxlast;
-  const float Tfinal = T;
+  const float Tf0 = T0, Tf1 = T1;
 
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f, ga = 0.f;
-  if (inside) {
-    const int64_t np = (int64_t)vi.W * vi.H;
-    const int64_t pix = (int64_t)py * vi.W + px;
-    const float* gi = a.dimage + 3 * vi.pix_base;
-    g0 = gi[pix]; g1 = gi[np + pix]; g2 = gi[2 * np + pix];
-    if (a.dalpha) ga = a.dalpha[vi.pix_base + pix];
+  const int64_t np = (int64_t)vi.W * vi.H;
+  const float* gimg = a.dimage + 3 * vi.pix_base;
+  float g00 = 0.f, g01 = 0.f, g02 = 0.f, ga0 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f, ga1 = 0.f;
+  if (tc.in0) {
+    const int64_t pix = (int64_t)tc.py0 * vi.W + tc.px;
+    g00 = gimg[pix]; g01 = gimg[np + pix]; g02 = gimg[2 * np + pix];
+    if (a.dalpha) ga0 = a.dalpha[vi.pix_base + pix];
   }
-  float acc0 = Tfinal * a.bg[0], acc1 = Tfinal * a.bg[1], acc2 = Tfinal * a.bg[2];
+  if (tc.in1) {
+    const int64_t pix = (int64_t)(tc.py0 + 1) * vi.W + tc.px;
+    g10 = gimg[pix]; g11 = gimg[np + pix]; g12 = gimg[2 * np + pix];
+    if (a.dalpha) ga1 = a.dalpha[vi.pix_base + pix];
+  }
+  float a00 = Tf0 * a.bg[0], a01 = Tf0 * a.bg[1], a02 = Tf0 * a.bg[2];
+  float a10 = Tf1 * a.bg[0], a11 = Tf1 * a.bg[1], a12 = Tf1 * a.bg[2];
 
   // pairs behind every pixel's last blended splat receive zero gradient
-  for (uint32_t p = (uint32_t)(maxlast + 1) + threadIdx.x; p < rg.y; p += kTilePixels) {
+  for (uint32_t p = (uint32_t)(maxlast + 1) + threadIdx.x; p < rg.y; p += kThreads) {
     const uint32_t g = a.vals[p];
     if (g >= a.n) continue;
     const int64_t gi = vbase + g;
-    const uint32_t pidx = a.pair_off[gi] + rect_index(a.rect[gi], tx, ty);
+    const uint32_t pidx = a.pair_off[gi] + rect_index(a.rect[gi], tc.tx, tc.ty);
     if ((int64_t)pidx >= a.cap) {
       atomicOr(&a.counts[2], 2u);
       continue;
     }
-    float* dst = a.partials + (int64_t)pidx * kPartialStride;
-#pragma unroll
-    for (int c = 0; c < kPartialStride; ++c) dst[c] = 0.f;
+    float4* dst = reinterpret_cast<float4*>(a.partials + (int64_t)pidx * kPartialStride);
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    dst[0] = z; dst[1] = z; dst[2] = z;
   }
 
   // ---- 2. back to front over [rg.x, maxlast]
-  for (int bend = maxlast + 1; bend > (int)rg.x; bend -= kBwdBatch) {
-    const int bstart = max((int)rg.x, bend - kBwdBatch);
+  const int mylast = max(last0, last1);
+  for (int bend = maxlast + 1; bend > (int)rg.x; bend -= kBatch) {
+    const int bstart = max((int)rg.x, bend - kBatch);
     const int cnt = bend - bstart;
     __syncthreads();
     if (threadIdx.x < cnt) {
-      const uint32_t g = a.vals[bstart + threadIdx.x];
-      uint32_t pidx = 0xffffffffu;
-      if (g < a.n) {
-        const int64_t gi = vbase + g;
-        s_xy[threadIdx.x] = a.xy[gi];
-        s_co[threadIdx.x] = a.conic[gi];
-        s_rgb[threadIdx.x] = a.rgb[gi];
-        pidx = a.pair_off[gi] + rect_index(a.rect[gi], tx, ty);
-      } else {
-        null_splat(s_xy[threadIdx.x], s_co[threadIdx.x], s_rgb[threadIdx.x]);
-      }
-      s_pidx[threadIdx.x] = pidx;
+      const uint32_t j = (uint32_t)(bstart + threadIdx.x);
+      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, s_xy, s_co, s_rgb, s_rows,
+                  nullptr);
+      const uint32_t g = a.vals[j];
+      s_pidx[threadIdx.x] =
+          g < a.n ? a.pair_off[vbase + g] + rect_index(a.rect[vbase + g], tc.tx, tc.ty) : 0xffffffffu;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
     }
     __syncthreads();
     for (int k = cnt - 1; k >= 0; --k) {
-      float d[kPartialStride];
+      const float2 rows = s_rows[k];
+      if (wrow_lo > rows.y || wrow_hi < rows.x) continue;  // warp-uniform: no contribution
+      const int pos = bstart + k;
+      float d[kPartialValues];
 #pragma unroll
-      for (int c = 0; c < kPartialStride; ++c) d[c] = 0.f;
+      for (int c = 0; c < kPartialValues; ++c) d[c] = 0.f;
       bool contrib = false;
-      Eval e;
-      if (bstart + k <= last) {
-        const float4 co = s_co[k];
-        const float4 col = s_rgb[k];
-        if (splat_alpha(s_xy[k], co, col.w, pxf, pyf, e)) {
-          // 1 - alpha >= 0.01: one approximate reciprocal (relative error ~1e-7)
-          // serves the transmittance recovery and the suffix terms
-          const float rom = __fdividef(1.f, 1.f - e.alpha);
-          const float Tb = T * rom;           // transmittance in front of this splat
-          const float w = e.alpha * Tb;
-          d[6] = g0 * w; d[7] = g1 * w; d[8] = g2 * w;
-          float dal = g0 * (col.x * Tb - acc0 * rom) + g1 * (col.y * Tb - acc1 * rom) +
-                      g2 * (col.z * Tb - acc2 * rom) + ga * Tfinal * rom;
-          acc0 += col.x * w; acc1 += col.y * w; acc2 += col.z * w;
-          if (e.raw <= kAlphaMax) {
-            d[5] = dal * e.ex;                // d alpha / d opacity = exp(power)
-            const float dp = dal * e.alpha;   // d alpha / d power = alpha
-            d[2] = -0.5f * e.dx * e.dx * dp;
-            d[3] = -e.dx * e.dy * dp;
-            d[4] = -0.5f * e.dy * e.dy * dp;
-            d[0] = -(co.x * e.dx + co.y * e.dy) * dp;
-            d[1] = -(co.z * e.dy + co.y * e.dx) * dp;
-          }
-          T = Tb;
+      if (pos <= mylast) {
+        const float4 m = s_xy[k], co = s_co[k], col = s_rgb[k];
+        Eval e;
+        if (pos <= last0 && splat_alpha(m, co, col.w, pxf, py0f, e)) {
+          splat_grad(e, co, col, g00, g01, g02, ga0, Tf0, T0, a00, a01, a02, d);
+          contrib = true;
+        }
+        if (pos <= last1 && splat_alpha(m, co, col.w, pxf, py1f, e)) {
+          splat_grad(e, co, col, g10, g11, g12, ga1, Tf1, T1, a10, a11, a12, d);
           contrib = true;
         }
       }
-      float s8 = 0.f, t8 = 0.f;
-      int idx = ((lane & 16) ? 4 : 0) + ((lane & 8) ? 2 : 0) + ((lane & 4) ? 1 : 0);
-      if (__any_sync(0xffffffffu, contrib)) warp_sum9(d, lane, s8, idx, t8);
-      if ((lane & 3) == 0) s_red[k][warp][idx] = s8;
-      if (lane == 0) s_red[k][warp][8] = t8;
+      if (__any_sync(0xffffffffu, contrib)) {
+        float s8, t8;
+        int idx;
+        warp_sum9(d, lane, s8, idx, t8);
+        if ((lane & 3) == 0) s_red[k][warp][idx] = s8;
+        if (lane == 0) {
+          s_red[k][warp][8] = t8;
+          s_hit[k][warp] = 1;
+        }
+      }
     }
     __syncthreads();
-    if (threadIdx.x < cnt && (int64_t)s_pidx[threadIdx.x] >= a.cap) atomicOr(&a.counts[2], 2u);
-    if (threadIdx.x < cnt && (int64_t)s_pidx[threadIdx.x] < a.cap) {
-      float* dst = a.partials + (int64_t)s_pidx[threadIdx.x] * kPartialStride;
+    if (threadIdx.x < cnt) {
+      const uint32_t pidx = s_pidx[threadIdx.x];
+      if ((int64_t)pidx < a.cap) {
+        float sum[kPartialValues];
 #pragma unroll
-      for (int c = 0; c < kPartialStride; ++c) {
-        float s = 0.f;
+        for (int c = 0; c < kPartialValues; ++c) {
+          float acc = 0.f;
 #pragma unroll
-        for (int w2 = 0; w2 < kWarps; ++w2) s += s_red[threadIdx.x][w2][c];
-        dst[c] = s;
+          for (int w2 = 0; w2 < kWarps; ++w2)
+            if (s_hit[threadIdx.x][w2]) acc += s_red[threadIdx.x][w2][c];
+          sum[c] = acc;
+        }
+        float4* dst = reinterpret_cast<float4*>(a.partials + (int64_t)pidx * kPartialStride);
+        dst[0] = make_float4(sum[0], sum[1], sum[2], sum[3]);
+        dst[1] = make_float4(sum[4], sum[5], sum[6], sum[7]);
+        dst[2] = make_float4(sum[8], 0.f, 0.f, 0.f);
+      } else if (pidx != 0xffffffffu) {
+        atomicOr(&a.counts[2], 2u);
       }
     }
   }
@@ -363,7 +469,7 @@ gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const View
   a.image = image;
   a.alpha = alpha;
   if (vt.total_tiles == 0) return GS_OK;
-  k_render_fwd<false><<<vt.total_tiles, kTilePixels, 0, s>>>(a, vt, nullptr);
+  k_render_fwd<false><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr);
   return check_launch("k_render_fwd");
 }
 
@@ -382,7 +488,7 @@ gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const Vi
   a.alpha = nullptr;
   if (cudaMemsetAsync(stats, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return check_launch("stats");
   if (vt.total_tiles == 0) return GS_OK;
-  k_render_fwd<true><<<vt.total_tiles, kTilePixels, 0, s>>>(a, vt, stats);
+  k_render_fwd<true><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, stats);
   return check_launch("k_render_fwd<count>");
 }
 
@@ -405,7 +511,7 @@ gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const View
   a.dalpha = dalpha;
   a.partials = partials;
   if (vt.total_tiles == 0) return GS_OK;
-  k_render_bwd<<<vt.total_tiles, kTilePixels, 0, s>>>(a, vt);
+  k_render_bwd<<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
   return check_launch("k_render_bwd");
 }
 
