@@ -80,6 +80,8 @@ typedef void* gs_stream;  /* cudaStream_t */
  *   quat      [n][4]  w, x, y, z (any non-zero norm; normalised inside)
  *   sh        [3*nc][n] planar: plane (channel*nc + k) holds coefficient k of
  *             that colour channel for every Gaussian; nc = (sh_degree+1)^2
+ * sh_stride: distance in floats between consecutive SH planes (0 means n;
+ * a larger stride lets a capacity-sized arena hold a growing scene).
  * All four base pointers must be 16-byte aligned. */
 typedef struct {
   const float* means4;
@@ -88,6 +90,7 @@ typedef struct {
   const float* sh;
   int64_t n;
   int32_t sh_degree; /* 0..3 */
+  int64_t sh_stride;
 } gs_params;
 
 /* Gradients in exactly the layout of gs_params (the ignored 4th component of
@@ -99,6 +102,7 @@ typedef struct {
   float* sh;
   int64_t n;
   int32_t sh_degree;
+  int64_t sh_stride;
 } gs_grads;
 
 /* Intrinsics and image size of one view, host memory. */
@@ -173,7 +177,7 @@ typedef struct {
   float lr[4];
 } gs_adam_group;
 
-#define GS_MAX_ADAM_GROUPS 16
+#define GS_MAX_ADAM_GROUPS 64
 
 typedef struct {
   const gs_adam_group* groups; /* host array */
@@ -197,6 +201,10 @@ typedef struct {
    * is set, view v's pose update uses pose_steps_dev[v] + 1 and increments it. */
   int32_t* step_dev;
   int32_t* pose_steps_dev;
+  /* optional device word: when nonzero at run time the whole update (and the
+   * step counters) is skipped, e.g. the bins status of the step, so a step
+   * whose tile lists overflowed leaves the optimiser state untouched */
+  const uint32_t* skip_dev;
 } gs_adam_cfg;
 
 /* ---------------------------------------------------------------------- */
@@ -314,6 +322,105 @@ GS_API size_t gs_image_loss_workspace(void);
 GS_API gs_status gs_image_loss(const float* image, const float* target, int64_t count, int32_t kind,
                                float* dL_dimage, float* loss_dev, void* ws, size_t ws_bytes,
                                gs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Streaming session (the live-capture mode of §5.2: optimisation runs
+ * asynchronously while frames keep arriving).  A session owns the Gaussians,
+ * their gradients and Adam moments (capacity max_gaussians, SH planes strided
+ * by the capacity), and a pool of batch contexts (device buffers for one
+ * batch in flight each).  Requests (render or train, one camera each) are
+ * queued by gs_session_submit from any thread; a worker thread forms batches
+ * of up to max_batch_views requests as soon as a context is free and enqueues
+ * each batch without waiting for earlier ones (continuous batching); a
+ * completion thread finishes requests as their batch's event fires (bounded
+ * wait).  Render views of a batch see the parameters before the batch's
+ * update; all train views of a batch share one Adam step over every active
+ * Gaussian.  The number of contexts is what the HBM budget admits (at most
+ * max_inflight); queued requests wait for a free context.  A batch whose tile
+ * lists overflow skips its update on the device, grows its pair capacity
+ * within the budget and runs again.
+ * ------------------------------------------------------------------------ */
+typedef struct gs_session gs_session;
+
+#define GS_REQUEST_RENDER 0
+#define GS_REQUEST_TRAIN 1
+
+typedef struct {
+  int64_t max_gaussians;     /* device capacity (fixed for the session) */
+  int32_t sh_degree;
+  int32_t max_batch_views;   /* requests per batch, 1..GS_MAX_VIEWS */
+  int32_t max_width, max_height;
+  int32_t max_inflight;      /* batch contexts wanted (>= 1) */
+  uint64_t hbm_budget_bytes; /* all device memory of the session */
+  double pair_factor;        /* initial pair capacity = pair_factor * max_gaussians (0 = 4) */
+  gs_raster_cfg raster;
+  float lr_means, lr_scale, lr_opacity, lr_quat, lr_sh_dc, lr_sh_rest;
+  float beta1, beta2, eps;
+  int32_t loss_kind;         /* 0 = L1, 1 = MSE */
+} gs_session_config;
+
+typedef struct {
+  int32_t kind;              /* GS_REQUEST_RENDER or GS_REQUEST_TRAIN */
+  gs_camera cam;             /* within the session's maximum resolution */
+  float pose[12];            /* world->camera [R | t], row-major 3x4 */
+  const float* target;       /* train: host [3][H][W], copied during submit */
+  float* image_out;          /* render: host [3][H][W], filled before the request completes (may be NULL) */
+  double arrival_s;          /* arrival time on gs_session_now()'s clock; 0 = submit time */
+} gs_request;
+
+typedef struct {
+  int64_t submitted, completed, failed, queued, inflight;
+  int64_t iterations;        /* Adam steps taken (batches with train views) */
+  int64_t batches;
+  int64_t gaussians;         /* active Gaussians */
+  double pixels;             /* pixels of completed requests */
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* arrival -> completion, completed requests */
+  double wall_s;             /* since creation */
+  uint64_t hbm_in_use, hbm_budget;
+  int32_t contexts;
+} gs_stats;
+
+typedef struct {
+  size_t fixed_bytes;        /* arenas of parameters, gradients, moments */
+  size_t context_bytes;      /* one batch context at the initial pair capacity */
+  int64_t initial_pair_capacity;
+  int32_t contexts;          /* contexts the budget admits (<= max_inflight) */
+} gs_session_plan_info;
+
+/* Seconds on the steady clock the session timestamps requests with. */
+GS_API double gs_session_now(void);
+/* Memory plan of a configuration (host only; GS_ERR_OOM if the budget holds
+ * no batch context). */
+GS_API gs_status gs_session_plan(const gs_session_config* cfg, gs_session_plan_info* out);
+/* Creates a session on the current device (allocates its device memory,
+ * starts its two threads). */
+GS_API gs_status gs_session_create(const gs_session_config* cfg, gs_session** out);
+/* Appends `count` Gaussians (host arrays in natural layout: means [count][3],
+ * log-scales [count][3], quaternions [count][4] (w,x,y,z), opacity logits
+ * [count], SH [count][3][nc]); batches submitted later see them.
+ * GS_ERR_OOM beyond the capacity. */
+GS_API gs_status gs_session_add_gaussians(gs_session* s, int64_t count, const float* means,
+                                          const float* log_scales, const float* quats,
+                                          const float* opa_logits, const float* sh);
+/* Queues a request; *id identifies it for poll/wait.  Never blocks on GPU work. */
+GS_API gs_status gs_session_submit(gs_session* s, const gs_request* req, int64_t* id);
+/* *done = 1 when the request finished (its status is returned), else 0. */
+GS_API gs_status gs_session_poll(gs_session* s, int64_t id, int32_t* done);
+/* Waits up to timeout_ms for a request; GS_ERR_TIMEOUT if it is still pending. */
+GS_API gs_status gs_session_wait(gs_session* s, int64_t id, int32_t timeout_ms);
+/* Waits up to timeout_ms until nothing is queued or in flight. */
+GS_API gs_status gs_session_drain(gs_session* s, int32_t timeout_ms);
+GS_API gs_status gs_session_stats(gs_session* s, gs_stats* out);
+/* Copies the active parameters to host arrays in the library layout (each
+ * pointer may be NULL): means4 [n][4], scale_opa [n][4], quat [n][4], sh
+ * [3*nc][n].  Drains first. */
+GS_API gs_status gs_session_read_params(gs_session* s, float* means4, float* scale_opa, float* quat, float* sh);
+/* Checkpoint (parameters, Adam moments, step, active count) to a file and
+ * back; both drain first.  A resumed session continues bit-identically. */
+GS_API gs_status gs_session_save(gs_session* s, const char* path);
+GS_API gs_status gs_session_load(gs_session* s, const char* path);
+/* Drains the queue, stops the threads, frees everything. */
+GS_API gs_status gs_session_destroy(gs_session* s);
 
 #ifdef __cplusplus
 }

@@ -14,14 +14,19 @@ LIB_PATH = os.path.join(HERE, "_build", "libgs.so")
 GS_OK, GS_ERR_INVALID, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NONFINITE, GS_ERR_BUSY = range(7)
 GS_MAX_VIEWS = 64
 GS_TILE = 16
-GS_MAX_ADAM_GROUPS = 16
+GS_MAX_ADAM_GROUPS = 64
 
 EXPORTED = (
     "gs_last_error", "gs_version", "gs_built_arch", "gs_splats_bytes", "gs_splats_carve",
     "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_render_fwd",
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
+    "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
+    "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_stats", "gs_session_read_params",
+    "gs_session_save", "gs_session_load", "gs_session_destroy",
 )
+
+GS_REQUEST_RENDER, GS_REQUEST_TRAIN = 0, 1
 
 
 class GsError(RuntimeError):
@@ -32,7 +37,7 @@ class GsError(RuntimeError):
 
 class GsParams(C.Structure):
     _fields_ = [("means4", C.c_void_p), ("scale_opa", C.c_void_p), ("quat", C.c_void_p),
-                ("sh", C.c_void_p), ("n", C.c_int64), ("sh_degree", C.c_int32)]
+                ("sh", C.c_void_p), ("n", C.c_int64), ("sh_degree", C.c_int32), ("sh_stride", C.c_int64)]
 
 
 GsGrads = GsParams  # same layout (non-const pointers)
@@ -69,7 +74,34 @@ class GsAdamCfg(C.Structure):
                 ("beta2", C.c_float), ("eps", C.c_float), ("status", C.c_void_p), ("pose", C.c_void_p),
                 ("dpose", C.c_void_p), ("pose_m", C.c_void_p), ("pose_v", C.c_void_p),
                 ("views", C.c_int32), ("pose_lr", C.c_float), ("pose_step", C.c_int32),
-                ("step_dev", C.c_void_p), ("pose_steps_dev", C.c_void_p)]
+                ("step_dev", C.c_void_p), ("pose_steps_dev", C.c_void_p), ("skip_dev", C.c_void_p)]
+
+
+class GsSessionConfig(C.Structure):
+    _fields_ = [("max_gaussians", C.c_int64), ("sh_degree", C.c_int32), ("max_batch_views", C.c_int32),
+                ("max_width", C.c_int32), ("max_height", C.c_int32), ("max_inflight", C.c_int32),
+                ("hbm_budget_bytes", C.c_uint64), ("pair_factor", C.c_double), ("raster", GsRasterCfg),
+                ("lr_means", C.c_float), ("lr_scale", C.c_float), ("lr_opacity", C.c_float),
+                ("lr_quat", C.c_float), ("lr_sh_dc", C.c_float), ("lr_sh_rest", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("loss_kind", C.c_int32)]
+
+
+class GsRequest(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("cam", GsCamera), ("pose", C.c_float * 12), ("target", C.c_void_p),
+                ("image_out", C.c_void_p), ("arrival_s", C.c_double)]
+
+
+class GsStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64),
+                ("inflight", C.c_int64), ("iterations", C.c_int64), ("batches", C.c_int64),
+                ("gaussians", C.c_int64), ("pixels", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("mean_ms", C.c_double), ("max_ms", C.c_double), ("wall_s", C.c_double),
+                ("hbm_in_use", C.c_uint64), ("hbm_budget", C.c_uint64), ("contexts", C.c_int32)]
+
+
+class GsSessionPlan(C.Structure):
+    _fields_ = [("fixed_bytes", C.c_size_t), ("context_bytes", C.c_size_t), ("initial_pair_capacity", C.c_int64),
+                ("contexts", C.c_int32)]
 
 
 _lib = None
@@ -113,6 +145,23 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_image_loss_workspace.argtypes = []
     L.gs_image_loss_workspace.restype = sz
     L.gs_image_loss.argtypes = [vp, vp, i64, i32, vp, vp, vp, sz, vp]
+    L.gs_session_now.restype = C.c_double
+    L.gs_session_plan.argtypes = [P(GsSessionConfig), P(GsSessionPlan)]
+    L.gs_session_create.argtypes = [P(GsSessionConfig), P(vp)]
+    L.gs_session_add_gaussians.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.gs_session_submit.argtypes = [vp, P(GsRequest), P(i64)]
+    L.gs_session_poll.argtypes = [vp, i64, P(i32)]
+    L.gs_session_wait.argtypes = [vp, i64, i32]
+    L.gs_session_drain.argtypes = [vp, i32]
+    L.gs_session_stats.argtypes = [vp, P(GsStats)]
+    L.gs_session_read_params.argtypes = [vp, vp, vp, vp, vp]
+    L.gs_session_save.argtypes = [vp, C.c_char_p]
+    L.gs_session_load.argtypes = [vp, C.c_char_p]
+    L.gs_session_destroy.argtypes = [vp]
+    for name in ("gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
+                 "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_stats",
+                 "gs_session_read_params", "gs_session_save", "gs_session_load", "gs_session_destroy"):
+        getattr(L, name).restype = C.c_int
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
                  "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
                  "gs_render_stats"):

@@ -10,7 +10,7 @@ namespace gs {
 namespace {
 
 constexpr int kAdamThreads = 256;
-constexpr int64_t kAdamChunk = kAdamThreads * 4 * 4;  // elements per block (4 float4 per thread)
+constexpr int64_t kAdamChunk = kAdamThreads * 4 * 4;  // elements per block (4 float4 per thread, 2 at a time)
 
 struct AdamArgs {
   float* p;
@@ -24,39 +24,45 @@ struct AdamArgs {
   gs_adam_group groups[GS_MAX_ADAM_GROUPS];
   int32_t block_start[GS_MAX_ADAM_GROUPS + 1];  // first block of each group
   uint32_t* status;
-  const int32_t* step_dev;  // optional: step = *step_dev + 1
+  const int32_t* step_dev;   // optional: step = *step_dev + 1
+  const uint32_t* skip_dev;  // optional: nonzero = skip the update
 };
 
-// 1 - beta^step in double, rounded once
-__device__ __forceinline__ float bias_corr(float beta, int step) {
-  return (float)(1.0 - pow((double)beta, (double)step));
+// 1 - beta^step: beta^step by exponentiation by squaring in double (only
+// multiplications, so host and device give the same bits), rounded once.
+__host__ __device__ __forceinline__ float bias_corr(float beta, int step) {
+  double r = 1.0, b = (double)beta;
+  for (unsigned e = (unsigned)step; e; e >>= 1) {
+    if (e & 1u) r *= b;
+    b *= b;
+  }
+  return (float)(1.0 - r);
 }
 
-__device__ __forceinline__ bool adam_elem(float& p, float g, float& m, float& v, float lr,
-                                          const AdamArgs& a, float bc1, float bc2) {
+// p -= lr * (m / bc1) / (sqrt(v / bc2) + eps), written as
+// p -= (lr / bc1) * m / (sqrt(v) * rsqrt_bc2 + eps) with the step constants
+// hoisted out of the element loop.
+__device__ __forceinline__ bool adam_elem(float& p, float g, float& m, float& v, float step_size,
+                                          const AdamArgs& a, float rs_bc2) {
   m = a.b1 * m + (1.f - a.b1) * g;
   v = a.b2 * v + (1.f - a.b2) * g * g;
-  const float mh = m / bc1, vh = v / bc2;
-  p -= lr * mh / (sqrtf(vh) + a.eps);
+  p -= step_size * __fdividef(m, sqrtf(v) * rs_bc2 + a.eps);
   return isfinite(g) && isfinite(v);
 }
 
 // Block b updates one chunk of one group: the group is found once per block
 // (no per-element search); the chunk's 16-byte aligned body is processed as
-// float4, its ragged head and tail element by element.
+// float4 (two chunks per thread, loads issued before the stores), its ragged
+// head and tail element by element.
 __global__ void __launch_bounds__(kAdamThreads) k_adam(const AdamArgs a) {
-  __shared__ float s_bc[2];
+  if (a.skip_dev && *a.skip_dev) return;
   float bc1 = a.bc1, bc2 = a.bc2;
   if (a.step_dev) {
-    if (threadIdx.x == 0) {
-      const int st = *a.step_dev + 1;
-      s_bc[0] = bias_corr(a.b1, st);
-      s_bc[1] = bias_corr(a.b2, st);
-    }
-    __syncthreads();
-    bc1 = s_bc[0];
-    bc2 = s_bc[1];
+    const int st = *a.step_dev + 1;
+    bc1 = bias_corr(a.b1, st);
+    bc2 = bias_corr(a.b2, st);
   }
+  const float rs_bc2 = rsqrtf(bc2);
   const int b = blockIdx.x;
   int gi = 0;
   while (gi + 1 < a.num_groups && a.block_start[gi + 1] <= b) ++gi;
@@ -66,44 +72,39 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(const AdamArgs a) {
   if (r0 >= r1) return;
   const int64_t a0 = min(r1, (r0 + 3) & ~(int64_t)3);  // first 16-byte aligned element
   const int64_t a1 = max(a0, r1 & ~(int64_t)3);        // end of the float4 body
+  const float ss = 1.f / bc1;
   bool bad = false;
   for (int64_t e = r0 + threadIdx.x; e < a0; e += kAdamThreads)
-    bad |= !adam_elem(a.p[e], a.g[e], a.m[e], a.v[e], G.lr[(e - G.begin) & 3], a, bc1, bc2);
+    bad |= !adam_elem(a.p[e], a.g[e], a.m[e], a.v[e], G.lr[(e - G.begin) & 3] * ss, a, rs_bc2);
   const int rot = (int)((a0 - G.begin) & 3);
-  const float lr4[4] = {G.lr[rot & 3], G.lr[(rot + 1) & 3], G.lr[(rot + 2) & 3], G.lr[(rot + 3) & 3]};
-  // Each thread owns up to 4 float4 chunks of the block's body: all 16 loads
-  // are issued before any store (the arrays are touched once: streaming hints).
+  const float s0 = G.lr[rot & 3] * ss, s1 = G.lr[(rot + 1) & 3] * ss;
+  const float s2 = G.lr[(rot + 2) & 3] * ss, s3 = G.lr[(rot + 3) & 3] * ss;
   float4* __restrict__ P4 = reinterpret_cast<float4*>(a.p);
   const float4* __restrict__ G4 = reinterpret_cast<const float4*>(a.g);
   float4* __restrict__ M4 = reinterpret_cast<float4*>(a.m);
   float4* __restrict__ V4 = reinterpret_cast<float4*>(a.v);
-  const int64_t c0 = a0 / 4 + threadIdx.x, c1 = a1 / 4;
-  float4 p[4], g[4], m[4], v[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int64_t c = c0 + (int64_t)u * kAdamThreads;
-    if (c < c1) {
-      p[u] = __ldcs(P4 + c);
-      g[u] = __ldcs(G4 + c);
-      m[u] = __ldcs(M4 + c);
-      v[u] = __ldcs(V4 + c);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int64_t c = c0 + (int64_t)u * kAdamThreads;
-    if (c < c1) {
-      bad |= !adam_elem(p[u].x, g[u].x, m[u].x, v[u].x, lr4[0], a, bc1, bc2);
-      bad |= !adam_elem(p[u].y, g[u].y, m[u].y, v[u].y, lr4[1], a, bc1, bc2);
-      bad |= !adam_elem(p[u].z, g[u].z, m[u].z, v[u].z, lr4[2], a, bc1, bc2);
-      bad |= !adam_elem(p[u].w, g[u].w, m[u].w, v[u].w, lr4[3], a, bc1, bc2);
-      __stcs(P4 + c, p[u]);
-      __stcs(M4 + c, m[u]);
-      __stcs(V4 + c, v[u]);
+  const int64_t c1 = a1 / 4;
+  for (int64_t c0 = a0 / 4 + threadIdx.x; c0 < c1; c0 += 2 * kAdamThreads) {
+    const int64_t cb = c0 + kAdamThreads;
+    const bool two = cb < c1;
+    float4 p0 = P4[c0], g0 = G4[c0], m0 = M4[c0], v0 = V4[c0];
+    float4 p1, g1, m1, v1;
+    if (two) { p1 = P4[cb]; g1 = G4[cb]; m1 = M4[cb]; v1 = V4[cb]; }
+    bad |= !adam_elem(p0.x, g0.x, m0.x, v0.x, s0, a, rs_bc2);
+    bad |= !adam_elem(p0.y, g0.y, m0.y, v0.y, s1, a, rs_bc2);
+    bad |= !adam_elem(p0.z, g0.z, m0.z, v0.z, s2, a, rs_bc2);
+    bad |= !adam_elem(p0.w, g0.w, m0.w, v0.w, s3, a, rs_bc2);
+    P4[c0] = p0; M4[c0] = m0; V4[c0] = v0;
+    if (two) {
+      bad |= !adam_elem(p1.x, g1.x, m1.x, v1.x, s0, a, rs_bc2);
+      bad |= !adam_elem(p1.y, g1.y, m1.y, v1.y, s1, a, rs_bc2);
+      bad |= !adam_elem(p1.z, g1.z, m1.z, v1.z, s2, a, rs_bc2);
+      bad |= !adam_elem(p1.w, g1.w, m1.w, v1.w, s3, a, rs_bc2);
+      P4[cb] = p1; M4[cb] = m1; V4[cb] = v1;
     }
   }
   for (int64_t e = a1 + threadIdx.x; e < r1; e += kAdamThreads)
-    bad |= !adam_elem(a.p[e], a.g[e], a.m[e], a.v[e], G.lr[(e - G.begin) & 3], a, bc1, bc2);
+    bad |= !adam_elem(a.p[e], a.g[e], a.m[e], a.v[e], G.lr[(e - G.begin) & 3] * ss, a, rs_bc2);
   if (bad && a.status) atomicOr(a.status, 1u);
 }
 
@@ -117,13 +118,14 @@ struct PoseArgs {
   uint32_t* status;
   const int32_t* step_dev;  // optional shared step (*step_dev + 1)
   int32_t* pose_steps;      // optional per-view steps, incremented here
+  const uint32_t* skip_dev;
 };
 
 // Pose step per view: Adam on xi (zero-based tangent), then the SE(3)
 // exponential (Rodrigues rotation, V-matrix translation) applied on the left.
 __global__ void k_pose_adam(const PoseArgs a) {
   const int vw = blockIdx.x * blockDim.x + threadIdx.x;
-  if (vw >= a.views) return;
+  if (vw >= a.views || (a.skip_dev && *a.skip_dev)) return;
   float bc1 = a.bc1, bc2 = a.bc2;
   if (a.pose_steps) {
     const int st = a.pose_steps[vw] + 1;
@@ -186,7 +188,9 @@ __global__ void k_pose_adam(const PoseArgs a) {
   if (bad && a.status) atomicOr(a.status, 1u);
 }
 
-__global__ void k_step_increment(int32_t* step) { *step += 1; }
+__global__ void k_step_increment(int32_t* step, const uint32_t* skip) {
+  if (!(skip && *skip)) *step += 1;
+}
 
 }  // namespace
 
@@ -195,8 +199,8 @@ gs_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
   AdamArgs a;
   a.p = p; a.g = g; a.m = m; a.v = v; a.n = n;
   a.b1 = cfg.beta1; a.b2 = cfg.beta2; a.eps = cfg.eps;
-  a.bc1 = (float)(1.0 - std::pow((double)cfg.beta1, step));
-  a.bc2 = (float)(1.0 - std::pow((double)cfg.beta2, step));
+  a.bc1 = bias_corr(cfg.beta1, step);
+  a.bc2 = bias_corr(cfg.beta2, step);
   a.num_groups = cfg.num_groups;
   int64_t blocks = 0;
   for (int k = 0; k < cfg.num_groups; ++k) {
@@ -207,20 +211,22 @@ gs_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
   a.block_start[cfg.num_groups] = (int32_t)blocks;
   a.status = cfg.status;
   a.step_dev = cfg.step_dev;
+  a.skip_dev = cfg.skip_dev;
   if (n > 0 && blocks > 0) k_adam<<<(unsigned)blocks, kAdamThreads, 0, s>>>(a);
   if (cfg.pose && cfg.views > 0) {
     PoseArgs pa;
     pa.pose = cfg.pose; pa.dpose = cfg.dpose; pa.m = cfg.pose_m; pa.v = cfg.pose_v;
     pa.views = cfg.views; pa.lr = cfg.pose_lr; pa.b1 = cfg.beta1; pa.b2 = cfg.beta2; pa.eps = cfg.eps;
     const int ps = cfg.pose_step > 0 ? cfg.pose_step : step;
-    pa.bc1 = (float)(1.0 - std::pow((double)cfg.beta1, ps));
-    pa.bc2 = (float)(1.0 - std::pow((double)cfg.beta2, ps));
+    pa.bc1 = bias_corr(cfg.beta1, ps);
+    pa.bc2 = bias_corr(cfg.beta2, ps);
     pa.status = cfg.status;
     pa.step_dev = cfg.step_dev;
     pa.pose_steps = cfg.pose_steps_dev;
+    pa.skip_dev = cfg.skip_dev;
     k_pose_adam<<<(cfg.views + 63) / 64, 64, 0, s>>>(pa);
   }
-  if (cfg.step_dev) k_step_increment<<<1, 1, 0, s>>>(cfg.step_dev);
+  if (cfg.step_dev) k_step_increment<<<1, 1, 0, s>>>(cfg.step_dev, cfg.skip_dev);
   return check_launch("adam");
 }
 

@@ -79,6 +79,7 @@ static gs_status check_cfg(const gs_raster_cfg* cfg) {
 static gs_status check_params(const gs_params* p) {
   if (!p) return fail(GS_ERR_INVALID, "params is NULL");
   if (p->n < 0 || p->n >= (1ll << 31)) return fail(GS_ERR_INVALID, "n out of range");
+  if (p->sh_stride != 0 && p->sh_stride < p->n) return fail(GS_ERR_INVALID, "sh_stride must be 0 or >= n");
   if (p->sh_degree < 0 || p->sh_degree > 3) return fail(GS_ERR_INVALID, "sh_degree must be 0..3");
   if (p->n > 0 && (!p->means4 || !p->scale_opa || !p->quat || !p->sh))
     return fail(GS_ERR_INVALID, "NULL parameter array");
@@ -217,8 +218,8 @@ gs_status gs_render_fwd(const gs_splats* splats, const gs_bins* bins, const gs_c
 }
 
 static size_t bwd_layout(int64_t n, int32_t views, int64_t capacity, char* base, float** partials,
-                         float** pose_partials, int* pose_blocks, float** drgb = nullptr) {
-  const int blocks = (int)std::max<int64_t>(1, (n + kGradBlock - 1) / kGradBlock);
+                         float** pose_partials, float** drgb) {
+  const int64_t warps = pose_partial_warps(n);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char* p = base ? base + off : nullptr;
@@ -226,14 +227,28 @@ static size_t bwd_layout(int64_t n, int32_t views, int64_t capacity, char* base,
     return p;
   };
   float* pa = (float*)take(sizeof(float) * kPartialStride * (size_t)std::max<int64_t>(0, capacity));
-  float* pp = (float*)take(sizeof(float) * 6 * (size_t)blocks * (size_t)std::max(1, views));
+  float* pp = (float*)take(sizeof(float) * 9 * (size_t)warps * (size_t)std::max(1, views));
   float* dc = (float*)take(sizeof(float) * 4 * (size_t)std::max<int64_t>(0, n) * (size_t)std::max(1, views));
   if (drgb) *drgb = dc;
   if (partials) *partials = pa;
   if (pose_partials) *pose_partials = pp;
-  if (pose_blocks) *pose_blocks = blocks;
   return off;
 }
+
+}  // extern "C"
+
+namespace gs {
+size_t render_bwd_ws_bytes(int64_t n, int32_t views, int64_t capacity) {
+  return bwd_layout(n, views, capacity, nullptr, nullptr, nullptr, nullptr);
+}
+
+void render_bwd_ws_layout(int64_t n, int32_t views, int64_t capacity, void* ws, float** partials,
+                          float** pose_partials, float** drgb) {
+  bwd_layout(n, views, capacity, static_cast<char*>(ws), partials, pose_partials, drgb);
+}
+}  // namespace gs
+
+extern "C" {
 
 size_t gs_render_bwd_workspace(int64_t n, int32_t views, int64_t capacity) {
   return bwd_layout(n, views, capacity, nullptr, nullptr, nullptr, nullptr);
@@ -254,9 +269,8 @@ gs_status gs_render_bwd_pixels(const gs_splats* splats, const gs_bins* bins, con
   if (!ws || ws_bytes < need)
     return fail(GS_ERR_OOM, "render_bwd workspace: need %zu bytes, got %zu", need, ws_bytes);
   if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
-  float *partials, *pose_partials;
-  int pose_blocks;
-  bwd_layout(n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks);
+  float *partials, *pose_partials, *drgb;
+  bwd_layout(n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &drgb);
   return launch_render_bwd(*splats, *bins, vt, *cfg, dL_dimage, dL_dalpha, partials, (cudaStream_t)stream);
 }
 
@@ -272,7 +286,8 @@ gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_de
   if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
   if ((st = check_splats(splats, params->n, views)) != GS_OK) return st;
   if ((st = check_bins(bins, vt, params->n)) != GS_OK) return st;
-  if (!grads || grads->n != params->n || grads->sh_degree != params->sh_degree)
+  if (!grads || grads->n != params->n || grads->sh_degree != params->sh_degree ||
+      (grads->sh_stride != 0 && grads->sh_stride < grads->n))
     return fail(GS_ERR_INVALID, "grads must match params");
   if (params->n > 0 && (!grads->means4 || !grads->scale_opa || !grads->quat || !grads->sh))
     return fail(GS_ERR_INVALID, "NULL gradient array");
@@ -283,11 +298,9 @@ gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_de
     return fail(GS_ERR_OOM, "render_bwd workspace: need %zu bytes, got %zu", need, ws_bytes);
   if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
   float *partials, *pose_partials, *drgb;
-  int pose_blocks;
-  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks,
-             &drgb);
+  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &drgb);
   return launch_project_bwd(*params, poses_dev, vt, *cfg, *splats, *bins, partials, *grads, pose_partials,
-                            pose_blocks, dL_dpose, drgb, (cudaStream_t)stream);
+                            dL_dpose, drgb, (cudaStream_t)stream);
 }
 
 gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const gs_camera* cams,
@@ -304,7 +317,8 @@ gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const g
   if ((st = check_splats(splats, params->n, views)) != GS_OK) return st;
   if ((st = check_bins(bins, vt, params->n)) != GS_OK) return st;
   if (!dL_dimage) return fail(GS_ERR_INVALID, "dL_dimage is NULL");
-  if (!grads || grads->n != params->n || grads->sh_degree != params->sh_degree)
+  if (!grads || grads->n != params->n || grads->sh_degree != params->sh_degree ||
+      (grads->sh_stride != 0 && grads->sh_stride < grads->n))
     return fail(GS_ERR_INVALID, "grads must match params");
   if (params->n > 0 && (!grads->means4 || !grads->scale_opa || !grads->quat || !grads->sh))
     return fail(GS_ERR_INVALID, "NULL gradient array");
@@ -315,14 +329,12 @@ gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const g
     return fail(GS_ERR_OOM, "render_bwd workspace: need %zu bytes, got %zu", need, ws_bytes);
   if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
   float *partials, *pose_partials, *drgb;
-  int pose_blocks;
-  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &pose_blocks,
-             &drgb);
+  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &drgb);
   cudaStream_t s = (cudaStream_t)stream;
   st = launch_render_bwd(*splats, *bins, vt, *cfg, dL_dimage, dL_dalpha, partials, s);
   if (st != GS_OK) return st;
   return launch_project_bwd(*params, poses_dev, vt, *cfg, *splats, *bins, partials, *grads, pose_partials,
-                            pose_blocks, dL_dpose, drgb, s);
+                            dL_dpose, drgb, s);
 }
 
 gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int64_t n,

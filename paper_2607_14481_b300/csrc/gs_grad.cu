@@ -1,11 +1,18 @@
 // Per-Gaussian backward: sums each (view, Gaussian)'s per-tile partial
 // gradients in a fixed order, then applies the chain rule of the projection
-// (pixel-space mean, conic, opacity, SH colour) to the parameters (means,
-// log-scales, quaternion, opacity logit, SH) and to each view's pose for the
-// left perturbation T <- Exp(xi) T, xi = (v, omega).  One thread per
-// Gaussian, all views in one fixed-order loop; pose gradients are reduced per
-// block (fixed tree) and then over blocks (fixed order): the result is
-// deterministic without atomics.
+// to the parameters (means, log-scales, quaternion, opacity logit, SH) and to
+// each view's pose for the left perturbation T <- Exp(xi) T, xi = (v, omega).
+//
+// Two kernels, one thread per Gaussian, all views in one fixed-order loop:
+//   k_project_bwd  pixel-space mean, conic, opacity -> means, log-scales,
+//                  quaternion, opacity logit, pose (t and rotation terms);
+//                  stores each visible (view, Gaussian)'s colour gradient;
+//   k_sh_bwd       colour -> SH coefficients and, through the view
+//                  direction, the means and the pose translation.
+// Pose gradients are reduced per warp (shuffles, fixed tree) and then over
+// warps in a fixed order: deterministic, no atomics, no block barriers.
+#include <algorithm>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -18,6 +25,7 @@ struct GradArgs {
   const float4* quat;
   const float* sh;
   int64_t n;
+  int64_t sh_stride;
   const float* poses;
   int clamp_j;
   const uint32_t* touched;
@@ -29,37 +37,39 @@ struct GradArgs {
   float4* g_scale_opa;
   float4* g_quat;
   float* g_sh;
-  float* pose_partials;  // [V][gridDim.x][6]
+  int64_t g_sh_stride;
+  float* pose_a;         // [V][warps][6] from k_project_bwd
+  float* pose_b;         // [V][warps][3] from k_sh_bwd (translation part)
   float4* drgb;          // [V][n] summed colour gradient of each visible (view, Gaussian)
 };
 
-// Deterministic 256-thread sum of 6 values per thread into out[6] (thread 0).
-__device__ __forceinline__ void block_sum6(float (&x)[6], float* s_tmp /*[8][6]*/, float* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Warp sum of K values; lane 0 writes them to out[0..K).
+template <int K>
+__device__ __forceinline__ void warp_store_sum(float (&x)[K], float* out) {
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
+  for (int c = 0; c < K; ++c) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x[c] += __shfl_xor_sync(0xffffffffu, x[c], o);
   }
-  if (lane == 0) {
+  if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s_tmp[warp * 6 + c] = x[c];
+    for (int c = 0; c < K; ++c) out[c] = x[c];
   }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    float s = 0.f;
-    for (int w = 0; w < kGradBlock / 32; ++w) s += s_tmp[w * 6 + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
+}
+
+__device__ __forceinline__ bool pair_range_ok(const GradArgs& a, int64_t o, uint32_t kpairs, uint32_t& tch) {
+  tch = a.touched[o];
+  // pairs cut off by a capacity overflow were never rendered: skip them
+  if (tch > 0 && (uint64_t)a.pair_off[o] + tch > kpairs) tch = 0;
+  return tch > 0;
 }
 
 template <int DEG>
 __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, const ViewTable vt) {
-  constexpr int NC = (DEG + 1) * (DEG + 1);
-  __shared__ float s_tmp[(kGradBlock / 32) * 6];
   const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
   const bool valid = i < a.n;
+  const int64_t warp_id = i >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (kGradBlock / 32);
 
   float4 mu = make_float4(0.f, 0.f, 0.f, 0.f), so = mu, q4 = mu;
   if (valid) { mu = a.means4[i]; so = a.scale_opa[i]; q4 = a.quat[i]; }
@@ -77,23 +87,21 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
     for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * s[c];
   const float opa = 1.0f / (1.0f + expf(-so.w));
 
-  float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+  float gmu[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   float gol = 0.f;
-  // gradient w.r.t. the rotation matrix entries, accumulated over views
-  float gRq[9];
+  float gRq[9];  // gradient w.r.t. the rotation matrix entries, over views
 #pragma unroll
   for (int k = 0; k < 9; ++k) gRq[k] = 0.f;
-  float gs_[3] = {0.f, 0.f, 0.f};
+  float gsc[3] = {0.f, 0.f, 0.f};
 
   const uint32_t kpairs = a.counts[3];
   for (int v = 0; v < vt.views; ++v) {
     float pv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int64_t o = (int64_t)v * a.n + i;
-    uint32_t tch = valid ? a.touched[o] : 0u;
-    // pairs cut off by a capacity overflow were never rendered: skip them
-    if (tch > 0 && (uint64_t)a.pair_off[o] + tch > kpairs) tch = 0;
-    if (tch > 0) {
+    uint32_t tch = 0;
+    if (valid && pair_range_ok(a, o, kpairs, tch)) {
       const ViewInfo vi = vt.v[v];
+      const uint32_t auxb = a.aux[o];
       // ---- sum of this (view, Gaussian)'s per-tile partials, fixed order
       float G[kPartialValues];
 #pragma unroll
@@ -105,7 +113,6 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
         G[4] += p1.x; G[5] += p1.y; G[6] += p1.z; G[7] += p1.w;
         G[8] += p2.x;
       }
-      const uint32_t auxb = a.aux[o];
       a.drgb[o] = make_float4(G[6], G[7], G[8], 0.f);
       const float* P = a.poses + 12 * v;
       const float R[9] = {P[0], P[1], P[2], P[4], P[5], P[6], P[8], P[9], P[10]};
@@ -115,37 +122,6 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
       for (int r = 0; r < 3; ++r) t[r] = R[3 * r] * mu.x + R[3 * r + 1] * mu.y + R[3 * r + 2] * mu.z + tc[r];
       const float iz = 1.0f / t[2], iz2 = iz * iz;
       float dt[3] = {0.f, 0.f, 0.f};
-
-      // ---- colour (SH) and the view direction
-      {
-        const float oc0 = -(R[0] * tc[0] + R[3] * tc[1] + R[6] * tc[2]);
-        const float oc1 = -(R[1] * tc[0] + R[4] * tc[1] + R[7] * tc[2]);
-        const float oc2 = -(R[2] * tc[0] + R[5] * tc[1] + R[8] * tc[2]);
-        float wx = mu.x - oc0, wy = mu.y - oc1, wz = mu.z - oc2;
-        const float wn = sqrtf(wx * wx + wy * wy + wz * wz), inv = 1.0f / wn;
-        const float dx = wx * inv, dy = wy * inv, dz = wz * inv;
-        // d rgb / d Y_k = c_k for unclamped channels (the SH coefficient
-        // gradients g_c Y_k are accumulated by k_sh_bwd)
-        float dY[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) dY[k] = 0.f;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          if (auxb & (1u << ch)) continue;
-          const float gc = G[6 + ch];
-#pragma unroll
-          for (int k = 1; k < NC; ++k) dY[k] += gc * a.sh[(int64_t)(ch * NC + k) * a.n + i];
-        }
-        float ddx, ddy, ddz;
-        sh_basis_grad<DEG>(dx, dy, dz, dY, ddx, ddy, ddz);
-        const float pr = dx * ddx + dy * ddy + dz * ddz;
-        const float dwx = (ddx - dx * pr) * inv, dwy = (ddy - dy * pr) * inv, dwz = (ddz - dz * pr) * inv;
-        gmu[0] += dwx; gmu[1] += dwy; gmu[2] += dwz;
-        // mu - centre moves by R^T v under the pose perturbation
-        pv[0] += R[0] * dwx + R[1] * dwy + R[2] * dwz;
-        pv[1] += R[3] * dwx + R[4] * dwy + R[5] * dwz;
-        pv[2] += R[6] * dwx + R[7] * dwy + R[8] * dwz;
-      }
 
       // ---- opacity
       gol += G[5] * opa * (1.f - opa);
@@ -201,7 +177,7 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const float dm = T0[r] * dP0[c] + T1[r] * dP1[c];
-          gs_[c] += dm * Rq[3 * r + c];
+          gsc[c] += dm * Rq[3 * r + c];
           gRq[3 * r + c] += dm * s[c];
         }
       // T = J R (rows): dJ and the rotation-matrix gradient of the pose
@@ -235,10 +211,10 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
       gmu[1] += R[1] * dt[0] + R[4] * dt[1] + R[7] * dt[2];
       gmu[2] += R[2] * dt[0] + R[5] * dt[1] + R[8] * dt[2];
       // pose: t -> t + omega x t + v ; R -> R + [omega]x R
-      pv[0] += dt[0]; pv[1] += dt[1]; pv[2] += dt[2];
-      pv[3] += t[1] * dt[2] - t[2] * dt[1];
-      pv[4] += t[2] * dt[0] - t[0] * dt[2];
-      pv[5] += t[0] * dt[1] - t[1] * dt[0];
+      pv[0] = dt[0]; pv[1] = dt[1]; pv[2] = dt[2];
+      pv[3] = t[1] * dt[2] - t[2] * dt[1];
+      pv[4] = t[2] * dt[0] - t[0] * dt[2];
+      pv[5] = t[0] * dt[1] - t[1] * dt[0];
       // N = R dR^T; d omega += (N12 - N21, N20 - N02, N01 - N10)
       float N[9];
 #pragma unroll
@@ -250,8 +226,7 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
       pv[4] += N[6] - N[2];
       pv[5] += N[1] - N[3];
     }
-    float* dst = a.pose_partials + ((int64_t)v * gridDim.x + blockIdx.x) * 6;
-    block_sum6(pv, s_tmp, dst);
+    warp_store_sum<6>(pv, a.pose_a + ((int64_t)v * warps + warp_id) * 6);
   }
 
   if (!valid) return;
@@ -272,64 +247,96 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
   gq[1] = (dqx - qx * pr) * qi;
   gq[2] = (dqy - qy * pr) * qi;
   gq[3] = (dqz - qz * pr) * qi;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) gls[c] = gs_[c] * s[c];
-
   a.g_means4[i] = make_float4(gmu[0], gmu[1], gmu[2], 0.f);
-  a.g_scale_opa[i] = make_float4(gls[0], gls[1], gls[2], gol);
+  a.g_scale_opa[i] = make_float4(gsc[0] * s[0], gsc[1] * s[1], gsc[2] * s[2], gol);
   a.g_quat[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
 }
 
-// SH coefficient gradients: sum over views (fixed order) of g_c Y_k(dir) for
-// every unclamped channel c, from the colour gradients k_project_bwd stored.
+// SH coefficients and the view direction: for every visible view (fixed
+// order), g_c Y_k(dir) for each unclamped channel c, and through dir =
+// normalise(mu - centre) the means (added to k_project_bwd's) and the pose
+// translation (mu - centre moves by R^T v).
 template <int DEG>
-__global__ void __launch_bounds__(256) k_sh_bwd(const GradArgs a, const ViewTable vt) {
+__global__ void __launch_bounds__(kGradBlock) k_sh_bwd(const GradArgs a, const ViewTable vt) {
   constexpr int NC = (DEG + 1) * (DEG + 1);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const float4 mu = a.means4[i];
+  const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
+  const bool valid = i < a.n;
+  const int64_t warp_id = i >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (kGradBlock / 32);
+  const float4 mu = valid ? a.means4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   float gsh[3][NC];
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch)
 #pragma unroll
     for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
+  float gmu[3] = {0.f, 0.f, 0.f};
   const uint32_t kpairs = a.counts[3];
   for (int v = 0; v < vt.views; ++v) {
+    float pv[3] = {0.f, 0.f, 0.f};
     const int64_t o = (int64_t)v * a.n + i;
-    const uint32_t tch = a.touched[o];
-    if (tch == 0 || (uint64_t)a.pair_off[o] + tch > kpairs) continue;
-    const float4 g = a.drgb[o];
-    const uint32_t auxb = a.aux[o];
-    const float* P = a.poses + 12 * v;
-    const float oc0 = -(P[0] * P[3] + P[4] * P[7] + P[8] * P[11]);
-    const float oc1 = -(P[1] * P[3] + P[5] * P[7] + P[9] * P[11]);
-    const float oc2 = -(P[2] * P[3] + P[6] * P[7] + P[10] * P[11]);
-    float wx = mu.x - oc0, wy = mu.y - oc1, wz = mu.z - oc2;
-    const float inv = 1.0f / sqrtf(wx * wx + wy * wy + wz * wz);
-    float Y[NC];
-    sh_basis<DEG>(wx * inv, wy * inv, wz * inv, Y);
-    const float gc[3] = {(auxb & 1u) ? 0.f : g.x, (auxb & 2u) ? 0.f : g.y, (auxb & 4u) ? 0.f : g.z};
+    uint32_t tch = 0;
+    if (valid && pair_range_ok(a, o, kpairs, tch)) {
+      const float4 g = a.drgb[o];
+      const uint32_t auxb = a.aux[o];
+      const float* P = a.poses + 12 * v;
+      const float oc0 = -(P[0] * P[3] + P[4] * P[7] + P[8] * P[11]);
+      const float oc1 = -(P[1] * P[3] + P[5] * P[7] + P[9] * P[11]);
+      const float oc2 = -(P[2] * P[3] + P[6] * P[7] + P[10] * P[11]);
+      const float wx = mu.x - oc0, wy = mu.y - oc1, wz = mu.z - oc2;
+      const float inv = 1.0f / sqrtf(wx * wx + wy * wy + wz * wz);
+      const float dx = wx * inv, dy = wy * inv, dz = wz * inv;
+      float Y[NC];
+      sh_basis<DEG>(dx, dy, dz, Y);
+      const float gc[3] = {(auxb & 1u) ? 0.f : g.x, (auxb & 2u) ? 0.f : g.y, (auxb & 4u) ? 0.f : g.z};
+      float dY[NC];
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
+      for (int k = 0; k < NC; ++k) dY[k] = 0.f;
 #pragma unroll
-      for (int k = 0; k < NC; ++k) gsh[ch][k] += gc[ch] * Y[k];
+      for (int ch = 0; ch < 3; ++ch) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          gsh[ch][k] += gc[ch] * Y[k];
+          if (k > 0) dY[k] += gc[ch] * a.sh[(int64_t)(ch * NC + k) * a.sh_stride + i];
+        }
+      }
+      if (DEG > 0) {
+        float ddx, ddy, ddz;
+        sh_basis_grad<DEG>(dx, dy, dz, dY, ddx, ddy, ddz);
+        const float pr = dx * ddx + dy * ddy + dz * ddz;
+        const float dwx = (ddx - dx * pr) * inv, dwy = (ddy - dy * pr) * inv, dwz = (ddz - dz * pr) * inv;
+        gmu[0] += dwx; gmu[1] += dwy; gmu[2] += dwz;
+        pv[0] = P[0] * dwx + P[1] * dwy + P[2] * dwz;
+        pv[1] = P[4] * dwx + P[5] * dwy + P[6] * dwz;
+        pv[2] = P[8] * dwx + P[9] * dwy + P[10] * dwz;
+      }
+    }
+    warp_store_sum<3>(pv, a.pose_b + ((int64_t)v * warps + warp_id) * 3);
   }
+  if (!valid) return;
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch)
 #pragma unroll
-    for (int k = 0; k < NC; ++k) a.g_sh[(int64_t)(ch * NC + k) * a.n + i] = gsh[ch][k];
+    for (int k = 0; k < NC; ++k) a.g_sh[(int64_t)(ch * NC + k) * a.g_sh_stride + i] = gsh[ch][k];
+  if (DEG > 0) {
+    float4 gm = a.g_means4[i];
+    gm.x += gmu[0]; gm.y += gmu[1]; gm.z += gmu[2];
+    a.g_means4[i] = gm;
+  }
 }
 
-// Sum of the per-block pose partials of each view, in a fixed order.
-__global__ void __launch_bounds__(256) k_pose_finalize(const float* __restrict__ partials,
-                                                       int blocks, float* __restrict__ dpose) {
+// Sum of the per-warp pose partials of each view, in a fixed order.
+__global__ void __launch_bounds__(256) k_pose_finalize(const float* __restrict__ pa, const float* __restrict__ pb,
+                                                       int64_t warps, float* __restrict__ dpose) {
   __shared__ float s[256][6];
   const int v = blockIdx.x;
   float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int b = threadIdx.x; b < blocks; b += 256) {
-    const float* p = partials + ((int64_t)v * blocks + b) * 6;
+  for (int64_t b = threadIdx.x; b < warps; b += 256) {
+    const float* p = pa + ((int64_t)v * warps + b) * 6;
+    const float* q = pb + ((int64_t)v * warps + b) * 3;
 #pragma unroll
     for (int c = 0; c < 6; ++c) acc[c] += p[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] += q[c];
   }
 #pragma unroll
   for (int c = 0; c < 6; ++c) s[threadIdx.x][c] = acc[c];
@@ -346,16 +353,21 @@ __global__ void __launch_bounds__(256) k_pose_finalize(const float* __restrict__
 
 }  // namespace
 
+int64_t pose_partial_warps(int64_t n) {
+  return std::max<int64_t>(1, (n + kGradBlock - 1) / kGradBlock) * (kGradBlock / 32);
+}
+
 gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewTable& vt,
                              const gs_raster_cfg& cfg, const gs_splats& sp, const gs_bins& bins,
-                             const float* partials, const gs_grads& g, float* pose_partials,
-                             int pose_blocks, float* dpose, float* drgb, cudaStream_t s) {
+                             const float* partials, const gs_grads& g, float* pose_partials, float* dpose,
+                             float* drgb, cudaStream_t s) {
   GradArgs a;
   a.means4 = reinterpret_cast<const float4*>(p.means4);
   a.scale_opa = reinterpret_cast<const float4*>(p.scale_opa);
   a.quat = reinterpret_cast<const float4*>(p.quat);
   a.sh = p.sh;
   a.n = p.n;
+  a.sh_stride = p.sh_stride > 0 ? p.sh_stride : p.n;
   a.poses = poses;
   a.clamp_j = cfg.clamp_jacobian;
   a.touched = sp.touched;
@@ -367,33 +379,35 @@ gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewT
   a.g_scale_opa = reinterpret_cast<float4*>(g.scale_opa);
   a.g_quat = reinterpret_cast<float4*>(g.quat);
   a.g_sh = g.sh;
-  a.pose_partials = pose_partials;
+  a.g_sh_stride = g.sh_stride > 0 ? g.sh_stride : g.n;
+  const int64_t warps = pose_partial_warps(p.n);
+  a.pose_a = pose_partials;
+  a.pose_b = pose_partials + 6 * warps * vt.views;
   a.drgb = reinterpret_cast<float4*>(drgb);
   if (p.n == 0) {
     if (dpose) cudaMemsetAsync(dpose, 0, sizeof(float) * 6 * vt.views, s);
     return check_launch("project_bwd");
   }
-  const unsigned grid = (unsigned)pose_blocks;
-  const unsigned sh_grid = (unsigned)((p.n + 255) / 256);
+  const unsigned grid = (unsigned)((p.n + kGradBlock - 1) / kGradBlock);
   switch (p.sh_degree) {
     case 0:
       k_project_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd<0><<<sh_grid, 256, 0, s>>>(a, vt);
+      k_sh_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt);
       break;
     case 1:
       k_project_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd<1><<<sh_grid, 256, 0, s>>>(a, vt);
+      k_sh_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt);
       break;
     case 2:
       k_project_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd<2><<<sh_grid, 256, 0, s>>>(a, vt);
+      k_sh_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt);
       break;
     default:
       k_project_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd<3><<<sh_grid, 256, 0, s>>>(a, vt);
+      k_sh_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt);
       break;
   }
-  if (dpose) k_pose_finalize<<<vt.views, 256, 0, s>>>(pose_partials, pose_blocks, dpose);
+  if (dpose) k_pose_finalize<<<vt.views, 256, 0, s>>>(a.pose_a, a.pose_b, warps, dpose);
   return check_launch("project_bwd");
 }
 

@@ -48,8 +48,10 @@ gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const View
                             float* partials, cudaStream_t s);
 gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewTable& vt,
                              const gs_raster_cfg& cfg, const gs_splats& sp, const gs_bins& bins,
-                             const float* partials, const gs_grads& g, float* pose_partials,
-                             int pose_blocks, float* dpose, float* drgb, cudaStream_t s);
+                             const float* partials, const gs_grads& g, float* pose_partials, float* dpose,
+                             float* drgb, cudaStream_t s);
+// warps of the per-Gaussian backward (pose partials are kept per warp)
+int64_t pose_partial_warps(int64_t n);
 gs_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
                       const gs_adam_cfg& cfg, int step, cudaStream_t s);
 

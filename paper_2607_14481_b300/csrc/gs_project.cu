@@ -15,6 +15,7 @@ struct ProjectArgs {
   const float4* quat;
   const float* sh;
   int64_t n;
+  int64_t sh_stride;
   const float* poses;
   float znear;
   int clamp_j;
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
     for (int ch = 0; ch < 3; ++ch) {
       float acc = 0.f;
 #pragma unroll
-      for (int k = 0; k < NC; ++k) acc += a.sh[(int64_t)(ch * NC + k) * a.n + i] * Y[k];
+      for (int k = 0; k < NC; ++k) acc += a.sh[(int64_t)(ch * NC + k) * a.sh_stride + i] * Y[k];
       acc += 0.5f;
       if (acc < 0.f) { acc = 0.f; auxbits |= 1u << ch; }
       cv[ch] = acc;
@@ -160,6 +161,7 @@ gs_status launch_project(const gs_params& p, const float* poses, const ViewTable
   a.quat = reinterpret_cast<const float4*>(p.quat);
   a.sh = p.sh;
   a.n = p.n;
+  a.sh_stride = p.sh_stride > 0 ? p.sh_stride : p.n;
   a.poses = poses;
   a.znear = cfg.znear;
   a.clamp_j = cfg.clamp_jacobian;

@@ -1,0 +1,870 @@
+// Streaming session: a persistent loop that admits render and train requests
+// as frames arrive (the live-capture mode of §5.2, where optimisation runs
+// asynchronously until the next keyframe), batches them continuously, keeps
+// the Gaussians, their Adam state and the tile lists resident on the device,
+// admits work by an HBM budget and reports latency percentiles beside
+// throughput.
+//
+// Threads.  gs_session_submit appends to a queue.  A worker thread forms a
+// batch of up to max_batch_views queued requests as soon as a batch context is
+// free and enqueues the batch's whole iteration on the session's stream
+// without waiting for earlier batches: a request that arrives while batches
+// run joins the next batch (continuous batching), and its copies overlap the
+// kernels of the batches ahead of it.  A completion thread waits for each
+// batch's event with a bounded poll, copies rendered images to the callers'
+// buffers and records per-request latency.
+//
+// Within a batch, render views are rasterised first (they see the parameters
+// before this batch's update), then the train views run forward, loss,
+// backward and one fused Adam step over every active Gaussian.  If a batch
+// overflows its pair capacity the Adam step is skipped on the device, the
+// capacity grows (within the budget) and the batch is issued again.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+size_t bin_sort_workspace_bytes(int64_t m, int64_t cap);
+gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bins& bins, void* ws,
+                          cudaStream_t s);
+size_t render_bwd_ws_bytes(int64_t n, int32_t views, int64_t capacity);
+void render_bwd_ws_layout(int64_t n, int32_t views, int64_t capacity, void* ws, float** partials,
+                          float** pose_partials, float** drgb);
+
+namespace {
+
+double steady_now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+  int64_t id = 0;
+  int32_t kind = 0;
+  gs_camera cam{};
+  float pose[12]{};
+  std::vector<float> target;
+  float* image_out = nullptr;
+  double arrival = 0.0;
+  double done_at = 0.0;
+  int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+  gs_status status = GS_OK;
+};
+
+struct Dev {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Device and pinned buffers of one batch in flight.
+struct Ctx {
+  cudaEvent_t done = nullptr;
+  Dev splat_buf, pair_off, ranges, counts, vals, ws_bin, ws_bwd, img, dimg, tgt, loss_ws, loss, poses, dpose;
+  float* h_img = nullptr;       // pinned staging of rendered images
+  float* h_tgt = nullptr;       // pinned staging of targets
+  float* h_poses = nullptr;     // pinned poses [2][max views][12]
+  uint32_t* h_counts = nullptr; // pinned [8]: counts of the render and train sub-batches
+  int64_t pair_cap = 0;
+  size_t bytes = 0;             // device bytes held
+  std::vector<std::shared_ptr<Req>> reqs;
+  bool busy = false;
+  bool has_train = false;
+};
+
+}  // namespace
+}  // namespace gs
+
+struct gs_session {
+  gs_session_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  gs::Dev arena[4];  // parameters, gradients, first and second moments (stride = capacity)
+  gs::Dev status_word, step_dev;
+  int64_t capacity = 0;
+  int64_t n_active = 0;
+  int nc = 1;
+  size_t fixed_bytes = 0, ctx_bytes = 0, in_use = 0;
+  std::vector<std::unique_ptr<gs::Ctx>> ctxs;
+  float* h_add = nullptr;  // pinned staging of added Gaussians
+  int64_t h_add_cap = 0;
+  cudaEvent_t add_done = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done, cv_ctx;
+  std::deque<std::shared_ptr<gs::Req>> queue;
+  std::deque<gs::Ctx*> inflight;
+  std::vector<std::shared_ptr<gs::Req>> all;  // index = id - 1
+  std::vector<double> latencies;
+  int64_t iterations = 0, batches = 0, completed = 0, failed = 0;
+  double pixels = 0.0, created_at = 0.0;
+  bool stop = false;
+  gs_status fatal = GS_OK;
+  std::thread worker, completer;
+};
+
+namespace gs {
+namespace {
+
+constexpr double kWaitTimeout = 30.0;  // seconds a batch may take before the session gives up
+
+size_t arena_floats(int64_t cap, int nc) { return (size_t)(12 + 3 * nc) * (size_t)cap; }
+
+int64_t max_pixels(const gs_session_config& c) { return (int64_t)c.max_width * c.max_height; }
+int64_t max_tiles(const gs_session_config& c) {
+  return (int64_t)((c.max_width + kTile - 1) / kTile) * ((c.max_height + kTile - 1) / kTile);
+}
+
+// Device bytes of one batch context at a given pair capacity.
+size_t ctx_device_bytes(const gs_session_config& c, int64_t cap_n, int64_t pair_cap) {
+  const int64_t V = c.max_batch_views;
+  size_t b = 0;
+  auto add = [&](size_t x) { b += align_up(std::max<size_t>(x, 16), 256); };
+  add(gs_splats_bytes(cap_n, (int32_t)V));
+  add(4 * (size_t)cap_n * V);                     // pair_off
+  add(8 * (size_t)max_tiles(c) * V);              // ranges
+  add(32);                                        // counts of both sub-batches
+  add(4 * (size_t)pair_cap);                      // vals
+  add(bin_sort_workspace_bytes(cap_n * V, pair_cap));
+  add(render_bwd_ws_bytes(cap_n, (int32_t)V, pair_cap));
+  add(12 * (size_t)max_pixels(c) * V);            // images
+  add(12 * (size_t)max_pixels(c) * V);            // loss gradient
+  add(12 * (size_t)max_pixels(c) * V);            // targets
+  add(loss_workspace_bytes());
+  add(8);                                         // loss
+  add(48 * 2 * (size_t)V);                        // poses
+  add(24 * (size_t)V);                            // pose gradient
+  return b;
+}
+
+size_t fixed_device_bytes(const gs_session_config& c) {
+  const int nc = (c.sh_degree + 1) * (c.sh_degree + 1);
+  return 4 * align_up(4 * arena_floats(c.max_gaussians, nc), 256) + 2 * 256;
+}
+
+int64_t initial_pair_cap(const gs_session_config& c) {
+  const double f = c.pair_factor > 0.0 ? c.pair_factor : 4.0;
+  return std::max<int64_t>(4096, (int64_t)(f * (double)c.max_gaussians));
+}
+
+gs_status dalloc(Dev& d, size_t bytes, size_t& counter) {
+  d.bytes = align_up(std::max<size_t>(bytes, 16), 256);
+  if (cudaMalloc(&d.p, d.bytes) != cudaSuccess) {
+    cudaGetLastError();
+    d.p = nullptr;
+    return fail(GS_ERR_OOM, "session: cudaMalloc of %zu bytes failed", d.bytes);
+  }
+  counter += d.bytes;
+  return GS_OK;
+}
+
+void dfree(Dev& d, size_t& counter) {
+  if (d.p) {
+    cudaFree(d.p);
+    counter -= d.bytes;
+  }
+  d.p = nullptr;
+  d.bytes = 0;
+}
+
+void free_pair_buffers(gs_session* S, Ctx& c) {
+  dfree(c.vals, S->in_use);
+  dfree(c.ws_bin, S->in_use);
+  dfree(c.ws_bwd, S->in_use);
+}
+
+gs_status alloc_pair_buffers(gs_session* S, Ctx& c, int64_t pair_cap) {
+  const auto& cf = S->cfg;
+  const int64_t V = cf.max_batch_views;
+  gs_status st;
+  if ((st = dalloc(c.vals, 4 * (size_t)pair_cap, S->in_use)) != GS_OK) return st;
+  if ((st = dalloc(c.ws_bin, bin_sort_workspace_bytes(S->capacity * V, pair_cap), S->in_use)) != GS_OK)
+    return st;
+  if ((st = dalloc(c.ws_bwd, render_bwd_ws_bytes(S->capacity, (int32_t)V, pair_cap), S->in_use)) != GS_OK)
+    return st;
+  c.pair_cap = pair_cap;
+  return GS_OK;
+}
+
+gs_status alloc_ctx(gs_session* S, Ctx& c) {
+  const auto& cf = S->cfg;
+  const int64_t V = cf.max_batch_views, px = max_pixels(cf);
+  size_t& u = S->in_use;
+  gs_status st;
+  if ((st = dalloc(c.splat_buf, gs_splats_bytes(S->capacity, (int32_t)V), u)) != GS_OK) return st;
+  if ((st = dalloc(c.pair_off, 4 * (size_t)S->capacity * V, u)) != GS_OK) return st;
+  if ((st = dalloc(c.ranges, 8 * (size_t)max_tiles(cf) * V, u)) != GS_OK) return st;
+  if ((st = dalloc(c.counts, 32, u)) != GS_OK) return st;
+  if ((st = dalloc(c.img, 12 * (size_t)px * V, u)) != GS_OK) return st;
+  if ((st = dalloc(c.dimg, 12 * (size_t)px * V, u)) != GS_OK) return st;
+  if ((st = dalloc(c.tgt, 12 * (size_t)px * V, u)) != GS_OK) return st;
+  if ((st = dalloc(c.loss_ws, loss_workspace_bytes(), u)) != GS_OK) return st;
+  if ((st = dalloc(c.loss, 8, u)) != GS_OK) return st;
+  if ((st = dalloc(c.poses, 48 * 2 * (size_t)V, u)) != GS_OK) return st;
+  if ((st = dalloc(c.dpose, 24 * (size_t)V, u)) != GS_OK) return st;
+  if ((st = alloc_pair_buffers(S, c, initial_pair_cap(cf))) != GS_OK) return st;
+  if (cudaMallocHost(&c.h_img, 12 * (size_t)px * V) != cudaSuccess ||
+      cudaMallocHost(&c.h_tgt, 12 * (size_t)px * V) != cudaSuccess ||
+      cudaMallocHost(&c.h_poses, 48 * 2 * (size_t)V) != cudaSuccess ||
+      cudaMallocHost(&c.h_counts, 32) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GS_ERR_OOM, "session: pinned host allocation failed");
+  }
+  if (cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) return check_launch("event");
+  return GS_OK;
+}
+
+void free_ctx(gs_session* S, Ctx& c) {
+  Dev* devs[] = {&c.splat_buf, &c.pair_off, &c.ranges, &c.counts, &c.vals, &c.ws_bin, &c.ws_bwd, &c.img,
+                 &c.dimg, &c.tgt, &c.loss_ws, &c.loss, &c.poses, &c.dpose};
+  for (Dev* d : devs) dfree(*d, S->in_use);
+  if (c.h_img) cudaFreeHost(c.h_img);
+  if (c.h_tgt) cudaFreeHost(c.h_tgt);
+  if (c.h_poses) cudaFreeHost(c.h_poses);
+  if (c.h_counts) cudaFreeHost(c.h_counts);
+  if (c.done) cudaEventDestroy(c.done);
+  c = Ctx();
+}
+
+float* arena_ptr(gs_session* S, int k) { return static_cast<float*>(S->arena[k].p); }
+
+gs_params params_of(gs_session* S, int k) {
+  float* a = arena_ptr(S, k);
+  const int64_t cap = S->capacity;
+  gs_params p;
+  p.means4 = a;
+  p.scale_opa = a + 4 * cap;
+  p.quat = a + 8 * cap;
+  p.sh = a + 12 * cap;
+  p.n = S->n_active;
+  p.sh_degree = S->cfg.sh_degree;
+  p.sh_stride = cap;
+  return p;
+}
+
+// Adam groups over the active slots of the capacity-strided arena.
+int adam_groups(gs_session* S, gs_adam_group* g) {
+  const auto& c = S->cfg;
+  const int64_t n = S->n_active, cap = S->capacity;
+  int k = 0;
+  auto set = [&](int64_t b, int64_t e, float l0, float l1, float l2, float l3) {
+    g[k].begin = b; g[k].end = e;
+    g[k].lr[0] = l0; g[k].lr[1] = l1; g[k].lr[2] = l2; g[k].lr[3] = l3;
+    ++k;
+  };
+  set(0, 4 * n, c.lr_means, c.lr_means, c.lr_means, 0.f);
+  set(4 * cap, 4 * cap + 4 * n, c.lr_scale, c.lr_scale, c.lr_scale, c.lr_opacity);
+  set(8 * cap, 8 * cap + 4 * n, c.lr_quat, c.lr_quat, c.lr_quat, c.lr_quat);
+  for (int p = 0; p < 3 * S->nc; ++p) {
+    const float lr = (p % S->nc == 0) ? c.lr_sh_dc : c.lr_sh_rest;
+    const int64_t b = 12 * cap + (int64_t)p * cap;
+    set(b, b + n, lr, lr, lr, lr);
+  }
+  return k;
+}
+
+// Enqueue one batch's whole iteration on the session stream (S->mu held).
+gs_status issue_batch(gs_session* S, Ctx& c) {
+  cudaStream_t s = S->stream;
+  const auto& cf = S->cfg;
+  const int64_t n = S->n_active;
+  std::vector<Req*> R, T;
+  std::vector<gs_camera> cR, cT;
+  for (auto& r : c.reqs) {
+    if (r->kind == GS_REQUEST_TRAIN) { T.push_back(r.get()); cT.push_back(r->cam); }
+    else { R.push_back(r.get()); cR.push_back(r->cam); }
+  }
+  c.has_train = !T.empty();
+  gs_params P = params_of(S, 0);
+  uint32_t* counts = static_cast<uint32_t*>(c.counts.p);
+  float* img = static_cast<float*>(c.img.p);
+  float* poses = static_cast<float*>(c.poses.p);
+  const int V = cf.max_batch_views;
+  gs_status st;
+  int64_t off = 0;
+  if (!R.empty()) {
+    ViewTable vt;
+    if (!make_view_table(cR.data(), (int)R.size(), &vt)) return GS_ERR_INVALID;
+    for (size_t i = 0; i < R.size(); ++i) std::memcpy(c.h_poses + 12 * i, R[i]->pose, 48);
+    if (cudaMemcpyAsync(poses, c.h_poses, 48 * R.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return check_launch("session poses");
+    gs_splats sp;
+    gs_splats_carve(c.splat_buf.p, n, (int32_t)R.size(), &sp);
+    gs_bins b{static_cast<uint32_t*>(c.vals.p), static_cast<uint32_t*>(c.ranges.p),
+              static_cast<uint32_t*>(c.pair_off.p), nullptr, counts, c.pair_cap, vt.total_tiles};
+    if ((st = launch_project(P, poses, vt, cf.raster, sp, s)) != GS_OK) return st;
+    if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, s)) != GS_OK) return st;
+    if ((st = launch_render_fwd(sp, b, vt, cf.raster, img, nullptr, s)) != GS_OK) return st;
+    for (Req* r : R) off += 3 * (int64_t)r->cam.width * r->cam.height;
+    if (cudaMemcpyAsync(c.h_img, img, 4 * off, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return check_launch("session images");
+    if (cudaMemcpyAsync(c.h_counts, counts, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return check_launch("session counts");
+  } else {
+    std::memset(c.h_counts, 0, 16);
+  }
+  if (!T.empty()) {
+    ViewTable vt;
+    if (!make_view_table(cT.data(), (int)T.size(), &vt)) return GS_ERR_INVALID;
+    int64_t tpx = 0;
+    for (Req* r : T) {
+      const int64_t k = 3 * (int64_t)r->cam.width * r->cam.height;
+      std::memcpy(c.h_tgt + tpx, r->target.data(), 4 * k);
+      tpx += k;
+    }
+    float* tgt = static_cast<float*>(c.tgt.p);
+    float* dimg = static_cast<float*>(c.dimg.p);
+    if (cudaMemcpyAsync(tgt, c.h_tgt, 4 * tpx, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return check_launch("session targets");
+    for (size_t i = 0; i < T.size(); ++i) std::memcpy(c.h_poses + 12 * (V + i), T[i]->pose, 48);
+    float* tposes = poses + 12 * V;
+    if (cudaMemcpyAsync(tposes, c.h_poses + 12 * V, 48 * T.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return check_launch("session poses");
+    gs_splats sp;
+    gs_splats_carve(c.splat_buf.p, n, (int32_t)T.size(), &sp);
+    gs_bins b{static_cast<uint32_t*>(c.vals.p), static_cast<uint32_t*>(c.ranges.p),
+              static_cast<uint32_t*>(c.pair_off.p), nullptr, counts + 4, c.pair_cap, vt.total_tiles};
+    float* timg = img + off;
+    if ((st = launch_project(P, tposes, vt, cf.raster, sp, s)) != GS_OK) return st;
+    if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, s)) != GS_OK) return st;
+    if ((st = launch_render_fwd(sp, b, vt, cf.raster, timg, nullptr, s)) != GS_OK) return st;
+    if ((st = launch_loss(timg, tgt, tpx, cf.loss_kind, dimg, static_cast<float*>(c.loss.p), c.loss_ws.p, s)) !=
+        GS_OK)
+      return st;
+    float *partials, *pose_partials, *drgb;
+    render_bwd_ws_layout(n, (int32_t)T.size(), c.pair_cap, c.ws_bwd.p, &partials, &pose_partials, &drgb);
+    if ((st = launch_render_bwd(sp, b, vt, cf.raster, dimg, nullptr, partials, s)) != GS_OK) return st;
+    gs_params G = params_of(S, 1);
+    gs_grads g{const_cast<float*>(G.means4), const_cast<float*>(G.scale_opa), const_cast<float*>(G.quat),
+               const_cast<float*>(G.sh), G.n, G.sh_degree, G.sh_stride};
+    if ((st = launch_project_bwd(P, tposes, vt, cf.raster, sp, b, partials, g, pose_partials, nullptr, drgb,
+                                 s)) != GS_OK)
+      return st;
+    gs_adam_group groups[GS_MAX_ADAM_GROUPS];
+    gs_adam_cfg ac{};
+    ac.groups = groups;
+    ac.num_groups = adam_groups(S, groups);
+    ac.beta1 = cf.beta1; ac.beta2 = cf.beta2; ac.eps = cf.eps;
+    ac.status = static_cast<uint32_t*>(S->status_word.p);
+    ac.step_dev = static_cast<int32_t*>(S->step_dev.p);
+    ac.skip_dev = counts + 6;  // the train sub-batch's bins status: skip on overflow
+    const int64_t arena_n = (int64_t)arena_floats(S->capacity, S->nc);
+    if ((st = launch_adam(arena_ptr(S, 0), arena_ptr(S, 1), arena_ptr(S, 2), arena_ptr(S, 3), arena_n, ac, 0,
+                          s)) != GS_OK)
+      return st;
+    if (cudaMemcpyAsync(c.h_counts + 4, counts + 4, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return check_launch("session counts");
+  }
+  if (cudaEventRecord(c.done, s) != cudaSuccess) return check_launch("session event");
+  return GS_OK;
+}
+
+Ctx* free_ctx_of(gs_session* S) {
+  for (auto& c : S->ctxs)
+    if (!c->busy) return c.get();
+  return nullptr;
+}
+
+void finish_req(gs_session* S, Req* r, gs_status st) {
+  r->done_at = steady_now();
+  r->status = st;
+  r->state = st == GS_OK ? 2 : 3;
+  if (st == GS_OK) {
+    S->completed++;
+    S->latencies.push_back(1e3 * (r->done_at - r->arrival));
+    S->pixels += (double)r->cam.width * r->cam.height;
+  } else {
+    S->failed++;
+  }
+}
+
+void worker_main(gs_session* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    // exit only once nothing is queued or in flight: a batch in flight may
+    // still send its requests back (pair capacity retry)
+    S->cv_work.wait(lk, [&] {
+      return (S->stop && S->queue.empty() && S->inflight.empty()) ||
+             (!S->queue.empty() && free_ctx_of(S) != nullptr);
+    });
+    if (S->queue.empty()) break;  // stop requested and drained
+    Ctx* c = free_ctx_of(S);
+    c->busy = true;
+    c->reqs.clear();
+    while (!S->queue.empty() && (int)c->reqs.size() < S->cfg.max_batch_views) {
+      c->reqs.push_back(S->queue.front());
+      S->queue.pop_front();
+      c->reqs.back()->state = 1;
+    }
+    const gs_status st = issue_batch(S, *c);
+    if (st != GS_OK) {
+      for (auto& r : c->reqs) finish_req(S, r.get(), st);
+      c->reqs.clear();
+      c->busy = false;
+      S->cv_done.notify_all();
+      continue;
+    }
+    S->batches++;
+    S->inflight.push_back(c);
+    S->cv_done.notify_all();
+  }
+  S->cv_done.notify_all();
+}
+
+void completer_main(gs_session* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    S->cv_done.wait(lk, [&] { return !S->inflight.empty() || (S->stop && S->queue.empty()); });
+    if (S->inflight.empty()) break;
+    Ctx* c = S->inflight.front();
+    lk.unlock();
+    const double t0 = steady_now();
+    cudaError_t e;
+    while ((e = cudaEventQuery(c->done)) == cudaErrorNotReady) {
+      if (steady_now() - t0 > kWaitTimeout) break;
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    // copy rendered images out before taking the lock
+    bool retry = false, bad_index = false;
+    if (e == cudaSuccess) {
+      const uint32_t sr = c->h_counts[2], strn = c->has_train ? c->h_counts[6] : 0u;
+      retry = ((sr | strn) & 1u) != 0;
+      bad_index = ((sr | strn) & 2u) != 0;
+      if (!retry && !bad_index) {
+        int64_t off = 0;
+        for (auto& r : c->reqs) {
+          if (r->kind != GS_REQUEST_RENDER) continue;
+          const int64_t k = 3 * (int64_t)r->cam.width * r->cam.height;
+          if (r->image_out) std::memcpy(r->image_out, c->h_img + off, 4 * k);
+          off += k;
+        }
+      }
+    }
+    lk.lock();
+    S->inflight.pop_front();
+    if (e == cudaErrorNotReady) {
+      S->fatal = GS_ERR_TIMEOUT;
+      for (auto& r : c->reqs) finish_req(S, r.get(), GS_ERR_TIMEOUT);
+    } else if (e != cudaSuccess) {
+      cudaGetLastError();
+      S->fatal = GS_ERR_CUDA;
+      for (auto& r : c->reqs) finish_req(S, r.get(), GS_ERR_CUDA);
+    } else if (bad_index) {
+      for (auto& r : c->reqs) finish_req(S, r.get(), GS_ERR_CUDA);
+    } else if (retry) {
+      const uint32_t K = std::max(c->h_counts[1], c->has_train ? c->h_counts[5] : 0u);
+      const int64_t want = (int64_t)(1.25 * (double)K) + 4096;
+      const size_t old = c->vals.bytes + c->ws_bin.bytes + c->ws_bwd.bytes;
+      const int64_t V = S->cfg.max_batch_views;
+      const size_t grow = align_up(4 * (size_t)want, 256) + bin_sort_workspace_bytes(S->capacity * V, want) +
+                          render_bwd_ws_bytes(S->capacity, (int32_t)V, want);
+      gs_status st = GS_OK;
+      if (S->in_use - old + grow > S->cfg.hbm_budget_bytes) {
+        st = fail(GS_ERR_OOM, "session: pair capacity %lld exceeds the HBM budget", (long long)want);
+      } else {
+        free_pair_buffers(S, *c);
+        st = alloc_pair_buffers(S, *c, want);
+      }
+      if (st != GS_OK) {
+        for (auto& r : c->reqs) finish_req(S, r.get(), st);
+      } else {
+        // issue the same requests again, ahead of everything queued
+        for (auto it = c->reqs.rbegin(); it != c->reqs.rend(); ++it) {
+          (*it)->state = 0;
+          S->queue.push_front(*it);
+        }
+      }
+    } else {
+      if (c->has_train) S->iterations++;
+      for (auto& r : c->reqs) finish_req(S, r.get(), GS_OK);
+    }
+    c->reqs.clear();
+    c->busy = false;
+    S->cv_work.notify_all();
+    S->cv_done.notify_all();
+    if (S->fatal != GS_OK) {
+      // a batch that does not finish (or a CUDA error) leaves the stream unusable:
+      // fail everything queued and stop
+      for (auto& r : S->queue) finish_req(S, r.get(), S->fatal);
+      S->queue.clear();
+      S->stop = true;
+      S->cv_work.notify_all();
+    }
+  }
+}
+
+gs_status wait_idle(gs_session* S, std::unique_lock<std::mutex>& lk, int timeout_ms) {
+  const bool ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                      [&] { return S->queue.empty() && S->inflight.empty(); });
+  if (!ok) return fail(GS_ERR_TIMEOUT, "session: not idle after %d ms", timeout_ms);
+  return S->fatal;
+}
+
+gs_status sync_stream(gs_session* S, double timeout_s) {
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return check_launch("event");
+  cudaEventRecord(ev, S->stream);
+  const double t0 = steady_now();
+  cudaError_t e;
+  while ((e = cudaEventQuery(ev)) == cudaErrorNotReady) {
+    if (steady_now() - t0 > timeout_s) break;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  if (e == cudaErrorNotReady) return fail(GS_ERR_TIMEOUT, "session: stream did not finish");
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, "session: %s", cudaGetErrorString(e));
+  return GS_OK;
+}
+
+}  // namespace
+}  // namespace gs
+
+using gs::Ctx;
+using gs::Req;
+
+extern "C" {
+
+double gs_session_now(void) { return gs::steady_now(); }
+
+gs_status gs_session_plan(const gs_session_config* cfg, gs_session_plan_info* out) {
+  if (!cfg || !out) return gs::fail(GS_ERR_INVALID, "NULL config or plan");
+  if (cfg->max_gaussians <= 0 || cfg->max_gaussians >= (1ll << 31) || cfg->sh_degree < 0 || cfg->sh_degree > 3)
+    return gs::fail(GS_ERR_INVALID, "session: bad max_gaussians or sh_degree");
+  if (cfg->max_batch_views < 1 || cfg->max_batch_views > GS_MAX_VIEWS)
+    return gs::fail(GS_ERR_INVALID, "session: max_batch_views must be 1..%d", GS_MAX_VIEWS);
+  if (cfg->max_width <= 0 || cfg->max_height <= 0 || cfg->max_width > 16 * 4096 || cfg->max_height > 16 * 4096)
+    return gs::fail(GS_ERR_INVALID, "session: bad maximum resolution");
+  if ((uint64_t)cfg->max_gaussians * (uint64_t)cfg->max_batch_views >= (1ull << 32))
+    return gs::fail(GS_ERR_INVALID, "session: max_gaussians * max_batch_views must be < 2^32");
+  out->fixed_bytes = gs::fixed_device_bytes(*cfg);
+  out->context_bytes = gs::ctx_device_bytes(*cfg, cfg->max_gaussians, gs::initial_pair_cap(*cfg));
+  out->initial_pair_capacity = gs::initial_pair_cap(*cfg);
+  const uint64_t budget = cfg->hbm_budget_bytes;
+  int64_t k = 0;
+  if (budget > out->fixed_bytes) k = (int64_t)((budget - out->fixed_bytes) / std::max<size_t>(1, out->context_bytes));
+  out->contexts = (int32_t)std::min<int64_t>(k, std::max(1, cfg->max_inflight));
+  return out->contexts >= 1 ? GS_OK
+                            : gs::fail(GS_ERR_OOM, "session: budget %llu B holds no batch context (fixed %zu B, "
+                                                   "context %zu B)",
+                                       (unsigned long long)budget, out->fixed_bytes, out->context_bytes);
+}
+
+gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
+  if (!out) return gs::fail(GS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  gs_session_plan_info plan;
+  gs_status st = gs_session_plan(cfg, &plan);
+  if (st != GS_OK) return st;
+  if (cfg->raster.tile_w != gs::kTile || cfg->raster.tile_h != gs::kTile || !(cfg->raster.znear > 0.f))
+    return gs::fail(GS_ERR_INVALID, "session: raster config must use %dx%d tiles and znear > 0", gs::kTile,
+                    gs::kTile);
+  if (cfg->loss_kind != 0 && cfg->loss_kind != 1) return gs::fail(GS_ERR_INVALID, "session: loss_kind 0 or 1");
+  auto S = std::make_unique<gs_session>();
+  S->cfg = *cfg;
+  S->nc = (cfg->sh_degree + 1) * (cfg->sh_degree + 1);
+  S->capacity = cfg->max_gaussians;
+  S->created_at = gs::steady_now();
+  cudaGetDevice(&S->device);
+  if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) return gs::check_launch("stream");
+  auto cleanup = [&](gs_status e) {
+    for (auto& c : S->ctxs) gs::free_ctx(S.get(), *c);
+    for (auto& a : S->arena) gs::dfree(a, S->in_use);
+    gs::dfree(S->status_word, S->in_use);
+    gs::dfree(S->step_dev, S->in_use);
+    if (S->h_add) cudaFreeHost(S->h_add);
+    if (S->add_done) cudaEventDestroy(S->add_done);
+    cudaStreamDestroy(S->stream);
+    return e;
+  };
+  const size_t af = gs::arena_floats(S->capacity, S->nc);
+  for (auto& a : S->arena) {
+    if ((st = gs::dalloc(a, 4 * af, S->in_use)) != GS_OK) return cleanup(st);
+    cudaMemsetAsync(a.p, 0, a.bytes, S->stream);
+  }
+  if ((st = gs::dalloc(S->status_word, 16, S->in_use)) != GS_OK) return cleanup(st);
+  if ((st = gs::dalloc(S->step_dev, 16, S->in_use)) != GS_OK) return cleanup(st);
+  cudaMemsetAsync(S->status_word.p, 0, 16, S->stream);
+  cudaMemsetAsync(S->step_dev.p, 0, 16, S->stream);
+  for (int k = 0; k < plan.contexts; ++k) {
+    S->ctxs.push_back(std::make_unique<Ctx>());
+    if ((st = gs::alloc_ctx(S.get(), *S->ctxs.back())) != GS_OK) return cleanup(st);
+  }
+  S->h_add_cap = 1 << 16;
+  if (cudaMallocHost(&S->h_add, sizeof(float) * (12 + 3 * S->nc) * S->h_add_cap) != cudaSuccess)
+    return cleanup(gs::fail(GS_ERR_OOM, "session: pinned staging"));
+  cudaEventCreateWithFlags(&S->add_done, cudaEventDisableTiming);
+  cudaEventRecord(S->add_done, S->stream);
+  if ((st = gs::sync_stream(S.get(), 30.0)) != GS_OK) return cleanup(st);
+  gs_session* raw = S.release();
+  raw->worker = std::thread(gs::worker_main, raw);
+  raw->completer = std::thread(gs::completer_main, raw);
+  *out = raw;
+  return GS_OK;
+}
+
+gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* means, const float* log_scales,
+                                   const float* quats, const float* opa_logits, const float* sh) {
+  if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
+  if (count < 0) return gs::fail(GS_ERR_INVALID, "count < 0");
+  if (count == 0) return GS_OK;
+  if (!means || !log_scales || !quats || !opa_logits || !sh) return gs::fail(GS_ERR_INVALID, "NULL array");
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
+  if (S->n_active + count > S->capacity)
+    return gs::fail(GS_ERR_OOM, "session: %lld + %lld Gaussians exceed the capacity %lld",
+                    (long long)S->n_active, (long long)count, (long long)S->capacity);
+  const int nc = S->nc;
+  const int64_t cap = S->capacity;
+  for (int64_t done = 0; done < count;) {
+    const int64_t k = std::min(S->h_add_cap, count - done);
+    // the staging buffer is free once the previous chunk's copies finished
+    const double t0 = gs::steady_now();
+    cudaError_t e;
+    while ((e = cudaEventQuery(S->add_done)) == cudaErrorNotReady) {
+      if (gs::steady_now() - t0 > 30.0) return gs::fail(GS_ERR_TIMEOUT, "session: add staging busy");
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    if (e != cudaSuccess) return gs::fail(GS_ERR_CUDA, "session: %s", cudaGetErrorString(e));
+    float* h = S->h_add;
+    float* hm = h;
+    float* hs = h + 4 * k;
+    float* hq = h + 8 * k;
+    float* hsh = h + 12 * k;
+    for (int64_t i = 0; i < k; ++i) {
+      const int64_t g = done + i;
+      hm[4 * i] = means[3 * g]; hm[4 * i + 1] = means[3 * g + 1]; hm[4 * i + 2] = means[3 * g + 2]; hm[4 * i + 3] = 0.f;
+      hs[4 * i] = log_scales[3 * g]; hs[4 * i + 1] = log_scales[3 * g + 1]; hs[4 * i + 2] = log_scales[3 * g + 2];
+      hs[4 * i + 3] = opa_logits[g];
+      for (int c = 0; c < 4; ++c) hq[4 * i + c] = quats[4 * g + c];
+      for (int p = 0; p < 3 * nc; ++p) hsh[(int64_t)p * k + i] = sh[(int64_t)g * 3 * nc + p];
+    }
+    const int64_t n0 = S->n_active + done;
+    float* A = gs::arena_ptr(S, 0);
+    cudaStream_t s = S->stream;
+    cudaMemcpyAsync(A + 4 * n0, hm, 16 * k, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(A + 4 * cap + 4 * n0, hs, 16 * k, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(A + 8 * cap + 4 * n0, hq, 16 * k, cudaMemcpyHostToDevice, s);
+    cudaMemcpy2DAsync(A + 12 * cap + n0, 4 * cap, hsh, 4 * k, 4 * k, 3 * nc, cudaMemcpyHostToDevice, s);
+    for (int a = 2; a < 4; ++a) {  // fresh Adam moments for the new slots
+      float* M = gs::arena_ptr(S, a);
+      cudaMemsetAsync(M + 4 * n0, 0, 16 * k, s);
+      cudaMemsetAsync(M + 4 * cap + 4 * n0, 0, 16 * k, s);
+      cudaMemsetAsync(M + 8 * cap + 4 * n0, 0, 16 * k, s);
+      cudaMemset2DAsync(M + 12 * cap + n0, 4 * cap, 0, 4 * k, 3 * nc, s);
+    }
+    cudaEventRecord(S->add_done, s);
+    gs_status st = gs::check_launch("session add");
+    if (st != GS_OK) return st;
+    done += k;
+  }
+  S->n_active += count;
+  return GS_OK;
+}
+
+gs_status gs_session_submit(gs_session* S, const gs_request* req, int64_t* id) {
+  if (!S || !req) return gs::fail(GS_ERR_INVALID, "NULL session or request");
+  if (req->kind != GS_REQUEST_RENDER && req->kind != GS_REQUEST_TRAIN)
+    return gs::fail(GS_ERR_INVALID, "request kind must be render or train");
+  const gs_camera& c = req->cam;
+  if (c.width <= 0 || c.height <= 0 || c.width > S->cfg.max_width || c.height > S->cfg.max_height ||
+      !(c.fx > 0.f) || !(c.fy > 0.f))
+    return gs::fail(GS_ERR_INVALID, "request camera %dx%d outside the session limits %dx%d", c.width, c.height,
+                    S->cfg.max_width, S->cfg.max_height);
+  if (req->kind == GS_REQUEST_TRAIN && !req->target) return gs::fail(GS_ERR_INVALID, "train request needs a target");
+  auto r = std::make_shared<Req>();
+  r->kind = req->kind;
+  r->cam = c;
+  std::memcpy(r->pose, req->pose, sizeof(r->pose));
+  r->image_out = req->image_out;
+  r->arrival = req->arrival_s > 0.0 ? req->arrival_s : gs::steady_now();
+  if (req->kind == GS_REQUEST_TRAIN) r->target.assign(req->target, req->target + 3 * (int64_t)c.width * c.height);
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
+  if (S->stop) return gs::fail(GS_ERR_BUSY, "session is stopping");
+  r->id = (int64_t)S->all.size() + 1;
+  S->all.push_back(r);
+  S->queue.push_back(r);
+  if (id) *id = r->id;
+  S->cv_work.notify_one();
+  return GS_OK;
+}
+
+gs_status gs_session_poll(gs_session* S, int64_t id, int32_t* done) {
+  if (!S || !done) return gs::fail(GS_ERR_INVALID, "NULL session or output");
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (id < 1 || id > (int64_t)S->all.size()) return gs::fail(GS_ERR_INVALID, "unknown request id %lld", (long long)id);
+  const Req& r = *S->all[id - 1];
+  *done = r.state >= 2 ? 1 : 0;
+  return r.state == 3 ? r.status : GS_OK;
+}
+
+gs_status gs_session_wait(gs_session* S, int64_t id, int32_t timeout_ms) {
+  if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (id < 1 || id > (int64_t)S->all.size()) return gs::fail(GS_ERR_INVALID, "unknown request id %lld", (long long)id);
+  auto r = S->all[id - 1];
+  if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->state >= 2; }))
+    return gs::fail(GS_ERR_TIMEOUT, "request %lld not done after %d ms", (long long)id, timeout_ms);
+  return r->state == 3 ? gs::fail(r->status, "request %lld failed", (long long)id) : GS_OK;
+}
+
+gs_status gs_session_drain(gs_session* S, int32_t timeout_ms) {
+  if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
+  std::unique_lock<std::mutex> lk(S->mu);
+  return gs::wait_idle(S, lk, timeout_ms);
+}
+
+gs_status gs_session_stats(gs_session* S, gs_stats* out) {
+  if (!S || !out) return gs::fail(GS_ERR_INVALID, "NULL session or stats");
+  std::unique_lock<std::mutex> lk(S->mu);
+  gs_stats st{};
+  st.submitted = (int64_t)S->all.size();
+  st.completed = S->completed;
+  st.failed = S->failed;
+  st.queued = (int64_t)S->queue.size();
+  int64_t inflight = 0;
+  for (auto* c : S->inflight) inflight += (int64_t)c->reqs.size();
+  st.inflight = inflight;
+  st.iterations = S->iterations;
+  st.batches = S->batches;
+  st.gaussians = S->n_active;
+  st.pixels = S->pixels;
+  st.wall_s = gs::steady_now() - S->created_at;
+  st.hbm_in_use = S->in_use;
+  st.hbm_budget = S->cfg.hbm_budget_bytes;
+  st.contexts = (int32_t)S->ctxs.size();
+  if (!S->latencies.empty()) {
+    std::vector<double> l = S->latencies;
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double q) {
+      // nearest rank
+      const size_t k = (size_t)std::min<double>((double)l.size() - 1, std::ceil(q * (double)l.size()) - 1);
+      return l[std::max<size_t>(0, k)];
+    };
+    st.p50_ms = pct(0.50);
+    st.p99_ms = pct(0.99);
+    st.max_ms = l.back();
+    double s = 0;
+    for (double x : l) s += x;
+    st.mean_ms = s / (double)l.size();
+  }
+  *out = st;
+  return GS_OK;
+}
+
+// Checkpoint: parameters, Adam moments, the step counter and the active count.
+gs_status gs_session_save(gs_session* S, const char* path) {
+  if (!S || !path) return gs::fail(GS_ERR_INVALID, "NULL session or path");
+  std::unique_lock<std::mutex> lk(S->mu);
+  gs_status st = gs::wait_idle(S, lk, 60000);
+  if (st != GS_OK) return st;
+  if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
+  const int64_t n = S->n_active, cap = S->capacity;
+  const int nc = S->nc;
+  int32_t step = 0;
+  cudaMemcpy(&step, S->step_dev.p, 4, cudaMemcpyDeviceToHost);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return gs::fail(GS_ERR_INVALID, "cannot open %s", path);
+  const int64_t hdr[4] = {0x3153534553534723ll, (int64_t)S->cfg.sh_degree, n, (int64_t)step};
+  bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1;
+  std::vector<float> buf((size_t)(12 + 3 * nc) * std::max<int64_t>(n, 1));
+  for (int a : {0, 2, 3}) {
+    const float* A = gs::arena_ptr(S, a);
+    cudaMemcpy(buf.data(), A, 16 * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(buf.data() + 4 * n, A + 4 * cap, 16 * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(buf.data() + 8 * n, A + 8 * cap, 16 * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy2D(buf.data() + 12 * n, 4 * n, A + 12 * cap, 4 * cap, 4 * n, 3 * nc, cudaMemcpyDeviceToHost);
+    ok = ok && std::fwrite(buf.data(), sizeof(float), (size_t)(12 + 3 * nc) * n, f) == (size_t)(12 + 3 * nc) * n;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if ((st = gs::check_launch("session save")) != GS_OK) return st;
+  return ok ? GS_OK : gs::fail(GS_ERR_INVALID, "write to %s failed", path);
+}
+
+gs_status gs_session_load(gs_session* S, const char* path) {
+  if (!S || !path) return gs::fail(GS_ERR_INVALID, "NULL session or path");
+  std::unique_lock<std::mutex> lk(S->mu);
+  gs_status st = gs::wait_idle(S, lk, 60000);
+  if (st != GS_OK) return st;
+  if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return gs::fail(GS_ERR_INVALID, "cannot open %s", path);
+  int64_t hdr[4];
+  if (std::fread(hdr, sizeof(hdr), 1, f) != 1 || hdr[0] != 0x3153534553534723ll || hdr[1] != S->cfg.sh_degree ||
+      hdr[2] < 0 || hdr[2] > S->capacity) {
+    std::fclose(f);
+    return gs::fail(GS_ERR_INVALID, "%s is not a checkpoint of this session's layout", path);
+  }
+  const int64_t n = hdr[2], cap = S->capacity;
+  const int nc = S->nc;
+  std::vector<float> buf((size_t)(12 + 3 * nc) * std::max<int64_t>(n, 1));
+  bool ok = true;
+  for (int a : {0, 2, 3}) {
+    ok = ok && std::fread(buf.data(), sizeof(float), (size_t)(12 + 3 * nc) * n, f) == (size_t)(12 + 3 * nc) * n;
+    if (!ok) break;
+    float* A = gs::arena_ptr(S, a);
+    cudaMemcpy(A, buf.data(), 16 * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(A + 4 * cap, buf.data() + 4 * n, 16 * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(A + 8 * cap, buf.data() + 8 * n, 16 * n, cudaMemcpyHostToDevice);
+    cudaMemcpy2D(A + 12 * cap, 4 * cap, buf.data() + 12 * n, 4 * n, 4 * n, 3 * nc, cudaMemcpyHostToDevice);
+  }
+  std::fclose(f);
+  if (!ok) return gs::fail(GS_ERR_INVALID, "%s is truncated", path);
+  const int32_t step = (int32_t)hdr[3];
+  cudaMemcpy(S->step_dev.p, &step, 4, cudaMemcpyHostToDevice);
+  S->n_active = n;
+  return gs::check_launch("session load");
+}
+
+gs_status gs_session_read_params(gs_session* S, float* means4, float* scale_opa, float* quat, float* sh) {
+  if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
+  std::unique_lock<std::mutex> lk(S->mu);
+  gs_status st = gs::wait_idle(S, lk, 60000);
+  if (st != GS_OK) return st;
+  if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
+  const int64_t n = S->n_active, cap = S->capacity;
+  const float* A = gs::arena_ptr(S, 0);
+  if (means4) cudaMemcpy(means4, A, 16 * n, cudaMemcpyDeviceToHost);
+  if (scale_opa) cudaMemcpy(scale_opa, A + 4 * cap, 16 * n, cudaMemcpyDeviceToHost);
+  if (quat) cudaMemcpy(quat, A + 8 * cap, 16 * n, cudaMemcpyDeviceToHost);
+  if (sh) cudaMemcpy2D(sh, 4 * n, A + 12 * cap, 4 * cap, 4 * n, 3 * S->nc, cudaMemcpyDeviceToHost);
+  return gs::check_launch("session read");
+}
+
+gs_status gs_session_destroy(gs_session* S) {
+  if (!S) return GS_OK;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv_work.notify_all();
+    S->cv_done.notify_all();
+  }
+  if (S->worker.joinable()) S->worker.join();
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->cv_done.notify_all();
+  }
+  if (S->completer.joinable()) S->completer.join();
+  gs::sync_stream(S, 30.0);
+  for (auto& c : S->ctxs) gs::free_ctx(S, *c);
+  for (auto& a : S->arena) gs::dfree(a, S->in_use);
+  gs::dfree(S->status_word, S->in_use);
+  gs::dfree(S->step_dev, S->in_use);
+  if (S->h_add) cudaFreeHost(S->h_add);
+  if (S->add_done) cudaEventDestroy(S->add_done);
+  cudaStreamDestroy(S->stream);
+  delete S;
+  return GS_OK;
+}
+
+}  // extern "C"

@@ -72,7 +72,7 @@ class Arena:
 
     def struct(self):
         return _lib.GsParams(self.means4.data_ptr(), self.scale_opa.data_ptr(), self.quat.data_ptr(),
-                             self.sh.data_ptr(), self.n, self.sh_degree)
+                             self.sh.data_ptr(), self.n, self.sh_degree, self.n)
 
     def adam_groups(self, lr_means=1.6e-4, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3,
                     lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4) -> List[_lib.GsAdamGroup]:
@@ -282,7 +282,8 @@ def adam_step(params: Arena, grads: Arena, m: Arena, v: Arena, step: int, groups
               eps=1e-15, status: Optional[torch.Tensor] = None, pose: Optional[torch.Tensor] = None,
               dpose: Optional[torch.Tensor] = None, pose_m: Optional[torch.Tensor] = None,
               pose_v: Optional[torch.Tensor] = None, pose_lr: float = 1e-4, pose_step: int = 0,
-              step_dev: Optional[torch.Tensor] = None, pose_steps_dev: Optional[torch.Tensor] = None) -> None:
+              step_dev: Optional[torch.Tensor] = None, pose_steps_dev: Optional[torch.Tensor] = None,
+              skip_dev: Optional[torch.Tensor] = None) -> None:
     """Fused Adam over the whole arena (+ optional pose step).  With step_dev
     (a device int32 scalar) the step is read and incremented on the device, so
     the call can be captured in a CUDA graph."""
@@ -290,7 +291,7 @@ def adam_step(params: Arena, grads: Arena, m: Arena, v: Arena, step: int, groups
     garr = (_lib.GsAdamGroup * len(groups))(*groups)
     cfg = _lib.GsAdamCfg(garr, len(groups), beta1, beta2, eps, _p(status), _p(pose), _p(dpose), _p(pose_m),
                          _p(pose_v), pose.shape[0] if pose is not None else 0, pose_lr, int(pose_step),
-                         _p(step_dev), _p(pose_steps_dev))
+                         _p(step_dev), _p(pose_steps_dev), _p(skip_dev))
     _lib.check(L.gs_adam_step(_p(params.buf), _p(grads.buf), _p(m.buf), _p(v.buf), params.padded, C.byref(cfg),
                               int(step), _stream()), "gs_adam_step")
 

@@ -1,0 +1,117 @@
+"""Python handle of the streaming session (gs_session_* in include/gs.h):
+argument marshalling only; batching, admission, the device work and the
+latency accounting run in libgs."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+from .synth import Camera, Scene
+
+
+def default_config(max_gaussians: int, sh_degree: int = 3, max_batch_views: int = 8, max_width: int = 1920,
+                   max_height: int = 1080, max_inflight: int = 2, hbm_budget_gb: float = 80.0,
+                   pair_factor: float = 4.0, loss_kind: int = 0, bg=(0.0, 0.0, 0.0), znear: float = 0.2,
+                   lr_means=1.6e-4, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3, lr_sh_dc=2.5e-3,
+                   lr_sh_rest=1.25e-4) -> _lib.GsSessionConfig:
+    raster = _lib.GsRasterCfg(_lib.GS_TILE, _lib.GS_TILE, (C.c_float * 3)(*bg), float(znear), 1)
+    return _lib.GsSessionConfig(int(max_gaussians), int(sh_degree), int(max_batch_views), int(max_width),
+                                int(max_height), int(max_inflight), int(hbm_budget_gb * (1 << 30)),
+                                float(pair_factor), raster, lr_means, lr_scale, lr_opacity, lr_quat, lr_sh_dc,
+                                lr_sh_rest, 0.9, 0.999, 1e-15, int(loss_kind))
+
+
+def plan(cfg: _lib.GsSessionConfig) -> dict:
+    L = _lib.load()
+    out = _lib.GsSessionPlan()
+    st = L.gs_session_plan(C.byref(cfg), C.byref(out))
+    return {"status": st, "fixed_bytes": out.fixed_bytes, "context_bytes": out.context_bytes,
+            "initial_pair_capacity": out.initial_pair_capacity, "contexts": out.contexts}
+
+
+def now() -> float:
+    return _lib.load().gs_session_now()
+
+
+class Session:
+    def __init__(self, cfg: _lib.GsSessionConfig):
+        self.L = _lib.load()
+        self.cfg = cfg
+        self.nc = (cfg.sh_degree + 1) ** 2
+        h = C.c_void_p()
+        _lib.check(self.L.gs_session_create(C.byref(cfg), C.byref(h)), "gs_session_create")
+        self.h = h
+        self._keep = {}  # host buffers referenced by queued requests
+
+    def close(self):
+        if self.h:
+            _lib.check(self.L.gs_session_destroy(self.h), "gs_session_destroy")
+            self.h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add(self, sc: Scene) -> None:
+        arrs = [np.ascontiguousarray(a, np.float32) for a in
+                (sc.means, sc.log_scales, sc.quats, sc.opa_logits, sc.sh)]
+        ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs]
+        _lib.check(self.L.gs_session_add_gaussians(self.h, sc.n, *ptrs), "gs_session_add_gaussians")
+
+    def submit(self, kind: int, cam: Camera, target: Optional[np.ndarray] = None, want_image: bool = False,
+               arrival: float = 0.0) -> int:
+        req = _lib.GsRequest()
+        req.kind = kind
+        req.cam = _lib.GsCamera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+        req.pose = (C.c_float * 12)(*np.asarray(cam.pose12(), np.float32).tolist())
+        tgt = None
+        if target is not None:
+            tgt = np.ascontiguousarray(target, np.float32)
+            req.target = tgt.ctypes.data
+        img = None
+        if want_image:
+            img = np.zeros((3, cam.height, cam.width), np.float32)
+            req.image_out = img.ctypes.data
+        req.arrival_s = float(arrival)
+        rid = C.c_int64()
+        _lib.check(self.L.gs_session_submit(self.h, C.byref(req), C.byref(rid)), "gs_session_submit")
+        self._keep[rid.value] = img
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = 60000) -> Optional[np.ndarray]:
+        _lib.check(self.L.gs_session_wait(self.h, rid, timeout_ms), "gs_session_wait")
+        return self._keep.pop(rid, None)
+
+    def image(self, rid: int) -> Optional[np.ndarray]:
+        return self._keep.get(rid)
+
+    def drain(self, timeout_ms: int = 120000) -> None:
+        _lib.check(self.L.gs_session_drain(self.h, timeout_ms), "gs_session_drain")
+
+    def stats(self) -> dict:
+        s = _lib.GsStats()
+        _lib.check(self.L.gs_session_stats(self.h, C.byref(s)), "gs_session_stats")
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def params(self) -> dict:
+        st = self.stats()
+        n = st["gaussians"]
+        m4 = np.zeros((n, 4), np.float32)
+        so = np.zeros((n, 4), np.float32)
+        q = np.zeros((n, 4), np.float32)
+        sh = np.zeros((3 * self.nc, n), np.float32)
+        _lib.check(self.L.gs_session_read_params(self.h, m4.ctypes.data, so.ctypes.data, q.ctypes.data,
+                                                 sh.ctypes.data), "gs_session_read_params")
+        return {"means4": m4, "scale_opa": so, "quat": q, "sh": sh}
+
+    def save(self, path: str) -> None:
+        _lib.check(self.L.gs_session_save(self.h, path.encode()), "gs_session_save")
+
+    def load(self, path: str) -> None:
+        _lib.check(self.L.gs_session_load(self.h, path.encode()), "gs_session_load")

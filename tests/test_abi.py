@@ -54,17 +54,17 @@ def test_invalid_arguments_rejected_on_host(lib):
     st = lib.gs_project(None, None, cam, 1, C.byref(cfg), C.byref(sp), None)
     assert st == _lib.GS_ERR_INVALID
     assert "params" in _lib.last_error()
-    params = _lib.GsParams(None, None, None, None, 0, 5)
+    params = _lib.GsParams(None, None, None, None, 0, 5, 0)
     st = lib.gs_project(C.byref(params), None, cam, 1, C.byref(cfg), C.byref(sp), None)
     assert st == _lib.GS_ERR_INVALID and "sh_degree" in _lib.last_error()
     bad = _lib.GsRasterCfg(8, 8, (C.c_float * 3)(0, 0, 0), 0.2, 1)
-    params = _lib.GsParams(None, None, None, None, 0, 0)
+    params = _lib.GsParams(None, None, None, None, 0, 0, 0)
     st = lib.gs_project(C.byref(params), None, cam, 1, C.byref(bad), C.byref(sp), None)
     assert st == _lib.GS_ERR_INVALID and "tile" in _lib.last_error()
     st = lib.gs_project(C.byref(params), None, cam, 0, C.byref(cfg), C.byref(sp), None)
     assert st == _lib.GS_ERR_INVALID
     grp = (_lib.GsAdamGroup * 1)(_lib.GsAdamGroup(0, 4, (C.c_float * 4)(1, 1, 1, 1)))
-    acfg = _lib.GsAdamCfg(grp, 1, 0.9, 0.999, 1e-15, None, None, None, None, None, 0, 0.0, 0, None, None)
+    acfg = _lib.GsAdamCfg(grp, 1, 0.9, 0.999, 1e-15, None, None, None, None, None, 0, 0.0, 0, None, None, None)
     st = lib.gs_adam_step(None, None, None, None, 0, C.byref(acfg), 0, None)
     assert st == _lib.GS_ERR_INVALID and "step" in _lib.last_error()
     st = lib.gs_adam_step(None, None, None, None, 4, C.byref(acfg), 1, None)
@@ -74,3 +74,19 @@ def test_invalid_arguments_rejected_on_host(lib):
     sp = _lib.GsSplats(256, 256, 256, 256, 256, 256, 256, 10, 1)
     st = lib.gs_bin_sort(C.byref(sp), cam, 1, C.byref(cfg), C.byref(bins), C.c_void_p(256), 16, None)
     assert st == _lib.GS_ERR_OOM and "workspace" in _lib.last_error()
+
+
+def test_session_plan_admits_by_budget(lib):
+    from paper_2607_14481_b300 import session
+    small = session.default_config(1_000_000, max_batch_views=8, hbm_budget_gb=0.5)
+    p = session.plan(small)
+    assert p["status"] == _lib.GS_ERR_OOM and p["contexts"] == 0
+    assert "budget" in _lib.last_error()
+    mid = session.default_config(1_000_000, max_batch_views=8, max_inflight=4, hbm_budget_gb=80.0)
+    q = session.plan(mid)
+    assert q["status"] == _lib.GS_OK and 1 <= q["contexts"] <= 4
+    # the arenas: parameters, gradients and two moments of (12 + 48) floats per Gaussian
+    assert q["fixed_bytes"] >= 4 * 60 * 4 * 1_000_000
+    need = q["fixed_bytes"] + 2 * q["context_bytes"]
+    two = session.default_config(1_000_000, max_batch_views=8, max_inflight=4, hbm_budget_gb=need / (1 << 30))
+    assert session.plan(two)["contexts"] == 2

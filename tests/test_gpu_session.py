@@ -1,0 +1,181 @@
+"""The streaming session (continuous batching, admission by HBM budget):
+
+  * a render request gives the same image alone and in a batch mixed with
+    other requests of other resolutions (bit-identical), equal to the direct
+    rasterizer and within tolerance of the FP64 oracle;
+  * training requests give the same parameters alone and with render
+    requests mixed into their batches, and the same as the direct API's
+    training steps (bit-identical: render views never enter the update);
+  * save / load resumes bit-identically;
+  * a batch that overflows its pair capacity grows it and runs again.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_14481_b300 import _lib, raster, session, synth
+from gpu_util import IMG_TOL, ensure_built
+
+pytestmark = pytest.mark.gpu
+
+RENDER, TRAIN = _lib.GS_REQUEST_RENDER, _lib.GS_REQUEST_TRAIN
+
+
+def _scene(n=20000, seed=5, deg=3):
+    return synth.random_scene(n, seed, deg, (-2, -1, -2), (2, 1, 2), -3.5, 0.5)
+
+
+def _cams(k, seed=8):
+    g = np.random.default_rng(seed)
+    sizes = [(320, 180), (480, 270), (400, 224), (256, 144)]
+    out = []
+    for i in range(k):
+        a = 2 * np.pi * i / k
+        w, h = sizes[int(g.integers(0, len(sizes)))]
+        out.append(synth.look_at((5 * np.sin(a), -0.5, -5 * np.cos(a)), (0, 0, 0), 0.8 * w, 0.8 * w, w / 2, h / 2, w, h))
+    return out
+
+
+def _cfg(n, **kw):
+    kw.setdefault("max_batch_views", 8)
+    kw.setdefault("max_width", 480)
+    kw.setdefault("max_height", 272)
+    kw.setdefault("hbm_budget_gb", 8.0)
+    return session.default_config(n, **kw)
+
+
+def _direct_render(sc, cam):
+    dev = torch.device("cuda:0")
+    a = raster.Arena.from_scene(sc, dev)
+    r = raster.Rasterizer(sc.n, sc.sh_degree, [cam], device=dev)
+    img, _ = r.forward(a, raster.poses_tensor([cam], dev), r.new_image(), None)
+    torch.cuda.synchronize()
+    return r.split(img.cpu(), 3)[0].numpy()
+
+
+def test_render_alone_equals_in_mix(cuda_device):
+    ensure_built()
+    sc = _scene()
+    cams = _cams(8)
+    with session.Session(_cfg(sc.n)) as s:
+        s.add(sc)
+        rid = s.submit(RENDER, cams[0], want_image=True)
+        alone = s.wait(rid)
+        ids = [s.submit(RENDER, c, want_image=True) for c in cams[1:4]]
+        rid2 = s.submit(RENDER, cams[0], want_image=True)
+        ids += [s.submit(RENDER, c, want_image=True) for c in cams[4:]]
+        mixed = s.wait(rid2)
+        for i in ids:
+            s.wait(i)
+        st = s.stats()
+    assert st["completed"] == 9 and st["failed"] == 0
+    assert st["batches"] < 9  # requests were batched together
+    assert np.array_equal(alone, mixed)
+    assert np.array_equal(alone, _direct_render(sc, cams[0]))
+    ref = oracle.render(sc, cams[:1])
+    ok = (ref["flags"][0] & 1) == 0
+    assert np.abs(alone.astype(np.float64) - ref["image"][0])[:, ok].max() <= IMG_TOL
+
+
+def _targets(cams, seed=3):
+    g = np.random.default_rng(seed)
+    return [g.random((3, c.height, c.width)).astype(np.float32) for c in cams]
+
+
+def _direct_train(sc, cams, targets, lrs):
+    """The same training steps through the direct API (one view per step)."""
+    dev = torch.device("cuda:0")
+    a = raster.Arena.from_scene(sc, dev)
+    g, m, v = a.like(), a.like(), a.like()
+    groups = a.adam_groups(**lrs)
+    loss = raster.ImageLoss(dev)
+    for k, (c, t) in enumerate(zip(cams, targets)):
+        r = raster.Rasterizer(sc.n, sc.sh_degree, [c], device=dev)
+        img, _ = r.forward(a, raster.poses_tensor([c], dev), r.new_image(), None)
+        dimg = r.new_image()
+        loss(img, torch.from_numpy(t.reshape(-1)).to(dev), dimg, 0)
+        r.backward(a, raster.poses_tensor([c], dev), dimg, None, g, None)
+        raster.adam_step(a, g, m, v, k + 1, groups)
+    torch.cuda.synchronize()
+    return a
+
+
+def test_train_alone_equals_with_renders_mixed_and_direct(cuda_device):
+    ensure_built()
+    sc = _scene(n=15000, seed=6)
+    cams = _cams(4, seed=9)
+    targets = _targets(cams)
+    lrs = dict(lr_means=1e-3, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4)
+    extra = _cams(6, seed=10)
+    results = []
+    for mixed in (False, True):
+        with session.Session(_cfg(sc.n + 1000, **lrs)) as s:
+            s.add(sc)
+            for c, t in zip(cams, targets):
+                rid = s.submit(TRAIN, c, target=t)
+                others = [s.submit(RENDER, e, want_image=True) for e in extra[:3]] if mixed else []
+                s.wait(rid)
+                for o in others:
+                    s.wait(o)
+            st = s.stats()
+            assert st["iterations"] == len(cams) and st["failed"] == 0
+            results.append(s.params())
+    for k in results[0]:
+        assert np.array_equal(results[0][k], results[1][k]), k
+    d = _direct_train(sc, cams, targets, lrs)
+    nat = d.buf.cpu().numpy()
+    n = sc.n
+    assert np.array_equal(results[0]["means4"], nat[0:4 * n].reshape(n, 4))
+    assert np.array_equal(results[0]["scale_opa"], nat[4 * n:8 * n].reshape(n, 4))
+    assert np.array_equal(results[0]["quat"], nat[8 * n:12 * n].reshape(n, 4))
+    assert np.array_equal(results[0]["sh"], nat[12 * n:12 * n + 48 * n].reshape(48, n))
+
+
+def test_save_load_resumes_bit_identically(cuda_device, tmp_path):
+    ensure_built()
+    sc = _scene(n=8000, seed=7, deg=1)
+    cams = _cams(4, seed=11)
+    targets = _targets(cams, seed=4)
+    path = str(tmp_path / "ckpt.bin")
+    with session.Session(_cfg(sc.n)) as s:
+        s.add(sc)
+        for c, t in zip(cams[:2], targets[:2]):
+            s.wait(s.submit(TRAIN, c, target=t))
+        s.save(path)
+        for c, t in zip(cams[2:], targets[2:]):
+            s.wait(s.submit(TRAIN, c, target=t))
+        full = s.params()
+    with session.Session(_cfg(sc.n)) as s2:
+        s2.load(path)
+        for c, t in zip(cams[2:], targets[2:]):
+            s2.wait(s2.submit(TRAIN, c, target=t))
+        resumed = s2.params()
+    for k in full:
+        assert np.array_equal(full[k], resumed[k]), k
+
+
+def test_pair_capacity_overflow_retries(cuda_device):
+    ensure_built()
+    sc = _scene(n=20000, seed=12)
+    cams = _cams(2, seed=13)
+    # initial pair capacity 4096 (the floor) is far below this scene's pairs
+    with session.Session(_cfg(sc.n, pair_factor=1e-6)) as s:
+        s.add(sc)
+        rid = s.submit(RENDER, cams[0], want_image=True)
+        img = s.wait(rid)
+        st = s.stats()
+    assert st["completed"] == 1 and st["failed"] == 0
+    assert st["batches"] >= 2  # the first attempt overflowed and was issued again
+    assert np.array_equal(img, _direct_render(sc, cams[0]))
+
+
+def test_empty_scene_renders_background(cuda_device):
+    ensure_built()
+    cam = _cams(1)[0]
+    with session.Session(_cfg(1000, bg=(0.25, 0.5, 0.75))) as s:
+        img = s.wait(s.submit(RENDER, cam, want_image=True))
+    for ch, b in enumerate((0.25, 0.5, 0.75)):
+        assert np.all(img[ch] == np.float32(b))
