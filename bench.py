@@ -224,7 +224,7 @@ class Workload:
         ev[3].record()
         st.loss(st.img, st.targets, st.dimg, st.kind)
         ev[4].record()
-        r.backward_pixels(st.dimg, None)
+        r.backward_pixels(st.dimg, None, st.img)
         ev[5].record()
         r.backward_gaussians(st.arena, st.poses, st.grads, st.dpose)
         ev[6].record()
@@ -388,8 +388,10 @@ def load_peaks():
 # the splat test (offsets 6, box test 2, quadratic form 7, power test 1,
 # exp 2, opacity product 1, clamp 1, threshold 1) = 21; a forward blend
 # (1 - alpha, transmittance, stop test, weight, 3 colour FMAs) = 7; a backward
-# blend (reciprocal, transmittance, weights, alpha gradient, suffix colour,
-# opacity, quadratic-form and mean gradients) = 50 + 4 replay + 9 reduction adds.
+# blend (reciprocal, weights, remaining colour, alpha gradient, opacity,
+# quadratic-form and mean gradients) = 50 + 4 transmittance / stop + 9
+# reduction adds.  The backward's algorithmic work tests each pair once (the
+# single front-to-back pass does exactly that).
 OPS_TEST, OPS_FWD_BLEND, OPS_BWD_BLEND = 21, 7, 63
 
 
@@ -410,7 +412,7 @@ def roofline(wl, stage_ms, work, peaks):
         "adam": ("hbm", 28.0 * wl.arena.padded),
         "loss": ("hbm", 3 * 4 * 3.0 * wl.pixels_per_iter),
         "render_fwd": ("alu", OPS_TEST * work["tested"] + OPS_FWD_BLEND * work["blended"]),
-        "render_bwd_pixels": ("alu", 2 * OPS_TEST * work["tested"] + OPS_BWD_BLEND * work["blended"]),
+        "render_bwd_pixels": ("alu", OPS_TEST * work["tested"] + OPS_BWD_BLEND * work["blended"]),
     }
     table = {}
     for k, (bound, amount) in per.items():

@@ -262,10 +262,17 @@ GS_API gs_status gs_render_fwd(const gs_splats* splats, const gs_bins* bins, con
 GS_API size_t gs_render_bwd_workspace(int64_t n, int32_t views, int64_t capacity);
 
 /* Backward of gs_project + gs_render_fwd for the loss gradients dL_dimage
- * (layout of image) and optional dL_dalpha (layout of alpha).  Per pixel the
- * forward pass is replayed to recover the final transmittance and the last
- * blended splat (no per-pixel state is stored), then splats are walked back to
- * front recovering T_i = T_{i+1} / (1 - alpha_i).  Per (tile, splat) the
+ * (layout of image) and optional dL_dalpha (layout of alpha).  image
+ * (optional, device, layout of gs_render_fwd's image) is the forward's output
+ * for these very splats and tile lists.  When image is given and dL_dalpha is
+ * NULL, one front-to-back pass per tile repeats the forward's decisions and
+ * takes the colour behind each splat as image minus the colour composited so
+ * far (dC/dalpha_i of the front-to-back composite needs only that and T_i).
+ * Otherwise the forward
+ * pass is replayed to recover the final transmittance and the last blended
+ * splat (no per-pixel state is stored), then splats are walked back to front
+ * recovering T_i = T_{i+1} / (1 - alpha_i).  The two forms agree to rounding
+ * (they take the same decisions).  Per (tile, splat) the
  * gradients of m, conic, opacity and rgb are reduced over the tile's pixels by
  * warp shuffles and shared memory (no global atomics) and stored per pair;
  * a per-Gaussian pass sums its pairs in a fixed order and applies the chain
@@ -275,8 +282,8 @@ GS_API size_t gs_render_bwd_workspace(int64_t n, int32_t views, int64_t capacity
 GS_API gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const gs_camera* cams,
                         int32_t views, const gs_splats* splats, const gs_bins* bins,
                         const gs_raster_cfg* cfg, const float* dL_dimage, const float* dL_dalpha,
-                        gs_grads* grads, float* dL_dpose, void* ws, size_t ws_bytes,
-                        gs_stream stream);
+                        const float* image, gs_grads* grads, float* dL_dpose, void* ws,
+                        size_t ws_bytes, gs_stream stream);
 
 /* The two halves of gs_render_bwd, for callers that time or overlap them:
  * gs_render_bwd_pixels runs the per-tile pass and leaves the per-pair
@@ -285,8 +292,8 @@ GS_API gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, 
  * gs_render_bwd. */
 GS_API gs_status gs_render_bwd_pixels(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
                                       int32_t views, const gs_raster_cfg* cfg, const float* dL_dimage,
-                                      const float* dL_dalpha, int64_t n, void* ws, size_t ws_bytes,
-                                      gs_stream stream);
+                                      const float* dL_dalpha, const float* image, int64_t n, void* ws,
+                                      size_t ws_bytes, gs_stream stream);
 GS_API gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_dev,
                                          const gs_camera* cams, int32_t views, const gs_splats* splats,
                                          const gs_bins* bins, const gs_raster_cfg* cfg, gs_grads* grads,

@@ -135,9 +135,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_render_bwd_workspace.argtypes = [i64, i32, i64]
     L.gs_render_bwd_workspace.restype = sz
     L.gs_render_bwd.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsSplats), P(GsBins),
-                                P(GsRasterCfg), vp, vp, P(GsGrads), vp, vp, sz, vp]
-    L.gs_render_bwd_pixels.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp, i64,
-                                       vp, sz, vp]
+                                P(GsRasterCfg), vp, vp, vp, P(GsGrads), vp, vp, sz, vp]
+    L.gs_render_bwd_pixels.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp, vp,
+                                       i64, vp, sz, vp]
     L.gs_render_bwd_gaussians.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsSplats), P(GsBins),
                                           P(GsRasterCfg), P(GsGrads), vp, vp, sz, vp]
     L.gs_adam_step.argtypes = [vp, vp, vp, vp, i64, P(GsAdamCfg), i32, vp]

@@ -30,6 +30,7 @@ class _RenderFn(torch.autograd.Function):
         rast.forward(arena, poses, image, alpha, check=True)
         ctx.arena, ctx.rast, ctx.poses = arena, rast, poses
         ctx.want_alpha = want_alpha
+        ctx.save_for_backward(image)  # selects the single front-to-back backward
         if want_alpha:
             return image, alpha
         return image, torch.empty(0, device=image.device)
@@ -40,7 +41,8 @@ class _RenderFn(torch.autograd.Function):
         grads = arena.like()
         dpose = torch.zeros((rast.views, 6), dtype=torch.float32, device=dimage.device)
         da = dalpha.contiguous() if (ctx.want_alpha and dalpha is not None) else None
-        rast.backward(arena, poses, dimage.contiguous(), da, grads, dpose)
+        (image,) = ctx.saved_tensors
+        rast.backward(arena, poses, dimage.contiguous(), da, grads, dpose, image)
         return grads.buf, dpose, None, None, None, None
 
 

@@ -256,8 +256,8 @@ size_t gs_render_bwd_workspace(int64_t n, int32_t views, int64_t capacity) {
 
 gs_status gs_render_bwd_pixels(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
                                int32_t views, const gs_raster_cfg* cfg, const float* dL_dimage,
-                               const float* dL_dalpha, int64_t n, void* ws, size_t ws_bytes,
-                               gs_stream stream) {
+                               const float* dL_dalpha, const float* image, int64_t n, void* ws,
+                               size_t ws_bytes, gs_stream stream) {
   gs_status st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
   ViewTable vt;
@@ -271,7 +271,8 @@ gs_status gs_render_bwd_pixels(const gs_splats* splats, const gs_bins* bins, con
   if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
   float *partials, *pose_partials, *drgb;
   bwd_layout(n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &drgb);
-  return launch_render_bwd(*splats, *bins, vt, *cfg, dL_dimage, dL_dalpha, partials, (cudaStream_t)stream);
+  return launch_render_bwd(*splats, *bins, vt, *cfg, dL_dimage, dL_dalpha, image, partials,
+                           (cudaStream_t)stream);
 }
 
 gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_dev, const gs_camera* cams,
@@ -306,8 +307,8 @@ gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_de
 gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const gs_camera* cams,
                         int32_t views, const gs_splats* splats, const gs_bins* bins,
                         const gs_raster_cfg* cfg, const float* dL_dimage, const float* dL_dalpha,
-                        gs_grads* grads, float* dL_dpose, void* ws, size_t ws_bytes,
-                        gs_stream stream) {
+                        const float* image, gs_grads* grads, float* dL_dpose, void* ws,
+                        size_t ws_bytes, gs_stream stream) {
   gs_status st;
   if ((st = check_params(params)) != GS_OK) return st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
@@ -331,7 +332,7 @@ gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const g
   float *partials, *pose_partials, *drgb;
   bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &drgb);
   cudaStream_t s = (cudaStream_t)stream;
-  st = launch_render_bwd(*splats, *bins, vt, *cfg, dL_dimage, dL_dalpha, partials, s);
+  st = launch_render_bwd(*splats, *bins, vt, *cfg, dL_dimage, dL_dalpha, image, partials, s);
   if (st != GS_OK) return st;
   return launch_project_bwd(*params, poses_dev, vt, *cfg, *splats, *bins, partials, *grads, pose_partials,
                             dL_dpose, drgb, s);

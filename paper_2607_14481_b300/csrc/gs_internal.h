@@ -45,7 +45,7 @@ gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const Vi
                               unsigned long long* stats, cudaStream_t s);
 gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                             const gs_raster_cfg& cfg, const float* dimage, const float* dalpha,
-                            float* partials, cudaStream_t s);
+                            const float* image, float* partials, cudaStream_t s);
 gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewTable& vt,
                              const gs_raster_cfg& cfg, const gs_splats& sp, const gs_bins& bins,
                              const float* partials, const gs_grads& g, float* pose_partials, float* dpose,

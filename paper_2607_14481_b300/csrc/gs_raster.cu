@@ -232,8 +232,56 @@ struct BwdArgs {
   float bg[3];
   const float* dimage;
   const float* dalpha;
+  const float* image;  // the forward's output (single-pass variant)
   float* partials;  // [K][12]: dmx, dmy, dA, dB | dC, dopacity, dr, dg | db, 0, 0, 0
 };
+
+// Slot of the (tile, Gaussian) pair of list position j, 0xffffffff for an
+// out-of-range id.
+__device__ __forceinline__ uint32_t pair_slot(const BwdArgs& a, int64_t vbase, uint32_t j,
+                                              const TileCoords& tc) {
+  const uint32_t g = a.vals[j];
+  return g < a.n ? a.pair_off[vbase + g] + rect_index(a.rect[vbase + g], tc.tx, tc.ty) : 0xffffffffu;
+}
+
+// Stores one pair's gradients: the sum over the warps that touched it, in
+// warp order (deterministic), or zeros when none did.
+__device__ __forceinline__ void store_pair(const BwdArgs& a, uint32_t pidx,
+                                           const float (&red)[kWarps][kPartialValues],
+                                           const uint8_t (&hit)[kWarps]) {
+  if ((int64_t)pidx >= a.cap) {
+    if (pidx != 0xffffffffu) atomicOr(&a.counts[2], 2u);
+    return;
+  }
+  float sum[kPartialValues];
+#pragma unroll
+  for (int c = 0; c < kPartialValues; ++c) {
+    float acc = 0.f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w)
+      if (hit[w]) acc += red[w][c];
+    sum[c] = acc;
+  }
+  float4* dst = reinterpret_cast<float4*>(a.partials + (int64_t)pidx * kPartialStride);
+  dst[0] = make_float4(sum[0], sum[1], sum[2], sum[3]);
+  dst[1] = make_float4(sum[4], sum[5], sum[6], sum[7]);
+  dst[2] = make_float4(sum[8], 0.f, 0.f, 0.f);
+}
+
+// Zero gradients for the pair of list position j (a splat no pixel reached).
+__device__ __forceinline__ void zero_pair(const BwdArgs& a, int64_t vbase, uint32_t j, const TileCoords& tc) {
+  const uint32_t g = a.vals[j];
+  if (g >= a.n) return;
+  const int64_t gi = vbase + g;
+  const uint32_t pidx = a.pair_off[gi] + rect_index(a.rect[gi], tc.tx, tc.ty);
+  if ((int64_t)pidx >= a.cap) {
+    atomicOr(&a.counts[2], 2u);
+    return;
+  }
+  float4* dst = reinterpret_cast<float4*>(a.partials + (int64_t)pidx * kPartialStride);
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  dst[0] = z; dst[1] = z; dst[2] = z;
+}
 
 // Warp sum of 9 values per lane with 14 shuffles instead of 45: values 0-7
 // are reduced by halving exchanges (each step a lane keeps half of what it
@@ -271,6 +319,21 @@ __device__ __forceinline__ void warp_sum9(const float (&d)[kPartialValues], int 
   t8 = v;
 }
 
+// Chain rule from dL/dalpha to the splat's mean, conic and opacity (none
+// while alpha is clamped at its maximum).
+__device__ __forceinline__ void alpha_grad(const Eval& e, const float4 co, float dal,
+                                           float (&d)[kPartialValues]) {
+  if (e.raw <= kAlphaMax) {
+    d[5] += dal * e.ex;                  // d alpha / d opacity = exp(power)
+    const float dp = dal * e.alpha;      // d alpha / d power = alpha
+    d[2] -= 0.5f * e.dx * e.dx * dp;
+    d[3] -= e.dx * e.dy * dp;
+    d[4] -= 0.5f * e.dy * e.dy * dp;
+    d[0] -= (co.x * e.dx + co.y * e.dy) * dp;
+    d[1] -= (co.z * e.dy + co.y * e.dx) * dp;
+  }
+}
+
 // Gradient contribution of one blended splat at one pixel, walking back to
 // front: T is the transmittance behind the splat on entry and in front of it
 // on return; acc is the colour behind it (background included).
@@ -287,16 +350,25 @@ __device__ __forceinline__ void splat_grad(const Eval& e, const float4 co, const
   const float dal = g0 * (col.x * Tb - acc0 * rom) + g1 * (col.y * Tb - acc1 * rom) +
                     g2 * (col.z * Tb - acc2 * rom) + ga * Tfinal * rom;
   acc0 += col.x * w; acc1 += col.y * w; acc2 += col.z * w;
-  if (e.raw <= kAlphaMax) {
-    d[5] += dal * e.ex;                  // d alpha / d opacity = exp(power)
-    const float dp = dal * e.alpha;      // d alpha / d power = alpha
-    d[2] -= 0.5f * e.dx * e.dx * dp;
-    d[3] -= e.dx * e.dy * dp;
-    d[4] -= 0.5f * e.dy * e.dy * dp;
-    d[0] -= (co.x * e.dx + co.y * e.dy) * dp;
-    d[1] -= (co.z * e.dy + co.y * e.dx) * dp;
-  }
+  alpha_grad(e, co, dal, d);
   T = Tb;
+}
+
+// Single-pass form, walking front to back: T is the transmittance in front
+// of the splat (unchanged here); rem is the colour still to come behind it,
+// background included, as the forward image minus the colour composited so
+// far; on return it no longer holds this splat's share.
+__device__ __forceinline__ void splat_grad_front(const Eval& e, const float4 co, const float4 col,
+                                                 float g0, float g1, float g2, float T, float& rem0,
+                                                 float& rem1, float& rem2, float (&d)[kPartialValues]) {
+  const float w = e.alpha * T;
+  d[6] += g0 * w; d[7] += g1 * w; d[8] += g2 * w;
+  rem0 -= col.x * w; rem1 -= col.y * w; rem2 -= col.z * w;
+  // colour behind the splat seen through it: T S = rem / (1 - alpha)
+  const float rom = __fdividef(1.f, 1.f - e.alpha);
+  const float dal = g0 * (col.x * T - rem0 * rom) + g1 * (col.y * T - rem1 * rom) +
+                    g2 * (col.z * T - rem2 * rom);
+  alpha_grad(e, co, dal, d);
 }
 
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const ViewTable vt) {
@@ -367,19 +439,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
   float a10 = Tf1 * a.bg[0], a11 = Tf1 * a.bg[1], a12 = Tf1 * a.bg[2];
 
   // pairs behind every pixel's last blended splat receive zero gradient
-  for (uint32_t p = (uint32_t)(maxlast + 1) + threadIdx.x; p < rg.y; p += kThreads) {
-    const uint32_t g = a.vals[p];
-    if (g >= a.n) continue;
-    const int64_t gi = vbase + g;
-    const uint32_t pidx = a.pair_off[gi] + rect_index(a.rect[gi], tc.tx, tc.ty);
-    if ((int64_t)pidx >= a.cap) {
-      atomicOr(&a.counts[2], 2u);
-      continue;
-    }
-    float4* dst = reinterpret_cast<float4*>(a.partials + (int64_t)pidx * kPartialStride);
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    dst[0] = z; dst[1] = z; dst[2] = z;
-  }
+  for (uint32_t p = (uint32_t)(maxlast + 1) + threadIdx.x; p < rg.y; p += kThreads) zero_pair(a, vbase, p, tc);
 
   // ---- 2. back to front over [rg.x, maxlast]
   const int mylast = max(last0, last1);
@@ -391,9 +451,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
       const uint32_t j = (uint32_t)(bstart + threadIdx.x);
       stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, s_xy, s_co, s_rgb, s_rows,
                   nullptr);
-      const uint32_t g = a.vals[j];
-      s_pidx[threadIdx.x] =
-          g < a.n ? a.pair_off[vbase + g] + rect_index(a.rect[vbase + g], tc.tx, tc.ty) : 0xffffffffu;
+      s_pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
     }
@@ -430,27 +488,106 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
       }
     }
     __syncthreads();
+    if (threadIdx.x < cnt) store_pair(a, s_pidx[threadIdx.x], s_red[threadIdx.x], s_hit[threadIdx.x]);
+  }
+}
+
+// Single front-to-back backward, for losses on the image alone: the colour
+// behind splat i is the forward's output minus what has been composited up to
+// and including i, so one traversal in the forward's order, with the forward's
+// own decisions (same splat test, same transmittance products, same stop),
+// yields every gradient without a replay and without recovering T by division.
+__global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, const ViewTable vt) {
+  __shared__ float4 s_xy[kBatch], s_co[kBatch], s_rgb[kBatch];
+  __shared__ float2 s_rows[kBatch];
+  __shared__ uint32_t s_pidx[kBatch];
+  __shared__ float s_red[kBatch][kWarps][kPartialValues];
+  __shared__ uint8_t s_hit[kBatch][kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const TileCoords tc = tile_coords(vt, blockIdx.x);
+  const ViewInfo& vi = vt.v[tc.v];
+  const float pxf = (float)tc.px, py0f = (float)tc.py0, py1f = py0f + 1.f;
+  const float wrow_lo = (float)(tc.ty * kTile + warp * kRowsPerWarp);
+  const float wrow_hi = wrow_lo + (float)(kRowsPerWarp - 1);
+  const uint2 rg = a.ranges[blockIdx.x];
+  const int64_t vbase = (int64_t)tc.v * a.n;
+
+  const int64_t np = (int64_t)vi.W * vi.H;
+  const float* gimg = a.dimage + 3 * vi.pix_base;
+  const float* cimg = a.image + 3 * vi.pix_base;
+  float g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f;
+  float r00 = 0.f, r01 = 0.f, r02 = 0.f, r10 = 0.f, r11 = 0.f, r12 = 0.f;
+  if (tc.in0) {
+    const int64_t pix = (int64_t)tc.py0 * vi.W + tc.px;
+    g00 = gimg[pix]; g01 = gimg[np + pix]; g02 = gimg[2 * np + pix];
+    r00 = cimg[pix]; r01 = cimg[np + pix]; r02 = cimg[2 * np + pix];
+  }
+  if (tc.in1) {
+    const int64_t pix = (int64_t)(tc.py0 + 1) * vi.W + tc.px;
+    g10 = gimg[pix]; g11 = gimg[np + pix]; g12 = gimg[2 * np + pix];
+    r10 = cimg[pix]; r11 = cimg[np + pix]; r12 = cimg[2 * np + pix];
+  }
+  float T0 = 1.f, T1 = 1.f;
+  bool d0 = !tc.in0, d1 = !tc.in1;
+  uint32_t start = rg.x;
+  for (; start < rg.y; start += kBatch) {
+    if (__syncthreads_count(d0 && d1) == kThreads) break;
+    const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     if (threadIdx.x < cnt) {
-      const uint32_t pidx = s_pidx[threadIdx.x];
-      if ((int64_t)pidx < a.cap) {
-        float sum[kPartialValues];
+      const uint32_t j = start + threadIdx.x;
+      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, s_xy, s_co, s_rgb, s_rows,
+                  nullptr);
+      s_pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
 #pragma unroll
-        for (int c = 0; c < kPartialValues; ++c) {
-          float acc = 0.f;
+      for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
+    }
+    __syncthreads();
+    for (int k = 0; k < cnt; ++k) {
+      if (__all_sync(0xffffffffu, d0 && d1)) break;  // the warp's pixels are done
+      const float2 rows = s_rows[k];
+      if (wrow_lo > rows.y || wrow_hi < rows.x) continue;  // warp-uniform: no contribution
+      float d[kPartialValues];
 #pragma unroll
-          for (int w2 = 0; w2 < kWarps; ++w2)
-            if (s_hit[threadIdx.x][w2]) acc += s_red[threadIdx.x][w2][c];
-          sum[c] = acc;
+      for (int c = 0; c < kPartialValues; ++c) d[c] = 0.f;
+      bool contrib = false;
+      const float4 m = s_xy[k], co = s_co[k], col = s_rgb[k];
+      Eval e;
+      if (!d0 && splat_alpha(m, co, col.w, pxf, py0f, e)) {
+        const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
+        if (Tn < kTransMin) {
+          d0 = true;
+        } else {
+          splat_grad_front(e, co, col, g00, g01, g02, T0, r00, r01, r02, d);
+          T0 = Tn;
+          contrib = true;
         }
-        float4* dst = reinterpret_cast<float4*>(a.partials + (int64_t)pidx * kPartialStride);
-        dst[0] = make_float4(sum[0], sum[1], sum[2], sum[3]);
-        dst[1] = make_float4(sum[4], sum[5], sum[6], sum[7]);
-        dst[2] = make_float4(sum[8], 0.f, 0.f, 0.f);
-      } else if (pidx != 0xffffffffu) {
-        atomicOr(&a.counts[2], 2u);
+      }
+      if (!d1 && splat_alpha(m, co, col.w, pxf, py1f, e)) {
+        const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
+        if (Tn < kTransMin) {
+          d1 = true;
+        } else {
+          splat_grad_front(e, co, col, g10, g11, g12, T1, r10, r11, r12, d);
+          T1 = Tn;
+          contrib = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, contrib)) {
+        float s8, t8;
+        int idx;
+        warp_sum9(d, lane, s8, idx, t8);
+        if ((lane & 3) == 0) s_red[k][warp][idx] = s8;
+        if (lane == 0) {
+          s_red[k][warp][8] = t8;
+          s_hit[k][warp] = 1;
+        }
       }
     }
+    __syncthreads();
+    if (threadIdx.x < cnt) store_pair(a, s_pidx[threadIdx.x], s_red[threadIdx.x], s_hit[threadIdx.x]);
   }
+  // pairs past the batch where every pixel of the tile had stopped
+  for (uint32_t p = start + threadIdx.x; p < rg.y; p += kThreads) zero_pair(a, vbase, p, tc);
 }
 
 }  // namespace
@@ -494,7 +631,7 @@ gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const Vi
 
 gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                             const gs_raster_cfg& cfg, const float* dimage, const float* dalpha,
-                            float* partials, cudaStream_t s) {
+                            const float* image, float* partials, cudaStream_t s) {
   BwdArgs a;
   a.xy = reinterpret_cast<const float4*>(sp.xy);
   a.conic = reinterpret_cast<const float4*>(sp.conic);
@@ -509,8 +646,13 @@ gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const View
   for (int c = 0; c < 3; ++c) a.bg[c] = cfg.bg[c];
   a.dimage = dimage;
   a.dalpha = dalpha;
+  a.image = image;
   a.partials = partials;
   if (vt.total_tiles == 0) return GS_OK;
+  if (image && !dalpha) {
+    k_render_bwd_front<<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
+    return check_launch("k_render_bwd_front");
+  }
   k_render_bwd<<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
   return check_launch("k_render_bwd");
 }

@@ -341,7 +341,7 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
       return st;
     float *partials, *pose_partials, *drgb;
     render_bwd_ws_layout(n, (int32_t)T.size(), c.pair_cap, c.ws_bwd.p, &partials, &pose_partials, &drgb);
-    if ((st = launch_render_bwd(sp, b, vt, cf.raster, dimg, nullptr, partials, s)) != GS_OK) return st;
+    if ((st = launch_render_bwd(sp, b, vt, cf.raster, dimg, nullptr, timg, partials, s)) != GS_OK) return st;
     gs_params G = params_of(S, 1);
     gs_grads g{const_cast<float*>(G.means4), const_cast<float*>(G.scale_opa), const_cast<float*>(G.quat),
                const_cast<float*>(G.sh), G.n, G.sh_degree, G.sh_stride};
@@ -434,13 +434,14 @@ void completer_main(gs_session* S) {
       if (steady_now() - t0 > kWaitTimeout) break;
       std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
-    // copy rendered images out before taking the lock
-    bool retry = false, bad_index = false;
+    // The render and train parts of a batch have their own tile lists and
+    // status: an overflowing part is issued again on its own (a train part
+    // that overflowed skipped its update on the device), the other completes.
+    uint32_t sr = 0, strn = 0;
     if (e == cudaSuccess) {
-      const uint32_t sr = c->h_counts[2], strn = c->has_train ? c->h_counts[6] : 0u;
-      retry = ((sr | strn) & 1u) != 0;
-      bad_index = ((sr | strn) & 2u) != 0;
-      if (!retry && !bad_index) {
+      sr = c->h_counts[2];
+      strn = c->has_train ? c->h_counts[6] : 0u;
+      if (!(sr & 3u)) {  // copy rendered images out before taking the lock
         int64_t off = 0;
         for (auto& r : c->reqs) {
           if (r->kind != GS_REQUEST_RENDER) continue;
@@ -450,6 +451,7 @@ void completer_main(gs_session* S) {
         }
       }
     }
+    const bool retry = ((sr | strn) & 1u) != 0, bad_index = ((sr | strn) & 2u) != 0;
     lk.lock();
     S->inflight.pop_front();
     if (e == cudaErrorNotReady) {
@@ -460,7 +462,11 @@ void completer_main(gs_session* S) {
       S->fatal = GS_ERR_CUDA;
       for (auto& r : c->reqs) finish_req(S, r.get(), GS_ERR_CUDA);
     } else if (bad_index) {
-      for (auto& r : c->reqs) finish_req(S, r.get(), GS_ERR_CUDA);
+      for (auto& r : c->reqs) {
+        const uint32_t part = r->kind == GS_REQUEST_TRAIN ? strn : sr;
+        finish_req(S, r.get(), (part & 2u) ? gs::fail(GS_ERR_CUDA, "session: internal index error") : GS_OK);
+      }
+      if (c->has_train && !(strn & 3u)) S->iterations++;
     } else if (retry) {
       const uint32_t K = std::max(c->h_counts[1], c->has_train ? c->h_counts[5] : 0u);
       const int64_t want = (int64_t)(1.25 * (double)K) + 4096;
@@ -475,12 +481,16 @@ void completer_main(gs_session* S) {
         free_pair_buffers(S, *c);
         st = alloc_pair_buffers(S, *c, want);
       }
-      if (st != GS_OK) {
-        for (auto& r : c->reqs) finish_req(S, r.get(), st);
-      } else {
-        // issue the same requests again, ahead of everything queued
-        for (auto it = c->reqs.rbegin(); it != c->reqs.rend(); ++it) {
-          (*it)->state = 0;
+      if (c->has_train && !(strn & 1u)) S->iterations++;
+      for (auto it = c->reqs.rbegin(); it != c->reqs.rend(); ++it) {
+        Req* r = it->get();
+        const bool over = ((r->kind == GS_REQUEST_TRAIN ? strn : sr) & 1u) != 0;
+        if (!over) {
+          finish_req(S, r, GS_OK);
+        } else if (st != GS_OK) {
+          finish_req(S, r, st);
+        } else {
+          r->state = 0;  // issued again, ahead of everything queued
           S->queue.push_front(*it);
         }
       }
@@ -772,7 +782,8 @@ gs_status gs_session_save(gs_session* S, const char* path) {
   const int64_t n = S->n_active, cap = S->capacity;
   const int nc = S->nc;
   int32_t step = 0;
-  cudaMemcpy(&step, S->step_dev.p, 4, cudaMemcpyDeviceToHost);
+  cudaMemcpyAsync(&step, S->step_dev.p, 4, cudaMemcpyDeviceToHost, S->stream);
+  if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
   FILE* f = std::fopen(path, "wb");
   if (!f) return gs::fail(GS_ERR_INVALID, "cannot open %s", path);
   const int64_t hdr[4] = {0x3153534553534723ll, (int64_t)S->cfg.sh_degree, n, (int64_t)step};
@@ -780,11 +791,17 @@ gs_status gs_session_save(gs_session* S, const char* path) {
   std::vector<float> buf((size_t)(12 + 3 * nc) * std::max<int64_t>(n, 1));
   for (int a : {0, 2, 3}) {
     const float* A = gs::arena_ptr(S, a);
-    cudaMemcpy(buf.data(), A, 16 * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy(buf.data() + 4 * n, A + 4 * cap, 16 * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy(buf.data() + 8 * n, A + 8 * cap, 16 * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy2D(buf.data() + 12 * n, 4 * n, A + 12 * cap, 4 * cap, 4 * n, 3 * nc, cudaMemcpyDeviceToHost);
+    cudaStream_t s = S->stream;
+    cudaMemcpyAsync(buf.data(), A, 16 * n, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(buf.data() + 4 * n, A + 4 * cap, 16 * n, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(buf.data() + 8 * n, A + 8 * cap, 16 * n, cudaMemcpyDeviceToHost, s);
+    cudaMemcpy2DAsync(buf.data() + 12 * n, 4 * n, A + 12 * cap, 4 * cap, 4 * n, 3 * nc, cudaMemcpyDeviceToHost, s);
+    if ((st = gs::sync_stream(S, 30.0)) != GS_OK) break;
     ok = ok && std::fwrite(buf.data(), sizeof(float), (size_t)(12 + 3 * nc) * n, f) == (size_t)(12 + 3 * nc) * n;
+  }
+  if (st != GS_OK) {
+    std::fclose(f);
+    return st;
   }
   ok = (std::fclose(f) == 0) && ok;
   if ((st = gs::check_launch("session save")) != GS_OK) return st;
@@ -812,16 +829,23 @@ gs_status gs_session_load(gs_session* S, const char* path) {
   for (int a : {0, 2, 3}) {
     ok = ok && std::fread(buf.data(), sizeof(float), (size_t)(12 + 3 * nc) * n, f) == (size_t)(12 + 3 * nc) * n;
     if (!ok) break;
+    // on the session stream, then waited for: a copy from pageable memory may
+    // return before its data lands, and the session stream does not wait for
+    // the legacy default stream
     float* A = gs::arena_ptr(S, a);
-    cudaMemcpy(A, buf.data(), 16 * n, cudaMemcpyHostToDevice);
-    cudaMemcpy(A + 4 * cap, buf.data() + 4 * n, 16 * n, cudaMemcpyHostToDevice);
-    cudaMemcpy(A + 8 * cap, buf.data() + 8 * n, 16 * n, cudaMemcpyHostToDevice);
-    cudaMemcpy2D(A + 12 * cap, 4 * cap, buf.data() + 12 * n, 4 * n, 4 * n, 3 * nc, cudaMemcpyHostToDevice);
+    cudaStream_t s = S->stream;
+    cudaMemcpyAsync(A, buf.data(), 16 * n, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(A + 4 * cap, buf.data() + 4 * n, 16 * n, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(A + 8 * cap, buf.data() + 8 * n, 16 * n, cudaMemcpyHostToDevice, s);
+    cudaMemcpy2DAsync(A + 12 * cap, 4 * cap, buf.data() + 12 * n, 4 * n, 4 * n, 3 * nc, cudaMemcpyHostToDevice, s);
+    if ((st = gs::sync_stream(S, 30.0)) != GS_OK) break;
   }
   std::fclose(f);
+  if (st != GS_OK) return st;
   if (!ok) return gs::fail(GS_ERR_INVALID, "%s is truncated", path);
   const int32_t step = (int32_t)hdr[3];
-  cudaMemcpy(S->step_dev.p, &step, 4, cudaMemcpyHostToDevice);
+  cudaMemcpyAsync(S->step_dev.p, &step, 4, cudaMemcpyHostToDevice, S->stream);
+  if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
   S->n_active = n;
   return gs::check_launch("session load");
 }
@@ -834,10 +858,12 @@ gs_status gs_session_read_params(gs_session* S, float* means4, float* scale_opa,
   if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
   const int64_t n = S->n_active, cap = S->capacity;
   const float* A = gs::arena_ptr(S, 0);
-  if (means4) cudaMemcpy(means4, A, 16 * n, cudaMemcpyDeviceToHost);
-  if (scale_opa) cudaMemcpy(scale_opa, A + 4 * cap, 16 * n, cudaMemcpyDeviceToHost);
-  if (quat) cudaMemcpy(quat, A + 8 * cap, 16 * n, cudaMemcpyDeviceToHost);
-  if (sh) cudaMemcpy2D(sh, 4 * n, A + 12 * cap, 4 * cap, 4 * n, 3 * S->nc, cudaMemcpyDeviceToHost);
+  cudaStream_t s = S->stream;
+  if (means4) cudaMemcpyAsync(means4, A, 16 * n, cudaMemcpyDeviceToHost, s);
+  if (scale_opa) cudaMemcpyAsync(scale_opa, A + 4 * cap, 16 * n, cudaMemcpyDeviceToHost, s);
+  if (quat) cudaMemcpyAsync(quat, A + 8 * cap, 16 * n, cudaMemcpyDeviceToHost, s);
+  if (sh) cudaMemcpy2DAsync(sh, 4 * n, A + 12 * cap, 4 * cap, 4 * n, 3 * S->nc, cudaMemcpyDeviceToHost, s);
+  if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
   return gs::check_launch("session read");
 }
 

@@ -223,20 +223,24 @@ class Rasterizer:
         return image, alpha
 
     def backward(self, params: Arena, poses: torch.Tensor, dimage: torch.Tensor, dalpha: Optional[torch.Tensor],
-                 grads: Arena, dpose: Optional[torch.Tensor]) -> None:
+                 grads: Arena, dpose: Optional[torch.Tensor], image: Optional[torch.Tensor] = None) -> None:
+        """image: the forward's output for the current tile lists; with it and
+        no dalpha the per-tile pass is the single front-to-back one."""
         ps = params.struct()
         gs = grads.struct()
         b = self.bins_struct()
         _lib.check(self.L.gs_render_bwd(C.byref(ps), _p(poses), self.cam_struct, self.views, C.byref(self.splats),
-                                        C.byref(b), C.byref(self.cfg), _p(dimage), _p(dalpha), C.byref(gs),
-                                        _p(dpose), _p(self.ws_bwd), self.ws_bwd.numel(), _stream()),
+                                        C.byref(b), C.byref(self.cfg), _p(dimage), _p(dalpha), _p(image),
+                                        C.byref(gs), _p(dpose), _p(self.ws_bwd), self.ws_bwd.numel(), _stream()),
                    "gs_render_bwd")
 
-    def backward_pixels(self, dimage: torch.Tensor, dalpha: Optional[torch.Tensor] = None) -> None:
+    def backward_pixels(self, dimage: torch.Tensor, dalpha: Optional[torch.Tensor] = None,
+                        image: Optional[torch.Tensor] = None) -> None:
         b = self.bins_struct()
         _lib.check(self.L.gs_render_bwd_pixels(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
-                                               C.byref(self.cfg), _p(dimage), _p(dalpha), self.n, _p(self.ws_bwd),
-                                               self.ws_bwd.numel(), _stream()), "gs_render_bwd_pixels")
+                                               C.byref(self.cfg), _p(dimage), _p(dalpha), _p(image), self.n,
+                                               _p(self.ws_bwd), self.ws_bwd.numel(), _stream()),
+                   "gs_render_bwd_pixels")
 
     def backward_gaussians(self, params: Arena, poses: torch.Tensor, grads: Arena,
                            dpose: Optional[torch.Tensor]) -> None:

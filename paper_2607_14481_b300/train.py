@@ -57,7 +57,7 @@ class TrainStep:
         r.bin_sort()
         r.render_fwd(self.img, None)
         self.loss(self.img, self.targets, self.dimg, self.kind)
-        r.backward_pixels(self.dimg, None)
+        r.backward_pixels(self.dimg, None, self.img)
         r.backward_gaussians(self.arena, self.poses, self.grads, self.dpose)
         with_pose = self.pose_m is not None
         raster.adam_step(self.arena, self.grads, self.m, self.v, 0, self.groups, status=self.status,

@@ -28,7 +28,9 @@ def gpu_forward(sc: Scene, cams, bg=(0.0, 0.0, 0.0), znear=0.2, clamp_j=True, ca
     return r, arena, poses, img, alpha
 
 
-def gpu_backward(r, arena, poses, dimage_list, dalpha_list=None):
+def gpu_backward(r, arena, poses, dimage_list, dalpha_list=None, image=None):
+    """image: the forward's output, selecting the single front-to-back pass
+    (when there is no alpha gradient)."""
     dev = arena.buf.device
     dimg = torch.from_numpy(np.concatenate([np.asarray(x, np.float32).reshape(-1) for x in dimage_list])).to(dev)
     dal = None
@@ -37,7 +39,7 @@ def gpu_backward(r, arena, poses, dimage_list, dalpha_list=None):
     grads = arena.like()
     grads.buf.fill_(float("nan"))  # every element must be written
     dpose = torch.full((r.views, 6), float("nan"), dtype=torch.float32, device=dev)
-    r.backward(arena, poses, dimg, dal, grads, dpose)
+    r.backward(arena, poses, dimg, dal, grads, dpose, image)
     torch.cuda.synchronize()
     g = grads.to_natural()
     g["pose"] = dpose.cpu().numpy().astype(np.float64)

@@ -191,15 +191,33 @@ def test_image_permutation_bit_exact(cuda_device):
 # ---------------------------------------------------------------------------
 # gradients
 # ---------------------------------------------------------------------------
-def test_gradients_plain_small_l1(cuda_device):
+@pytest.mark.parametrize("single_pass", [False, True])
+def test_gradients_plain_small_l1(cuda_device, single_pass):
     sc, cams, targets = synth.plain_small()
     ref = oracle.render(sc, cams)
     _, dimg = oracle.l1_loss(ref["image"], targets)
     dimg = _masked(dimg, ref["flags"])
     r, arena, poses, img, alpha = gpu_forward(sc, cams)
-    g_gpu = gpu_backward(r, arena, poses, dimg)
+    g_gpu = gpu_backward(r, arena, poses, dimg, image=img if single_pass else None)
     g_ref = oracle.backward(sc, cams, dimg)
     compare_grads(g_gpu, g_ref)
+
+
+def test_single_pass_backward_mse_background_multiview(cuda_device):
+    """The front-to-back form (colour behind = forward image minus composited
+    prefix) against the oracle, with a background (the remainder ends at
+    T_final * bg) and several views of different sizes in one launch."""
+    sc, cams, targets = synth.diffcheck()
+    bg = (0.1, 0.2, 0.3)
+    ref = oracle.render(sc, cams, bg=bg)
+    _, dimg = oracle.mse_loss(ref["image"], targets)
+    dimg = _masked(dimg, ref["flags"])
+    r, arena, poses, img, alpha = gpu_forward(sc, cams, bg=bg)
+    g_one = gpu_backward(r, arena, poses, dimg, image=img)
+    g_ref = oracle.backward(sc, cams, dimg, bg=bg)
+    compare_grads(g_one, g_ref)
+    g_two = gpu_backward(r, arena, poses, dimg)
+    compare_grads(g_one, g_two)
 
 
 def test_gradients_diffcheck_mse_with_alpha_and_background(cuda_device):
@@ -216,13 +234,15 @@ def test_gradients_diffcheck_mse_with_alpha_and_background(cuda_device):
     compare_grads(g_gpu, g_ref)
 
 
-def test_backward_deterministic(cuda_device):
+@pytest.mark.parametrize("single_pass", [False, True])
+def test_backward_deterministic(cuda_device, single_pass):
     sc, cams, targets = synth.diffcheck()
     ref = oracle.render(sc, cams)
     _, dimg = oracle.mse_loss(ref["image"], targets)
     r, arena, poses, img, alpha = gpu_forward(sc, cams)
-    a = gpu_backward(r, arena, poses, dimg)
-    b = gpu_backward(r, arena, poses, dimg)
+    image = img if single_pass else None
+    a = gpu_backward(r, arena, poses, dimg, image=image)
+    b = gpu_backward(r, arena, poses, dimg, image=image)
     for k in a:
         assert np.array_equal(a[k], b[k]), k
 
@@ -241,9 +261,10 @@ def test_empty_and_all_culled(cuda_device):
     for ch in range(3):
         assert np.all(im[ch] == np.float32(bg[ch]))
     assert torch.all(alpha == 0)
-    g = gpu_backward(r, arena, poses, [np.ones((3, 128, 128))])
-    for k in ("means", "log_scales", "quats", "opa_logits", "sh", "pose"):
-        assert np.all(g[k] == 0), k
+    for image in (None, img):
+        g = gpu_backward(r, arena, poses, [np.ones((3, 128, 128))], image=image)
+        for k in ("means", "log_scales", "quats", "opa_logits", "sh", "pose"):
+            assert np.all(g[k] == 0), k
     # a single Gaussian (n = 1) far outside the view
     one = sc.subset([0])
     one.means[0] = (50.0, 0.0, 0.0)
@@ -295,6 +316,7 @@ def test_full_size_500k_720p_sampled_windows(cuda_device):
     gw = np.where(ref["flags"][0][None] != 0, 0.0, gw)
     dfull = np.zeros((3, 720, 1280))
     dfull[:, y0:y0 + h, x0:x0 + w] = gw
-    g_gpu = gpu_backward(r, arena, poses, [dfull])
     g_ref = oracle.backward(sc, cams, [gw], windows=[wins[0]])
-    compare_grads(g_gpu, g_ref)
+    for image in (None, img):  # replay + reverse walk, and the single front-to-back pass
+        g_gpu = gpu_backward(r, arena, poses, [dfull], image=image)
+        compare_grads(g_gpu, g_ref)

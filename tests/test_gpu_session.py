@@ -97,7 +97,7 @@ def _direct_train(sc, cams, targets, lrs):
         img, _ = r.forward(a, raster.poses_tensor([c], dev), r.new_image(), None)
         dimg = r.new_image()
         loss(img, torch.from_numpy(t.reshape(-1)).to(dev), dimg, 0)
-        r.backward(a, raster.poses_tensor([c], dev), dimg, None, g, None)
+        r.backward(a, raster.poses_tensor([c], dev), dimg, None, g, None, img)
         raster.adam_step(a, g, m, v, k + 1, groups)
     torch.cuda.synchronize()
     return a
@@ -140,7 +140,7 @@ def test_save_load_resumes_bit_identically(cuda_device, tmp_path):
     cams = _cams(4, seed=11)
     targets = _targets(cams, seed=4)
     path = str(tmp_path / "ckpt.bin")
-    with session.Session(_cfg(sc.n)) as s:
+    with session.Session(_cfg(sc.n, sh_degree=1)) as s:
         s.add(sc)
         for c, t in zip(cams[:2], targets[:2]):
             s.wait(s.submit(TRAIN, c, target=t))
@@ -148,11 +148,12 @@ def test_save_load_resumes_bit_identically(cuda_device, tmp_path):
         for c, t in zip(cams[2:], targets[2:]):
             s.wait(s.submit(TRAIN, c, target=t))
         full = s.params()
-    with session.Session(_cfg(sc.n)) as s2:
+    with session.Session(_cfg(sc.n, sh_degree=1)) as s2:
         s2.load(path)
         for c, t in zip(cams[2:], targets[2:]):
             s2.wait(s2.submit(TRAIN, c, target=t))
         resumed = s2.params()
+    assert np.all(np.isfinite(full["means4"]))
     for k in full:
         assert np.array_equal(full[k], resumed[k]), k
 
