@@ -61,8 +61,8 @@ class Session:
     def add(self, sc: Scene) -> None:
         if sc.sh_degree != self.cfg.sh_degree:
             raise ValueError(f"scene has SH degree {sc.sh_degree}, the session {self.cfg.sh_degree}")
-        if sc.sh.shape != (3 * self.nc, sc.n):
-            raise ValueError(f"sh must be [{3 * self.nc}][{sc.n}], got {sc.sh.shape}")
+        if sc.sh.shape != (sc.n, 3, self.nc):
+            raise ValueError(f"sh must be [{sc.n}][3][{self.nc}], got {sc.sh.shape}")
         arrs = [np.ascontiguousarray(a, np.float32) for a in
                 (sc.means, sc.log_scales, sc.quats, sc.opa_logits, sc.sh)]
         ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs]
