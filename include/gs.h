@@ -248,6 +248,30 @@ GS_API gs_status gs_bin_sort(const gs_splats* splats, const gs_camera* cams, int
                       const gs_raster_cfg* cfg, gs_bins* out, void* ws, size_t ws_bytes,
                       gs_stream stream);
 
+/* Bytes of the static scratch behind gs_bin_sort_noalloc: enough for, e.g.,
+ * n * views <= 65536 items with capacity <= 262144 pairs. */
+#define GS_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* gs_bin_sort without a workspace argument and without allocating anything
+ * (no cudaMalloc / cudaFree, no allocating library).  The paper has no
+ * counterpart: this entry point serves callers that cannot allocate device
+ * memory (a C host whose device buffers come from an owner's pool, a
+ * latency-critical thread where an allocation may synchronise the device, a
+ * caller held to a fixed memory budget).  The workspace is one file-scope
+ * device array of GS_NOALLOC_SCRATCH_BYTES inside libgs; its device address
+ * is looked up once per device (cudaGetSymbolAddress) on the first call made
+ * with that device current.  Results are identical to gs_bin_sort's.
+ * Errors: GS_ERR_OOM (with a message) when gs_bin_sort_workspace(n, views,
+ * capacity) exceeds the scratch; gs_bin_sort's own checks otherwise.
+ * Nothing in the scratch has to start at zero (the call writes every word it
+ * reads).  All calls on a device share the one scratch: two calls whose
+ * device work overlaps (different streams, or host threads without
+ * ordering) race on it and give wrong results, so order them on one stream.
+ * Because the first call on a device performs the lookup, make it before
+ * any stream capture. */
+GS_API gs_status gs_bin_sort_noalloc(const gs_splats* splats, const gs_camera* cams, int32_t views,
+                                     const gs_raster_cfg* cfg, gs_bins* out, gs_stream stream);
+
 /* Forward compositing, one CTA per 16x16 tile: per pixel, splats in list
  * order; skip when the centre is outside [m-r, m+r]^2, power > 0 or
  * alpha < 1/255; stop before a splat that would make T < 1e-4;

@@ -14,11 +14,12 @@ LIB_PATH = os.path.join(HERE, "_build", "libgs.so")
 GS_OK, GS_ERR_INVALID, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NONFINITE, GS_ERR_BUSY = range(7)
 GS_MAX_VIEWS = 64
 GS_TILE = 16
+GS_NOALLOC_SCRATCH_BYTES = 8 << 20  # static scratch of gs_bin_sort_noalloc
 GS_MAX_ADAM_GROUPS = 64
 
 EXPORTED = (
     "gs_last_error", "gs_version", "gs_built_arch", "gs_splats_bytes", "gs_splats_carve",
-    "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_render_fwd",
+    "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
@@ -131,6 +132,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_bin_sort_workspace.argtypes = [i64, i32, i64]
     L.gs_bin_sort_workspace.restype = sz
     L.gs_bin_sort.argtypes = [P(GsSplats), P(GsCamera), i32, P(GsRasterCfg), P(GsBins), vp, sz, vp]
+    L.gs_bin_sort_noalloc.argtypes = [P(GsSplats), P(GsCamera), i32, P(GsRasterCfg), P(GsBins), vp]
     L.gs_render_fwd.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp, vp]
     L.gs_render_bwd_workspace.argtypes = [i64, i32, i64]
     L.gs_render_bwd_workspace.restype = sz
@@ -162,7 +164,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                  "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_stats",
                  "gs_session_read_params", "gs_session_save", "gs_session_load", "gs_session_destroy"):
         getattr(L, name).restype = C.c_int
-    for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
+    for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
+                 "gs_render_bwd",
                  "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
                  "gs_render_stats"):
         getattr(L, name).restype = C.c_int

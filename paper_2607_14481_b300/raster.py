@@ -188,6 +188,13 @@ class Rasterizer:
         _lib.check(self.L.gs_bin_sort(C.byref(self.splats), self.cam_struct, self.views, C.byref(self.cfg),
                                       C.byref(b), _p(self.ws_bin), self.ws_bin.numel(), _stream()), "gs_bin_sort")
 
+    def bin_sort_noalloc(self) -> None:
+        """gs_bin_sort_noalloc: the same binning with libgs's static scratch
+        (small scenes; no workspace)."""
+        b = self.bins_struct()
+        _lib.check(self.L.gs_bin_sort_noalloc(C.byref(self.splats), self.cam_struct, self.views, C.byref(self.cfg),
+                                              C.byref(b), _stream()), "gs_bin_sort_noalloc")
+
     def render_fwd(self, image: torch.Tensor, alpha: Optional[torch.Tensor]) -> None:
         b = self.bins_struct()
         _lib.check(self.L.gs_render_fwd(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
