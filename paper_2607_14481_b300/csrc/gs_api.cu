@@ -228,7 +228,8 @@ static size_t bwd_layout(int64_t n, int32_t views, int64_t capacity, char* base,
   };
   float* pa = (float*)take(sizeof(float) * kPartialStride * (size_t)std::max<int64_t>(0, capacity));
   float* pp = (float*)take(sizeof(float) * 9 * (size_t)warps * (size_t)std::max(1, views));
-  float* dc = (float*)take(sizeof(float) * 4 * (size_t)std::max<int64_t>(0, n) * (size_t)std::max(1, views));
+  // three float4 planes per (view, Gaussian): summed geometry / opacity and colour gradients
+  float* dc = (float*)take(sizeof(float) * 12 * (size_t)std::max<int64_t>(0, n) * (size_t)std::max(1, views));
   if (drgb) *drgb = dc;
   if (partials) *partials = pa;
   if (pose_partials) *pose_partials = pp;

@@ -3,14 +3,18 @@
 // to the parameters (means, log-scales, quaternion, opacity logit, SH) and to
 // each view's pose for the left perturbation T <- Exp(xi) T, xi = (v, omega).
 //
-// Two kernels, one thread per Gaussian, all views in one fixed-order loop:
+// k_pair_sum, one thread per (view, Gaussian), sums its per-tile partials in
+// list order (pairs of one (view, Gaussian) are contiguous) into three
+// planes; then two kernels, one thread per Gaussian, all views in one
+// fixed-order loop:
 //   k_project_bwd  pixel-space mean, conic, opacity -> means, log-scales,
 //                  quaternion, opacity logit, pose (t and rotation terms);
-//                  stores each visible (view, Gaussian)'s colour gradient;
 //   k_sh_bwd       colour -> SH coefficients and, through the view
 //                  direction, the means and the pose translation.
-// Pose gradients are reduced per warp (shuffles, fixed tree) and then over
-// warps in a fixed order: deterministic, no atomics, no block barriers.
+// Pose gradients are reduced per warp (shuffles, fixed tree), then over
+// fixed chunks of warps and the chunks in a fixed order: deterministic, no
+// atomics.  The pair sum is its own kernel so that its scattered loads run at
+// full occupancy: the chain-rule kernels hold ~120 registers per thread.
 #include <algorithm>
 
 #include "gs_internal.h"
@@ -40,6 +44,7 @@ struct GradArgs {
   int64_t g_sh_stride;
   float* pose_a;         // [V][warps][6] from k_project_bwd
   float* pose_b;         // [V][warps][3] from k_sh_bwd (translation part)
+  float4* gsum;          // [2][V][n]: (dmx, dmy, dA, dB), (dC, dopacity, -, -) per visible (view, Gaussian)
   float4* drgb;          // [V][n] summed colour gradient of each visible (view, Gaussian)
 };
 
@@ -62,6 +67,93 @@ __device__ __forceinline__ bool pair_range_ok(const GradArgs& a, int64_t o, uint
   // pairs cut off by a capacity overflow were never rendered: skip them
   if (tch > 0 && (uint64_t)a.pair_off[o] + tch > kpairs) tch = 0;
   return tch > 0;
+}
+
+// Sum of each visible (view, Gaussian)'s per-tile partials, in a fixed
+// order.  A (view, Gaussian) with at most kWideSegment pairs is summed by its
+// own thread in list order, four pairs per step so that their twelve loads
+// are in flight together.  Wider ones (a splat near the camera can cover
+// thousands of tiles) are summed by the whole warp, one at a time: lane l
+// takes pairs l, l + 32, ... in order, then a fixed butterfly combines the
+// lanes, so the warp's time is not set by one thread walking a long segment.
+constexpr uint32_t kWideSegment = 16;
+
+__global__ void __launch_bounds__(256) k_pair_sum(const GradArgs a, int64_t m) {
+  const int64_t o = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  uint32_t tch = 0;
+  const bool live = o < m && pair_range_ok(a, o, a.counts[3], tch);
+  const uint32_t off = live ? a.pair_off[o] : 0u;
+  const bool wide = live && tch > kWideSegment;
+  if (live && !wide) {
+    const float4* pp = reinterpret_cast<const float4*>(a.partials + (int64_t)off * kPartialStride);
+    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+    float s2 = 0.f;
+    uint32_t k = 0;
+    for (; k + 4 <= tch; k += 4) {
+      float4 p[12];
+#pragma unroll
+      for (int j = 0; j < 12; ++j) p[j] = pp[3 * k + j];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        s0.x += p[3 * j].x; s0.y += p[3 * j].y; s0.z += p[3 * j].z; s0.w += p[3 * j].w;
+        s1.x += p[3 * j + 1].x; s1.y += p[3 * j + 1].y; s1.z += p[3 * j + 1].z; s1.w += p[3 * j + 1].w;
+        s2 += p[3 * j + 2].x;
+      }
+    }
+    for (; k < tch; ++k) {
+      const float4 p0 = pp[3 * k], p1 = pp[3 * k + 1], p2 = pp[3 * k + 2];
+      s0.x += p0.x; s0.y += p0.y; s0.z += p0.z; s0.w += p0.w;
+      s1.x += p1.x; s1.y += p1.y; s1.z += p1.z; s1.w += p1.w;
+      s2 += p2.x;
+    }
+    a.gsum[o] = s0;
+    a.gsum[m + o] = make_float4(s1.x, s1.y, 0.f, 0.f);
+    a.drgb[o] = make_float4(s1.z, s1.w, s2, 0.f);
+  }
+  unsigned pending = __ballot_sync(0xffffffffu, wide);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const uint32_t cnt = __shfl_sync(0xffffffffu, tch, src);
+    const uint32_t base = __shfl_sync(0xffffffffu, off, src);
+    const float4* pp = reinterpret_cast<const float4*>(a.partials + (int64_t)base * kPartialStride);
+    float acc[kPartialValues];
+#pragma unroll
+    for (int c = 0; c < kPartialValues; ++c) acc[c] = 0.f;
+    uint32_t k = lane;
+    for (; k + 96 < cnt; k += 128) {
+      float4 p[12];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        p[3 * j] = pp[3 * (k + 32 * j)];
+        p[3 * j + 1] = pp[3 * (k + 32 * j) + 1];
+        p[3 * j + 2] = pp[3 * (k + 32 * j) + 2];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[0] += p[3 * j].x; acc[1] += p[3 * j].y; acc[2] += p[3 * j].z; acc[3] += p[3 * j].w;
+        acc[4] += p[3 * j + 1].x; acc[5] += p[3 * j + 1].y; acc[6] += p[3 * j + 1].z; acc[7] += p[3 * j + 1].w;
+        acc[8] += p[3 * j + 2].x;
+      }
+    }
+    for (; k < cnt; k += 32) {
+      const float4 p0 = pp[3 * k], p1 = pp[3 * k + 1], p2 = pp[3 * k + 2];
+      acc[0] += p0.x; acc[1] += p0.y; acc[2] += p0.z; acc[3] += p0.w;
+      acc[4] += p1.x; acc[5] += p1.y; acc[6] += p1.z; acc[7] += p1.w;
+      acc[8] += p2.x;
+    }
+#pragma unroll
+    for (int c = 0; c < kPartialValues; ++c) {
+#pragma unroll
+      for (int x = 16; x > 0; x >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], x);
+    }
+    if (lane == src) {
+      a.gsum[o] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      a.gsum[m + o] = make_float4(acc[4], acc[5], 0.f, 0.f);
+      a.drgb[o] = make_float4(acc[6], acc[7], acc[8], 0.f);
+    }
+  }
 }
 
 template <int DEG>
@@ -102,18 +194,9 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
     if (valid && pair_range_ok(a, o, kpairs, tch)) {
       const ViewInfo vi = vt.v[v];
       const uint32_t auxb = a.aux[o];
-      // ---- sum of this (view, Gaussian)'s per-tile partials, fixed order
-      float G[kPartialValues];
-#pragma unroll
-      for (int c = 0; c < kPartialValues; ++c) G[c] = 0.f;
-      const float4* pp = reinterpret_cast<const float4*>(a.partials + (int64_t)a.pair_off[o] * kPartialStride);
-      for (uint32_t k = 0; k < tch; ++k) {
-        const float4 p0 = pp[3 * k], p1 = pp[3 * k + 1], p2 = pp[3 * k + 2];
-        G[0] += p0.x; G[1] += p0.y; G[2] += p0.z; G[3] += p0.w;
-        G[4] += p1.x; G[5] += p1.y; G[6] += p1.z; G[7] += p1.w;
-        G[8] += p2.x;
-      }
-      a.drgb[o] = make_float4(G[6], G[7], G[8], 0.f);
+      // ---- this (view, Gaussian)'s summed pixel-space gradients
+      const float4 ga4 = a.gsum[o], gb4 = a.gsum[(int64_t)vt.views * a.n + o];
+      const float G[6] = {ga4.x, ga4.y, ga4.z, ga4.w, gb4.x, gb4.y};
       const float* P = a.poses + 12 * v;
       const float R[9] = {P[0], P[1], P[2], P[4], P[5], P[6], P[8], P[9], P[10]};
       const float tc[3] = {P[3], P[7], P[11]};
@@ -324,13 +407,19 @@ __global__ void __launch_bounds__(kGradBlock) k_sh_bwd(const GradArgs a, const V
   }
 }
 
-// Sum of the per-warp pose partials of each view, in a fixed order.
-__global__ void __launch_bounds__(256) k_pose_finalize(const float* __restrict__ pa, const float* __restrict__ pb,
-                                                       int64_t warps, float* __restrict__ dpose) {
+constexpr int kPoseChunks = 64;
+
+// Stage 1 of the pose sum: block (chunk j, view v) sums the per-warp partials
+// of warps [j c, (j+1) c) in a fixed order and stores the 6 values in place
+// of the chunk's first warp (no other block reads that chunk).
+__global__ void __launch_bounds__(256) k_pose_chunks(float* __restrict__ pa, const float* __restrict__ pb,
+                                                     int64_t warps, int64_t chunk) {
   __shared__ float s[256][6];
-  const int v = blockIdx.x;
+  const int v = blockIdx.y;
+  const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(warps, b0 + chunk);
+  if (b0 >= warps) return;  // block-uniform
   float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int64_t b = threadIdx.x; b < warps; b += 256) {
+  for (int64_t b = b0 + threadIdx.x; b < b1; b += 256) {
     const float* p = pa + ((int64_t)v * warps + b) * 6;
     const float* q = pb + ((int64_t)v * warps + b) * 3;
 #pragma unroll
@@ -348,7 +437,24 @@ __global__ void __launch_bounds__(256) k_pose_finalize(const float* __restrict__
     }
     __syncthreads();
   }
-  if (threadIdx.x < 6) dpose[v * 6 + threadIdx.x] = s[0][threadIdx.x];
+  if (threadIdx.x < 6) pa[((int64_t)v * warps + b0) * 6 + threadIdx.x] = s[0][threadIdx.x];
+}
+
+// Stage 2: the chunks of each view in order (staged through shared memory so
+// that the loads are issued together).
+__global__ void __launch_bounds__(kPoseChunks) k_pose_finalize(const float* __restrict__ pa, int64_t warps,
+                                                             int64_t chunk, float* __restrict__ dpose) {
+  __shared__ float s[kPoseChunks][6];
+  const int v = blockIdx.x, t = threadIdx.x;
+  const int64_t b0 = (int64_t)t * chunk;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s[t][c] = b0 < warps ? pa[((int64_t)v * warps + b0) * 6 + c] : 0.f;
+  __syncthreads();
+  if (t < 6) {
+    float acc = 0.f;
+    for (int j = 0; j < kPoseChunks; ++j) acc += s[j][t];
+    dpose[v * 6 + t] = acc;
+  }
 }
 
 }  // namespace
@@ -383,12 +489,16 @@ gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewT
   const int64_t warps = pose_partial_warps(p.n);
   a.pose_a = pose_partials;
   a.pose_b = pose_partials + 6 * warps * vt.views;
-  a.drgb = reinterpret_cast<float4*>(drgb);
+  // drgb: three planes [V][n] float4, the colour gradients last
+  a.gsum = reinterpret_cast<float4*>(drgb);
+  a.drgb = a.gsum + 2 * p.n * vt.views;
   if (p.n == 0) {
     if (dpose) cudaMemsetAsync(dpose, 0, sizeof(float) * 6 * vt.views, s);
     return check_launch("project_bwd");
   }
   const unsigned grid = (unsigned)((p.n + kGradBlock - 1) / kGradBlock);
+  const int64_t m = p.n * vt.views;
+  k_pair_sum<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(a, m);
   switch (p.sh_degree) {
     case 0:
       k_project_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt);
@@ -407,7 +517,11 @@ gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewT
       k_sh_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt);
       break;
   }
-  if (dpose) k_pose_finalize<<<vt.views, 256, 0, s>>>(a.pose_a, a.pose_b, warps, dpose);
+  if (dpose) {
+    const int64_t chunk = (warps + kPoseChunks - 1) / kPoseChunks;
+    k_pose_chunks<<<dim3(kPoseChunks, vt.views), 256, 0, s>>>(a.pose_a, a.pose_b, warps, chunk);
+    k_pose_finalize<<<vt.views, kPoseChunks, 0, s>>>(a.pose_a, warps, chunk, dpose);
+  }
   return check_launch("project_bwd");
 }
 

@@ -10,9 +10,13 @@
 // it never skips a splat the exact per-pixel test would accept).  The CTA
 // leaves the list as soon as every pixel has saturated (__syncthreads_count).
 //
-// The splat test is written once (splat_alpha) with explicit round-to-nearest
-// intrinsics so that the forward, the backward's replay and the backward's
-// reverse walk take bit-identical decisions.
+// Each staged splat carries its centre relative to the tile origin, its conic
+// scaled to base-2 exponent units and the exponent threshold below which its
+// alpha would fall under 1/255, so a pixel test is a few FMAs and two
+// compares, and the exponential is evaluated only for splats that pass.  The
+// test is written once (splat_x + splat_alpha) with explicit round-to-nearest
+// intrinsics so that the forward and every backward form take bit-identical
+// decisions.
 #include "gs_internal.h"
 
 namespace gs {
@@ -25,47 +29,59 @@ constexpr int kBatch = kThreads;            // splats staged per batch
 constexpr int kRowsPerWarp = 32 / kTile * 2;  // 4
 
 struct Eval {
-  float dx, dy, power, ex, raw, alpha;
+  float dx, dy, ex, raw, alpha;  // ex = exp(power), raw = opacity ex, alpha = min(0.99, raw)
 };
 
-// Alpha of one splat at pixel (px, py): false when the splat is skipped
-// (centre outside [m-r, m+r]^2, power > 0 or alpha < 1/255).
-__device__ __forceinline__ bool splat_alpha(const float4 m, const float4 co, float r, float px,
-                                            float py, Eval& e) {
-  e.dx = __fadd_rn(__fsub_rn(m.x, px), __fsub_rn(m.z, 0.5f));
-  e.dy = __fadd_rn(__fsub_rn(m.y, py), __fsub_rn(m.w, 0.5f));
-  if (fabsf(e.dx) > r || fabsf(e.dy) > r) return false;
-  const float q = __fmaf_rn(co.x, __fmul_rn(e.dx, e.dx), __fmul_rn(co.z, __fmul_rn(e.dy, e.dy)));
-  e.power = __fmaf_rn(-0.5f, q, __fmul_rn(-co.y, __fmul_rn(e.dx, e.dy)));
-  if (e.power > 0.f) return false;
-  e.ex = __expf(e.power);
-  e.raw = __fmul_rn(co.w, e.ex);
+constexpr float kLog2e = 1.4426950408889634f;
+
+// 2^x by the PTX instruction ex2.approx.ftz.f32 (relative error ~2^-22; the
+// arguments here lie in [-8, 0], far from subnormal results).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Terms of the pixel test that depend only on the splat and the pixel
+// column, shared by a thread's two pixels.
+struct XTerms {
+  float dx, a2dx2, b2dx;
+};
+
+// geo = (cx, cy, a2, b2): centre relative to the tile origin; a2 = -A/2 log2 e,
+// b2 = -B log2 e.  geo2 = (c2, thr, opacity, r): c2 = -C/2 log2 e;
+// thr = log2(1 / (255 opacity)).  lx = pixel column within the tile.
+__device__ __forceinline__ XTerms splat_x(const float4 g, float lx) {
+  XTerms t;
+  t.dx = __fsub_rn(g.x, lx);
+  t.b2dx = __fmul_rn(g.w, t.dx);
+  t.a2dx2 = __fmul_rn(__fmul_rn(g.z, t.dx), t.dx);
+  return t;
+}
+
+// Alpha of one splat at the pixel (lx, ly) of the tile: false when it is
+// skipped (centre outside [m-r, m+r]^2, power > 0 or alpha < 1/255).  With
+// p = power log2 e = a2 dx^2 + dy (b2 dx + c2 dy), alpha >= 1/255 is
+// p >= thr, tested before the exponential.
+__device__ __forceinline__ bool splat_alpha(const XTerms& x, const float4 g, const float4 g2, float ly,
+                                            Eval& e) {
+  e.dx = x.dx;
+  e.dy = __fsub_rn(g.y, ly);
+  if (fabsf(e.dx) > g2.w || fabsf(e.dy) > g2.w) return false;
+  const float p = __fmaf_rn(e.dy, __fmaf_rn(g2.x, e.dy, x.b2dx), x.a2dx2);
+  if (!(p <= 0.f && p >= g2.y)) return false;
+  e.ex = ex2_approx(p);
+  e.raw = __fmul_rn(g2.z, e.ex);
   e.alpha = fminf(kAlphaMax, e.raw);
-  return e.alpha >= kAlphaMin;
-}
-
-// Rows a splat can touch, with a margin of one pixel (plus the rounding of
-// the single-precision centre far off screen): [my - r - e, my + r + e].  The
-// exact per-pixel test accepts rows within half a pixel of [my - r, my + r].
-// A negative radius (null splat) gives an empty range.
-__device__ __forceinline__ float2 splat_rows(const float4 m, float r) {
-  if (r < 0.f) return make_float2(1e30f, -1e30f);
-  const float my = m.y + m.w;
-  const float e = 1.f + 1e-6f * fabsf(my) + 1e-6f * r;
-  return make_float2(my - r - e, my + r + e);
-}
-
-// A splat that never passes the test (radius -1): stands in for an
-// out-of-range id, which is reported through counts[2] bit 2.
-__device__ __forceinline__ void null_splat(float4& m, float4& co, float4& col) {
-  m = make_float4(0.f, 0.f, 0.f, 0.f);
-  co = make_float4(0.f, 0.f, 0.f, 0.f);
-  col = make_float4(0.f, 0.f, 0.f, -1.f);
+  return true;
 }
 
 struct TileCoords {
   int v, tx, ty, px, py0;
   bool in0, in1;
+  float ox, oy;        // tile origin (pixels)
+  float lx, ly0, ly1;  // the thread's pixels within the tile
+  float wlo, whi;      // the warp's first and last tile row
 };
 
 __device__ __forceinline__ TileCoords tile_coords(const ViewTable& vt, int gt) {
@@ -79,6 +95,13 @@ __device__ __forceinline__ TileCoords tile_coords(const ViewTable& vt, int gt) {
   c.py0 = c.ty * kTile + 2 * (threadIdx.x / kTile);
   c.in0 = c.px < vi.W && c.py0 < vi.H;
   c.in1 = c.px < vi.W && c.py0 + 1 < vi.H;
+  c.ox = (float)(c.tx * kTile);
+  c.oy = (float)(c.ty * kTile);
+  c.lx = (float)(threadIdx.x % kTile);
+  c.ly0 = (float)(2 * (threadIdx.x / kTile));
+  c.ly1 = c.ly0 + 1.f;
+  c.wlo = (float)((threadIdx.x >> 5) * kRowsPerWarp);
+  c.whi = c.wlo + (float)(kRowsPerWarp - 1);
   return c;
 }
 
@@ -95,11 +118,16 @@ struct FwdArgs {
   float* alpha;
 };
 
-// Stages splat `j` of the list (or a null splat) in shared memory slot `t`.
+// Stages splat `j` of the list (or a null splat: radius -1, opacity 0, which
+// never passes the test, standing in for an out-of-range id reported through
+// counts[2] bit 2) in shared memory slot `t`, relative to the tile origin
+// (ox, oy).  rows = the tile rows [cy - r - 1, cy + r + 1] the splat can touch
+// (one pixel of margin over the exact test), empty for a null splat.
+// s_co (optional) keeps the unscaled conic and opacity for the backward.
 __device__ __forceinline__ void stage_splat(const float4* xy, const float4* conic, const float4* rgb,
                                             const uint32_t* vals, int64_t n, int64_t vbase, uint32_t j,
-                                            int t, float4* s_xy, float4* s_co, float4* s_rgb,
-                                            float2* s_rows, uint32_t* counts) {
+                                            int t, float ox, float oy, float4* s_geo, float4* s_geo2,
+                                            float4* s_rgb, float2* s_rows, float4* s_co, uint32_t* counts) {
   const uint32_t g = vals[j];
   float4 m, co, col;
   if (g < n) {
@@ -108,13 +136,18 @@ __device__ __forceinline__ void stage_splat(const float4* xy, const float4* coni
     co = conic[gi];
     col = rgb[gi];
   } else {
-    null_splat(m, co, col);
+    m = make_float4(0.f, 0.f, 0.f, 0.f);
+    co = m;
+    col = make_float4(0.f, 0.f, 0.f, -1.f);
     if (counts) atomicOr(&counts[2], 2u);
   }
-  s_xy[t] = m;
-  s_co[t] = co;
+  const float cx = __fadd_rn(__fsub_rn(m.x, ox), __fsub_rn(m.z, 0.5f));
+  const float cy = __fadd_rn(__fsub_rn(m.y, oy), __fsub_rn(m.w, 0.5f));
+  s_geo[t] = make_float4(cx, cy, __fmul_rn(-0.5f * kLog2e, co.x), __fmul_rn(-kLog2e, co.y));
+  s_geo2[t] = make_float4(__fmul_rn(-0.5f * kLog2e, co.z), -log2f(255.f * co.w), co.w, col.w);
   s_rgb[t] = col;
-  s_rows[t] = splat_rows(m, col.w);
+  if (s_co) s_co[t] = co;
+  s_rows[t] = col.w < 0.f ? make_float2(1e30f, -1e30f) : make_float2(cy - col.w - 1.f, cy + col.w + 1.f);
 }
 
 // COUNT = true is the diagnostic instantiation behind gs_render_stats: the
@@ -123,14 +156,11 @@ __device__ __forceinline__ void stage_splat(const float4* xy, const float4* coni
 template <bool COUNT>
 __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const ViewTable vt,
                                                          unsigned long long* stats) {
-  __shared__ float4 s_xy[kBatch], s_co[kBatch], s_rgb[kBatch];
+  __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch];
   __shared__ float2 s_rows[kBatch];
   __shared__ int s_last;
   const TileCoords tc = tile_coords(vt, blockIdx.x);
   const ViewInfo& vi = vt.v[tc.v];
-  const float pxf = (float)tc.px, py0f = (float)tc.py0, py1f = py0f + 1.f;
-  const float wrow_lo = (float)(tc.ty * kTile + (threadIdx.x >> 5) * kRowsPerWarp);
-  const float wrow_hi = wrow_lo + (float)(kRowsPerWarp - 1);
   const uint2 rg = a.ranges[blockIdx.x];
   const int64_t vbase = (int64_t)tc.v * a.n;
   float T0 = 1.f, T1 = 1.f;
@@ -143,22 +173,24 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
     if (__syncthreads_count(d0 && d1) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
     if (j < rg.y)
-      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, s_xy, s_co, s_rgb, s_rows,
-                  COUNT ? nullptr : a.counts);
+      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
+                  s_rgb, s_rows, nullptr, COUNT ? nullptr : a.counts);
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     for (int k = 0; k < cnt && !(d0 && d1); ++k) {
       const float2 rows = s_rows[k];
-      if (wrow_lo > rows.y || wrow_hi < rows.x) continue;  // warp-uniform
-      const float4 m = s_xy[k], co = s_co[k], col = s_rgb[k];
+      if (tc.wlo > rows.y || tc.whi < rows.x) continue;  // warp-uniform
+      const float4 g = s_geo[k], g2 = s_geo2[k];
+      const XTerms x = splat_x(g, tc.lx);
       Eval e;
       if (!d0) {
         if (COUNT) ++n_tested;
-        if (splat_alpha(m, co, col.w, pxf, py0f, e)) {
+        if (splat_alpha(x, g, g2, tc.ly0, e)) {
           const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
           if (Tn < kTransMin) {
             d0 = true;
           } else {
+            const float4 col = s_rgb[k];
             const float w = e.alpha * T0;
             c00 += col.x * w; c01 += col.y * w; c02 += col.z * w;
             T0 = Tn;
@@ -168,11 +200,12 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
       }
       if (!d1) {
         if (COUNT) ++n_tested;
-        if (splat_alpha(m, co, col.w, pxf, py1f, e)) {
+        if (splat_alpha(x, g, g2, tc.ly1, e)) {
           const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
           if (Tn < kTransMin) {
             d1 = true;
           } else {
+            const float4 col = s_rgb[k];
             const float w = e.alpha * T1;
             c10 += col.x * w; c11 += col.y * w; c12 += col.z * w;
             T1 = Tn;
@@ -372,7 +405,7 @@ __device__ __forceinline__ void splat_grad_front(const Eval& e, const float4 co,
 }
 
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const ViewTable vt) {
-  __shared__ float4 s_xy[kBatch], s_co[kBatch], s_rgb[kBatch];
+  __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
   __shared__ float2 s_rows[kBatch];
   __shared__ uint32_t s_pidx[kBatch];
   __shared__ float s_red[kBatch][kWarps][kPartialValues];
@@ -381,9 +414,6 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TileCoords tc = tile_coords(vt, blockIdx.x);
   const ViewInfo& vi = vt.v[tc.v];
-  const float pxf = (float)tc.px, py0f = (float)tc.py0, py1f = py0f + 1.f;
-  const float wrow_lo = (float)(tc.ty * kTile + warp * kRowsPerWarp);
-  const float wrow_hi = wrow_lo + (float)(kRowsPerWarp - 1);
   const uint2 rg = a.ranges[blockIdx.x];
   const int64_t vbase = (int64_t)tc.v * a.n;
   if (threadIdx.x == 0) s_maxlast = -1;
@@ -396,21 +426,21 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
     if (__syncthreads_count(d0 && d1) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
     if (j < rg.y)
-      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, s_xy, s_co, s_rgb, s_rows,
-                  nullptr);
+      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
+                  s_rgb, s_rows, nullptr, nullptr);
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     for (int k = 0; k < cnt && !(d0 && d1); ++k) {
       const float2 rows = s_rows[k];
-      if (wrow_lo > rows.y || wrow_hi < rows.x) continue;
-      const float4 m = s_xy[k], co = s_co[k];
-      const float r = s_rgb[k].w;
+      if (tc.wlo > rows.y || tc.whi < rows.x) continue;
+      const float4 g = s_geo[k], g2 = s_geo2[k];
+      const XTerms x = splat_x(g, tc.lx);
       Eval e;
-      if (!d0 && splat_alpha(m, co, r, pxf, py0f, e)) {
+      if (!d0 && splat_alpha(x, g, g2, tc.ly0, e)) {
         const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
         if (Tn < kTransMin) d0 = true; else { T0 = Tn; last0 = (int)(start + k); }
       }
-      if (!d1 && splat_alpha(m, co, r, pxf, py1f, e)) {
+      if (!d1 && splat_alpha(x, g, g2, tc.ly1, e)) {
         const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
         if (Tn < kTransMin) d1 = true; else { T1 = Tn; last1 = (int)(start + k); }
       }
@@ -449,8 +479,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
     __syncthreads();
     if (threadIdx.x < cnt) {
       const uint32_t j = (uint32_t)(bstart + threadIdx.x);
-      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, s_xy, s_co, s_rgb, s_rows,
-                  nullptr);
+      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
+                  s_rgb, s_rows, s_co, nullptr);
       s_pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
@@ -458,20 +488,21 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
     __syncthreads();
     for (int k = cnt - 1; k >= 0; --k) {
       const float2 rows = s_rows[k];
-      if (wrow_lo > rows.y || wrow_hi < rows.x) continue;  // warp-uniform: no contribution
+      if (tc.wlo > rows.y || tc.whi < rows.x) continue;  // warp-uniform: no contribution
       const int pos = bstart + k;
       float d[kPartialValues];
 #pragma unroll
       for (int c = 0; c < kPartialValues; ++c) d[c] = 0.f;
       bool contrib = false;
       if (pos <= mylast) {
-        const float4 m = s_xy[k], co = s_co[k], col = s_rgb[k];
+        const float4 g = s_geo[k], g2 = s_geo2[k], co = s_co[k], col = s_rgb[k];
+        const XTerms x = splat_x(g, tc.lx);
         Eval e;
-        if (pos <= last0 && splat_alpha(m, co, col.w, pxf, py0f, e)) {
+        if (pos <= last0 && splat_alpha(x, g, g2, tc.ly0, e)) {
           splat_grad(e, co, col, g00, g01, g02, ga0, Tf0, T0, a00, a01, a02, d);
           contrib = true;
         }
-        if (pos <= last1 && splat_alpha(m, co, col.w, pxf, py1f, e)) {
+        if (pos <= last1 && splat_alpha(x, g, g2, tc.ly1, e)) {
           splat_grad(e, co, col, g10, g11, g12, ga1, Tf1, T1, a10, a11, a12, d);
           contrib = true;
         }
@@ -498,7 +529,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
 // own decisions (same splat test, same transmittance products, same stop),
 // yields every gradient without a replay and without recovering T by division.
 __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, const ViewTable vt) {
-  __shared__ float4 s_xy[kBatch], s_co[kBatch], s_rgb[kBatch];
+  __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
   __shared__ float2 s_rows[kBatch];
   __shared__ uint32_t s_pidx[kBatch];
   __shared__ float s_red[kBatch][kWarps][kPartialValues];
@@ -506,9 +537,6 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TileCoords tc = tile_coords(vt, blockIdx.x);
   const ViewInfo& vi = vt.v[tc.v];
-  const float pxf = (float)tc.px, py0f = (float)tc.py0, py1f = py0f + 1.f;
-  const float wrow_lo = (float)(tc.ty * kTile + warp * kRowsPerWarp);
-  const float wrow_hi = wrow_lo + (float)(kRowsPerWarp - 1);
   const uint2 rg = a.ranges[blockIdx.x];
   const int64_t vbase = (int64_t)tc.v * a.n;
 
@@ -535,8 +563,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     if (threadIdx.x < cnt) {
       const uint32_t j = start + threadIdx.x;
-      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, s_xy, s_co, s_rgb, s_rows,
-                  nullptr);
+      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
+                  s_rgb, s_rows, s_co, nullptr);
       s_pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
@@ -545,29 +573,30 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
     for (int k = 0; k < cnt; ++k) {
       if (__all_sync(0xffffffffu, d0 && d1)) break;  // the warp's pixels are done
       const float2 rows = s_rows[k];
-      if (wrow_lo > rows.y || wrow_hi < rows.x) continue;  // warp-uniform: no contribution
+      if (tc.wlo > rows.y || tc.whi < rows.x) continue;  // warp-uniform: no contribution
       float d[kPartialValues];
 #pragma unroll
       for (int c = 0; c < kPartialValues; ++c) d[c] = 0.f;
       bool contrib = false;
-      const float4 m = s_xy[k], co = s_co[k], col = s_rgb[k];
+      const float4 g = s_geo[k], g2 = s_geo2[k];
+      const XTerms x = splat_x(g, tc.lx);
       Eval e;
-      if (!d0 && splat_alpha(m, co, col.w, pxf, py0f, e)) {
+      if (!d0 && splat_alpha(x, g, g2, tc.ly0, e)) {
         const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
         if (Tn < kTransMin) {
           d0 = true;
         } else {
-          splat_grad_front(e, co, col, g00, g01, g02, T0, r00, r01, r02, d);
+          splat_grad_front(e, s_co[k], s_rgb[k], g00, g01, g02, T0, r00, r01, r02, d);
           T0 = Tn;
           contrib = true;
         }
       }
-      if (!d1 && splat_alpha(m, co, col.w, pxf, py1f, e)) {
+      if (!d1 && splat_alpha(x, g, g2, tc.ly1, e)) {
         const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
         if (Tn < kTransMin) {
           d1 = true;
         } else {
-          splat_grad_front(e, co, col, g10, g11, g12, T1, r10, r11, r12, d);
+          splat_grad_front(e, s_co[k], s_rgb[k], g10, g11, g12, T1, r10, r11, r12, d);
           T1 = Tn;
           contrib = true;
         }
