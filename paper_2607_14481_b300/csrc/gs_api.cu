@@ -104,6 +104,9 @@ static gs_status check_bins(const gs_bins* b, const ViewTable& vt, int64_t n) {
   if (!b) return fail(GS_ERR_INVALID, "bins is NULL");
   if (!b->vals || !b->ranges || !b->pair_off || !b->counts) return fail(GS_ERR_INVALID, "NULL bins array");
   if (b->capacity < 0 || b->capacity >= (1ll << 32) - 1) return fail(GS_ERR_INVALID, "capacity out of range");
+  if (vt.total_tiles > bin_sort_max_tiles())
+    return fail(GS_ERR_INVALID, "%d tiles exceed the binning limit of %lld", vt.total_tiles,
+                (long long)bin_sort_max_tiles());
   if (b->num_tiles != vt.total_tiles)
     return fail(GS_ERR_INVALID, "bins.num_tiles (%lld) != tiles of the views (%d)", (long long)b->num_tiles,
                 vt.total_tiles);

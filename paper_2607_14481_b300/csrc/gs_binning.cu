@@ -2,16 +2,21 @@
 // (tile, depth) sort that orders every tile's list front to back, then the
 // [start, end) range of each tile.
 //
-// The 64-bit (global tile << 32 | depth bits) order is produced by two stable
-// LSD radix sorts instead of one sort of 64-bit keys:
-//   1. the visible (view, Gaussian) items are sorted by their 32-bit depth key
-//      (items are compacted in (view, id) order, so equal depths stay in id
-//      order);
-//   2. every item, in that depth order, emits one pair per tile of its rect;
-//      the pairs are sorted stably by global tile id on its significant bits
-//      only (12 bits at 720p, 17 for 16 views at 1080p).
-// Within one tile the pairs then sit in (depth, id) order: the same result as
-// the 64-bit sort, with about a third of the bytes moved.
+// A counting sort by tile followed by a sort of each tile's own list:
+//   1. an exclusive scan of the per-(view, Gaussian) tile counts gives every
+//      visible splat a contiguous block of pair slots (pair_off, emission
+//      order: what the backward indexes its per-pair gradients by);
+//   2. every pair takes a place in its tile with one shared-counter atomic
+//      (the counters live in the ranges array);
+//   3. a scan over the tiles turns the counts into list starts; every pair
+//      writes its (depth bits, Gaussian id) key at start + place;
+//   4. one CTA per tile sorts its list in shared memory (bitonic network, up
+//      to kShortList keys; longer lists take a CTA-wide stable radix sort
+//      through global memory) and writes the ids and the tile's range.
+// Within a tile every Gaussian appears once, so (depth bits, id) keys are
+// distinct and the sorted list is unique: the atomics' order never shows.
+// This is the order of one sort of 64-bit (tile, depth) keys with depth ties
+// in id order, with ~40 bytes moved per pair and a fixed dozen launches.
 //
 // Every count (visible items, pairs) stays in device memory: kernels are
 // launched for the capacity and read the live count, so the whole stage runs
@@ -25,13 +30,29 @@ namespace gs {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kIPT = 8;                      // items per thread
+constexpr int kIPT = 8;                      // items per thread (scans)
 constexpr int kItemsPerBlock = kThreads * kIPT;
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 8;                // long-list fallback sort
 constexpr int kRadixDigits = 1 << kRadixBits;
+constexpr uint32_t kShortList = 2048;        // tile lists sorted in shared memory
+constexpr int64_t kMaxScanTiles = 1ll << 25; // bound of the tile scan's workspace
 
 __device__ __forceinline__ uint32_t num_blocks(uint32_t n) {
   return (n + kItemsPerBlock - 1) / kItemsPerBlock;
+}
+
+// Lanes of the warp that are `ok` and hold the same 8-bit digit as this lane
+// (a multi-split by one ballot per digit bit; lanes not ok get no meaningful
+// result).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool ok) {
+  uint32_t m = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+  for (int b = 0; b < kRadixBits; ++b) {
+    const uint32_t bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit != 0u);
+    m &= bit ? bal : ~bal;
+  }
+  return m;
 }
 
 // Exclusive scan of one value per thread over a 256-thread block.
@@ -67,7 +88,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* s
 // ---------------------------------------------------------------------------
 // Device-wide exclusive scan (reduce, scan block sums, scan + add)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t* __restrict__ in,
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t* __restrict__ in, int in_stride,
                                                           const uint32_t* __restrict__ n_dev,
                                                           uint32_t* __restrict__ block_sums) {
   __shared__ uint32_t s_warp[kThreads / 32 + 1];
@@ -79,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t* __rest
 #pragma unroll
   for (int r = 0; r < kIPT; ++r) {
     uint64_t idx = base + (uint64_t)r * kThreads + threadIdx.x;
-    if (idx < n) sum += in[idx];
+    if (idx < n) sum += in[idx * in_stride];
   }
   uint32_t total;
   block_exclusive_scan(sum, s_warp, &total);
@@ -114,9 +135,10 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ block_
 }
 
 // in and out may alias (in-place scan): each thread reads its items before the
-// block barrier and writes only those items afterwards.
-__global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* in, uint32_t* out,
-                                                        const uint32_t* __restrict__ block_sums,
+// block barrier and writes only those items afterwards.  Strides are in
+// elements (2 for the tile counts that sit in the ranges array).
+__global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* in, int in_stride, uint32_t* out,
+                                                        int out_stride, const uint32_t* __restrict__ block_sums,
                                                         const uint32_t* __restrict__ n_dev) {
   __shared__ uint32_t s_warp[kThreads / 32 + 1];
   const uint32_t n = *n_dev;
@@ -128,144 +150,29 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* in, uint
   uint32_t sum = 0;
 #pragma unroll
   for (int r = 0; r < kIPT; ++r) {
-    x[r] = (base + r < n) ? in[base + r] : 0u;
+    x[r] = (base + r < n) ? in[(base + r) * in_stride] : 0u;
     sum += x[r];
   }
   uint32_t total;
   uint32_t run = block_exclusive_scan(sum, s_warp, &total) + block_sums[b];
 #pragma unroll
   for (int r = 0; r < kIPT; ++r) {
-    if (base + r < n) out[base + r] = run;
+    if (base + r < n) out[(base + r) * out_stride] = run;
     run += x[r];
   }
 }
 
-// ---------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys,
-                                                         const uint32_t* __restrict__ n_dev,
-                                                         int shift, uint32_t* __restrict__ hist,
-                                                         uint32_t* __restrict__ hist_n_dev) {
-  __shared__ uint32_t s_h[kRadixDigits];
-  const uint32_t n = *n_dev;
-  const uint32_t nb = num_blocks(n);
-  const uint32_t b = blockIdx.x;
-  if (b == 0 && threadIdx.x == 0) *hist_n_dev = kRadixDigits * nb;
-  if (b >= nb) return;
-  s_h[threadIdx.x] = 0;
-  __syncthreads();
-  const uint64_t base = (uint64_t)b * kItemsPerBlock;
-#pragma unroll
-  for (int r = 0; r < kIPT; ++r) {
-    uint64_t idx = base + (uint64_t)r * kThreads + threadIdx.x;
-    if (idx < n) atomicAdd(&s_h[(keys[idx] >> shift) & (kRadixDigits - 1)], 1u);
-  }
-  __syncthreads();
-  // digit-major layout: all blocks of digit 0, then digit 1, ...
-  hist[(uint64_t)threadIdx.x * nb + b] = s_h[threadIdx.x];
-}
-
-// Each warp ranks 256 consecutive items (8 rounds of 32) with __match_any_sync;
-// the block's offset for a digit is the scanned histogram entry, the warp's
-// offset is the count of that digit in earlier warps: order is preserved.
-__global__ void __launch_bounds__(kThreads) k_radix_scatter(
-    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-    const uint32_t* __restrict__ n_dev, int shift, const uint32_t* __restrict__ hist_scanned,
-    uint32_t n_cap) {
-  __shared__ uint32_t s_wh[kThreads / 32][kRadixDigits];
-  __shared__ uint32_t s_bo[kRadixDigits];
-  const uint32_t n = *n_dev;
-  const uint32_t nb = num_blocks(n);
-  const uint32_t b = blockIdx.x;
-  if (b >= nb) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int w = 0; w < kThreads / 32; ++w) s_wh[w][threadIdx.x] = 0;
-  s_bo[threadIdx.x] = hist_scanned[(uint64_t)threadIdx.x * nb + b];
-  __syncthreads();
-  const uint64_t wbase = (uint64_t)b * kItemsPerBlock + (uint64_t)warp * (32 * kIPT);
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  uint32_t key[kIPT], val[kIPT], rank[kIPT], dig[kIPT];
-#pragma unroll
-  for (int r = 0; r < kIPT; ++r) {
-    const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
-    const bool ok = idx < n;
-    key[r] = ok ? keys_in[idx] : 0u;
-    val[r] = ok ? vals_in[idx] : 0u;
-    dig[r] = ok ? ((key[r] >> shift) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
-    const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
-    uint32_t prev = 0;
-    if (ok) prev = s_wh[warp][dig[r]];
-    __syncwarp();
-    if (ok && lane == __ffs(peers) - 1) s_wh[warp][dig[r]] = prev + __popc(peers);
-    __syncwarp();
-    rank[r] = prev + __popc(peers & lt_mask);
-  }
-  __syncthreads();
-  {
-    // exclusive scan over warps for digit threadIdx.x
-    uint32_t run = 0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-      uint32_t c = s_wh[w][threadIdx.x];
-      s_wh[w][threadIdx.x] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < kIPT; ++r) {
-    if (dig[r] < (uint32_t)kRadixDigits) {
-      const uint32_t pos = s_bo[dig[r]] + s_wh[warp][dig[r]] + rank[r];
-      if (pos < n_cap) {  // always true for a consistent histogram
-        keys_out[pos] = key[r];
-        vals_out[pos] = val[r];
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
-// Item and pair kernels
+// Pair kernels
 // ---------------------------------------------------------------------------
-__global__ void k_visible_flags(const uint32_t* __restrict__ touched, int64_t m,
-                                uint32_t* __restrict__ flags) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) flags[i] = touched[i] > 0u ? 1u : 0u;
-}
-
-__global__ void k_compact(const uint32_t* __restrict__ touched, const float* __restrict__ depth,
-                          const uint32_t* __restrict__ offs, int64_t m,
-                          uint32_t* __restrict__ dkeys, uint32_t* __restrict__ items) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m || touched[i] == 0u) return;
-  const uint32_t o = offs[i];
-  dkeys[o] = __float_as_uint(depth[i]);  // positive floats order like their bits
-  items[o] = (uint32_t)i;
-}
-
 // Status bits written to counts[2]: 1 = pair capacity exceeded, 2 = an index
 // read from an earlier stage was out of range (the access was skipped).
 constexpr uint32_t kStatusCapacity = 1u, kStatusIndex = 2u;
 
-__global__ void k_pair_counts(const uint32_t* __restrict__ items, const uint32_t* __restrict__ touched,
-                              const uint32_t* __restrict__ n_dev, int64_t m, uint32_t* __restrict__ cnt,
-                              uint32_t* __restrict__ counts) {
-  uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= *n_dev || (int64_t)j >= m) return;
-  const uint32_t it = items[j];
-  if ((int64_t)it >= m) {
-    cnt[j] = 0;
-    atomicOr(&counts[2], kStatusIndex);
-    return;
-  }
-  cnt[j] = touched[it];
-}
-
-__global__ void k_init_counts(uint32_t* counts, uint32_t* m_dev, uint32_t m) {
-  *m_dev = m;  // live length of the first (item) scan; its total goes to counts[0]
+__global__ void k_init_counts(uint32_t* counts, uint32_t* scalars, uint32_t m, uint32_t tiles) {
+  scalars[0] = m;      // live length of the item scan
+  scalars[1] = tiles;  // live length of the tile scan
   counts[0] = 0; counts[1] = 0; counts[2] = 0; counts[3] = 0;
 }
 
@@ -275,98 +182,245 @@ __global__ void k_pair_status(uint32_t* counts, int64_t cap) {
   counts[3] = (int64_t)K > cap ? (uint32_t)cap : K;
 }
 
-struct EmitArgs {
-  const uint32_t* items;
-  const uint32_t* poff;
+struct PairArgs {
+  const uint32_t* touched;
   const uint2* rect;
-  const uint32_t* counts;
+  const float* depth;
+  const uint32_t* pair_off;  // emission offset of every (view, Gaussian)
+  uint32_t* counts;
   int64_t n;
   int64_t cap;
-  uint32_t* pair_off;
-  uint32_t* tkeys;
-  uint32_t* tvals;
+  uint32_t* ranges;          // [tiles][2]: (start, count) while binning
+  uint32_t* slot;            // [cap] place of each pair within its tile
+  uint64_t* keys;            // [cap] (depth bits << 32 | id) at the pair's list position
 };
 
-// Warp-cooperative emission: each warp takes 32 consecutive items (in depth
-// order); lane l loads item l's record, then the warp emits the items one
-// after another with its 32 lanes striding over the item's tiles, so a splat
-// covering hundreds of tiles is written by 32 lanes and consecutive pairs are
-// written by consecutive lanes (coalesced).
-__global__ void __launch_bounds__(256) k_emit(const EmitArgs a, const ViewTable vt) {
-  const uint32_t M = a.counts[0];
+// Warp-cooperative walk over the pairs of 32 consecutive (view, Gaussian)
+// items: the warp scans the items' pair counts and its lanes take the pairs
+// 32 at a time, each finding its item by a binary search over the scan, so
+// the lanes stay busy whatever the mix of small and large splats and every
+// pair's memory operations of a round are in flight together.  Pairs of an
+// item are its rect's tiles in row-major order.
+// PLACE: take each pair's place in its tile (count the tile, note the place);
+// otherwise write its key at the tile's start + place.
+template <bool PLACE>
+__global__ void __launch_bounds__(256) k_pairs(const PairArgs a, const ViewTable vt) {
+  const int64_t m = a.n * vt.views;
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const uint32_t j0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
-  if (j0 >= M || (int64_t)j0 >= a.n * vt.views) return;
-  const uint32_t j = j0 + lane;
-  const int64_t total = a.n * vt.views;
-  bool ok = j < M && (int64_t)j < total;
-  uint32_t item = 0, off = 0, rx = 1u, ry = 0u;
-  int v = 0;
+  const int64_t j0 = ((int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  if (j0 >= m) return;  // warp-uniform
+  const int64_t j = j0 + lane;
+  bool ok = j < m && a.touched[j] > 0u;
+  if (PLACE) {
+    const unsigned vis = __ballot_sync(full, ok);
+    if (lane == 0 && vis) atomicAdd(&a.counts[0], (uint32_t)__popc(vis));
+  }
+  uint32_t off = 0, x0y0 = 0, w = 1, cnt = 0, key_hi = 0, tb = 0, tx_n = 1, gid = 0;
   if (ok) {
-    item = a.items[j];
-    if ((int64_t)item >= total) {
-      atomicOr(const_cast<uint32_t*>(&a.counts[2]), kStatusIndex);
+    const int v = (int)(j / a.n);
+    off = a.pair_off[j];
+    const uint2 rc = a.rect[j];
+    const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
+    if (x1 >= vt.v[v].TX || y1 >= vt.v[v].TY || x0 > x1 || y0 > y1) {
+      atomicOr(&a.counts[2], kStatusIndex);
       ok = false;
     } else {
-      v = (int)(item / (uint64_t)a.n);
-      off = a.poff[j];
-      a.pair_off[item] = off;
-      const uint2 rc = a.rect[item];
-      rx = rc.x;
-      ry = rc.y;
-      if ((int)(ry & 0xffff) >= vt.v[v].TX || (int)(ry >> 16) >= vt.v[v].TY) {
-        atomicOr(const_cast<uint32_t*>(&a.counts[2]), kStatusIndex);
-        ok = false;
+      x0y0 = rc.x;
+      w = (uint32_t)(x1 - x0 + 1);
+      // never beyond the item's own block of slots
+      cnt = min(w * (uint32_t)(y1 - y0 + 1), a.touched[j]);
+      tb = (uint32_t)vt.v[v].tile_base;
+      tx_n = (uint32_t)vt.v[v].TX;
+      if (!PLACE) {
+        key_hi = __float_as_uint(a.depth[j]);  // positive floats order like their bits
+        gid = (uint32_t)(j - (int64_t)v * a.n);
       }
     }
   }
-  for (int src = 0; src < 32; ++src) {
-    const bool sok = __shfl_sync(0xffffffffu, ok, src);
-    const uint32_t sitem = __shfl_sync(0xffffffffu, item, src);
-    const uint32_t soff = __shfl_sync(0xffffffffu, off, src);
-    const uint32_t sx = __shfl_sync(0xffffffffu, rx, src);
-    const uint32_t sy = __shfl_sync(0xffffffffu, ry, src);
-    const int sv = __shfl_sync(0xffffffffu, v, src);
-    if (!sok) continue;
-    const int x0 = sx & 0xffff, y0 = sx >> 16, x1 = sy & 0xffff, y1 = sy >> 16;
-    const int w = x1 - x0 + 1;
-    const int cnt = w * (y1 - y0 + 1);
-    const int TX = vt.v[sv].TX;
-    const uint32_t tb = (uint32_t)vt.v[sv].tile_base;
-    const uint32_t g = (uint32_t)(sitem - (uint64_t)sv * a.n);
-    for (int t = lane; t < cnt; t += 32) {
-      const uint64_t k = (uint64_t)soff + t;
-      if ((int64_t)k >= a.cap) break;
-      const int ty = y0 + t / w, tx = x0 + t % w;
-      a.tkeys[k] = tb + (uint32_t)(ty * TX + tx);
-      a.tvals[k] = g;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(full, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const uint32_t total = __shfl_sync(full, incl, 31);
+  const uint32_t excl = incl - cnt;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t q = base + lane;
+    // owner: the number of lanes whose inclusive count is <= q
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+      if (__shfl_sync(full, incl, o + step - 1) <= q) o += step;
+    const uint32_t so = __shfl_sync(full, off, o), se = __shfl_sync(full, excl, o);
+    const uint32_t sxy = __shfl_sync(full, x0y0, o), sw = __shfl_sync(full, w, o);
+    const uint32_t stb = __shfl_sync(full, tb, o), stx = __shfl_sync(full, tx_n, o);
+    const uint32_t skey = __shfl_sync(full, key_hi, o), sg = __shfl_sync(full, gid, o);
+    if (q >= total) continue;
+    const uint32_t t = q - se;
+    const uint64_t p = (uint64_t)so + t;
+    if ((int64_t)p >= a.cap) continue;
+    const uint32_t tile = stb + ((sxy >> 16) + t / sw) * stx + (sxy & 0xffff) + t % sw;
+    if (PLACE) {
+      a.slot[p] = atomicAdd(&a.ranges[2 * (uint64_t)tile + 1], 1u);
+    } else {
+      const uint64_t pos = (uint64_t)a.ranges[2 * (uint64_t)tile] + a.slot[p];
+      if ((int64_t)pos < a.cap) {
+        a.keys[pos] = ((uint64_t)skey << 32) | sg;
+      } else {
+        atomicOr(&a.counts[2], kStatusIndex);
+      }
     }
   }
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ tkeys, uint32_t* __restrict__ counts,
-                         uint2* __restrict__ ranges, uint32_t num_tiles) {
-  const uint32_t K = counts[3];
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const uint32_t g = tkeys[k];
-  if (g >= num_tiles) {
-    atomicOr(&counts[2], kStatusIndex);
-    return;
+struct TileSortArgs {
+  uint64_t* keys;       // [cap] tile lists, unsorted
+  uint64_t* keys_b;     // [cap] ping-pong buffer of lists too long for shared memory
+  uint32_t* ranges;     // [tiles][2]: (start, count) in, (start, end) out; (0, 0) when empty
+  uint32_t* vals;       // [cap] Gaussian ids in list order
+  uint64_t* full_keys;  // optional: (tile << 32 | depth bits) in list order
+  int id_bits;          // significant bits of the id (low word)
+};
+
+// One stable CTA-wide LSD radix pass over src[0, cnt) on key bits
+// [lo, lo + 8), writing dst (shared or global memory).  A digit histogram of
+// the whole list gives each digit's base; then, chunk by chunk (2048 keys),
+// warp w ranks its contiguous share of the chunk with __match_any_sync and
+// the keys go after everything of the same digit in earlier warps and chunks.
+// Returns false (and writes nothing) when every key has the same digit: the
+// pass would not move anything.
+__device__ bool cta_radix_pass(const uint64_t* src, uint64_t* dst, uint32_t cnt, int lo, uint32_t* s_base,
+                               uint32_t (*s_wh)[kRadixDigits]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  s_base[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t i0 = 0; i0 < cnt; i0 += kThreads) {
+    const uint32_t i = i0 + threadIdx.x;
+    const bool ok = i < cnt;
+    const uint32_t d = ok ? (uint32_t)(src[i] >> lo) & (kRadixDigits - 1) : 0u;
+    const uint32_t peers = digit_peers(d, ok);
+    if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_base[d], (uint32_t)__popc(peers));
   }
-  if (k == 0 || tkeys[k - 1] != g) ranges[g].x = k;
-  if (k == K - 1 || tkeys[k + 1] != g) ranges[g].y = k + 1;
+  __syncthreads();
+  {
+    uint32_t total;
+    const uint32_t c = s_base[threadIdx.x];
+    const int uniform = __syncthreads_or(c == cnt);
+    if (uniform) return false;
+    s_base[threadIdx.x] = block_exclusive_scan(c, &s_wh[0][0], &total);
+    __syncthreads();
+  }
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (uint32_t c0 = 0; c0 < cnt; c0 += kItemsPerBlock) {
+    const uint32_t cc = min((uint32_t)kItemsPerBlock, cnt - c0);
+    const uint32_t per = (cc + kThreads / 32 - 1) / (kThreads / 32);  // keys per warp
+    const uint32_t w0 = c0 + (uint32_t)warp * per, w1 = c0 + min(cc, (uint32_t)(warp + 1) * per);
+    const int rounds = (int)((per + 31) / 32);
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s_wh[w][threadIdx.x] = 0;
+    __syncthreads();
+    uint64_t key[kIPT];
+    uint32_t rank[kIPT], dig[kIPT];
+#pragma unroll
+    for (int r = 0; r < kIPT; ++r) {
+      dig[r] = (uint32_t)kRadixDigits;
+      if (r < rounds) {
+        const uint32_t idx = w0 + (uint32_t)r * 32 + lane;
+        const bool ok = idx < w1;
+        key[r] = ok ? src[idx] : 0ull;
+        dig[r] = ok ? ((uint32_t)(key[r] >> lo) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+        uint32_t prev = 0;
+        if (ok) prev = s_wh[warp][dig[r]];
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) s_wh[warp][dig[r]] = prev + __popc(peers);
+        __syncwarp();
+        rank[r] = prev + __popc(peers & lt_mask);
+      }
+    }
+    __syncthreads();
+    uint32_t chunk_total = 0;
+    {
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) {
+        const uint32_t c = s_wh[w][threadIdx.x];
+        s_wh[w][threadIdx.x] = run;
+        run += c;
+      }
+      chunk_total = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kIPT; ++r)
+      if (dig[r] < (uint32_t)kRadixDigits) dst[s_base[dig[r]] + s_wh[warp][dig[r]] + rank[r]] = key[r];
+    __syncthreads();
+    s_base[threadIdx.x] += chunk_total;
+    __syncthreads();
+  }
+  return true;
 }
 
-__global__ void k_full_keys(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
-                            const uint32_t* __restrict__ counts, const float* __restrict__ depth,
-                            int64_t n, uint64_t* __restrict__ keys, const ViewTable vt) {
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= counts[3]) return;
-  const uint32_t g = tkeys[k];
-  const int v = view_of_tile(vt, (int)g);
-  const uint32_t gid = vals[k];
-  keys[k] = ((uint64_t)g << 32) | (gid < n ? __float_as_uint(depth[(int64_t)v * n + gid]) : 0u);
+// Stable radix passes over key bits [lo0, lo1) in steps of 8; returns the
+// buffer holding the result.
+__device__ uint64_t* cta_radix_sort(uint64_t* a, uint64_t* b, uint32_t cnt, int lo0, int lo1, uint32_t* s_base,
+                                    uint32_t (*s_wh)[kRadixDigits]) {
+  for (int lo = lo0; lo < lo1; lo += kRadixBits) {
+    if (!cta_radix_pass(a, b, cnt, lo, s_base, s_wh)) continue;
+    uint64_t* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// One CTA per tile: sort the tile's (depth bits << 32 | id) keys, write the
+// ids (and optionally the full keys) and the tile's [start, end) range.
+// Stable passes over the depth bits order the list by depth (a pass whose
+// digit is the same for every key is skipped); a tile in which two keys share
+// a depth is then sorted again over id and depth bits (stable LSD: id first),
+// which leaves equal depths in id order.  Lists of up to kShortList keys are
+// sorted in shared memory, longer ones through global memory.
+__global__ void __launch_bounds__(kThreads) k_tile_sort(const TileSortArgs a) {
+  __shared__ uint64_t s_a[kShortList], s_b[kShortList];
+  __shared__ uint32_t s_base[kRadixDigits];
+  __shared__ uint32_t s_wh[kThreads / 32][kRadixDigits];
+  const uint32_t t = blockIdx.x;
+  const uint32_t start = a.ranges[2 * (uint64_t)t], cnt = a.ranges[2 * (uint64_t)t + 1];
+  if (cnt == 0) {
+    if (threadIdx.x == 0) a.ranges[2 * (uint64_t)t] = 0u;
+    return;
+  }
+  uint64_t *buf_a, *buf_b;
+  if (cnt <= kShortList) {
+    for (uint32_t i = threadIdx.x; i < cnt; i += kThreads) s_a[i] = a.keys[start + i];
+    buf_a = s_a;
+    buf_b = s_b;
+  } else {
+    buf_a = a.keys + start;
+    buf_b = a.keys_b + start;
+  }
+  __syncthreads();
+  uint64_t* sorted = cta_radix_sort(buf_a, buf_b, cnt, 32, 64, s_base, s_wh);
+  bool tie = false;
+  for (uint32_t i = threadIdx.x; i + 1 < cnt; i += kThreads)
+    tie |= (uint32_t)(sorted[i] >> 32) == (uint32_t)(sorted[i + 1] >> 32);
+  if (__syncthreads_or(tie)) {
+    uint64_t* other = sorted == buf_a ? buf_b : buf_a;
+    sorted = cta_radix_sort(sorted, other, cnt, 0, (a.id_bits + kRadixBits - 1) / kRadixBits * kRadixBits,
+                            s_base, s_wh);
+    other = sorted == buf_a ? buf_b : buf_a;
+    sorted = cta_radix_sort(sorted, other, cnt, 32, 64, s_base, s_wh);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < cnt; i += kThreads) {
+    const uint64_t k = sorted[i];
+    a.vals[start + i] = (uint32_t)k;
+    if (a.full_keys) a.full_keys[start + i] = ((uint64_t)t << 32) | (k >> 32);
+  }
+  if (threadIdx.x == 0) a.ranges[2 * (uint64_t)t + 1] = start + cnt;
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -380,58 +434,23 @@ size_t scan_workspace(int64_t n_cap) {
   return align_up(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, (n_cap + kItemsPerBlock - 1) / kItemsPerBlock), 256);
 }
 
-gs_status launch_scan(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, int64_t n_cap,
-                      uint32_t* total_dev, void* ws, cudaStream_t s) {
+gs_status launch_scan(const uint32_t* in, int in_stride, uint32_t* out, int out_stride, const uint32_t* n_dev,
+                      int64_t n_cap, uint32_t* total_dev, void* ws, cudaStream_t s) {
   uint32_t* block_sums = static_cast<uint32_t*>(ws);
   const unsigned nb = grid_for(n_cap, kItemsPerBlock);
-  k_scan_reduce<<<nb, kThreads, 0, s>>>(in, n_dev, block_sums);
+  k_scan_reduce<<<nb, kThreads, 0, s>>>(in, in_stride, n_dev, block_sums);
   k_scan_top<<<1, 1024, 0, s>>>(block_sums, n_dev, total_dev);
-  k_scan_down<<<nb, kThreads, 0, s>>>(in, out, block_sums, n_dev);
+  k_scan_down<<<nb, kThreads, 0, s>>>(in, in_stride, out, out_stride, block_sums, n_dev);
   return check_launch("scan");
 }
 
-size_t radix_workspace(int64_t n_cap) {
-  const int64_t nb = std::max<int64_t>(1, (n_cap + kItemsPerBlock - 1) / kItemsPerBlock);
-  return align_up(sizeof(uint32_t) * kRadixDigits * nb, 256) + scan_workspace(kRadixDigits * nb) + 256;
-}
-
-gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
-                            uint32_t* keys_out, uint32_t* vals_out, const uint32_t* n_dev,
-                            int64_t n_cap, int bits, void* ws, cudaStream_t s) {
-  const int64_t nb = std::max<int64_t>(1, (n_cap + kItemsPerBlock - 1) / kItemsPerBlock);
-  char* w = static_cast<char*>(ws);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(w);
-  w += align_up(sizeof(uint32_t) * kRadixDigits * nb, 256);
-  void* scan_ws = w;
-  w += scan_workspace(kRadixDigits * nb);
-  uint32_t* hist_n = reinterpret_cast<uint32_t*>(w);
-  uint32_t* hist_total = hist_n + 1;
-  const int passes = std::max(1, (bits + kRadixBits - 1) / kRadixBits);
-  const uint32_t* ksrc = keys_a;
-  const uint32_t* vsrc = vals_a;
-  for (int p = 0; p < passes; ++p) {
-    uint32_t* kdst = (p == passes - 1) ? keys_out : ((p & 1) == 0 ? keys_b : keys_a);
-    uint32_t* vdst = (p == passes - 1) ? vals_out : ((p & 1) == 0 ? vals_b : vals_a);
-    const int shift = p * kRadixBits;
-    k_radix_hist<<<(unsigned)nb, kThreads, 0, s>>>(ksrc, n_dev, shift, hist, hist_n);
-    gs_status st = launch_scan(hist, hist, hist_n, kRadixDigits * nb, hist_total, scan_ws, s);
-    if (st != GS_OK) return st;
-    k_radix_scatter<<<(unsigned)nb, kThreads, 0, s>>>(ksrc, vsrc, kdst, vdst, n_dev, shift, hist,
-                                                       (uint32_t)n_cap);
-    ksrc = kdst;
-    vsrc = vdst;
-  }
-  return check_launch("radix_sort");
-}
-
 // ---------------------------------------------------------------------------
-// Workspace of gs_bin_sort: item arrays sized n*V, pair arrays sized capacity.
+// Workspace of gs_bin_sort: pair arrays sized capacity, one scan workspace.
 // ---------------------------------------------------------------------------
 struct BinWs {
-  uint32_t* scalars;  // [0] = item count m (input length of the first scan)
-  uint32_t *offs, *dk_a, *it_a, *dk_b, *it_b, *dk_s, *it_s, *cnt;
-  uint32_t *tk_a, *tv_a, *tk_b, *tv_b, *tk_s;
-  void* radix;
+  uint32_t* scalars;  // [0] = item count, [1] = tile count, [2] = scanned tile total
+  uint32_t* slot;
+  uint64_t *keys_a, *keys_b;
   void* scan;
   size_t bytes;
 };
@@ -444,24 +463,19 @@ static BinWs bin_layout(char* base, int64_t m, int64_t cap) {
     off += align_up(bytes, 256);
     return p;
   };
-  const size_t mi = sizeof(uint32_t) * (size_t)std::max<int64_t>(1, m);
-  const size_t ci = sizeof(uint32_t) * (size_t)std::max<int64_t>(1, cap);
+  const size_t c = (size_t)std::max<int64_t>(1, cap);
   w.scalars = (uint32_t*)take(16);
-  w.offs = (uint32_t*)take(mi);
-  w.dk_a = (uint32_t*)take(mi); w.it_a = (uint32_t*)take(mi);
-  w.dk_b = (uint32_t*)take(mi); w.it_b = (uint32_t*)take(mi);
-  w.dk_s = (uint32_t*)take(mi); w.it_s = (uint32_t*)take(mi);
-  w.cnt = (uint32_t*)take(mi);
-  w.tk_a = (uint32_t*)take(ci); w.tv_a = (uint32_t*)take(ci);
-  w.tk_b = (uint32_t*)take(ci); w.tv_b = (uint32_t*)take(ci);
-  w.tk_s = (uint32_t*)take(ci);
-  w.radix = take(radix_workspace(std::max(m, cap)));
-  w.scan = take(scan_workspace(std::max(m, cap)));
+  w.slot = (uint32_t*)take(sizeof(uint32_t) * c);
+  w.keys_a = (uint64_t*)take(sizeof(uint64_t) * c);
+  w.keys_b = (uint64_t*)take(sizeof(uint64_t) * c);
+  w.scan = take(scan_workspace(std::max(m, kMaxScanTiles)));
   w.bytes = off;
   return w;
 }
 
 size_t bin_sort_workspace_bytes(int64_t m, int64_t cap) { return bin_layout(nullptr, m, cap).bytes; }
+
+int64_t bin_sort_max_tiles() { return kMaxScanTiles; }
 
 gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bins& bins, void* ws,
                           cudaStream_t s) {
@@ -469,40 +483,29 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   const int64_t cap = bins.capacity;
   BinWs w = bin_layout(static_cast<char*>(ws), m, cap);
   uint32_t* counts = bins.counts;
-  const int T = 256;
-  k_init_counts<<<1, 1, 0, s>>>(counts, w.scalars, (uint32_t)m);
+  k_init_counts<<<1, 1, 0, s>>>(counts, w.scalars, (uint32_t)m, (uint32_t)vt.total_tiles);
+  // the ranges array holds each tile's (start, count) until the tile is sorted
   if (cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)bins.num_tiles, s) != cudaSuccess)
     return check_launch("memset ranges");
   if (m == 0) return check_launch("bin_sort");
-  // 1. compact the visible items in (view, id) order with their depth keys
-  k_visible_flags<<<grid_for(m, T), T, 0, s>>>(sp.touched, m, w.offs);
-  // the scan's length (m) and its total (visible items -> counts[0]) must not alias
-  gs_status st = launch_scan(w.offs, w.offs, w.scalars, m, counts, w.scan, s);
-  if (st != GS_OK) return st;
-  k_compact<<<grid_for(m, T), T, 0, s>>>(sp.touched, sp.depth, w.offs, m, w.dk_a, w.it_a);
-  // 2. stable sort of the visible items by depth
-  st = launch_radix_sort(w.dk_a, w.it_a, w.dk_b, w.it_b, w.dk_s, w.it_s, counts, m, 32, w.radix, s);
-  if (st != GS_OK) return st;
-  // 3. pair offsets in depth order, emission, pair count status
-  k_pair_counts<<<grid_for(m, T), T, 0, s>>>(w.it_s, sp.touched, counts, m, w.cnt, counts);
-  st = launch_scan(w.cnt, w.cnt, counts, m, counts + 1, w.scan, s);
+  // 1. pair slots per (view, Gaussian): exclusive scan of the tile counts
+  gs_status st = launch_scan(sp.touched, 1, bins.pair_off, 1, w.scalars, m, counts + 1, w.scan, s);
   if (st != GS_OK) return st;
   k_pair_status<<<1, 1, 0, s>>>(counts, cap);
-  EmitArgs ea{w.it_s, w.cnt, reinterpret_cast<const uint2*>(sp.rect), counts, sp.n, cap,
-              bins.pair_off, w.tk_a, w.tv_a};
-  k_emit<<<grid_for(m, T), T, 0, s>>>(ea, vt);
-  // 4. stable sort of the pairs by global tile on its significant bits
-  int bits = 1;
-  while ((1ll << bits) < (int64_t)vt.total_tiles) ++bits;
-  if (cap > 0) {
-    st = launch_radix_sort(w.tk_a, w.tv_a, w.tk_b, w.tv_b, w.tk_s, bins.vals, counts + 3, cap, bits,
-                           w.radix, s);
-    if (st != GS_OK) return st;
-    k_ranges<<<grid_for(cap, T), T, 0, s>>>(w.tk_s, counts, reinterpret_cast<uint2*>(bins.ranges),
-                                            (uint32_t)bins.num_tiles);
-    if (bins.keys)
-      k_full_keys<<<grid_for(cap, T), T, 0, s>>>(w.tk_s, bins.vals, counts, sp.depth, sp.n, bins.keys, vt);
-  }
+  if (cap == 0 || vt.total_tiles == 0) return check_launch("bin_sort");
+  PairArgs pa{sp.touched, reinterpret_cast<const uint2*>(sp.rect), sp.depth, bins.pair_off, counts, sp.n, cap,
+              bins.ranges, w.slot, w.keys_a};
+  const unsigned pgrid = grid_for(m, 256);  // 8 warps of 32 items per block
+  // 2. a place in its tile for every pair; 3. list starts; keys at their places
+  k_pairs<true><<<pgrid, 256, 0, s>>>(pa, vt);
+  st = launch_scan(bins.ranges + 1, 2, bins.ranges, 2, w.scalars + 1, vt.total_tiles, w.scalars + 2, w.scan, s);
+  if (st != GS_OK) return st;
+  k_pairs<false><<<pgrid, 256, 0, s>>>(pa, vt);
+  // 4. every tile's list by (depth bits, id)
+  int id_bits = 1;
+  while (id_bits < 32 && (1ll << id_bits) < sp.n) ++id_bits;
+  TileSortArgs ta{w.keys_a, w.keys_b, bins.ranges, bins.vals, reinterpret_cast<uint64_t*>(bins.keys), id_bits};
+  k_tile_sort<<<(unsigned)vt.total_tiles, kThreads, 0, s>>>(ta);
   return check_launch("bin_sort");
 }
 

@@ -25,19 +25,14 @@ bool make_view_table(const gs_camera* cams, int views, ViewTable* vt);
 gs_status launch_project(const gs_params& p, const float* poses, const ViewTable& vt,
                          const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s);
 
-// Exclusive scan of n_cap u32 values (in place allowed); the number of valid
-// entries is *n_dev (device); the total goes to *total_dev.
+// Exclusive scan of n_cap u32 values read every in_stride and written every
+// out_stride elements (in place allowed); the number of valid entries is
+// *n_dev (device); the total goes to *total_dev.
 size_t scan_workspace(int64_t n_cap);
-gs_status launch_scan(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, int64_t n_cap,
-                      uint32_t* total_dev, void* ws, cudaStream_t s);
-
-// Stable LSD radix sort of (key, value) u32 pairs on key bits [0, bits);
-// count *n_dev (device) <= n_cap.  keys/vals ping-pong between the *_a and
-// *_b buffers; the result lands in (keys_out, vals_out).
-size_t radix_workspace(int64_t n_cap);
-gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
-                            uint32_t* keys_out, uint32_t* vals_out, const uint32_t* n_dev,
-                            int64_t n_cap, int bits, void* ws, cudaStream_t s);
+gs_status launch_scan(const uint32_t* in, int in_stride, uint32_t* out, int out_stride, const uint32_t* n_dev,
+                      int64_t n_cap, uint32_t* total_dev, void* ws, cudaStream_t s);
+// Largest number of tiles (all views) the binning workspace is sized for.
+int64_t bin_sort_max_tiles();
 
 gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                             const gs_raster_cfg& cfg, float* image, float* alpha, cudaStream_t s);

@@ -139,6 +139,48 @@ def test_bins_bit_exact_on_records(cuda_device, shape):
     assert np.array_equal(starts[order][1:], np.cumsum(lens[order])[:-1])
 
 
+def test_bins_bit_exact_long_tile_lists(cuda_device):
+    """Tile lists longer than the shared-memory sort (4096 pairs) take the
+    CTA-wide radix sort: every record covers the whole 4x3-tile view, with
+    three depth levels so that the id order of equal depths is exercised."""
+    tiles = [(4, 3)]
+    n = 9000
+    g = np.random.default_rng(77)
+    depth = np.zeros((1, n), np.float32)
+    depth[0] = np.float32([0.5, 2.0, 7.25])[g.integers(0, 3, n)]
+    rect = np.zeros((1, n, 4), np.int32)
+    rect[0, :, 2], rect[0, :, 3] = 3, 2
+    culled = g.random(n) < 0.2
+    rect[0, culled] = (1, 1, 0, 0)
+    rect[0, :50] = (1, 0, 2, 1)  # a few smaller footprints
+    keys_o, vals_o, ranges_o = oracle.bin_records(depth, rect, tiles)
+    lens = ranges_o[:, 1] - ranges_o[:, 0]
+    assert lens.max() > 4096
+    cams = [synth.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 100.0, 100.0, 0.0, 0.0, 64, 48)]
+    from paper_2607_14481_b300 import raster
+    from gpu_util import ensure_built
+    ensure_built()
+    r = raster.Rasterizer(n, 0, cams, capacity=len(keys_o) + 5, device=cuda_device, keep_keys=True)
+    sv = r.splat_views()
+    sv["depth"].copy_(torch.from_numpy(depth))
+    packed = np.zeros((1, n, 2), np.uint32)
+    packed[..., 0] = rect[..., 0].astype(np.uint32) | (rect[..., 1].astype(np.uint32) << 16)
+    packed[..., 1] = rect[..., 2].astype(np.uint32) | (rect[..., 3].astype(np.uint32) << 16)
+    sv["rect"].copy_(torch.from_numpy(packed.view(np.int32)))
+    ok = (rect[..., 0] <= rect[..., 2]) & (rect[..., 1] <= rect[..., 3])
+    touched = np.where(ok, (rect[..., 2] - rect[..., 0] + 1) * (rect[..., 3] - rect[..., 1] + 1), 0)
+    sv["touched"].copy_(torch.from_numpy(touched.astype(np.int32)))
+    for _ in range(2):
+        r.bin_sort()
+        torch.cuda.synchronize()
+        K = len(keys_o)
+        cnt = r.read_counts()
+        assert cnt[1] == K and cnt[2] == 0 and cnt[3] == K
+        assert np.array_equal(r.keys[:K].cpu().numpy().view(np.uint64), keys_o)
+        assert np.array_equal(r.vals[:K].cpu().numpy().view(np.uint32), vals_o)
+        assert np.array_equal(r.ranges[:2 * r.num_tiles].cpu().numpy().view(np.uint32).reshape(-1, 2), ranges_o)
+
+
 def test_bins_capacity_overflow_is_flagged_and_recovered(cuda_device):
     sc, cams, _ = synth.plain_small()
     r, arena, poses, img, alpha = gpu_forward(sc, cams, capacity=64)

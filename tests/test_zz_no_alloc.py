@@ -63,8 +63,8 @@ def test_noalloc_sort_rejects_oversize(cuda_device):
     dev = torch.device("cuda:0")
     sc = synth.random_scene(70000, 3, 0, (-1, -1, -1), (1, 1, 1), -3.5, 0.4)
     cams = synth.plain_small()[1]
-    r = raster.Rasterizer(sc.n, sc.sh_degree, cams, capacity=300000, device=dev)
-    need = r.L.gs_bin_sort_workspace(sc.n, 1, 300000)
+    r = raster.Rasterizer(sc.n, sc.sh_degree, cams, capacity=1_000_000, device=dev)
+    need = r.L.gs_bin_sort_workspace(sc.n, 1, 1_000_000)
     assert need > _lib.GS_NOALLOC_SCRATCH_BYTES
     arena = raster.Arena.from_scene(sc, dev)
     r.project(arena, raster.poses_tensor(cams, dev))
