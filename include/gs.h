@@ -240,9 +240,12 @@ GS_API size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity);
 /* Tile binning: every visible (view, Gaussian) emits one pair per tile of its
  * rect; pairs are sorted by (global tile, depth bits) with equal keys in
  * Gaussian-id order, and each tile's [start, end) range is written.  The sort
- * is two stable LSD radix sorts written for this library: depth keys of the
- * visible items (32 bits), then the emitted pairs by global tile (only the
- * significant tile bits).  No host synchronisation: K stays on the device
+ * is a counting sort by tile (each pair takes a place in its tile list with
+ * one atomic; a scan over the tiles gives the list starts) followed by a sort
+ * of every tile's own (depth bits, id) keys by one CTA (in shared memory up
+ * to 4096 pairs, else by a CTA-wide stable radix sort); the keys of one tile
+ * are distinct, so the result does not depend on the atomics' order.  At most
+ * 2^25 tiles over all views.  No host synchronisation: K stays on the device
  * (counts).  ws: device, >= gs_bin_sort_workspace bytes, 256-byte aligned. */
 GS_API gs_status gs_bin_sort(const gs_splats* splats, const gs_camera* cams, int32_t views,
                       const gs_raster_cfg* cfg, gs_bins* out, void* ws, size_t ws_bytes,
@@ -402,7 +405,8 @@ typedef struct {
 typedef struct {
   int64_t submitted, completed, failed, queued, inflight;
   int64_t iterations;        /* Adam steps taken (batches with train views) */
-  int64_t batches;
+  int64_t batches;           /* batches issued, capacity retries included */
+  int64_t retries;           /* batch parts issued again after a pair-capacity overflow */
   int64_t gaussians;         /* active Gaussians */
   double pixels;             /* pixels of completed requests */
   double p50_ms, p99_ms, mean_ms, max_ms;  /* arrival -> completion, completed requests */
@@ -441,6 +445,12 @@ GS_API gs_status gs_session_poll(gs_session* s, int64_t id, int32_t* done);
 GS_API gs_status gs_session_wait(gs_session* s, int64_t id, int32_t timeout_ms);
 /* Waits up to timeout_ms until nothing is queued or in flight. */
 GS_API gs_status gs_session_drain(gs_session* s, int32_t timeout_ms);
+/* on != 0 pauses admission: submitted requests queue up and no new batch is
+ * formed (batches in flight complete); on == 0 resumes, and the queued
+ * requests are batched together.  For a client that submits one frame's
+ * requests as a group.  Waiting on a held request times out; destroying a
+ * held session still drains its queue. */
+GS_API gs_status gs_session_hold(gs_session* s, int32_t on);
 GS_API gs_status gs_session_stats(gs_session* s, gs_stats* out);
 /* Copies the active parameters to host arrays in the library layout (each
  * pointer may be NULL): means4 [n][4], scale_opa [n][4], quat [n][4], sh

@@ -23,7 +23,7 @@ EXPORTED = (
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
-    "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_stats", "gs_session_read_params",
+    "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_stats", "gs_session_read_params",
     "gs_session_save", "gs_session_load", "gs_session_destroy",
 )
 
@@ -94,7 +94,7 @@ class GsRequest(C.Structure):
 
 class GsStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64),
-                ("inflight", C.c_int64), ("iterations", C.c_int64), ("batches", C.c_int64),
+                ("inflight", C.c_int64), ("iterations", C.c_int64), ("batches", C.c_int64), ("retries", C.c_int64),
                 ("gaussians", C.c_int64), ("pixels", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
                 ("mean_ms", C.c_double), ("max_ms", C.c_double), ("wall_s", C.c_double),
                 ("hbm_in_use", C.c_uint64), ("hbm_budget", C.c_uint64), ("contexts", C.c_int32)]
@@ -155,13 +155,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_session_poll.argtypes = [vp, i64, P(i32)]
     L.gs_session_wait.argtypes = [vp, i64, i32]
     L.gs_session_drain.argtypes = [vp, i32]
+    L.gs_session_hold.argtypes = [vp, i32]
     L.gs_session_stats.argtypes = [vp, P(GsStats)]
     L.gs_session_read_params.argtypes = [vp, vp, vp, vp, vp]
     L.gs_session_save.argtypes = [vp, C.c_char_p]
     L.gs_session_load.argtypes = [vp, C.c_char_p]
     L.gs_session_destroy.argtypes = [vp]
     for name in ("gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
-                 "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_stats",
+                 "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_stats",
                  "gs_session_read_params", "gs_session_save", "gs_session_load", "gs_session_destroy"):
         getattr(L, name).restype = C.c_int
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",

@@ -104,9 +104,10 @@ struct gs_session {
   std::deque<gs::Ctx*> inflight;
   std::vector<std::shared_ptr<gs::Req>> all;  // index = id - 1
   std::vector<double> latencies;
-  int64_t iterations = 0, batches = 0, completed = 0, failed = 0;
+  int64_t iterations = 0, batches = 0, retries = 0, completed = 0, failed = 0;
   double pixels = 0.0, created_at = 0.0;
   bool stop = false;
+  bool hold = false;  // admission paused: requests queue up, no batch is formed
   gs_status fatal = GS_OK;
   std::thread worker, completer;
 };
@@ -394,7 +395,7 @@ void worker_main(gs_session* S) {
     // still send its requests back (pair capacity retry)
     S->cv_work.wait(lk, [&] {
       return (S->stop && S->queue.empty() && S->inflight.empty()) ||
-             (!S->queue.empty() && free_ctx_of(S) != nullptr);
+             (!S->queue.empty() && (!S->hold || S->stop) && free_ctx_of(S) != nullptr);
     });
     if (S->queue.empty()) break;  // stop requested and drained
     Ctx* c = free_ctx_of(S);
@@ -482,6 +483,7 @@ void completer_main(gs_session* S) {
         st = alloc_pair_buffers(S, *c, want);
       }
       if (c->has_train && !(strn & 1u)) S->iterations++;
+      if (st == GS_OK) S->retries++;
       for (auto it = c->reqs.rbegin(); it != c->reqs.rend(); ++it) {
         Req* r = it->get();
         const bool over = ((r->kind == GS_REQUEST_TRAIN ? strn : sr) & 1u) != 0;
@@ -728,6 +730,14 @@ gs_status gs_session_wait(gs_session* S, int64_t id, int32_t timeout_ms) {
   return r->state == 3 ? gs::fail(r->status, "request %lld failed", (long long)id) : GS_OK;
 }
 
+gs_status gs_session_hold(gs_session* S, int32_t on) {
+  if (!S) return gs::fail(GS_ERR_INVALID, "NULL session");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->hold = on != 0;
+  S->cv_work.notify_all();
+  return GS_OK;
+}
+
 gs_status gs_session_drain(gs_session* S, int32_t timeout_ms) {
   if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
   std::unique_lock<std::mutex> lk(S->mu);
@@ -747,6 +757,7 @@ gs_status gs_session_stats(gs_session* S, gs_stats* out) {
   st.inflight = inflight;
   st.iterations = S->iterations;
   st.batches = S->batches;
+  st.retries = S->retries;
   st.gaussians = S->n_active;
   st.pixels = S->pixels;
   st.wall_s = gs::steady_now() - S->created_at;

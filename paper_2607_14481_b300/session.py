@@ -95,6 +95,11 @@ class Session:
     def image(self, rid: int) -> Optional[np.ndarray]:
         return self._keep.get(rid)
 
+    def hold(self, on: bool = True) -> None:
+        """Pause (or resume) admission: requests submitted while held are
+        batched together on resume."""
+        _lib.check(self.L.gs_session_hold(self.h, int(bool(on))), "gs_session_hold")
+
     def drain(self, timeout_ms: int = 120000) -> None:
         _lib.check(self.L.gs_session_drain(self.h, timeout_ms), "gs_session_drain")
 
