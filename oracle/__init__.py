@@ -257,3 +257,98 @@ def mse_loss(images: Sequence[np.ndarray], targets: Sequence[np.ndarray]):
     d = [np.asarray(i, np.float64) - t for i, t in zip(images, targets)]
     loss = sum((x * x).sum() for x in d) / n
     return loss, [2.0 * x / n for x in d]
+
+
+# ---------------------------------------------------------------------------
+# Level-of-detail hierarchy (gs_lod_oracle.cpp)
+# ---------------------------------------------------------------------------
+
+def _lod_lib():
+    L = lib()
+    if not hasattr(L, "_lod_ready"):
+        d = C.POINTER(C.c_double)
+        i64 = C.POINTER(C.c_int64)
+        L.orc_lod_morton.argtypes = [C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_uint32), i64]
+        L.orc_lod_merge.argtypes = [C.c_int, d, d, d, d, d, C.c_int, d, d, d, d, d, d]
+        L.orc_lod_build.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_float), d, d, d, d, d, i64, i64,
+                                    d, d, d, d, d, d]
+        L.orc_lod_build.restype = C.c_int64
+        L.orc_lod_cut.argtypes = [C.c_int64, C.c_int64, d, d, i64, d, C.c_double, C.c_double, C.c_double,
+                                  d, C.POINTER(C.c_uint8), C.POINTER(C.c_uint8)]
+        L._lod_ready = True
+    return L
+
+
+def lod_morton(means32):
+    """Morton codes (10 bits per axis over the bounding box, single-precision
+    quantisation) and the (code, index) order of float32 points [n, 3]."""
+    m = np.ascontiguousarray(means32, np.float32)
+    n = m.shape[0]
+    code = np.zeros(n, np.uint32)
+    order = np.zeros(n, np.int64)
+    _lod_lib().orc_lod_morton(n, m.ctypes.data_as(C.POINTER(C.c_float)), code.ctypes.data_as(C.POINTER(C.c_uint32)),
+                              order.ctypes.data_as(C.POINTER(C.c_int64)))
+    return code, order
+
+
+def _cov3(c6):
+    c = np.asarray(c6)
+    out = np.empty(c.shape[:-1] + (3, 3))
+    out[..., 0, 0], out[..., 0, 1], out[..., 0, 2] = c[..., 0], c[..., 1], c[..., 2]
+    out[..., 1, 0], out[..., 1, 1], out[..., 1, 2] = c[..., 1], c[..., 3], c[..., 4]
+    out[..., 2, 0], out[..., 2, 1], out[..., 2, 2] = c[..., 2], c[..., 4], c[..., 5]
+    return out
+
+
+def lod_merge(means, log_scales, quats, opa_logits, sh):
+    """Moment-matching merge of k children (natural layouts; sh [k, nsh])."""
+    mu, ls, q, o = _f64(means), _f64(log_scales), _f64(quats), _f64(opa_logits).reshape(-1)
+    s = _f64(sh).reshape(len(o), -1)
+    k, nsh = s.shape
+    mean, cov6, lso, qo, oo, sho = np.zeros(3), np.zeros(6), np.zeros(3), np.zeros(4), np.zeros(1), np.zeros(nsh)
+    _lod_lib().orc_lod_merge(k, _p(mu), _p(ls), _p(q), _p(o), _p(s), nsh, _p(mean), _p(cov6), _p(lso), _p(qo),
+                             _p(oo), _p(sho))
+    return {"mean": mean, "cov": _cov3(cov6), "log_scales": lso, "quat": qo, "opa_logit": float(oo[0]), "sh": sho}
+
+
+def lod_build(scene):
+    """Three-level hierarchy over the scene's Gaussians (the leaves).  Node
+    numbering: leaves [0, n), level 1 [n, n + n1), level 2 after.  Returns
+    parent [N] (-1 for roots), n1, n2 and the coarse nodes' parameters."""
+    n = scene.n
+    nc = (scene.sh_degree + 1) ** 2
+    nsh = 3 * nc
+    m32 = np.ascontiguousarray(scene.means, np.float32)
+    mu, ls, q, o = _f64(scene.means), _f64(scene.log_scales), _f64(scene.quats), _f64(scene.opa_logits)
+    sh = _f64(scene.sh).reshape(n, nsh)
+    n1 = (n + 7) // 8
+    n2 = (n1 + 7) // 8
+    k = n1 + n2
+    parent = np.zeros(n + k, np.int64)
+    n1o = np.zeros(1, np.int64)
+    pm, pc, pl, pq, po, ps = (np.zeros((k, 3)), np.zeros((k, 6)), np.zeros((k, 3)), np.zeros((k, 4)), np.zeros(k),
+                              np.zeros((k, nsh)))
+    got = _lod_lib().orc_lod_build(n, nsh, m32.ctypes.data_as(C.POINTER(C.c_float)), _p(mu), _p(ls), _p(q), _p(o),
+                                   _p(sh), parent.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   n1o.ctypes.data_as(C.POINTER(C.c_int64)), _p(pm), _p(pc), _p(pl), _p(pq), _p(po),
+                                   _p(ps))
+    assert got == k and n1o[0] == n1
+    return {"parent": parent, "n1": n1, "n2": n2, "means": pm, "cov": _cov3(pc), "log_scales": pl, "quats": pq,
+            "opa_logits": po, "sh": ps.reshape(k, 3, nc)}
+
+
+def lod_cut(means, log_scales, parent, n_leaf, cam, tau=1.0, znear=0.2):
+    """Screen size of every node and the cut for one camera: selected[i] = 1
+    if node i is rendered; amb[i] = 1 where a decision sits within 1e-5 tau
+    of the threshold."""
+    mu, ls = _f64(means), _f64(log_scales)
+    par = np.ascontiguousarray(parent, np.int64)
+    N = mu.shape[0]
+    pose = _f64(cam.pose12())
+    screen = np.zeros(N)
+    sel = np.zeros(N, np.uint8)
+    amb = np.zeros(N, np.uint8)
+    _lod_lib().orc_lod_cut(N, int(n_leaf), _p(mu), _p(ls), par.ctypes.data_as(C.POINTER(C.c_int64)), _p(pose),
+                           float(cam.fx), float(znear), float(tau), _p(screen),
+                           sel.ctypes.data_as(C.POINTER(C.c_uint8)), amb.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return {"screen": screen, "selected": sel.astype(bool), "amb": amb.astype(bool)}
