@@ -234,6 +234,41 @@ GS_API gs_status gs_splats_carve(void* base, int64_t n, int32_t views, gs_splats
 GS_API gs_status gs_project(const gs_params* params, const float* poses_dev, const gs_camera* cams,
                      int32_t views, const gs_raster_cfg* cfg, gs_splats* out, gs_stream stream);
 
+/* Level-of-detail hierarchy (Sec. 6: coarse nodes hold the parameters of a
+ * merged group of children; rendering descends from the roots until a node's
+ * screen size falls below tau pixels or a leaf is reached).  Three levels:
+ * the n_leaf leaves, level 1 (one node per 8 leaves) and level 2 (one node
+ * per 8 level-1 nodes).  Readings where the paper is silent or differs: it
+ * merges 4 nearest neighbours by a KL criterion; here the leaves are grouped
+ * by Morton order of their means (10 bits per axis over their bounding box,
+ * quantised in single precision, equal codes in index order), runs of 8
+ * consecutive leaves (then of 8 consecutive level-1 nodes) share a parent, and
+ * a parent is the moment-matching merge of its children with weights
+ * w = opacity: the mixture's mean and covariance, opacity-weighted SH and
+ * opacity min(0.99, sum w o / sum w); its rotation and scales are the
+ * eigenvectors and square-root eigenvalues of the covariance.
+ * Node numbering: leaves [0, n_leaf), level 1 [n_leaf, n_leaf + n1),
+ * level 2 after them; gs_lod_nodes(n_leaf) = n_leaf + n1 + n2. */
+GS_API int64_t gs_lod_nodes(int64_t n_leaf);
+/* Workspace bytes of gs_lod_build. */
+GS_API size_t gs_lod_build_workspace(int64_t n_leaf);
+/* Builds levels 1 and 2 over the first n_leaf Gaussians of `nodes` (writable
+ * parameter arrays in the layout of gs_params, nodes->n >= gs_lod_nodes(n_leaf))
+ * and writes the coarse nodes after the leaves.  parent_dev: device int32
+ * [gs_lod_nodes(n_leaf)], overwritten: parent node, -1 for level 2.
+ * ws: device, >= gs_lod_build_workspace bytes, 256-byte aligned. */
+GS_API gs_status gs_lod_build(gs_grads* nodes, int64_t n_leaf, int32_t* parent_dev, void* ws, size_t ws_bytes,
+                              gs_stream stream);
+/* gs_project over all nodes->n nodes of a hierarchy with the level-of-detail
+ * cut of every view applied: a node is projected iff (it is a leaf, index <
+ * n_leaf, or its screen size S = f_x * 3 * max scale / t_z is below tau) and
+ * every ancestor has S >= tau; S is infinite at or behind the near plane.
+ * Other nodes are culled (touched = 0).  The rest of the pipeline
+ * (gs_bin_sort, gs_render_fwd) is unchanged. */
+GS_API gs_status gs_project_lod(const gs_params* nodes, int64_t n_leaf, const int32_t* parent_dev, float tau,
+                                const float* poses_dev, const gs_camera* cams, int32_t views,
+                                const gs_raster_cfg* cfg, gs_splats* out, gs_stream stream);
+
 /* Workspace bytes of gs_bin_sort. */
 GS_API size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity);
 

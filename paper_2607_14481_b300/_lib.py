@@ -22,6 +22,7 @@ EXPORTED = (
     "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
+    "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
     "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_stats", "gs_session_read_params",
     "gs_session_save", "gs_session_load", "gs_session_destroy",
@@ -143,6 +144,13 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_render_bwd_gaussians.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsSplats), P(GsBins),
                                           P(GsRasterCfg), P(GsGrads), vp, vp, sz, vp]
     L.gs_adam_step.argtypes = [vp, vp, vp, vp, i64, P(GsAdamCfg), i32, vp]
+    L.gs_lod_nodes.argtypes = [i64]
+    L.gs_lod_nodes.restype = i64
+    L.gs_lod_build_workspace.argtypes = [i64]
+    L.gs_lod_build_workspace.restype = sz
+    L.gs_lod_build.argtypes = [P(GsGrads), i64, vp, vp, sz, vp]
+    L.gs_project_lod.argtypes = [P(GsParams), i64, vp, C.c_float, vp, P(GsCamera), i32, P(GsRasterCfg), P(GsSplats),
+                                 vp]
     L.gs_render_stats.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp]
     L.gs_image_loss_workspace.argtypes = []
     L.gs_image_loss_workspace.restype = sz
@@ -168,7 +176,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
                  "gs_render_bwd",
                  "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
-                 "gs_render_stats"):
+                 "gs_render_stats", "gs_lod_build", "gs_project_lod"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -185,6 +185,46 @@ gs_status gs_project(const gs_params* params, const float* poses_dev, const gs_c
   return launch_project(*params, poses_dev, vt, *cfg, *out, (cudaStream_t)stream);
 }
 
+int64_t gs_lod_nodes(int64_t n_leaf) {
+  return n_leaf <= 0 ? 0 : n_leaf + lod_level1(n_leaf) + lod_level2(n_leaf);
+}
+
+size_t gs_lod_build_workspace(int64_t n_leaf) { return lod_build_workspace_bytes(std::max<int64_t>(0, n_leaf)); }
+
+gs_status gs_lod_build(gs_grads* nodes, int64_t n_leaf, int32_t* parent_dev, void* ws, size_t ws_bytes,
+                       gs_stream stream) {
+  if (!nodes) return fail(GS_ERR_INVALID, "nodes is NULL");
+  gs_params view{nodes->means4, nodes->scale_opa, nodes->quat, nodes->sh, nodes->n, nodes->sh_degree,
+                 nodes->sh_stride};
+  gs_status st;
+  if ((st = check_params(&view)) != GS_OK) return st;
+  if (n_leaf < 0 || n_leaf > (1ll << 30)) return fail(GS_ERR_INVALID, "n_leaf out of range");
+  if (gs_lod_nodes(n_leaf) > nodes->n)
+    return fail(GS_ERR_INVALID, "nodes hold %lld Gaussians, the hierarchy over %lld leaves needs %lld",
+                (long long)nodes->n, (long long)n_leaf, (long long)gs_lod_nodes(n_leaf));
+  if (n_leaf > 0 && !parent_dev) return fail(GS_ERR_INVALID, "parent is NULL");
+  const size_t need = gs_lod_build_workspace(n_leaf);
+  if (!ws || ws_bytes < need) return fail(GS_ERR_OOM, "lod_build workspace: need %zu bytes, got %zu", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+  return launch_lod_build(*nodes, n_leaf, parent_dev, ws, (cudaStream_t)stream);
+}
+
+gs_status gs_project_lod(const gs_params* nodes, int64_t n_leaf, const int32_t* parent_dev, float tau,
+                         const float* poses_dev, const gs_camera* cams, int32_t views, const gs_raster_cfg* cfg,
+                         gs_splats* out, gs_stream stream) {
+  gs_status st;
+  if ((st = check_params(nodes)) != GS_OK) return st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
+  if (n_leaf < 0 || n_leaf > nodes->n) return fail(GS_ERR_INVALID, "n_leaf out of range");
+  if (nodes->n > 0 && !parent_dev) return fail(GS_ERR_INVALID, "parent is NULL");
+  if (!(tau >= 0.f)) return fail(GS_ERR_INVALID, "tau must be >= 0");
+  if ((st = check_splats(out, nodes->n, views)) != GS_OK) return st;
+  return launch_project(*nodes, poses_dev, vt, *cfg, *out, (cudaStream_t)stream, parent_dev, n_leaf, tau);
+}
+
 size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity) {
   return bin_sort_workspace_bytes(std::max<int64_t>(0, n) * std::max(0, views), std::max<int64_t>(0, capacity));
 }

@@ -164,6 +164,94 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* in, int 
 
 
 // ---------------------------------------------------------------------------
+// Stable LSD radix sort of (u32 key, u32 value) pairs, 8-bit digits (used by
+// the level-of-detail grouping)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                         const uint32_t* __restrict__ n_dev,
+                                                         int shift, uint32_t* __restrict__ hist,
+                                                         uint32_t* __restrict__ hist_n_dev) {
+  __shared__ uint32_t s_h[kRadixDigits];
+  const uint32_t n = *n_dev;
+  const uint32_t nb = num_blocks(n);
+  const uint32_t b = blockIdx.x;
+  if (b == 0 && threadIdx.x == 0) *hist_n_dev = kRadixDigits * nb;
+  if (b >= nb) return;
+  s_h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t base = (uint64_t)b * kItemsPerBlock;
+#pragma unroll
+  for (int r = 0; r < kIPT; ++r) {
+    uint64_t idx = base + (uint64_t)r * kThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&s_h[(keys[idx] >> shift) & (kRadixDigits - 1)], 1u);
+  }
+  __syncthreads();
+  // digit-major layout: all blocks of digit 0, then digit 1, ...
+  hist[(uint64_t)threadIdx.x * nb + b] = s_h[threadIdx.x];
+}
+
+// Each warp ranks 256 consecutive items (8 rounds of 32) with __match_any_sync;
+// the block's offset for a digit is the scanned histogram entry, the warp's
+// offset is the count of that digit in earlier warps: order is preserved.
+__global__ void __launch_bounds__(kThreads) k_radix_scatter(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+    const uint32_t* __restrict__ n_dev, int shift, const uint32_t* __restrict__ hist_scanned,
+    uint32_t n_cap) {
+  __shared__ uint32_t s_wh[kThreads / 32][kRadixDigits];
+  __shared__ uint32_t s_bo[kRadixDigits];
+  const uint32_t n = *n_dev;
+  const uint32_t nb = num_blocks(n);
+  const uint32_t b = blockIdx.x;
+  if (b >= nb) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) s_wh[w][threadIdx.x] = 0;
+  s_bo[threadIdx.x] = hist_scanned[(uint64_t)threadIdx.x * nb + b];
+  __syncthreads();
+  const uint64_t wbase = (uint64_t)b * kItemsPerBlock + (uint64_t)warp * (32 * kIPT);
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t key[kIPT], val[kIPT], rank[kIPT], dig[kIPT];
+#pragma unroll
+  for (int r = 0; r < kIPT; ++r) {
+    const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+    const bool ok = idx < n;
+    key[r] = ok ? keys_in[idx] : 0u;
+    val[r] = ok ? vals_in[idx] : 0u;
+    dig[r] = ok ? ((key[r] >> shift) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
+    const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+    uint32_t prev = 0;
+    if (ok) prev = s_wh[warp][dig[r]];
+    __syncwarp();
+    if (ok && lane == __ffs(peers) - 1) s_wh[warp][dig[r]] = prev + __popc(peers);
+    __syncwarp();
+    rank[r] = prev + __popc(peers & lt_mask);
+  }
+  __syncthreads();
+  {
+    // exclusive scan over warps for digit threadIdx.x
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) {
+      uint32_t c = s_wh[w][threadIdx.x];
+      s_wh[w][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kIPT; ++r) {
+    if (dig[r] < (uint32_t)kRadixDigits) {
+      const uint32_t pos = s_bo[dig[r]] + s_wh[warp][dig[r]] + rank[r];
+      if (pos < n_cap) {  // always true for a consistent histogram
+        keys_out[pos] = key[r];
+        vals_out[pos] = val[r];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Pair kernels
 // ---------------------------------------------------------------------------
 // Status bits written to counts[2]: 1 = pair capacity exceeded, 2 = an index
@@ -442,6 +530,40 @@ gs_status launch_scan(const uint32_t* in, int in_stride, uint32_t* out, int out_
   k_scan_top<<<1, 1024, 0, s>>>(block_sums, n_dev, total_dev);
   k_scan_down<<<nb, kThreads, 0, s>>>(in, in_stride, out, out_stride, block_sums, n_dev);
   return check_launch("scan");
+}
+
+size_t radix_workspace(int64_t n_cap) {
+  const int64_t nb = std::max<int64_t>(1, (n_cap + kItemsPerBlock - 1) / kItemsPerBlock);
+  return align_up(sizeof(uint32_t) * kRadixDigits * nb, 256) + scan_workspace(kRadixDigits * nb) + 256;
+}
+
+gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
+                            uint32_t* keys_out, uint32_t* vals_out, const uint32_t* n_dev,
+                            int64_t n_cap, int bits, void* ws, cudaStream_t s) {
+  const int64_t nb = std::max<int64_t>(1, (n_cap + kItemsPerBlock - 1) / kItemsPerBlock);
+  char* w = static_cast<char*>(ws);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(w);
+  w += align_up(sizeof(uint32_t) * kRadixDigits * nb, 256);
+  void* scan_ws = w;
+  w += scan_workspace(kRadixDigits * nb);
+  uint32_t* hist_n = reinterpret_cast<uint32_t*>(w);
+  uint32_t* hist_total = hist_n + 1;
+  const int passes = std::max(1, (bits + kRadixBits - 1) / kRadixBits);
+  const uint32_t* ksrc = keys_a;
+  const uint32_t* vsrc = vals_a;
+  for (int p = 0; p < passes; ++p) {
+    uint32_t* kdst = (p == passes - 1) ? keys_out : ((p & 1) == 0 ? keys_b : keys_a);
+    uint32_t* vdst = (p == passes - 1) ? vals_out : ((p & 1) == 0 ? vals_b : vals_a);
+    const int shift = p * kRadixBits;
+    k_radix_hist<<<(unsigned)nb, kThreads, 0, s>>>(ksrc, n_dev, shift, hist, hist_n);
+    gs_status st = launch_scan(hist, 1, hist, 1, hist_n, kRadixDigits * nb, hist_total, scan_ws, s);
+    if (st != GS_OK) return st;
+    k_radix_scatter<<<(unsigned)nb, kThreads, 0, s>>>(ksrc, vsrc, kdst, vdst, n_dev, shift, hist,
+                                                       (uint32_t)n_cap);
+    ksrc = kdst;
+    vsrc = vdst;
+  }
+  return check_launch("radix_sort");
 }
 
 // ---------------------------------------------------------------------------

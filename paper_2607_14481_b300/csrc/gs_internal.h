@@ -22,8 +22,16 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 bool make_view_table(const gs_camera* cams, int views, ViewTable* vt);
 
 // ---- kernels' host launchers (each enqueues on `s`, returns GS_OK or GS_ERR_CUDA)
+// parent != nullptr: level-of-detail cut (nodes [0, n_leaf) are leaves).
 gs_status launch_project(const gs_params& p, const float* poses, const ViewTable& vt,
-                         const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s);
+                         const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s,
+                         const int32_t* parent = nullptr, int64_t n_leaf = 0, float tau = 0.f);
+
+// Level-of-detail hierarchy (coarse nodes after the leaves in `nodes`).
+int64_t lod_level1(int64_t n);
+int64_t lod_level2(int64_t n);
+size_t lod_build_workspace_bytes(int64_t n);
+gs_status launch_lod_build(const gs_grads& nodes, int64_t n_leaf, int32_t* parent, void* ws, cudaStream_t s);
 
 // Exclusive scan of n_cap u32 values read every in_stride and written every
 // out_stride elements (in place allowed); the number of valid entries is
@@ -33,6 +41,14 @@ gs_status launch_scan(const uint32_t* in, int in_stride, uint32_t* out, int out_
                       int64_t n_cap, uint32_t* total_dev, void* ws, cudaStream_t s);
 // Largest number of tiles (all views) the binning workspace is sized for.
 int64_t bin_sort_max_tiles();
+
+// Stable LSD radix sort of (key, value) u32 pairs on key bits [0, bits);
+// count *n_dev (device) <= n_cap.  keys/vals ping-pong between the *_a and
+// *_b buffers; the result lands in (keys_out, vals_out).
+size_t radix_workspace(int64_t n_cap);
+gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
+                            uint32_t* keys_out, uint32_t* vals_out, const uint32_t* n_dev,
+                            int64_t n_cap, int bits, void* ws, cudaStream_t s);
 
 gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                             const gs_raster_cfg& cfg, float* image, float* alpha, cudaStream_t s);

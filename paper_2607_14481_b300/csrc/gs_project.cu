@@ -26,7 +26,16 @@ struct ProjectArgs {
   uint2* rect;
   uint32_t* touched;
   uint32_t* aux;
+  const int32_t* parent;  // level-of-detail cut (nullptr: every Gaussian is a candidate)
+  int64_t n_leaf;
+  float tau;
 };
+
+// Screen size of a node: f_x * 3 * max_k scale_k / t_z, infinite at or
+// behind the near plane (never coarse enough).
+__device__ __forceinline__ float screen_size(float tz, float4 so, float fx, float znear) {
+  return tz <= znear ? INFINITY : fx * 3.0f * expf(fmaxf(so.x, fmaxf(so.y, so.z))) / tz;
+}
 
 template <int DEG>
 __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const ViewTable vt) {
@@ -52,6 +61,19 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
     my = df_add_f(df_mul_f(df_div(ty, tz), vi.fy), vi.cy);
     // far off-screen (or non-finite) centres are culled before the split
     vis = fabsf(mx.hi) < 1e7f && fabsf(my.hi) < 1e7f;
+  }
+  if (vis && a.parent) {
+    // level-of-detail cut: rendered iff (a leaf or S < tau) and every
+    // ancestor has S >= tau
+    bool sel = i < a.n_leaf || screen_size(tz.hi, a.scale_opa[i], vi.fx, a.znear) < a.tau;
+    int32_t p = a.parent[i];
+    for (int d = 0; d < 8 && sel && p >= 0 && p < a.n; ++d) {
+      const float4 mp = a.means4[p];
+      const float tzp = R[6] * mp.x + R[7] * mp.y + R[8] * mp.z + tc[2];
+      sel = screen_size(tzp, a.scale_opa[p], vi.fx, a.znear) >= a.tau;
+      p = a.parent[p];
+    }
+    vis = sel;
   }
   float A = 0.f, B = 0.f, C = 0.f, r = 0.f, opa = 0.f;
   float mix = 0.f, miy = 0.f, mfx = 0.f, mfy = 0.f;
@@ -154,7 +176,8 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
 }  // namespace
 
 gs_status launch_project(const gs_params& p, const float* poses, const ViewTable& vt,
-                         const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s) {
+                         const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s, const int32_t* parent,
+                         int64_t n_leaf, float tau) {
   ProjectArgs a;
   a.means4 = reinterpret_cast<const float4*>(p.means4);
   a.scale_opa = reinterpret_cast<const float4*>(p.scale_opa);
@@ -172,6 +195,9 @@ gs_status launch_project(const gs_params& p, const float* poses, const ViewTable
   a.rect = reinterpret_cast<uint2*>(out.rect);
   a.touched = out.touched;
   a.aux = out.aux;
+  a.parent = parent;
+  a.n_leaf = n_leaf;
+  a.tau = tau;
   if (p.n == 0) return GS_OK;
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)vt.views);
   switch (p.sh_degree) {

@@ -43,16 +43,19 @@ class Arena:
         self.sh = buf[3 * n4:3 * n4 + 3 * self.nc * self.n].view(3 * self.nc, self.n)
 
     @classmethod
-    def from_scene(cls, sc: Scene, device="cuda") -> "Arena":
-        a = cls(sc.n, sc.sh_degree, device)
+    def from_scene(cls, sc: Scene, device="cuda", capacity: Optional[int] = None) -> "Arena":
+        """The scene's Gaussians in the first sc.n rows; with a larger
+        capacity the remaining rows are zero (room for hierarchy nodes)."""
+        a = cls(sc.n if capacity is None else capacity, sc.sh_degree, device)
         h = np.zeros(a.padded, np.float32)
-        n, nc = a.n, a.nc
-        h[0:4 * n].reshape(n, 4)[:, :3] = sc.means
+        n, nc, k = a.n, a.nc, sc.n
+        assert k <= n
+        h[0:4 * n].reshape(n, 4)[:k, :3] = sc.means
         so = h[4 * n:8 * n].reshape(n, 4)
-        so[:, :3] = sc.log_scales
-        so[:, 3] = sc.opa_logits
-        h[8 * n:12 * n] = sc.quats.reshape(-1)
-        h[12 * n:12 * n + 3 * nc * n] = np.ascontiguousarray(sc.sh.reshape(n, 3 * nc).T).reshape(-1)
+        so[:k, :3] = sc.log_scales
+        so[:k, 3] = sc.opa_logits
+        h[8 * n:12 * n].reshape(n, 4)[:k] = sc.quats
+        h[12 * n:12 * n + 3 * nc * n].reshape(3 * nc, n)[:, :k] = sc.sh.reshape(k, 3 * nc).T
         a.buf.copy_(torch.from_numpy(h).to(a.buf.device))
         return a
 
@@ -70,9 +73,16 @@ class Arena:
                 "opa_logits": so[:, 3].copy(), "quats": h[8 * n:12 * n].reshape(n, 4).copy(),
                 "sh": h[12 * n:12 * n + 3 * nc * n].reshape(3 * nc, n).T.reshape(n, 3, nc).copy()}
 
-    def struct(self):
+    def struct(self, n: Optional[int] = None):
+        """gs_params over the first n rows (default all), SH planes strided by
+        the arena's row count."""
         return _lib.GsParams(self.means4.data_ptr(), self.scale_opa.data_ptr(), self.quat.data_ptr(),
-                             self.sh.data_ptr(), self.n, self.sh_degree, self.n)
+                             self.sh.data_ptr(), self.n if n is None else int(n), self.sh_degree, self.n)
+
+    def rw_struct(self):
+        """The same arrays as writable pointers (gs_grads layout)."""
+        return _lib.GsGrads(self.means4.data_ptr(), self.scale_opa.data_ptr(), self.quat.data_ptr(),
+                            self.sh.data_ptr(), self.n, self.sh_degree, self.n)
 
     def adam_groups(self, lr_means=1.6e-4, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3,
                     lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4) -> List[_lib.GsAdamGroup]:
@@ -92,6 +102,29 @@ class Arena:
             if nc > 1:
                 groups.append(G(b + n, b + nc * n, f4(lr_sh_rest, lr_sh_rest, lr_sh_rest, lr_sh_rest)))
         return groups
+
+
+class LodHierarchy:
+    """Three-level hierarchy (gs_lod_build) over the first n_leaf Gaussians of
+    a node arena; coarse nodes are written after the leaves."""
+
+    def __init__(self, arena: Arena, n_leaf: int):
+        self.L = _lib.load()
+        self.arena, self.n_leaf = arena, int(n_leaf)
+        self.n_nodes = int(self.L.gs_lod_nodes(self.n_leaf))
+        if self.n_nodes > arena.n:
+            raise ValueError(f"arena holds {arena.n} rows, the hierarchy needs {self.n_nodes}")
+        dev = arena.buf.device
+        self.parent = torch.empty(max(1, self.n_nodes), dtype=torch.int32, device=dev)
+        self.ws = torch.empty(max(1, self.L.gs_lod_build_workspace(self.n_leaf)), dtype=torch.uint8, device=dev)
+
+    def build(self) -> None:
+        rw = self.arena.rw_struct()
+        _lib.check(self.L.gs_lod_build(C.byref(rw), self.n_leaf, _p(self.parent), _p(self.ws), self.ws.numel(),
+                                       _stream()), "gs_lod_build")
+
+    def nodes(self):
+        return self.arena.struct(self.n_nodes)
 
 
 def cameras_struct(cams: Sequence[Camera]):
@@ -183,6 +216,15 @@ class Rasterizer:
         _lib.check(self.L.gs_project(C.byref(ps), _p(poses), self.cam_struct, self.views, C.byref(self.cfg),
                                      C.byref(self.splats), _stream()), "gs_project")
 
+    def project_lod(self, lod: "LodHierarchy", poses: torch.Tensor, tau: float = 1.0) -> None:
+        """gs_project_lod over the hierarchy's nodes (the Rasterizer holds
+        lod.n_nodes Gaussians)."""
+        assert self.n == lod.n_nodes
+        ps = lod.nodes()
+        _lib.check(self.L.gs_project_lod(C.byref(ps), lod.n_leaf, _p(lod.parent), float(tau), _p(poses),
+                                         self.cam_struct, self.views, C.byref(self.cfg), C.byref(self.splats),
+                                         _stream()), "gs_project_lod")
+
     def bin_sort(self) -> None:
         b = self.bins_struct()
         _lib.check(self.L.gs_bin_sort(C.byref(self.splats), self.cam_struct, self.views, C.byref(self.cfg),
@@ -213,9 +255,15 @@ class Rasterizer:
     def read_counts(self) -> np.ndarray:
         return self.counts.cpu().numpy().view(np.uint32).copy()
 
-    def forward(self, params: Arena, poses: torch.Tensor, image=None, alpha=None, check=True):
+    def forward(self, params: Arena, poses: torch.Tensor, image=None, alpha=None, check=True,
+                lod: Optional["LodHierarchy"] = None, tau: float = 1.0):
+        """Project (with the level-of-detail cut when lod is given), bin and
+        composite."""
         image = self.new_image() if image is None else image
-        self.project(params, poses)
+        if lod is not None:
+            self.project_lod(lod, poses, tau)
+        else:
+            self.project(params, poses)
         self.bin_sort()
         if check:
             cnt = self.read_counts()

@@ -47,6 +47,15 @@ def test_size_queries(lib):
     assert lib.gs_render_bwd_workspace(1000, 1, 10_000) >= 36 * 10_000
 
 
+def test_lod_sizes_and_validation(lib):
+    assert lib.gs_lod_nodes(0) == 0 and lib.gs_lod_nodes(1) == 3 and lib.gs_lod_nodes(8) == 10
+    assert lib.gs_lod_nodes(9) == 9 + 2 + 1 and lib.gs_lod_nodes(65) == 65 + 9 + 2
+    assert lib.gs_lod_build_workspace(1000) > lib.gs_lod_build_workspace(10)
+    nodes = _lib.GsGrads(256, 256, 256, 256, 10, 0, 0)  # 10 rows cannot hold 9 leaves + 3 coarse nodes
+    st = lib.gs_lod_build(C.byref(nodes), 9, C.c_void_p(256), C.c_void_p(256), 1 << 20, None)
+    assert st == _lib.GS_ERR_INVALID and "needs 12" in _lib.last_error()
+
+
 def test_invalid_arguments_rejected_on_host(lib):
     cam = (_lib.GsCamera * 1)(_lib.GsCamera(100.0, 100.0, 32.0, 32.0, 64, 64))
     cfg = _lib.GsRasterCfg(16, 16, (C.c_float * 3)(0, 0, 0), 0.2, 1)
