@@ -426,6 +426,8 @@ typedef struct {
   float lr_means, lr_scale, lr_opacity, lr_quat, lr_sh_dc, lr_sh_rest;
   float beta1, beta2, eps;
   int32_t loss_kind;         /* 0 = L1, 1 = MSE */
+  int32_t lod;               /* 1: render requests go through a level-of-detail cut (gs_lod_build) */
+  float lod_tau;             /* cut threshold in pixels (> 0; the paper's tau = 1) */
 } gs_session_config;
 
 typedef struct {
@@ -442,6 +444,7 @@ typedef struct {
   int64_t iterations;        /* Adam steps taken (batches with train views) */
   int64_t batches;           /* batches issued, capacity retries included */
   int64_t retries;           /* batch parts issued again after a pair-capacity overflow */
+  int64_t lod_builds;        /* hierarchy builds (one before the first render after Gaussians were added) */
   int64_t gaussians;         /* active Gaussians */
   double pixels;             /* pixels of completed requests */
   double p50_ms, p99_ms, mean_ms, max_ms;  /* arrival -> completion, completed requests */

@@ -85,7 +85,8 @@ class GsSessionConfig(C.Structure):
                 ("hbm_budget_bytes", C.c_uint64), ("pair_factor", C.c_double), ("raster", GsRasterCfg),
                 ("lr_means", C.c_float), ("lr_scale", C.c_float), ("lr_opacity", C.c_float),
                 ("lr_quat", C.c_float), ("lr_sh_dc", C.c_float), ("lr_sh_rest", C.c_float),
-                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("loss_kind", C.c_int32)]
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("loss_kind", C.c_int32),
+                ("lod", C.c_int32), ("lod_tau", C.c_float)]
 
 
 class GsRequest(C.Structure):
@@ -96,6 +97,7 @@ class GsRequest(C.Structure):
 class GsStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64),
                 ("inflight", C.c_int64), ("iterations", C.c_int64), ("batches", C.c_int64), ("retries", C.c_int64),
+                ("lod_builds", C.c_int64),
                 ("gaussians", C.c_int64), ("pixels", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
                 ("mean_ms", C.c_double), ("max_ms", C.c_double), ("wall_s", C.c_double),
                 ("hbm_in_use", C.c_uint64), ("hbm_budget", C.c_uint64), ("contexts", C.c_int32)]

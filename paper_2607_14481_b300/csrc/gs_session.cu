@@ -90,6 +90,9 @@ struct gs_session {
   cudaStream_t stream = nullptr;
   gs::Dev arena[4];  // parameters, gradients, first and second moments (stride = capacity)
   gs::Dev status_word, step_dev;
+  gs::Dev lod_parent, lod_ws;  // level-of-detail hierarchy (cfg.lod)
+  bool lod_dirty = true;       // leaves added since the last build
+  int64_t lod_builds = 0;
   int64_t capacity = 0;
   int64_t n_active = 0;
   int nc = 1;
@@ -146,9 +149,18 @@ size_t ctx_device_bytes(const gs_session_config& c, int64_t cap_n, int64_t pair_
   return b;
 }
 
+// Rows of the parameter arenas: the leaves, and with a hierarchy its coarse
+// nodes after them.
+int64_t arena_rows(const gs_session_config& c) {
+  return c.lod ? c.max_gaussians + lod_level1(c.max_gaussians) + lod_level2(c.max_gaussians) : c.max_gaussians;
+}
+
 size_t fixed_device_bytes(const gs_session_config& c) {
   const int nc = (c.sh_degree + 1) * (c.sh_degree + 1);
-  return 4 * align_up(4 * arena_floats(c.max_gaussians, nc), 256) + 2 * 256;
+  size_t b = 4 * align_up(4 * arena_floats(arena_rows(c), nc), 256) + 2 * 256;
+  if (c.lod)
+    b += align_up(4 * (size_t)arena_rows(c), 256) + align_up(lod_build_workspace_bytes(c.max_gaussians), 256);
+  return b;
 }
 
 int64_t initial_pair_cap(const gs_session_config& c) {
@@ -297,11 +309,25 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     for (size_t i = 0; i < R.size(); ++i) std::memcpy(c.h_poses + 12 * i, R[i]->pose, 48);
     if (cudaMemcpyAsync(poses, c.h_poses, 48 * R.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return check_launch("session poses");
+    gs_params PR = P;
+    const int32_t* parent = nullptr;
+    if (cf.lod && n > 0) {
+      if (S->lod_dirty) {
+        gs_grads rw{const_cast<float*>(P.means4), const_cast<float*>(P.scale_opa), const_cast<float*>(P.quat),
+                    const_cast<float*>(P.sh), S->capacity, P.sh_degree, P.sh_stride};
+        if ((st = launch_lod_build(rw, n, static_cast<int32_t*>(S->lod_parent.p), S->lod_ws.p, s)) != GS_OK)
+          return st;
+        S->lod_dirty = false;
+        S->lod_builds++;
+      }
+      PR.n = n + lod_level1(n) + lod_level2(n);
+      parent = static_cast<const int32_t*>(S->lod_parent.p);
+    }
     gs_splats sp;
-    gs_splats_carve(c.splat_buf.p, n, (int32_t)R.size(), &sp);
+    gs_splats_carve(c.splat_buf.p, PR.n, (int32_t)R.size(), &sp);
     gs_bins b{static_cast<uint32_t*>(c.vals.p), static_cast<uint32_t*>(c.ranges.p),
               static_cast<uint32_t*>(c.pair_off.p), nullptr, counts, c.pair_cap, vt.total_tiles};
-    if ((st = launch_project(P, poses, vt, cf.raster, sp, s)) != GS_OK) return st;
+    if ((st = launch_project(PR, poses, vt, cf.raster, sp, s, parent, n, cf.lod_tau)) != GS_OK) return st;
     if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, s)) != GS_OK) return st;
     if ((st = launch_render_fwd(sp, b, vt, cf.raster, img, nullptr, s)) != GS_OK) return st;
     for (Req* r : R) off += 3 * (int64_t)r->cam.width * r->cam.height;
@@ -556,10 +582,12 @@ gs_status gs_session_plan(const gs_session_config* cfg, gs_session_plan_info* ou
     return gs::fail(GS_ERR_INVALID, "session: max_batch_views must be 1..%d", GS_MAX_VIEWS);
   if (cfg->max_width <= 0 || cfg->max_height <= 0 || cfg->max_width > 16 * 4096 || cfg->max_height > 16 * 4096)
     return gs::fail(GS_ERR_INVALID, "session: bad maximum resolution");
-  if ((uint64_t)cfg->max_gaussians * (uint64_t)cfg->max_batch_views >= (1ull << 32))
+  if ((uint64_t)gs::arena_rows(*cfg) * (uint64_t)cfg->max_batch_views >= (1ull << 32))
     return gs::fail(GS_ERR_INVALID, "session: max_gaussians * max_batch_views must be < 2^32");
+  if (cfg->lod != 0 && cfg->lod != 1) return gs::fail(GS_ERR_INVALID, "session: lod must be 0 or 1");
+  if (cfg->lod && !(cfg->lod_tau > 0.f)) return gs::fail(GS_ERR_INVALID, "session: lod_tau must be > 0");
   out->fixed_bytes = gs::fixed_device_bytes(*cfg);
-  out->context_bytes = gs::ctx_device_bytes(*cfg, cfg->max_gaussians, gs::initial_pair_cap(*cfg));
+  out->context_bytes = gs::ctx_device_bytes(*cfg, gs::arena_rows(*cfg), gs::initial_pair_cap(*cfg));
   out->initial_pair_capacity = gs::initial_pair_cap(*cfg);
   const uint64_t budget = cfg->hbm_budget_bytes;
   int64_t k = 0;
@@ -584,7 +612,7 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
   auto S = std::make_unique<gs_session>();
   S->cfg = *cfg;
   S->nc = (cfg->sh_degree + 1) * (cfg->sh_degree + 1);
-  S->capacity = cfg->max_gaussians;
+  S->capacity = gs::arena_rows(*cfg);
   S->created_at = gs::steady_now();
   cudaGetDevice(&S->device);
   if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) return gs::check_launch("stream");
@@ -593,6 +621,8 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
     for (auto& a : S->arena) gs::dfree(a, S->in_use);
     gs::dfree(S->status_word, S->in_use);
     gs::dfree(S->step_dev, S->in_use);
+    gs::dfree(S->lod_parent, S->in_use);
+    gs::dfree(S->lod_ws, S->in_use);
     if (S->h_add) cudaFreeHost(S->h_add);
     if (S->add_done) cudaEventDestroy(S->add_done);
     cudaStreamDestroy(S->stream);
@@ -607,6 +637,11 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
   if ((st = gs::dalloc(S->step_dev, 16, S->in_use)) != GS_OK) return cleanup(st);
   cudaMemsetAsync(S->status_word.p, 0, 16, S->stream);
   cudaMemsetAsync(S->step_dev.p, 0, 16, S->stream);
+  if (cfg->lod) {
+    if ((st = gs::dalloc(S->lod_parent, 4 * (size_t)S->capacity, S->in_use)) != GS_OK) return cleanup(st);
+    if ((st = gs::dalloc(S->lod_ws, gs::lod_build_workspace_bytes(cfg->max_gaussians), S->in_use)) != GS_OK)
+      return cleanup(st);
+  }
   for (int k = 0; k < plan.contexts; ++k) {
     S->ctxs.push_back(std::make_unique<Ctx>());
     if ((st = gs::alloc_ctx(S.get(), *S->ctxs.back())) != GS_OK) return cleanup(st);
@@ -632,9 +667,9 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
   if (!means || !log_scales || !quats || !opa_logits || !sh) return gs::fail(GS_ERR_INVALID, "NULL array");
   std::unique_lock<std::mutex> lk(S->mu);
   if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
-  if (S->n_active + count > S->capacity)
+  if (S->n_active + count > S->cfg.max_gaussians)
     return gs::fail(GS_ERR_OOM, "session: %lld + %lld Gaussians exceed the capacity %lld",
-                    (long long)S->n_active, (long long)count, (long long)S->capacity);
+                    (long long)S->n_active, (long long)count, (long long)S->cfg.max_gaussians);
   const int nc = S->nc;
   const int64_t cap = S->capacity;
   for (int64_t done = 0; done < count;) {
@@ -680,6 +715,7 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
     done += k;
   }
   S->n_active += count;
+  S->lod_dirty = true;  // the new leaves overwrote coarse nodes
   return GS_OK;
 }
 
@@ -758,6 +794,7 @@ gs_status gs_session_stats(gs_session* S, gs_stats* out) {
   st.iterations = S->iterations;
   st.batches = S->batches;
   st.retries = S->retries;
+  st.lod_builds = S->lod_builds;
   st.gaussians = S->n_active;
   st.pixels = S->pixels;
   st.wall_s = gs::steady_now() - S->created_at;
@@ -829,7 +866,7 @@ gs_status gs_session_load(gs_session* S, const char* path) {
   if (!f) return gs::fail(GS_ERR_INVALID, "cannot open %s", path);
   int64_t hdr[4];
   if (std::fread(hdr, sizeof(hdr), 1, f) != 1 || hdr[0] != 0x3153534553534723ll || hdr[1] != S->cfg.sh_degree ||
-      hdr[2] < 0 || hdr[2] > S->capacity) {
+      hdr[2] < 0 || hdr[2] > S->cfg.max_gaussians) {
     std::fclose(f);
     return gs::fail(GS_ERR_INVALID, "%s is not a checkpoint of this session's layout", path);
   }
@@ -858,6 +895,7 @@ gs_status gs_session_load(gs_session* S, const char* path) {
   cudaMemcpyAsync(S->step_dev.p, &step, 4, cudaMemcpyHostToDevice, S->stream);
   if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
   S->n_active = n;
+  S->lod_dirty = true;
   return gs::check_launch("session load");
 }
 

@@ -184,3 +184,39 @@ def test_empty_scene_renders_background(cuda_device):
         img = s.wait(s.submit(RENDER, cam, want_image=True))
     for ch, b in enumerate((0.25, 0.5, 0.75)):
         assert np.all(img[ch] == np.float32(b))
+
+
+def test_lod_render_equals_direct_hierarchy_and_rebuilds_on_add(cuda_device):
+    """Render requests through the session's level-of-detail cut give the
+    image of the direct pipeline (gs_lod_build + gs_project_lod); Gaussians
+    added later trigger a rebuild before the next render."""
+    ensure_built()
+    sc = synth.random_scene(6000, 12, 1, (-4, -1, -4), (4, 1, 4), -2.5, 0.5)
+    cam = synth.look_at((0.0, -0.5, -40.0), (0, 0, 0), 300.0, 300.0, 160, 120, 320, 240)
+    tau = 16.0
+    more = synth.random_scene(500, 13, 1, (-4, -1, -4), (4, 1, 4), -2.5, 0.5)
+    with session.Session(_cfg(sc.n + more.n, sh_degree=1, lod=True, lod_tau=tau)) as s:
+        s.add(sc)
+        a = s.wait(s.submit(RENDER, cam, want_image=True))
+        st1 = s.stats()
+        s.add(more)
+        b = s.wait(s.submit(RENDER, cam, want_image=True))
+        st2 = s.stats()
+    assert st1["lod_builds"] == 1 and st2["lod_builds"] == 2
+
+    def direct(scene):
+        dev = torch.device("cuda:0")
+        cap = int(_lib.load().gs_lod_nodes(scene.n))
+        arena = raster.Arena.from_scene(scene, dev, capacity=cap)
+        lod = raster.LodHierarchy(arena, scene.n)
+        lod.build()
+        r = raster.Rasterizer(lod.n_nodes, scene.sh_degree, [cam], device=dev)
+        img, _ = r.forward(arena, raster.poses_tensor([cam], dev), r.new_image(), None, lod=lod, tau=tau)
+        torch.cuda.synchronize()
+        return r.split(img.cpu(), 3)[0].numpy()
+
+    assert np.array_equal(a, direct(sc))
+    both = synth.Scene(*(np.concatenate([x, y]) for x, y in zip(
+        (sc.means, sc.log_scales, sc.quats, sc.opa_logits, sc.sh),
+        (more.means, more.log_scales, more.quats, more.opa_logits, more.sh))))
+    assert np.array_equal(b, direct(both))
