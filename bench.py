@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd+Adam iters/s at 1M Gaussians (plain single-view 1280x720 SH3)"
 N_GAUSS = 1_000_000
 N_POSES = 100
-SEED_SCENE, SEED_TRAJ, SEED_TARGET = 1007, 1008, 1009
+SEED_SCENE, SEED_TRAJ, SEED_TARGET, SEED_STREAM = 1007, 1008, 1009, 4007
 
 
 def parse_args():
@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--stream-max", type=int, default=5_000_000)
     return ap.parse_args()
 
 
@@ -342,6 +344,10 @@ def run_ours(args, ws, rank, local):
         del wb
         torch.cuda.empty_cache()
 
+    stream = None
+    if not args.no_stream and rank == 0:
+        stream = run_streaming(args.stream_max)
+
     out = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / K, "higher_is_better": True,
@@ -356,6 +362,7 @@ def run_ours(args, ws, rank, local):
         "e2e": e2e,
         "roofline": roof,
         "batched": batched,
+        "streaming": stream,
         "clocks": clk,
         "gpu_launches": n_launch * K,
         "nonfinite_flag": bad,
@@ -365,13 +372,78 @@ def run_ours(args, ws, rank, local):
     return out, rank
 
 
+def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
+    """The streaming session loop: the scene grows from n0 to n_max Gaussians
+    while frames arrive in real time at rate_hz; every frame adds its new
+    Gaussians (U{10k..50k}, in the frame camera's frustum) and submits
+    U{1..8} render / train requests at 540p-1080p as one group; a
+    three-level hierarchy serves the render requests (tau = 1 px); admission
+    by an 80 GB HBM budget.  Frame-update latency = a train request's
+    arrival (its frame's arrival) to the completion of the Adam step that
+    used it."""
+    import time
+    from paper_2607_14481_b300 import session, synth
+    avg_new = 30_000
+    n_frames = max(1, (n_max - n0) // avg_new)
+    cfg = session.default_config(n_max + 60_000, sh_degree=3, max_batch_views=8, max_width=1920, max_height=1080,
+                                 max_inflight=2, hbm_budget_gb=80.0, pair_factor=8.0, lod=True, lod_tau=1.0)
+    g = np.random.default_rng(seed)
+    targets = {wh: [g.random((3, wh[1], wh[0]), dtype=np.float32) for _ in range(2)]
+               for wh in synth.STREAM_RESOLUTIONS}
+    frames = [synth.stream_frame(k, n_frames, seed) for k in range(n_frames)]
+    ids = []
+    with session.Session(cfg) as s:
+        s.add(synth.frustum_gaussians(synth.stream_camera(0, n_frames), n0, seed + 1))
+        n = n0
+        t0 = session.now() + 0.5
+        for k, (cam, new, reqs) in enumerate(frames):
+            t_arr = t0 + k / rate_hz
+            while session.now() < t_arr:
+                time.sleep(min(0.002, max(0.0, t_arr - session.now())))
+            if n + new.n <= n_max + 60_000:
+                s.add(new)
+                n += new.n
+            s.hold(True)
+            for i, (kind, w, h) in enumerate(reqs):
+                c = synth.with_resolution(cam, w, h)
+                tgt = targets[(w, h)][(k + i) % 2] if kind == 1 else None
+                ids.append((kind, s.submit(kind, c, target=tgt, arrival=t_arr)))
+            s.hold(False)
+        s.drain(timeout_ms=600_000)
+        st = s.stats()
+        times = [(kind, s.times(i)) for kind, i in ids]
+    lat = {0: [], 1: []}
+    last = t0
+    for kind, (a, d) in times:
+        lat[kind].append(1e3 * (d - a))
+        last = max(last, d)
+    wall = last - t0
+
+    def pct(x, q):
+        return float(np.percentile(x, q)) if x else None
+
+    return {"frames": n_frames, "rate_hz": rate_hz, "requests": len(ids), "train_requests": len(lat[1]),
+            "gaussians_start": n0, "gaussians_final": int(st["gaussians"]),
+            "frame_update_p50_ms": pct(lat[1], 50), "frame_update_p99_ms": pct(lat[1], 99),
+            "render_p50_ms": pct(lat[0], 50), "render_p99_ms": pct(lat[0], 99),
+            "iterations": int(st["iterations"]), "iters_per_s": st["iterations"] / wall, "wall_s": wall,
+            "batches": int(st["batches"]), "retries": int(st["retries"]), "lod_builds": int(st["lod_builds"]),
+            "hbm_in_use_gb": st["hbm_in_use"] / 2 ** 30, "hbm_budget_gb": st["hbm_budget"] / 2 ** 30,
+            "contexts": int(st["contexts"]),
+            "workload": "camera on a 200 m loop, frames at 30 Hz, U{10k..50k} new Gaussians per frame in the "
+                        "frame camera's frustum, U{1..8} requests per frame (render/train p = 0.5, 540p-1080p), "
+                        "3-level LoD (8-child moment merge, tau = 1 px) for renders, 80 GB HBM budget"}
+
+
 def launches_per_step(views, num_tiles):
-    """Kernels one training step launches (memsets excluded)."""
-    bits = max(1, int(np.ceil(np.log2(max(2, num_tiles)))))
-    tile_passes = (bits + 7) // 8
+    """Kernels one training step launches (memsets excluded): projection 1;
+    binning 11 (counts, pair-offset scan 3, status, place, tile scan 3,
+    keys, tile sort); composite 1; loss 2; per-pixel backward 1;
+    per-Gaussian backward 5 (pair sums, projection, SH, pose chunks and
+    total); Adam 3 (parameters, poses, step counter)."""
     scan = 3
-    bin_sort = 1 + 1 + scan + 1 + 4 * (2 + scan) + 1 + scan + 1 + 1 + tile_passes * (2 + scan) + 1
-    return 1 + bin_sort + 1 + 2 + 1 + 3 + 3
+    bin_sort = 1 + scan + 1 + 1 + scan + 1 + 1
+    return 1 + bin_sort + 1 + 2 + 1 + 5 + 3
 
 
 def load_peaks():

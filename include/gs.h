@@ -481,6 +481,9 @@ GS_API gs_status gs_session_submit(gs_session* s, const gs_request* req, int64_t
 GS_API gs_status gs_session_poll(gs_session* s, int64_t id, int32_t* done);
 /* Waits up to timeout_ms for a request; GS_ERR_TIMEOUT if it is still pending. */
 GS_API gs_status gs_session_wait(gs_session* s, int64_t id, int32_t timeout_ms);
+/* Arrival and completion time (gs_session_now's clock, seconds) of a finished
+ * request; GS_ERR_BUSY (no message) while it is pending. */
+GS_API gs_status gs_session_times(gs_session* s, int64_t id, double* arrival_s, double* done_s);
 /* Waits up to timeout_ms until nothing is queued or in flight. */
 GS_API gs_status gs_session_drain(gs_session* s, int32_t timeout_ms);
 /* on != 0 pauses admission: submitted requests queue up and no new batch is

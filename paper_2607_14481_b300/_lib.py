@@ -24,7 +24,7 @@ EXPORTED = (
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
     "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
-    "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_stats", "gs_session_read_params",
+    "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_stats", "gs_session_read_params",
     "gs_session_save", "gs_session_load", "gs_session_destroy",
 )
 
@@ -166,13 +166,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_session_wait.argtypes = [vp, i64, i32]
     L.gs_session_drain.argtypes = [vp, i32]
     L.gs_session_hold.argtypes = [vp, i32]
+    L.gs_session_times.argtypes = [vp, i64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.gs_session_stats.argtypes = [vp, P(GsStats)]
     L.gs_session_read_params.argtypes = [vp, vp, vp, vp, vp]
     L.gs_session_save.argtypes = [vp, C.c_char_p]
     L.gs_session_load.argtypes = [vp, C.c_char_p]
     L.gs_session_destroy.argtypes = [vp]
     for name in ("gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
-                 "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_stats",
+                 "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_stats",
                  "gs_session_read_params", "gs_session_save", "gs_session_load", "gs_session_destroy"):
         getattr(L, name).restype = C.c_int
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",

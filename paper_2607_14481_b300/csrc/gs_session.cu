@@ -27,6 +27,7 @@
 #include <cstring>
 #include <deque>
 #include <memory>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -53,7 +54,8 @@ struct Req {
   int32_t kind = 0;
   gs_camera cam{};
   float pose[12]{};
-  std::vector<float> target;
+  float* target = nullptr;       // pinned copy of a train target (from the session's pool)
+  size_t target_bytes = 0;
   float* image_out = nullptr;
   double arrival = 0.0;
   double done_at = 0.0;
@@ -71,7 +73,6 @@ struct Ctx {
   cudaEvent_t done = nullptr;
   Dev splat_buf, pair_off, ranges, counts, vals, ws_bin, ws_bwd, img, dimg, tgt, loss_ws, loss, poses, dpose;
   float* h_img = nullptr;       // pinned staging of rendered images
-  float* h_tgt = nullptr;       // pinned staging of targets
   float* h_poses = nullptr;     // pinned poses [2][max views][12]
   uint32_t* h_counts = nullptr; // pinned [8]: counts of the render and train sub-batches
   int64_t pair_cap = 0;
@@ -101,6 +102,11 @@ struct gs_session {
   float* h_add = nullptr;  // pinned staging of added Gaussians
   int64_t h_add_cap = 0;
   cudaEvent_t add_done = nullptr;
+  std::mutex add_mu;       // serialises adds (one staging buffer)
+  // pinned buffers for train targets, recycled by size once a request ends
+  std::mutex pool_mu;
+  std::multimap<size_t, float*> pinned_free;
+  std::vector<float*> pinned_all;
   std::mutex mu;
   std::condition_variable cv_work, cv_done, cv_ctx;
   std::deque<std::shared_ptr<gs::Req>> queue;
@@ -225,7 +231,6 @@ gs_status alloc_ctx(gs_session* S, Ctx& c) {
   if ((st = dalloc(c.dpose, 24 * (size_t)V, u)) != GS_OK) return st;
   if ((st = alloc_pair_buffers(S, c, initial_pair_cap(cf))) != GS_OK) return st;
   if (cudaMallocHost(&c.h_img, 12 * (size_t)px * V) != cudaSuccess ||
-      cudaMallocHost(&c.h_tgt, 12 * (size_t)px * V) != cudaSuccess ||
       cudaMallocHost(&c.h_poses, 48 * 2 * (size_t)V) != cudaSuccess ||
       cudaMallocHost(&c.h_counts, 32) != cudaSuccess) {
     cudaGetLastError();
@@ -240,7 +245,6 @@ void free_ctx(gs_session* S, Ctx& c) {
                  &c.dimg, &c.tgt, &c.loss_ws, &c.loss, &c.poses, &c.dpose};
   for (Dev* d : devs) dfree(*d, S->in_use);
   if (c.h_img) cudaFreeHost(c.h_img);
-  if (c.h_tgt) cudaFreeHost(c.h_tgt);
   if (c.h_poses) cudaFreeHost(c.h_poses);
   if (c.h_counts) cudaFreeHost(c.h_counts);
   if (c.done) cudaEventDestroy(c.done);
@@ -341,16 +345,15 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
   if (!T.empty()) {
     ViewTable vt;
     if (!make_view_table(cT.data(), (int)T.size(), &vt)) return GS_ERR_INVALID;
-    int64_t tpx = 0;
-    for (Req* r : T) {
-      const int64_t k = 3 * (int64_t)r->cam.width * r->cam.height;
-      std::memcpy(c.h_tgt + tpx, r->target.data(), 4 * k);
-      tpx += k;
-    }
     float* tgt = static_cast<float*>(c.tgt.p);
     float* dimg = static_cast<float*>(c.dimg.p);
-    if (cudaMemcpyAsync(tgt, c.h_tgt, 4 * tpx, cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return check_launch("session targets");
+    int64_t tpx = 0;
+    for (Req* r : T) {  // straight from each request's pinned copy
+      const int64_t k = 3 * (int64_t)r->cam.width * r->cam.height;
+      if (cudaMemcpyAsync(tgt + tpx, r->target, 4 * k, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return check_launch("session targets");
+      tpx += k;
+    }
     for (size_t i = 0; i < T.size(); ++i) std::memcpy(c.h_poses + 12 * (V + i), T[i]->pose, 48);
     float* tposes = poses + 12 * V;
     if (cudaMemcpyAsync(tposes, c.h_poses + 12 * V, 48 * T.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -400,10 +403,39 @@ Ctx* free_ctx_of(gs_session* S) {
   return nullptr;
 }
 
+// A pinned buffer of at least `bytes` from the pool (allocated on demand).
+float* acquire_pinned(gs_session* S, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(S->pool_mu);
+    auto it = S->pinned_free.lower_bound(bytes);
+    if (it != S->pinned_free.end() && it->first <= 2 * bytes) {
+      float* p = it->second;
+      S->pinned_free.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(S->pool_mu);
+  S->pinned_all.push_back(static_cast<float*>(p));
+  return static_cast<float*>(p);
+}
+
+void release_target(gs_session* S, Req* r) {
+  if (!r->target) return;
+  std::lock_guard<std::mutex> lk(S->pool_mu);
+  S->pinned_free.emplace(r->target_bytes, r->target);
+  r->target = nullptr;
+}
+
 void finish_req(gs_session* S, Req* r, gs_status st) {
   r->done_at = steady_now();
   r->status = st;
   r->state = st == GS_OK ? 2 : 3;
+  release_target(S, r);  // the pinned copy of a target is not needed once finished
   if (st == GS_OK) {
     S->completed++;
     S->latencies.push_back(1e3 * (r->done_at - r->arrival));
@@ -665,55 +697,71 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
   if (count < 0) return gs::fail(GS_ERR_INVALID, "count < 0");
   if (count == 0) return GS_OK;
   if (!means || !log_scales || !quats || !opa_logits || !sh) return gs::fail(GS_ERR_INVALID, "NULL array");
-  std::unique_lock<std::mutex> lk(S->mu);
-  if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
-  if (S->n_active + count > S->cfg.max_gaussians)
-    return gs::fail(GS_ERR_OOM, "session: %lld + %lld Gaussians exceed the capacity %lld",
-                    (long long)S->n_active, (long long)count, (long long)S->cfg.max_gaussians);
+  // Adds are serialised; the host-side staging runs without the session lock,
+  // the device copies are enqueued under it together with the new count (so
+  // a batch never sees rows that are being filled, and the hierarchy, whose
+  // coarse nodes the new rows overwrite, is marked for a rebuild).
+  std::lock_guard<std::mutex> add_lk(S->add_mu);
+  int64_t n0;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
+    if (S->n_active + count > S->cfg.max_gaussians)
+      return gs::fail(GS_ERR_OOM, "session: %lld + %lld Gaussians exceed the capacity %lld",
+                      (long long)S->n_active, (long long)count, (long long)S->cfg.max_gaussians);
+    n0 = S->n_active;  // only adds change it, and they are serialised
+  }
   const int nc = S->nc;
   const int64_t cap = S->capacity;
-  for (int64_t done = 0; done < count;) {
-    const int64_t k = std::min(S->h_add_cap, count - done);
-    // the staging buffer is free once the previous chunk's copies finished
-    const double t0 = gs::steady_now();
-    cudaError_t e;
-    while ((e = cudaEventQuery(S->add_done)) == cudaErrorNotReady) {
-      if (gs::steady_now() - t0 > 30.0) return gs::fail(GS_ERR_TIMEOUT, "session: add staging busy");
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
-    }
-    if (e != cudaSuccess) return gs::fail(GS_ERR_CUDA, "session: %s", cudaGetErrorString(e));
-    float* h = S->h_add;
-    float* hm = h;
-    float* hs = h + 4 * k;
-    float* hq = h + 8 * k;
-    float* hsh = h + 12 * k;
-    for (int64_t i = 0; i < k; ++i) {
-      const int64_t g = done + i;
-      hm[4 * i] = means[3 * g]; hm[4 * i + 1] = means[3 * g + 1]; hm[4 * i + 2] = means[3 * g + 2]; hm[4 * i + 3] = 0.f;
-      hs[4 * i] = log_scales[3 * g]; hs[4 * i + 1] = log_scales[3 * g + 1]; hs[4 * i + 2] = log_scales[3 * g + 2];
-      hs[4 * i + 3] = opa_logits[g];
-      for (int c = 0; c < 4; ++c) hq[4 * i + c] = quats[4 * g + c];
-      for (int p = 0; p < 3 * nc; ++p) hsh[(int64_t)p * k + i] = sh[(int64_t)g * 3 * nc + p];
-    }
-    const int64_t n0 = S->n_active + done;
-    float* A = gs::arena_ptr(S, 0);
-    cudaStream_t s = S->stream;
-    cudaMemcpyAsync(A + 4 * n0, hm, 16 * k, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(A + 4 * cap + 4 * n0, hs, 16 * k, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(A + 8 * cap + 4 * n0, hq, 16 * k, cudaMemcpyHostToDevice, s);
-    cudaMemcpy2DAsync(A + 12 * cap + n0, 4 * cap, hsh, 4 * k, 4 * k, 3 * nc, cudaMemcpyHostToDevice, s);
-    for (int a = 2; a < 4; ++a) {  // fresh Adam moments for the new slots
-      float* M = gs::arena_ptr(S, a);
-      cudaMemsetAsync(M + 4 * n0, 0, 16 * k, s);
-      cudaMemsetAsync(M + 4 * cap + 4 * n0, 0, 16 * k, s);
-      cudaMemsetAsync(M + 8 * cap + 4 * n0, 0, 16 * k, s);
-      cudaMemset2DAsync(M + 12 * cap + n0, 4 * cap, 0, 4 * k, 3 * nc, s);
-    }
-    cudaEventRecord(S->add_done, s);
-    gs_status st = gs::check_launch("session add");
-    if (st != GS_OK) return st;
-    done += k;
+  // the staging buffer is free once the previous add's copies finished
+  const double t0 = gs::steady_now();
+  cudaError_t e;
+  while ((e = cudaEventQuery(S->add_done)) == cudaErrorNotReady) {
+    if (gs::steady_now() - t0 > 30.0) return gs::fail(GS_ERR_TIMEOUT, "session: add staging busy");
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
+  if (e != cudaSuccess) return gs::fail(GS_ERR_CUDA, "session: %s", cudaGetErrorString(e));
+  if (count > S->h_add_cap) {
+    cudaFreeHost(S->h_add);
+    S->h_add = nullptr;
+    if (cudaMallocHost(&S->h_add, sizeof(float) * (12 + 3 * nc) * count) != cudaSuccess) {
+      cudaGetLastError();
+      S->h_add_cap = 0;
+      return gs::fail(GS_ERR_OOM, "session: pinned staging of %lld Gaussians", (long long)count);
+    }
+    S->h_add_cap = count;
+  }
+  const int64_t k = count;
+  float* h = S->h_add;
+  float* hm = h;
+  float* hs = h + 4 * k;
+  float* hq = h + 8 * k;
+  float* hsh = h + 12 * k;
+  for (int64_t i = 0; i < k; ++i) {
+    hm[4 * i] = means[3 * i]; hm[4 * i + 1] = means[3 * i + 1]; hm[4 * i + 2] = means[3 * i + 2]; hm[4 * i + 3] = 0.f;
+    hs[4 * i] = log_scales[3 * i]; hs[4 * i + 1] = log_scales[3 * i + 1]; hs[4 * i + 2] = log_scales[3 * i + 2];
+    hs[4 * i + 3] = opa_logits[i];
+    for (int c = 0; c < 4; ++c) hq[4 * i + c] = quats[4 * i + c];
+  }
+  for (int p = 0; p < 3 * nc; ++p)
+    for (int64_t i = 0; i < k; ++i) hsh[(int64_t)p * k + i] = sh[i * 3 * nc + p];
+  std::unique_lock<std::mutex> lk(S->mu);
+  float* A = gs::arena_ptr(S, 0);
+  cudaStream_t s = S->stream;
+  cudaMemcpyAsync(A + 4 * n0, hm, 16 * k, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(A + 4 * cap + 4 * n0, hs, 16 * k, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(A + 8 * cap + 4 * n0, hq, 16 * k, cudaMemcpyHostToDevice, s);
+  cudaMemcpy2DAsync(A + 12 * cap + n0, 4 * cap, hsh, 4 * k, 4 * k, 3 * nc, cudaMemcpyHostToDevice, s);
+  for (int a = 2; a < 4; ++a) {  // fresh Adam moments for the new slots
+    float* M = gs::arena_ptr(S, a);
+    cudaMemsetAsync(M + 4 * n0, 0, 16 * k, s);
+    cudaMemsetAsync(M + 4 * cap + 4 * n0, 0, 16 * k, s);
+    cudaMemsetAsync(M + 8 * cap + 4 * n0, 0, 16 * k, s);
+    cudaMemset2DAsync(M + 12 * cap + n0, 4 * cap, 0, 4 * k, 3 * nc, s);
+  }
+  cudaEventRecord(S->add_done, s);
+  gs_status st = gs::check_launch("session add");
+  if (st != GS_OK) return st;
   S->n_active += count;
   S->lod_dirty = true;  // the new leaves overwrote coarse nodes
   return GS_OK;
@@ -735,10 +783,18 @@ gs_status gs_session_submit(gs_session* S, const gs_request* req, int64_t* id) {
   std::memcpy(r->pose, req->pose, sizeof(r->pose));
   r->image_out = req->image_out;
   r->arrival = req->arrival_s > 0.0 ? req->arrival_s : gs::steady_now();
-  if (req->kind == GS_REQUEST_TRAIN) r->target.assign(req->target, req->target + 3 * (int64_t)c.width * c.height);
+  if (req->kind == GS_REQUEST_TRAIN) {
+    r->target_bytes = sizeof(float) * 3 * (size_t)c.width * c.height;
+    r->target = gs::acquire_pinned(S, r->target_bytes);
+    if (!r->target) return gs::fail(GS_ERR_OOM, "session: pinned host memory for a target");
+    std::memcpy(r->target, req->target, r->target_bytes);
+  }
   std::unique_lock<std::mutex> lk(S->mu);
-  if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
-  if (S->stop) return gs::fail(GS_ERR_BUSY, "session is stopping");
+  if (S->fatal != GS_OK || S->stop) {
+    gs::release_target(S, r.get());
+    if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
+    return gs::fail(GS_ERR_BUSY, "session is stopping");
+  }
   r->id = (int64_t)S->all.size() + 1;
   S->all.push_back(r);
   S->queue.push_back(r);
@@ -764,6 +820,17 @@ gs_status gs_session_wait(gs_session* S, int64_t id, int32_t timeout_ms) {
   if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->state >= 2; }))
     return gs::fail(GS_ERR_TIMEOUT, "request %lld not done after %d ms", (long long)id, timeout_ms);
   return r->state == 3 ? gs::fail(r->status, "request %lld failed", (long long)id) : GS_OK;
+}
+
+gs_status gs_session_times(gs_session* S, int64_t id, double* arrival_s, double* done_s) {
+  if (!S || !arrival_s || !done_s) return gs::fail(GS_ERR_INVALID, "NULL session or output");
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (id < 1 || id > (int64_t)S->all.size()) return gs::fail(GS_ERR_INVALID, "unknown request id %lld", (long long)id);
+  const Req& r = *S->all[id - 1];
+  if (r.state < 2) return GS_ERR_BUSY;
+  *arrival_s = r.arrival;
+  *done_s = r.done_at;
+  return GS_OK;
 }
 
 gs_status gs_session_hold(gs_session* S, int32_t on) {
@@ -935,8 +1002,12 @@ gs_status gs_session_destroy(gs_session* S) {
   for (auto& a : S->arena) gs::dfree(a, S->in_use);
   gs::dfree(S->status_word, S->in_use);
   gs::dfree(S->step_dev, S->in_use);
+  gs::dfree(S->lod_parent, S->in_use);
+  gs::dfree(S->lod_ws, S->in_use);
   if (S->h_add) cudaFreeHost(S->h_add);
   if (S->add_done) cudaEventDestroy(S->add_done);
+  for (auto& r : S->all) r->target = nullptr;  // pooled buffers are freed below
+  for (float* p : S->pinned_all) cudaFreeHost(p);
   cudaStreamDestroy(S->stream);
   delete S;
   return GS_OK;

@@ -95,6 +95,15 @@ class Session:
         _lib.check(self.L.gs_session_wait(self.h, rid, timeout_ms), "gs_session_wait")
         return self._keep.pop(rid, None)
 
+    def times(self, rid: int) -> Optional[tuple]:
+        """(arrival, completion) in gs_session_now seconds, None while pending."""
+        a, d = C.c_double(), C.c_double()
+        st = self.L.gs_session_times(self.h, rid, C.byref(a), C.byref(d))
+        if st == _lib.GS_ERR_BUSY:
+            return None
+        _lib.check(st, "gs_session_times")
+        return a.value, d.value
+
     def image(self, rid: int) -> Optional[np.ndarray]:
         return self._keep.get(rid)
 

@@ -229,3 +229,66 @@ def random_records(views: Sequence[tuple], n: int, seed: int, tie_levels: int = 
         rect[v, :, 2] = np.where(culled, 0, x1)
         rect[v, :, 3] = np.where(culled, 0, y1)
     return depth, rect
+
+
+# ---------------------------------------------------------------------------
+# Streaming workload: a camera walking a 200 m loop; every frame brings new
+# Gaussians in its frustum and a handful of mixed-resolution requests
+# ---------------------------------------------------------------------------
+STREAM_RESOLUTIONS = ((960, 540), (1280, 720), (1600, 900), (1920, 1080))
+
+
+def stream_camera(k: int, n_frames: int, width: int = 1920, height: int = 1080, loop_m: float = 200.0,
+                  height_m: float = -1.5) -> Camera:
+    """Frame k's camera on a loop of loop_m metres (radius loop_m / 2 pi, at
+    height 1.5 m with y down), looking along the direction of travel;
+    f = 0.78 W, principal point at the image centre."""
+    r = loop_m / (2 * np.pi)
+    a = 2 * np.pi * k / max(1, n_frames)
+    eye = np.array([r * np.cos(a), height_m, r * np.sin(a)])
+    fwd = np.array([-np.sin(a), 0.0, np.cos(a)])
+    return look_at(eye, eye + fwd, 0.78 * width, 0.78 * width, width / 2, height / 2, width, height)
+
+
+def with_resolution(cam: Camera, width: int, height: int) -> Camera:
+    """The same pose with another image size (f = 0.78 W)."""
+    return Camera(cam.R, cam.t, 0.78 * width, 0.78 * width, width / 2, height / 2, int(width), int(height))
+
+
+def frustum_gaussians(cam: Camera, n: int, seed: int, sh_degree: int = 3, depth=(1.0, 8.0)) -> Scene:
+    """n Gaussians spawned in the camera's frustum: a uniform pixel, depth
+    U(1, 8) m, log-scale log(1.5 depth / f) + N(0, 0.2^2) per axis (about 1.5
+    px on screen), random rotation, opacity logit N(0, 1), SH DC U[0, 1] and
+    higher bands N(0, 0.05^2)."""
+    g = _rng(seed)
+    u = g.uniform(0, cam.width, n)
+    v = g.uniform(0, cam.height, n)
+    z = g.uniform(depth[0], depth[1], n)
+    pc = np.stack([(u - cam.cx) * z / cam.fx, (v - cam.cy) * z / cam.fy, z], axis=1)
+    R = np.asarray(cam.R, np.float64)
+    t = np.asarray(cam.t, np.float64)
+    means = ((pc - t) @ R).astype(np.float32)  # R^T (p - t)
+    log_scales = (np.log(1.5 * z / cam.fx)[:, None] + g.normal(0, 0.2, (n, 3))).astype(np.float32)
+    quats = g.normal(size=(n, 4)).astype(np.float32)
+    opa = g.normal(0.0, 1.0, n).astype(np.float32)
+    nc = (sh_degree + 1) ** 2
+    sh = np.zeros((n, 3, nc), np.float32)
+    sh[:, :, 0] = g.uniform(0, 1, (n, 3))
+    if nc > 1:
+        sh[:, :, 1:] = g.normal(0.0, 0.05, (n, 3, nc - 1))
+    return Scene(means, log_scales, quats, opa, sh)
+
+
+def stream_frame(k: int, n_frames: int, seed: int):
+    """Frame k of the stream: (camera at 1080p, U{10k..50k} new Gaussians in
+    its frustum, requests [(kind, width, height)] with U{1..8} requests, each
+    render (kind 0) or train (kind 1) with probability 1/2 and a resolution
+    drawn from 540p..1080p)."""
+    g = _rng(seed * 1000003 + k)
+    cam = stream_camera(k, n_frames)
+    new = frustum_gaussians(cam, int(g.integers(10_000, 50_001)), seed * 7919 + k)
+    reqs = []
+    for _ in range(int(g.integers(1, 9))):
+        w, h = STREAM_RESOLUTIONS[int(g.integers(0, len(STREAM_RESOLUTIONS)))]
+        reqs.append((0 if g.random() < 0.5 else 1, w, h))
+    return cam, new, reqs
