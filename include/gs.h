@@ -116,7 +116,19 @@ typedef struct {
   float bg[3];            /* background colour behind the last splat */
   float znear;            /* near plane (> 0) */
   int32_t clamp_jacobian; /* 1: guard t_x/t_z, t_y/t_z at +-1.3 (W/2)/fx, (H/2)/fy */
+  uint32_t schedule;      /* GS_SCHED_* bits (0 = defaults); set by gs_autotune_blend */
 } gs_raster_cfg;
+
+/* Schedule of the blend kernels (no effect on any result):
+ *   GS_SCHED_FWD_LONGEST_FIRST / GS_SCHED_BWD_LONGEST_FIRST: the composite /
+ *     backward takes the tiles in gs_bins.tile_order (longest lists first);
+ *   GS_SCHED_FWD_BATCH(b): splats staged in shared memory per batch by the
+ *     composite, b = 0: 128, 1: 64, 2: 256;
+ *   GS_SCHED_BWD_BATCH(b): the same for the single-pass backward, 0: 128, 1: 64. */
+#define GS_SCHED_FWD_LONGEST_FIRST 0x1u
+#define GS_SCHED_BWD_LONGEST_FIRST 0x2u
+#define GS_SCHED_FWD_BATCH(b) ((uint32_t)(b) << 4)
+#define GS_SCHED_BWD_BATCH(b) ((uint32_t)(b) << 8)
 
 /* Projected splats of V views, device memory, each array [V][n] (view-major):
  *   xy       float4  m = (x_int + x_frac, y_int + y_frac): the pixel-space
@@ -157,7 +169,13 @@ typedef struct {
  *             capacity (the lists are then truncated and must not be
  *             rendered), 2 = an index read from an earlier stage was out of
  *             range and its access was skipped (an internal error), [3]
- *             min(K, capacity) */
+ *             min(K, capacity)
+ *   tile_order optional [num_tiles]: written by gs_bin_sort, the tiles
+ *             ordered by decreasing list length (bucketed by powers of two;
+ *             empty tiles last); the composite and backward kernels then
+ *             take the longest lists first, so the long ones do not trail at
+ *             the end of the grid.  The order within a bucket is not fixed;
+ *             every output is independent of it.  NULL = natural order. */
 typedef struct {
   uint32_t* vals;
   uint32_t* ranges;
@@ -166,6 +184,7 @@ typedef struct {
   uint32_t* counts;
   int64_t capacity;
   int64_t num_tiles;
+  uint32_t* tile_order;
 } gs_bins;
 
 /* One Adam parameter group: elements [begin, end) of the arena; element e
@@ -360,6 +379,23 @@ GS_API gs_status gs_render_bwd_gaussians(const gs_params* params, const float* p
                                          const gs_camera* cams, int32_t views, const gs_splats* splats,
                                          const gs_bins* bins, const gs_raster_cfg* cfg, gs_grads* grads,
                                          float* dL_dpose, void* ws, size_t ws_bytes, gs_stream stream);
+
+/* Autotuner of the blend schedule: times every composite schedule (tile
+ * order natural / longest lists first x 128 / 64 / 256 splats per batch) and
+ * every single-pass backward schedule (order x 128 / 64) on the caller's
+ * current splats and tile lists, `reps` launches each after one warm-up, and
+ * writes the fastest of each into cfg->schedule (other bits unchanged).
+ * Longest-first candidates need bins->tile_order.  image: device, the image's
+ * size (overwritten; on return it holds the composite of the chosen
+ * schedule); dL_dimage: device upstream gradient; ws: the gs_render_bwd
+ * workspace (n Gaussians).  times_ms (optional, host, 10 floats): mean time
+ * of each candidate, the 6 composite ones first (NaN where skipped).
+ * Synchronises on its own events (bounded wait, GS_ERR_TIMEOUT): not for use
+ * under stream capture.  Schedules change no result. */
+GS_API gs_status gs_autotune_blend(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
+                                   int32_t views, gs_raster_cfg* cfg, float* image, const float* dL_dimage,
+                                   int64_t n, void* ws, size_t ws_bytes, int32_t reps, float* times_ms,
+                                   gs_stream stream);
 
 /* Fused Adam over one flat float arena of n elements (parameters p, gradients
  * g, moments m, v; all device, 16-byte aligned), in one launch for all groups

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgs.so")
 GS_OK, GS_ERR_INVALID, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NONFINITE, GS_ERR_BUSY = range(7)
 GS_MAX_VIEWS = 64
 GS_TILE = 16
+GS_SCHED_FWD_LONGEST_FIRST, GS_SCHED_BWD_LONGEST_FIRST = 0x1, 0x2
 GS_NOALLOC_SCRATCH_BYTES = 8 << 20  # static scratch of gs_bin_sort_noalloc
 GS_MAX_ADAM_GROUPS = 64
 
@@ -22,7 +23,7 @@ EXPORTED = (
     "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
-    "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod",
+    "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod", "gs_autotune_blend",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
     "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_stats", "gs_session_read_params",
     "gs_session_save", "gs_session_load", "gs_session_destroy",
@@ -52,7 +53,7 @@ class GsCamera(C.Structure):
 
 class GsRasterCfg(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("bg", C.c_float * 3),
-                ("znear", C.c_float), ("clamp_jacobian", C.c_int32)]
+                ("znear", C.c_float), ("clamp_jacobian", C.c_int32), ("schedule", C.c_uint32)]
 
 
 class GsSplats(C.Structure):
@@ -64,7 +65,7 @@ class GsSplats(C.Structure):
 class GsBins(C.Structure):
     _fields_ = [("vals", C.c_void_p), ("ranges", C.c_void_p), ("pair_off", C.c_void_p),
                 ("keys", C.c_void_p), ("counts", C.c_void_p), ("capacity", C.c_int64),
-                ("num_tiles", C.c_int64)]
+                ("num_tiles", C.c_int64), ("tile_order", C.c_void_p)]
 
 
 class GsAdamGroup(C.Structure):
@@ -146,6 +147,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_render_bwd_gaussians.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsSplats), P(GsBins),
                                           P(GsRasterCfg), P(GsGrads), vp, vp, sz, vp]
     L.gs_adam_step.argtypes = [vp, vp, vp, vp, i64, P(GsAdamCfg), i32, vp]
+    L.gs_autotune_blend.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp, i64, vp, sz,
+                                    i32, C.POINTER(C.c_float), vp]
     L.gs_lod_nodes.argtypes = [i64]
     L.gs_lod_nodes.restype = i64
     L.gs_lod_build_workspace.argtypes = [i64]
@@ -179,7 +182,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
                  "gs_render_bwd",
                  "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
-                 "gs_render_stats", "gs_lod_build", "gs_project_lod"):
+                 "gs_render_stats", "gs_lod_build", "gs_project_lod", "gs_autotune_blend"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

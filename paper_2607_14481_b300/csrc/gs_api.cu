@@ -73,6 +73,9 @@ static gs_status check_cfg(const gs_raster_cfg* cfg) {
   if (cfg->tile_w != kTile || cfg->tile_h != kTile)
     return fail(GS_ERR_INVALID, "tile must be %dx%d (got %dx%d)", kTile, kTile, cfg->tile_w, cfg->tile_h);
   if (!(cfg->znear > 0.f)) return fail(GS_ERR_INVALID, "znear must be > 0");
+  if ((cfg->schedule & ~kSchedKnown) || ((cfg->schedule >> kSchedFwdBatchShift) & 3u) == 3u ||
+      ((cfg->schedule >> kSchedBwdBatchShift) & 3u) > 1u)
+    return fail(GS_ERR_INVALID, "unknown schedule 0x%x", cfg->schedule);
   return GS_OK;
 }
 

@@ -259,6 +259,9 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
 constexpr uint32_t kStatusCapacity = 1u, kStatusIndex = 2u;
 
 __global__ void k_init_counts(uint32_t* counts, uint32_t* scalars, uint32_t m, uint32_t tiles) {
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) scalars[i] = 0;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   scalars[0] = m;      // live length of the item scan
   scalars[1] = tiles;  // live length of the tile scan
   counts[0] = 0; counts[1] = 0; counts[2] = 0; counts[3] = 0;
@@ -511,6 +514,48 @@ __global__ void __launch_bounds__(kThreads) k_tile_sort(const TileSortArgs a) {
   if (threadIdx.x == 0) a.ranges[2 * (uint64_t)t + 1] = start + cnt;
 }
 
+// Tiles in decreasing order of list length, bucketed by powers of two:
+// bucket 0 holds lists of >= 2^15 pairs, bucket 15 single pairs, bucket 16
+// the empty tiles.  Counting pass, then placement; the order within a bucket
+// follows the atomics and does not matter (tiles are independent).
+constexpr int kOrderBuckets = 17;
+
+__device__ __forceinline__ int order_bucket(uint32_t len) {
+  return len == 0 ? kOrderBuckets - 1 : 15 - min(15, 31 - __clz(len));
+}
+
+__global__ void __launch_bounds__(kThreads) k_order_count(const uint32_t* __restrict__ ranges, uint32_t tiles,
+                                                          uint32_t* __restrict__ bucket_count) {
+  __shared__ uint32_t s[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) s[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
+    const uint32_t len = ranges[2 * (uint64_t)t + 1] - ranges[2 * (uint64_t)t];
+    atomicAdd(&s[order_bucket(len)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets && s[threadIdx.x]) atomicAdd(&bucket_count[threadIdx.x], s[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_order_place(const uint32_t* __restrict__ ranges, uint32_t tiles,
+                                                          const uint32_t* __restrict__ bucket_count,
+                                                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_base[kOrderBuckets];
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < kOrderBuckets; ++b) {
+      s_base[b] = run;
+      run += bucket_count[b];
+    }
+  }
+  __syncthreads();
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
+    const int b = order_bucket(ranges[2 * (uint64_t)t + 1] - ranges[2 * (uint64_t)t]);
+    const uint32_t pos = s_base[b] + atomicAdd(&cursor[b], 1u);
+    if (pos < tiles) order[pos] = t;
+  }
+}
+
 inline unsigned grid_for(int64_t n, int threads) {
   return (unsigned)std::max<int64_t>(1, (n + threads - 1) / threads);
 }
@@ -570,7 +615,8 @@ gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b
 // Workspace of gs_bin_sort: pair arrays sized capacity, one scan workspace.
 // ---------------------------------------------------------------------------
 struct BinWs {
-  uint32_t* scalars;  // [0] = item count, [1] = tile count, [2] = scanned tile total
+  uint32_t* scalars;  // [0] = item count, [1] = tile count, [2] = scanned tile total,
+                      // [32, 49) tile-order bucket counts, [64, 81) their cursors
   uint32_t* slot;
   uint64_t *keys_a, *keys_b;
   void* scan;
@@ -586,7 +632,7 @@ static BinWs bin_layout(char* base, int64_t m, int64_t cap) {
     return p;
   };
   const size_t c = (size_t)std::max<int64_t>(1, cap);
-  w.scalars = (uint32_t*)take(16);
+  w.scalars = (uint32_t*)take(128 * sizeof(uint32_t));
   w.slot = (uint32_t*)take(sizeof(uint32_t) * c);
   w.keys_a = (uint64_t*)take(sizeof(uint64_t) * c);
   w.keys_b = (uint64_t*)take(sizeof(uint64_t) * c);
@@ -605,16 +651,26 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   const int64_t cap = bins.capacity;
   BinWs w = bin_layout(static_cast<char*>(ws), m, cap);
   uint32_t* counts = bins.counts;
-  k_init_counts<<<1, 1, 0, s>>>(counts, w.scalars, (uint32_t)m, (uint32_t)vt.total_tiles);
+  // the tile order (when asked for) is written on every path, from the final ranges
+  auto finish = [&]() {
+    if (bins.tile_order && vt.total_tiles > 0) {
+      const unsigned og = (unsigned)std::min<int64_t>(592, (vt.total_tiles + kThreads - 1) / kThreads);
+      k_order_count<<<og, kThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, w.scalars + 32);
+      k_order_place<<<og, kThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, w.scalars + 32,
+                                            w.scalars + 64, bins.tile_order);
+    }
+    return check_launch("bin_sort");
+  };
+  k_init_counts<<<1, 128, 0, s>>>(counts, w.scalars, (uint32_t)m, (uint32_t)vt.total_tiles);
   // the ranges array holds each tile's (start, count) until the tile is sorted
   if (cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)bins.num_tiles, s) != cudaSuccess)
     return check_launch("memset ranges");
-  if (m == 0) return check_launch("bin_sort");
+  if (m == 0) return finish();
   // 1. pair slots per (view, Gaussian): exclusive scan of the tile counts
   gs_status st = launch_scan(sp.touched, 1, bins.pair_off, 1, w.scalars, m, counts + 1, w.scan, s);
   if (st != GS_OK) return st;
   k_pair_status<<<1, 1, 0, s>>>(counts, cap);
-  if (cap == 0 || vt.total_tiles == 0) return check_launch("bin_sort");
+  if (cap == 0 || vt.total_tiles == 0) return finish();
   PairArgs pa{sp.touched, reinterpret_cast<const uint2*>(sp.rect), sp.depth, bins.pair_off, counts, sp.n, cap,
               bins.ranges, w.slot, w.keys_a};
   const unsigned pgrid = grid_for(m, 256);  // 8 warps of 32 items per block
@@ -628,7 +684,7 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   while (id_bits < 32 && (1ll << id_bits) < sp.n) ++id_bits;
   TileSortArgs ta{w.keys_a, w.keys_b, bins.ranges, bins.vals, reinterpret_cast<uint64_t*>(bins.keys), id_bits};
   k_tile_sort<<<(unsigned)vt.total_tiles, kThreads, 0, s>>>(ta);
-  return check_launch("bin_sort");
+  return finish();
 }
 
 }  // namespace gs

@@ -17,6 +17,13 @@ gs_status check_launch(const char* what);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Schedule bits of gs_raster_cfg (see gs.h).
+constexpr uint32_t kSchedFwdLongestFirst = GS_SCHED_FWD_LONGEST_FIRST;
+constexpr uint32_t kSchedBwdLongestFirst = GS_SCHED_BWD_LONGEST_FIRST;
+constexpr int kSchedFwdBatchShift = 4;
+constexpr int kSchedBwdBatchShift = 8;
+constexpr uint32_t kSchedKnown = 0x3u | (3u << 4) | (3u << 8);
+
 // Fills a ViewTable from host cameras; returns false (with a message) on
 // invalid cameras.
 bool make_view_table(const gs_camera* cams, int views, ViewTable* vt);

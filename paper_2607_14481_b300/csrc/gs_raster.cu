@@ -25,7 +25,8 @@ namespace {
 
 constexpr int kThreads = kTilePixels / 2;   // two pixels per thread
 constexpr int kWarps = kThreads / 32;
-constexpr int kBatch = kThreads;            // splats staged per batch
+// Splats staged per batch: a template parameter of the composite (64, 128,
+// 256) and of the single-pass backward (64, 128), chosen by the schedule.
 constexpr int kRowsPerWarp = 32 / kTile * 2;  // 4
 
 struct Eval {
@@ -106,6 +107,7 @@ __device__ __forceinline__ TileCoords tile_coords(const ViewTable& vt, int gt) {
 }
 
 struct FwdArgs {
+  const uint32_t* order;  // tile of each block (nullptr: block index)
   const float4* xy;
   const float4* conic;
   const float4* rgb;
@@ -153,15 +155,16 @@ __device__ __forceinline__ void stage_splat(const float4* xy, const float4* coni
 // COUNT = true is the diagnostic instantiation behind gs_render_stats: the
 // same loop, also counting per pixel the splats tested (up to and including
 // the one that stops it) and blended, and per tile the backward's walk length.
-template <bool COUNT>
+template <bool COUNT, int kBatch>
 __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const ViewTable vt,
                                                          unsigned long long* stats) {
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch];
   __shared__ float2 s_rows[kBatch];
   __shared__ int s_last;
-  const TileCoords tc = tile_coords(vt, blockIdx.x);
+  const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
+  const TileCoords tc = tile_coords(vt, gt);
   const ViewInfo& vi = vt.v[tc.v];
-  const uint2 rg = a.ranges[blockIdx.x];
+  const uint2 rg = a.ranges[gt];
   const int64_t vbase = (int64_t)tc.v * a.n;
   float T0 = 1.f, T1 = 1.f;
   float c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
@@ -171,12 +174,11 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
   if (COUNT && threadIdx.x == 0) s_last = -1;
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
     if (__syncthreads_count(d0 && d1) == kThreads) break;
-    const uint32_t j = start + threadIdx.x;
-    if (j < rg.y)
-      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
+    const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
+    for (int t = threadIdx.x; t < cnt; t += kThreads)
+      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + t, t, tc.ox, tc.oy, s_geo, s_geo2,
                   s_rgb, s_rows, nullptr, COUNT ? nullptr : a.counts);
     __syncthreads();
-    const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     for (int k = 0; k < cnt && !(d0 && d1); ++k) {
       const float2 rows = s_rows[k];
       if (tc.wlo > rows.y || tc.whi < rows.x) continue;  // warp-uniform
@@ -252,6 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
 }
 
 struct BwdArgs {
+  const uint32_t* order;  // tile of each block (nullptr: block index)
   const float4* xy;
   const float4* conic;
   const float4* rgb;
@@ -405,6 +408,7 @@ __device__ __forceinline__ void splat_grad_front(const Eval& e, const float4 co,
 }
 
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const ViewTable vt) {
+  constexpr int kBatch = kThreads;
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
   __shared__ float2 s_rows[kBatch];
   __shared__ uint32_t s_pidx[kBatch];
@@ -412,9 +416,10 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
   __shared__ uint8_t s_hit[kBatch][kWarps];
   __shared__ int s_maxlast;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const TileCoords tc = tile_coords(vt, blockIdx.x);
+  const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
+  const TileCoords tc = tile_coords(vt, gt);
   const ViewInfo& vi = vt.v[tc.v];
-  const uint2 rg = a.ranges[blockIdx.x];
+  const uint2 rg = a.ranges[gt];
   const int64_t vbase = (int64_t)tc.v * a.n;
   if (threadIdx.x == 0) s_maxlast = -1;
 
@@ -528,16 +533,19 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
 // and including i, so one traversal in the forward's order, with the forward's
 // own decisions (same splat test, same transmittance products, same stop),
 // yields every gradient without a replay and without recovering T by division.
+template <int kBatch>
 __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, const ViewTable vt) {
+  static_assert(kBatch <= kThreads, "one staged splat per thread");
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
   __shared__ float2 s_rows[kBatch];
   __shared__ uint32_t s_pidx[kBatch];
   __shared__ float s_red[kBatch][kWarps][kPartialValues];
   __shared__ uint8_t s_hit[kBatch][kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const TileCoords tc = tile_coords(vt, blockIdx.x);
+  const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
+  const TileCoords tc = tile_coords(vt, gt);
   const ViewInfo& vi = vt.v[tc.v];
-  const uint2 rg = a.ranges[blockIdx.x];
+  const uint2 rg = a.ranges[gt];
   const int64_t vbase = (int64_t)tc.v * a.n;
 
   const int64_t np = (int64_t)vi.W * vi.H;
@@ -624,6 +632,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
 gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                             const gs_raster_cfg& cfg, float* image, float* alpha, cudaStream_t s) {
   FwdArgs a;
+  a.order = (cfg.schedule & kSchedFwdLongestFirst) ? bins.tile_order : nullptr;
   a.xy = reinterpret_cast<const float4*>(sp.xy);
   a.conic = reinterpret_cast<const float4*>(sp.conic);
   a.rgb = reinterpret_cast<const float4*>(sp.rgb);
@@ -635,13 +644,18 @@ gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const View
   a.image = image;
   a.alpha = alpha;
   if (vt.total_tiles == 0) return GS_OK;
-  k_render_fwd<false><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr);
+  switch ((cfg.schedule >> kSchedFwdBatchShift) & 3u) {
+    case 1: k_render_fwd<false, 64><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr); break;
+    case 2: k_render_fwd<false, 256><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr); break;
+    default: k_render_fwd<false, 128><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr); break;
+  }
   return check_launch("k_render_fwd");
 }
 
 gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                               unsigned long long* stats, cudaStream_t s) {
   FwdArgs a;
+  a.order = nullptr;
   a.xy = reinterpret_cast<const float4*>(sp.xy);
   a.conic = reinterpret_cast<const float4*>(sp.conic);
   a.rgb = reinterpret_cast<const float4*>(sp.rgb);
@@ -654,7 +668,7 @@ gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const Vi
   a.alpha = nullptr;
   if (cudaMemsetAsync(stats, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return check_launch("stats");
   if (vt.total_tiles == 0) return GS_OK;
-  k_render_fwd<true><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, stats);
+  k_render_fwd<true, 128><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, stats);
   return check_launch("k_render_fwd<count>");
 }
 
@@ -662,6 +676,7 @@ gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const View
                             const gs_raster_cfg& cfg, const float* dimage, const float* dalpha,
                             const float* image, float* partials, cudaStream_t s) {
   BwdArgs a;
+  a.order = (cfg.schedule & kSchedBwdLongestFirst) ? bins.tile_order : nullptr;
   a.xy = reinterpret_cast<const float4*>(sp.xy);
   a.conic = reinterpret_cast<const float4*>(sp.conic);
   a.rgb = reinterpret_cast<const float4*>(sp.rgb);
@@ -679,7 +694,10 @@ gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const View
   a.partials = partials;
   if (vt.total_tiles == 0) return GS_OK;
   if (image && !dalpha) {
-    k_render_bwd_front<<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
+    if (((cfg.schedule >> kSchedBwdBatchShift) & 3u) == 1)
+      k_render_bwd_front<64><<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
+    else
+      k_render_bwd_front<128><<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
     return check_launch("k_render_bwd_front");
   }
   k_render_bwd<<<vt.total_tiles, kThreads, 0, s>>>(a, vt);

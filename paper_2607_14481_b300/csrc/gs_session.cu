@@ -71,7 +71,7 @@ struct Dev {
 // Device and pinned buffers of one batch in flight.
 struct Ctx {
   cudaEvent_t done = nullptr;
-  Dev splat_buf, pair_off, ranges, counts, vals, ws_bin, ws_bwd, img, dimg, tgt, loss_ws, loss, poses, dpose;
+  Dev splat_buf, pair_off, ranges, order, counts, vals, ws_bin, ws_bwd, img, dimg, tgt, loss_ws, loss, poses, dpose;
   float* h_img = nullptr;       // pinned staging of rendered images
   float* h_poses = nullptr;     // pinned poses [2][max views][12]
   uint32_t* h_counts = nullptr; // pinned [8]: counts of the render and train sub-batches
@@ -141,6 +141,7 @@ size_t ctx_device_bytes(const gs_session_config& c, int64_t cap_n, int64_t pair_
   add(gs_splats_bytes(cap_n, (int32_t)V));
   add(4 * (size_t)cap_n * V);                     // pair_off
   add(8 * (size_t)max_tiles(c) * V);              // ranges
+  add(4 * (size_t)max_tiles(c) * V);              // tile order
   add(32);                                        // counts of both sub-batches
   add(4 * (size_t)pair_cap);                      // vals
   add(bin_sort_workspace_bytes(cap_n * V, pair_cap));
@@ -221,6 +222,7 @@ gs_status alloc_ctx(gs_session* S, Ctx& c) {
   if ((st = dalloc(c.splat_buf, gs_splats_bytes(S->capacity, (int32_t)V), u)) != GS_OK) return st;
   if ((st = dalloc(c.pair_off, 4 * (size_t)S->capacity * V, u)) != GS_OK) return st;
   if ((st = dalloc(c.ranges, 8 * (size_t)max_tiles(cf) * V, u)) != GS_OK) return st;
+  if ((st = dalloc(c.order, 4 * (size_t)max_tiles(cf) * V, u)) != GS_OK) return st;
   if ((st = dalloc(c.counts, 32, u)) != GS_OK) return st;
   if ((st = dalloc(c.img, 12 * (size_t)px * V, u)) != GS_OK) return st;
   if ((st = dalloc(c.dimg, 12 * (size_t)px * V, u)) != GS_OK) return st;
@@ -241,7 +243,7 @@ gs_status alloc_ctx(gs_session* S, Ctx& c) {
 }
 
 void free_ctx(gs_session* S, Ctx& c) {
-  Dev* devs[] = {&c.splat_buf, &c.pair_off, &c.ranges, &c.counts, &c.vals, &c.ws_bin, &c.ws_bwd, &c.img,
+  Dev* devs[] = {&c.splat_buf, &c.pair_off, &c.ranges, &c.order, &c.counts, &c.vals, &c.ws_bin, &c.ws_bwd, &c.img,
                  &c.dimg, &c.tgt, &c.loss_ws, &c.loss, &c.poses, &c.dpose};
   for (Dev* d : devs) dfree(*d, S->in_use);
   if (c.h_img) cudaFreeHost(c.h_img);
@@ -330,7 +332,8 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     gs_splats sp;
     gs_splats_carve(c.splat_buf.p, PR.n, (int32_t)R.size(), &sp);
     gs_bins b{static_cast<uint32_t*>(c.vals.p), static_cast<uint32_t*>(c.ranges.p),
-              static_cast<uint32_t*>(c.pair_off.p), nullptr, counts, c.pair_cap, vt.total_tiles};
+              static_cast<uint32_t*>(c.pair_off.p), nullptr, counts, c.pair_cap, vt.total_tiles,
+              static_cast<uint32_t*>(c.order.p)};
     if ((st = launch_project(PR, poses, vt, cf.raster, sp, s, parent, n, cf.lod_tau)) != GS_OK) return st;
     if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, s)) != GS_OK) return st;
     if ((st = launch_render_fwd(sp, b, vt, cf.raster, img, nullptr, s)) != GS_OK) return st;
@@ -361,7 +364,8 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     gs_splats sp;
     gs_splats_carve(c.splat_buf.p, n, (int32_t)T.size(), &sp);
     gs_bins b{static_cast<uint32_t*>(c.vals.p), static_cast<uint32_t*>(c.ranges.p),
-              static_cast<uint32_t*>(c.pair_off.p), nullptr, counts + 4, c.pair_cap, vt.total_tiles};
+              static_cast<uint32_t*>(c.pair_off.p), nullptr, counts + 4, c.pair_cap, vt.total_tiles,
+              static_cast<uint32_t*>(c.order.p)};
     float* timg = img + off;
     if ((st = launch_project(P, tposes, vt, cf.raster, sp, s)) != GS_OK) return st;
     if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, s)) != GS_OK) return st;

@@ -147,7 +147,8 @@ class Rasterizer:
     device counts (one 16-byte copy); with check=False nothing synchronises."""
 
     def __init__(self, n: int, sh_degree: int, cams: Sequence[Camera], bg=(0.0, 0.0, 0.0), znear=0.2,
-                 clamp_jacobian=True, capacity: Optional[int] = None, device="cuda", keep_keys=False):
+                 clamp_jacobian=True, capacity: Optional[int] = None, device="cuda", keep_keys=False,
+                 largest_first: bool = True):
         self.L = _lib.load()
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.device = torch.device(device)
@@ -161,6 +162,7 @@ class Rasterizer:
         self.pair_off = torch.empty(max(1, self.n * V), dtype=torch.int32, device=self.device)
         self.counts = torch.zeros(4, dtype=torch.int32, device=self.device)
         self.keep_keys = keep_keys
+        self.largest_first = largest_first
         self.capacity = 0
         self.set_capacity(capacity if capacity is not None else max(4096, 4 * self.n * V))
 
@@ -176,6 +178,7 @@ class Rasterizer:
         if hasattr(self, "ranges") and self.ranges.numel() >= 2 * self.num_tiles:
             return
         self.ranges = torch.zeros(max(2, 2 * self.num_tiles), dtype=torch.int32, device=self.device)
+        self.tile_order = torch.zeros(max(1, self.num_tiles), dtype=torch.int32, device=self.device)
 
     def set_capacity(self, cap: int) -> None:
         cap = int(cap)
@@ -190,9 +193,10 @@ class Rasterizer:
                                   device=self.device)
 
     def bins_struct(self):
+        order = self.tile_order.data_ptr() if self.largest_first else None
         return _lib.GsBins(self.vals.data_ptr(), self.ranges.data_ptr(), self.pair_off.data_ptr(),
                            self.keys.data_ptr() if self.keys is not None else None, self.counts.data_ptr(),
-                           self.capacity, self.num_tiles)
+                           self.capacity, self.num_tiles, order)
 
     def new_image(self) -> torch.Tensor:
         return torch.empty(3 * self.pixels, dtype=torch.float32, device=self.device)
@@ -241,6 +245,20 @@ class Rasterizer:
         b = self.bins_struct()
         _lib.check(self.L.gs_render_fwd(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
                                         C.byref(self.cfg), _p(image), _p(alpha), _stream()), "gs_render_fwd")
+
+    def autotune(self, image: torch.Tensor, dimage: torch.Tensor, reps: int = 5) -> dict:
+        """gs_autotune_blend on the current tile lists: picks the composite
+        and backward schedules (tile order, splats per batch) and keeps them
+        in this Rasterizer's config.  Synchronises.  Returns the candidates'
+        times and the chosen schedule."""
+        b = self.bins_struct()
+        t = (C.c_float * 10)()
+        _lib.check(self.L.gs_autotune_blend(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
+                                            C.byref(self.cfg), _p(image), _p(dimage), self.n, _p(self.ws_bwd),
+                                            self.ws_bwd.numel(), int(reps), t, _stream()), "gs_autotune_blend")
+        names = [f"fwd_{o}_{b}" for o in ("natural", "longest") for b in (128, 64, 256)] + \
+                [f"bwd_{o}_{b}" for o in ("natural", "longest") for b in (128, 64)]
+        return {"schedule": int(self.cfg.schedule), "ms": {k: float(v) for k, v in zip(names, t)}}
 
     def render_stats(self) -> dict:
         """Work counts of the current tile lists (synchronises): pairs tested

@@ -362,3 +362,64 @@ def test_full_size_500k_720p_sampled_windows(cuda_device):
     for image in (None, img):  # replay + reverse walk, and the single front-to-back pass
         g_gpu = gpu_backward(r, arena, poses, [dfull], image=image)
         compare_grads(g_gpu, g_ref)
+
+
+def test_tile_order_is_a_bucketed_permutation_and_changes_nothing(cuda_device):
+    """Longest-lists-first scheduling: the order is a permutation of the
+    tiles with non-increasing power-of-two length buckets (empty tiles last),
+    and images and gradients are bit-identical to the natural order."""
+    sc, cams, _ = synth.diffcheck()
+    ref = oracle.render(sc, cams)
+    _, dimg = oracle.mse_loss(ref["image"], synth.diffcheck()[2])
+    out = []
+    for lf in (False, True):
+        r, arena, poses, img, alpha = gpu_forward(sc, cams)
+        r.largest_first = lf
+        r.forward(arena, poses, img, alpha)
+        g = gpu_backward(r, arena, poses, dimg, image=img)
+        torch.cuda.synchronize()
+        out.append((img.clone(), alpha.clone(), g))
+        if lf:
+            order = r.tile_order[:r.num_tiles].cpu().numpy().astype(np.int64)
+            assert np.array_equal(np.sort(order), np.arange(r.num_tiles))
+            rg = r.ranges[:2 * r.num_tiles].cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+            L = (rg[:, 1] - rg[:, 0])[order]
+            b = np.where(L == 0, 16, 15 - np.minimum(15, np.floor(np.log2(np.maximum(L, 1))).astype(np.int64)))
+            assert np.all(np.diff(b) >= 0)
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    for k in out[0][2]:
+        assert np.array_equal(out[0][2][k], out[1][2][k]), k
+
+
+def test_schedules_change_no_result_and_autotune_picks_one(cuda_device):
+    """Every blend schedule (tile order x splats per batch) gives bit-identical
+    images and gradients; the autotuner times them and keeps one."""
+    from paper_2607_14481_b300 import _lib
+    sc, cams, targets = synth.diffcheck()
+    ref = oracle.render(sc, cams)
+    _, dimg = oracle.mse_loss(ref["image"], targets)
+    base = None
+    for order in (0, 1):
+        for fb in (0, 1, 2):
+            for bb in (0, 1):
+                sched = (order * (_lib.GS_SCHED_FWD_LONGEST_FIRST | _lib.GS_SCHED_BWD_LONGEST_FIRST)) | (fb << 4) | \
+                        (bb << 8)
+                r, arena, poses, img, alpha = gpu_forward(sc, cams)
+                r.cfg.schedule = sched
+                r.forward(arena, poses, img, alpha)
+                g = gpu_backward(r, arena, poses, dimg, image=img)
+                torch.cuda.synchronize()
+                got = (img.clone(), alpha.clone(), g)
+                if base is None:
+                    base = got
+                    continue
+                assert torch.equal(base[0], got[0]) and torch.equal(base[1], got[1]), hex(sched)
+                for k in base[2]:
+                    assert np.array_equal(base[2][k], got[2][k]), (hex(sched), k)
+    r, arena, poses, img, alpha = gpu_forward(sc, cams)
+    d = torch.from_numpy(np.concatenate([np.asarray(x, np.float32).reshape(-1) for x in dimg])).cuda()
+    res = r.autotune(img, d, reps=2)
+    assert r.cfg.schedule == res["schedule"]
+    assert all(np.isfinite(v) and v > 0 for v in res["ms"].values())
+    # the image the autotuner leaves behind is the composite
+    assert torch.equal(img, base[0])
