@@ -332,7 +332,7 @@ def run_ours(args, ws, rank, local):
     peaks = load_peaks()
     roof = roofline(wl, stage_ms, work, peaks)
     plain_pixels = wl.pixels_per_iter
-    n_launch = launches_per_step(1, wl.rast.num_tiles)
+    n_launch = launches_per_step(1, wl.rast.num_tiles, bool(wl.tuning["schedule"] & 3))
     plain_tuning = wl.tuning
     del wl
     torch.cuda.empty_cache()
@@ -453,14 +453,15 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
                         "3-level LoD (8-child moment merge, tau = 1 px) for renders, 80 GB HBM budget"}
 
 
-def launches_per_step(views, num_tiles):
+def launches_per_step(views, num_tiles, tile_order=False):
     """Kernels one training step launches (memsets excluded): projection 1;
     binning 11 (counts, pair-offset scan 3, status, place, tile scan 3,
     keys, tile sort); composite 1; loss 2; per-pixel backward 1;
     per-Gaussian backward 5 (pair sums, projection, SH, pose chunks and
-    total); Adam 3 (parameters, poses, step counter)."""
+    total); Adam 3 (parameters, poses, step counter); with a longest-first
+    schedule the binning adds 2 (tile order)."""
     scan = 3
-    bin_sort = 1 + scan + 1 + 1 + scan + 1 + 1
+    bin_sort = 1 + scan + 1 + 1 + scan + 1 + 1 + (2 if tile_order else 0)
     return 1 + bin_sort + 1 + 2 + 1 + 5 + 3
 
 
@@ -483,6 +484,16 @@ def load_peaks():
 # reduction adds.  The backward's algorithmic work tests each pair once (the
 # single front-to-back pass does exactly that).
 OPS_TEST, OPS_FWD_BLEND, OPS_BWD_BLEND = 21, 7, 63
+
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), for the workload it was
+# taken on; the source summary is under profiles/.
+MEASURED_TRAFFIC = {
+    ("render_bwd_pixels", 1_000_000, (1280, 720), 1): {
+        "bytes": 75.768e6 + 22.544e6,
+        "source": "profiles/k_render_bwd_front_1M_720p.md (k_render_bwd_front<64>, pose 50)"},
+}
 
 
 def roofline(wl, stage_ms, work, peaks):
@@ -517,7 +528,11 @@ def roofline(wl, stage_ms, work, peaks):
                         "frac": ach / fp32_peak, "algorithmic": amount}
     dom = max(per, key=lambda k: stage_ms[k])
     out = dict(table[dom])
-    out.update({"kernel": dom, "traffic": None,
+    views = len(wl.steps[0].cams)
+    key = (dom, wl.n, (wl.cams[0].width, wl.cams[0].height), views)
+    tr = MEASURED_TRAFFIC.get(key)
+    out.update({"kernel": dom, "traffic": tr["bytes"] if tr else None,
+                "traffic_source": tr["source"] if tr else None,
                 "peak_source": (f"{peaks['source']} HBM copy (burst)" if out["bound"] == "hbm" else
                                 "148 SMs x 128 FP32 lanes x max SM clock"),
                 "work_counts": work, "per_stage": table})

@@ -192,8 +192,12 @@ class Rasterizer:
         self.ws_bwd = torch.empty(self.L.gs_render_bwd_workspace(self.n, self.views, cap), dtype=torch.uint8,
                                   device=self.device)
 
-    def bins_struct(self):
-        order = self.tile_order.data_ptr() if self.largest_first else None
+    def bins_struct(self, with_order: Optional[bool] = None):
+        """The tile lists; the longest-first tile order is computed only when
+        the schedule reads it (or when asked, for the autotuner)."""
+        if with_order is None:
+            with_order = bool(self.cfg.schedule & (_lib.GS_SCHED_FWD_LONGEST_FIRST | _lib.GS_SCHED_BWD_LONGEST_FIRST))
+        order = self.tile_order.data_ptr() if (self.largest_first and with_order) else None
         return _lib.GsBins(self.vals.data_ptr(), self.ranges.data_ptr(), self.pair_off.data_ptr(),
                            self.keys.data_ptr() if self.keys is not None else None, self.counts.data_ptr(),
                            self.capacity, self.num_tiles, order)
@@ -251,7 +255,10 @@ class Rasterizer:
         and backward schedules (tile order, splats per batch) and keeps them
         in this Rasterizer's config.  Synchronises.  Returns the candidates'
         times and the chosen schedule."""
-        b = self.bins_struct()
+        # the current lists once more, with their longest-first order
+        b = self.bins_struct(with_order=True)
+        _lib.check(self.L.gs_bin_sort(C.byref(self.splats), self.cam_struct, self.views, C.byref(self.cfg),
+                                      C.byref(b), _p(self.ws_bin), self.ws_bin.numel(), _stream()), "gs_bin_sort")
         t = (C.c_float * 10)()
         _lib.check(self.L.gs_autotune_blend(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
                                             C.byref(self.cfg), _p(image), _p(dimage), self.n, _p(self.ws_bwd),

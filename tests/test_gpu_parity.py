@@ -373,8 +373,9 @@ def test_tile_order_is_a_bucketed_permutation_and_changes_nothing(cuda_device):
     _, dimg = oracle.mse_loss(ref["image"], synth.diffcheck()[2])
     out = []
     for lf in (False, True):
+        from paper_2607_14481_b300 import _lib
         r, arena, poses, img, alpha = gpu_forward(sc, cams)
-        r.largest_first = lf
+        r.cfg.schedule = (_lib.GS_SCHED_FWD_LONGEST_FIRST | _lib.GS_SCHED_BWD_LONGEST_FIRST) if lf else 0
         r.forward(arena, poses, img, alpha)
         g = gpu_backward(r, arena, poses, dimg, image=img)
         torch.cuda.synchronize()
