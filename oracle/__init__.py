@@ -352,3 +352,49 @@ def lod_cut(means, log_scales, parent, n_leaf, cam, tau=1.0, znear=0.2):
                            float(cam.fx), float(znear), float(tau), _p(screen),
                            sel.ctypes.data_as(C.POINTER(C.c_uint8)), amb.ctypes.data_as(C.POINTER(C.c_uint8)))
     return {"screen": screen, "selected": sel.astype(bool), "amb": amb.astype(bool)}
+
+
+# ---------------------------------------------------------------------------
+# Loop-closure update of the Gaussians (Sec. 5.5 / 6)
+# ---------------------------------------------------------------------------
+
+def _qmul(a, b):
+    """Hamilton product of quaternions (w, x, y, z), row-wise."""
+    aw, ax, ay, az = a[..., 0], a[..., 1], a[..., 2], a[..., 3]
+    bw, bx, by, bz = b[..., 0], b[..., 1], b[..., 2], b[..., 3]
+    return np.stack([aw * bw - ax * bx - ay * by - az * bz,
+                     aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx,
+                     aw * bz + ax * by - ay * bx + az * bw], axis=-1)
+
+
+def _qrot(q):
+    """Rotation matrices of unit quaternions (w, x, y, z)."""
+    q = q / np.linalg.norm(q, axis=-1, keepdims=True)
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    R = np.empty(q.shape[:-1] + (3, 3))
+    R[..., 0, 0] = 1 - 2 * (y * y + z * z); R[..., 0, 1] = 2 * (x * y - w * z); R[..., 0, 2] = 2 * (x * z + w * y)
+    R[..., 1, 0] = 2 * (x * y + w * z); R[..., 1, 1] = 1 - 2 * (x * x + z * z); R[..., 1, 2] = 2 * (y * z - w * x)
+    R[..., 2, 0] = 2 * (x * z - w * y); R[..., 2, 1] = 2 * (y * z + w * x); R[..., 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def sim3_update(means, log_scales, quats, kf, sim3):
+    """Every Gaussian moves with the Sim(3) correction of the keyframe that
+    spawned it (Sec. 5.5: the same transformation as its keyframe, scale and
+    rotation updated accordingly): mean' = s R mean + t, rotation' = R * rotation
+    (quaternion q_S q), log-scales' = log-scales + log s; a negative keyframe
+    leaves the Gaussian unchanged.  sim3 [K, 8] = (qw, qx, qy, qz, tx, ty, tz, s)
+    with the rotation as a unit quaternion.  FP64; returns new arrays."""
+    mu, ls, q = _f64(means).copy(), _f64(log_scales).copy(), _f64(quats).copy()
+    kf = np.asarray(kf, np.int64)
+    S = _f64(sim3).reshape(-1, 8)
+    sel = kf >= 0
+    k = kf[sel]
+    qs = S[k, :4] / np.linalg.norm(S[k, :4], axis=1, keepdims=True)
+    R = _qrot(qs)
+    s = S[k, 7]
+    mu[sel] = s[:, None] * np.einsum("nij,nj->ni", R, mu[sel]) + S[k, 4:7]
+    q[sel] = _qmul(qs, q[sel])
+    ls[sel] = ls[sel] + np.log(s)[:, None]
+    return mu, ls, q
