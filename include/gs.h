@@ -253,6 +253,21 @@ GS_API gs_status gs_splats_carve(void* base, int64_t n, int32_t views, gs_splats
 GS_API gs_status gs_project(const gs_params* params, const float* poses_dev, const gs_camera* cams,
                      int32_t views, const gs_raster_cfg* cfg, gs_splats* out, gs_stream stream);
 
+/* Loop-closure update (Sec. 5.5: every Gaussian keeps the keyframe that
+ * added it and receives the Sim(3) correction of that keyframe, with scale
+ * and rotation updated accordingly).  For Gaussian i with k = kf_dev[i] >= 0
+ * and the correction sim3_dev[k] = (qw, qx, qy, qz, tx, ty, tz, s) (rotation
+ * as a quaternion of any non-zero norm, s > 0):
+ *   mean' = s R mean + t;  log-scales' = log-scales + log s;
+ *   quaternion' = q_S q (Hamilton product; the input's norm is kept).
+ * Opacity and SH are unchanged (the paper updates scale and rotation; the SH
+ * coefficients are not rotated), and so are the Adam moments.  kf_dev < 0:
+ * not moved; kf_dev >= num_kf: not moved and bit 0 of *status_dev set.
+ * params: writable parameter arrays (gs_params layout), n Gaussians; kf_dev
+ * int32 [n], sim3_dev float [num_kf][8], status_dev uint32: device. */
+GS_API gs_status gs_sim3_update(gs_grads* params, const int32_t* kf_dev, const float* sim3_dev, int32_t num_kf,
+                                uint32_t* status_dev, gs_stream stream);
+
 /* Level-of-detail hierarchy (Sec. 6: coarse nodes hold the parameters of a
  * merged group of children; rendering descends from the roots until a node's
  * screen size falls below tau pixels or a leaf is reached).  Three levels:
@@ -511,6 +526,16 @@ GS_API gs_status gs_session_create(const gs_session_config* cfg, gs_session** ou
 GS_API gs_status gs_session_add_gaussians(gs_session* s, int64_t count, const float* means,
                                           const float* log_scales, const float* quats,
                                           const float* opa_logits, const float* sh);
+/* Gaussians added after this call are tagged with keyframe kf (< 0: none;
+ * the default): the keyframe whose correction moves them at a loop closure. */
+GS_API gs_status gs_session_set_keyframe(gs_session* s, int32_t kf);
+/* Loop closure (Sec. 5.5): every active Gaussian tagged with keyframe k <
+ * num_kf moves with the correction sim3[k] = (qw, qx, qy, qz, tx, ty, tz, s)
+ * (host [num_kf][8], s > 0) as gs_sim3_update does; untagged Gaussians and
+ * tags >= num_kf stay.  Enqueued on the session stream after the batches
+ * already issued (it never waits for them), before any later one; the
+ * hierarchy is rebuilt before the next render. */
+GS_API gs_status gs_session_loop_closure(gs_session* s, int32_t num_kf, const float* sim3);
 /* Queues a request; *id identifies it for poll/wait.  Never blocks on GPU work. */
 GS_API gs_status gs_session_submit(gs_session* s, const gs_request* req, int64_t* id);
 /* *done = 1 when the request finished (its status is returned), else 0. */

@@ -188,6 +188,19 @@ gs_status gs_project(const gs_params* params, const float* poses_dev, const gs_c
   return launch_project(*params, poses_dev, vt, *cfg, *out, (cudaStream_t)stream);
 }
 
+gs_status gs_sim3_update(gs_grads* params, const int32_t* kf_dev, const float* sim3_dev, int32_t num_kf,
+                         uint32_t* status_dev, gs_stream stream) {
+  if (!params) return fail(GS_ERR_INVALID, "params is NULL");
+  gs_params view{params->means4, params->scale_opa, params->quat, params->sh, params->n, params->sh_degree,
+                 params->sh_stride};
+  gs_status st;
+  if ((st = check_params(&view)) != GS_OK) return st;
+  if (num_kf < 0) return fail(GS_ERR_INVALID, "num_kf < 0");
+  if (params->n > 0 && (!kf_dev || !status_dev || (num_kf > 0 && !sim3_dev)))
+    return fail(GS_ERR_INVALID, "NULL keyframe ids, corrections or status");
+  return launch_sim3_update(*params, kf_dev, sim3_dev, num_kf, status_dev, (cudaStream_t)stream);
+}
+
 int64_t gs_lod_nodes(int64_t n_leaf) {
   return n_leaf <= 0 ? 0 : n_leaf + lod_level1(n_leaf) + lod_level2(n_leaf);
 }

@@ -34,6 +34,11 @@ gs_status launch_project(const gs_params& p, const float* poses, const ViewTable
                          const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s,
                          const int32_t* parent = nullptr, int64_t n_leaf = 0, float tau = 0.f);
 
+// Loop-closure update: Gaussian i moves with the Sim(3) of keyframe kf[i].
+gs_status launch_sim3_update(const gs_grads& p, const int32_t* kf, const float* sim3, int32_t num_kf,
+                             uint32_t* status, cudaStream_t s);
+gs_status launch_fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s);
+
 // Level-of-detail hierarchy (coarse nodes after the leaves in `nodes`).
 int64_t lod_level1(int64_t n);
 int64_t lod_level2(int64_t n);

@@ -92,6 +92,9 @@ struct gs_session {
   gs::Dev arena[4];  // parameters, gradients, first and second moments (stride = capacity)
   gs::Dev status_word, step_dev;
   gs::Dev lod_parent, lod_ws;  // level-of-detail hierarchy (cfg.lod)
+  gs::Dev kf_of;               // int32 [max_gaussians]: keyframe that added each Gaussian (-1: none)
+  gs::Dev sim3, sim3_status;   // loop-closure corrections [num_kf][8], status word
+  int32_t keyframe = -1;       // tag of the Gaussians added next
   bool lod_dirty = true;       // leaves added since the last build
   int64_t lod_builds = 0;
   int64_t capacity = 0;
@@ -659,6 +662,8 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
     gs::dfree(S->step_dev, S->in_use);
     gs::dfree(S->lod_parent, S->in_use);
     gs::dfree(S->lod_ws, S->in_use);
+    gs::dfree(S->kf_of, S->in_use);
+    gs::dfree(S->sim3_status, S->in_use);
     if (S->h_add) cudaFreeHost(S->h_add);
     if (S->add_done) cudaEventDestroy(S->add_done);
     cudaStreamDestroy(S->stream);
@@ -673,6 +678,9 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
   if ((st = gs::dalloc(S->step_dev, 16, S->in_use)) != GS_OK) return cleanup(st);
   cudaMemsetAsync(S->status_word.p, 0, 16, S->stream);
   cudaMemsetAsync(S->step_dev.p, 0, 16, S->stream);
+  if ((st = gs::dalloc(S->kf_of, 4 * (size_t)cfg->max_gaussians, S->in_use)) != GS_OK) return cleanup(st);
+  if ((st = gs::dalloc(S->sim3_status, 16, S->in_use)) != GS_OK) return cleanup(st);
+  cudaMemsetAsync(S->sim3_status.p, 0, 16, S->stream);
   if (cfg->lod) {
     if ((st = gs::dalloc(S->lod_parent, 4 * (size_t)S->capacity, S->in_use)) != GS_OK) return cleanup(st);
     if ((st = gs::dalloc(S->lod_ws, gs::lod_build_workspace_bytes(cfg->max_gaussians), S->in_use)) != GS_OK)
@@ -763,11 +771,50 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
     cudaMemsetAsync(M + 8 * cap + 4 * n0, 0, 16 * k, s);
     cudaMemset2DAsync(M + 12 * cap + n0, 4 * cap, 0, 4 * k, 3 * nc, s);
   }
+  gs_status st = gs::launch_fill_i32(static_cast<int32_t*>(S->kf_of.p) + n0, S->keyframe, k, s);
+  if (st != GS_OK) return st;
   cudaEventRecord(S->add_done, s);
-  gs_status st = gs::check_launch("session add");
+  st = gs::check_launch("session add");
   if (st != GS_OK) return st;
   S->n_active += count;
   S->lod_dirty = true;  // the new leaves overwrote coarse nodes
+  return GS_OK;
+}
+
+gs_status gs_session_set_keyframe(gs_session* S, int32_t kf) {
+  if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
+  std::lock_guard<std::mutex> add_lk(S->add_mu);
+  S->keyframe = kf < 0 ? -1 : kf;
+  return GS_OK;
+}
+
+gs_status gs_session_loop_closure(gs_session* S, int32_t num_kf, const float* sim3) {
+  if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
+  if (num_kf < 0 || (num_kf > 0 && !sim3)) return gs::fail(GS_ERR_INVALID, "bad corrections");
+  for (int32_t k = 0; k < num_kf; ++k)
+    if (!(sim3[8 * k + 7] > 0.f)) return gs::fail(GS_ERR_INVALID, "keyframe %d: scale must be > 0", k);
+  std::lock_guard<std::mutex> add_lk(S->add_mu);
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
+  const size_t bytes = 32 * (size_t)std::max(1, num_kf);
+  if (S->sim3.bytes < bytes) {
+    // the corrections of an earlier closure may still be read by the stream
+    gs_status st = gs::sync_stream(S, 30.0);
+    if (st != GS_OK) return st;
+    gs::dfree(S->sim3, S->in_use);
+    if ((st = gs::dalloc(S->sim3, bytes, S->in_use)) != GS_OK) return st;
+  }
+  cudaStream_t s = S->stream;
+  if (num_kf > 0 && cudaMemcpyAsync(S->sim3.p, sim3, 32 * (size_t)num_kf, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return gs::check_launch("session sim3");
+  gs_params P = gs::params_of(S, 0);
+  gs_grads rw{const_cast<float*>(P.means4), const_cast<float*>(P.scale_opa), const_cast<float*>(P.quat),
+              const_cast<float*>(P.sh), S->n_active, P.sh_degree, P.sh_stride};
+  gs_status st = gs::launch_sim3_update(rw, static_cast<const int32_t*>(S->kf_of.p),
+                                        static_cast<const float*>(S->sim3.p), num_kf,
+                                        static_cast<uint32_t*>(S->sim3_status.p), s);
+  if (st != GS_OK) return st;
+  S->lod_dirty = true;  // coarse nodes follow the moved leaves at the next build
   return GS_OK;
 }
 
@@ -1008,6 +1055,9 @@ gs_status gs_session_destroy(gs_session* S) {
   gs::dfree(S->step_dev, S->in_use);
   gs::dfree(S->lod_parent, S->in_use);
   gs::dfree(S->lod_ws, S->in_use);
+  gs::dfree(S->kf_of, S->in_use);
+  gs::dfree(S->sim3, S->in_use);
+  gs::dfree(S->sim3_status, S->in_use);
   if (S->h_add) cudaFreeHost(S->h_add);
   if (S->add_done) cudaEventDestroy(S->add_done);
   for (auto& r : S->all) r->target = nullptr;  // pooled buffers are freed below

@@ -104,6 +104,22 @@ class Arena:
         return groups
 
 
+def sim3_update(arena: Arena, kf: torch.Tensor, sim3: torch.Tensor, status: Optional[torch.Tensor] = None):
+    """gs_sim3_update: every Gaussian of the arena moves with the Sim(3)
+    correction of its keyframe kf[i] (int32 [n], device; < 0: unchanged);
+    sim3 [K, 8] float32 (qw, qx, qy, qz, tx, ty, tz, s).  Returns the status
+    word (bit 0: a keyframe id without a correction)."""
+    L = _lib.load()
+    assert kf.dtype == torch.int32 and kf.numel() >= arena.n and sim3.dtype == torch.float32
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=arena.buf.device)
+    rw = arena.rw_struct()
+    sim3 = sim3.contiguous()
+    _lib.check(L.gs_sim3_update(C.byref(rw), _p(kf), _p(sim3), sim3.shape[0], _p(status), _stream()),
+               "gs_sim3_update")
+    return status
+
+
 class LodHierarchy:
     """Three-level hierarchy (gs_lod_build) over the first n_leaf Gaussians of
     a node arena; coarse nodes are written after the leaves."""

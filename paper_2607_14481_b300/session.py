@@ -107,6 +107,17 @@ class Session:
     def image(self, rid: int) -> Optional[np.ndarray]:
         return self._keep.get(rid)
 
+    def set_keyframe(self, kf: int) -> None:
+        """Tag the Gaussians added next with keyframe kf (< 0: none)."""
+        _lib.check(self.L.gs_session_set_keyframe(self.h, int(kf)), "gs_session_set_keyframe")
+
+    def loop_closure(self, sim3) -> None:
+        """Move every tagged Gaussian with its keyframe's correction
+        sim3[k] = (qw, qx, qy, qz, tx, ty, tz, s)."""
+        s = np.ascontiguousarray(sim3, np.float32).reshape(-1, 8)
+        _lib.check(self.L.gs_session_loop_closure(self.h, s.shape[0], s.ctypes.data_as(C.POINTER(C.c_float))),
+                   "gs_session_loop_closure")
+
     def hold(self, on: bool = True) -> None:
         """Pause (or resume) admission: requests submitted while held are
         batched together on resume."""

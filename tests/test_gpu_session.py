@@ -220,3 +220,40 @@ def test_lod_render_equals_direct_hierarchy_and_rebuilds_on_add(cuda_device):
         (sc.means, sc.log_scales, sc.quats, sc.opa_logits, sc.sh),
         (more.means, more.log_scales, more.quats, more.opa_logits, more.sh))))
     assert np.array_equal(b, direct(both))
+
+
+def test_loop_closure_moves_gaussians_with_their_keyframe(cuda_device):
+    """Gaussians added under keyframes 0 and 1 (and untagged ones) move with
+    their keyframe's Sim(3) correction at a loop closure (FP64 oracle), and a
+    render after it equals the direct render of the moved scene."""
+    ensure_built()
+    g = np.random.default_rng(21)
+    parts = [synth.random_scene(3000, 30 + i, 1, (-2, -1, -2), (2, 1, 2), -3.0, 0.4) for i in range(3)]
+    tags = [0, 1, -1]
+
+    def sim3():
+        q = g.normal(size=4)
+        q /= np.linalg.norm(q)
+        return np.concatenate([q, 0.2 * g.normal(size=3), [np.exp(0.2 * g.normal())]])
+
+    S = np.stack([sim3(), sim3()]).astype(np.float32)
+    cam = _cams(1, seed=22)[0]
+    n = sum(p.n for p in parts)
+    with session.Session(_cfg(n, sh_degree=1)) as s:
+        for p, k in zip(parts, tags):
+            s.set_keyframe(k)
+            s.add(p)
+        s.loop_closure(S)
+        img = s.wait(s.submit(RENDER, cam, want_image=True))
+        got = s.params()
+    before = synth.Scene(*(np.concatenate([getattr(p, f) for p in parts]) for f in
+                           ("means", "log_scales", "quats", "opa_logits", "sh")))
+    kf = np.concatenate([np.full(p.n, k) for p, k in zip(parts, tags)])
+    mu, ls, q = oracle.sim3_update(before.means, before.log_scales, before.quats, kf, S.astype(np.float64))
+    scale = np.maximum(1.0, np.abs(mu))
+    assert np.all(np.abs(got["means4"][:, :3] - mu) <= 4e-6 * scale)
+    assert np.abs(got["scale_opa"][:, :3] - ls).max() <= 2e-6
+    assert np.abs(got["quat"] - q).max() <= 2e-6 * max(1.0, np.abs(q).max())
+    moved = synth.Scene(got["means4"][:, :3].copy(), got["scale_opa"][:, :3].copy(), got["quat"].copy(),
+                        got["scale_opa"][:, 3].copy(), got["sh"].T.reshape(n, 3, 4).copy())
+    assert np.array_equal(img, _direct_render(moved, cam))
