@@ -398,3 +398,26 @@ def sim3_update(means, log_scales, quats, kf, sim3):
     q[sel] = _qmul(qs, q[sel])
     ls[sel] = ls[sel] + np.log(s)[:, None]
     return mu, ls, q
+
+
+# ---------------------------------------------------------------------------
+# Keyframe selection for optimisation (Sec. 6.2)
+# ---------------------------------------------------------------------------
+
+def keyframe_weights(kf, num_kf, min_keep=50, frac=0.05):
+    """Sampling probabilities of the keyframes (Sec. 6.2): keyframe k is drawn
+    with probability proportional to the number of active leaf Gaussians it
+    generated (c_k); keyframes whose count is below frac * max_j c_j are
+    offloaded, except that the min_keep keyframes with the largest counts
+    (ties: smaller id first) always stay.  Returns (counts, probabilities,
+    kept mask)."""
+    kf = np.asarray(kf, np.int64)
+    kf = kf[(kf >= 0) & (kf < num_kf)]
+    c = np.bincount(kf, minlength=num_kf).astype(np.int64)
+    kept = c >= frac * c.max() if num_kf and c.max() > 0 else np.zeros(num_kf, bool)
+    order = sorted(range(num_kf), key=lambda k: (-c[k], k))
+    for k in order[:min_keep]:
+        kept[k] = True
+    w = np.where(kept, c, 0).astype(np.float64)
+    p = w / w.sum() if w.sum() > 0 else w
+    return c, p, kept
