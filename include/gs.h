@@ -268,6 +268,13 @@ GS_API gs_status gs_project(const gs_params* params, const float* poses_dev, con
 GS_API gs_status gs_sim3_update(gs_grads* params, const int32_t* kf_dev, const float* sim3_dev, int32_t num_kf,
                                 uint32_t* status_dev, gs_stream stream);
 
+/* Leaf Gaussians per keyframe (Sec. 6.2: keyframes are sampled for
+ * optimisation in proportion to the active leaves they generated):
+ * counts_dev[k] = #{i < n : kf_dev[i] == k} for k < num_kf; other ids are not
+ * counted.  counts_dev: device uint32 [num_kf], overwritten. */
+GS_API gs_status gs_keyframe_counts(const int32_t* kf_dev, int64_t n, int32_t num_kf, uint32_t* counts_dev,
+                                    gs_stream stream);
+
 /* Level-of-detail hierarchy (Sec. 6: coarse nodes hold the parameters of a
  * merged group of children; rendering descends from the roots until a node's
  * screen size falls below tau pixels or a leaf is reached).  Three levels:
@@ -536,6 +543,16 @@ GS_API gs_status gs_session_set_keyframe(gs_session* s, int32_t kf);
  * already issued (it never waits for them), before any later one; the
  * hierarchy is rebuilt before the next render. */
 GS_API gs_status gs_session_loop_closure(gs_session* s, int32_t num_kf, const float* sim3);
+/* Keyframe sampling weights (Sec. 6.2): keyframe k < num_kf is drawn for
+ * optimisation with probability proportional to the active leaf Gaussians it
+ * generated; keyframes whose count is below frac * the largest count are
+ * offloaded (probability 0), except that the min_keep keyframes with the
+ * largest counts (ties: smaller id) always stay (the paper: frac = 0.05,
+ * min_keep = 50).  Counts are taken after everything enqueued so far; the
+ * call waits for them (bounded).  p_out: host double [num_kf];
+ * counts_out / kept_out (optional): host uint32 / uint8 [num_kf]. */
+GS_API gs_status gs_session_keyframe_weights(gs_session* s, int32_t num_kf, int32_t min_keep, float frac,
+                                             double* p_out, uint32_t* counts_out, uint8_t* kept_out);
 /* Queues a request; *id identifies it for poll/wait.  Never blocks on GPU work. */
 GS_API gs_status gs_session_submit(gs_session* s, const gs_request* req, int64_t* id);
 /* *done = 1 when the request finished (its status is returned), else 0. */

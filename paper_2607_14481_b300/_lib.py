@@ -23,9 +23,9 @@ EXPORTED = (
     "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
-    "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_autotune_blend",
+    "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
-    "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_stats", "gs_session_read_params",
+    "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_keyframe_weights", "gs_session_stats", "gs_session_read_params",
     "gs_session_save", "gs_session_load", "gs_session_destroy",
 )
 
@@ -150,6 +150,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_autotune_blend.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp, i64, vp, sz,
                                     i32, C.POINTER(C.c_float), vp]
     L.gs_sim3_update.argtypes = [P(GsGrads), vp, vp, i32, vp, vp]
+    L.gs_keyframe_counts.argtypes = [vp, i64, i32, vp, vp]
     L.gs_lod_nodes.argtypes = [i64]
     L.gs_lod_nodes.restype = i64
     L.gs_lod_build_workspace.argtypes = [i64]
@@ -172,6 +173,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_session_hold.argtypes = [vp, i32]
     L.gs_session_set_keyframe.argtypes = [vp, i32]
     L.gs_session_loop_closure.argtypes = [vp, i32, C.POINTER(C.c_float)]
+    L.gs_session_keyframe_weights.argtypes = [vp, i32, i32, C.c_float, C.POINTER(C.c_double),
+                                              C.POINTER(C.c_uint32), C.POINTER(C.c_uint8)]
     L.gs_session_times.argtypes = [vp, i64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.gs_session_stats.argtypes = [vp, P(GsStats)]
     L.gs_session_read_params.argtypes = [vp, vp, vp, vp, vp]
@@ -179,13 +182,13 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_session_load.argtypes = [vp, C.c_char_p]
     L.gs_session_destroy.argtypes = [vp]
     for name in ("gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
-                 "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_stats",
+                 "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_keyframe_weights", "gs_session_stats",
                  "gs_session_read_params", "gs_session_save", "gs_session_load", "gs_session_destroy"):
         getattr(L, name).restype = C.c_int
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
                  "gs_render_bwd",
                  "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
-                 "gs_render_stats", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_autotune_blend"):
+                 "gs_render_stats", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

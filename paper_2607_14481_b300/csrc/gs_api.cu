@@ -201,6 +201,13 @@ gs_status gs_sim3_update(gs_grads* params, const int32_t* kf_dev, const float* s
   return launch_sim3_update(*params, kf_dev, sim3_dev, num_kf, status_dev, (cudaStream_t)stream);
 }
 
+gs_status gs_keyframe_counts(const int32_t* kf_dev, int64_t n, int32_t num_kf, uint32_t* counts_dev,
+                             gs_stream stream) {
+  if (n < 0 || num_kf < 0) return fail(GS_ERR_INVALID, "n or num_kf < 0");
+  if ((n > 0 && !kf_dev) || (num_kf > 0 && !counts_dev)) return fail(GS_ERR_INVALID, "NULL array");
+  return launch_keyframe_counts(kf_dev, n, num_kf, counts_dev, (cudaStream_t)stream);
+}
+
 int64_t gs_lod_nodes(int64_t n_leaf) {
   return n_leaf <= 0 ? 0 : n_leaf + lod_level1(n_leaf) + lod_level2(n_leaf);
 }

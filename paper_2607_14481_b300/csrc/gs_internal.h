@@ -38,6 +38,7 @@ gs_status launch_project(const gs_params& p, const float* poses, const ViewTable
 gs_status launch_sim3_update(const gs_grads& p, const int32_t* kf, const float* sim3, int32_t num_kf,
                              uint32_t* status, cudaStream_t s);
 gs_status launch_fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s);
+gs_status launch_keyframe_counts(const int32_t* kf, int64_t n, int32_t num_kf, uint32_t* counts, cudaStream_t s);
 
 // Level-of-detail hierarchy (coarse nodes after the leaves in `nodes`).
 int64_t lod_level1(int64_t n);

@@ -818,6 +818,51 @@ gs_status gs_session_loop_closure(gs_session* S, int32_t num_kf, const float* si
   return GS_OK;
 }
 
+gs_status gs_session_keyframe_weights(gs_session* S, int32_t num_kf, int32_t min_keep, float frac, double* p_out,
+                                      uint32_t* counts_out, uint8_t* kept_out) {
+  if (!S || !p_out) return gs::fail(GS_ERR_INVALID, "NULL session or output");
+  if (num_kf <= 0 || min_keep < 0 || !(frac >= 0.f && frac <= 1.f))
+    return gs::fail(GS_ERR_INVALID, "bad num_kf, min_keep or frac");
+  std::vector<uint32_t> c((size_t)num_kf);
+  {
+    std::lock_guard<std::mutex> add_lk(S->add_mu);
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
+    gs::Dev counts;
+    gs_status st = gs::dalloc(counts, sizeof(uint32_t) * (size_t)num_kf, S->in_use);
+    if (st != GS_OK) return st;
+    // after everything enqueued so far (adds, closures), on the session stream
+    st = gs::launch_keyframe_counts(static_cast<const int32_t*>(S->kf_of.p), S->n_active, num_kf,
+                                    static_cast<uint32_t*>(counts.p), S->stream);
+    if (st == GS_OK &&
+        cudaMemcpyAsync(c.data(), counts.p, sizeof(uint32_t) * (size_t)num_kf, cudaMemcpyDeviceToHost, S->stream) !=
+            cudaSuccess)
+      st = gs::check_launch("keyframe counts");
+    if (st == GS_OK) st = gs::sync_stream(S, 30.0);
+    gs::dfree(counts, S->in_use);
+    if (st != GS_OK) return st;
+  }
+  // Sec. 6.2: probability proportional to the leaf count; keyframes below
+  // frac of the largest count are offloaded, but the min_keep largest stay
+  uint32_t cmax = 0;
+  for (uint32_t v : c) cmax = std::max(cmax, v);
+  std::vector<uint8_t> kept((size_t)num_kf, 0);
+  for (int32_t k = 0; k < num_kf; ++k) kept[k] = cmax > 0 && (double)c[k] >= (double)frac * (double)cmax;
+  std::vector<int32_t> order((size_t)num_kf);
+  for (int32_t k = 0; k < num_kf; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return c[a] > c[b]; });
+  for (int32_t i = 0; i < std::min(min_keep, num_kf); ++i) kept[order[i]] = 1;
+  double total = 0;
+  for (int32_t k = 0; k < num_kf; ++k)
+    if (kept[k]) total += c[k];
+  for (int32_t k = 0; k < num_kf; ++k) {
+    p_out[k] = (kept[k] && total > 0) ? c[k] / total : 0.0;
+    if (counts_out) counts_out[k] = c[k];
+    if (kept_out) kept_out[k] = kept[k];
+  }
+  return GS_OK;
+}
+
 gs_status gs_session_submit(gs_session* S, const gs_request* req, int64_t* id) {
   if (!S || !req) return gs::fail(GS_ERR_INVALID, "NULL session or request");
   if (req->kind != GS_REQUEST_RENDER && req->kind != GS_REQUEST_TRAIN)

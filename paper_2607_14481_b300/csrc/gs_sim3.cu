@@ -3,6 +3,8 @@
 // scale and rotation updated accordingly).  One thread per Gaussian; the
 // corrections of all keyframes are small and stay in L1/L2.  HBM-bound: 4 B
 // keyframe id + 48 B read and 48 B written per Gaussian.
+#include <algorithm>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -39,12 +41,43 @@ __global__ void __launch_bounds__(256) k_sim3_update(float4* __restrict__ means4
                         w * q.z - x * q.w + y * q.x + z * q.y, w * q.w + x * q.z - y * q.y + z * q.x);
 }
 
+// Leaf Gaussians per keyframe (integer counts: the order of the atomics does
+// not show); ids outside [0, num_kf) are not counted.
+__global__ void __launch_bounds__(256) k_keyframe_counts(const int32_t* __restrict__ kf, int64_t n, int32_t num_kf,
+                                                         uint32_t* __restrict__ counts) {
+  extern __shared__ uint32_t s_c[];
+  const bool local = num_kf <= 8192;  // histogram in shared memory
+  if (local)
+    for (int k = threadIdx.x; k < num_kf; k += blockDim.x) s_c[k] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = kf[i];
+    if (k < 0 || k >= num_kf) continue;
+    atomicAdd(local ? &s_c[k] : &counts[k], 1u);
+  }
+  __syncthreads();
+  if (local)
+    for (int k = threadIdx.x; k < num_kf; k += blockDim.x)
+      if (s_c[k]) atomicAdd(&counts[k], s_c[k]);
+}
+
 __global__ void k_fill_i32(int32_t* p, int32_t v, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
 }
 
 }  // namespace
+
+gs_status launch_keyframe_counts(const int32_t* kf, int64_t n, int32_t num_kf, uint32_t* counts, cudaStream_t s) {
+  if (num_kf <= 0) return GS_OK;
+  if (cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)num_kf, s) != cudaSuccess)
+    return check_launch("keyframe counts");
+  if (n <= 0) return GS_OK;
+  const unsigned grid = (unsigned)std::min<int64_t>(592, (n + 255) / 256);
+  const size_t smem = num_kf <= 8192 ? sizeof(uint32_t) * (size_t)num_kf : 0;
+  k_keyframe_counts<<<grid, 256, smem, s>>>(kf, n, num_kf, counts);
+  return check_launch("k_keyframe_counts");
+}
 
 gs_status launch_fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s) {
   if (n <= 0) return GS_OK;

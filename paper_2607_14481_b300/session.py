@@ -118,6 +118,24 @@ class Session:
         _lib.check(self.L.gs_session_loop_closure(self.h, s.shape[0], s.ctypes.data_as(C.POINTER(C.c_float))),
                    "gs_session_loop_closure")
 
+    def keyframe_weights(self, num_kf: int, min_keep: int = 50, frac: float = 0.05) -> dict:
+        """Sampling probabilities of keyframes [0, num_kf) (Sec. 6.2), with the
+        leaf counts and the kept mask."""
+        p = np.zeros(num_kf, np.float64)
+        c = np.zeros(num_kf, np.uint32)
+        k = np.zeros(num_kf, np.uint8)
+        _lib.check(self.L.gs_session_keyframe_weights(self.h, int(num_kf), int(min_keep), float(frac),
+                                                      p.ctypes.data_as(C.POINTER(C.c_double)),
+                                                      c.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                                      k.ctypes.data_as(C.POINTER(C.c_uint8))),
+                   "gs_session_keyframe_weights")
+        return {"p": p, "counts": c, "kept": k.astype(bool)}
+
+    def sample_keyframes(self, num_kf: int, m: int, rng: np.random.Generator) -> np.ndarray:
+        """m keyframes drawn with the weights of keyframe_weights."""
+        p = self.keyframe_weights(num_kf)["p"]
+        return rng.choice(num_kf, size=m, p=p)
+
     def hold(self, on: bool = True) -> None:
         """Pause (or resume) admission: requests submitted while held are
         batched together on resume."""

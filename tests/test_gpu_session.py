@@ -257,3 +257,32 @@ def test_loop_closure_moves_gaussians_with_their_keyframe(cuda_device):
     moved = synth.Scene(got["means4"][:, :3].copy(), got["scale_opa"][:, :3].copy(), got["quat"].copy(),
                         got["scale_opa"][:, 3].copy(), got["sh"].T.reshape(n, 3, 4).copy())
     assert np.array_equal(img, _direct_render(moved, cam))
+
+
+def test_keyframe_weights_match_oracle(cuda_device):
+    """Leaf counts per keyframe on the device and the Sec. 6.2 sampling rule
+    (5% offload, at least min_keep kept) against the oracle."""
+    ensure_built()
+    g = np.random.default_rng(31)
+    K = 120
+    sizes = (g.pareto(1.2, K) * 40).astype(int)[:K]
+    sizes = np.minimum(sizes, 3000)
+    tags = []
+    with session.Session(_cfg(int(sizes.sum()) + 200, sh_degree=0)) as s:
+        for k in range(K):
+            if sizes[k] == 0:
+                continue
+            s.set_keyframe(k)
+            s.add(synth.random_scene(int(sizes[k]), 40 + k, 0, (-1, -1, -1), (1, 1, 1), -3.0, 0.3))
+            tags.append(np.full(sizes[k], k))
+        s.set_keyframe(-1)
+        s.add(synth.random_scene(200, 7, 0, (-1, -1, -1), (1, 1, 1), -3.0, 0.3))  # untagged
+        tags.append(np.full(200, -1))
+        for min_keep in (0, 50, 200):
+            got = s.keyframe_weights(K, min_keep=min_keep)
+            c, p, kept = oracle.keyframe_weights(np.concatenate(tags), K, min_keep=min_keep)
+            assert np.array_equal(got["counts"], c)
+            assert np.array_equal(got["kept"], kept)
+            assert np.allclose(got["p"], p, rtol=1e-12, atol=0)
+        picks = s.sample_keyframes(K, 1000, np.random.default_rng(0))
+        assert np.all(kept[picks])
