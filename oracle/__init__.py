@@ -5,7 +5,8 @@ benchmark's CPU-baseline leg may import this package.  It loads
 oracle/_build/liboracle.so (built from gs_oracle.cpp by oracle/build.py) and
 shares nothing with the CUDA path.  Every function takes scenes and cameras in
 natural layout (paper_2607_14481_b300.synth.Scene / Camera) and upcasts them to
-float64.
+float64.  The local bundle adjustment oracle is the separate module
+oracle/ba.py (numpy/scipy).
 """
 from __future__ import annotations
 

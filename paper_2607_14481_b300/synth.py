@@ -292,3 +292,65 @@ def stream_frame(k: int, n_frames: int, seed: int):
         w, h = STREAM_RESOLUTIONS[int(g.integers(0, len(STREAM_RESOLUTIONS)))]
         reqs.append((0 if g.random() < 0.5 else 1, w, h))
     return cam, new, reqs
+
+
+# ---------------------------------------------------------------------------
+# Local bundle adjustment problem (Sec. 5.3: N = 20 keyframes, n_f = 4 of them
+# fixed, K = 10,000 landmarks, each observed by a fixed subset of keyframes)
+# ---------------------------------------------------------------------------
+
+def ba_problem(seed: int, n_cams: int = 20, n_points: int = 10_000, obs_per_point: int = 8, n_fixed: int = 4,
+               width: int = 1280, height: int = 720, noise_px: float = 0.5, rot_sigma: float = 0.01,
+               trans_sigma: float = 0.05, point_sigma: float = 0.05, focal_err: float = 0.02):
+    """Synthetic local BA problem: keyframes on a gently curving path looking
+    forward, landmarks in the volume they see, each landmark observed by a
+    fixed random subset of obs_per_point of the keyframes that see it, observations = true
+    projections + N(0, noise_px^2); the first n_fixed keyframes are fixed and
+    exact, the others start with pose noise, landmarks with position noise,
+    the shared focal length with a relative error.  Poses are world->camera
+    [R | t] row-major float32 [N][12]."""
+    g = _rng(seed)
+    f_true = 0.8 * width
+    cams = []
+    for k in range(n_cams):
+        a = 0.3 * k / max(1, n_cams - 1)
+        eye = np.array([4.0 * np.sin(a), -0.2 * np.sin(2.1 * a), 0.35 * k])
+        fwd = np.array([np.sin(a + 0.15), 0.0, np.cos(a + 0.15)])
+        cams.append(look_at(eye, eye + fwd, f_true, f_true, width / 2, height / 2, width, height))
+    # landmarks: in front of a random keyframe, inside its view; kept when at
+    # least obs_per_point keyframes see it (depth > 1, inside the image), and
+    # observed by a random fixed subset of obs_per_point of those keyframes
+    Rs = np.stack([np.asarray(c.R, np.float64) for c in cams])
+    ts = np.stack([np.asarray(c.t, np.float64) for c in cams])
+    pts = np.zeros((0, 3))
+    obs_cam = np.zeros((0, obs_per_point), np.int32)
+    while pts.shape[0] < n_points:
+        m = 2 * n_points
+        k = g.integers(0, n_cams, m)
+        u, v, z = g.uniform(0.1 * width, 0.9 * width, m), g.uniform(0.1 * height, 0.9 * height, m), g.uniform(3.0, 12.0, m)
+        pc = np.stack([(u - width / 2) * z / f_true, (v - height / 2) * z / f_true, z], axis=1)
+        P = np.einsum("mji,mj->mi", Rs[k], pc - ts[k])
+        Xc = np.einsum("kij,mj->mki", Rs, P) + ts[None]
+        uu = f_true * Xc[..., 0] / np.maximum(Xc[..., 2], 1e-9) + width / 2
+        vv = f_true * Xc[..., 1] / np.maximum(Xc[..., 2], 1e-9) + height / 2
+        vis = (Xc[..., 2] > 1.0) & (uu > 0) & (uu < width) & (vv > 0) & (vv < height)
+        ok = vis.sum(axis=1) >= obs_per_point
+        P, vis = P[ok], vis[ok]
+        key = np.where(vis, g.random(vis.shape), 2.0)
+        sel = np.sort(np.argsort(key, axis=1, kind="stable")[:, :obs_per_point], axis=1).astype(np.int32)
+        pts = np.concatenate([pts, P])[:n_points]
+        obs_cam = np.concatenate([obs_cam, sel])[:n_points]
+    Xc = np.einsum("lkij,lkj->lki", Rs[obs_cam], np.broadcast_to(pts[:, None, :], obs_cam.shape + (3,))) + ts[obs_cam]
+    uv = np.stack([f_true * Xc[..., 0] / Xc[..., 2] + width / 2, f_true * Xc[..., 1] / Xc[..., 2] + height / 2], axis=-1)
+    uv = uv + g.normal(0.0, noise_px, uv.shape)
+    poses_true = np.concatenate([Rs, ts[:, :, None]], axis=2).reshape(n_cams, 12)
+    poses0 = poses_true.copy()
+    for k in range(n_fixed, n_cams):
+        R = Rs[k] @ _small_rotation(g, np.rad2deg(rot_sigma))
+        t = ts[k] + g.normal(0.0, trans_sigma, 3)
+        poses0[k] = np.concatenate([R, t[:, None]], axis=1).reshape(12)
+    pts0 = pts + g.normal(0.0, point_sigma, pts.shape)
+    return {"poses_true": poses_true.astype(np.float32), "points_true": pts.astype(np.float32), "f_true": f_true,
+            "poses0": poses0.astype(np.float32), "points0": pts0.astype(np.float32),
+            "f0": f_true * (1.0 + focal_err), "obs_cam": obs_cam, "obs_uv": uv.astype(np.float32),
+            "cx": width / 2, "cy": height / 2, "n_fixed": n_fixed}
