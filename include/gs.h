@@ -275,6 +275,64 @@ GS_API gs_status gs_sim3_update(gs_grads* params, const int32_t* kf_dev, const f
 GS_API gs_status gs_keyframe_counts(const int32_t* kf_dev, int64_t n, int32_t num_kf, uint32_t* counts_dev,
                                     gs_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Local bundle adjustment (Sec. 5.1 "Local Bundle Adjustment" and the
+ * supplementary "Fast Bundle Adjustment"): N keyframes, n_f of them fixed, K
+ * landmarks, each observed by a fixed subset of at most M keyframes, the
+ * shared focal length optimised; per-observation residual/Jacobian kernels and
+ * a dense Schur complement over the free keyframes.
+ *
+ * Readings where the paper is silent: pinhole u = f x/z + cx, v = f y/z + cy
+ * with (x, y, z) = R X + t (pose world->camera, row-major [R | t]); residual in
+ * pixels, cost = sum of squared residuals, no robust kernel; an observation
+ * with z <= 1e-6 contributes nothing.  Update R <- Exp(dtheta) R, t <- t + dt,
+ * X <- X + dX, f <- f + df.  Levenberg-Marquardt with Marquardt's scaling:
+ * (H + lambda D) delta = -g, D = diag(H) clamped to [1e-6, 1e32]; a candidate
+ * with a lower cost is accepted and lambda /= 10, otherwise lambda *= 10.
+ * One iteration = one linearisation, one damped solve, one decision; the
+ * iteration count is fixed.
+ *
+ * Precision: residuals, Jacobians and per-observation Schur terms in float32;
+ * sums over observations in double-float (float32 value + error term), the
+ * reduced camera system in float64 with Jacobi scaling, factorised in float32
+ * and refined with float64 residuals; each landmark's 3x3 block factorised in
+ * float64.
+ * --------------------------------------------------------------------------- */
+#define GS_BA_MAX_CAMS 64   /* keyframes per problem */
+#define GS_BA_MAX_FREE 20   /* keyframes that are optimised */
+#define GS_BA_MAX_OBS 16    /* observation slots per landmark */
+/* status bits (device word, OR-ed) */
+#define GS_BA_BAD_OBS 0x1u        /* a slot named a keyframe out of range or twice: slot ignored */
+#define GS_BA_SOLVE_FAILED 0x2u   /* a reduced system was not positive definite: step rejected */
+#define GS_BA_DEGENERATE 0x4u     /* a landmark's damped 3x3 block was not positive definite: landmark kept */
+
+typedef struct gs_ba_problem {
+  int32_t num_cams;       /* N, 1..GS_BA_MAX_CAMS */
+  int32_t num_points;     /* K >= 0 */
+  int32_t obs_per_point;  /* M, 1..GS_BA_MAX_OBS */
+  int32_t opt_focal;      /* 1: the shared focal length is optimised, 0: kept */
+  float cx, cy;           /* principal point, fixed */
+  const int32_t* obs_cam; /* device int32 [K][M]: keyframe of each slot, -1 = empty */
+  const float* obs_uv;    /* device float32 [K][M][2]: observed pixel position */
+  uint8_t fixed[GS_BA_MAX_CAMS]; /* host flags: 1 = keyframe fixed (not optimised) */
+} gs_ba_problem;
+
+/* Workspace bytes of gs_ba_solve for a problem of this size. */
+GS_API size_t gs_ba_workspace_bytes(int32_t num_cams, int32_t num_points, int32_t obs_per_point);
+/* Runs `iters` Levenberg-Marquardt iterations from the given state, starting
+ * with lambda = lambda0 (> 0).  poses: device float32 [N][12] (in/out; fixed
+ * keyframes are never written), points: device float32 [K][3] (in/out),
+ * focal: device float32 [1] (in/out).  trace (optional): device float64
+ * [iters][4] = (cost at the current state, candidate cost (+inf when the
+ * solve failed), lambda used, 1 if accepted else 0).  status: device uint32,
+ * GS_BA_* bits OR-ed in.  No host synchronisation and no allocation: the call
+ * can be captured in a CUDA graph.  GS_ERR_INVALID: sizes out of range, more
+ * than GS_BA_MAX_FREE free keyframes, NULL arrays, lambda0 not > 0;
+ * GS_ERR_OOM: ws_bytes below gs_ba_workspace_bytes. */
+GS_API gs_status gs_ba_solve(const gs_ba_problem* prob, float* poses, float* points, float* focal, int32_t iters,
+                             double lambda0, double* trace, uint32_t* status, void* ws, size_t ws_bytes,
+                             gs_stream stream);
+
 /* Level-of-detail hierarchy (Sec. 6: coarse nodes hold the parameters of a
  * merged group of children; rendering descends from the roots until a node's
  * screen size falls below tau pixels or a leaf is reached).  Three levels:

@@ -17,6 +17,8 @@ GS_TILE = 16
 GS_SCHED_FWD_LONGEST_FIRST, GS_SCHED_BWD_LONGEST_FIRST = 0x1, 0x2
 GS_NOALLOC_SCRATCH_BYTES = 8 << 20  # static scratch of gs_bin_sort_noalloc
 GS_MAX_ADAM_GROUPS = 64
+GS_BA_MAX_CAMS, GS_BA_MAX_FREE, GS_BA_MAX_OBS = 64, 20, 16
+GS_BA_BAD_OBS, GS_BA_SOLVE_FAILED, GS_BA_DEGENERATE = 0x1, 0x2, 0x4
 
 EXPORTED = (
     "gs_last_error", "gs_version", "gs_built_arch", "gs_splats_bytes", "gs_splats_carve",
@@ -24,6 +26,7 @@ EXPORTED = (
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
     "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
+    "gs_ba_workspace_bytes", "gs_ba_solve",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
     "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_keyframe_weights", "gs_session_stats", "gs_session_read_params",
     "gs_session_save", "gs_session_load", "gs_session_destroy",
@@ -78,6 +81,12 @@ class GsAdamCfg(C.Structure):
                 ("dpose", C.c_void_p), ("pose_m", C.c_void_p), ("pose_v", C.c_void_p),
                 ("views", C.c_int32), ("pose_lr", C.c_float), ("pose_step", C.c_int32),
                 ("step_dev", C.c_void_p), ("pose_steps_dev", C.c_void_p), ("skip_dev", C.c_void_p)]
+
+
+class GsBaProblem(C.Structure):
+    _fields_ = [("num_cams", C.c_int32), ("num_points", C.c_int32), ("obs_per_point", C.c_int32),
+                ("opt_focal", C.c_int32), ("cx", C.c_float), ("cy", C.c_float), ("obs_cam", C.c_void_p),
+                ("obs_uv", C.c_void_p), ("fixed", C.c_uint8 * GS_BA_MAX_CAMS)]
 
 
 class GsSessionConfig(C.Structure):
@@ -158,6 +167,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_lod_build.argtypes = [P(GsGrads), i64, vp, vp, sz, vp]
     L.gs_project_lod.argtypes = [P(GsParams), i64, vp, C.c_float, vp, P(GsCamera), i32, P(GsRasterCfg), P(GsSplats),
                                  vp]
+    L.gs_ba_workspace_bytes.argtypes = [i32, i32, i32]
+    L.gs_ba_workspace_bytes.restype = sz
+    L.gs_ba_solve.argtypes = [P(GsBaProblem), vp, vp, vp, i32, C.c_double, vp, vp, vp, sz, vp]
     L.gs_render_stats.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp]
     L.gs_image_loss_workspace.argtypes = []
     L.gs_image_loss_workspace.restype = sz
@@ -188,7 +200,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
                  "gs_render_bwd",
                  "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
-                 "gs_render_stats", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend"):
+                 "gs_render_stats", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
+                 "gs_ba_solve"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

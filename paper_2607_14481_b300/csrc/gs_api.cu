@@ -208,6 +208,39 @@ gs_status gs_keyframe_counts(const int32_t* kf_dev, int64_t n, int32_t num_kf, u
   return launch_keyframe_counts(kf_dev, n, num_kf, counts_dev, (cudaStream_t)stream);
 }
 
+static bool ba_sizes_ok(int32_t num_cams, int32_t num_points, int32_t obs_per_point) {
+  return num_cams >= 1 && num_cams <= GS_BA_MAX_CAMS && num_points >= 0 && num_points < (1 << 23) &&
+         obs_per_point >= 1 && obs_per_point <= GS_BA_MAX_OBS;
+}
+
+size_t gs_ba_workspace_bytes(int32_t num_cams, int32_t num_points, int32_t obs_per_point) {
+  if (!ba_sizes_ok(num_cams, num_points, obs_per_point)) return 0;
+  return ba_workspace_bytes(num_cams, num_points, obs_per_point);
+}
+
+gs_status gs_ba_solve(const gs_ba_problem* prob, float* poses, float* points, float* focal, int32_t iters,
+                      double lambda0, double* trace, uint32_t* status, void* ws, size_t ws_bytes,
+                      gs_stream stream) {
+  if (!prob) return fail(GS_ERR_INVALID, "problem is NULL");
+  if (!ba_sizes_ok(prob->num_cams, prob->num_points, prob->obs_per_point))
+    return fail(GS_ERR_INVALID, "num_cams must be 1..%d, num_points 0..2^23-1, obs_per_point 1..%d",
+                GS_BA_MAX_CAMS, GS_BA_MAX_OBS);
+  int n_free = 0;
+  for (int k = 0; k < prob->num_cams; ++k) n_free += prob->fixed[k] ? 0 : 1;
+  if (n_free > GS_BA_MAX_FREE) return fail(GS_ERR_INVALID, "%d free keyframes (at most %d)", n_free, GS_BA_MAX_FREE);
+  if (iters < 0) return fail(GS_ERR_INVALID, "iters < 0");
+  if (!(lambda0 > 0.0) || !std::isfinite(lambda0)) return fail(GS_ERR_INVALID, "lambda0 must be finite and > 0");
+  if (!poses || !focal || !status || !ws) return fail(GS_ERR_INVALID, "NULL poses, focal, status or workspace");
+  if (prob->num_points > 0 && (!points || !prob->obs_cam || !prob->obs_uv))
+    return fail(GS_ERR_INVALID, "NULL points or observations");
+  if ((reinterpret_cast<uintptr_t>(prob->obs_uv) & 7) || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(GS_ERR_INVALID, "obs_uv must be 8-byte and ws 256-byte aligned");
+  const size_t need = ba_workspace_bytes(prob->num_cams, prob->num_points, prob->obs_per_point);
+  if (ws_bytes < need) return fail(GS_ERR_OOM, "workspace %zu bytes, need %zu", ws_bytes, need);
+  if (iters == 0) return GS_OK;
+  return launch_ba(*prob, poses, points, focal, iters, lambda0, trace, status, ws, (cudaStream_t)stream);
+}
+
 int64_t gs_lod_nodes(int64_t n_leaf) {
   return n_leaf <= 0 ? 0 : n_leaf + lod_level1(n_leaf) + lod_level2(n_leaf);
 }

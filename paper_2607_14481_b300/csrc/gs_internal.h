@@ -40,6 +40,11 @@ gs_status launch_sim3_update(const gs_grads& p, const int32_t* kf, const float* 
 gs_status launch_fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s);
 gs_status launch_keyframe_counts(const int32_t* kf, int64_t n, int32_t num_kf, uint32_t* counts, cudaStream_t s);
 
+// Local bundle adjustment (arguments validated by the caller).
+size_t ba_workspace_bytes(int num_cams, int num_points, int obs_per_point);
+gs_status launch_ba(const gs_ba_problem& prob, float* poses, float* points, float* focal, int iters,
+                    double lambda0, double* trace, uint32_t* status, void* ws, cudaStream_t s);
+
 // Level-of-detail hierarchy (coarse nodes after the leaves in `nodes`).
 int64_t lod_level1(int64_t n);
 int64_t lod_level2(int64_t n);

@@ -309,6 +309,8 @@ def ba_problem(seed: int, n_cams: int = 20, n_points: int = 10_000, obs_per_poin
     exact, the others start with pose noise, landmarks with position noise,
     the shared focal length with a relative error.  Poses are world->camera
     [R | t] row-major float32 [N][12]."""
+    if not 1 <= obs_per_point <= n_cams:
+        raise ValueError("obs_per_point must be in [1, n_cams]")
     g = _rng(seed)
     f_true = 0.8 * width
     cams = []

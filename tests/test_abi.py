@@ -109,3 +109,33 @@ def test_session_plan_admits_by_budget(lib):
     need = q["fixed_bytes"] + 2 * q["context_bytes"]
     two = session.default_config(1_000_000, max_batch_views=8, max_inflight=4, hbm_budget_gb=need / (1 << 30))
     assert session.plan(two)["contexts"] == 2
+
+
+def test_bundle_adjustment_validation(lib):
+    """gs_ba_solve rejects bad problems on the host, before any device work."""
+    assert lib.gs_ba_workspace_bytes(20, 10000, 8) > 0
+    assert lib.gs_ba_workspace_bytes(0, 10, 8) == 0
+    assert lib.gs_ba_workspace_bytes(65, 10, 8) == 0
+    assert lib.gs_ba_workspace_bytes(20, 10, 17) == 0
+    fake = C.c_void_p(256)  # never dereferenced: every call below fails its checks first
+    trace = C.c_void_p(0)
+
+    def call(prob, iters=10, lam=1e-3, ws_bytes=1 << 30, poses=fake):
+        return lib.gs_ba_solve(C.byref(prob), poses, fake, fake, iters, lam, trace, fake, fake, ws_bytes,
+                               C.c_void_p(0))
+
+    prob = _lib.GsBaProblem()
+    prob.num_cams, prob.num_points, prob.obs_per_point, prob.opt_focal = 24, 100, 8, 1
+    prob.obs_cam, prob.obs_uv = 256, 256
+    for k in range(3):
+        prob.fixed[k] = 1
+    assert call(prob) == _lib.GS_ERR_INVALID          # 21 free keyframes
+    assert "free keyframes" in _lib.last_error()
+    prob.fixed[3] = 1
+    assert call(prob, lam=0.0) == _lib.GS_ERR_INVALID
+    assert call(prob, lam=float("nan")) == _lib.GS_ERR_INVALID
+    assert call(prob, iters=-1) == _lib.GS_ERR_INVALID
+    assert call(prob, poses=C.c_void_p(0)) == _lib.GS_ERR_INVALID
+    assert call(prob, ws_bytes=16) == _lib.GS_ERR_OOM
+    prob.obs_per_point = 0
+    assert call(prob) == _lib.GS_ERR_INVALID
