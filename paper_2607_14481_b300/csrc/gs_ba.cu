@@ -45,9 +45,9 @@ constexpr int kD = 40;    // floats per observation: net 6x6 upper triangle (21)
 constexpr int kLR = 16;   // floats per landmark: L^-1 (6), q = L^-1 g_p (3), p_f = L^-1 w_f (3), focal net,
                           // raw sum J_f^2, focal rhs, cost
 constexpr int kBR = 48;   // (hi, lo) values per block result
-constexpr int kSplitD = 16, kSplitP = 4, kSplitF = 4;  // CTAs per diagonal / pair / focal block
+constexpr int kSplitD = 16, kSplitP = 4, kSplitF = 32;  // CTAs per diagonal / pair / focal block
 constexpr int kUnroll = 4;                             // independent record loads in flight per thread
-constexpr int kRedThreads = 320, kSlots = 8;          // reduce CTA: 8 entries x 40 (36) values
+constexpr int kRedThreads = 320;  // threads of a reduce CTA
 constexpr int kMaxPairs = GS_BA_MAX_FREE * (GS_BA_MAX_FREE - 1) / 2;
 constexpr int kMaxDim = 6 * GS_BA_MAX_FREE + 1;
 constexpr int kSolveThreads = 1024;  // one thread per 4x4 block of the (padded) reduced system
@@ -82,7 +82,8 @@ struct BaArgs {
   float* focal;
   float* xcand;
   float* zrec;
-  float* drec;
+  float* drec;      // diagonal-block records, keyframe-major: [free keyframe][list position]
+  int32_t* dpos;    // list position of each observation slot of a free keyframe
   float* lrec;
   int32_t* lists;
   int32_t* counts;
@@ -181,29 +182,40 @@ __global__ void __launch_bounds__(256) k_ba_lists(const BaArgs a) {
   int32_t* out = a.lists + (size_t)b * a.P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int base = 0;
-  for (int l0 = 0; l0 < a.P; l0 += blockDim.x) {
-    const int l = l0 + threadIdx.x;
-    int sa = -1, sc = -1;
-    if (l < a.P)
-      for (int m = 0; m < a.M; ++m) {
-        const int k = a.obs[(size_t)l * a.M + m];
-        if (k == ka) sa = m;
-        if (k == kc) sc = m;
-      }
-    const bool hit = sa >= 0 && (diag || sc >= 0);
-    const unsigned bal = __ballot_sync(0xffffffffu, hit);
-    if (lane == 0) s_warp[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      before += w < warp ? s_warp[w] : 0;
-      total += s_warp[w];
+  constexpr int kPer = 4;  // landmarks per thread and chunk, loaded before the compaction
+  for (int l0 = 0; l0 < a.P; l0 += kPer * blockDim.x) {
+    int sa[kPer], sc[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int l = l0 + u * blockDim.x + threadIdx.x;
+      sa[u] = sc[u] = -1;
+      if (l < a.P)
+        for (int m = 0; m < a.M; ++m) {
+          const int k = a.obs[(size_t)l * a.M + m];
+          if (k == ka) sa[u] = m;
+          if (k == kc) sc[u] = m;
+        }
     }
-    if (hit)
-      out[base + before + __popc(bal & ((1u << lane) - 1u))] =
-          diag ? (l << 4) | sa : (l << 8) | (sa << 4) | sc;
-    base += total;
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {  // compaction in landmark order
+      const int l = l0 + u * blockDim.x + threadIdx.x;
+      const bool hit = sa[u] >= 0 && (diag || sc[u] >= 0);
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) s_warp[warp] = __popc(bal);
+      __syncthreads();
+      int before = 0, total = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        before += w < warp ? s_warp[w] : 0;
+        total += s_warp[w];
+      }
+      if (hit) {
+        const int pos = base + before + __popc(bal & ((1u << lane) - 1u));
+        out[pos] = diag ? (l << 4) | sa[u] : (l << 8) | (sa[u] << 4) | sc[u];
+        if (diag) a.dpos[(size_t)l * a.M + sa[u]] = pos;
+      }
+      base += total;
+      __syncthreads();
+    }
   }
   if (threadIdx.x == 0) a.counts[b] = base;
 }
@@ -358,7 +370,7 @@ __global__ void __launch_bounds__(256) k_ba_linearize(const BaArgs a) {
       d[33 + i] = fmaf(jc0[i], jc0[i], jc1[i] * jc1[i]);
     }
     d[39] = 0.f;
-    float4* dout = reinterpret_cast<float4*>(a.drec + o * kD);
+    float4* dout = reinterpret_cast<float4*>(a.drec + ((size_t)fi * a.P + a.dpos[o]) * kD);
 #pragma unroll
     for (int e = 0; e < kD / 4; ++e) dout[e] = make_float4(d[4 * e], d[4 * e + 1], d[4 * e + 2], d[4 * e + 3]);
   }
@@ -373,15 +385,21 @@ __global__ void __launch_bounds__(256) k_ba_linearize(const BaArgs a) {
   }
 }
 
-// CTA c covers one split of one block; thread t owns value t % nv of entry
-// slot t / nv and keeps kUnroll record loads in flight.  The last split CTA of
-// a block to finish combines the splits' (hi, lo) results in split order.
+// CTA c covers one split of one block.  Diagonal block: thread (slot, g)
+// adds values 4g..4g+3 of the records of entries slot, slot + 32, ... (float4
+// reads of the keyframe-major records); pair block: thread (slot, i) adds row
+// i of Z_a Z_c^T for its entries (Z_c read whole); focal block: thread
+// (slot, v) adds value v of the landmark records.  Per-thread sums are float32
+// over a few entries (double-float for the focal block, which carries the
+// cost); slots are combined in double-float in a fixed order, and the last
+// split CTA of a block to finish combines the splits' (hi, lo) results.
+constexpr int kDiagSlots = kRedThreads / 10, kPairSlots = kRedThreads / 6, kFocSlots = kRedThreads / 4;
 __global__ void __launch_bounds__(kRedThreads) k_ba_reduce(const BaArgs a) {
-  __shared__ float2 red[kRedThreads];
+  __shared__ float red[kRedThreads * 6];  // per thread up to 6 values (pair rows)
+  __shared__ float redc[kRedThreads];     // focal: double-float error terms
   __shared__ bool s_last;
   const int c = blockIdx.x, t = threadIdx.x;
   const int nd = a.n_free * kSplitD, npp = a.n_pairs * kSplitP;
-  float s = 0.f, cc = 0.f;
   int nv, blk, chunk0, nsplit;
   if (c < nd) {  // diagonal block of free keyframe c / kSplitD
     const int b = c / kSplitD, sp = c % kSplitD;
@@ -389,47 +407,72 @@ __global__ void __launch_bounds__(kRedThreads) k_ba_reduce(const BaArgs a) {
     blk = b;
     chunk0 = b * kSplitD;
     nsplit = kSplitD;
-    const int slot = t / 40, v = t % 40, stride = kSplitD * kSlots;
-    const int32_t* L = a.lists + (size_t)b * a.P;
+    const int slot = t / 10, g = t % 10, stride = kSplitD * kDiagSlots;
+    const float4* R = reinterpret_cast<const float4*>(a.drec + (size_t)b * a.P * kD) + g;
     const int n = a.counts[b];
-    for (int e0 = sp * kSlots + slot; e0 < n; e0 += kUnroll * stride) {
-      float x[kUnroll];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e0 = sp * kDiagSlots + slot; e0 < n; e0 += kUnroll * stride) {
+      float4 x[kUnroll];
+      float w[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         const int e = e0 + u * stride;
-        const int ent = e < n ? L[e] : -1;
-        x[u] = ent >= 0 ? a.drec[((size_t)(ent >> 4) * a.M + (ent & 15)) * kD + v] : 0.f;
+        w[u] = e < n ? 1.f : 0.f;
+        x[u] = R[(size_t)min(e, n - 1) * (kD / 4)];
       }
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) df_add(s, cc, x[u]);
+      for (int u = 0; u < kUnroll; ++u) {
+        acc.x = fmaf(w[u], x[u].x, acc.x);
+        acc.y = fmaf(w[u], x[u].y, acc.y);
+        acc.z = fmaf(w[u], x[u].z, acc.z);
+        acc.w = fmaf(w[u], x[u].w, acc.w);
+      }
     }
+    red[slot * 40 + 4 * g] = acc.x;
+    red[slot * 40 + 4 * g + 1] = acc.y;
+    red[slot * 40 + 4 * g + 2] = acc.z;
+    red[slot * 40 + 4 * g + 3] = acc.w;
   } else if (c < nd + npp) {  // off-diagonal block: sum Z_a Z_c^T
     const int p = (c - nd) / kSplitP, sp = (c - nd) % kSplitP;
     nv = 36;
     blk = a.n_free + p;
     chunk0 = nd + p * kSplitP;
     nsplit = kSplitP;
-    const int slot = t / 36, v = t % 36, i = v / 6, j = v % 6, stride = kSplitP * kSlots;
-    if (slot < kSlots) {
+    const int slot = t / 6, i = t % 6, stride = kSplitP * kPairSlots;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (slot < kPairSlots) {
       const int32_t* L = a.lists + (size_t)blk * a.P;
       const int n = a.counts[blk];
-      for (int e0 = sp * kSlots + slot; e0 < n; e0 += kUnroll * stride) {
-        float x[kUnroll];
+      for (int e0 = sp * kPairSlots + slot; e0 < n; e0 += kUnroll * stride) {
+        // unconditional loads (past the end: the last entry, weighted 0), so
+        // that the list reads, then the record reads, are in flight together
+        int ent[kUnroll];
+        float w[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
           const int e = e0 + u * stride;
-          const int ent = e < n ? L[e] : -1;
-          x[u] = 0.f;
-          if (ent >= 0) {
-            const size_t base = (size_t)(ent >> 8) * a.M;
-            const float* za = a.zrec + (base + ((ent >> 4) & 15)) * kZ + 3 * i;
-            const float* zc = a.zrec + (base + (ent & 15)) * kZ + 3 * j;
-            x[u] = fmaf(za[0], zc[0], fmaf(za[1], zc[1], za[2] * zc[2]));
-          }
+          w[u] = e < n ? 1.f : 0.f;
+          ent[u] = __ldg(L + min(e, n - 1));
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) df_add(s, cc, x[u]);
+        for (int u = 0; u < kUnroll; ++u) {
+          const size_t base = (size_t)(ent[u] >> 8) * a.M;
+          const float* za = a.zrec + (base + ((ent[u] >> 4) & 15)) * kZ + 3 * i;
+          const float4* zc4 = reinterpret_cast<const float4*>(a.zrec + (base + (ent[u] & 15)) * kZ);
+          const float z0 = w[u] * za[0], z1 = w[u] * za[1], z2 = w[u] * za[2];
+          float zc[20];
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const float4 v = zc4[q];
+            zc[4 * q] = v.x; zc[4 * q + 1] = v.y; zc[4 * q + 2] = v.z; zc[4 * q + 3] = v.w;
+          }
+#pragma unroll
+          for (int j = 0; j < 6; ++j)
+            acc[j] = fmaf(z0, zc[3 * j], fmaf(z1, zc[3 * j + 1], fmaf(z2, zc[3 * j + 2], acc[j])));
+        }
       }
+      #pragma unroll
+      for (int j = 0; j < 6; ++j) red[slot * 36 + 6 * i + j] = acc[j];
     }
   } else {  // focal entry, its raw diagonal, its right-hand side, the cost
     const int sp = c - nd - npp;
@@ -437,17 +480,28 @@ __global__ void __launch_bounds__(kRedThreads) k_ba_reduce(const BaArgs a) {
     blk = a.n_free + a.n_pairs;
     chunk0 = nd + npp;
     nsplit = kSplitF;
-    const int slot = t / 4, v = t % 4, ns = kRedThreads / 4;
-    for (int l = sp * ns + slot; l < a.P; l += kSplitF * ns) df_add(s, cc, a.lrec[(size_t)l * kLR + 12 + v]);
+    const int slot = t / 4, v = t % 4, stride = kSplitF * kFocSlots;
+    float s = 0.f, cc = 0.f;
+    for (int l0 = sp * kFocSlots + slot; l0 < a.P; l0 += kUnroll * stride) {
+      float x[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int l = l0 + u * stride;
+        x[u] = (l < a.P ? 1.f : 0.f) * a.lrec[(size_t)min(l, a.P - 1) * kLR + 12 + v];
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) df_add(s, cc, x[u]);
+    }
+    red[t] = s;
+    redc[t] = cc;
   }
-  red[t] = make_float2(s, cc);
   __syncthreads();
   if (t < nv) {
+    const int slots = c < nd ? kDiagSlots : c < nd + npp ? kPairSlots : kFocSlots;
     float hs = 0.f, hc = 0.f;
-    for (int q = 0; q < kRedThreads / nv; ++q) {
-      const float2 u = red[q * nv + t];
-      df_add(hs, hc, u.x);
-      hc += u.y;
+    for (int q = 0; q < slots; ++q) {
+      df_add(hs, hc, red[q * nv + t]);
+      if (c >= nd + npp) hc += redc[q * nv + t];
     }
     const float hi = hs + hc;
     a.bres[(size_t)c * kBR + t] = make_float2(hi, hc - (hi - hs));
@@ -600,35 +654,38 @@ __global__ void __launch_bounds__(kSolveThreads) k_ba_solve(const BaArgs a) {
   __syncthreads();
   // symmetric block sweep (Gauss-Jordan on 4x4 pivot blocks): after pivoting
   // on every block K the matrix holds -A^-1.  Thread t owns the 4x4 block
-  // (I, J) = (t % nbk, t / nbk) of the full matrix in registers, so the
-  // owners of block column K are consecutive threads (one or two warps).
-  // Per pivot block: D = A_KK, U_I = A_IK D^-1;  A_IJ -= U_I A_JK^T for
-  // I, J != K, A_IK <- U_I, A_KJ <- U_J^T, A_KK <- -D^-1.  Look-ahead: the
-  // owners of column K + 1 update their blocks first and prepare pivot K + 1
-  // (publish the column, invert D, form U) behind a barrier of their own
-  // warps, while the other warps finish step K; one CTA barrier per step.
-  __shared__ __align__(16) float s_P[2][kMaxPad / 4][16];  // pivot column blocks A_IK
-  __shared__ __align__(16) float s_U[2][kMaxPad / 4][20];  // U_I (rows padded against bank conflicts)
-  __shared__ __align__(16) float s_D[2][16];               // D^-1
+  // (I, J) = (t / nbk, t % nbk) of the full matrix in registers, so the
+  // owners of block row K are consecutive threads (one or two warps) and the
+  // threads of a warp share one or two block rows.  By symmetry everything a
+  // step needs comes from the pivot row: with D = A_KK, P_J = A_KJ and
+  // W_J = D^-1 A_KJ,  A_IJ -= W_I^T P_J (I, J != K), A_IK <- W_I^T,
+  // A_KJ <- W_J, A_KK <- -D^-1.  Look-ahead: the owners of row K + 1 update
+  // their blocks first and prepare pivot K + 1 (publish P, invert D, form W)
+  // behind a barrier of their own warps while the other warps finish step K;
+  // one CTA barrier per step.
+  constexpr int kRowPad = 20;  // floats per published 4x4 block (bank-conflict padding)
+  __shared__ __align__(16) float s_P[2][kMaxPad / 4][kRowPad];  // pivot row blocks A_KJ
+  __shared__ __align__(16) float s_W[2][kMaxPad / 4][kRowPad];  // W_J = D^-1 A_KJ
+  __shared__ __align__(16) float s_D[2][16];                    // D^-1
   const bool own = tid < nbk * nbk;
-  const int I = own ? tid % nbk : 0, J = own ? tid / nbk : 0;
+  const int I = own ? tid / nbk : 0, J = own ? tid % nbk : 0;
   float A[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c)
       A[r][c] = own ? Sh[(4 * I + r) * np + 4 * J + c] * dsc[4 * I + r] * dsc[4 * J + c] : 0.f;
-  // prepare pivot block K: run by every thread of the warps that own column K
+  // prepare pivot block K: run by every thread of the warps that own row K
   auto prepare = [&](int K) {
     const int pb = K & 1, w0 = (K * nbk) >> 5, w1 = (K * nbk + nbk - 1) >> 5;
     const unsigned nbar = (unsigned)(w1 - w0 + 1) * 32u;
-    const bool colown = own && J == K;
-    if (colown) {
-      float4* P4 = reinterpret_cast<float4*>(s_P[pb][I]);
+    const bool rowown = own && I == K;
+    if (rowown) {
+      float4* P4 = reinterpret_cast<float4*>(s_P[pb][J]);
 #pragma unroll
       for (int r = 0; r < 4; ++r) P4[r] = make_float4(A[r][0], A[r][1], A[r][2], A[r][3]);
     }
-    if (colown && I == K) {  // D^-1 by the scalar sweep of the 4x4 pivot block
+    if (rowown && J == K) {  // D^-1 by the scalar sweep of the 4x4 pivot block
       float D[4][4];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
@@ -660,18 +717,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_ba_solve(const BaArgs a) {
         for (int c = 0; c < 4; ++c) s_D[pb][4 * r + c] = -D[r][c];
     }
     asm volatile("bar.sync 1, %0;" ::"r"(nbar) : "memory");
-    if (colown) {  // U_I = A_IK D^-1
+    if (rowown) {  // W_J = D^-1 A_KJ
       float Dv[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) Dv[e] = s_D[pb][e];
-      float4* U4 = reinterpret_cast<float4*>(s_U[pb][I]);
+      float4* W4 = reinterpret_cast<float4*>(s_W[pb][J]);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        float u[4];
+        float w[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          u[c] = fmaf(A[r][0], Dv[c], fmaf(A[r][1], Dv[4 + c], fmaf(A[r][2], Dv[8 + c], A[r][3] * Dv[12 + c])));
-        U4[r] = make_float4(u[0], u[1], u[2], u[3]);
+          w[c] = fmaf(Dv[4 * r], A[0][c], fmaf(Dv[4 * r + 1], A[1][c], fmaf(Dv[4 * r + 2], A[2][c], Dv[4 * r + 3] * A[3][c])));
+        W4[r] = make_float4(w[0], w[1], w[2], w[3]);
       }
     }
   };
@@ -682,14 +739,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_ba_solve(const BaArgs a) {
   for (int K = 0; K < nbk && ok; ++K) {
     const int pb = K & 1;
     if (own) {
-      if (I != K && J != K) {
-        float U[16], Pj[16];
-        const float4* U4 = reinterpret_cast<const float4*>(s_U[pb][I]);
+      if (I != K && J != K) {  // A_IJ -= W_I^T P_J
+        float W[16], Pj[16];
+        const float4* W4 = reinterpret_cast<const float4*>(s_W[pb][I]);
         const float4* P4 = reinterpret_cast<const float4*>(s_P[pb][J]);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          const float4 u = U4[r], p = P4[r];
-          U[4 * r] = u.x; U[4 * r + 1] = u.y; U[4 * r + 2] = u.z; U[4 * r + 3] = u.w;
+          const float4 w = W4[r], p = P4[r];
+          W[4 * r] = w.x; W[4 * r + 1] = w.y; W[4 * r + 2] = w.z; W[4 * r + 3] = w.w;
           Pj[4 * r] = p.x; Pj[4 * r + 1] = p.y; Pj[4 * r + 2] = p.z; Pj[4 * r + 3] = p.w;
         }
 #pragma unroll
@@ -697,17 +754,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_ba_solve(const BaArgs a) {
 #pragma unroll
           for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int m = 0; m < 4; ++m) A[r][c] = fmaf(-U[4 * r + m], Pj[4 * c + m], A[r][c]);
-      } else if (I != K) {  // J == K: A_IK <- U_I
+            for (int m = 0; m < 4; ++m) A[r][c] = fmaf(-W[4 * m + r], Pj[4 * m + c], A[r][c]);
+      } else if (I != K) {  // J == K: A_IK <- W_I^T
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) A[r][c] = s_U[pb][I][4 * r + c];
-      } else if (J != K) {  // I == K: A_KJ <- U_J^T
+          for (int c = 0; c < 4; ++c) A[r][c] = s_W[pb][I][4 * c + r];
+      } else if (J != K) {  // I == K: A_KJ <- W_J
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) A[r][c] = s_U[pb][J][4 * c + r];
+          for (int c = 0; c < 4; ++c) A[r][c] = s_W[pb][J][4 * r + c];
       } else {
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -921,7 +978,7 @@ __global__ void __launch_bounds__(256) k_ba_finish(const BaArgs a) {
 }
 
 struct BaLayout {
-  size_t st, obs, xcand, zrec, drec, lrec, lists, counts, bres, bfin, bticket, partials, total;
+  size_t st, obs, xcand, zrec, drec, dpos, lrec, lists, counts, bres, bfin, bticket, partials, total;
 };
 
 int max_free(int N) { return std::min(N, GS_BA_MAX_FREE); }
@@ -943,7 +1000,8 @@ BaLayout ba_layout(int N, int P, int M) {
   L.obs = take((size_t)P * M);
   L.xcand = take(sizeof(float) * 3 * (size_t)P);
   L.zrec = take(sizeof(float) * kZ * (size_t)P * M);
-  L.drec = take(sizeof(float) * kD * (size_t)P * M);
+  L.drec = take(sizeof(float) * kD * (size_t)P * fm);
+  L.dpos = take(sizeof(int32_t) * (size_t)P * M);
   L.lrec = take(sizeof(float) * kLR * (size_t)P);
   L.lists = take(sizeof(int32_t) * (nb - 1) * (size_t)P);
   L.counts = take(sizeof(int32_t) * nb);
@@ -1014,6 +1072,7 @@ gs_status launch_ba(const gs_ba_problem& pr, float* poses, float* points, float*
   a.xcand = reinterpret_cast<float*>(w + L.xcand);
   a.zrec = reinterpret_cast<float*>(w + L.zrec);
   a.drec = reinterpret_cast<float*>(w + L.drec);
+  a.dpos = reinterpret_cast<int32_t*>(w + L.dpos);
   a.lrec = reinterpret_cast<float*>(w + L.lrec);
   a.lists = reinterpret_cast<int32_t*>(w + L.lists);
   a.counts = reinterpret_cast<int32_t*>(w + L.counts);
