@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--stream-max", type=int, default=5_000_000)
     ap.add_argument("--no-ba", action="store_true")
+    ap.add_argument("--ba-only", action="store_true",
+                    help="run only the local bundle adjustment measurement (one JSON line)")
     return ap.parse_args()
 
 
@@ -497,13 +499,18 @@ def run_local_ba(device, iters=10, reps=30, cpu=True, seed=SEED_BA):
            "e2e_ms": e2e_ms, "paper_ms_rtx4090": PAPER_BA_MS,
            "note": "the paper's figure is another GPU's (context, not a target)"}
     if cpu:
-        from threadpoolctl import threadpool_limits
-        from oracle import ba as oba
-        with threadpool_limits(1):
-            t0 = time.perf_counter()
-            o = oba.solve(p["poses0"], p["points0"], p["f0"], p["obs_cam"], p["obs_uv"], p["cx"], p["cy"],
-                          np.array(fixed), iters=iters)
-            cpu_ms = 1e3 * (time.perf_counter() - t0)
+        # the oracle in a fresh single-threaded interpreter (BLAS/OpenMP pools of 1)
+        code = ("import json, sys, time; sys.path.insert(0, %r); import numpy as np; "
+                "from paper_2607_14481_b300 import synth; from oracle import ba as oba; "
+                "p = synth.ba_problem(%d, n_cams=20, n_points=10000, obs_per_point=8, n_fixed=4); "
+                "fx = np.array([True] * 4 + [False] * 16); t0 = time.perf_counter(); "
+                "o = oba.solve(p['poses0'], p['points0'], p['f0'], p['obs_cam'], p['obs_uv'], p['cx'], p['cy'], "
+                "fx, iters=%d); print(json.dumps({'ms': 1e3 * (time.perf_counter() - t0), 'cost': o['cost']}))"
+                % (os.path.dirname(os.path.abspath(__file__)), seed, iters))
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+        o = json.loads(res.stdout.strip().splitlines()[-1])
+        cpu_ms = o["ms"]
         out["cpu_baseline"] = {"value": cpu_ms, "unit": "ms per solve", "cores": 1, "kind": "oracle",
                                "sample": f"the full problem, {iters} iterations (numpy/scipy FP64)",
                                "final_cost": o["cost"]}
@@ -740,6 +747,11 @@ def main():
         out, rank = run_reference(args, ws, rank)
         if rank == 0 and out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.ba_only:
+        import torch
+        out = run_local_ba(torch.device("cuda", 0), cpu=not args.no_cpu_baseline)
+        print(json.dumps({"local_ba": out}), flush=True)
         return
     ws, rank, local = dist_setup(args.gpus)
     out, rank = run_ours(args, ws, rank, local)
