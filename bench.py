@@ -263,22 +263,47 @@ class Workload:
 
 def timed_loop(wl, K, ws, e2e=False):
     """K iterations between a barrier + synchronize on both sides; device time
-    from CUDA events on the launching stream, max over ranks."""
+    from CUDA events on the launching stream, max over ranks.
+
+    e2e: every iteration also copies its target image from pinned host memory
+    (on a copy stream, one iteration ahead, so the copy of iteration i + 1
+    overlaps the compute of iteration i; iteration i waits for its own copy)
+    and reads its loss back to pinned host memory."""
     import torch
     loss_host = torch.zeros(max(K, 1), dtype=torch.float32).pin_memory() if e2e else None
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream() if e2e else None
+    n_buf = len(wl.steps)
+    done_ev = [None] * n_buf  # last iteration that read each target buffer
+
+    def issue_copy(j):
+        k = (wl.i + j) % n_buf
+        ev = torch.cuda.Event()
+        with torch.cuda.stream(copy):
+            if done_ev[k] is not None:
+                copy.wait_event(done_ev[k])
+            wl.steps[k].targets.copy_(wl.targets_host[k], non_blocking=True)
+            ev.record(copy)
+        return ev
+
     barrier(ws)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
     t0.record()
+    ready = issue_copy(0) if e2e else None
     for i in range(K):
         if e2e:
-            k = wl.i % len(wl.steps)
-            wl.steps[k].targets.copy_(wl.targets_host[k], non_blocking=True)
+            nxt = issue_copy(1) if i + 1 < K else None
+            comp.wait_event(ready)
+            k = wl.i % n_buf
         st = wl.step()
         if e2e:
             loss_host[i:i + 1].copy_(st.loss.loss, non_blocking=True)
+            done_ev[k] = torch.cuda.Event()
+            done_ev[k].record(comp)
+            ready = nxt
     t1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
