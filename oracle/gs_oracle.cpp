@@ -24,6 +24,10 @@
 //   support     r = ceil(3 sqrt(lambda_max)); a splat touches a pixel only if the
 //               pixel centre lies in [m-r, m+r]^2 (so the image does not depend
 //               on the tile shape)
+//   tile rect   the tiles of [m-h, m+h] per axis, h = min(r, the half-width of
+//               the bounding box of the ellipse where alpha can reach 1/255,
+//               widened by 0.1% + 0.05 px): only tiles where a pixel can pass
+//               the alpha test hold the splat, so the image is unchanged
 //   SH          real orthonormal SH up to l = 3 without Condon-Shortley phase,
 //               index k = l^2 + l + m; rgb = max(0, sum_k c_k Y_k(d) + 1/2)
 //   quaternion  (w,x,y,z), normalised inside the forward
@@ -295,9 +299,19 @@ Proj<S> project_one(const Scene& sc, const Scene* tg, int64_t i, const View<S>& 
   if (near_int(rr, cf.m_r)) P.r_amb = true;
   P.r = std::ceil(rr);
   if (P.r <= 0.0) return P;
+  P.opa = S(1.0) / (S(1.0) + exp(-ol));
+  // tile rect: alpha can reach 1/255 only where A dx^2 + 2B dx dy + C dy^2
+  // <= k = 2 ln(255 opacity), an ellipse whose bounding box has half-widths
+  // sqrt(k a), sqrt(k c) (a, c: diagonal of the dilated 2D covariance);
+  // widened by 0.1% + 0.05 px, capped by the support box r
+  double kk = 2.0 * std::log(255.0 * val(P.opa));
+  if (std::fabs(kk) <= 1e-4) P.bin_amb = true;
+  if (!(kk > 0.0)) return P;
+  double hx = std::min(P.r, std::sqrt(kk * av) * 1.001 + 0.05);
+  double hy = std::min(P.r, std::sqrt(kk * cv) * 1.001 + 0.05);
   double mxv = val(P.mx), myv = val(P.my);
-  double fxl = (mxv - P.r) / cf.tw, fxh = (mxv + P.r) / cf.tw;
-  double fyl = (myv - P.r) / cf.th, fyh = (myv + P.r) / cf.th;
+  double fxl = (mxv - hx) / cf.tw, fxh = (mxv + hx) / cf.tw;
+  double fyl = (myv - hy) / cf.th, fyh = (myv + hy) / cf.th;
   P.xlo = std::max(0, (int)std::floor(fxl));
   P.xhi = std::min(vw.TX - 1, (int)std::floor(fxh));
   P.ylo = std::max(0, (int)std::floor(fyl));
@@ -308,7 +322,6 @@ Proj<S> project_one(const Scene& sc, const Scene* tg, int64_t i, const View<S>& 
     P.bin_amb = true;
   if (P.xlo > P.xhi || P.ylo > P.yhi) return P;
 
-  P.opa = S(1.0) / (S(1.0) + exp(-ol));
   // view direction from the camera centre o_c = -R^T tau
   S oc[3];
   for (int k = 0; k < 3; ++k) oc[k] = -(vw.R[k] * vw.tau[0] + vw.R[3 + k] * vw.tau[1] + vw.R[6 + k] * vw.tau[2]);

@@ -126,13 +126,24 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
       const float hd = 0.5f * (ca - cc);
       const float lam = 0.5f * (ca + cc) + sqrtf(fmaxf(0.f, hd * hd + cb * cb));
       r = ceilf(3.0f * sqrtf(lam));
-      // tile rect of [m - r, m + r]^2; m = mi + frac with frac in [0,1)
-      xlo = max(0, (int)floorf((mix - r) * (1.0f / kTile)));
-      xhi = min(vi.TX - 1, (int)floorf((mix + r) * (1.0f / kTile)));
-      ylo = max(0, (int)floorf((miy - r) * (1.0f / kTile)));
-      yhi = min(vi.TY - 1, (int)floorf((miy + r) * (1.0f / kTile)));
-      vis = xlo <= xhi && ylo <= yhi;
       opa = 1.0f / (1.0f + expf(-so.w));
+      // tile rect: alpha can reach 1/255 only where A dx^2 + 2B dx dy + C dy^2
+      // <= k = 2 ln(255 opacity), an ellipse whose bounding box has
+      // half-widths sqrt(k ca), sqrt(k cc); widened by 0.1% + 0.05 px against
+      // rounding and capped by the support box r, so that no tile where a
+      // pixel passes the alpha test is left out (the image is unchanged)
+      const float k = 2.0f * logf(255.0f * opa);
+      vis = k > 0.f;
+      if (vis) {
+        const float hx = fminf(r, fmaf(sqrtf(k * ca), 1.001f, 0.05f));
+        const float hy = fminf(r, fmaf(sqrtf(k * cc), 1.001f, 0.05f));
+        const float mxf = mix + mfx, myf = miy + mfy;  // m = mi + frac, frac in [0,1)
+        xlo = max(0, (int)floorf((mxf - hx) * (1.0f / kTile)));
+        xhi = min(vi.TX - 1, (int)floorf((mxf + hx) * (1.0f / kTile)));
+        ylo = max(0, (int)floorf((myf - hy) * (1.0f / kTile)));
+        yhi = min(vi.TY - 1, (int)floorf((myf + hy) * (1.0f / kTile)));
+        vis = xlo <= xhi && ylo <= yhi;
+      }
     }
   }
   float3 col = make_float3(0.f, 0.f, 0.f);

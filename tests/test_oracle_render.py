@@ -213,3 +213,45 @@ def test_window_equals_crop_of_full_render():
     b = oracle.backward(sc, cams, [gfull])
     for k in a:
         assert np.abs(a[k] - b[k]).max() <= 1e-12 * max(1.0, np.abs(b[k]).max())
+
+
+def test_tile_rect_holds_every_pixel_that_can_blend():
+    """The tile rect (tiles of [m-h, m+h], h from the alpha >= 1/255 ellipse)
+    must contain every pixel whose centre lies in the support box and whose
+    alpha reaches 1/255 (brute force over pixels in FP64, from the oracle's
+    own conic and opacity); splats culled for low opacity reach it nowhere.
+    A rect computed from the 3-sigma square alone would also pass; the check
+    is that the tighter one never drops a contributing pixel."""
+    sc = synth.box_scene(3000, seed=77)
+    sc.opa_logits[:] = np.random.default_rng(5).normal(-1.0, 2.5, sc.n).astype(np.float32)  # many faint splats
+    cams = synth.forward_trajectory(3, seed=78)[1:2]
+    P = oracle.render(sc, cams, want_proj=True)["proj"][0]
+    F = {k: i for i, k in enumerate(oracle.PROJ_FIELDS)}
+    W, H = cams[0].width, cams[0].height
+    checked = tighter = 0
+    for i in range(sc.n):
+        r = P[i, F["radius"]]
+        if r <= 0:
+            continue
+        mx, my, A, B, C, o = (P[i, F[k]] for k in ("mx", "my", "A", "B", "C", "opacity"))
+        x0, x1 = int(max(0, np.floor(mx - r))), int(min(W - 1, np.ceil(mx + r)))
+        y0, y1 = int(max(0, np.floor(my - r))), int(min(H - 1, np.ceil(my + r)))
+        if x0 > x1 or y0 > y1:
+            continue
+        px, py = np.meshgrid(np.arange(x0, x1 + 1) + 0.5, np.arange(y0, y1 + 1) + 0.5)
+        dx, dy = mx - px, my - py
+        inbox = (np.abs(dx) <= r) & (np.abs(dy) <= r)
+        power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy
+        hit = inbox & (power <= 0) & (o * np.exp(power) >= 1.0 / 255.0)
+        if P[i, F["bin_amb"]]:
+            continue
+        if not P[i, F["vis"]]:
+            assert not hit.any(), i
+            continue
+        tx, ty = np.floor(px[hit] / 16).astype(int), np.floor(py[hit] / 16).astype(int)
+        assert np.all(tx >= P[i, F["xlo"]]) and np.all(tx <= P[i, F["xhi"]]), i
+        assert np.all(ty >= P[i, F["ylo"]]) and np.all(ty <= P[i, F["yhi"]]), i
+        checked += int(hit.any())
+        full = (int(np.floor(max(0, mx - r) / 16)), int(min(W // 16 - 1, np.floor((mx + r) / 16))))
+        tighter += int(P[i, F["xhi"]] - P[i, F["xlo"]] < full[1] - full[0])
+    assert checked > 200 and tighter > 0.2 * checked, (checked, tighter)
