@@ -5,9 +5,9 @@
 // adjacent pixels, so a warp covers 4 tile rows and every splat fetched from
 // shared memory serves two pixels.  Each batch of the tile's sorted splat list
 // is staged in shared memory by the CTA's threads with coalesced float4 loads,
-// together with the splat's vertical support range; a warp skips a splat whose
-// support misses its 4 rows (a warp-uniform test with one pixel of margin, so
-// it never skips a splat the exact per-pixel test would accept).  The CTA
+// together with a mask of the warps whose strip of 4 rows the splat can reach
+// at alpha >= 1/255 (the exponent's maximum over the strip, a conservative
+// test, so a warp never skips a splat the exact per-pixel test would accept).  The CTA
 // leaves the list as soon as every pixel has saturated (__syncthreads_count).
 //
 // Each staged splat carries its centre relative to the tile origin, its conic
@@ -120,6 +120,49 @@ struct FwdArgs {
   float* alpha;
 };
 
+// Largest exponent p(dx, dy) = a2 dx^2 + b2 dx dy + c2 dy^2 (a2, c2 < 0) over
+// the rectangle [dxl, dxh] x [dyl, dyh]: 0 if it holds the centre, else the
+// largest of the four edge maxima (each a concave parabola, its vertex
+// clamped to the edge).
+__device__ __forceinline__ float rect_pmax(float a2, float b2, float c2, float dxl, float dxh, float dyl,
+                                           float dyh) {
+  if (dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f) return 0.f;
+  const float ia = -0.5f / a2, ic = -0.5f / c2;
+  float best = -INFINITY;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float dx = e ? dxh : dxl;  // vertical edge: maximise over dy
+    const float dy = fminf(fmaxf(b2 * dx * ic, dyl), dyh);
+    best = fmaxf(best, fmaf(c2 * dy + b2 * dx, dy, a2 * dx * dx));
+    const float dy2 = e ? dyh : dyl;  // horizontal edge: maximise over dx
+    const float dx2 = fminf(fmaxf(b2 * dy2 * ia, dxl), dxh);
+    best = fmaxf(best, fmaf(a2 * dx2 + b2 * dy2, dx2, c2 * dy2 * dy2));
+  }
+  return best;
+}
+
+// Warp culling of a staged splat: bit w is set unless no point of warp w's
+// strip of the tile (rows kRowsPerWarp w .. kRowsPerWarp (w + 1) - 1, columns
+// 0..15, as a continuous rectangle, cut to the support box |dx|, |dy| <= r)
+// reaches the alpha threshold p >= thr (with a margin of 1e-3 (1 + |thr|)).
+// Conservative: a warp with its bit clear has no pixel that passes the exact
+// per-pixel test, so skipping it changes nothing.
+__device__ __forceinline__ uint8_t warp_mask(float cx, float cy, float a2, float b2, float c2, float thr,
+                                             float r) {
+  const float xl = fmaxf(0.f, cx - r), xh = fminf((float)(kTile - 1), cx + r);
+  if (!(a2 < 0.f && c2 < 0.f) || xl > xh) return 0u;
+  const float lim = thr - 1e-3f * (1.f + fabsf(thr));
+  uint8_t m = 0u;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const float yl = fmaxf((float)(kRowsPerWarp * w), cy - r);
+    const float yh = fminf((float)(kRowsPerWarp * w + kRowsPerWarp - 1), cy + r);
+    if (yl > yh) continue;
+    if (rect_pmax(a2, b2, c2, cx - xh, cx - xl, cy - yh, cy - yl) >= lim) m |= (uint8_t)(1u << w);
+  }
+  return m;
+}
+
 // Stages splat `j` of the list (or a null splat: radius -1, opacity 0, which
 // never passes the test, standing in for an out-of-range id reported through
 // counts[2] bit 2) in shared memory slot `t`, relative to the tile origin
@@ -129,7 +172,7 @@ struct FwdArgs {
 __device__ __forceinline__ void stage_splat(const float4* xy, const float4* conic, const float4* rgb,
                                             const uint32_t* vals, int64_t n, int64_t vbase, uint32_t j,
                                             int t, float ox, float oy, float4* s_geo, float4* s_geo2,
-                                            float4* s_rgb, float2* s_rows, float4* s_co, uint32_t* counts) {
+                                            float4* s_rgb, uint8_t* s_mask, float4* s_co, uint32_t* counts) {
   const uint32_t g = vals[j];
   float4 m, co, col;
   if (g < n) {
@@ -149,7 +192,8 @@ __device__ __forceinline__ void stage_splat(const float4* xy, const float4* coni
   s_geo2[t] = make_float4(__fmul_rn(-0.5f * kLog2e, co.z), -log2f(255.f * co.w), co.w, col.w);
   s_rgb[t] = col;
   if (s_co) s_co[t] = co;
-  s_rows[t] = col.w < 0.f ? make_float2(1e30f, -1e30f) : make_float2(cy - col.w - 1.f, cy + col.w + 1.f);
+  s_mask[t] = col.w < 0.f ? 0u : warp_mask(cx, cy, __fmul_rn(-0.5f * kLog2e, co.x), __fmul_rn(-kLog2e, co.y),
+                                             __fmul_rn(-0.5f * kLog2e, co.z), -log2f(255.f * co.w), col.w);
 }
 
 // COUNT = true is the diagnostic instantiation behind gs_render_stats: the
@@ -159,8 +203,9 @@ template <bool COUNT, int kBatch>
 __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const ViewTable vt,
                                                          unsigned long long* stats) {
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch];
-  __shared__ float2 s_rows[kBatch];
+  __shared__ uint8_t s_mask[kBatch];
   __shared__ int s_last;
+  const int warp = threadIdx.x >> 5;
   const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
   const TileCoords tc = tile_coords(vt, gt);
   const ViewInfo& vi = vt.v[tc.v];
@@ -177,11 +222,10 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     for (int t = threadIdx.x; t < cnt; t += kThreads)
       stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + t, t, tc.ox, tc.oy, s_geo, s_geo2,
-                  s_rgb, s_rows, nullptr, COUNT ? nullptr : a.counts);
+                  s_rgb, s_mask, nullptr, COUNT ? nullptr : a.counts);
     __syncthreads();
     for (int k = 0; k < cnt && !(d0 && d1); ++k) {
-      const float2 rows = s_rows[k];
-      if (tc.wlo > rows.y || tc.whi < rows.x) continue;  // warp-uniform
+      if (!((s_mask[k] >> warp) & 1u)) continue;  // warp-uniform
       const float4 g = s_geo[k], g2 = s_geo2[k];
       const XTerms x = splat_x(g, tc.lx);
       Eval e;
@@ -410,7 +454,7 @@ __device__ __forceinline__ void splat_grad_front(const Eval& e, const float4 co,
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const ViewTable vt) {
   constexpr int kBatch = kThreads;
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
-  __shared__ float2 s_rows[kBatch];
+  __shared__ uint8_t s_mask[kBatch];
   __shared__ uint32_t s_pidx[kBatch];
   __shared__ float s_red[kBatch][kWarps][kPartialValues];
   __shared__ uint8_t s_hit[kBatch][kWarps];
@@ -432,12 +476,11 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
     const uint32_t j = start + threadIdx.x;
     if (j < rg.y)
       stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
-                  s_rgb, s_rows, nullptr, nullptr);
+                  s_rgb, s_mask, nullptr, nullptr);
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     for (int k = 0; k < cnt && !(d0 && d1); ++k) {
-      const float2 rows = s_rows[k];
-      if (tc.wlo > rows.y || tc.whi < rows.x) continue;
+      if (!((s_mask[k] >> warp) & 1u)) continue;
       const float4 g = s_geo[k], g2 = s_geo2[k];
       const XTerms x = splat_x(g, tc.lx);
       Eval e;
@@ -485,15 +528,14 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
     if (threadIdx.x < cnt) {
       const uint32_t j = (uint32_t)(bstart + threadIdx.x);
       stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
-                  s_rgb, s_rows, s_co, nullptr);
+                  s_rgb, s_mask, s_co, nullptr);
       s_pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
     }
     __syncthreads();
     for (int k = cnt - 1; k >= 0; --k) {
-      const float2 rows = s_rows[k];
-      if (tc.wlo > rows.y || tc.whi < rows.x) continue;  // warp-uniform: no contribution
+      if (!((s_mask[k] >> warp) & 1u)) continue;  // warp-uniform: no contribution
       const int pos = bstart + k;
       float d[kPartialValues];
 #pragma unroll
@@ -537,7 +579,7 @@ template <int kBatch>
 __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, const ViewTable vt) {
   static_assert(kBatch <= kThreads, "one staged splat per thread");
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
-  __shared__ float2 s_rows[kBatch];
+  __shared__ uint8_t s_mask[kBatch];
   __shared__ uint32_t s_pidx[kBatch];
   __shared__ float s_red[kBatch][kWarps][kPartialValues];
   __shared__ uint8_t s_hit[kBatch][kWarps];
@@ -572,7 +614,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
     if (threadIdx.x < cnt) {
       const uint32_t j = start + threadIdx.x;
       stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
-                  s_rgb, s_rows, s_co, nullptr);
+                  s_rgb, s_mask, s_co, nullptr);
       s_pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
@@ -580,8 +622,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
     __syncthreads();
     for (int k = 0; k < cnt; ++k) {
       if (__all_sync(0xffffffffu, d0 && d1)) break;  // the warp's pixels are done
-      const float2 rows = s_rows[k];
-      if (tc.wlo > rows.y || tc.whi < rows.x) continue;  // warp-uniform: no contribution
+      if (!((s_mask[k] >> warp) & 1u)) continue;  // warp-uniform: no contribution
       float d[kPartialValues];
 #pragma unroll
       for (int c = 0; c < kPartialValues; ++c) d[c] = 0.f;
