@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--stream-max", type=int, default=5_000_000)
     ap.add_argument("--no-ba", action="store_true")
+    ap.add_argument("--no-lod", action="store_true")
     ap.add_argument("--ba-only", action="store_true",
                     help="run only the local bundle adjustment measurement (one JSON line)")
     return ap.parse_args()
@@ -397,6 +398,7 @@ def run_ours(args, ws, rank, local):
     loop = run_loop_closure(5_000_000, device) if rank == 0 else None
     local_ba = run_local_ba(device, cpu=(ws == 1 and not args.no_cpu_baseline)) \
         if rank == 0 and not args.no_ba else None
+    lod = run_lod(device) if rank == 0 and not args.no_lod else None
 
     out = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": K,
@@ -416,6 +418,7 @@ def run_ours(args, ws, rank, local):
         "streaming": stream,
         "loop_closure": loop,
         "local_ba": local_ba,
+        "lod": lod,
         "clocks": clk,
         "gpu_launches": n_launch * K,
         "nonfinite_flag": bad,
@@ -539,6 +542,79 @@ def run_local_ba(device, iters=10, reps=30, cpu=True, seed=SEED_BA):
         out["cpu_baseline"] = {"value": cpu_ms, "unit": "ms per solve", "cores": 1, "kind": "oracle",
                                "sample": f"the full problem, {iters} iterations (numpy/scipy FP64)",
                                "final_cost": o["cost"]}
+    return out
+
+
+def run_lod(device, n_frames=100, per_frame=50_000, reps=10, taus=(1.0, 4.0, 16.0), seed=SEED_STREAM):
+    """The level-of-detail hierarchy on a streamed scene: n_frames x per_frame
+    Gaussians spawned in the frustums of a camera walking the 200 m loop (the
+    streaming workload's generator), SH3.  Times, with CUDA events over `reps`
+    launches each: gs_lod_build (Morton grouping, sort, two merge levels) and,
+    for frame 0's 1080p view, the projection of all leaves against the cut
+    projection at each tau (pixels), then binning + composite of each.  HBM figure of
+    the build: 340 B per leaf (means for the codes 16 B, three 8-bit sort
+    passes over (code, index) 48 B, leaf parameters read by the first merge
+    240 B, a level-1 node written per 8 leaves 30 B, parent ids 4 B)."""
+    import torch
+    from paper_2607_14481_b300 import raster, synth
+    cams = [synth.stream_camera(k, n_frames) for k in range(n_frames)]
+    parts = [synth.frustum_gaussians(cams[k], per_frame, seed * 7919 + k) for k in range(n_frames)]
+    sc = synth.Scene(*(np.concatenate([getattr(p, f) for p in parts]) for f in
+                       ("means", "log_scales", "quats", "opa_logits", "sh")))
+    del parts
+    n = sc.n
+    from paper_2607_14481_b300 import _lib
+    n_nodes = int(_lib.load().gs_lod_nodes(n))
+    arena = raster.Arena.from_scene(sc, device, capacity=n_nodes)
+    del sc
+    lod = raster.LodHierarchy(arena, n)
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    build_ms = timed(lod.build, reps)
+    cam = [cams[0]]
+    poses = raster.poses_tensor(cam, device)
+    out = {"leaves": n, "nodes": n_nodes, "view": [cam[0].width, cam[0].height], "build_ms": build_ms}
+    class _Leaves:  # the first n rows of the node arena (its SH stride), as projection parameters
+        def struct(self):
+            return arena.struct(n)
+    leaves_arena = _Leaves()
+    for name, r_n, proj in [("leaves", n, None)] + [(f"cut_tau{t:g}", n_nodes, t) for t in taus]:
+        r = raster.Rasterizer(r_n, 3, cam, device=device)
+        img = r.new_image()
+        if proj is None:
+            r.forward(leaves_arena, poses, img, None, check=True)
+            pj = lambda: r.project(leaves_arena, poses)
+        else:
+            r.forward(arena, poses, img, None, check=True, lod=lod, tau=proj)
+            pj = lambda: r.project_lod(lod, poses, proj)
+        cnt = r.read_counts()
+        proj_ms = timed(pj, reps)
+
+        def fwd():
+            pj()
+            r.bin_sort()
+            r.render_fwd(img, None)
+        out[name] = {"project_ms": proj_ms, "project_bin_render_ms": timed(fwd, reps),
+                     "rendered_splats": int(cnt[0]), "pairs": int(cnt[1])}
+        del r, img
+        torch.cuda.empty_cache()
+    peaks = load_peaks()
+    gbs = 340.0 * n / (build_ms / 1e3) / 1e9
+    out["build_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": gbs / peaks["hbm_gbs"], "bytes_per_leaf": 340}
+    out["paper_traversal_ms"] = "5-30 (the paper's hierarchy traversal per frame; another GPU; context)"
+    del lod, arena, leaves_arena
+    torch.cuda.empty_cache()
     return out
 
 
