@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--stream-max", type=int, default=5_000_000)
     ap.add_argument("--no-ba", action="store_true")
     ap.add_argument("--no-lod", action="store_true")
+    ap.add_argument("--lod-only", action="store_true",
+                    help="run only the level-of-detail measurement (one JSON line)")
     ap.add_argument("--ba-only", action="store_true",
                     help="run only the local bundle adjustment measurement (one JSON line)")
     return ap.parse_args()
@@ -848,6 +850,10 @@ def main():
         out, rank = run_reference(args, ws, rank)
         if rank == 0 and out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.lod_only:
+        import torch
+        print(json.dumps({"lod": run_lod(torch.device("cuda", 0))}), flush=True)
         return
     if args.ba_only:
         import torch

@@ -114,6 +114,8 @@ struct MergeArgs {
   int64_t sh_stride;
   int32_t* parent;
   const uint32_t* order;  // level 1: leaves in Morton order
+  float* wts;             // [n1 + n2][8] children's merge weights (opacities), level 1 then level 2
+  float* iws;             // [n1 + n2] 1 / sum of the weights
   int64_t n_leaf, n1, n2;
 };
 
@@ -182,7 +184,8 @@ __device__ float4 rot_to_quat(const float* R) {
 }
 
 // One thread per coarse node of the level: the moment-matching merge of its
-// (up to 8) children.
+// (up to 8) children's geometry and opacity; the weights go to a.wts for the
+// SH pass.
 template <int NC, bool LEVEL2>
 __global__ void __launch_bounds__(kLodThreads) k_lod_merge(const MergeArgs a) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -234,14 +237,12 @@ __global__ void __launch_bounds__(kLodThreads) k_lod_merge(const MergeArgs a) {
   }
 #pragma unroll
   for (int e = 0; e < 6; ++e) C[e] *= iW;
-  // SH: opacity-weighted mean of every coefficient
-#pragma unroll 4
-  for (int p = 0; p < 3 * NC; ++p) {
-    float acc = 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (j < k) acc += w[j] * a.sh[(int64_t)p * a.sh_stride + child[j]];
-    a.sh[(int64_t)p * a.sh_stride + node] = acc * iW;
+  {  // the SH pass (k_lod_merge_sh) averages the coefficients with these weights
+    const int64_t wi = LEVEL2 ? a.n1 + g : g;
+    float4* w4 = reinterpret_cast<float4*>(a.wts + 8 * wi);
+    w4[0] = make_float4(w[0], w[1], w[2], w[3]);
+    w4[1] = make_float4(w[4], w[5], w[6], w[7]);
+    a.iws[wi] = iW;
   }
   // rotation and scales from the eigen-decomposition
   float A[9] = {C[0], C[1], C[2], C[1], C[3], C[4], C[2], C[4], C[5]};
@@ -263,9 +264,47 @@ __global__ void __launch_bounds__(kLodThreads) k_lod_merge(const MergeArgs a) {
   if (LEVEL2) a.parent[node] = -1;
 }
 
+// SH of the level's coarse nodes: the opacity-weighted mean of every
+// coefficient of the (up to 8) children.  Block (x, y) covers 256 nodes and
+// kShPlanes coefficient planes; the blocks of one group of planes run before
+// the next group's, so the planes being gathered (n floats each) stay in L2
+// while the children, scattered in memory in level 1, are read one value at a
+// time.
+constexpr int kShPlanes = 4;
+template <int NC, bool LEVEL2>
+__global__ void __launch_bounds__(kLodThreads) k_lod_merge_sh(const MergeArgs a) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t groups = LEVEL2 ? a.n2 : a.n1;
+  if (g >= groups) return;
+  const int64_t members = LEVEL2 ? a.n1 : a.n_leaf;
+  const int k = (int)min((int64_t)8, members - 8 * g);
+  const int64_t node = LEVEL2 ? a.n_leaf + a.n1 + g : a.n_leaf + g;
+  const int64_t wi = LEVEL2 ? a.n1 + g : g;
+  const float4* w4 = reinterpret_cast<const float4*>(a.wts + 8 * wi);
+  const float4 wa = w4[0], wb = w4[1];
+  const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+  const float iW = a.iws[wi];
+  int64_t child[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    child[j] = j < k ? (LEVEL2 ? a.n_leaf + 8 * g + j : (int64_t)a.order[8 * g + j]) : 0;
+  const int p0 = blockIdx.y * kShPlanes;
+#pragma unroll
+  for (int q = 0; q < kShPlanes; ++q) {
+    const int p = p0 + q;
+    if (p >= 3 * NC) break;
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j < k) acc += w[j] * a.sh[(int64_t)p * a.sh_stride + child[j]];
+    a.sh[(int64_t)p * a.sh_stride + node] = acc * iW;
+  }
+}
+
 struct LodWs {
   uint32_t *bbox, *n_word;
   uint32_t *keys_a, *vals_a, *keys_b, *vals_b, *keys_out, *vals_out;
+  float *wts, *iws;
   void* radix;
   size_t bytes;
 };
@@ -284,6 +323,9 @@ LodWs lod_layout(char* base, int64_t n) {
   w.keys_a = (uint32_t*)take(m); w.vals_a = (uint32_t*)take(m);
   w.keys_b = (uint32_t*)take(m); w.vals_b = (uint32_t*)take(m);
   w.keys_out = (uint32_t*)take(m); w.vals_out = (uint32_t*)take(m);
+  const int64_t coarse = lod_level1(std::max<int64_t>(1, n)) + lod_level2(std::max<int64_t>(1, n));
+  w.wts = (float*)take(sizeof(float) * 8 * (size_t)coarse);
+  w.iws = (float*)take(sizeof(float) * (size_t)coarse);
   w.radix = take(radix_workspace(std::max<int64_t>(1, n)));
   w.bytes = off;
   return w;
@@ -291,10 +333,17 @@ LodWs lod_layout(char* base, int64_t n) {
 
 template <int NC>
 void launch_merges(const MergeArgs& a, cudaStream_t s) {
-  if (a.n1 > 0)
-    k_lod_merge<NC, false><<<(unsigned)((a.n1 + kLodThreads - 1) / kLodThreads), kLodThreads, 0, s>>>(a);
-  if (a.n2 > 0)
-    k_lod_merge<NC, true><<<(unsigned)((a.n2 + kLodThreads - 1) / kLodThreads), kLodThreads, 0, s>>>(a);
+  const unsigned planes = (unsigned)((3 * NC + kShPlanes - 1) / kShPlanes);
+  if (a.n1 > 0) {
+    const unsigned gx = (unsigned)((a.n1 + kLodThreads - 1) / kLodThreads);
+    k_lod_merge<NC, false><<<gx, kLodThreads, 0, s>>>(a);
+    k_lod_merge_sh<NC, false><<<dim3(gx, planes), kLodThreads, 0, s>>>(a);
+  }
+  if (a.n2 > 0) {
+    const unsigned gx = (unsigned)((a.n2 + kLodThreads - 1) / kLodThreads);
+    k_lod_merge<NC, true><<<gx, kLodThreads, 0, s>>>(a);
+    k_lod_merge_sh<NC, true><<<dim3(gx, planes), kLodThreads, 0, s>>>(a);
+  }
 }
 
 }  // namespace
@@ -323,6 +372,8 @@ gs_status launch_lod_build(const gs_grads& nodes, int64_t n_leaf, int32_t* paren
   a.sh_stride = nodes.sh_stride > 0 ? nodes.sh_stride : nodes.n;
   a.parent = parent;
   a.order = w.vals_out;
+  a.wts = w.wts;
+  a.iws = w.iws;
   a.n_leaf = n_leaf;
   a.n1 = lod_level1(n_leaf);
   a.n2 = lod_level2(n_leaf);
