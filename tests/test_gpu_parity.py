@@ -364,6 +364,45 @@ def test_full_size_500k_720p_sampled_windows(cuda_device):
         compare_grads(g_gpu, g_ref)
 
 
+# ---------------------------------------------------------------------------
+# full size, batched: 2M Gaussians, SH3, 16 views of uneven resolution
+# (540p-1080p) on the inward loop, all in one launch per stage, with the blend
+# schedule the autotuner picks (the bench's batched launch configuration)
+# ---------------------------------------------------------------------------
+def test_full_size_batched_2m_16_views_sampled_windows(cuda_device):
+    sc = synth.box_scene(2_000_000, seed=1007)
+    cams = synth.loop_views(16, 1009)
+    rng = np.random.default_rng(3)
+    wins = [(int(rng.integers(0, c.width - 32)), int(rng.integers(0, c.height - 32)), 32, 32) for c in cams[:-1]]
+    wins.append((cams[-1].width - 24, cams[-1].height - 20, 24, 20))  # a ragged corner
+    ref = oracle.render(sc, cams, windows=wins)
+    # a loss gradient living in the windows, zero on pixels whose decisions
+    # the oracle flags as too close to a threshold to be compared
+    gw = [np.where(f[None] != 0, 0.0, rng.normal(size=(3, w[3], w[2])) / (3 * w[2] * w[3] * 16))
+          for f, w in zip(ref["flags"], wins)]
+    dfull = [np.zeros((3, c.height, c.width)) for c in cams]
+    for d, g, (x0, y0, w, h) in zip(dfull, gw, wins):
+        d[:, y0:y0 + h, x0:x0 + w] = g
+    r, arena, poses, img, alpha = gpu_forward(sc, cams)
+    dimg = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dfull]).astype(np.float32)).to(cuda_device)
+    r.autotune(img, dimg, reps=1)
+    r.forward(arena, poses, img, alpha)
+    imgs, alphas = r.split(img.cpu(), 3), r.split(alpha.cpu(), 1)
+    flagged = total = 0
+    for v, (x0, y0, w, h) in enumerate(wins):
+        ok = (ref["flags"][v] & 1) == 0
+        flagged += int((~ok).sum())
+        total += ok.size
+        d = np.abs(imgs[v].numpy().astype(np.float64)[:, y0:y0 + h, x0:x0 + w] - ref["image"][v])
+        assert d[:, ok].max(initial=0.0) <= IMG_TOL, v
+        da = np.abs(alphas[v].numpy().astype(np.float64)[y0:y0 + h, x0:x0 + w] - ref["alpha"][v])
+        assert da[ok].max(initial=0.0) <= IMG_TOL, v
+    assert flagged <= 0.03 * total
+    g_ref = oracle.backward(sc, cams, gw, windows=wins)
+    g_gpu = gpu_backward(r, arena, poses, dfull, image=img)
+    compare_grads(g_gpu, g_ref)
+
+
 def test_tile_order_is_a_bucketed_permutation_and_changes_nothing(cuda_device):
     """Longest-lists-first scheduling: the order is a permutation of the
     tiles with non-increasing power-of-two length buckets (empty tiles last),
