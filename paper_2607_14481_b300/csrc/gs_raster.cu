@@ -325,10 +325,16 @@ __device__ __forceinline__ uint32_t pair_slot(const BwdArgs& a, int64_t vbase, u
 }
 
 // Stores one pair's gradients: the sum over the warps that touched it, in
-// warp order (deterministic), or zeros when none did.
+// warp order (deterministic), or zeros when none did.  Values 0-4 arrive as
+// the moments S = (sum dx dp, sum dy dp, sum dx^2 dp, sum dx dy dp,
+// sum dy^2 dp) of dp = dL/dpower over the tile's pixels (alpha_grad); with
+// power = -(A dx^2 / 2 + B dx dy + C dy^2 / 2) and dx = m_x - p_x they give,
+// with the splat's conic co = (A, B, C):
+//   dL/dm_x = -(A S_x + B S_y),  dL/dm_y = -(B S_x + C S_y),
+//   dL/dA = -S_xx / 2,  dL/dB = -S_xy,  dL/dC = -S_yy / 2.
 __device__ __forceinline__ void store_pair(const BwdArgs& a, uint32_t pidx,
                                            const float (&red)[kWarps][kPartialValues],
-                                           const uint8_t (&hit)[kWarps]) {
+                                           const uint8_t (&hit)[kWarps], const float4 co) {
   if ((int64_t)pidx >= a.cap) {
     if (pidx != 0xffffffffu) atomicOr(&a.counts[2], 2u);
     return;
@@ -342,6 +348,12 @@ __device__ __forceinline__ void store_pair(const BwdArgs& a, uint32_t pidx,
       if (hit[w]) acc += red[w][c];
     sum[c] = acc;
   }
+  const float sx = sum[0], sy = sum[1], sxx = sum[2], sxy = sum[3], syy = sum[4];
+  sum[0] = -(co.x * sx + co.y * sy);
+  sum[1] = -(co.y * sx + co.z * sy);
+  sum[2] = -0.5f * sxx;
+  sum[3] = -sxy;
+  sum[4] = -0.5f * syy;
   float4* dst = reinterpret_cast<float4*>(a.partials + (int64_t)pidx * kPartialStride);
   dst[0] = make_float4(sum[0], sum[1], sum[2], sum[3]);
   dst[1] = make_float4(sum[4], sum[5], sum[6], sum[7]);
@@ -399,25 +411,28 @@ __device__ __forceinline__ void warp_sum9(const float (&d)[kPartialValues], int 
   t8 = v;
 }
 
-// Chain rule from dL/dalpha to the splat's mean, conic and opacity (none
-// while alpha is clamped at its maximum).
-__device__ __forceinline__ void alpha_grad(const Eval& e, const float4 co, float dal,
-                                           float (&d)[kPartialValues]) {
+// Chain rule from dL/dalpha to the splat's opacity and to dp = dL/dpower
+// (none while alpha is clamped at its maximum).  The mean and conic
+// gradients are linear in dp with coefficients from the pixel offset and the
+// conic, so a pixel adds only the moments dx dp, dy dp, dx^2 dp, dx dy dp,
+// dy^2 dp to d[0..4]; store_pair applies the conic once per (tile, splat).
+__device__ __forceinline__ void alpha_grad(const Eval& e, float dal, float (&d)[kPartialValues]) {
   if (e.raw <= kAlphaMax) {
     d[5] += dal * e.ex;                  // d alpha / d opacity = exp(power)
     const float dp = dal * e.alpha;      // d alpha / d power = alpha
-    d[2] -= 0.5f * e.dx * e.dx * dp;
-    d[3] -= e.dx * e.dy * dp;
-    d[4] -= 0.5f * e.dy * e.dy * dp;
-    d[0] -= (co.x * e.dx + co.y * e.dy) * dp;
-    d[1] -= (co.z * e.dy + co.y * e.dx) * dp;
+    const float xp = e.dx * dp, yp = e.dy * dp;
+    d[0] += xp;
+    d[1] += yp;
+    d[2] += e.dx * xp;
+    d[3] += e.dy * xp;
+    d[4] += e.dy * yp;
   }
 }
 
 // Gradient contribution of one blended splat at one pixel, walking back to
 // front: T is the transmittance behind the splat on entry and in front of it
 // on return; acc is the colour behind it (background included).
-__device__ __forceinline__ void splat_grad(const Eval& e, const float4 co, const float4 col, float g0,
+__device__ __forceinline__ void splat_grad(const Eval& e, const float4 col, float g0,
                                            float g1, float g2, float ga, float Tfinal, float& T,
                                            float& acc0, float& acc1, float& acc2,
                                            float (&d)[kPartialValues]) {
@@ -430,25 +445,25 @@ __device__ __forceinline__ void splat_grad(const Eval& e, const float4 co, const
   const float dal = g0 * (col.x * Tb - acc0 * rom) + g1 * (col.y * Tb - acc1 * rom) +
                     g2 * (col.z * Tb - acc2 * rom) + ga * Tfinal * rom;
   acc0 += col.x * w; acc1 += col.y * w; acc2 += col.z * w;
-  alpha_grad(e, co, dal, d);
+  alpha_grad(e, dal, d);
   T = Tb;
 }
 
 // Single-pass form, walking front to back: T is the transmittance in front
-// of the splat (unchanged here); rem is the colour still to come behind it,
-// background included, as the forward image minus the colour composited so
-// far; on return it no longer holds this splat's share.
-__device__ __forceinline__ void splat_grad_front(const Eval& e, const float4 co, const float4 col,
-                                                 float g0, float g1, float g2, float T, float& rem0,
-                                                 float& rem1, float& rem2, float (&d)[kPartialValues]) {
+// of the splat (unchanged here).  rem, the colour still to come behind the
+// splat (background included, the forward image minus the colour composited
+// so far), enters the gradient only through g . rem, so the pixel carries
+// that one number, R = g . rem; on return it no longer holds this splat's
+// share.  dL/dalpha = T (g . c) - (g . rem) / (1 - alpha): the colour behind
+// the splat seen through it is T S = rem / (1 - alpha).
+__device__ __forceinline__ void splat_grad_front(const Eval& e, const float4 col, float g0, float g1,
+                                                 float g2, float T, float& R, float (&d)[kPartialValues]) {
   const float w = e.alpha * T;
   d[6] += g0 * w; d[7] += g1 * w; d[8] += g2 * w;
-  rem0 -= col.x * w; rem1 -= col.y * w; rem2 -= col.z * w;
-  // colour behind the splat seen through it: T S = rem / (1 - alpha)
+  const float gc = g0 * col.x + g1 * col.y + g2 * col.z;
+  R -= gc * w;
   const float rom = __fdividef(1.f, 1.f - e.alpha);
-  const float dal = g0 * (col.x * T - rem0 * rom) + g1 * (col.y * T - rem1 * rom) +
-                    g2 * (col.z * T - rem2 * rom);
-  alpha_grad(e, co, dal, d);
+  alpha_grad(e, gc * T - R * rom, d);
 }
 
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const ViewTable vt) {
@@ -542,15 +557,15 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
       for (int c = 0; c < kPartialValues; ++c) d[c] = 0.f;
       bool contrib = false;
       if (pos <= mylast) {
-        const float4 g = s_geo[k], g2 = s_geo2[k], co = s_co[k], col = s_rgb[k];
+        const float4 g = s_geo[k], g2 = s_geo2[k], col = s_rgb[k];
         const XTerms x = splat_x(g, tc.lx);
         Eval e;
         if (pos <= last0 && splat_alpha(x, g, g2, tc.ly0, e)) {
-          splat_grad(e, co, col, g00, g01, g02, ga0, Tf0, T0, a00, a01, a02, d);
+          splat_grad(e, col, g00, g01, g02, ga0, Tf0, T0, a00, a01, a02, d);
           contrib = true;
         }
         if (pos <= last1 && splat_alpha(x, g, g2, tc.ly1, e)) {
-          splat_grad(e, co, col, g10, g11, g12, ga1, Tf1, T1, a10, a11, a12, d);
+          splat_grad(e, col, g10, g11, g12, ga1, Tf1, T1, a10, a11, a12, d);
           contrib = true;
         }
       }
@@ -566,7 +581,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
       }
     }
     __syncthreads();
-    if (threadIdx.x < cnt) store_pair(a, s_pidx[threadIdx.x], s_red[threadIdx.x], s_hit[threadIdx.x]);
+    if (threadIdx.x < cnt)
+      store_pair(a, s_pidx[threadIdx.x], s_red[threadIdx.x], s_hit[threadIdx.x], s_co[threadIdx.x]);
   }
 }
 
@@ -594,16 +610,16 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
   const float* gimg = a.dimage + 3 * vi.pix_base;
   const float* cimg = a.image + 3 * vi.pix_base;
   float g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f;
-  float r00 = 0.f, r01 = 0.f, r02 = 0.f, r10 = 0.f, r11 = 0.f, r12 = 0.f;
+  float R0 = 0.f, R1 = 0.f;  // g . (colour still to come), per pixel
   if (tc.in0) {
     const int64_t pix = (int64_t)tc.py0 * vi.W + tc.px;
     g00 = gimg[pix]; g01 = gimg[np + pix]; g02 = gimg[2 * np + pix];
-    r00 = cimg[pix]; r01 = cimg[np + pix]; r02 = cimg[2 * np + pix];
+    R0 = g00 * cimg[pix] + g01 * cimg[np + pix] + g02 * cimg[2 * np + pix];
   }
   if (tc.in1) {
     const int64_t pix = (int64_t)(tc.py0 + 1) * vi.W + tc.px;
     g10 = gimg[pix]; g11 = gimg[np + pix]; g12 = gimg[2 * np + pix];
-    r10 = cimg[pix]; r11 = cimg[np + pix]; r12 = cimg[2 * np + pix];
+    R1 = g10 * cimg[pix] + g11 * cimg[np + pix] + g12 * cimg[2 * np + pix];
   }
   float T0 = 1.f, T1 = 1.f;
   bool d0 = !tc.in0, d1 = !tc.in1;
@@ -635,7 +651,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
         if (Tn < kTransMin) {
           d0 = true;
         } else {
-          splat_grad_front(e, s_co[k], s_rgb[k], g00, g01, g02, T0, r00, r01, r02, d);
+          splat_grad_front(e, s_rgb[k], g00, g01, g02, T0, R0, d);
           T0 = Tn;
           contrib = true;
         }
@@ -645,7 +661,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
         if (Tn < kTransMin) {
           d1 = true;
         } else {
-          splat_grad_front(e, s_co[k], s_rgb[k], g10, g11, g12, T1, r10, r11, r12, d);
+          splat_grad_front(e, s_rgb[k], g10, g11, g12, T1, R1, d);
           T1 = Tn;
           contrib = true;
         }
@@ -662,7 +678,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
       }
     }
     __syncthreads();
-    if (threadIdx.x < cnt) store_pair(a, s_pidx[threadIdx.x], s_red[threadIdx.x], s_hit[threadIdx.x]);
+    if (threadIdx.x < cnt)
+      store_pair(a, s_pidx[threadIdx.x], s_red[threadIdx.x], s_hit[threadIdx.x], s_co[threadIdx.x]);
   }
   // pairs past the batch where every pixel of the tile had stopped
   for (uint32_t p = start + threadIdx.x; p < rg.y; p += kThreads) zero_pair(a, vbase, p, tc);
