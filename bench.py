@@ -732,7 +732,7 @@ OPS_TEST, OPS_FWD_BLEND, OPS_BWD_BLEND = 21, 7, 63
 # taken on; the source summary is under profiles/.
 MEASURED_TRAFFIC = {
     ("render_bwd_pixels", 1_000_000, (1280, 720), 1): {
-        "bytes": 73.038e6 + 13.476e6,
+        "bytes": 73.056e6 + 13.642e6,
         "source": "profiles/k_render_bwd_front_1M_720p.md (k_render_bwd_front<64>, pose 50)"},
 }
 
