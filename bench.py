@@ -98,16 +98,38 @@ def allreduce_max(x, ws):
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
+    """SM clock and clock-event reasons while the timed loops run: read-only
+    NVML queries every 5 ms from a thread (the timed region is a fraction of
+    a second), else nvidia-smi at its 200 ms period."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.nv = None
         self.lines = []
+        self.samples = []
 
     def start(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self.smax = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
+            self.bits = dict(zip(self.REASONS, (pynvml.nvmlClocksEventReasonHwSlowdown,
+                                                pynvml.nvmlClocksEventReasonHwThermalSlowdown,
+                                                pynvml.nvmlClocksEventReasonSwThermalSlowdown,
+                                                pynvml.nvmlClocksEventReasonSwPowerCap)))
+            self.nv = pynvml
+            self.done = threading.Event()
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
+        except Exception:
+            self.nv = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
@@ -118,11 +140,33 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
+    def _poll(self):
+        nv = self.nv
+        while not self.done.is_set():
+            try:
+                sm = float(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
+                r = int(nv.nvmlDeviceGetCurrentClocksEventReasons(self.h))
+            except Exception:
+                return
+            self.samples.append((sm, r))
+            self.done.wait(0.005)
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nv is not None:
+            self.done.set()
+            self.thread.join(timeout=2)
+            try:
+                self.nv.nvmlShutdown()
+            except Exception:
+                pass
+            sm = [x for x, _ in self.samples]
+            reasons = sorted({nm for _, r in self.samples for nm, b in self.bits.items() if r & b})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.smax,
+                    "reasons": reasons, "samples": len(sm), "source": "NVML every 5 ms"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -132,7 +176,6 @@ class ClockSampler:
             self.proc.kill()
         self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
@@ -142,12 +185,12 @@ class ClockSampler:
                 smax.append(float(parts[1]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[4:8]):
+            for nm, val in zip(self.REASONS, parts[4:8]):
                 if val.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi every 200 ms"}
 
 
 # ---------------------------------------------------------------------------
@@ -372,10 +415,9 @@ def run_ours(args, ws, rank, local):
     for _ in range(max(3, args.warmup)):
         wl.step()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local)  # over both timed loops (device-timed and end-to-end)
     clocks.start()
     elapsed = timed_loop(wl, K, ws)
-    clk = clocks.stop()
     bad = wl.check_device_status()
     value = ws * K / elapsed
     e2e = None
@@ -384,6 +426,8 @@ def run_ours(args, ws, rank, local):
         e2e = {"value": ws * K / e_el, "unit": "iters/s",
                "h2d_bytes_per_step": int(wl.targets[0].numel() * 4), "d2h_bytes_per_step": 4,
                "ms_per_step": 1e3 * e_el / K}
+    clk = clocks.stop()
+    if not args.no_e2e:
         wl.check_device_status()
     stage_ms, work = stage_times(wl, min(K, 30))
     wl.check_device_status()
