@@ -97,6 +97,52 @@ def allreduce_max(x, ws):
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
+class _NvmlLib:
+    """The few read-only NVML queries the clock sampler makes, through the
+    driver's libnvidia-ml with ctypes, for hosts without the Python binding.
+    Reason bits are the NVML API's clocks-event-reason values."""
+    NVML_CLOCK_SM = 1
+    nvmlClocksEventReasonSwPowerCap = 0x4
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+
+    def __init__(self):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, rc):
+        if rc != 0:
+            raise RuntimeError(f"NVML error {rc}")
+
+    def nvmlInit(self):
+        self._ok(self.lib.nvmlInit_v2())
+
+    def nvmlShutdown(self):
+        self.lib.nvmlShutdown()
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self.C.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByIndex_v2(self.C.c_uint(i), self.C.byref(h)))
+        return h
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        v = self.C.c_uint()
+        self._ok(self.lib.nvmlDeviceGetClockInfo(h, self.C.c_int(kind), self.C.byref(v)))
+        return v.value
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        v = self.C.c_uint()
+        self._ok(self.lib.nvmlDeviceGetMaxClockInfo(h, self.C.c_int(kind), self.C.byref(v)))
+        return v.value
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.C.c_ulonglong()
+        self._ok(self.lib.nvmlDeviceGetCurrentClocksThrottleReasons(h, self.C.byref(v)))
+        return v.value
+
+
 class ClockSampler:
     """SM clock and clock-event reasons while the timed loops run: read-only
     NVML queries every 5 ms from a thread (the timed region is a fraction of
@@ -115,7 +161,10 @@ class ClockSampler:
 
     def start(self):
         try:
-            import pynvml
+            try:
+                import pynvml
+            except ImportError:
+                pynvml = _NvmlLib()
             pynvml.nvmlInit()
             self.h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
             self.smax = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
