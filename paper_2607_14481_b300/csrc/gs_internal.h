@@ -88,7 +88,10 @@ size_t loss_workspace_bytes();
 gs_status launch_loss(const float* img, const float* tgt, int64_t count, int kind, float* grad,
                       float* loss, void* ws, cudaStream_t s);
 
-constexpr int kPartialValues = 9;       // dmx, dmy, dA, dB, dC, dopacity, dr, dg, db
+// Per (tile, splat) pair as stored: dmx, dmy, dA, dB, dC, dopacity, dr, dg, db.
+// Inside the blend kernels values 0-4 hold the moments of dL/dpower until
+// store_pair applies the splat's conic.
+constexpr int kPartialValues = 9;
 constexpr int kPartialStride = 12;      // floats per (tile, splat) pair: 3 float4, last 3 unused
 constexpr int kGradBlock = 256;         // threads per block of the per-Gaussian backward
 
