@@ -495,6 +495,12 @@ def run_ours(args, ws, rank, local):
         cams16 = synth.loop_views(16, SEED_TRAJ + 1)
         batched = run_batched(args.n, device, cams16, K, args.warmup, ws, rank)
         batched["vs_plain_view_iters"] = batched["view_iters_per_s"] / (ws * K / elapsed)
+        # equal work per view: the same 16 loop views, all at the plain mode's 1280x720
+        eq = run_batched(args.n, device, [synth.with_resolution(c, 1280, 720) for c in cams16], K,
+                         args.warmup, ws, rank)
+        batched["equal_work_720p"] = {k: eq[k] for k in ("view_iters_per_s", "mpix_per_s", "ms_per_iter",
+                                                         "pixels_per_iter", "pairs_max", "stage_ms")}
+        batched["equal_work_720p"]["vs_plain_view_iters"] = eq["view_iters_per_s"] / (ws * K / elapsed)
         if args.n != N_BATCHED:
             batched["at_2m"] = run_batched(N_BATCHED, device, cams16, K, args.warmup, ws, rank)
 
