@@ -196,6 +196,22 @@ __device__ __forceinline__ void stage_splat(const float4* xy, const float4* coni
                                              __fmul_rn(-0.5f * kLog2e, co.z), -log2f(255.f * co.w), col.w);
 }
 
+// Bit set of the staged splats [0, cnt) that warp `warp` can reach (its bit
+// of s_mask), 32 per word, written to s_wb[0 .. ceil(cnt/32)): the warp's
+// loop visits only these, in ascending order (front to back), instead of
+// stepping over every staged splat and testing its bit.  Each warp builds
+// and reads its own words (a __syncwarp orders them).
+template <int kBatch>
+__device__ __forceinline__ void warp_bits(const uint8_t* s_mask, int cnt, int warp, int lane, uint32_t* s_wb) {
+#pragma unroll
+  for (int q = 0; q < kBatch / 32; ++q) {
+    const int k = q * 32 + lane;
+    const uint32_t word = __ballot_sync(0xffffffffu, k < cnt && ((s_mask[k] >> warp) & 1u));
+    if (lane == 0) s_wb[q] = word;
+  }
+  __syncwarp();
+}
+
 // COUNT = true is the diagnostic instantiation behind gs_render_stats: the
 // same loop, also counting per pixel the splats tested (up to and including
 // the one that stops it) and blended, and per tile the backward's walk length.
@@ -204,8 +220,9 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
                                                          unsigned long long* stats) {
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch];
   __shared__ uint8_t s_mask[kBatch];
+  __shared__ uint32_t s_wb[kWarps][kBatch / 32];
   __shared__ int s_last;
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
   const TileCoords tc = tile_coords(vt, gt);
   const ViewInfo& vi = vt.v[tc.v];
@@ -224,8 +241,10 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
       stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + t, t, tc.ox, tc.oy, s_geo, s_geo2,
                   s_rgb, s_mask, nullptr, COUNT ? nullptr : a.counts);
     __syncthreads();
-    for (int k = 0; k < cnt && !(d0 && d1); ++k) {
-      if (!((s_mask[k] >> warp) & 1u)) continue;  // warp-uniform
+    warp_bits<kBatch>(s_mask, cnt, warp, lane, s_wb[warp]);
+    for (int q = 0; q * 32 < cnt && !(d0 && d1); ++q) {
+     for (uint32_t bits = s_wb[warp][q]; bits && !(d0 && d1); bits &= bits - 1) {
+      const int k = q * 32 + __ffs(bits) - 1;
       const float4 g = s_geo[k], g2 = s_geo2[k];
       const XTerms x = splat_x(g, tc.lx);
       Eval e;
@@ -259,6 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
           }
         }
       }
+     }
     }
   }
   if (COUNT) {
@@ -596,6 +616,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
   static_assert(kBatch <= kThreads, "one staged splat per thread");
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
   __shared__ uint8_t s_mask[kBatch];
+  __shared__ uint32_t s_wb[kWarps][kBatch / 32];
   __shared__ uint32_t s_pidx[kBatch];
   __shared__ float s_red[kBatch][kWarps][kPartialValues];
   __shared__ uint8_t s_hit[kBatch][kWarps];
@@ -636,9 +657,15 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
       for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
     }
     __syncthreads();
-    for (int k = 0; k < cnt; ++k) {
-      if (__all_sync(0xffffffffu, d0 && d1)) break;  // the warp's pixels are done
-      if (!((s_mask[k] >> warp) & 1u)) continue;  // warp-uniform: no contribution
+    warp_bits<kBatch>(s_mask, cnt, warp, lane, s_wb[warp]);
+    bool live = true;
+    for (int q = 0; q * 32 < cnt && live; ++q) {
+     for (uint32_t bits = s_wb[warp][q]; bits; bits &= bits - 1) {  // warp-uniform
+      if (__all_sync(0xffffffffu, d0 && d1)) {  // the warp's pixels are done
+        live = false;
+        break;
+      }
+      const int k = q * 32 + __ffs(bits) - 1;
       float d[kPartialValues];
 #pragma unroll
       for (int c = 0; c < kPartialValues; ++c) d[c] = 0.f;
@@ -676,6 +703,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
           s_hit[k][warp] = 1;
         }
       }
+     }
     }
     __syncthreads();
     if (threadIdx.x < cnt)
