@@ -829,7 +829,11 @@ OPS_TEST, OPS_FWD_BLEND, OPS_BWD_BLEND = 21, 7, 63
 # DRAM bytes per launch of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), for the workload it was
 # taken on; the source summary is under profiles/.
-MEASURED_TRAFFIC = {}  # (empty until the changed per-pixel backward is captured again)
+MEASURED_TRAFFIC = {
+    ("render_bwd_pixels", 1_000_000, (1280, 720), 1): {
+        "bytes": 73.157e6 + 13.708e6,
+        "source": "profiles/k_render_bwd_front_1M_720p.md (k_render_bwd_front<64>, pose 50)"},
+}
 
 
 def roofline(wl, stage_ms, work, peaks):
