@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
   constexpr int kBatch = kThreads;
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
   __shared__ uint8_t s_mask[kBatch];
+  __shared__ uint32_t s_wb[kWarps][kBatch / 32];
   __shared__ uint32_t s_pidx[kBatch];
   __shared__ float s_red[kBatch][kWarps][kPartialValues];
   __shared__ uint8_t s_hit[kBatch][kWarps];
@@ -514,8 +515,10 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
                   s_rgb, s_mask, nullptr, nullptr);
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
-    for (int k = 0; k < cnt && !(d0 && d1); ++k) {
-      if (!((s_mask[k] >> warp) & 1u)) continue;
+    warp_bits<kBatch>(s_mask, cnt, warp, lane, s_wb[warp]);
+    for (int q = 0; q * 32 < cnt && !(d0 && d1); ++q) {
+     for (uint32_t bits = s_wb[warp][q]; bits && !(d0 && d1); bits &= bits - 1) {
+      const int k = q * 32 + __ffs(bits) - 1;
       const float4 g = s_geo[k], g2 = s_geo2[k];
       const XTerms x = splat_x(g, tc.lx);
       Eval e;
@@ -527,6 +530,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
         const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
         if (Tn < kTransMin) d1 = true; else { T1 = Tn; last1 = (int)(start + k); }
       }
+     }
     }
   }
   __syncthreads();
@@ -569,8 +573,12 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
       for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
     }
     __syncthreads();
-    for (int k = cnt - 1; k >= 0; --k) {
-      if (!((s_mask[k] >> warp) & 1u)) continue;  // warp-uniform: no contribution
+    warp_bits<kBatch>(s_mask, cnt, warp, lane, s_wb[warp]);
+    for (int q = (cnt - 1) >> 5; q >= 0; --q) {
+     for (uint32_t bits = s_wb[warp][q]; bits;) {  // highest bit first: back to front
+      const int hb = 31 - __clz(bits);
+      bits ^= 1u << hb;
+      const int k = q * 32 + hb;
       const int pos = bstart + k;
       float d[kPartialValues];
 #pragma unroll
@@ -599,6 +607,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
           s_hit[k][warp] = 1;
         }
       }
+     }
     }
     __syncthreads();
     if (threadIdx.x < cnt)
