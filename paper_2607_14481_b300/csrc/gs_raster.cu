@@ -7,8 +7,15 @@
 // is staged in shared memory by the CTA's threads with coalesced float4 loads,
 // together with a mask of the warps whose strip of 4 rows the splat can reach
 // at alpha >= 1/255 (the exponent's maximum over the strip, a conservative
-// test, so a warp never skips a splat the exact per-pixel test would accept).  The CTA
-// leaves the list as soon as every pixel has saturated (__syncthreads_count).
+// test, so a warp never skips a splat the exact per-pixel test would accept).
+// Each warp turns its bits of the masks into a bit set with one ballot per 32
+// staged splats and visits only the set bits, in list order.  The CTA leaves
+// the list as soon as every pixel has saturated (__syncthreads_count).
+//
+// The backward accumulates per pixel only the moments of dL/dpower (dx dp,
+// dy dp, dx^2 dp, dx dy dp, dy^2 dp) for the splat's mean and conic; the conic
+// is applied once per (tile, splat) when the pair's reduced gradient is
+// stored.
 //
 // Each staged splat carries its centre relative to the tile origin, its conic
 // scaled to base-2 exponent units and the exponent threshold below which its
