@@ -15,7 +15,9 @@ on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -316,6 +318,10 @@ class Workload:
             self.pool = torch.cuda.graph_pool_handle()
             for st in self.steps:
                 st.capture(pool=self.pool)
+            # every graph replayed once, so no timed step is a graph's first replay
+            for st in self.steps:
+                st.run()
+            torch.cuda.synchronize()
         self.targets_host = [t.cpu().pin_memory() for t in self.targets]
         self.i = 0
         self.pixels_per_iter = self.view_pixels[0] if batched else self.cams[0].width * self.cams[0].height
@@ -326,10 +332,20 @@ class Workload:
         st.run()
         return st
 
-    def instrumented_step(self, ev):
-        """The same iteration run eagerly with CUDA events at the stage
-        boundaries (on the launching stream)."""
-        st = self.steps[self.i % len(self.steps)]
+    def sequence(self, K):
+        """Trajectory positions of K timed steps spread evenly over the whole
+        trajectory (step i takes pose floor(i P / K) of the P poses), so the
+        timed window covers every part of it whatever K is."""
+        P = len(self.steps)
+        return [(i * P) // K % P for i in range(K)]
+
+    def instrumented_step(self, ev, k=None):
+        """The same iteration (trajectory position k, default the next one)
+        run eagerly with CUDA events at the stage boundaries (on the launching
+        stream)."""
+        if k is None:
+            k = self.i % len(self.steps)
+        st = self.steps[k]
         self.i += 1
         r = st.rast
         r.set_cameras(st.cams)
@@ -359,21 +375,22 @@ class Workload:
 
 def timed_loop(wl, K, ws, e2e=False):
     """K iterations between a barrier + synchronize on both sides; device time
-    from CUDA events on the launching stream, max over ranks.
+    from CUDA events on the launching stream, max over ranks.  The K steps
+    take the poses of wl.sequence(K) (spread over the whole trajectory).
 
     e2e: every iteration also copies its target image from pinned host memory
     (on a copy stream, one iteration ahead, so the copy of iteration i + 1
-    overlaps the compute of iteration i; iteration i waits for its own copy)
-    and reads its loss back to pinned host memory."""
+    overlaps the compute of iteration i; iteration i waits for its own copy,
+    and a copy into a target buffer waits for the last iteration that read
+    it) and reads its loss back to pinned host memory."""
     import torch
+    seq = wl.sequence(K)
     loss_host = torch.zeros(max(K, 1), dtype=torch.float32).pin_memory() if e2e else None
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream() if e2e else None
-    n_buf = len(wl.steps)
-    done_ev = [None] * n_buf  # last iteration that read each target buffer
+    done_ev = [None] * len(wl.steps)  # last iteration that read each target buffer
 
-    def issue_copy(j):
-        k = (wl.i + j) % n_buf
+    def issue_copy(k):
         ev = torch.cuda.Event()
         with torch.cuda.stream(copy):
             if done_ev[k] is not None:
@@ -388,36 +405,39 @@ def timed_loop(wl, K, ws, e2e=False):
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
     t0.record()
-    ready = issue_copy(0) if e2e else None
+    ready = issue_copy(seq[0]) if e2e else None
     for i in range(K):
+        k = seq[i]
+        st = wl.steps[k]
         if e2e:
-            nxt = issue_copy(1) if i + 1 < K else None
             comp.wait_event(ready)
-            k = wl.i % n_buf
-        st = wl.step()
+        st.run()
         if e2e:
             loss_host[i:i + 1].copy_(st.loss.loss, non_blocking=True)
             done_ev[k] = torch.cuda.Event()
             done_ev[k].record(comp)
-            ready = nxt
+            if i + 1 < K:
+                ready = issue_copy(seq[i + 1])
     t1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(ws)
+    wl.i += K
     return allreduce_max(t0.elapsed_time(t1) / 1e3, ws)
 
 
 def stage_times(wl, K):
     """Per-stage device times (CUDA events on the launching stream) of K eager
-    iterations, and the blend work counts of each iteration's tile lists."""
+    iterations over poses spread along the trajectory, and the blend work
+    counts of each iteration's tile lists (their means)."""
     import torch
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)]
     counts = []
+    seq = wl.sequence(K)
     torch.cuda.nvtx.range_push("eager")
     for i in range(K):
-        wl.instrumented_step(evs[i])
-        if i < 8:
-            counts.append(wl.rast.render_stats())
+        wl.instrumented_step(evs[i], seq[i])
+        counts.append(wl.rast.render_stats())
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = {s: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K)]))
@@ -444,7 +464,7 @@ def run_batched(n, device, cams16, K, warmup, ws, rank):
            "pixels_per_iter": wb.pixels_per_iter, "pairs_max": wb.kmax,
            "resolutions": [[c.width, c.height] for c in cams16], "stage_ms": sb,
            "blend_schedule": wb.tuning,
-           "roofline": roofline(wb, sb, wkb, load_peaks())}
+           "roofline": roofline(wb, sb, wkb, load_peaks(), sm_count(device))}
     del wb
     torch.cuda.empty_cache()
     return out
@@ -481,7 +501,8 @@ def run_ours(args, ws, rank, local):
     stage_ms, work = stage_times(wl, min(K, 30))
     wl.check_device_status()
     peaks = load_peaks()
-    roof = roofline(wl, stage_ms, work, peaks)
+    roof = roofline(wl, stage_ms, work, peaks, sm_count(device), workload_key=traffic_key(args.n))
+    poses_timed = wl.sequence(K)
     plain_pixels = wl.pixels_per_iter
     n_launch = launches_per_step(1, wl.rast.num_tiles, bool(wl.tuning["schedule"] & 3))
     plain_tuning = wl.tuning
@@ -516,12 +537,12 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"plain single-view training, {args.n} Gaussians SH3, 1280x720, "
-                               f"100-pose forward trajectory, L1 loss, one CUDA graph per pose",
-                   "gaussians": args.n, "views_per_iter": 1, "resolution": [1280, 720],
-                   "parallelism": f"replicas{ws}",
-                   "l2": "inputs larger than L2 (parameter arena 240 MB, x4 with gradients and moments)",
-                   "blend_schedule": plain_tuning},
+        "config": workload_config(args.n, ws),
+        "poses_timed": {"trajectory_poses": N_POSES, "timed_steps": K, "first": poses_timed[0],
+                        "last": poses_timed[-1], "distinct": len(set(poses_timed)),
+                        "rule": "step i takes pose floor(i * 100 / K) mod 100; every pose's graph replayed "
+                                "once before timing"},
+        "blend_schedule": plain_tuning,
         "mpix_per_s": value * plain_pixels / 1e6,
         "stage_ms": stage_ms,
         "e2e": e2e,
@@ -536,8 +557,21 @@ def run_ours(args, ws, rank, local):
         "nonfinite_flag": bad,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.n, budget_s=20.0)
+        out["cpu_baseline"] = cpu_baseline(args.n)
     return out, rank
+
+
+def workload_config(n, ws=1):
+    """The workload both arms measure (identical dict in both JSON lines)."""
+    return {"workload": f"plain single-view training, {n} Gaussians SH3, 1280x720, 100-pose forward "
+                        f"trajectory, L1 loss (fwd + bwd incl. pose + Adam per iteration)",
+            "gaussians": n, "views_per_iter": 1, "resolution": [1280, 720], "sh_degree": 3,
+            "parallelism": f"replicas{ws}",
+            "l2": "inputs larger than L2 (parameter arena 240 MB, x4 with gradients and moments)"}
+
+
+def traffic_key(n):
+    return f"plain 1280x720 SH3 n={n}"
 
 
 def run_loop_closure(n, device, reps=20, n_kf=160, seed=SEED_STREAM):
@@ -815,138 +849,216 @@ def load_peaks():
         return {"hbm_gbs": 6400.0, "source": "fallback", "sm_max_mhz": 2032.0}
 
 
-# FP32 operations per (pixel, splat) pair, counted from the kernels' source:
-# the splat test (offsets 6, box test 2, quadratic form 7, power test 1,
-# exp 2, opacity product 1, clamp 1, threshold 1) = 21; a forward blend
-# (1 - alpha, transmittance, stop test, weight, 3 colour FMAs) = 7; a backward
-# blend (reciprocal, weights, remaining colour, alpha gradient, opacity,
-# quadratic-form and mean gradients) = 50 + 4 transmittance / stop + 9
-# reduction adds.  The backward's algorithmic work tests each pair once (the
-# single front-to-back pass does exactly that).
-OPS_TEST, OPS_FWD_BLEND, OPS_BWD_BLEND = 21, 7, 63
+# Per evaluated (pixel, splat) pair of the plain per-pixel loop (a pair is
+# evaluated when the pixel reaches the splat in its tile's list: up to and
+# including the splat that stops it):
+#   forward composite  ~12 FP32 operations + 1 MUFU (the exponential);
+#   backward           ~45 FP32 operations + 2 MUFU / divides (two traversals:
+#                      the forward's decisions and the gradient walk).
+# Algorithmic operation counts, not the kernels' own (their per-warp culling
+# skips pairs no pixel of a warp can reach, which still count here).
+OPS_FWD_FP32, OPS_FWD_MUFU = 12, 1
+OPS_BWD_FP32, OPS_BWD_MUFU = 45, 2
+FP32_PER_SM_CLK, MUFU_PER_SM_CLK = 128, 16
+RADIX_DIGIT_BITS = 11  # the LSD radix sort the binning's algorithmic bytes are counted for
 
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), for the workload it was
-# taken on; the source summary is under profiles/.
-MEASURED_TRAFFIC = {
-    ("render_bwd_pixels", 1_000_000, (1280, 720), 1): {
-        "bytes": 73.157e6 + 13.708e6,
-        "source": "profiles/k_render_bwd_front_1M_720p.md (k_render_bwd_front<64>, pose 50)"},
-}
+def bin_sort_bytes(pairs, items, tiles):
+    """Algorithmic bytes of binning: per pair 12 B emitted (key + value), a
+    stable LSD radix sort of the significant key bits (32 depth bits + the
+    tile bits) at 24 B per pass over 11-bit digits, 8 B of range reads; 4 B of
+    scan per (view, Gaussian)."""
+    bits = 32 + max(1, math.ceil(math.log2(max(2, tiles))))
+    passes = math.ceil(bits / RADIX_DIGIT_BITS)
+    return pairs * (12 + 24 * passes + 8) + 4 * items, passes
 
 
-def roofline(wl, stage_ms, work, peaks):
-    """Achieved fraction of each stage's bound; the dominant stage's object is
-    the JSON line's roofline.  HBM stages count algorithmic bytes per launch,
-    the blend stages FP32 operations per launch (work counts from
-    gs_render_stats) against the FP32 issue rate at the maximum SM clock."""
+def sm_count(device=None):
+    import torch
+    return int(torch.cuda.get_device_properties(device if device is not None else 0).multi_processor_count)
+
+
+def alu_roofline(pairs, fp32_per, mufu_per, t_s, sms, clk_mhz):
+    """Algorithmic FP32 operations per second against the bound of the pair
+    rate: min(SMs x 128 FP32 / clk / fp32_per, SMs x 16 MUFU / clk / mufu_per)."""
+    clk = clk_mhz * 1e6
+    fp32_pairs = sms * FP32_PER_SM_CLK * clk / fp32_per
+    mufu_pairs = sms * MUFU_PER_SM_CLK * clk / mufu_per
+    binding = "fp32" if fp32_pairs <= mufu_pairs else "mufu"
+    peak_pairs = min(fp32_pairs, mufu_pairs)
+    rate = pairs / t_s
+    return {"bound": "alu", "achieved": rate * fp32_per / 1e9, "peak": peak_pairs * fp32_per / 1e9,
+            "unit": "Gop/s", "frac": rate / peak_pairs, "binding_unit": binding,
+            "pairs_per_s": rate, "algorithmic": pairs * fp32_per,
+            "per_pair": {"fp32": fp32_per, "mufu": mufu_per}}
+
+
+def load_traffic(kernel, workload_key):
+    """DRAM bytes per launch of `kernel` from the machine-readable capture
+    summary, if one was taken on this workload with the current source of the
+    kernel (sha256 of its .cu file); else None and the reason."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as fh:
+            entries = json.load(fh)["entries"]
+    except (OSError, KeyError, ValueError):
+        return None, "no capture summary"
+    for e in entries:
+        if e.get("kernel") != kernel or e.get("workload") != workload_key:
+            continue
+        src = os.path.join(ROOT, e["source"])
+        try:
+            with open(src, "rb") as fh:
+                sha = hashlib.sha256(fh.read()).hexdigest()
+        except OSError:
+            return None, "kernel source missing"
+        if sha != e.get("source_sha256"):
+            return None, "kernel source changed since the capture"
+        return float(e["bytes_per_launch"]), f"ncu capture ({e.get('kernel_name', kernel)})"
+    return None, "no capture of this kernel on this workload"
+
+
+def roofline(wl, stage_ms, work, peaks, sms, workload_key=None):
+    """Achieved fraction of each stage's bound, with the algorithmic work per
+    unit of the hot path's scope table: HBM bytes for projection, binning,
+    the per-Gaussian backward, Adam and the loss; FP32 / MUFU operations per
+    evaluated pair for the blend stages.  The dominant stage's object is the
+    JSON line's roofline."""
     n = wl.n
     V = len(wl.steps[0].cams)
-    nc = 16
     K = work["listed"]
-    fp32_peak = 148 * 128 * peaks["sm_max_mhz"] * 1e6 / 1e9  # Gop/s
-    per = {
-        "project": ("hbm", (48 + 3 * nc * 4) * n + 68.0 * n * V),
-        "render_bwd_gaussians": ("hbm", (48 + 3 * nc * 4) * n + (48 + 3 * nc * 4) * n + 36.0 * K
-                                 + (12 + 16) * n * V + (16 + 12 + 16) * n * V),
-        "adam": ("hbm", 28.0 * wl.arena.padded),
-        "loss": ("hbm", 3 * 4 * 3.0 * wl.pixels_per_iter),
-        "render_fwd": ("alu", OPS_TEST * work["tested"] + OPS_FWD_BLEND * work["blended"]),
-        "render_bwd_pixels": ("alu", OPS_TEST * work["tested"] + OPS_BWD_BLEND * work["blended"]),
+    E = work["evaluated"]
+    clk = peaks["sm_max_mhz"]
+    bs_bytes, passes = bin_sort_bytes(K, n * V, wl.rast.num_tiles)
+    hbm = {
+        "project": (240.0 + 48.0) * n * V,
+        "bin_sort": bs_bytes,
+        "render_bwd_gaussians": 36.0 * K + 480.0 * n,
+        "adam": 28.0 * wl.arena.padded,
+        "loss": 36.0 * wl.pixels_per_iter,
     }
     table = {}
-    for k, (bound, amount) in per.items():
+    for k, amount in hbm.items():
         t = stage_ms[k] / 1e3
-        if bound == "hbm":
-            ach = amount / t / 1e9
-            table[k] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": ach / peaks["hbm_gbs"], "algorithmic": amount}
-        else:
-            ach = amount / t / 1e9
-            table[k] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "Gop/s",
-                        "frac": ach / fp32_peak, "algorithmic": amount}
-    dom = max(per, key=lambda k: stage_ms[k])
+        ach = amount / t / 1e9
+        table[k] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "algorithmic": amount}
+    table["bin_sort"]["radix_passes"] = passes
+    table["render_fwd"] = alu_roofline(E, OPS_FWD_FP32, OPS_FWD_MUFU, stage_ms["render_fwd"] / 1e3, sms, clk)
+    table["render_bwd_pixels"] = alu_roofline(E, OPS_BWD_FP32, OPS_BWD_MUFU, stage_ms["render_bwd_pixels"] / 1e3,
+                                              sms, clk)
+    dom = max(table, key=lambda k: stage_ms[k])
     out = dict(table[dom])
-    views = len(wl.steps[0].cams)
-    key = (dom, wl.n, (wl.cams[0].width, wl.cams[0].height), views)
-    tr = MEASURED_TRAFFIC.get(key)
-    out.update({"kernel": dom, "traffic": tr["bytes"] if tr else None,
-                "traffic_source": tr["source"] if tr else None,
+    tr, tr_note = load_traffic(dom, workload_key) if workload_key else (None, "no workload key")
+    out.update({"kernel": dom, "traffic": tr, "traffic_note": tr_note,
                 "peak_source": (f"{peaks['source']} HBM copy (burst)" if out["bound"] == "hbm" else
-                                "148 SMs x 128 FP32 lanes x max SM clock"),
-                "work_counts": work, "per_stage": table})
+                                f"{sms} SMs x (128 FP32 | 16 MUFU) per clock x {clk:g} MHz"),
+                "sms": sms, "work_counts": work, "per_stage": table})
     return out
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle baseline (bounded sample)
+# CPU oracle baseline: full iterations of the same workload
 # ---------------------------------------------------------------------------
-def oracle_sample_step(scene, cams, k, targets=None):
-    """One oracle iteration of the sampled workload: forward, L1 loss
-    gradient, backward, Adam (FP64) over the sample's parameters."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+class OracleStep:
+    """One oracle iteration of the workload: FP64 forward render of one
+    1280x720 view of the whole scene, L1 loss gradient, analytic backward,
+    Adam over every parameter.  The target is a seeded uniform image (the
+    work does not depend on its values)."""
+
+    def __init__(self, n, seed=SEED_SCENE):
+        import oracle  # noqa: F401  (builds the oracle if needed)
+        from paper_2607_14481_b300 import synth
+        self.sc = synth.box_scene(n, seed)
+        self.cams = synth.forward_trajectory(N_POSES, SEED_TRAJ)
+        g = np.random.default_rng(SEED_TARGET)
+        self.target = g.random((3, 720, 1280))
+        self.p = np.concatenate([np.asarray(getattr(self.sc, a), np.float64).ravel()
+                                 for a in ("means", "log_scales", "quats", "opa_logits", "sh")])
+        self.m = np.zeros_like(self.p)
+        self.v = np.zeros_like(self.p)
+        self.t = 0
+
+    def __call__(self, k):
+        import oracle
+        cam = [self.cams[k % len(self.cams)]]
+        out = oracle.render(self.sc, cam)
+        _, dimg = oracle.l1_loss(out["image"], [self.target])
+        g = oracle.backward(self.sc, cam, dimg)
+        gg = np.concatenate([g[a].ravel() for a in ("means", "log_scales", "quats", "opa_logits", "sh")])
+        self.t += 1
+        oracle.adam(self.p, gg, self.m, self.v, 1e-3, self.t)
+
+
+def cpu_baseline(n):
+    """The FP64 oracle as it stands timed on full iterations of the workload
+    (1M Gaussians, one 1280x720 view, fwd + bwd + Adam) on this host: one
+    iteration with every core (OpenMP over Gaussians and tiles; the result
+    does not depend on the thread count) and one single-threaded."""
     import oracle
-    cam = [cams[k % len(cams)]]
-    out = oracle.render(scene, cam)
-    tgt = targets if targets is not None else [np.zeros_like(out["image"][0])]
-    _, dimg = oracle.l1_loss(out["image"], tgt)
-    g = oracle.backward(scene, cam, dimg)
-    p = np.concatenate([np.asarray(getattr(scene, a), np.float64).ravel()
-                        for a in ("means", "log_scales", "quats", "opa_logits", "sh")])
-    gg = np.concatenate([g[a].ravel() for a in ("means", "log_scales", "quats", "opa_logits", "sh")])
-    m = np.zeros_like(p)
-    v = np.zeros_like(p)
-    oracle.adam(p, gg, m, v, 1e-3, 1)
-
-
-def cpu_baseline(n, budget_s=20.0, divisor=64, steps=None):
-    """The FP64 oracle as it stands, single-threaded, on 1/divisor of the
-    Gaussians (the first n/divisor of the same scene) over the full 1280x720
-    view; iterations/s scaled by that fraction (the per-iteration work of the
-    renderer grows about linearly with the number of Gaussians)."""
-    from paper_2607_14481_b300 import synth
-    sc = synth.box_scene(n, SEED_SCENE).subset(np.arange(n // divisor))
-    cams = synth.forward_trajectory(N_POSES, SEED_TRAJ)
-    t0 = time.time()
-    done = 0
-    while True:
-        oracle_sample_step(sc, cams, 10 + done)
-        done += 1
-        el = time.time() - t0
-        if (steps is not None and done >= steps) or (steps is None and el >= budget_s):
-            break
-    per = el / done
-    return {"value": 1.0 / (per * divisor), "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} iteration(s) of fwd+bwd+Adam on {n // divisor} of the {n} Gaussians "
-                      f"(1/{divisor}) over full 1280x720 views; value scaled by 1/{divisor}",
-            "seconds": el}
+    step = OracleStep(n)
+    cores = host_cores()
+    before = oracle.get_threads()
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    step(50)
+    t_all = time.perf_counter() - t0
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    step(51)
+    t_one = time.perf_counter() - t0
+    oracle.set_threads(before)
+    return {"value": 1.0 / t_all, "unit": "iters/s", "cores": cores, "threads": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "seconds": t_all,
+            "sample": f"one full iteration (fwd + bwd + Adam) of {n} Gaussians SH3 on one 1280x720 view "
+                      f"(pose 50), FP64, {cores} threads; no scaling",
+            "single_thread": {"value": 1.0 / t_one, "unit": "iters/s", "seconds": t_one, "threads": 1,
+                              "sample": "one full iteration (pose 51), 1 thread"}}
 
 
 def run_reference(args, ws, rank):
+    """The oracle as the reference arm: each step one full iteration of the
+    workload on every host core (rank 0 only)."""
     if rank != 0:
         return None, rank
-    import oracle  # noqa: F401  (builds the oracle if needed)
-    divisor = 64
-    from paper_2607_14481_b300 import synth
-    sc = synth.box_scene(args.n, SEED_SCENE).subset(np.arange(args.n // divisor))
-    cams = synth.forward_trajectory(N_POSES, SEED_TRAJ)
+    import oracle
+    step = OracleStep(args.n)
+    cores = host_cores()
+    oracle.set_threads(cores)
     for i in range(args.warmup):
-        oracle_sample_step(sc, cams, i)
-    t0 = time.time()
+        step(i)
+    t0 = time.perf_counter()
     for i in range(args.steps):
-        oracle_sample_step(sc, cams, args.warmup + i)
-    el = time.time() - t0
-    value = args.steps / (el * divisor)
-    sample = (f"per step: fwd+bwd+Adam of the FP64 oracle on {args.n // divisor} of the {args.n} "
-              f"Gaussians (1/{divisor}) over one full 1280x720 view; value scaled by 1/{divisor}")
+        step(args.warmup + i)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    sample = (f"per step: one full fwd+bwd+Adam iteration of the FP64 oracle on all {args.n} Gaussians over "
+              f"one 1280x720 view, {cores} threads; no scaling")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps * divisor,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"plain single-view training, {args.n} Gaussians SH3, 1280x720, "
-                               f"100-pose forward trajectory, L1 loss", "gaussians": args.n},
-        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": workload_config(args.n, ws),
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "threads": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }, rank
 

@@ -248,7 +248,12 @@ GS_API gs_status gs_splats_carve(void* base, int64_t n, int32_t views, gs_splats
  * Per (view, Gaussian): t = R mu + t_cam (double-single); culled if
  * t_z <= znear; Sigma = Rq diag(e^{2s}) Rq^T; 2D covariance
  * J R Sigma R^T J^T + 0.3 I; conic = its inverse; r = ceil(3 sqrt(lambda_max));
- * tile rect of [m-r, m+r]^2; colour from SH at dir = normalise(mu - centre).
+ * colour from SH at dir = normalise(mu - centre).  Tile rect: per axis the
+ * tiles of [m - h, m + h], where h = min(r, the half-width of the bounding
+ * box of the ellipse A dx^2 + 2B dx dy + C dy^2 <= 2 ln(255 opacity) on which
+ * alpha can reach 1/255, widened by 0.1% + 0.05 px); a splat with
+ * opacity <= 1/255 is culled.  Every pixel that can blend the splat lies in
+ * a tile of its rect, so the image equals that of the [m-r, m+r]^2 rect.
  * Writes every field of `out` for every (view, Gaussian). */
 GS_API gs_status gs_project(const gs_params* params, const float* poses_dev, const gs_camera* cams,
                      int32_t views, const gs_raster_cfg* cfg, gs_splats* out, gs_stream stream);
@@ -386,8 +391,10 @@ GS_API gs_status gs_bin_sort(const gs_splats* splats, const gs_camera* cams, int
                       gs_stream stream);
 
 /* Bytes of the static scratch behind gs_bin_sort_noalloc: enough for, e.g.,
- * n * views <= 65536 items with capacity <= 262144 pairs. */
+ * n * views <= 65536 items with capacity <= 262144 pairs.  The library also
+ * exports the value as the data symbol gs_noalloc_scratch_bytes. */
 #define GS_NOALLOC_SCRATCH_BYTES (8u << 20)
+GS_API extern const uint64_t gs_noalloc_scratch_bytes;
 
 /* gs_bin_sort without a workspace argument and without allocating anything
  * (no cudaMalloc / cudaFree, no allocating library).  The paper has no
@@ -396,16 +403,19 @@ GS_API gs_status gs_bin_sort(const gs_splats* splats, const gs_camera* cams, int
  * latency-critical thread where an allocation may synchronise the device, a
  * caller held to a fixed memory budget).  The workspace is one file-scope
  * device array of GS_NOALLOC_SCRATCH_BYTES inside libgs; its device address
- * is looked up once per device (cudaGetSymbolAddress) on the first call made
- * with that device current.  Results are identical to gs_bin_sort's.
+ * is looked up (cudaGetSymbolAddress, with that device current) on every
+ * call made outside stream capture, so a cudaDeviceReset between calls
+ * leaves no stale address; a call made while its stream is capturing uses
+ * the address found by an earlier call on the device (GS_ERR_INVALID when
+ * there was none).  Results are identical to gs_bin_sort's.
  * Errors: GS_ERR_OOM (with a message) when gs_bin_sort_workspace(n, views,
  * capacity) exceeds the scratch; gs_bin_sort's own checks otherwise.
  * Nothing in the scratch has to start at zero (the call writes every word it
  * reads).  All calls on a device share the one scratch: two calls whose
  * device work overlaps (different streams, or host threads without
  * ordering) race on it and give wrong results, so order them on one stream.
- * Because the first call on a device performs the lookup, make it before
- * any stream capture. */
+ * Because the lookup cannot run under capture, make the first call on a
+ * device before any stream capture. */
 GS_API gs_status gs_bin_sort_noalloc(const gs_splats* splats, const gs_camera* cams, int32_t views,
                                      const gs_raster_cfg* cfg, gs_bins* out, gs_stream stream);
 
@@ -488,11 +498,15 @@ GS_API gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int6
                        const gs_adam_cfg* cfg, int32_t step, gs_stream stream);
 
 /* Work counts of one forward composite (diagnostics for roofline accounting;
- * no image is written): stats_dev[0] = (pixel, splat) pairs tested, up to and
- * including the splat that stops a pixel; [1] = pairs blended; [2] = sum over
- * tiles of the backward's reverse-walk length (list positions up to the last
- * blended splat of any pixel of the tile); [3] = sum over tiles of the list
- * length.  stats_dev: device, 4 uint64, 8-byte aligned, overwritten. */
+ * no image is written): stats_dev[0] = (pixel, splat) pairs the kernel tests
+ * (after its conservative per-warp culling), up to and including the splat
+ * that stops a pixel; [1] = pairs blended; [2] = sum over tiles of the
+ * backward's reverse-walk length (list positions up to the last blended
+ * splat of any pixel of the tile); [3] = sum over tiles of the list length;
+ * [4] = pairs the plain per-pixel loop evaluates: for every pixel, the list
+ * entries of its tile up to and including the splat that stops it (the whole
+ * list when none does).  stats_dev: device, 5 uint64, 8-byte aligned,
+ * overwritten. */
 GS_API gs_status gs_render_stats(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
                                  int32_t views, const gs_raster_cfg* cfg, uint64_t* stats_dev,
                                  gs_stream stream);

@@ -43,8 +43,22 @@ def lib():
         L.orc_pose_adam.argtypes = [C.c_int, d, d, d, d, C.c_double, C.c_double, C.c_double,
                                     C.c_double, C.c_int]
         L.orc_se3_exp.argtypes = [d, d, d]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = C.c_int
+        L.orc_get_threads.argtypes = []
+        L.orc_get_threads.restype = C.c_int
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (OpenMP; results do not depend
+    on it).  Returns the setting in force."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def _p(a: np.ndarray, ct=C.c_double):

@@ -2,7 +2,9 @@
 (the renderer in gs_oracle.cpp, the level-of-detail hierarchy in
 gs_lod_oracle.cpp).
 
-Plain g++, IEEE double arithmetic (no fast-math, no FMA contraction flags).
+Plain g++, IEEE double arithmetic (no fast-math, no FMA contraction flags);
+OpenMP for the loops over Gaussians and tiles (results do not depend on the
+thread count).
 """
 import os
 import subprocess
@@ -18,7 +20,7 @@ def build(force: bool = False) -> str:
             and all(os.path.getmtime(OUT) >= os.path.getmtime(src) for src in SRCS)):
         return OUT
     tmp = OUT + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
            "-Wall", "-Wextra", "-o", tmp, *SRCS]
     subprocess.run(cmd, check=True)
     os.replace(tmp, OUT)

@@ -45,6 +45,10 @@
 #include <cstring>
 #include <vector>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 namespace {
 
 // ----------------------------------------------------------------------------
@@ -373,6 +377,7 @@ int64_t bin_entries(int V, int64_t N, const uint32_t* depth_bits, const int32_t*
 // ----------------------------------------------------------------------------
 struct Blended {
   int64_t i;          // Gaussian id
+  int64_t k;          // position in the tile's list
   double alpha, T;    // alpha_i and transmittance before it
   double e;           // exp(power)
   double dx, dy;      // m - p
@@ -387,16 +392,26 @@ struct ViewOut {
 };
 
 // One view: project, bin (by FP64 depth), composite.
-// `on_pixel(pix, blended list, T_final)` is called after each pixel when
-// `record` is set (the backward consumes the list at once, so memory stays
-// O(list length)).
-struct NoPixel { void operator()(size_t, const std::vector<Blended>&, double) const {} };
+// `on_pixel(tile, list length, pix, blended list, T_final)` is called after
+// each pixel when `record` is set (the backward consumes the list at once, so
+// memory stays O(list length)).
+//
+// Threads (OpenMP): the projection runs over Gaussians and the composite over
+// tiles; every pixel belongs to one tile and every (view, Gaussian) record to
+// one iteration, so outputs do not depend on the thread count.  on_pixel is
+// called by the thread that owns the tile (the caller keeps per-tile state).
+// tiles_out (optional) receives every tile's list, in blend order.
+struct NoPixel {
+  void operator()(size_t, size_t, size_t, const std::vector<Blended>&, double) const {}
+};
 
 template <class S, class F>
 void render_view(const Scene& sc, const Scene* tg, const View<S>& vw, const Cfg& cf,
-                 std::vector<Proj<S>>& proj, ViewOut<S> out, bool record, F&& on_pixel) {
+                 std::vector<Proj<S>>& proj, ViewOut<S> out, bool record, F&& on_pixel,
+                 std::vector<std::vector<int64_t>>* tiles_out = nullptr) {
   const int64_t N = sc.n;
   proj.resize(N);
+#pragma omp parallel for schedule(dynamic, 1024)
   for (int64_t i = 0; i < N; ++i) proj[i] = project_one<S>(sc, tg, i, vw, cf);
 
   // per-tile lists ordered by (depth, id)
@@ -414,12 +429,14 @@ void render_view(const Scene& sc, const Scene* tg, const View<S>& vw, const Cfg&
       for (int tx = p.xlo; tx <= p.xhi; ++tx) tiles[(size_t)ty * vw.TX + tx].push_back(i);
   }
   const double a_min = 1.0 / 255.0, t_min = 1e-4;
-  std::vector<Blended> bl;
 
   const int wx1 = vw.wx0 + vw.ww, wy1 = vw.wy0 + vw.wh;
-  for (int ty = 0; ty < vw.TY; ++ty)
-    for (int tx = 0; tx < vw.TX; ++tx) {
-      const std::vector<int64_t>& lst = tiles[(size_t)ty * vw.TX + tx];
+  const int64_t n_tiles = (int64_t)vw.TX * vw.TY;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t t = 0; t < n_tiles; ++t) {
+      const int ty = (int)(t / vw.TX), tx = (int)(t % vw.TX);
+      std::vector<Blended> bl;
+      const std::vector<int64_t>& lst = tiles[(size_t)t];
       for (int py = std::max(vw.wy0, ty * cf.th); py < std::min(wy1, (ty + 1) * cf.th); ++py)
         for (int px = std::max(vw.wx0, tx * cf.tw); px < std::min(wx1, (tx + 1) * cf.tw); ++px) {
           const double pcx = px + 0.5, pcy = py + 0.5;
@@ -428,7 +445,8 @@ void render_view(const Scene& sc, const Scene* tg, const View<S>& vw, const Cfg&
           uint8_t fl = 0;
           double last_depth = -1.0;
           bl.clear();
-          for (int64_t i : lst) {
+          for (size_t li = 0; li < lst.size(); ++li) {
+            const int64_t i = lst[li];
             const Proj<S>& p = proj[i];
             double mxv = val(p.mx), myv = val(p.my);
             // signed distance of the pixel centre to the support box edge
@@ -458,16 +476,17 @@ void render_view(const Scene& sc, const Scene* tg, const View<S>& vw, const Cfg&
             if (last_depth >= 0.0 && val(p.depth) - last_depth <= cf.m_depth * val(p.depth)) fl |= 1;
             last_depth = val(p.depth);
             for (int ch = 0; ch < 3; ++ch) Cc[ch] += p.rgb[ch] * al * T;
-            if (record) bl.push_back({i, val(al), val(T), val(ex), val(dx), val(dy), clamped});
+            if (record) bl.push_back({i, (int64_t)li, val(al), val(T), val(ex), val(dx), val(dy), clamped});
             T = Tn;
           }
           const size_t pix = (size_t)(py - vw.wy0) * vw.ww + (px - vw.wx0);
           for (int ch = 0; ch < 3; ++ch) out.image[(size_t)ch * vw.ww * vw.wh + pix] = Cc[ch] + T * S(cf.bg[ch]);
           if (out.alpha) out.alpha[pix] = S(1.0) - T;
           if (out.flags) out.flags[pix] = fl;
-          if (record) on_pixel(pix, bl, val(T));
+          if (record) on_pixel((size_t)t, lst.size(), pix, bl, val(T));
         }
-    }
+  }
+  if (tiles_out) tiles_out->swap(tiles);
 }
 
 // Views from [V][12] poses, [V][4] intrinsics, [V][2] sizes and optional
@@ -872,10 +891,16 @@ int orc_backward(int64_t N, int deg, const double* means, const double* lsc, con
     const View<double>& vw = views[v];
     size_t np = (size_t)vw.ww * vw.wh;
     std::vector<double> img(3 * np), al(np);
-    std::vector<Grad2D> g2(N);
-    std::memset(g2.data(), 0, sizeof(Grad2D) * N);
     ViewOut<double> o{img.data(), al.data(), nullptr};
-    auto per_pixel = [&](size_t pix, const std::vector<Blended>& L, double Tfin) {
+    // Per-pixel contributions are summed per tile first (pixels of the tile in
+    // row-major order, each walked back to front), into part[tile][list
+    // position]; the tiles are then added in tile order.  The order of every
+    // sum is fixed by the tile lists alone, so any number of threads gives the
+    // same bits.
+    std::vector<std::vector<Grad2D>> part((size_t)vw.TX * vw.TY);
+    auto per_pixel = [&](size_t tile, size_t list_len, size_t pix, const std::vector<Blended>& L, double Tfin) {
+      std::vector<Grad2D>& P = part[tile];
+      if (P.empty()) P.assign(list_len, Grad2D{0, 0, 0, 0, 0, 0, {0, 0, 0}});
       double gc[3];
       for (int ch = 0; ch < 3; ++ch) gc[ch] = dimage[off_img + ch * np + pix];
       double ga = dalpha ? dalpha[off_px + pix] : 0.0;
@@ -884,7 +909,7 @@ int orc_backward(int64_t N, int deg, const double* means, const double* lsc, con
       for (int k = (int)L.size() - 1; k >= 0; --k) {
         const Blended& b = L[k];
         const Proj<double>& p = pj[b.i];
-        Grad2D& G = g2[b.i];
+        Grad2D& G = P[(size_t)b.k];
         double dal = 0;
         for (int ch = 0; ch < 3; ++ch) {
           G.rgb[ch] += gc[ch] * b.alpha * b.T;
@@ -905,11 +930,31 @@ int orc_backward(int64_t N, int deg, const double* means, const double* lsc, con
         G.my += -(p.C * b.dy + p.B * b.dx) * dpow;
       }
     };
-    render_view<double>(sc, nullptr, vw, cf, pj, o, true, per_pixel);
+    std::vector<std::vector<int64_t>> tiles;
+    render_view<double>(sc, nullptr, vw, cf, pj, o, true, per_pixel, &tiles);
+    std::vector<Grad2D> g2(N);
+    std::memset(g2.data(), 0, sizeof(Grad2D) * N);
+    for (size_t t = 0; t < tiles.size(); ++t) {
+      const std::vector<Grad2D>& P = part[t];
+      for (size_t k = 0; k < P.size(); ++k) {
+        Grad2D& G = g2[tiles[t][k]];
+        const Grad2D& q = P[k];
+        G.mx += q.mx; G.my += q.my; G.A += q.A; G.B += q.B; G.C += q.C; G.opa += q.opa;
+        for (int ch = 0; ch < 3; ++ch) G.rgb[ch] += q.rgb[ch];
+      }
+    }
+    part.clear();
+    // chain rule per Gaussian (independent), pose terms summed in Gaussian order
+    std::vector<double> gp((size_t)6 * N, 0.0);
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t i = 0; i < N; ++i) {
       if (!pj[i].vis) continue;
       project_backward(sc, i, vw, cf, pj[i], g2[i], gmeans + 3 * i, glsc + 3 * i, gquat + 4 * i,
-                       gopl + i, gsh + 3 * nc * i, gpose + 6 * v);
+                       gopl + i, gsh + 3 * nc * i, gp.data() + 6 * i);
+    }
+    for (int64_t i = 0; i < N; ++i) {
+      if (!pj[i].vis) continue;
+      for (int k = 0; k < 6; ++k) gpose[6 * v + k] += gp[6 * i + k];
     }
     off_img += 3 * np;
     off_px += np;
@@ -945,6 +990,7 @@ int orc_adam(int64_t n, double* p, const double* g, double* m, double* v, const 
              double b1, double b2, double eps, int step) {
   if (step < 1) return 1;
   double bc1 = 1.0 - std::pow(b1, step), bc2 = 1.0 - std::pow(b2, step);
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < n; ++k) {
     m[k] = b1 * m[k] + (1.0 - b1) * g[k];
     v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
@@ -981,6 +1027,26 @@ int orc_pose_adam(int V, double* poses, const double* gpose, double* m, double* 
     }
   }
   return 0;
+}
+
+// Threads used by the oracle's parallel loops (OpenMP; 1 = serial).  Results
+// do not depend on it.  orc_get_threads returns the current setting (1 when
+// built without OpenMP).
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+int orc_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 // SE(3) exponential, for tests: xi [6] -> R [9], t [3].

@@ -15,7 +15,6 @@ GS_OK, GS_ERR_INVALID, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NONFINITE
 GS_MAX_VIEWS = 64
 GS_TILE = 16
 GS_SCHED_FWD_LONGEST_FIRST, GS_SCHED_BWD_LONGEST_FIRST = 0x1, 0x2
-GS_NOALLOC_SCRATCH_BYTES = 8 << 20  # static scratch of gs_bin_sort_noalloc
 GS_MAX_ADAM_GROUPS = 64
 GS_BA_MAX_CAMS, GS_BA_MAX_FREE, GS_BA_MAX_OBS = 64, 20, 16
 GS_BA_BAD_OBS, GS_BA_SOLVE_FAILED, GS_BA_DEGENERATE = 0x1, 0x2, 0x4
@@ -119,6 +118,12 @@ class GsSessionPlan(C.Structure):
 
 
 _lib = None
+
+
+def noalloc_scratch_bytes() -> int:
+    """Bytes of gs_bin_sort_noalloc's static scratch, read from the library's
+    data symbol gs_noalloc_scratch_bytes."""
+    return int(C.c_uint64.in_dll(load(), "gs_noalloc_scratch_bytes").value)
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:

@@ -1,7 +1,10 @@
 """torch.autograd adjoint of the rasterizer: forward = gs_project + gs_bin_sort
-+ gs_render_fwd, backward = gs_render_bwd (recomputes per-pixel
-transmittance by replaying the tile's list; only per-Gaussian records and the
-tile lists are kept between the two passes, no per-pixel state).
++ gs_render_fwd, backward = gs_render_bwd in its replay form: per tile the
+forward's list is walked again front to back to recover each pixel's final
+transmittance and last blended splat, then back to front recovering
+T_i = T_{i+1} / (1 - alpha_i).  Between the two passes only the per-Gaussian
+splat records and the tile lists are kept; no per-pixel state (not the image,
+not the transmittance) is stored.
 
 The differentiable inputs are the flat parameter buffer of an Arena (its
 layout is the library's: means4 | scale_opa | quat | planar SH) and a
@@ -30,7 +33,7 @@ class _RenderFn(torch.autograd.Function):
         rast.forward(arena, poses, image, alpha, check=True)
         ctx.arena, ctx.rast, ctx.poses = arena, rast, poses
         ctx.want_alpha = want_alpha
-        ctx.save_for_backward(image)  # selects the single front-to-back backward
+        # nothing per pixel is kept: the backward replays the tile lists
         if want_alpha:
             return image, alpha
         return image, torch.empty(0, device=image.device)
@@ -41,8 +44,8 @@ class _RenderFn(torch.autograd.Function):
         grads = arena.like()
         dpose = torch.zeros((rast.views, 6), dtype=torch.float32, device=dimage.device)
         da = dalpha.contiguous() if (ctx.want_alpha and dalpha is not None) else None
-        (image,) = ctx.saved_tensors
-        rast.backward(arena, poses, dimage.contiguous(), da, grads, dpose, image)
+        # image=None selects the replay backward (recomputed transmittance)
+        rast.backward(arena, poses, dimage.contiguous(), da, grads, dpose, None)
         return grads.buf, dpose, None, None, None, None
 
 

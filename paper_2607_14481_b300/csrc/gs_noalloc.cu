@@ -28,29 +28,45 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per
-// device (the first call on a device does this lookup).
-gs_status scratch_address(void** out) {
+// Device address of the scratch on the current device.  Outside stream
+// capture it is looked up on every call (cheap), so a device reset or a
+// re-created context never leaves a stale address behind; under capture the
+// address cached by an earlier call on this device is used (the lookup may
+// load the module, which must not happen inside a capture).
+gs_status scratch_address(cudaStream_t stream, void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return gs::check_launch("gs_bin_sort_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices)
     return gs::fail(GS_ERR_INVALID, "gs_bin_sort_noalloc: device %d unsupported", dev);
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return gs::fail(GS_ERR_CUDA, "gs_bin_sort_noalloc: cudaGetSymbolAddress failed: %s",
-                      cudaGetErrorString(e));
-    }
-    g_scratch_ptr[dev] = p;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return gs::fail(GS_ERR_CUDA, "gs_bin_sort_noalloc: cudaStreamIsCapturing failed");
   }
-  *out = g_scratch_ptr[dev];
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (cap != cudaStreamCaptureStatusNone) {
+    if (!g_scratch_ptr[dev])
+      return gs::fail(GS_ERR_INVALID, "gs_bin_sort_noalloc: the first call on a device must come before any "
+                                      "stream capture");
+    *out = g_scratch_ptr[dev];
+    return GS_OK;
+  }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return gs::fail(GS_ERR_CUDA, "gs_bin_sort_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+  }
+  g_scratch_ptr[dev] = p;
+  *out = p;
   return GS_OK;
 }
 
 }  // namespace
+
+// The scratch size as a data symbol, so that bindings read it from the library
+// instead of repeating the constant.
+extern "C" GS_API const uint64_t gs_noalloc_scratch_bytes = GS_NOALLOC_SCRATCH_BYTES;
 
 // Validation beyond the size check, and the launches, are gs_bin_sort's own:
 // the scratch is handed to it as the workspace.
@@ -66,7 +82,7 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_splats* splats, const gs_camer
                     (long long)splats->n * views, (long long)out->capacity, need,
                     (size_t)GS_NOALLOC_SCRATCH_BYTES);
   void* ws = nullptr;
-  const gs_status st = scratch_address(&ws);
+  const gs_status st = scratch_address((cudaStream_t)stream, &ws);
   if (st != GS_OK) return st;
   return gs_bin_sort(splats, cams, views, cfg, out, ws, (size_t)GS_NOALLOC_SCRATCH_BYTES, stream);
 }

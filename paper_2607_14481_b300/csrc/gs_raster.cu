@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
   float c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
   bool d0 = !tc.in0, d1 = !tc.in1;
   uint32_t n_tested = 0, n_blended = 0;
+  uint32_t stop0 = 0xffffffffu, stop1 = 0xffffffffu;  // list position of the splat that stopped the pixel
   int last = -1;
   if (COUNT && threadIdx.x == 0) s_last = -1;
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
           const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
           if (Tn < kTransMin) {
             d0 = true;
+            if (COUNT) stop0 = start + k;
           } else {
             const float4 col = s_rgb[k];
             const float w = e.alpha * T0;
@@ -276,6 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
           const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
           if (Tn < kTransMin) {
             d1 = true;
+            if (COUNT) stop1 = start + k;
           } else {
             const float4 col = s_rgb[k];
             const float w = e.alpha * T1;
@@ -292,14 +295,21 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const 
     __syncthreads();
     if (last >= 0) atomicMax(&s_last, last);
     unsigned long long t = n_tested, b = n_blended;
+    // pairs the plain per-pixel loop evaluates: every list entry up to and
+    // including the one that stops the pixel (the whole list otherwise)
+    const uint32_t len = rg.y - rg.x;
+    unsigned long long ev = (tc.in0 ? (stop0 != 0xffffffffu ? stop0 - rg.x + 1u : len) : 0u) +
+                            (tc.in1 ? (stop1 != 0xffffffffu ? stop1 - rg.x + 1u : len) : 0u);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       t += __shfl_xor_sync(0xffffffffu, t, o);
       b += __shfl_xor_sync(0xffffffffu, b, o);
+      ev += __shfl_xor_sync(0xffffffffu, ev, o);
     }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&stats[0], t);
       atomicAdd(&stats[1], b);
+      atomicAdd(&stats[4], ev);
     }
     __syncthreads();
     if (threadIdx.x == 0 && s_last >= 0) atomicAdd(&stats[2], (unsigned long long)(s_last + 1 - (int)rg.x));
@@ -768,7 +778,7 @@ gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const Vi
   a.bg[0] = a.bg[1] = a.bg[2] = 0.f;
   a.image = nullptr;
   a.alpha = nullptr;
-  if (cudaMemsetAsync(stats, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return check_launch("stats");
+  if (cudaMemsetAsync(stats, 0, 5 * sizeof(unsigned long long), s) != cudaSuccess) return check_launch("stats");
   if (vt.total_tiles == 0) return GS_OK;
   k_render_fwd<true, 128><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, stats);
   return check_launch("k_render_fwd<count>");

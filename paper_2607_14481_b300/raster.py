@@ -285,13 +285,16 @@ class Rasterizer:
 
     def render_stats(self) -> dict:
         """Work counts of the current tile lists (synchronises): pairs tested
-        and blended by the forward, the backward's walk length, list length."""
-        st = torch.zeros(4, dtype=torch.int64, device=self.device)
+        (after the kernels' warp culling) and blended by the forward, the
+        backward's walk length, list length, and the pairs the plain per-pixel
+        loop evaluates (up to each pixel's stop)."""
+        st = torch.zeros(5, dtype=torch.int64, device=self.device)
         b = self.bins_struct()
         _lib.check(self.L.gs_render_stats(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
                                           C.byref(self.cfg), _p(st), _stream()), "gs_render_stats")
         v = st.cpu().numpy()
-        return {"tested": int(v[0]), "blended": int(v[1]), "walk": int(v[2]), "listed": int(v[3])}
+        return {"tested": int(v[0]), "blended": int(v[1]), "walk": int(v[2]), "listed": int(v[3]),
+                "evaluated": int(v[4])}
 
     def read_counts(self) -> np.ndarray:
         return self.counts.cpu().numpy().view(np.uint32).copy()

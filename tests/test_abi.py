@@ -32,6 +32,13 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
+def test_noalloc_scratch_size_is_exported(lib):
+    # the binding reads the scratch size from the library's data symbol
+    text = open(os.path.join(ROOT, "include", "gs.h")).read()
+    m = re.search(r"#define GS_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", text)
+    assert m and _lib.noalloc_scratch_bytes() == int(m.group(1)) << int(m.group(2))
+
+
 def test_version_and_arch(lib):
     assert lib.gs_version() == 1
     assert lib.gs_built_arch() == 1030

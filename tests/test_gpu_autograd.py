@@ -1,6 +1,7 @@
 """The torch.autograd adjoint (differentiation check): 256 Gaussians, SH
 degree 3, three 64x64 views, mean-squared-error loss written in torch on the
-rendered image.  autograd gradients of every parameter group and of the camera
+rendered image; the adjoint keeps no per-pixel state and takes the replay
+backward (transmittance recomputed in reverse).  autograd gradients of every parameter group and of the camera
 poses must match the FP64 oracle's analytic gradient (itself pinned to dual
 numbers and central finite differences) within 1e-3 relative, and a sample of
 coordinates is checked directly against central differences (step 1e-4) of the
@@ -30,6 +31,8 @@ def test_autograd_matches_oracle_and_finite_differences(cuda_device):
     twist = torch.zeros((len(cams), 6), dtype=torch.float32, device=cuda_device, requires_grad=True)
     rast = raster.Rasterizer(sc.n, sc.sh_degree, cams, device=cuda_device)
     img, _ = autograd.render(arena, rast, poses, twist)
+    # nothing per pixel is kept for the backward (it replays the tile lists)
+    assert len(img.grad_fn.saved_tensors) == 0
     views = rast.split(img, 3)
     n = sum(t.size for t in targets)
     loss = 0.0

@@ -35,7 +35,7 @@ def test_noalloc_sort_equals_workspace_sort_twice(cuda_device, case):
     arena = raster.Arena.from_scene(sc, dev)
     poses = raster.poses_tensor(cams, dev)
     r = raster.Rasterizer(sc.n, sc.sh_degree, cams, capacity=65536, device=dev, keep_keys=True)
-    assert r.L.gs_bin_sort_workspace(sc.n, len(cams), 65536) <= _lib.GS_NOALLOC_SCRATCH_BYTES
+    assert r.L.gs_bin_sort_workspace(sc.n, len(cams), 65536) <= _lib.noalloc_scratch_bytes()
     r.project(arena, poses)
 
     _poison(r)
@@ -65,7 +65,7 @@ def test_noalloc_sort_rejects_oversize(cuda_device):
     cams = synth.plain_small()[1]
     r = raster.Rasterizer(sc.n, sc.sh_degree, cams, capacity=1_000_000, device=dev)
     need = r.L.gs_bin_sort_workspace(sc.n, 1, 1_000_000)
-    assert need > _lib.GS_NOALLOC_SCRATCH_BYTES
+    assert need > _lib.noalloc_scratch_bytes()
     arena = raster.Arena.from_scene(sc, dev)
     r.project(arena, raster.poses_tensor(cams, dev))
     with pytest.raises(_lib.GsError) as ei:
