@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--stream-max", type=int, default=5_000_000)
     ap.add_argument("--no-ba", action="store_true")
@@ -247,7 +248,8 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-STAGES = ("project", "bin_sort", "render_fwd", "loss", "render_bwd_pixels", "render_bwd_gaussians", "adam")
+STAGES = ("project", "bin_sort", "render_fused", "render_bwd_gaussians", "adam")
+STAGES_UNFUSED = ("project", "bin_sort", "render_fwd", "loss", "render_bwd_pixels", "render_bwd_gaussians", "adam")
 
 
 class Workload:
@@ -257,7 +259,7 @@ class Workload:
     one captured CUDA graph per pose.  batched: all views of `cams` in every
     iteration (one Adam step), one captured graph."""
 
-    def __init__(self, n, device, cams, batched, rank=0, use_graphs=True):
+    def __init__(self, n, device, cams, batched, rank=0, use_graphs=True, fused=True):
         import torch
         from paper_2607_14481_b300 import raster, synth, train
         self.torch, self.raster = torch, raster
@@ -291,18 +293,36 @@ class Workload:
             self.rast.forward(self.arena, self.poses[sl], self.rast.new_image(), None, check=True)
             kmax = max(kmax, int(self.rast.read_counts()[1]))
         del pert
-        self.rast.set_capacity(int(kmax * 1.3) + 4096)  # fixed: no host synchronisation per step
-        self.kmax = kmax
-        # blend schedule from the autotuner, on the middle view group
+        self.fused = fused
         k = len(groups) // 2
         sl = slice(0, P) if batched else slice(k, k + 1)
-        self.rast.set_cameras(groups[k])
-        timg = self.rast.new_image()
-        tdimg = self.rast.new_image()
-        self.rast.forward(self.arena, self.poses[sl], timg, None, check=True)
-        self.loss(timg, self.targets[k], tdimg, 0)
-        self.tuning = self.rast.autotune(timg, tdimg, reps=3)
-        del timg, tdimg
+        timg = self.rast.new_image() if batched else torch.empty(3 * max(self.view_pixels), device=device)
+        if fused:
+            # tile shape, splats per batch and work order of the fused pass, on
+            # the middle view group; then the pair capacity for that tile shape
+            self.rast.set_capacity(int(kmax * 1.5) + 4096)
+            self.rast.set_cameras(groups[k])
+            self.tuning = self.rast.autotune_fused(self.arena, self.poses[sl], self.targets[k], 0,
+                                                   timg[:3 * self.view_pixels[k]], self.loss.loss, reps=3)
+            kmax = 0
+            for j, g in enumerate(groups):
+                self.rast.set_cameras(g)
+                slj = slice(0, P) if batched else slice(j, j + 1)
+                self.rast.forward(self.arena, self.poses[slj], timg[:3 * self.view_pixels[j]], None, check=True)
+                kmax = max(kmax, int(self.rast.read_counts()[1]))
+            self.rast.set_capacity(int(kmax * 1.3) + 4096)  # fixed: no host synchronisation per step
+        else:
+            self.rast.set_capacity(int(kmax * 1.3) + 4096)
+            # blend schedule of the separate kernels, on the middle view group
+            self.rast.set_cameras(groups[k])
+            ti = self.rast.new_image()
+            tdimg = self.rast.new_image()
+            self.rast.forward(self.arena, self.poses[sl], ti, None, check=True)
+            self.loss(ti, self.targets[k], tdimg, 0)
+            self.tuning = self.rast.autotune(ti, tdimg, reps=3)
+            del ti, tdimg
+        self.kmax = kmax
+        del timg
         img = self.rast.new_image() if batched else torch.empty(3 * max(self.view_pixels), device=device)
         dimg = torch.empty_like(img)
         self.steps = []
@@ -313,7 +333,7 @@ class Workload:
                 self.arena, self.grads, self.m, self.v, self.groups, self.rast, self.poses[sl], self.targets[k],
                 self.step_dev, pose_m=self.pose_m[sl], pose_v=self.pose_v[sl], pose_steps=self.pose_steps[sl],
                 pose_lr=1e-4, loss_kind=0, status=self.status, image=img[:3 * px], dimage=dimg[:3 * px],
-                loss=self.loss, cams=g))
+                loss=self.loss, cams=g, fused=fused))
         if use_graphs:
             self.pool = torch.cuda.graph_pool_handle()
             for st in self.steps:
@@ -349,23 +369,31 @@ class Workload:
         self.i += 1
         r = st.rast
         r.set_cameras(st.cams)
-        ev[0].record()
+        e = iter(ev)
+        next(e).record()
         r.project(st.arena, st.poses)
-        ev[1].record()
+        next(e).record()
         r.bin_sort()
-        ev[2].record()
-        r.render_fwd(st.img, None)
-        ev[3].record()
-        st.loss(st.img, st.targets, st.dimg, st.kind)
-        ev[4].record()
-        r.backward_pixels(st.dimg, None, st.img)
-        ev[5].record()
+        next(e).record()
+        if self.fused:
+            r.fused(st.targets, st.kind, st.img, None, st.loss.loss)
+            next(e).record()
+        else:
+            r.render_fwd(st.img, None)
+            next(e).record()
+            st.loss(st.img, st.targets, st.dimg, st.kind)
+            next(e).record()
+            r.backward_pixels(st.dimg, None, st.img)
+            next(e).record()
         r.backward_gaussians(st.arena, st.poses, st.grads, st.dpose)
-        ev[6].record()
+        next(e).record()
         self.raster.adam_step(st.arena, st.grads, st.m, st.v, 0, st.groups, status=st.status, pose=st.poses,
                               dpose=st.dpose, pose_m=st.pose_m, pose_v=st.pose_v, pose_lr=st.pose_lr,
                               step_dev=st.step_dev, pose_steps_dev=st.pose_steps)
-        ev[7].record()
+        next(e).record()
+
+    def stages(self):
+        return STAGES if self.fused else STAGES_UNFUSED
 
     def check_device_status(self):
         cnt = self.rast.read_counts()
@@ -431,7 +459,8 @@ def stage_times(wl, K):
     iterations over poses spread along the trajectory, and the blend work
     counts of each iteration's tile lists (their means)."""
     import torch
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)]
+    names = wl.stages()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(K)]
     counts = []
     seq = wl.sequence(K)
     torch.cuda.nvtx.range_push("eager")
@@ -441,7 +470,7 @@ def stage_times(wl, K):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = {s: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K)]))
-          for j, s in enumerate(STAGES)}
+          for j, s in enumerate(names)}
     work = {k: float(np.mean([c[k] for c in counts])) for k in counts[0]}
     return ms, work
 
@@ -504,10 +533,27 @@ def run_ours(args, ws, rank, local):
     roof = roofline(wl, stage_ms, work, peaks, sm_count(device), workload_key=traffic_key(args.n))
     poses_timed = wl.sequence(K)
     plain_pixels = wl.pixels_per_iter
-    n_launch = launches_per_step(1, wl.rast.num_tiles, bool(wl.tuning["schedule"] & 3))
+    n_launch = launches_per_step(1, wl.rast.num_tiles, bool(wl.tuning["schedule"] & 7))
     plain_tuning = wl.tuning
     del wl
     torch.cuda.empty_cache()
+
+    # ---- the same plain step with the three separate blend launches
+    # (composite, loss, per-pixel backward) instead of the fused pass
+    unfused = None
+    if not args.no_unfused:
+        wu = Workload(args.n, device, synth.forward_trajectory(N_POSES, SEED_TRAJ), batched=False, rank=rank,
+                      fused=False)
+        for _ in range(max(3, args.warmup)):
+            wu.step()
+        torch.cuda.synchronize()
+        eu = timed_loop(wu, K, ws)
+        wu.check_device_status()
+        su, _ = stage_times(wu, min(K, 10))
+        unfused = {"value": ws * K / eu, "unit": "iters/s", "ms_per_step": 1e3 * eu / K, "stage_ms": su,
+                   "fused_speedup": value / (ws * K / eu), "blend_schedule": wu.tuning}
+        del wu
+        torch.cuda.empty_cache()
 
     # ---- batched: 16 views of uneven size per iteration (one Adam step), at
     # the headline's Gaussian count and at the batched workload's 2M
@@ -545,6 +591,7 @@ def run_ours(args, ws, rank, local):
         "blend_schedule": plain_tuning,
         "mpix_per_s": value * plain_pixels / 1e6,
         "stage_ms": stage_ms,
+        "unfused": unfused,
         "e2e": e2e,
         "roofline": roof,
         "batched": batched,
@@ -827,16 +874,18 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
                         "3-level LoD (8-child moment merge, tau = 1 px) for renders, 80 GB HBM budget"}
 
 
-def launches_per_step(views, num_tiles, tile_order=False):
+def launches_per_step(views, num_tiles, tile_order=False, fused=True):
     """Kernels one training step launches (memsets excluded): projection 1;
     binning 11 (counts, pair-offset scan 3, status, place, tile scan 3,
-    keys, tile sort); composite 1; loss 2; per-pixel backward 1;
-    per-Gaussian backward 5 (pair sums, projection, SH, pose chunks and
-    total); Adam 3 (parameters, poses, step counter); with a longest-first
-    schedule the binning adds 2 (tile order)."""
+    keys, tile sort); the fused composite + loss + per-pixel backward 1 (or,
+    unfused, composite 1, loss 2, per-pixel backward 1); per-Gaussian
+    backward 5 (pair sums, projection, SH, pose chunks and total); Adam 3
+    (parameters, poses, step counter); with a longest-first schedule the
+    binning adds 2 (tile order)."""
     scan = 3
     bin_sort = 1 + scan + 1 + 1 + scan + 1 + 1 + (2 if tile_order else 0)
-    return 1 + bin_sort + 1 + 2 + 1 + 5 + 3
+    blend = 1 if fused else 1 + 2 + 1
+    return 1 + bin_sort + blend + 5 + 3
 
 
 def load_peaks():
@@ -939,14 +988,21 @@ def roofline(wl, stage_ms, work, peaks, sms, workload_key=None):
     }
     table = {}
     for k, amount in hbm.items():
+        if k not in stage_ms:
+            continue
         t = stage_ms[k] / 1e3
         ach = amount / t / 1e9
         table[k] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "algorithmic": amount}
     table["bin_sort"]["radix_passes"] = passes
-    table["render_fwd"] = alu_roofline(E, OPS_FWD_FP32, OPS_FWD_MUFU, stage_ms["render_fwd"] / 1e3, sms, clk)
-    table["render_bwd_pixels"] = alu_roofline(E, OPS_BWD_FP32, OPS_BWD_MUFU, stage_ms["render_bwd_pixels"] / 1e3,
-                                              sms, clk)
+    if "render_fused" in stage_ms:
+        # composite + loss + backward: both traversals' work per evaluated pair
+        table["render_fused"] = alu_roofline(E, OPS_FWD_FP32 + OPS_BWD_FP32, OPS_FWD_MUFU + OPS_BWD_MUFU,
+                                             stage_ms["render_fused"] / 1e3, sms, clk)
+    else:
+        table["render_fwd"] = alu_roofline(E, OPS_FWD_FP32, OPS_FWD_MUFU, stage_ms["render_fwd"] / 1e3, sms, clk)
+        table["render_bwd_pixels"] = alu_roofline(E, OPS_BWD_FP32, OPS_BWD_MUFU,
+                                                  stage_ms["render_bwd_pixels"] / 1e3, sms, clk)
     dom = max(table, key=lambda k: stage_ms[k])
     out = dict(table[dom])
     tr, tr_note = load_traffic(dom, workload_key) if workload_key else (None, "no workload key")

@@ -8,8 +8,11 @@
  *
  *   gs_project     EWA projection + SH colour of every (view, Gaussian)
  *   gs_bin_sort    per-tile duplication and (tile, depth) sort, tile ranges
- *   gs_render_fwd  front-to-back alpha compositing per 16x16 tile
+ *   gs_render_fwd  front-to-back alpha compositing per tile
  *   gs_render_bwd  analytic backward to all parameters and the camera poses
+ *   gs_render_fused  composite + image loss + per-pixel backward of a
+ *                  training step in one persistent launch over all views'
+ *                  tiles (then gs_render_bwd_gaussians)
  *   gs_adam_step   fused Adam over the parameter arena (+ optional pose step)
  *
  * The primitive (Sec. 7: position, opacity, rotation, scale, SH coefficients)
@@ -70,7 +73,7 @@ typedef int gs_status;
 #define GS_ERR_BUSY 6
 
 #define GS_MAX_VIEWS 64   /* views per call */
-#define GS_TILE 16        /* tile edge in pixels (16x16 tiles) */
+#define GS_TILE 16        /* default tile edge in pixels (16x16 tiles) */
 
 typedef void* gs_stream;  /* cudaStream_t */
 
@@ -112,11 +115,13 @@ typedef struct {
 } gs_camera;
 
 typedef struct {
-  int32_t tile_w, tile_h; /* must be GS_TILE x GS_TILE */
+  int32_t tile_w, tile_h; /* tile shape in pixels: 16x16, 32x8 or 8x32 (every
+                             shape has 256 pixels; the image does not depend
+                             on it, gradients only through rounding order) */
   float bg[3];            /* background colour behind the last splat */
   float znear;            /* near plane (> 0) */
   int32_t clamp_jacobian; /* 1: guard t_x/t_z, t_y/t_z at +-1.3 (W/2)/fx, (H/2)/fy */
-  uint32_t schedule;      /* GS_SCHED_* bits (0 = defaults); set by gs_autotune_blend */
+  uint32_t schedule;      /* GS_SCHED_* bits (0 = defaults); set by the autotuners */
 } gs_raster_cfg;
 
 /* Schedule of the blend kernels (no effect on any result):
@@ -124,11 +129,17 @@ typedef struct {
  *     backward takes the tiles in gs_bins.tile_order (longest lists first);
  *   GS_SCHED_FWD_BATCH(b): splats staged in shared memory per batch by the
  *     composite, b = 0: 128, 1: 64, 2: 256;
- *   GS_SCHED_BWD_BATCH(b): the same for the single-pass backward, 0: 128, 1: 64. */
+ *   GS_SCHED_BWD_BATCH(b): the same for the single-pass backward, 0: 128, 1: 64;
+ *   GS_SCHED_FUSED_LONGEST_FIRST: gs_render_fused hands out its (view, tile)
+ *     items in gs_bins.tile_order (longest lists of all views first) instead
+ *     of view-major order;
+ *   GS_SCHED_FUSED_BATCH(b): splats per batch of gs_render_fused, 0: 128, 1: 64. */
 #define GS_SCHED_FWD_LONGEST_FIRST 0x1u
 #define GS_SCHED_BWD_LONGEST_FIRST 0x2u
+#define GS_SCHED_FUSED_LONGEST_FIRST 0x4u
 #define GS_SCHED_FWD_BATCH(b) ((uint32_t)(b) << 4)
 #define GS_SCHED_BWD_BATCH(b) ((uint32_t)(b) << 8)
+#define GS_SCHED_FUSED_BATCH(b) ((uint32_t)(b) << 12)
 
 /* Projected splats of V views, device memory, each array [V][n] (view-major):
  *   xy       float4  m = (x_int + x_frac, y_int + y_frac): the pixel-space
@@ -419,7 +430,7 @@ GS_API extern const uint64_t gs_noalloc_scratch_bytes;
 GS_API gs_status gs_bin_sort_noalloc(const gs_splats* splats, const gs_camera* cams, int32_t views,
                                      const gs_raster_cfg* cfg, gs_bins* out, gs_stream stream);
 
-/* Forward compositing, one CTA per 16x16 tile: per pixel, splats in list
+/* Forward compositing, one CTA per tile: per pixel, splats in list
  * order; skip when the centre is outside [m-r, m+r]^2, power > 0 or
  * alpha < 1/255; stop before a splat that would make T < 1e-4;
  * C += rgb alpha T; image = C + T bg.
@@ -470,6 +481,36 @@ GS_API gs_status gs_render_bwd_gaussians(const gs_params* params, const float* p
                                          const gs_bins* bins, const gs_raster_cfg* cfg, gs_grads* grads,
                                          float* dL_dpose, void* ws, size_t ws_bytes, gs_stream stream);
 
+/* Workspace bytes of gs_render_fused: the gs_render_bwd workspace (same
+ * layout at its start, so the same buffer then serves
+ * gs_render_bwd_gaussians) plus a work counter and one float per tile. */
+GS_API size_t gs_render_fused_workspace(int64_t n, int32_t views, int64_t capacity, int64_t num_tiles);
+
+/* The per-pixel half of a training step in one persistent launch (the batched
+ * iteration of the joint optimisation, Sec. 5.2: sampled views rendered,
+ * compared with their images and back-propagated together).  A grid of as
+ * many CTAs as the device holds at once takes (view, tile) items from a
+ * device counter, in view-major order or, with GS_SCHED_FUSED_LONGEST_FIRST,
+ * in gs_bins.tile_order (longest lists of all views first); per item it
+ * composites the tile (as gs_render_fwd), writes image (and alpha when not
+ * NULL), takes the image loss of its pixels against target (loss_kind 0:
+ * L1, mean |image - target|; 1: mean squared error; the mean over all views'
+ * pixels and channels, as gs_image_loss) and runs the single front-to-back
+ * backward of gs_render_bwd_pixels with that loss gradient, the composite's
+ * colour kept in registers.  No per-pixel state is stored besides the image.
+ * The per-pair gradients are left in ws for gs_render_bwd_gaussians (same n,
+ * views, bins, ws).  *loss_dev receives the loss; per tile its terms are
+ * summed in a fixed order and the tiles in tile order (deterministic; equal
+ * to gs_image_loss's value up to summation order).  Items do not wait for
+ * one another (each tile's list is complete when the launch starts).
+ * image, target: device, layout of gs_render_fwd's image; loss_dev: device
+ * float; ws: >= gs_render_fused_workspace(n, views, bins->capacity,
+ * bins->num_tiles) bytes, 256-byte aligned. */
+GS_API gs_status gs_render_fused(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
+                                 int32_t views, const gs_raster_cfg* cfg, const float* target, int32_t loss_kind,
+                                 float* image, float* alpha, float* loss_dev, int64_t n, void* ws, size_t ws_bytes,
+                                 gs_stream stream);
+
 /* Autotuner of the blend schedule: times every composite schedule (tile
  * order natural / longest lists first x 128 / 64 / 256 splats per batch) and
  * every single-pass backward schedule (order x 128 / 64) on the caller's
@@ -486,6 +527,29 @@ GS_API gs_status gs_autotune_blend(const gs_splats* splats, const gs_bins* bins,
                                    int32_t views, gs_raster_cfg* cfg, float* image, const float* dL_dimage,
                                    int64_t n, void* ws, size_t ws_bytes, int32_t reps, float* times_ms,
                                    gs_stream stream);
+
+/* Autotuner of the fused pass (the batched iteration's knobs: tile shape,
+ * splats per shared-memory batch, work order).  For each tile shape (16x16,
+ * 32x8, 8x32) the caller's Gaussians are projected and binned again; each
+ * candidate shape x batch (128, 64) x order (view-major, longest lists first
+ * when bins->tile_order is given) is timed over `reps` runs of gs_project +
+ * gs_bin_sort + gs_render_fused after one warm-up, with CUDA events.  A shape
+ * whose lists exceed bins->capacity, whose tiles exceed ranges_tiles (the
+ * entries bins->ranges and bins->tile_order hold) or whose workspace exceeds
+ * ws_bytes is skipped.  On return cfg holds the fastest tile shape and fused
+ * schedule (other schedule bits unchanged), bins->num_tiles that shape's tile
+ * count, and splats / bins / image / loss the results of that configuration.
+ * times_ms (optional, host, 12 floats): mean time of each candidate in the
+ * order shape (16x16, 32x8, 8x32) x batch (128, 64) x order (view-major,
+ * longest first); NaN where skipped.  bin_ws: the gs_bin_sort workspace; ws:
+ * the gs_render_fused workspace.  Synchronises (bounded waits,
+ * GS_ERR_TIMEOUT): not for use under stream capture.  The image does not
+ * depend on the choice; gradients only through summation order. */
+GS_API gs_status gs_autotune_fused(const gs_params* params, const float* poses_dev, const gs_camera* cams,
+                                   int32_t views, gs_raster_cfg* cfg, gs_splats* splats, gs_bins* bins,
+                                   int64_t ranges_tiles, void* bin_ws, size_t bin_ws_bytes, const float* target,
+                                   int32_t loss_kind, float* image, float* loss_dev, void* ws, size_t ws_bytes,
+                                   int32_t reps, float* times_ms, gs_stream stream);
 
 /* Fused Adam over one flat float arena of n elements (parameters p, gradients
  * g, moments m, v; all device, 16-byte aligned), in one launch for all groups
@@ -538,6 +602,13 @@ GS_API gs_status gs_image_loss(const float* image, const float* target, int64_t 
  * max_inflight); queued requests wait for a free context.  A batch whose tile
  * lists overflow skips its update on the device, grows its pair capacity
  * within the budget and runs again.
+ * Streams: writes of the parameters (train parts, adds, loop closures,
+ * hierarchy builds) run in issue order on the session's stream; each batch
+ * context renders on its own stream.  A render part waits for the writes
+ * issued before it and a write waits for the render parts issued before it,
+ * so every render sees exactly the updates submitted ahead of it, while render
+ * parts run beside one another and beside the forward and backward of a
+ * later train part.  Train parts use gs_render_fused.
  * ------------------------------------------------------------------------ */
 typedef struct gs_session gs_session;
 
@@ -581,6 +652,8 @@ typedef struct {
   double wall_s;             /* since creation */
   uint64_t hbm_in_use, hbm_budget;
   int32_t contexts;
+  int64_t train_beside_render;  /* train parts issued while a render part was in flight: their
+                                   forward and backward ran beside it on the device */
 } gs_stats;
 
 typedef struct {
@@ -651,6 +724,11 @@ GS_API gs_status gs_session_read_params(gs_session* s, float* means4, float* sca
  * back; both drain first.  A resumed session continues bit-identically. */
 GS_API gs_status gs_session_save(gs_session* s, const char* path);
 GS_API gs_status gs_session_load(gs_session* s, const char* path);
+/* Host-side fault injection for tests: the session's next `count` device
+ * allocations fail as if the device were out of memory (no device fault is
+ * made).  A batch whose pair buffers cannot grow finishes its requests with
+ * GS_ERR_OOM and keeps serving at its old capacity. */
+GS_API gs_status gs_session_inject_alloc_failures(gs_session* s, int32_t count);
 /* Drains the queue, stops the threads, frees everything. */
 GS_API gs_status gs_session_destroy(gs_session* s);
 

@@ -14,7 +14,12 @@ LIB_PATH = os.path.join(HERE, "_build", "libgs.so")
 GS_OK, GS_ERR_INVALID, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NONFINITE, GS_ERR_BUSY = range(7)
 GS_MAX_VIEWS = 64
 GS_TILE = 16
-GS_SCHED_FWD_LONGEST_FIRST, GS_SCHED_BWD_LONGEST_FIRST = 0x1, 0x2
+GS_SCHED_FWD_LONGEST_FIRST, GS_SCHED_BWD_LONGEST_FIRST, GS_SCHED_FUSED_LONGEST_FIRST = 0x1, 0x2, 0x4
+TILE_SHAPES = ((16, 16), (32, 8), (8, 32))
+
+
+def GS_SCHED_FUSED_BATCH(b: int) -> int:
+    return int(b) << 12
 GS_MAX_ADAM_GROUPS = 64
 GS_BA_MAX_CAMS, GS_BA_MAX_FREE, GS_BA_MAX_OBS = 64, 20, 16
 GS_BA_BAD_OBS, GS_BA_SOLVE_FAILED, GS_BA_DEGENERATE = 0x1, 0x2, 0x4
@@ -25,10 +30,11 @@ EXPORTED = (
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
     "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
+    "gs_render_fused_workspace", "gs_render_fused", "gs_autotune_fused",
     "gs_ba_workspace_bytes", "gs_ba_solve",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
     "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_keyframe_weights", "gs_session_stats", "gs_session_read_params",
-    "gs_session_save", "gs_session_load", "gs_session_destroy",
+    "gs_session_save", "gs_session_load", "gs_session_inject_alloc_failures", "gs_session_destroy",
 )
 
 GS_REQUEST_RENDER, GS_REQUEST_TRAIN = 0, 1
@@ -109,7 +115,8 @@ class GsStats(C.Structure):
                 ("lod_builds", C.c_int64),
                 ("gaussians", C.c_int64), ("pixels", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
                 ("mean_ms", C.c_double), ("max_ms", C.c_double), ("wall_s", C.c_double),
-                ("hbm_in_use", C.c_uint64), ("hbm_budget", C.c_uint64), ("contexts", C.c_int32)]
+                ("hbm_in_use", C.c_uint64), ("hbm_budget", C.c_uint64), ("contexts", C.c_int32),
+                ("train_beside_render", C.c_int64)]
 
 
 class GsSessionPlan(C.Structure):
@@ -163,6 +170,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_adam_step.argtypes = [vp, vp, vp, vp, i64, P(GsAdamCfg), i32, vp]
     L.gs_autotune_blend.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp, i64, vp, sz,
                                     i32, C.POINTER(C.c_float), vp]
+    L.gs_render_fused_workspace.argtypes = [i64, i32, i64, i64]
+    L.gs_render_fused_workspace.restype = sz
+    L.gs_render_fused.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, i32, vp, vp, vp,
+                                  i64, vp, sz, vp]
+    L.gs_autotune_fused.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsRasterCfg), P(GsSplats), P(GsBins), i64,
+                                    vp, sz, vp, i32, vp, vp, vp, sz, i32, C.POINTER(C.c_float), vp]
     L.gs_sim3_update.argtypes = [P(GsGrads), vp, vp, i32, vp, vp]
     L.gs_keyframe_counts.argtypes = [vp, i64, i32, vp, vp]
     L.gs_lod_nodes.argtypes = [i64]
@@ -197,16 +210,18 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_session_read_params.argtypes = [vp, vp, vp, vp, vp]
     L.gs_session_save.argtypes = [vp, C.c_char_p]
     L.gs_session_load.argtypes = [vp, C.c_char_p]
+    L.gs_session_inject_alloc_failures.argtypes = [vp, i32]
     L.gs_session_destroy.argtypes = [vp]
     for name in ("gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
                  "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_keyframe_weights", "gs_session_stats",
-                 "gs_session_read_params", "gs_session_save", "gs_session_load", "gs_session_destroy"):
+                 "gs_session_read_params", "gs_session_save", "gs_session_load", "gs_session_inject_alloc_failures",
+                 "gs_session_destroy"):
         getattr(L, name).restype = C.c_int
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
                  "gs_render_bwd",
                  "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
                  "gs_render_stats", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
-                 "gs_ba_solve"):
+                 "gs_ba_solve", "gs_render_fused", "gs_autotune_fused"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -29,13 +29,19 @@ gs_status check_launch(const char* what) {
   return GS_OK;
 }
 
-bool make_view_table(const gs_camera* cams, int views, ViewTable* vt) {
+bool make_view_table(const gs_camera* cams, int views, ViewTable* vt, int tw, int th) {
   if (!cams || views <= 0 || views > GS_MAX_VIEWS) {
     fail(GS_ERR_INVALID, "views must be in [1, %d] with a camera array", GS_MAX_VIEWS);
     return false;
   }
+  if (!tile_shape_ok(tw, th)) {
+    fail(GS_ERR_INVALID, "unsupported tile shape %dx%d (16x16, 32x8 or 8x32)", tw, th);
+    return false;
+  }
   std::memset(vt, 0, sizeof(*vt));
   vt->views = views;
+  vt->tw = tw;
+  vt->th = th;
   int64_t tiles = 0, pix = 0;
   for (int v = 0; v < views; ++v) {
     const gs_camera& c = cams[v];
@@ -47,8 +53,8 @@ bool make_view_table(const gs_camera* cams, int views, ViewTable* vt) {
     ViewInfo& vi = vt->v[v];
     vi.fx = c.fx; vi.fy = c.fy; vi.cx = c.cx; vi.cy = c.cy;
     vi.W = c.width; vi.H = c.height;
-    vi.TX = (c.width + kTile - 1) / kTile;
-    vi.TY = (c.height + kTile - 1) / kTile;
+    vi.TX = (c.width + tw - 1) / tw;
+    vi.TY = (c.height + th - 1) / th;
     vi.tile_base = (int32_t)tiles;
     vi.pix_base = pix;
     tiles += (int64_t)vi.TX * vi.TY;
@@ -70,12 +76,13 @@ static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_
 
 static gs_status check_cfg(const gs_raster_cfg* cfg) {
   if (!cfg) return fail(GS_ERR_INVALID, "cfg is NULL");
-  if (cfg->tile_w != kTile || cfg->tile_h != kTile)
-    return fail(GS_ERR_INVALID, "tile must be %dx%d (got %dx%d)", kTile, kTile, cfg->tile_w, cfg->tile_h);
+  if (!tile_shape_ok(cfg->tile_w, cfg->tile_h))
+    return fail(GS_ERR_INVALID, "tile must be 16x16, 32x8 or 8x32 (got %dx%d)", cfg->tile_w, cfg->tile_h);
   if (!(cfg->znear > 0.f)) return fail(GS_ERR_INVALID, "znear must be > 0");
   if ((cfg->schedule & ~kSchedKnown) || ((cfg->schedule >> kSchedFwdBatchShift) & 3u) == 3u ||
       ((cfg->schedule >> kSchedBwdBatchShift) & 3u) > 1u)
     return fail(GS_ERR_INVALID, "unknown schedule 0x%x", cfg->schedule);
+
   return GS_OK;
 }
 
@@ -169,6 +176,7 @@ static size_t splat_layout(int64_t n, int32_t views, char* base, gs_splats* out)
 size_t gs_splats_bytes(int64_t n, int32_t views) { return splat_layout(n, views, nullptr, nullptr); }
 
 gs_status gs_splats_carve(void* base, int64_t n, int32_t views, gs_splats* out) {
+  GS_NVTX("gs_splats_carve");
   if (!base || !out) return fail(GS_ERR_INVALID, "NULL base or out");
   if (n < 0 || views <= 0 || views > GS_MAX_VIEWS) return fail(GS_ERR_INVALID, "bad n or views");
   if (reinterpret_cast<uintptr_t>(base) % 256) return fail(GS_ERR_INVALID, "base must be 256-byte aligned");
@@ -178,11 +186,12 @@ gs_status gs_splats_carve(void* base, int64_t n, int32_t views, gs_splats* out) 
 
 gs_status gs_project(const gs_params* params, const float* poses_dev, const gs_camera* cams,
                      int32_t views, const gs_raster_cfg* cfg, gs_splats* out, gs_stream stream) {
+  GS_NVTX("gs_project");
   gs_status st;
   if ((st = check_params(params)) != GS_OK) return st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
   ViewTable vt;
-  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
   if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
   if ((st = check_splats(out, params->n, views)) != GS_OK) return st;
   return launch_project(*params, poses_dev, vt, *cfg, *out, (cudaStream_t)stream);
@@ -190,6 +199,7 @@ gs_status gs_project(const gs_params* params, const float* poses_dev, const gs_c
 
 gs_status gs_sim3_update(gs_grads* params, const int32_t* kf_dev, const float* sim3_dev, int32_t num_kf,
                          uint32_t* status_dev, gs_stream stream) {
+  GS_NVTX("gs_sim3_update");
   if (!params) return fail(GS_ERR_INVALID, "params is NULL");
   gs_params view{params->means4, params->scale_opa, params->quat, params->sh, params->n, params->sh_degree,
                  params->sh_stride};
@@ -203,6 +213,7 @@ gs_status gs_sim3_update(gs_grads* params, const int32_t* kf_dev, const float* s
 
 gs_status gs_keyframe_counts(const int32_t* kf_dev, int64_t n, int32_t num_kf, uint32_t* counts_dev,
                              gs_stream stream) {
+  GS_NVTX("gs_keyframe_counts");
   if (n < 0 || num_kf < 0) return fail(GS_ERR_INVALID, "n or num_kf < 0");
   if ((n > 0 && !kf_dev) || (num_kf > 0 && !counts_dev)) return fail(GS_ERR_INVALID, "NULL array");
   return launch_keyframe_counts(kf_dev, n, num_kf, counts_dev, (cudaStream_t)stream);
@@ -221,6 +232,7 @@ size_t gs_ba_workspace_bytes(int32_t num_cams, int32_t num_points, int32_t obs_p
 gs_status gs_ba_solve(const gs_ba_problem* prob, float* poses, float* points, float* focal, int32_t iters,
                       double lambda0, double* trace, uint32_t* status, void* ws, size_t ws_bytes,
                       gs_stream stream) {
+  GS_NVTX("gs_ba_solve");
   if (!prob) return fail(GS_ERR_INVALID, "problem is NULL");
   if (!ba_sizes_ok(prob->num_cams, prob->num_points, prob->obs_per_point))
     return fail(GS_ERR_INVALID, "num_cams must be 1..%d, num_points 0..2^23-1, obs_per_point 1..%d",
@@ -249,6 +261,7 @@ size_t gs_lod_build_workspace(int64_t n_leaf) { return lod_build_workspace_bytes
 
 gs_status gs_lod_build(gs_grads* nodes, int64_t n_leaf, int32_t* parent_dev, void* ws, size_t ws_bytes,
                        gs_stream stream) {
+  GS_NVTX("gs_lod_build");
   if (!nodes) return fail(GS_ERR_INVALID, "nodes is NULL");
   gs_params view{nodes->means4, nodes->scale_opa, nodes->quat, nodes->sh, nodes->n, nodes->sh_degree,
                  nodes->sh_stride};
@@ -268,11 +281,12 @@ gs_status gs_lod_build(gs_grads* nodes, int64_t n_leaf, int32_t* parent_dev, voi
 gs_status gs_project_lod(const gs_params* nodes, int64_t n_leaf, const int32_t* parent_dev, float tau,
                          const float* poses_dev, const gs_camera* cams, int32_t views, const gs_raster_cfg* cfg,
                          gs_splats* out, gs_stream stream) {
+  GS_NVTX("gs_project_lod");
   gs_status st;
   if ((st = check_params(nodes)) != GS_OK) return st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
   ViewTable vt;
-  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
   if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
   if (n_leaf < 0 || n_leaf > nodes->n) return fail(GS_ERR_INVALID, "n_leaf out of range");
   if (nodes->n > 0 && !parent_dev) return fail(GS_ERR_INVALID, "parent is NULL");
@@ -288,10 +302,11 @@ size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity) {
 gs_status gs_bin_sort(const gs_splats* splats, const gs_camera* cams, int32_t views,
                       const gs_raster_cfg* cfg, gs_bins* out, void* ws, size_t ws_bytes,
                       gs_stream stream) {
+  GS_NVTX("gs_bin_sort");
   gs_status st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
   ViewTable vt;
-  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
   if (!splats) return fail(GS_ERR_INVALID, "splats is NULL");
   if ((st = check_splats(splats, splats->n, views)) != GS_OK) return st;
   if ((st = check_bins(out, vt, splats->n)) != GS_OK) return st;
@@ -305,10 +320,11 @@ gs_status gs_bin_sort(const gs_splats* splats, const gs_camera* cams, int32_t vi
 gs_status gs_render_fwd(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams,
                         int32_t views, const gs_raster_cfg* cfg, float* image, float* alpha,
                         gs_stream stream) {
+  GS_NVTX("gs_render_fwd");
   gs_status st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
   ViewTable vt;
-  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
   if (!splats) return fail(GS_ERR_INVALID, "splats is NULL");
   if ((st = check_splats(splats, splats->n, views)) != GS_OK) return st;
   if ((st = check_bins(bins, vt, splats->n)) != GS_OK) return st;
@@ -358,10 +374,11 @@ gs_status gs_render_bwd_pixels(const gs_splats* splats, const gs_bins* bins, con
                                int32_t views, const gs_raster_cfg* cfg, const float* dL_dimage,
                                const float* dL_dalpha, const float* image, int64_t n, void* ws,
                                size_t ws_bytes, gs_stream stream) {
+  GS_NVTX("gs_render_bwd_pixels");
   gs_status st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
   ViewTable vt;
-  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
   if ((st = check_splats(splats, n, views)) != GS_OK) return st;
   if ((st = check_bins(bins, vt, n)) != GS_OK) return st;
   if (!dL_dimage) return fail(GS_ERR_INVALID, "dL_dimage is NULL");
@@ -379,11 +396,12 @@ gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_de
                                   int32_t views, const gs_splats* splats, const gs_bins* bins,
                                   const gs_raster_cfg* cfg, gs_grads* grads, float* dL_dpose, void* ws,
                                   size_t ws_bytes, gs_stream stream) {
+  GS_NVTX("gs_render_bwd_gaussians");
   gs_status st;
   if ((st = check_params(params)) != GS_OK) return st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
   ViewTable vt;
-  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
   if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
   if ((st = check_splats(splats, params->n, views)) != GS_OK) return st;
   if ((st = check_bins(bins, vt, params->n)) != GS_OK) return st;
@@ -404,16 +422,57 @@ gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_de
                             dL_dpose, drgb, (cudaStream_t)stream);
 }
 
+static size_t fused_layout(int64_t n, int32_t views, int64_t capacity, int64_t num_tiles, char* base,
+                           uint32_t** queue, float** tile_loss) {
+  size_t off = bwd_layout(n, views, capacity, nullptr, nullptr, nullptr, nullptr);
+  if (queue) *queue = base ? reinterpret_cast<uint32_t*>(base + off) : nullptr;
+  off += 256;
+  if (tile_loss) *tile_loss = base ? reinterpret_cast<float*>(base + off) : nullptr;
+  off += align_up(sizeof(float) * (size_t)std::max<int64_t>(1, num_tiles), 256);
+  return off;
+}
+
+size_t gs_render_fused_workspace(int64_t n, int32_t views, int64_t capacity, int64_t num_tiles) {
+  return fused_layout(n, views, capacity, num_tiles, nullptr, nullptr, nullptr);
+}
+
+gs_status gs_render_fused(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams, int32_t views,
+                          const gs_raster_cfg* cfg, const float* target, int32_t loss_kind, float* image,
+                          float* alpha, float* loss_dev, int64_t n, void* ws, size_t ws_bytes, gs_stream stream) {
+  GS_NVTX("gs_render_fused");
+  gs_status st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
+  if ((st = check_splats(splats, n, views)) != GS_OK) return st;
+  if ((st = check_bins(bins, vt, n)) != GS_OK) return st;
+  if (!target || !image || !loss_dev) return fail(GS_ERR_INVALID, "NULL target, image or loss");
+  if (loss_kind != 0 && loss_kind != 1) return fail(GS_ERR_INVALID, "loss_kind must be 0 (L1) or 1 (MSE)");
+  if ((cfg->schedule & GS_SCHED_FUSED_LONGEST_FIRST) && !bins->tile_order)
+    return fail(GS_ERR_INVALID, "GS_SCHED_FUSED_LONGEST_FIRST needs bins.tile_order");
+  const size_t need = gs_render_fused_workspace(n, views, bins->capacity, bins->num_tiles);
+  if (!ws || ws_bytes < need)
+    return fail(GS_ERR_OOM, "render_fused workspace: need %zu bytes, got %zu", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+  float *partials, *pose_partials, *drgb, *tile_loss;
+  uint32_t* queue;
+  bwd_layout(n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &drgb);
+  fused_layout(n, views, bins->capacity, bins->num_tiles, static_cast<char*>(ws), &queue, &tile_loss);
+  return launch_render_fused(*splats, *bins, vt, *cfg, target, loss_kind, image, alpha, loss_dev, partials,
+                             tile_loss, queue, (cudaStream_t)stream);
+}
+
 gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const gs_camera* cams,
                         int32_t views, const gs_splats* splats, const gs_bins* bins,
                         const gs_raster_cfg* cfg, const float* dL_dimage, const float* dL_dalpha,
                         const float* image, gs_grads* grads, float* dL_dpose, void* ws,
                         size_t ws_bytes, gs_stream stream) {
+  GS_NVTX("gs_render_bwd");
   gs_status st;
   if ((st = check_params(params)) != GS_OK) return st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
   ViewTable vt;
-  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
   if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
   if ((st = check_splats(splats, params->n, views)) != GS_OK) return st;
   if ((st = check_bins(bins, vt, params->n)) != GS_OK) return st;
@@ -440,6 +499,7 @@ gs_status gs_render_bwd(const gs_params* params, const float* poses_dev, const g
 
 gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
                        const gs_adam_cfg* cfg, int32_t step, gs_stream stream) {
+  GS_NVTX("gs_adam_step");
   if (!cfg) return fail(GS_ERR_INVALID, "cfg is NULL");
   if (n < 0) return fail(GS_ERR_INVALID, "n < 0");
   if (step < 1 && !cfg->step_dev) return fail(GS_ERR_INVALID, "step must be >= 1");
@@ -467,10 +527,11 @@ gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
 
 gs_status gs_render_stats(const gs_splats* splats, const gs_bins* bins, const gs_camera* cams, int32_t views,
                           const gs_raster_cfg* cfg, uint64_t* stats_dev, gs_stream stream) {
+  GS_NVTX("gs_render_stats");
   gs_status st;
   if ((st = check_cfg(cfg)) != GS_OK) return st;
   ViewTable vt;
-  if (!make_view_table(cams, views, &vt)) return GS_ERR_INVALID;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
   if (!splats) return fail(GS_ERR_INVALID, "splats is NULL");
   if ((st = check_splats(splats, splats->n, views)) != GS_OK) return st;
   if ((st = check_bins(bins, vt, splats->n)) != GS_OK) return st;
@@ -483,6 +544,7 @@ size_t gs_image_loss_workspace(void) { return loss_workspace_bytes(); }
 
 gs_status gs_image_loss(const float* image, const float* target, int64_t count, int32_t kind,
                         float* dL_dimage, float* loss_dev, void* ws, size_t ws_bytes, gs_stream stream) {
+  GS_NVTX("gs_image_loss");
   if (count <= 0) return fail(GS_ERR_INVALID, "count must be > 0");
   if (!image || !target || !loss_dev) return fail(GS_ERR_INVALID, "NULL image, target or loss");
   if (kind != 0 && kind != 1) return fail(GS_ERR_INVALID, "kind must be 0 (L1) or 1 (MSE)");

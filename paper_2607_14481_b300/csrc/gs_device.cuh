@@ -10,8 +10,8 @@
 
 namespace gs {
 
-constexpr int kTile = GS_TILE;                  // 16x16 pixel tiles
-constexpr int kTilePixels = kTile * kTile;      // one thread per pixel
+constexpr int kTile = GS_TILE;                  // default tile: 16x16 pixels
+constexpr int kTilePixels = kTile * kTile;      // pixels of every supported tile shape (16x16, 32x8, 8x32)
 constexpr float kAlphaMax = 0.99f;              // alpha clamp
 constexpr float kAlphaMin = 1.0f / 255.0f;      // skip threshold
 constexpr float kTransMin = 1e-4f;              // early-stop threshold
@@ -33,7 +33,13 @@ struct ViewTable {
   ViewInfo v[GS_MAX_VIEWS];
   int32_t views;
   int32_t total_tiles;
+  int32_t tw, th;        // tile shape in pixels (TX = ceil(W / tw), TY = ceil(H / th))
 };
+
+// Supported tile shapes: 256 pixels, width 8, 16 or 32.
+inline bool tile_shape_ok(int tw, int th) {
+  return (tw == 16 && th == 16) || (tw == 32 && th == 8) || (tw == 8 && th == 32);
+}
 
 // View owning global tile gt (binary search over tile_base).
 __device__ __forceinline__ int view_of_tile(const ViewTable& vt, int gt) {

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/gs.h"
 #include "gs_device.cuh"
@@ -17,16 +18,27 @@ gs_status check_launch(const char* what);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// NVTX range over a scope (an ABI call or a session stage): visible in a
+// profiler's timeline, a no-op when no tool is attached (NVTX 3 is header-only).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define GS_NVTX(name) ::gs::NvtxRange gs_nvtx_scope_(name)
+
 // Schedule bits of gs_raster_cfg (see gs.h).
 constexpr uint32_t kSchedFwdLongestFirst = GS_SCHED_FWD_LONGEST_FIRST;
 constexpr uint32_t kSchedBwdLongestFirst = GS_SCHED_BWD_LONGEST_FIRST;
 constexpr int kSchedFwdBatchShift = 4;
 constexpr int kSchedBwdBatchShift = 8;
-constexpr uint32_t kSchedKnown = 0x3u | (3u << 4) | (3u << 8);
+constexpr int kSchedFusedBatchShift = 12;
+constexpr uint32_t kSchedKnown = 0x7u | (3u << 4) | (3u << 8) | (1u << 12);
 
-// Fills a ViewTable from host cameras; returns false (with a message) on
-// invalid cameras.
-bool make_view_table(const gs_camera* cams, int views, ViewTable* vt);
+// Fills a ViewTable from host cameras for tiles of tw x th pixels; returns
+// false (with a message) on invalid cameras or an unsupported tile shape.
+bool make_view_table(const gs_camera* cams, int views, ViewTable* vt, int tw = kTile, int th = kTile);
 
 // ---- kernels' host launchers (each enqueues on `s`, returns GS_OK or GS_ERR_CUDA)
 // parent != nullptr: level-of-detail cut (nodes [0, n_leaf) are leaves).
@@ -72,6 +84,12 @@ gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const View
                             const gs_raster_cfg& cfg, float* image, float* alpha, cudaStream_t s);
 gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                               unsigned long long* stats, cudaStream_t s);
+// Persistent fused composite + image loss + single-pass backward (see
+// gs_render_fused); queue: 2 device words, tile_loss: [tiles] device floats.
+gs_status launch_render_fused(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
+                              const gs_raster_cfg& cfg, const float* target, int loss_kind, float* image,
+                              float* alpha, float* loss, float* partials, float* tile_loss, uint32_t* queue,
+                              cudaStream_t s);
 gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
                             const gs_raster_cfg& cfg, const float* dimage, const float* dalpha,
                             const float* image, float* partials, cudaStream_t s);

@@ -72,6 +72,7 @@ extern "C" GS_API const uint64_t gs_noalloc_scratch_bytes = GS_NOALLOC_SCRATCH_B
 // the scratch is handed to it as the workspace.
 extern "C" gs_status gs_bin_sort_noalloc(const gs_splats* splats, const gs_camera* cams, int32_t views,
                                          const gs_raster_cfg* cfg, gs_bins* out, gs_stream stream) {
+  GS_NVTX("gs_bin_sort_noalloc");
   if (!splats || !out) return gs::fail(GS_ERR_INVALID, "gs_bin_sort_noalloc: NULL splats or bins");
   const size_t need = gs_bin_sort_workspace(splats->n, views, out->capacity);
   if (need > (size_t)GS_NOALLOC_SCRATCH_BYTES)

@@ -138,10 +138,12 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
         const float hx = fminf(r, fmaf(sqrtf(k * ca), 1.001f, 0.05f));
         const float hy = fminf(r, fmaf(sqrtf(k * cc), 1.001f, 0.05f));
         const float mxf = mix + mfx, myf = miy + mfy;  // m = mi + frac, frac in [0,1)
-        xlo = max(0, (int)floorf((mxf - hx) * (1.0f / kTile)));
-        xhi = min(vi.TX - 1, (int)floorf((mxf + hx) * (1.0f / kTile)));
-        ylo = max(0, (int)floorf((myf - hy) * (1.0f / kTile)));
-        yhi = min(vi.TY - 1, (int)floorf((myf + hy) * (1.0f / kTile)));
+        // tile edges are powers of two: the scale by their inverse is exact
+        const float itw = 1.0f / (float)vt.tw, ith = 1.0f / (float)vt.th;
+        xlo = max(0, (int)floorf((mxf - hx) * itw));
+        xhi = min(vi.TX - 1, (int)floorf((mxf + hx) * itw));
+        ylo = max(0, (int)floorf((myf - hy) * ith));
+        yhi = min(vi.TY - 1, (int)floorf((myf + hy) * ith));
         vis = xlo <= xhi && ylo <= yhi;
       }
     }

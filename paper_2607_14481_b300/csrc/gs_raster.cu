@@ -24,6 +24,10 @@
 // test is written once (splat_x + splat_alpha) with explicit round-to-nearest
 // intrinsics so that the forward and every backward form take bit-identical
 // decisions.
+#include <algorithm>
+#include <mutex>
+#include <type_traits>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -34,7 +38,18 @@ constexpr int kThreads = kTilePixels / 2;   // two pixels per thread
 constexpr int kWarps = kThreads / 32;
 // Splats staged per batch: a template parameter of the composite (64, 128,
 // 256) and of the single-pass backward (64, 128), chosen by the schedule.
-constexpr int kRowsPerWarp = 32 / kTile * 2;  // 4
+//
+// Tile shapes (a template parameter TW, the tile width; every shape has 256
+// pixels): 16x16, 32x8, 8x32.  Thread t owns column t % TW and rows
+// 2 (t / TW), 2 (t / TW) + 1, so warp w covers the strip of rows
+// [w R, (w + 1) R) with R = 64 / TW rows: 16 x 4, 32 x 2 or 8 x 8 pixels.
+template <int TW>
+struct TileShape {
+  static_assert(TW == 8 || TW == 16 || TW == 32, "tile width 8, 16 or 32");
+  static constexpr int kW = TW;
+  static constexpr int kH = kTilePixels / TW;
+  static constexpr int kRowsPerWarp = 64 / TW;
+};
 
 struct Eval {
   float dx, dy, ex, raw, alpha;  // ex = exp(power), raw = opacity ex, alpha = min(0.99, raw)
@@ -92,24 +107,26 @@ struct TileCoords {
   float wlo, whi;      // the warp's first and last tile row
 };
 
+template <int TW>
 __device__ __forceinline__ TileCoords tile_coords(const ViewTable& vt, int gt) {
+  using S = TileShape<TW>;
   TileCoords c;
   c.v = view_of_tile(vt, gt);
   const ViewInfo& vi = vt.v[c.v];
   const int lt = gt - vi.tile_base;
   c.tx = lt % vi.TX;
   c.ty = lt / vi.TX;
-  c.px = c.tx * kTile + (threadIdx.x % kTile);
-  c.py0 = c.ty * kTile + 2 * (threadIdx.x / kTile);
+  c.px = c.tx * S::kW + (threadIdx.x % S::kW);
+  c.py0 = c.ty * S::kH + 2 * (threadIdx.x / S::kW);
   c.in0 = c.px < vi.W && c.py0 < vi.H;
   c.in1 = c.px < vi.W && c.py0 + 1 < vi.H;
-  c.ox = (float)(c.tx * kTile);
-  c.oy = (float)(c.ty * kTile);
-  c.lx = (float)(threadIdx.x % kTile);
-  c.ly0 = (float)(2 * (threadIdx.x / kTile));
+  c.ox = (float)(c.tx * S::kW);
+  c.oy = (float)(c.ty * S::kH);
+  c.lx = (float)(threadIdx.x % S::kW);
+  c.ly0 = (float)(2 * (threadIdx.x / S::kW));
   c.ly1 = c.ly0 + 1.f;
-  c.wlo = (float)((threadIdx.x >> 5) * kRowsPerWarp);
-  c.whi = c.wlo + (float)(kRowsPerWarp - 1);
+  c.wlo = (float)((threadIdx.x >> 5) * S::kRowsPerWarp);
+  c.whi = c.wlo + (float)(S::kRowsPerWarp - 1);
   return c;
 }
 
@@ -149,21 +166,23 @@ __device__ __forceinline__ float rect_pmax(float a2, float b2, float c2, float d
 }
 
 // Warp culling of a staged splat: bit w is set unless no point of warp w's
-// strip of the tile (rows kRowsPerWarp w .. kRowsPerWarp (w + 1) - 1, columns
-// 0..15, as a continuous rectangle, cut to the support box |dx|, |dy| <= r)
+// strip of the tile (rows R w .. R (w + 1) - 1 with R = 64 / TW, columns
+// 0..TW-1, as a continuous rectangle, cut to the support box |dx|, |dy| <= r)
 // reaches the alpha threshold p >= thr (with a margin of 1e-3 (1 + |thr|)).
 // Conservative: a warp with its bit clear has no pixel that passes the exact
 // per-pixel test, so skipping it changes nothing.
+template <int TW>
 __device__ __forceinline__ uint8_t warp_mask(float cx, float cy, float a2, float b2, float c2, float thr,
                                              float r) {
-  const float xl = fmaxf(0.f, cx - r), xh = fminf((float)(kTile - 1), cx + r);
+  constexpr int R = TileShape<TW>::kRowsPerWarp;
+  const float xl = fmaxf(0.f, cx - r), xh = fminf((float)(TW - 1), cx + r);
   if (!(a2 < 0.f && c2 < 0.f) || xl > xh) return 0u;
   const float lim = thr - 1e-3f * (1.f + fabsf(thr));
   uint8_t m = 0u;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) {
-    const float yl = fmaxf((float)(kRowsPerWarp * w), cy - r);
-    const float yh = fminf((float)(kRowsPerWarp * w + kRowsPerWarp - 1), cy + r);
+    const float yl = fmaxf((float)(R * w), cy - r);
+    const float yh = fminf((float)(R * w + R - 1), cy + r);
     if (yl > yh) continue;
     if (rect_pmax(a2, b2, c2, cx - xh, cx - xl, cy - yh, cy - yl) >= lim) m |= (uint8_t)(1u << w);
   }
@@ -176,6 +195,7 @@ __device__ __forceinline__ uint8_t warp_mask(float cx, float cy, float a2, float
 // (ox, oy).  rows = the tile rows [cy - r - 1, cy + r + 1] the splat can touch
 // (one pixel of margin over the exact test), empty for a null splat.
 // s_co (optional) keeps the unscaled conic and opacity for the backward.
+template <int TW>
 __device__ __forceinline__ void stage_splat(const float4* xy, const float4* conic, const float4* rgb,
                                             const uint32_t* vals, int64_t n, int64_t vbase, uint32_t j,
                                             int t, float ox, float oy, float4* s_geo, float4* s_geo2,
@@ -199,7 +219,7 @@ __device__ __forceinline__ void stage_splat(const float4* xy, const float4* coni
   s_geo2[t] = make_float4(__fmul_rn(-0.5f * kLog2e, co.z), -log2f(255.f * co.w), co.w, col.w);
   s_rgb[t] = col;
   if (s_co) s_co[t] = co;
-  s_mask[t] = col.w < 0.f ? 0u : warp_mask(cx, cy, __fmul_rn(-0.5f * kLog2e, co.x), __fmul_rn(-kLog2e, co.y),
+  s_mask[t] = col.w < 0.f ? 0u : warp_mask<TW>(cx, cy, __fmul_rn(-0.5f * kLog2e, co.x), __fmul_rn(-kLog2e, co.y),
                                              __fmul_rn(-0.5f * kLog2e, co.z), -log2f(255.f * co.w), col.w);
 }
 
@@ -219,78 +239,106 @@ __device__ __forceinline__ void warp_bits(const uint8_t* s_mask, int cnt, int wa
   __syncwarp();
 }
 
-// COUNT = true is the diagnostic instantiation behind gs_render_stats: the
-// same loop, also counting per pixel the splats tested (up to and including
-// the one that stops it) and blended, and per tile the backward's walk length.
-template <bool COUNT, int kBatch>
-__global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const ViewTable vt,
-                                                         unsigned long long* stats) {
-  __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch];
-  __shared__ uint8_t s_mask[kBatch];
-  __shared__ uint32_t s_wb[kWarps][kBatch / 32];
-  __shared__ int s_last;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
-  const TileCoords tc = tile_coords(vt, gt);
-  const ViewInfo& vi = vt.v[tc.v];
-  const uint2 rg = a.ranges[gt];
-  const int64_t vbase = (int64_t)tc.v * a.n;
-  float T0 = 1.f, T1 = 1.f;
-  float c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
-  bool d0 = !tc.in0, d1 = !tc.in1;
+// Counters of the diagnostic instantiation (gs_render_stats).
+struct CountState {
   uint32_t n_tested = 0, n_blended = 0;
   uint32_t stop0 = 0xffffffffu, stop1 = 0xffffffffu;  // list position of the splat that stopped the pixel
-  int last = -1;
-  if (COUNT && threadIdx.x == 0) s_last = -1;
+  int last = -1;                                       // last blended list position
+};
+
+// Front-to-back composite of one tile's list for the thread's two pixels:
+// on return T0/T1 hold the final transmittance and c0/c1 the colour
+// composited (background not added).  Shared arrays: the staging slots of
+// kBatch splats and the calling warp's words of the bit sets.  COUNT = true
+// also counts per pixel the splats tested (up to and including the one that
+// stops it) and blended.
+template <bool COUNT, int kBatch, int TW>
+__device__ __forceinline__ void composite_tile(const FwdArgs& a, const TileCoords& tc, const uint2 rg,
+                                               const int64_t vbase, float4* s_geo, float4* s_geo2, float4* s_rgb,
+                                               uint8_t* s_mask, uint32_t* s_wbw, float& T0, float& T1,
+                                               float (&c0)[3], float (&c1)[3], CountState& cs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T0 = 1.f;
+  T1 = 1.f;
+  float c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
+  bool d0 = !tc.in0, d1 = !tc.in1;
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
     if (__syncthreads_count(d0 && d1) == kThreads) break;
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     for (int t = threadIdx.x; t < cnt; t += kThreads)
-      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + t, t, tc.ox, tc.oy, s_geo, s_geo2,
-                  s_rgb, s_mask, nullptr, COUNT ? nullptr : a.counts);
+      stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + t, t, tc.ox, tc.oy, s_geo, s_geo2,
+                      s_rgb, s_mask, nullptr, COUNT ? nullptr : a.counts);
     __syncthreads();
-    warp_bits<kBatch>(s_mask, cnt, warp, lane, s_wb[warp]);
+    warp_bits<kBatch>(s_mask, cnt, warp, lane, s_wbw);
     for (int q = 0; q * 32 < cnt && !(d0 && d1); ++q) {
-     for (uint32_t bits = s_wb[warp][q]; bits && !(d0 && d1); bits &= bits - 1) {
+     for (uint32_t bits = s_wbw[q]; bits && !(d0 && d1); bits &= bits - 1) {
       const int k = q * 32 + __ffs(bits) - 1;
       const float4 g = s_geo[k], g2 = s_geo2[k];
       const XTerms x = splat_x(g, tc.lx);
       Eval e;
       if (!d0) {
-        if (COUNT) ++n_tested;
+        if (COUNT) ++cs.n_tested;
         if (splat_alpha(x, g, g2, tc.ly0, e)) {
           const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
           if (Tn < kTransMin) {
             d0 = true;
-            if (COUNT) stop0 = start + k;
+            if (COUNT) cs.stop0 = start + k;
           } else {
             const float4 col = s_rgb[k];
             const float w = e.alpha * T0;
             c00 += col.x * w; c01 += col.y * w; c02 += col.z * w;
             T0 = Tn;
-            if (COUNT) { ++n_blended; last = max(last, (int)(start + k)); }
+            if (COUNT) { ++cs.n_blended; cs.last = max(cs.last, (int)(start + k)); }
           }
         }
       }
       if (!d1) {
-        if (COUNT) ++n_tested;
+        if (COUNT) ++cs.n_tested;
         if (splat_alpha(x, g, g2, tc.ly1, e)) {
           const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
           if (Tn < kTransMin) {
             d1 = true;
-            if (COUNT) stop1 = start + k;
+            if (COUNT) cs.stop1 = start + k;
           } else {
             const float4 col = s_rgb[k];
             const float w = e.alpha * T1;
             c10 += col.x * w; c11 += col.y * w; c12 += col.z * w;
             T1 = Tn;
-            if (COUNT) { ++n_blended; last = max(last, (int)(start + k)); }
+            if (COUNT) { ++cs.n_blended; cs.last = max(cs.last, (int)(start + k)); }
           }
         }
       }
      }
     }
   }
+  c0[0] = c00; c0[1] = c01; c0[2] = c02;
+  c1[0] = c10; c1[1] = c11; c1[2] = c12;
+}
+
+// COUNT = true is the diagnostic instantiation behind gs_render_stats: the
+// same loop, also counting per pixel the splats tested (up to and including
+// the one that stops it) and blended, and per tile the backward's walk length.
+template <bool COUNT, int kBatch, int TW>
+__global__ void __launch_bounds__(kThreads) k_render_fwd(const FwdArgs a, const ViewTable vt,
+                                                         unsigned long long* stats) {
+  __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch];
+  __shared__ uint8_t s_mask[kBatch];
+  __shared__ uint32_t s_wb[kWarps][kBatch / 32];
+  __shared__ int s_last;
+  const int warp = threadIdx.x >> 5;
+  const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
+  const TileCoords tc = tile_coords<TW>(vt, gt);
+  const ViewInfo& vi = vt.v[tc.v];
+  const uint2 rg = a.ranges[gt];
+  const int64_t vbase = (int64_t)tc.v * a.n;
+  if (COUNT && threadIdx.x == 0) s_last = -1;
+  float T0, T1, cc0[3], cc1[3];
+  CountState cs;
+  composite_tile<COUNT, kBatch, TW>(a, tc, rg, vbase, s_geo, s_geo2, s_rgb, s_mask, s_wb[warp], T0, T1, cc0, cc1,
+                                    cs);
+  const uint32_t n_tested = cs.n_tested, n_blended = cs.n_blended, stop0 = cs.stop0, stop1 = cs.stop1;
+  const int last = cs.last;
+  const float c00 = cc0[0], c01 = cc0[1], c02 = cc0[2], c10 = cc1[0], c11 = cc1[1], c12 = cc1[2];
   if (COUNT) {
     __syncthreads();
     if (last >= 0) atomicMax(&s_last, last);
@@ -503,6 +551,7 @@ __device__ __forceinline__ void splat_grad_front(const Eval& e, const float4 col
   alpha_grad(e, gc * T - R * rom, d);
 }
 
+template <int TW>
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const ViewTable vt) {
   constexpr int kBatch = kThreads;
   __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
@@ -514,7 +563,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
   __shared__ int s_maxlast;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
-  const TileCoords tc = tile_coords(vt, gt);
+  const TileCoords tc = tile_coords<TW>(vt, gt);
   const ViewInfo& vi = vt.v[tc.v];
   const uint2 rg = a.ranges[gt];
   const int64_t vbase = (int64_t)tc.v * a.n;
@@ -528,7 +577,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
     if (__syncthreads_count(d0 && d1) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
     if (j < rg.y)
-      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
+      stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
                   s_rgb, s_mask, nullptr, nullptr);
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
@@ -583,7 +632,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
     __syncthreads();
     if (threadIdx.x < cnt) {
       const uint32_t j = (uint32_t)(bstart + threadIdx.x);
-      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
+      stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
                   s_rgb, s_mask, s_co, nullptr);
       s_pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
 #pragma unroll
@@ -632,42 +681,34 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
   }
 }
 
-// Single front-to-back backward, for losses on the image alone: the colour
-// behind splat i is the forward's output minus what has been composited up to
-// and including i, so one traversal in the forward's order, with the forward's
-// own decisions (same splat test, same transmittance products, same stop),
-// yields every gradient without a replay and without recovering T by division.
+// Shared arrays of the per-pixel backward: the staged splats (with the
+// unscaled conic), the bit sets, and per staged splat its pair slot and the
+// warps' reduced partials.
 template <int kBatch>
-__global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, const ViewTable vt) {
-  static_assert(kBatch <= kThreads, "one staged splat per thread");
-  __shared__ float4 s_geo[kBatch], s_geo2[kBatch], s_rgb[kBatch], s_co[kBatch];
-  __shared__ uint8_t s_mask[kBatch];
-  __shared__ uint32_t s_wb[kWarps][kBatch / 32];
-  __shared__ uint32_t s_pidx[kBatch];
-  __shared__ float s_red[kBatch][kWarps][kPartialValues];
-  __shared__ uint8_t s_hit[kBatch][kWarps];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
-  const TileCoords tc = tile_coords(vt, gt);
-  const ViewInfo& vi = vt.v[tc.v];
-  const uint2 rg = a.ranges[gt];
-  const int64_t vbase = (int64_t)tc.v * a.n;
+struct BwdSmem {
+  float4 geo[kBatch], geo2[kBatch], rgb[kBatch], co[kBatch];
+  uint8_t mask[kBatch];
+  uint32_t wb[kWarps][kBatch / 32];
+  uint32_t pidx[kBatch];
+  float red[kBatch][kWarps][kPartialValues];
+  uint8_t hit[kBatch][kWarps];
+};
 
-  const int64_t np = (int64_t)vi.W * vi.H;
-  const float* gimg = a.dimage + 3 * vi.pix_base;
-  const float* cimg = a.image + 3 * vi.pix_base;
-  float g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f;
-  float R0 = 0.f, R1 = 0.f;  // g . (colour still to come), per pixel
-  if (tc.in0) {
-    const int64_t pix = (int64_t)tc.py0 * vi.W + tc.px;
-    g00 = gimg[pix]; g01 = gimg[np + pix]; g02 = gimg[2 * np + pix];
-    R0 = g00 * cimg[pix] + g01 * cimg[np + pix] + g02 * cimg[2 * np + pix];
-  }
-  if (tc.in1) {
-    const int64_t pix = (int64_t)(tc.py0 + 1) * vi.W + tc.px;
-    g10 = gimg[pix]; g11 = gimg[np + pix]; g12 = gimg[2 * np + pix];
-    R1 = g10 * cimg[pix] + g11 * cimg[np + pix] + g12 * cimg[2 * np + pix];
-  }
+// Single front-to-back backward pass over one tile's list for the thread's
+// two pixels, with upstream colour gradients g0/g1 and R0/R1 = g . (forward
+// image): the colour behind splat i is the forward's output minus what has
+// been composited up to and including i, so one traversal in the forward's
+// order, with the forward's own decisions (same splat test, same
+// transmittance products, same stop), yields every gradient without a replay
+// and without recovering T by division.  Stores every pair's partials (zeros
+// for pairs no pixel reached).
+template <int kBatch, int TW>
+__device__ __forceinline__ void bwd_front_tile(const BwdArgs& a, const TileCoords& tc, const uint2 rg,
+                                               const int64_t vbase, const float (&gp0)[3], const float (&gp1)[3],
+                                               float R0, float R1, BwdSmem<kBatch>& sm) {
+  static_assert(kBatch <= kThreads, "one staged splat per thread");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float g00 = gp0[0], g01 = gp0[1], g02 = gp0[2], g10 = gp1[0], g11 = gp1[1], g12 = gp1[2];
   float T0 = 1.f, T1 = 1.f;
   bool d0 = !tc.in0, d1 = !tc.in1;
   uint32_t start = rg.x;
@@ -676,17 +717,17 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     if (threadIdx.x < cnt) {
       const uint32_t j = start + threadIdx.x;
-      stage_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, s_geo, s_geo2,
-                  s_rgb, s_mask, s_co, nullptr);
-      s_pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
+      stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, sm.geo, sm.geo2,
+                      sm.rgb, sm.mask, sm.co, nullptr);
+      sm.pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) s_hit[threadIdx.x][w] = 0;
+      for (int w = 0; w < kWarps; ++w) sm.hit[threadIdx.x][w] = 0;
     }
     __syncthreads();
-    warp_bits<kBatch>(s_mask, cnt, warp, lane, s_wb[warp]);
+    warp_bits<kBatch>(sm.mask, cnt, warp, lane, sm.wb[warp]);
     bool live = true;
     for (int q = 0; q * 32 < cnt && live; ++q) {
-     for (uint32_t bits = s_wb[warp][q]; bits; bits &= bits - 1) {  // warp-uniform
+     for (uint32_t bits = sm.wb[warp][q]; bits; bits &= bits - 1) {  // warp-uniform
       if (__all_sync(0xffffffffu, d0 && d1)) {  // the warp's pixels are done
         live = false;
         break;
@@ -696,7 +737,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
 #pragma unroll
       for (int c = 0; c < kPartialValues; ++c) d[c] = 0.f;
       bool contrib = false;
-      const float4 g = s_geo[k], g2 = s_geo2[k];
+      const float4 g = sm.geo[k], g2 = sm.geo2[k];
       const XTerms x = splat_x(g, tc.lx);
       Eval e;
       if (!d0 && splat_alpha(x, g, g2, tc.ly0, e)) {
@@ -704,7 +745,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
         if (Tn < kTransMin) {
           d0 = true;
         } else {
-          splat_grad_front(e, s_rgb[k], g00, g01, g02, T0, R0, d);
+          splat_grad_front(e, sm.rgb[k], g00, g01, g02, T0, R0, d);
           T0 = Tn;
           contrib = true;
         }
@@ -714,7 +755,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
         if (Tn < kTransMin) {
           d1 = true;
         } else {
-          splat_grad_front(e, s_rgb[k], g10, g11, g12, T1, R1, d);
+          splat_grad_front(e, sm.rgb[k], g10, g11, g12, T1, R1, d);
           T1 = Tn;
           contrib = true;
         }
@@ -723,20 +764,188 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, 
         float s8, t8;
         int idx;
         warp_sum9(d, lane, s8, idx, t8);
-        if ((lane & 3) == 0) s_red[k][warp][idx] = s8;
+        if ((lane & 3) == 0) sm.red[k][warp][idx] = s8;
         if (lane == 0) {
-          s_red[k][warp][8] = t8;
-          s_hit[k][warp] = 1;
+          sm.red[k][warp][8] = t8;
+          sm.hit[k][warp] = 1;
         }
       }
      }
     }
     __syncthreads();
-    if (threadIdx.x < cnt)
-      store_pair(a, s_pidx[threadIdx.x], s_red[threadIdx.x], s_hit[threadIdx.x], s_co[threadIdx.x]);
+    if (threadIdx.x < cnt) store_pair(a, sm.pidx[threadIdx.x], sm.red[threadIdx.x], sm.hit[threadIdx.x], sm.co[threadIdx.x]);
   }
   // pairs past the batch where every pixel of the tile had stopped
   for (uint32_t p = start + threadIdx.x; p < rg.y; p += kThreads) zero_pair(a, vbase, p, tc);
+}
+
+// Single front-to-back backward, for losses on the image alone (the forward's
+// image and the loss gradient read from memory).
+template <int kBatch, int TW>
+__global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, const ViewTable vt) {
+  __shared__ BwdSmem<kBatch> sm;
+  const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
+  const TileCoords tc = tile_coords<TW>(vt, gt);
+  const ViewInfo& vi = vt.v[tc.v];
+  const uint2 rg = a.ranges[gt];
+  const int64_t vbase = (int64_t)tc.v * a.n;
+
+  const int64_t np = (int64_t)vi.W * vi.H;
+  const float* gimg = a.dimage + 3 * vi.pix_base;
+  const float* cimg = a.image + 3 * vi.pix_base;
+  float g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f};
+  float R0 = 0.f, R1 = 0.f;  // g . (colour still to come), per pixel
+  if (tc.in0) {
+    const int64_t pix = (int64_t)tc.py0 * vi.W + tc.px;
+    g0[0] = gimg[pix]; g0[1] = gimg[np + pix]; g0[2] = gimg[2 * np + pix];
+    R0 = g0[0] * cimg[pix] + g0[1] * cimg[np + pix] + g0[2] * cimg[2 * np + pix];
+  }
+  if (tc.in1) {
+    const int64_t pix = (int64_t)(tc.py0 + 1) * vi.W + tc.px;
+    g1[0] = gimg[pix]; g1[1] = gimg[np + pix]; g1[2] = gimg[2 * np + pix];
+    R1 = g1[0] * cimg[pix] + g1[1] * cimg[np + pix] + g1[2] * cimg[2 * np + pix];
+  }
+  bwd_front_tile<kBatch, TW>(a, tc, rg, vbase, g0, g1, R0, R1, sm);
+}
+
+// ---------------------------------------------------------------------------
+// The fused per-tile training pass: one persistent launch over every
+// (view, tile) item of all views.  Each CTA takes items from a device counter
+// (one atomicAdd per item, in `order`: longest lists first, or view-major)
+// and for each runs the composite, the image loss of its pixels (L1 or mean
+// squared error against the target, over all views' pixels and channels) and
+// the single front-to-back backward, with the composite's colour held in
+// registers in between (nothing per pixel goes through memory but the image
+// written out).  Items never wait for one another: every tile list is
+// complete when the launch starts, so no CTA spins.  Per tile the loss terms
+// of its pixels are summed in a fixed order; the last CTA to finish (a ticket
+// counter) sums the tiles in tile order, so the loss is deterministic.
+// ---------------------------------------------------------------------------
+struct FusedArgs {
+  FwdArgs f;                // composite: splats, lists, background, image, alpha
+  BwdArgs b;                // backward: splats, lists, pair slots, partials
+  const uint32_t* order;    // item -> global tile (nullptr: item = tile)
+  const float* target;      // [3 * pixels], layout of the image
+  float inv_count;          // 1 / (3 * pixels of all views)
+  float* tile_loss;         // [tiles] loss terms summed per tile
+  uint32_t* queue;          // [0] next item, [1] CTAs finished (zero at launch)
+  float* loss;              // mean loss (one float)
+  int32_t tiles;
+};
+
+template <int kBatch, int TW, int LOSS>
+__global__ void __launch_bounds__(kThreads) k_render_fused(const FusedArgs a, const ViewTable vt) {
+  __shared__ BwdSmem<kBatch> sm;
+  __shared__ int s_item;
+  __shared__ float s_red[kWarps];
+  __shared__ bool s_last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(&a.queue[0], 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= a.tiles) break;
+    const int gt = a.order ? (int)a.order[item] : item;
+    const TileCoords tc = tile_coords<TW>(vt, gt);
+    const ViewInfo& vi = vt.v[tc.v];
+    const uint2 rg = a.f.ranges[gt];
+    const int64_t vbase = (int64_t)tc.v * a.f.n;
+    // 1. composite
+    float T0, T1, cc0[3], cc1[3];
+    CountState cs;
+    composite_tile<false, kBatch, TW>(a.f, tc, rg, vbase, sm.geo, sm.geo2, sm.rgb, sm.mask, sm.wb[warp], T0, T1,
+                                      cc0, cc1, cs);
+    // 2. image, loss terms and dL/dimage per pixel
+    const int64_t np = (int64_t)vi.W * vi.H;
+    float* img = a.f.image + 3 * vi.pix_base;
+    const float* tgt = a.target + 3 * vi.pix_base;
+    // (the same expressions as gs_render_fwd, gs_image_loss and the
+    // single-pass backward's set-up, so the two paths give the same bits)
+    float g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f};
+    float R0 = 0.f, R1 = 0.f, lsum = 0.f;
+    if (tc.in0) {
+      const int64_t pix = (int64_t)tc.py0 * vi.W + tc.px;
+      float out[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        out[c] = cc0[c] + T0 * a.f.bg[c];
+        img[c * np + pix] = out[c];
+        const float d = out[c] - tgt[c * np + pix];
+        if (LOSS == 0) {
+          lsum += fabsf(d);
+          g0[c] = d > 0.f ? a.inv_count : (d < 0.f ? -a.inv_count : 0.f);
+        } else {
+          lsum += d * d;
+          g0[c] = 2.f * d * a.inv_count;
+        }
+      }
+      R0 = g0[0] * out[0] + g0[1] * out[1] + g0[2] * out[2];
+      if (a.f.alpha) a.f.alpha[vi.pix_base + pix] = 1.f - T0;
+    }
+    if (tc.in1) {
+      const int64_t pix = (int64_t)(tc.py0 + 1) * vi.W + tc.px;
+      float out[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        out[c] = cc1[c] + T1 * a.f.bg[c];
+        img[c * np + pix] = out[c];
+        const float d = out[c] - tgt[c * np + pix];
+        if (LOSS == 0) {
+          lsum += fabsf(d);
+          g1[c] = d > 0.f ? a.inv_count : (d < 0.f ? -a.inv_count : 0.f);
+        } else {
+          lsum += d * d;
+          g1[c] = 2.f * d * a.inv_count;
+        }
+      }
+      R1 = g1[0] * out[0] + g1[1] * out[1] + g1[2] * out[2];
+      if (a.f.alpha) a.f.alpha[vi.pix_base + pix] = 1.f - T1;
+    }
+    // the tile's loss terms in a fixed order: lanes by a butterfly, warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) s_red[warp] = lsum;
+    // 3. backward (its first barrier also orders s_red and s_item)
+    bwd_front_tile<kBatch, TW>(a.b, tc, rg, vbase, g0, g1, R0, R1, sm);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t += s_red[w];
+      a.tile_loss[gt] = t;
+    }
+  }
+  // ticket: the last CTA to finish sums the tiles' loss terms in tile order
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&a.queue[1], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  float t = 0.f;
+  for (int i = threadIdx.x; i < a.tiles; i += kThreads) t += __ldcg(&a.tile_loss[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) s_red[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sum = 0.f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) sum += s_red[w];
+    *a.loss = sum * a.inv_count;
+  }
+}
+
+// Calls f(std::integral_constant<int, TW>) for the view table's tile width.
+template <class F>
+void with_tile_width(const ViewTable& vt, F&& f) {
+  switch (vt.tw) {
+    case 8: f(std::integral_constant<int, 8>()); break;
+    case 32: f(std::integral_constant<int, 32>()); break;
+    default: f(std::integral_constant<int, 16>()); break;
+  }
 }
 
 }  // namespace
@@ -756,11 +965,15 @@ gs_status launch_render_fwd(const gs_splats& sp, const gs_bins& bins, const View
   a.image = image;
   a.alpha = alpha;
   if (vt.total_tiles == 0) return GS_OK;
-  switch ((cfg.schedule >> kSchedFwdBatchShift) & 3u) {
-    case 1: k_render_fwd<false, 64><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr); break;
-    case 2: k_render_fwd<false, 256><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr); break;
-    default: k_render_fwd<false, 128><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr); break;
-  }
+  const uint32_t batch = (cfg.schedule >> kSchedFwdBatchShift) & 3u;
+  with_tile_width(vt, [&](auto tw) {
+    constexpr int TW = decltype(tw)::value;
+    switch (batch) {
+      case 1: k_render_fwd<false, 64, TW><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr); break;
+      case 2: k_render_fwd<false, 256, TW><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr); break;
+      default: k_render_fwd<false, 128, TW><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, nullptr); break;
+    }
+  });
   return check_launch("k_render_fwd");
 }
 
@@ -780,15 +993,17 @@ gs_status launch_render_stats(const gs_splats& sp, const gs_bins& bins, const Vi
   a.alpha = nullptr;
   if (cudaMemsetAsync(stats, 0, 5 * sizeof(unsigned long long), s) != cudaSuccess) return check_launch("stats");
   if (vt.total_tiles == 0) return GS_OK;
-  k_render_fwd<true, 128><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, stats);
+  with_tile_width(vt, [&](auto tw) {
+    constexpr int TW = decltype(tw)::value;
+    k_render_fwd<true, 128, TW><<<vt.total_tiles, kThreads, 0, s>>>(a, vt, stats);
+  });
   return check_launch("k_render_fwd<count>");
 }
 
-gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
-                            const gs_raster_cfg& cfg, const float* dimage, const float* dalpha,
-                            const float* image, float* partials, cudaStream_t s) {
+static BwdArgs bwd_args(const gs_splats& sp, const gs_bins& bins, const gs_raster_cfg& cfg, const float* dimage,
+                        const float* dalpha, const float* image, float* partials, bool longest_first) {
   BwdArgs a;
-  a.order = (cfg.schedule & kSchedBwdLongestFirst) ? bins.tile_order : nullptr;
+  a.order = longest_first ? bins.tile_order : nullptr;
   a.xy = reinterpret_cast<const float4*>(sp.xy);
   a.conic = reinterpret_cast<const float4*>(sp.conic);
   a.rgb = reinterpret_cast<const float4*>(sp.rgb);
@@ -804,16 +1019,102 @@ gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const View
   a.dalpha = dalpha;
   a.image = image;
   a.partials = partials;
+  return a;
+}
+
+gs_status launch_render_bwd(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
+                            const gs_raster_cfg& cfg, const float* dimage, const float* dalpha,
+                            const float* image, float* partials, cudaStream_t s) {
+  const BwdArgs a = bwd_args(sp, bins, cfg, dimage, dalpha, image, partials,
+                             (cfg.schedule & kSchedBwdLongestFirst) != 0);
   if (vt.total_tiles == 0) return GS_OK;
   if (image && !dalpha) {
-    if (((cfg.schedule >> kSchedBwdBatchShift) & 3u) == 1)
-      k_render_bwd_front<64><<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
-    else
-      k_render_bwd_front<128><<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
+    const bool b64 = ((cfg.schedule >> kSchedBwdBatchShift) & 3u) == 1;
+    with_tile_width(vt, [&](auto tw) {
+      constexpr int TW = decltype(tw)::value;
+      if (b64)
+        k_render_bwd_front<64, TW><<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
+      else
+        k_render_bwd_front<128, TW><<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
+    });
     return check_launch("k_render_bwd_front");
   }
-  k_render_bwd<<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
+  with_tile_width(vt, [&](auto tw) {
+    constexpr int TW = decltype(tw)::value;
+    k_render_bwd<TW><<<vt.total_tiles, kThreads, 0, s>>>(a, vt);
+  });
   return check_launch("k_render_bwd");
+}
+
+// Resident CTAs of a kernel on the current device (occupancy x SMs), cached
+// per device and kernel: the persistent grid size.
+template <class K>
+int persistent_grid(K kernel, size_t slot) {
+  constexpr int kDev = 64, kSlots = 64;
+  static int cache[kDev][kSlots] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev || slot >= (size_t)kSlots) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev][slot] == 0) {
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess)
+      return 0;
+    cache[dev][slot] = std::max(1, sms * std::max(1, per_sm));
+  }
+  return cache[dev][slot];
+}
+
+gs_status launch_render_fused(const gs_splats& sp, const gs_bins& bins, const ViewTable& vt,
+                              const gs_raster_cfg& cfg, const float* target, int loss_kind, float* image,
+                              float* alpha, float* loss, float* partials, float* tile_loss, uint32_t* queue,
+                              cudaStream_t s) {
+  FusedArgs a;
+  a.f.order = nullptr;
+  a.f.xy = reinterpret_cast<const float4*>(sp.xy);
+  a.f.conic = reinterpret_cast<const float4*>(sp.conic);
+  a.f.rgb = reinterpret_cast<const float4*>(sp.rgb);
+  a.f.vals = bins.vals;
+  a.f.ranges = reinterpret_cast<const uint2*>(bins.ranges);
+  a.f.counts = bins.counts;
+  a.f.n = sp.n;
+  for (int c = 0; c < 3; ++c) a.f.bg[c] = cfg.bg[c];
+  a.f.image = image;
+  a.f.alpha = alpha;
+  a.b = bwd_args(sp, bins, cfg, nullptr, nullptr, nullptr, partials, false);
+  a.order = (cfg.schedule & GS_SCHED_FUSED_LONGEST_FIRST) ? bins.tile_order : nullptr;
+  a.target = target;
+  int64_t pixels = 0;
+  for (int v = 0; v < vt.views; ++v) pixels += (int64_t)vt.v[v].W * vt.v[v].H;
+  a.inv_count = 1.0f / (float)(3 * pixels);
+  a.tile_loss = tile_loss;
+  a.queue = queue;
+  a.loss = loss;
+  a.tiles = vt.total_tiles;
+  if (cudaMemsetAsync(queue, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) return check_launch("fused queue");
+  if (vt.total_tiles == 0) {
+    if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return check_launch("fused loss");
+    return GS_OK;
+  }
+  const bool b64 = ((cfg.schedule >> kSchedFusedBatchShift) & 1u) != 0;
+  bool ok = true;
+  with_tile_width(vt, [&](auto tw) {
+    constexpr int TW = decltype(tw)::value;
+    auto go = [&](auto kernel, size_t slot) {
+      const int g = std::min(persistent_grid(kernel, slot), vt.total_tiles);
+      if (g <= 0) { ok = false; return; }
+      kernel<<<g, kThreads, 0, s>>>(a, vt);
+    };
+    const size_t base = (TW == 8 ? 0 : TW == 16 ? 4 : 8);
+    if (loss_kind == 0) {
+      if (b64) go(k_render_fused<64, TW, 0>, base + 0); else go(k_render_fused<128, TW, 0>, base + 1);
+    } else {
+      if (b64) go(k_render_fused<64, TW, 1>, base + 2); else go(k_render_fused<128, TW, 1>, base + 3);
+    }
+  });
+  if (!ok) return fail(GS_ERR_CUDA, "k_render_fused: occupancy query failed");
+  return check_launch("k_render_fused");
 }
 
 }  // namespace gs

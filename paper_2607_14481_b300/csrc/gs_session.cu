@@ -7,18 +7,27 @@
 //
 // Threads.  gs_session_submit appends to a queue.  A worker thread forms a
 // batch of up to max_batch_views queued requests as soon as a batch context is
-// free and enqueues the batch's whole iteration on the session's stream
-// without waiting for earlier batches: a request that arrives while batches
-// run joins the next batch (continuous batching), and its copies overlap the
-// kernels of the batches ahead of it.  A completion thread waits for each
-// batch's event with a bounded poll, copies rendered images to the callers'
-// buffers and records per-request latency.
+// free and enqueues the batch without waiting for earlier batches: a request
+// that arrives while batches run joins the next batch (continuous batching).
+// A completion thread polls the events of every batch in flight (bounded
+// waits), finishes whichever completes first, copies rendered images to the
+// callers' buffers and records per-request latency.
+//
+// Streams.  Everything that writes the parameters (train parts, adds of
+// Gaussians, loop closures, hierarchy builds) runs in issue order on the
+// session's stream.  Render parts run on their own batch context's stream:
+// a render part first waits for the event of the last write issued before it
+// (it sees every update issued earlier), and a later write waits, on the
+// device, for the render parts issued before it (its Adam step, or the add,
+// does not change what they read).  So render parts run beside one another
+// and beside the forward and backward of a train part issued after them.
 //
 // Within a batch, render views are rasterised first (they see the parameters
-// before this batch's update), then the train views run forward, loss,
-// backward and one fused Adam step over every active Gaussian.  If a batch
-// overflows its pair capacity the Adam step is skipped on the device, the
-// capacity grows (within the budget) and the batch is issued again.
+// before this batch's update), then the train views run the fused forward,
+// loss and per-pixel backward, the per-Gaussian backward and one fused Adam
+// step over every active Gaussian.  If a batch overflows its pair capacity
+// the Adam step is skipped on the device, the capacity grows (within the
+// budget) and the batch is issued again.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -71,7 +80,11 @@ struct Dev {
 // Device and pinned buffers of one batch in flight.
 struct Ctx {
   cudaEvent_t done = nullptr;
-  Dev splat_buf, pair_off, ranges, order, counts, vals, ws_bin, ws_bwd, img, dimg, tgt, loss_ws, loss, poses, dpose;
+  cudaStream_t rs = nullptr;     // stream of the batch's render part
+  cudaEvent_t rdone = nullptr;   // the render part's last work
+  double issued_at = 0.0;
+  bool dead = false;             // lost its pair buffers (allocation failure): never used again
+  Dev splat_buf, pair_off, ranges, order, counts, vals, ws_bin, ws_bwd, img, tgt, loss, poses, dpose;
   float* h_img = nullptr;       // pinned staging of rendered images
   float* h_poses = nullptr;     // pinned poses [2][max views][12]
   uint32_t* h_counts = nullptr; // pinned [8]: counts of the render and train sub-batches
@@ -94,6 +107,9 @@ struct gs_session {
   gs::Dev lod_parent, lod_ws;  // level-of-detail hierarchy (cfg.lod)
   gs::Dev kf_of;               // int32 [max_gaussians]: keyframe that added each Gaussian (-1: none)
   gs::Dev sim3, sim3_status;   // loop-closure corrections [num_kf][8], status word
+  cudaEvent_t mut_done = nullptr;  // the last write of the parameters issued (session stream)
+  int64_t fail_allocs = 0;     // host-side fault injection: device allocations still to fail
+  int64_t train_beside_render = 0;  // train parts issued while a render part was in flight
   int32_t keyframe = -1;       // tag of the Gaussians added next
   bool lod_dirty = true;       // leaves added since the last build
   int64_t lod_builds = 0;
@@ -133,7 +149,8 @@ size_t arena_floats(int64_t cap, int nc) { return (size_t)(12 + 3 * nc) * (size_
 
 int64_t max_pixels(const gs_session_config& c) { return (int64_t)c.max_width * c.max_height; }
 int64_t max_tiles(const gs_session_config& c) {
-  return (int64_t)((c.max_width + kTile - 1) / kTile) * ((c.max_height + kTile - 1) / kTile);
+  const int tw = c.raster.tile_w, th = c.raster.tile_h;
+  return (int64_t)((c.max_width + tw - 1) / tw) * ((c.max_height + th - 1) / th);
 }
 
 // Device bytes of one batch context at a given pair capacity.
@@ -148,11 +165,9 @@ size_t ctx_device_bytes(const gs_session_config& c, int64_t cap_n, int64_t pair_
   add(32);                                        // counts of both sub-batches
   add(4 * (size_t)pair_cap);                      // vals
   add(bin_sort_workspace_bytes(cap_n * V, pair_cap));
-  add(render_bwd_ws_bytes(cap_n, (int32_t)V, pair_cap));
+  add(gs_render_fused_workspace(cap_n, (int32_t)V, pair_cap, max_tiles(c) * V));
   add(12 * (size_t)max_pixels(c) * V);            // images
-  add(12 * (size_t)max_pixels(c) * V);            // loss gradient
   add(12 * (size_t)max_pixels(c) * V);            // targets
-  add(loss_workspace_bytes());
   add(8);                                         // loss
   add(48 * 2 * (size_t)V);                        // poses
   add(24 * (size_t)V);                            // pose gradient
@@ -178,8 +193,14 @@ int64_t initial_pair_cap(const gs_session_config& c) {
   return std::max<int64_t>(4096, (int64_t)(f * (double)c.max_gaussians));
 }
 
-gs_status dalloc(Dev& d, size_t bytes, size_t& counter) {
+gs_status dalloc(Dev& d, size_t bytes, size_t& counter, int64_t* fail_next = nullptr) {
   d.bytes = align_up(std::max<size_t>(bytes, 16), 256);
+  if (fail_next && *fail_next > 0) {  // injected failure (tests): as if the device were out of memory
+    --*fail_next;
+    d.p = nullptr;
+    d.bytes = 0;
+    return fail(GS_ERR_OOM, "session: device allocation of %zu bytes failed (injected)", align_up(bytes, 256));
+  }
   if (cudaMalloc(&d.p, d.bytes) != cudaSuccess) {
     cudaGetLastError();
     d.p = nullptr;
@@ -204,37 +225,47 @@ void free_pair_buffers(gs_session* S, Ctx& c) {
   dfree(c.ws_bwd, S->in_use);
 }
 
+size_t fused_ws_bytes(gs_session* S, int64_t pair_cap) {
+  const int64_t V = S->cfg.max_batch_views;
+  return gs_render_fused_workspace(S->capacity, (int32_t)V, pair_cap, max_tiles(S->cfg) * V);
+}
+
+// All three or none: on failure nothing stays allocated.
 gs_status alloc_pair_buffers(gs_session* S, Ctx& c, int64_t pair_cap) {
   const auto& cf = S->cfg;
   const int64_t V = cf.max_batch_views;
   gs_status st;
-  if ((st = dalloc(c.vals, 4 * (size_t)pair_cap, S->in_use)) != GS_OK) return st;
-  if ((st = dalloc(c.ws_bin, bin_sort_workspace_bytes(S->capacity * V, pair_cap), S->in_use)) != GS_OK)
-    return st;
-  if ((st = dalloc(c.ws_bwd, render_bwd_ws_bytes(S->capacity, (int32_t)V, pair_cap), S->in_use)) != GS_OK)
-    return st;
-  c.pair_cap = pair_cap;
-  return GS_OK;
+  if ((st = dalloc(c.vals, 4 * (size_t)pair_cap, S->in_use, &S->fail_allocs)) == GS_OK &&
+      (st = dalloc(c.ws_bin, bin_sort_workspace_bytes(S->capacity * V, pair_cap), S->in_use, &S->fail_allocs)) ==
+          GS_OK &&
+      (st = dalloc(c.ws_bwd, fused_ws_bytes(S, pair_cap), S->in_use, &S->fail_allocs)) == GS_OK) {
+    c.pair_cap = pair_cap;
+    return GS_OK;
+  }
+  free_pair_buffers(S, c);
+  c.pair_cap = 0;
+  return st;
 }
 
 gs_status alloc_ctx(gs_session* S, Ctx& c) {
   const auto& cf = S->cfg;
   const int64_t V = cf.max_batch_views, px = max_pixels(cf);
   size_t& u = S->in_use;
+  int64_t* fa = &S->fail_allocs;
   gs_status st;
-  if ((st = dalloc(c.splat_buf, gs_splats_bytes(S->capacity, (int32_t)V), u)) != GS_OK) return st;
-  if ((st = dalloc(c.pair_off, 4 * (size_t)S->capacity * V, u)) != GS_OK) return st;
-  if ((st = dalloc(c.ranges, 8 * (size_t)max_tiles(cf) * V, u)) != GS_OK) return st;
-  if ((st = dalloc(c.order, 4 * (size_t)max_tiles(cf) * V, u)) != GS_OK) return st;
-  if ((st = dalloc(c.counts, 32, u)) != GS_OK) return st;
-  if ((st = dalloc(c.img, 12 * (size_t)px * V, u)) != GS_OK) return st;
-  if ((st = dalloc(c.dimg, 12 * (size_t)px * V, u)) != GS_OK) return st;
-  if ((st = dalloc(c.tgt, 12 * (size_t)px * V, u)) != GS_OK) return st;
-  if ((st = dalloc(c.loss_ws, loss_workspace_bytes(), u)) != GS_OK) return st;
-  if ((st = dalloc(c.loss, 8, u)) != GS_OK) return st;
-  if ((st = dalloc(c.poses, 48 * 2 * (size_t)V, u)) != GS_OK) return st;
-  if ((st = dalloc(c.dpose, 24 * (size_t)V, u)) != GS_OK) return st;
+  if ((st = dalloc(c.splat_buf, gs_splats_bytes(S->capacity, (int32_t)V), u, fa)) != GS_OK) return st;
+  if ((st = dalloc(c.pair_off, 4 * (size_t)S->capacity * V, u, fa)) != GS_OK) return st;
+  if ((st = dalloc(c.ranges, 8 * (size_t)max_tiles(cf) * V, u, fa)) != GS_OK) return st;
+  if ((st = dalloc(c.order, 4 * (size_t)max_tiles(cf) * V, u, fa)) != GS_OK) return st;
+  if ((st = dalloc(c.counts, 32, u, fa)) != GS_OK) return st;
+  if ((st = dalloc(c.img, 12 * (size_t)px * V, u, fa)) != GS_OK) return st;
+  if ((st = dalloc(c.tgt, 12 * (size_t)px * V, u, fa)) != GS_OK) return st;
+  if ((st = dalloc(c.loss, 8, u, fa)) != GS_OK) return st;
+  if ((st = dalloc(c.poses, 48 * 2 * (size_t)V, u, fa)) != GS_OK) return st;
+  if ((st = dalloc(c.dpose, 24 * (size_t)V, u, fa)) != GS_OK) return st;
   if ((st = alloc_pair_buffers(S, c, initial_pair_cap(cf))) != GS_OK) return st;
+  if (cudaStreamCreateWithFlags(&c.rs, cudaStreamNonBlocking) != cudaSuccess) return check_launch("stream");
+  if (cudaEventCreateWithFlags(&c.rdone, cudaEventDisableTiming) != cudaSuccess) return check_launch("event");
   if (cudaMallocHost(&c.h_img, 12 * (size_t)px * V) != cudaSuccess ||
       cudaMallocHost(&c.h_poses, 48 * 2 * (size_t)V) != cudaSuccess ||
       cudaMallocHost(&c.h_counts, 32) != cudaSuccess) {
@@ -247,12 +278,14 @@ gs_status alloc_ctx(gs_session* S, Ctx& c) {
 
 void free_ctx(gs_session* S, Ctx& c) {
   Dev* devs[] = {&c.splat_buf, &c.pair_off, &c.ranges, &c.order, &c.counts, &c.vals, &c.ws_bin, &c.ws_bwd, &c.img,
-                 &c.dimg, &c.tgt, &c.loss_ws, &c.loss, &c.poses, &c.dpose};
+                 &c.tgt, &c.loss, &c.poses, &c.dpose};
   for (Dev* d : devs) dfree(*d, S->in_use);
   if (c.h_img) cudaFreeHost(c.h_img);
   if (c.h_poses) cudaFreeHost(c.h_poses);
   if (c.h_counts) cudaFreeHost(c.h_counts);
   if (c.done) cudaEventDestroy(c.done);
+  if (c.rdone) cudaEventDestroy(c.rdone);
+  if (c.rs) cudaStreamDestroy(c.rs);
   c = Ctx();
 }
 
@@ -293,7 +326,19 @@ int adam_groups(gs_session* S, gs_adam_group* g) {
   return k;
 }
 
-// Enqueue one batch's whole iteration on the session stream (S->mu held).
+// The session stream waits, on the device, for every render part issued so
+// far (a write must not change what they read).
+void wait_renders(gs_session* S, cudaStream_t s) {
+  for (auto& c : S->ctxs)
+    if (c->rdone) cudaStreamWaitEvent(s, c->rdone, 0);
+}
+
+// A write of the parameters was issued on the session stream: later render
+// parts wait for it.
+void mark_write(gs_session* S) { cudaEventRecord(S->mut_done, S->stream); }
+
+// Enqueue one batch: its render part on the context's stream, its train part
+// on the session stream (S->mu held).
 gs_status issue_batch(gs_session* S, Ctx& c) {
   cudaStream_t s = S->stream;
   const auto& cf = S->cfg;
@@ -305,54 +350,70 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     else { R.push_back(r.get()); cR.push_back(r->cam); }
   }
   c.has_train = !T.empty();
+  c.issued_at = steady_now();
   gs_params P = params_of(S, 0);
   uint32_t* counts = static_cast<uint32_t*>(c.counts.p);
   float* img = static_cast<float*>(c.img.p);
   float* poses = static_cast<float*>(c.poses.p);
   const int V = cf.max_batch_views;
+  const int tw = cf.raster.tile_w, th = cf.raster.tile_h;
   gs_status st;
   int64_t off = 0;
   if (!R.empty()) {
+    GS_NVTX("session render part");
+    cudaStream_t rs = c.rs;
     ViewTable vt;
-    if (!make_view_table(cR.data(), (int)R.size(), &vt)) return GS_ERR_INVALID;
+    if (!make_view_table(cR.data(), (int)R.size(), &vt, tw, th)) return GS_ERR_INVALID;
     for (size_t i = 0; i < R.size(); ++i) std::memcpy(c.h_poses + 12 * i, R[i]->pose, 48);
-    if (cudaMemcpyAsync(poses, c.h_poses, 48 * R.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(poses, c.h_poses, 48 * R.size(), cudaMemcpyHostToDevice, rs) != cudaSuccess)
       return check_launch("session poses");
     gs_params PR = P;
     const int32_t* parent = nullptr;
     if (cf.lod && n > 0) {
       if (S->lod_dirty) {
+        // the build writes the coarse nodes: after the render parts that read them
+        GS_NVTX("session hierarchy build");
+        wait_renders(S, s);
         gs_grads rw{const_cast<float*>(P.means4), const_cast<float*>(P.scale_opa), const_cast<float*>(P.quat),
                     const_cast<float*>(P.sh), S->capacity, P.sh_degree, P.sh_stride};
         if ((st = launch_lod_build(rw, n, static_cast<int32_t*>(S->lod_parent.p), S->lod_ws.p, s)) != GS_OK)
           return st;
+        mark_write(S);
         S->lod_dirty = false;
         S->lod_builds++;
       }
       PR.n = n + lod_level1(n) + lod_level2(n);
       parent = static_cast<const int32_t*>(S->lod_parent.p);
     }
+    // every write issued before this render part
+    if (cudaStreamWaitEvent(rs, S->mut_done, 0) != cudaSuccess) return check_launch("session wait");
     gs_splats sp;
     gs_splats_carve(c.splat_buf.p, PR.n, (int32_t)R.size(), &sp);
     gs_bins b{static_cast<uint32_t*>(c.vals.p), static_cast<uint32_t*>(c.ranges.p),
               static_cast<uint32_t*>(c.pair_off.p), nullptr, counts, c.pair_cap, vt.total_tiles,
               static_cast<uint32_t*>(c.order.p)};
-    if ((st = launch_project(PR, poses, vt, cf.raster, sp, s, parent, n, cf.lod_tau)) != GS_OK) return st;
-    if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, s)) != GS_OK) return st;
-    if ((st = launch_render_fwd(sp, b, vt, cf.raster, img, nullptr, s)) != GS_OK) return st;
+    if ((st = launch_project(PR, poses, vt, cf.raster, sp, rs, parent, n, cf.lod_tau)) != GS_OK) return st;
+    if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, rs)) != GS_OK) return st;
+    if ((st = launch_render_fwd(sp, b, vt, cf.raster, img, nullptr, rs)) != GS_OK) return st;
     for (Req* r : R) off += 3 * (int64_t)r->cam.width * r->cam.height;
-    if (cudaMemcpyAsync(c.h_img, img, 4 * off, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (cudaMemcpyAsync(c.h_img, img, 4 * off, cudaMemcpyDeviceToHost, rs) != cudaSuccess)
       return check_launch("session images");
-    if (cudaMemcpyAsync(c.h_counts, counts, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (cudaMemcpyAsync(c.h_counts, counts, 16, cudaMemcpyDeviceToHost, rs) != cudaSuccess)
       return check_launch("session counts");
+    if (cudaEventRecord(c.rdone, rs) != cudaSuccess) return check_launch("session event");
   } else {
     std::memset(c.h_counts, 0, 16);
   }
   if (!T.empty()) {
+    GS_NVTX("session train part");
+    for (auto& o : S->ctxs)
+      if (o.get() != &c && o->busy && !o->reqs.empty() && o->reqs.front()->kind == GS_REQUEST_RENDER) {
+        S->train_beside_render++;  // its forward and backward run beside that render part
+        break;
+      }
     ViewTable vt;
-    if (!make_view_table(cT.data(), (int)T.size(), &vt)) return GS_ERR_INVALID;
+    if (!make_view_table(cT.data(), (int)T.size(), &vt, tw, th)) return GS_ERR_INVALID;
     float* tgt = static_cast<float*>(c.tgt.p);
-    float* dimg = static_cast<float*>(c.dimg.p);
     int64_t tpx = 0;
     for (Req* r : T) {  // straight from each request's pinned copy
       const int64_t k = 3 * (int64_t)r->cam.width * r->cam.height;
@@ -372,13 +433,17 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     float* timg = img + off;
     if ((st = launch_project(P, tposes, vt, cf.raster, sp, s)) != GS_OK) return st;
     if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, s)) != GS_OK) return st;
-    if ((st = launch_render_fwd(sp, b, vt, cf.raster, timg, nullptr, s)) != GS_OK) return st;
-    if ((st = launch_loss(timg, tgt, tpx, cf.loss_kind, dimg, static_cast<float*>(c.loss.p), c.loss_ws.p, s)) !=
-        GS_OK)
-      return st;
+    // composite, loss and per-pixel backward in one persistent launch
     float *partials, *pose_partials, *drgb;
     render_bwd_ws_layout(n, (int32_t)T.size(), c.pair_cap, c.ws_bwd.p, &partials, &pose_partials, &drgb);
-    if ((st = launch_render_bwd(sp, b, vt, cf.raster, dimg, nullptr, timg, partials, s)) != GS_OK) return st;
+    char* wsb = static_cast<char*>(c.ws_bwd.p);
+    const size_t bwd_bytes = render_bwd_ws_bytes(n, (int32_t)T.size(), c.pair_cap);
+    gs_raster_cfg rc = cf.raster;
+    rc.schedule &= ~GS_SCHED_FUSED_LONGEST_FIRST;  // the session bins without a tile order
+    if ((st = launch_render_fused(sp, b, vt, rc, tgt, cf.loss_kind, timg, nullptr, static_cast<float*>(c.loss.p),
+                                  partials, reinterpret_cast<float*>(wsb + bwd_bytes + 256),
+                                  reinterpret_cast<uint32_t*>(wsb + bwd_bytes), s)) != GS_OK)
+      return st;
     gs_params G = params_of(S, 1);
     gs_grads g{const_cast<float*>(G.means4), const_cast<float*>(G.scale_opa), const_cast<float*>(G.quat),
                const_cast<float*>(G.sh), G.n, G.sh_degree, G.sh_stride};
@@ -394,19 +459,22 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     ac.step_dev = static_cast<int32_t*>(S->step_dev.p);
     ac.skip_dev = counts + 6;  // the train sub-batch's bins status: skip on overflow
     const int64_t arena_n = (int64_t)arena_floats(S->capacity, S->nc);
+    // the update waits for the render parts issued before it (this batch's included)
+    wait_renders(S, s);
     if ((st = launch_adam(arena_ptr(S, 0), arena_ptr(S, 1), arena_ptr(S, 2), arena_ptr(S, 3), arena_n, ac, 0,
                           s)) != GS_OK)
       return st;
+    mark_write(S);
     if (cudaMemcpyAsync(c.h_counts + 4, counts + 4, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return check_launch("session counts");
   }
-  if (cudaEventRecord(c.done, s) != cudaSuccess) return check_launch("session event");
+  if (cudaEventRecord(c.done, T.empty() ? c.rs : s) != cudaSuccess) return check_launch("session event");
   return GS_OK;
 }
 
 Ctx* free_ctx_of(gs_session* S) {
   for (auto& c : S->ctxs)
-    if (!c->busy) return c.get();
+    if (!c->busy && !c->dead) return c.get();
   return nullptr;
 }
 
@@ -492,13 +560,29 @@ void completer_main(gs_session* S) {
   for (;;) {
     S->cv_done.wait(lk, [&] { return !S->inflight.empty() || (S->stop && S->queue.empty()); });
     if (S->inflight.empty()) break;
-    Ctx* c = S->inflight.front();
-    lk.unlock();
-    const double t0 = steady_now();
-    cudaError_t e;
-    while ((e = cudaEventQuery(c->done)) == cudaErrorNotReady) {
-      if (steady_now() - t0 > kWaitTimeout) break;
+    // the first batch in flight to complete (render-only batches may finish
+    // before a train batch issued earlier); a batch still running
+    // kWaitTimeout seconds after its issue is given up
+    Ctx* c = nullptr;
+    cudaError_t e = cudaErrorNotReady;
+    for (;;) {
+      std::vector<Ctx*> snap(S->inflight.begin(), S->inflight.end());
+      lk.unlock();
+      double oldest = 1e300;
+      Ctx* old_c = nullptr;
+      for (Ctx* x : snap) {
+        const cudaError_t q = cudaEventQuery(x->done);
+        if (q != cudaErrorNotReady) {
+          c = x;
+          e = q;
+          break;
+        }
+        if (x->issued_at < oldest) { oldest = x->issued_at; old_c = x; }
+      }
+      if (!c && old_c && steady_now() - oldest > kWaitTimeout) c = old_c;  // e stays NotReady: timeout
+      if (c) break;
       std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
     }
     // The render and train parts of a batch have their own tile lists and
     // status: an overflowing part is issued again on its own (a train part
@@ -519,7 +603,7 @@ void completer_main(gs_session* S) {
     }
     const bool retry = ((sr | strn) & 1u) != 0, bad_index = ((sr | strn) & 2u) != 0;
     lk.lock();
-    S->inflight.pop_front();
+    S->inflight.erase(std::find(S->inflight.begin(), S->inflight.end(), c));
     if (e == cudaErrorNotReady) {
       S->fatal = GS_ERR_TIMEOUT;
       for (auto& r : c->reqs) finish_req(S, r.get(), GS_ERR_TIMEOUT);
@@ -539,13 +623,21 @@ void completer_main(gs_session* S) {
       const size_t old = c->vals.bytes + c->ws_bin.bytes + c->ws_bwd.bytes;
       const int64_t V = S->cfg.max_batch_views;
       const size_t grow = align_up(4 * (size_t)want, 256) + bin_sort_workspace_bytes(S->capacity * V, want) +
-                          render_bwd_ws_bytes(S->capacity, (int32_t)V, want);
+                          fused_ws_bytes(S, want);
       gs_status st = GS_OK;
       if (S->in_use - old + grow > S->cfg.hbm_budget_bytes) {
         st = fail(GS_ERR_OOM, "session: pair capacity %lld exceeds the HBM budget", (long long)want);
       } else {
+        const int64_t old_cap = c->pair_cap;
         free_pair_buffers(S, *c);
         st = alloc_pair_buffers(S, *c, want);
+        if (st != GS_OK) {
+          // keep the context serving at its old capacity if that still fits
+          char msg[512];
+          gs_last_error(msg, sizeof(msg));
+          if (alloc_pair_buffers(S, *c, old_cap) != GS_OK) c->dead = true;
+          st = fail(GS_ERR_OOM, "%s", msg);
+        }
       }
       if (c->has_train && !(strn & 1u)) S->iterations++;
       if (st == GS_OK) S->retries++;
@@ -567,6 +659,10 @@ void completer_main(gs_session* S) {
     }
     c->reqs.clear();
     c->busy = false;
+    if (S->fatal == GS_OK && free_ctx_of(S) == nullptr && S->inflight.empty()) {
+      // every context lost its buffers: nothing can be served any more
+      S->fatal = fail(GS_ERR_OOM, "session: no batch context left after allocation failures");
+    }
     S->cv_work.notify_all();
     S->cv_done.notify_all();
     if (S->fatal != GS_OK) {
@@ -614,6 +710,7 @@ extern "C" {
 double gs_session_now(void) { return gs::steady_now(); }
 
 gs_status gs_session_plan(const gs_session_config* cfg, gs_session_plan_info* out) {
+  GS_NVTX("gs_session_plan");
   if (!cfg || !out) return gs::fail(GS_ERR_INVALID, "NULL config or plan");
   if (cfg->max_gaussians <= 0 || cfg->max_gaussians >= (1ll << 31) || cfg->sh_degree < 0 || cfg->sh_degree > 3)
     return gs::fail(GS_ERR_INVALID, "session: bad max_gaussians or sh_degree");
@@ -639,14 +736,14 @@ gs_status gs_session_plan(const gs_session_config* cfg, gs_session_plan_info* ou
 }
 
 gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
+  GS_NVTX("gs_session_create");
   if (!out) return gs::fail(GS_ERR_INVALID, "out is NULL");
   *out = nullptr;
   gs_session_plan_info plan;
   gs_status st = gs_session_plan(cfg, &plan);
   if (st != GS_OK) return st;
-  if (cfg->raster.tile_w != gs::kTile || cfg->raster.tile_h != gs::kTile || !(cfg->raster.znear > 0.f))
-    return gs::fail(GS_ERR_INVALID, "session: raster config must use %dx%d tiles and znear > 0", gs::kTile,
-                    gs::kTile);
+  if (!gs::tile_shape_ok(cfg->raster.tile_w, cfg->raster.tile_h) || !(cfg->raster.znear > 0.f))
+    return gs::fail(GS_ERR_INVALID, "session: raster config needs a 16x16, 32x8 or 8x32 tile and znear > 0");
   if (cfg->loss_kind != 0 && cfg->loss_kind != 1) return gs::fail(GS_ERR_INVALID, "session: loss_kind 0 or 1");
   auto S = std::make_unique<gs_session>();
   S->cfg = *cfg;
@@ -666,9 +763,12 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
     gs::dfree(S->sim3_status, S->in_use);
     if (S->h_add) cudaFreeHost(S->h_add);
     if (S->add_done) cudaEventDestroy(S->add_done);
+    if (S->mut_done) cudaEventDestroy(S->mut_done);
     cudaStreamDestroy(S->stream);
     return e;
   };
+  if (cudaEventCreateWithFlags(&S->mut_done, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(gs::check_launch("event"));
   const size_t af = gs::arena_floats(S->capacity, S->nc);
   for (auto& a : S->arena) {
     if ((st = gs::dalloc(a, 4 * af, S->in_use)) != GS_OK) return cleanup(st);
@@ -695,6 +795,7 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
     return cleanup(gs::fail(GS_ERR_OOM, "session: pinned staging"));
   cudaEventCreateWithFlags(&S->add_done, cudaEventDisableTiming);
   cudaEventRecord(S->add_done, S->stream);
+  gs::mark_write(S.get());  // the zeroed arenas
   if ((st = gs::sync_stream(S.get(), 30.0)) != GS_OK) return cleanup(st);
   gs_session* raw = S.release();
   raw->worker = std::thread(gs::worker_main, raw);
@@ -705,6 +806,7 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
 
 gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* means, const float* log_scales,
                                    const float* quats, const float* opa_logits, const float* sh) {
+  GS_NVTX("gs_session_add_gaussians");
   if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
   if (count < 0) return gs::fail(GS_ERR_INVALID, "count < 0");
   if (count == 0) return GS_OK;
@@ -760,6 +862,7 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
   std::unique_lock<std::mutex> lk(S->mu);
   float* A = gs::arena_ptr(S, 0);
   cudaStream_t s = S->stream;
+  gs::wait_renders(S, s);  // the new rows overwrite coarse nodes that render parts may be reading
   cudaMemcpyAsync(A + 4 * n0, hm, 16 * k, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(A + 4 * cap + 4 * n0, hs, 16 * k, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(A + 8 * cap + 4 * n0, hq, 16 * k, cudaMemcpyHostToDevice, s);
@@ -774,6 +877,7 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
   gs_status st = gs::launch_fill_i32(static_cast<int32_t*>(S->kf_of.p) + n0, S->keyframe, k, s);
   if (st != GS_OK) return st;
   cudaEventRecord(S->add_done, s);
+  gs::mark_write(S);
   st = gs::check_launch("session add");
   if (st != GS_OK) return st;
   S->n_active += count;
@@ -782,6 +886,7 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
 }
 
 gs_status gs_session_set_keyframe(gs_session* S, int32_t kf) {
+  GS_NVTX("gs_session_set_keyframe");
   if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
   std::lock_guard<std::mutex> add_lk(S->add_mu);
   S->keyframe = kf < 0 ? -1 : kf;
@@ -789,6 +894,7 @@ gs_status gs_session_set_keyframe(gs_session* S, int32_t kf) {
 }
 
 gs_status gs_session_loop_closure(gs_session* S, int32_t num_kf, const float* sim3) {
+  GS_NVTX("gs_session_loop_closure");
   if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
   if (num_kf < 0 || (num_kf > 0 && !sim3)) return gs::fail(GS_ERR_INVALID, "bad corrections");
   for (int32_t k = 0; k < num_kf; ++k)
@@ -805,6 +911,7 @@ gs_status gs_session_loop_closure(gs_session* S, int32_t num_kf, const float* si
     if ((st = gs::dalloc(S->sim3, bytes, S->in_use)) != GS_OK) return st;
   }
   cudaStream_t s = S->stream;
+  gs::wait_renders(S, s);  // the update moves what render parts issued earlier read
   if (num_kf > 0 && cudaMemcpyAsync(S->sim3.p, sim3, 32 * (size_t)num_kf, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return gs::check_launch("session sim3");
   gs_params P = gs::params_of(S, 0);
@@ -814,12 +921,14 @@ gs_status gs_session_loop_closure(gs_session* S, int32_t num_kf, const float* si
                                         static_cast<const float*>(S->sim3.p), num_kf,
                                         static_cast<uint32_t*>(S->sim3_status.p), s);
   if (st != GS_OK) return st;
+  gs::mark_write(S);
   S->lod_dirty = true;  // coarse nodes follow the moved leaves at the next build
   return GS_OK;
 }
 
 gs_status gs_session_keyframe_weights(gs_session* S, int32_t num_kf, int32_t min_keep, float frac, double* p_out,
                                       uint32_t* counts_out, uint8_t* kept_out) {
+  GS_NVTX("gs_session_keyframe_weights");
   if (!S || !p_out) return gs::fail(GS_ERR_INVALID, "NULL session or output");
   if (num_kf <= 0 || min_keep < 0 || !(frac >= 0.f && frac <= 1.f))
     return gs::fail(GS_ERR_INVALID, "bad num_kf, min_keep or frac");
@@ -864,6 +973,7 @@ gs_status gs_session_keyframe_weights(gs_session* S, int32_t num_kf, int32_t min
 }
 
 gs_status gs_session_submit(gs_session* S, const gs_request* req, int64_t* id) {
+  GS_NVTX("gs_session_submit");
   if (!S || !req) return gs::fail(GS_ERR_INVALID, "NULL session or request");
   if (req->kind != GS_REQUEST_RENDER && req->kind != GS_REQUEST_TRAIN)
     return gs::fail(GS_ERR_INVALID, "request kind must be render or train");
@@ -900,6 +1010,7 @@ gs_status gs_session_submit(gs_session* S, const gs_request* req, int64_t* id) {
 }
 
 gs_status gs_session_poll(gs_session* S, int64_t id, int32_t* done) {
+  GS_NVTX("gs_session_poll");
   if (!S || !done) return gs::fail(GS_ERR_INVALID, "NULL session or output");
   std::unique_lock<std::mutex> lk(S->mu);
   if (id < 1 || id > (int64_t)S->all.size()) return gs::fail(GS_ERR_INVALID, "unknown request id %lld", (long long)id);
@@ -909,6 +1020,7 @@ gs_status gs_session_poll(gs_session* S, int64_t id, int32_t* done) {
 }
 
 gs_status gs_session_wait(gs_session* S, int64_t id, int32_t timeout_ms) {
+  GS_NVTX("gs_session_wait");
   if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
   std::unique_lock<std::mutex> lk(S->mu);
   if (id < 1 || id > (int64_t)S->all.size()) return gs::fail(GS_ERR_INVALID, "unknown request id %lld", (long long)id);
@@ -919,6 +1031,7 @@ gs_status gs_session_wait(gs_session* S, int64_t id, int32_t timeout_ms) {
 }
 
 gs_status gs_session_times(gs_session* S, int64_t id, double* arrival_s, double* done_s) {
+  GS_NVTX("gs_session_times");
   if (!S || !arrival_s || !done_s) return gs::fail(GS_ERR_INVALID, "NULL session or output");
   std::unique_lock<std::mutex> lk(S->mu);
   if (id < 1 || id > (int64_t)S->all.size()) return gs::fail(GS_ERR_INVALID, "unknown request id %lld", (long long)id);
@@ -930,6 +1043,7 @@ gs_status gs_session_times(gs_session* S, int64_t id, double* arrival_s, double*
 }
 
 gs_status gs_session_hold(gs_session* S, int32_t on) {
+  GS_NVTX("gs_session_hold");
   if (!S) return gs::fail(GS_ERR_INVALID, "NULL session");
   std::lock_guard<std::mutex> lk(S->mu);
   S->hold = on != 0;
@@ -938,12 +1052,14 @@ gs_status gs_session_hold(gs_session* S, int32_t on) {
 }
 
 gs_status gs_session_drain(gs_session* S, int32_t timeout_ms) {
+  GS_NVTX("gs_session_drain");
   if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
   std::unique_lock<std::mutex> lk(S->mu);
   return gs::wait_idle(S, lk, timeout_ms);
 }
 
 gs_status gs_session_stats(gs_session* S, gs_stats* out) {
+  GS_NVTX("gs_session_stats");
   if (!S || !out) return gs::fail(GS_ERR_INVALID, "NULL session or stats");
   std::unique_lock<std::mutex> lk(S->mu);
   gs_stats st{};
@@ -964,6 +1080,7 @@ gs_status gs_session_stats(gs_session* S, gs_stats* out) {
   st.hbm_in_use = S->in_use;
   st.hbm_budget = S->cfg.hbm_budget_bytes;
   st.contexts = (int32_t)S->ctxs.size();
+  st.train_beside_render = S->train_beside_render;
   if (!S->latencies.empty()) {
     std::vector<double> l = S->latencies;
     std::sort(l.begin(), l.end());
@@ -985,6 +1102,7 @@ gs_status gs_session_stats(gs_session* S, gs_stats* out) {
 
 // Checkpoint: parameters, Adam moments, the step counter and the active count.
 gs_status gs_session_save(gs_session* S, const char* path) {
+  GS_NVTX("gs_session_save");
   if (!S || !path) return gs::fail(GS_ERR_INVALID, "NULL session or path");
   std::unique_lock<std::mutex> lk(S->mu);
   gs_status st = gs::wait_idle(S, lk, 60000);
@@ -1020,6 +1138,7 @@ gs_status gs_session_save(gs_session* S, const char* path) {
 }
 
 gs_status gs_session_load(gs_session* S, const char* path) {
+  GS_NVTX("gs_session_load");
   if (!S || !path) return gs::fail(GS_ERR_INVALID, "NULL session or path");
   std::unique_lock<std::mutex> lk(S->mu);
   gs_status st = gs::wait_idle(S, lk, 60000);
@@ -1056,6 +1175,7 @@ gs_status gs_session_load(gs_session* S, const char* path) {
   if (!ok) return gs::fail(GS_ERR_INVALID, "%s is truncated", path);
   const int32_t step = (int32_t)hdr[3];
   cudaMemcpyAsync(S->step_dev.p, &step, 4, cudaMemcpyHostToDevice, S->stream);
+  gs::mark_write(S);
   if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
   S->n_active = n;
   S->lod_dirty = true;
@@ -1063,6 +1183,7 @@ gs_status gs_session_load(gs_session* S, const char* path) {
 }
 
 gs_status gs_session_read_params(gs_session* S, float* means4, float* scale_opa, float* quat, float* sh) {
+  GS_NVTX("gs_session_read_params");
   if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
   std::unique_lock<std::mutex> lk(S->mu);
   gs_status st = gs::wait_idle(S, lk, 60000);
@@ -1079,7 +1200,16 @@ gs_status gs_session_read_params(gs_session* S, float* means4, float* scale_opa,
   return gs::check_launch("session read");
 }
 
+gs_status gs_session_inject_alloc_failures(gs_session* S, int32_t count) {
+  GS_NVTX("gs_session_inject_alloc_failures");
+  if (!S || count < 0) return gs::fail(GS_ERR_INVALID, "NULL session or count < 0");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->fail_allocs = count;
+  return GS_OK;
+}
+
 gs_status gs_session_destroy(gs_session* S) {
+  GS_NVTX("gs_session_destroy");
   if (!S) return GS_OK;
   {
     std::unique_lock<std::mutex> lk(S->mu);

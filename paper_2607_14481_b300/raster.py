@@ -164,12 +164,13 @@ class Rasterizer:
 
     def __init__(self, n: int, sh_degree: int, cams: Sequence[Camera], bg=(0.0, 0.0, 0.0), znear=0.2,
                  clamp_jacobian=True, capacity: Optional[int] = None, device="cuda", keep_keys=False,
-                 largest_first: bool = True):
+                 largest_first: bool = True, tile=(16, 16)):
         self.L = _lib.load()
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.device = torch.device(device)
+        self.tile = (int(tile[0]), int(tile[1]))
         self.set_cameras(cams)
-        self.cfg = _lib.GsRasterCfg(_lib.GS_TILE, _lib.GS_TILE, (C.c_float * 3)(*bg), float(znear),
+        self.cfg = _lib.GsRasterCfg(self.tile[0], self.tile[1], (C.c_float * 3)(*bg), float(znear),
                                     int(bool(clamp_jacobian)))
         V = self.views
         self.splat_buf = torch.empty(self.L.gs_splats_bytes(self.n, V), dtype=torch.uint8, device=self.device)
@@ -189,12 +190,26 @@ class Rasterizer:
         self.cams = cams
         self.views = len(cams)
         self.cam_struct = cameras_struct(cams)
-        self.num_tiles = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in cams)
+        self.num_tiles = self.tiles_for(self.tile)
+        # ranges and tile order hold the largest tile count of any supported shape
+        self.max_tiles = max(self.tiles_for(t) for t in _lib.TILE_SHAPES)
         self.pixels = sum(c.width * c.height for c in cams)
-        if hasattr(self, "ranges") and self.ranges.numel() >= 2 * self.num_tiles:
+        if hasattr(self, "ranges") and self.ranges.numel() >= 2 * self.max_tiles:
             return
-        self.ranges = torch.zeros(max(2, 2 * self.num_tiles), dtype=torch.int32, device=self.device)
-        self.tile_order = torch.zeros(max(1, self.num_tiles), dtype=torch.int32, device=self.device)
+        self.ranges = torch.zeros(max(2, 2 * self.max_tiles), dtype=torch.int32, device=self.device)
+        self.tile_order = torch.zeros(max(1, self.max_tiles), dtype=torch.int32, device=self.device)
+        if hasattr(self, "ws_bwd"):
+            self._alloc_pairs()
+
+    def tiles_for(self, tile) -> int:
+        tw, th = tile
+        return sum(((c.width + tw - 1) // tw) * ((c.height + th - 1) // th) for c in self.cams)
+
+    def set_tile(self, tile) -> None:
+        """Tile shape (16x16, 32x8 or 8x32) of the following calls."""
+        self.tile = (int(tile[0]), int(tile[1]))
+        self.cfg.tile_w, self.cfg.tile_h = self.tile
+        self.num_tiles = self.tiles_for(self.tile)
 
     def set_capacity(self, cap: int) -> None:
         cap = int(cap)
@@ -203,16 +218,22 @@ class Rasterizer:
         self.capacity = cap
         self.vals = torch.empty(max(1, cap), dtype=torch.int32, device=self.device)
         self.keys = torch.empty(max(1, cap), dtype=torch.int64, device=self.device) if self.keep_keys else None
+        self._alloc_pairs()
+
+    def _alloc_pairs(self) -> None:
+        cap = self.capacity
         self.ws_bin = torch.empty(self.L.gs_bin_sort_workspace(self.n, self.views, cap), dtype=torch.uint8,
                                   device=self.device)
-        self.ws_bwd = torch.empty(self.L.gs_render_bwd_workspace(self.n, self.views, cap), dtype=torch.uint8,
-                                  device=self.device)
+        # the fused pass's workspace: the backward's layout plus its counter and per-tile loss terms
+        self.ws_bwd = torch.empty(self.L.gs_render_fused_workspace(self.n, self.views, cap, self.max_tiles),
+                                  dtype=torch.uint8, device=self.device)
 
     def bins_struct(self, with_order: Optional[bool] = None):
         """The tile lists; the longest-first tile order is computed only when
         the schedule reads it (or when asked, for the autotuner)."""
         if with_order is None:
-            with_order = bool(self.cfg.schedule & (_lib.GS_SCHED_FWD_LONGEST_FIRST | _lib.GS_SCHED_BWD_LONGEST_FIRST))
+            with_order = bool(self.cfg.schedule & (_lib.GS_SCHED_FWD_LONGEST_FIRST | _lib.GS_SCHED_BWD_LONGEST_FIRST
+                                                   | _lib.GS_SCHED_FUSED_LONGEST_FIRST))
         order = self.tile_order.data_ptr() if (self.largest_first and with_order) else None
         return _lib.GsBins(self.vals.data_ptr(), self.ranges.data_ptr(), self.pair_off.data_ptr(),
                            self.keys.data_ptr() if self.keys is not None else None, self.counts.data_ptr(),
@@ -282,6 +303,38 @@ class Rasterizer:
         names = [f"fwd_{o}_{b}" for o in ("natural", "longest") for b in (128, 64, 256)] + \
                 [f"bwd_{o}_{b}" for o in ("natural", "longest") for b in (128, 64)]
         return {"schedule": int(self.cfg.schedule), "ms": {k: float(v) for k, v in zip(names, t)}}
+
+    def fused(self, target: torch.Tensor, loss_kind: int, image: torch.Tensor, alpha: Optional[torch.Tensor],
+              loss: torch.Tensor) -> None:
+        """gs_render_fused: composite, image loss against target and the
+        per-pixel backward in one persistent launch; the per-pair gradients
+        stay in the workspace for backward_gaussians()."""
+        b = self.bins_struct()
+        _lib.check(self.L.gs_render_fused(C.byref(self.splats), C.byref(b), self.cam_struct, self.views,
+                                          C.byref(self.cfg), _p(target), int(loss_kind), _p(image), _p(alpha),
+                                          _p(loss), self.n, _p(self.ws_bwd), self.ws_bwd.numel(), _stream()),
+                   "gs_render_fused")
+
+    def autotune_fused(self, params: "Arena", poses: torch.Tensor, target: torch.Tensor, loss_kind: int,
+                       image: torch.Tensor, loss: torch.Tensor, reps: int = 5) -> dict:
+        """gs_autotune_fused: picks the tile shape, splats per batch and work
+        order of the fused pass on this workload (re-projecting and re-binning
+        per shape) and keeps them in this Rasterizer.  Synchronises.  Returns
+        the candidates' times and the choice."""
+        ps = params.struct()
+        b = self.bins_struct(with_order=True)
+        t = (C.c_float * 12)()
+        _lib.check(self.L.gs_autotune_fused(C.byref(ps), _p(poses), self.cam_struct, self.views, C.byref(self.cfg),
+                                            C.byref(self.splats), C.byref(b), self.max_tiles, _p(self.ws_bin),
+                                            self.ws_bin.numel(), _p(target), int(loss_kind), _p(image), _p(loss),
+                                            _p(self.ws_bwd), self.ws_bwd.numel(), int(reps), t, _stream()),
+                   "gs_autotune_fused")
+        self.tile = (int(self.cfg.tile_w), int(self.cfg.tile_h))
+        self.num_tiles = self.tiles_for(self.tile)
+        names = [f"{tw}x{th}_b{bt}_{o}" for tw, th in _lib.TILE_SHAPES for bt in (128, 64)
+                 for o in ("viewmajor", "longest")]
+        return {"tile": list(self.tile), "schedule": int(self.cfg.schedule),
+                "ms": {k: float(v) for k, v in zip(names, t)}}
 
     def render_stats(self) -> dict:
         """Work counts of the current tile lists (synchronises): pairs tested

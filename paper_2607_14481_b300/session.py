@@ -16,11 +16,12 @@ def default_config(max_gaussians: int, sh_degree: int = 3, max_batch_views: int 
                    max_height: int = 1080, max_inflight: int = 2, hbm_budget_gb: float = 80.0,
                    pair_factor: float = 4.0, loss_kind: int = 0, bg=(0.0, 0.0, 0.0), znear: float = 0.2,
                    lr_means=1.6e-4, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3, lr_sh_dc=2.5e-3,
-                   lr_sh_rest=1.25e-4, lod: bool = False, lod_tau: float = 1.0) -> _lib.GsSessionConfig:
+                   lr_sh_rest=1.25e-4, lod: bool = False, lod_tau: float = 1.0,
+                   tile=(16, 16)) -> _lib.GsSessionConfig:
     """lod: render requests go through the three-level hierarchy's cut at
     lod_tau pixels (rebuilt before the first render after Gaussians were
-    added); train requests always use the leaves."""
-    raster = _lib.GsRasterCfg(_lib.GS_TILE, _lib.GS_TILE, (C.c_float * 3)(*bg), float(znear), 1)
+    added); train requests always use the leaves.  tile: 16x16, 32x8 or 8x32."""
+    raster = _lib.GsRasterCfg(int(tile[0]), int(tile[1]), (C.c_float * 3)(*bg), float(znear), 1)
     return _lib.GsSessionConfig(int(max_gaussians), int(sh_degree), int(max_batch_views), int(max_width),
                                 int(max_height), int(max_inflight), int(hbm_budget_gb * (1 << 30)),
                                 float(pair_factor), raster, lr_means, lr_scale, lr_opacity, lr_quat, lr_sh_dc,
@@ -143,6 +144,11 @@ class Session:
 
     def drain(self, timeout_ms: int = 120000) -> None:
         _lib.check(self.L.gs_session_drain(self.h, timeout_ms), "gs_session_drain")
+
+    def inject_alloc_failures(self, count: int) -> None:
+        """The session's next `count` device allocations fail as if the
+        device were out of memory (host-side fault injection, for tests)."""
+        _lib.check(self.L.gs_session_inject_alloc_failures(self.h, int(count)), "gs_session_inject_alloc_failures")
 
     def stats(self) -> dict:
         s = _lib.GsStats()

@@ -18,7 +18,10 @@ from .raster import Arena, ImageLoss, Rasterizer
 
 class TrainStep:
     """Forward, image loss (L1 or MSE), backward (parameters and pose twist),
-    fused Adam (parameters + poses) for the views of `rast`.
+    fused Adam (parameters + poses) for the views of `rast`.  With fused=True
+    (the default) the composite, the loss and the per-pixel backward run as
+    one persistent launch over all views' tiles (gs_render_fused); otherwise
+    as three launches (gs_render_fwd, gs_image_loss, gs_render_bwd_pixels).
 
     poses, dpose, pose_m, pose_v, pose_steps: device tensors with one row per
     view of this step (slices of larger per-trajectory tensors are fine);
@@ -31,7 +34,7 @@ class TrainStep:
                  pose_steps: Optional[torch.Tensor] = None, pose_lr: float = 1e-4, loss_kind: int = 0,
                  status: Optional[torch.Tensor] = None, image: Optional[torch.Tensor] = None,
                  dimage: Optional[torch.Tensor] = None, loss: Optional[ImageLoss] = None,
-                 cams: Optional[Sequence] = None):
+                 cams: Optional[Sequence] = None, fused: bool = True):
         self.arena, self.grads, self.m, self.v, self.groups = arena, grads, m, v, groups
         self.rast = rast
         self.cams = list(cams) if cams is not None else list(rast.cams)
@@ -48,6 +51,7 @@ class TrainStep:
         self.img = image if image is not None else rast.new_image()
         self.dimg = dimage if dimage is not None else rast.new_image()
         self.loss = loss if loss is not None else ImageLoss(dev)
+        self.fused = fused
         self.graph: Optional[torch.cuda.CUDAGraph] = None
 
     def body(self) -> None:
@@ -55,9 +59,13 @@ class TrainStep:
         r.set_cameras(self.cams)
         r.project(self.arena, self.poses)
         r.bin_sort()
-        r.render_fwd(self.img, None)
-        self.loss(self.img, self.targets, self.dimg, self.kind)
-        r.backward_pixels(self.dimg, None, self.img)
+        if self.fused:
+            # composite + loss + per-pixel backward: one persistent launch
+            r.fused(self.targets, self.kind, self.img, None, self.loss.loss)
+        else:
+            r.render_fwd(self.img, None)
+            self.loss(self.img, self.targets, self.dimg, self.kind)
+            r.backward_pixels(self.dimg, None, self.img)
         r.backward_gaussians(self.arena, self.poses, self.grads, self.dpose)
         with_pose = self.pose_m is not None
         raster.adam_step(self.arena, self.grads, self.m, self.v, 0, self.groups, status=self.status,

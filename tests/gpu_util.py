@@ -14,13 +14,14 @@ def ensure_built():
     build.build()
 
 
-def gpu_forward(sc: Scene, cams, bg=(0.0, 0.0, 0.0), znear=0.2, clamp_j=True, capacity=None, keep_keys=False):
+def gpu_forward(sc: Scene, cams, bg=(0.0, 0.0, 0.0), znear=0.2, clamp_j=True, capacity=None, keep_keys=False,
+                tile=(16, 16)):
     ensure_built()
     dev = torch.device("cuda:0")
     arena = raster.Arena.from_scene(sc, dev)
     poses = raster.poses_tensor(cams, dev)
     r = raster.Rasterizer(sc.n, sc.sh_degree, cams, bg=bg, znear=znear, clamp_jacobian=clamp_j,
-                          capacity=capacity, device=dev, keep_keys=keep_keys)
+                          capacity=capacity, device=dev, keep_keys=keep_keys, tile=tile)
     img = r.new_image()
     alpha = r.new_alpha()
     r.forward(arena, poses, img, alpha, check=True)
@@ -58,3 +59,45 @@ def compare_grads(g_gpu, g_ref, tol=GRAD_TOL, groups=("means", "log_scales", "qu
     assert not bad, f"gradient parity failed: {errs}"
     assert np.all(g_gpu["means_pad"] == 0.0)
     return errs
+
+
+def fused_step(r, arena, poses, target, kind, alpha=None):
+    """gs_render_fused then gs_render_bwd_gaussians on the rasterizer's current
+    tile lists: image, loss, gradients (natural layout, pose included)."""
+    dev = arena.buf.device
+    img = r.new_image()
+    img.fill_(float("nan"))
+    loss = torch.full((1,), float("nan"), dtype=torch.float32, device=dev)
+    r.fused(target, kind, img, alpha, loss)
+    grads = arena.like()
+    grads.buf.fill_(float("nan"))
+    dpose = torch.full((r.views, 6), float("nan"), dtype=torch.float32, device=dev)
+    r.backward_gaussians(arena, poses, grads, dpose)
+    torch.cuda.synchronize()
+    g = grads.to_natural()
+    g["pose"] = dpose.cpu().numpy().astype(np.float64)
+    return img, float(loss.item()), g
+
+
+def target_near(img_views, flags, rng, lo=0.02, hi=0.2):
+    """Targets equal to the image plus a random offset of magnitude in
+    [lo, hi] and random sign, and equal to the image where the oracle flags a
+    pixel (there both losses' gradients are exactly 0).  Returns the per-view
+    targets as float32 arrays [3, H, W]."""
+    out = []
+    for im, f in zip(img_views, flags):
+        im = np.asarray(im, np.float32)
+        d = rng.uniform(lo, hi, size=im.shape) * rng.choice([-1.0, 1.0], size=im.shape)
+        t = (im.astype(np.float64) + d).astype(np.float32)
+        out.append(np.where((f != 0)[None], im, t).astype(np.float32))
+    return out
+
+
+def loss_grad(img_views, tgt_views, kind, count):
+    """dL/dimage of the L1 (kind 0) or MSE (kind 1) mean loss, in float64 from
+    the float32 images and targets (the gradient the fused kernel forms)."""
+    out = []
+    for im, t in zip(img_views, tgt_views):
+        d = np.asarray(im, np.float32).astype(np.float64) - np.asarray(t, np.float32).astype(np.float64)
+        out.append(np.sign(d) / count if kind == 0 else 2.0 * d / count)
+    return out

@@ -108,7 +108,20 @@ def test_both_arms_report_the_same_config():
 
 
 def test_library_kernels_per_training_step():
-    # projection 1, binning 11, composite 1, loss 2, per-pixel backward 1,
-    # per-Gaussian backward 5, Adam 3; a longest-first schedule adds 2
-    assert bench.launches_per_step(1, 3600) == 24
-    assert bench.launches_per_step(1, 3600, tile_order=True) == 26
+    # projection 1, binning 11, fused composite + loss + per-pixel backward 1,
+    # per-Gaussian backward 5, Adam 3; a longest-first schedule adds 2;
+    # unfused: composite 1, loss 2, per-pixel backward 1 instead of the fused 1
+    assert bench.launches_per_step(1, 3600) == 21
+    assert bench.launches_per_step(1, 3600, tile_order=True) == 23
+    assert bench.launches_per_step(1, 3600, fused=False) == 24
+
+
+def test_roofline_of_the_fused_step():
+    cam = synth.forward_trajectory(3, seed=1008)[0]
+    st = {"project": 0.08, "bin_sort": 0.21, "render_fused": 0.55, "render_bwd_gaussians": 0.2, "adam": 0.32}
+    r = bench.roofline(_workload(1_000_000, [cam]), st, WORK, PEAKS, sms=148)
+    # both traversals per evaluated pair: 12 + 45 FP32, 1 + 2 MUFU
+    assert r["kernel"] == "render_fused" and r["binding_unit"] == "fp32"
+    assert r["algorithmic"] == pytest.approx(57 * 178e6)
+    assert r["frac"] == pytest.approx(57 * 178e6 / 0.55e-3 / (148 * 128 * 2032e6))
+    assert "loss" not in r["per_stage"] and "render_fwd" not in r["per_stage"]

@@ -286,3 +286,86 @@ def test_keyframe_weights_match_oracle(cuda_device):
             assert np.allclose(got["p"], p, rtol=1e-12, atol=0)
         picks = s.sample_keyframes(K, 1000, np.random.default_rng(0))
         assert np.all(kept[picks])
+
+
+def test_render_beside_train_sees_exactly_the_updates_issued_before_it(cuda_device):
+    """Render parts run on their own batch contexts' streams.  A render issued
+    before a train batch runs beside that batch's forward and backward and
+    shows the parameters before its update; a render submitted while a train
+    batch is executing waits for its update on the device.  Each equals the
+    same render alone, bit for bit."""
+    ensure_built()
+    sc = _scene(n=20000, seed=12)
+    view = _cams(1, seed=13)[0]
+    tcam = synth.look_at((0.5, -0.4, -4.5), (0, 0, 0), 380.0, 380.0, 240.0, 136.0, 480, 272)
+    tgt = _targets([tcam], seed=14)[0]
+    cfg = _cfg(sc.n, max_batch_views=1, max_inflight=3, pair_factor=16.0, lr_means=1e-2, lr_opacity=0.2)
+    with session.Session(cfg) as s:
+        s.add(sc)
+        assert s.stats()["contexts"] >= 2
+        before = s.wait(s.submit(RENDER, view, want_image=True))  # alone, no update yet
+        # render, then train, released together as two batches
+        s.hold(True)
+        ra = s.submit(RENDER, view, want_image=True)
+        t1 = s.submit(TRAIN, tcam, target=tgt)
+        s.hold(False)
+        img_a = s.wait(ra)
+        s.wait(t1)
+        # train, then a render submitted while it executes
+        t2 = s.submit(TRAIN, tcam, target=tgt)
+        rb = s.submit(RENDER, view, want_image=True)
+        img_b = s.wait(rb)
+        s.wait(t2)
+        after = s.wait(s.submit(RENDER, view, want_image=True))  # alone, after both updates
+        st = s.stats()
+    assert st["failed"] == 0 and st["iterations"] == 2 and st["retries"] == 0
+    assert st["train_beside_render"] >= 1
+    assert np.array_equal(img_a, before)
+    assert np.array_equal(img_b, after)
+    assert not np.array_equal(after, before)  # the two updates changed what the view shows
+
+
+def test_allocation_failure_is_reported_and_the_session_keeps_serving(cuda_device):
+    """Host-side fault injection: the pair buffers of a batch that overflowed
+    cannot grow (the allocation fails as if the device were out of memory),
+    so its request finishes with GS_ERR_OOM; the context keeps its old
+    buffers and the session serves the next request (which grows them)."""
+    ensure_built()
+    sc = _scene(n=20000, seed=15)
+    big = _cams(1, seed=16)[0]
+    with session.Session(_cfg(sc.n, max_batch_views=1, max_inflight=1, pair_factor=0.01)) as s:
+        s.add(sc)
+        assert session.plan(_cfg(sc.n, max_batch_views=1, max_inflight=1, pair_factor=0.01))[
+            "initial_pair_capacity"] == 4096
+        s.inject_alloc_failures(1)
+        rid = s.submit(RENDER, big, want_image=True)
+        with pytest.raises(_lib.GsError) as ei:
+            s.wait(rid)
+        assert ei.value.status == _lib.GS_ERR_OOM
+        img = s.wait(s.submit(RENDER, big, want_image=True))
+        st = s.stats()
+    assert st["failed"] == 1 and st["completed"] == 1 and st["retries"] >= 1
+    assert np.array_equal(img, _direct_render(sc, big))
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (8, 32)])
+def test_session_with_other_tile_shapes(cuda_device, tile):
+    """Sessions take any supported tile shape: renders equal the direct
+    rasterizer at that shape and the oracle; training runs."""
+    ensure_built()
+    sc = _scene(n=8000, seed=17)
+    cams = _cams(2, seed=18)
+    with session.Session(_cfg(sc.n, tile=tile)) as s:
+        s.add(sc)
+        img = s.wait(s.submit(RENDER, cams[0], want_image=True))
+        s.wait(s.submit(TRAIN, cams[1], target=_targets(cams[1:], seed=19)[0]))
+        st = s.stats()
+    assert st["failed"] == 0 and st["iterations"] == 1
+    dev = torch.device("cuda:0")
+    a = raster.Arena.from_scene(sc, dev)
+    r = raster.Rasterizer(sc.n, sc.sh_degree, cams[:1], device=dev, tile=tile)
+    d, _ = r.forward(a, raster.poses_tensor(cams[:1], dev), r.new_image(), None)
+    assert np.array_equal(img, r.split(d.cpu(), 3)[0].numpy())
+    ref = oracle.render(sc, cams[:1], tile=tile)
+    ok = (ref["flags"][0] & 1) == 0
+    assert np.abs(img.astype(np.float64) - ref["image"][0])[:, ok].max() <= IMG_TOL

@@ -1,7 +1,8 @@
 """The training step exactly as the benchmark runs it, against the FP64 oracle
 on outputs the oracle can compute one by one.  The step is 1M Gaussians, SH3,
 one 1280x720 view of the forward trajectory, L1 loss and the pose step, with
-the autotuned blend schedule, replayed from a captured CUDA graph.  Checked:
+the fused composite + loss + backward pass and the tile shape and schedule
+its autotuner picks, replayed from a captured CUDA graph.  Checked:
 
 - image windows of the replayed step, among them the ragged corner;
 - the replayed step's Adam update of sampled Gaussians' parameters and of
@@ -36,13 +37,13 @@ def _lr_per_element(arena, groups):
     return lr
 
 
-def _disjoint_small_splats(rec, rng, want):
-    """Gaussians whose rect is at most 2x2 tiles, with pairwise disjoint
-    rects (their pixel windows then never overlap)."""
+def _disjoint_small_splats(rec, rng, want, tw, th):
+    """Gaussians whose rect is at most 2x2 tiles (of tw x th pixels), with
+    pairwise disjoint rects (their pixel windows then never overlap)."""
     touched = rec["touched"][0].astype(np.int64)
     cand = np.flatnonzero((touched >= 1) & (touched <= 4))
     rng.shuffle(cand)
-    used = np.zeros((H // 16 + 1, W // 16 + 1), bool)
+    used = np.zeros((H // th + 2, W // tw + 2), bool)
     out = []
     for i in cand:
         r0, r1 = int(rec["rect"][0][i, 0]), int(rec["rect"][0][i, 1])
@@ -50,7 +51,7 @@ def _disjoint_small_splats(rec, rng, want):
         if used[y0:y1 + 1, x0:x1 + 1].any():
             continue
         used[max(0, y0 - 1):y1 + 2, max(0, x0 - 1):x1 + 2] = True
-        out.append((int(i), (16 * x0, 16 * y0, min(16 * (x1 + 1), W) - 16 * x0, min(16 * (y1 + 1), H) - 16 * y0)))
+        out.append((int(i), (tw * x0, th * y0, min(tw * (x1 + 1), W) - tw * x0, min(th * (y1 + 1), H) - th * y0)))
         if len(out) == want:
             break
     return out
@@ -77,8 +78,9 @@ def test_graph_replayed_step_1m_720p(cuda_device):
     gen = torch.Generator(device="cpu").manual_seed(1009)
     target = torch.rand(3 * W * H, generator=gen).to(dev)
     loss = raster.ImageLoss(dev)
-    loss(img, target, dimg, 0)
-    rast.autotune(img, dimg, reps=1)
+    rast.autotune_fused(arena, poses, target, 0, img, loss.loss, reps=1)
+    rast.forward(arena, poses, img, None, check=True)  # pair capacity at the chosen tile shape
+    rast.set_capacity(int(rast.read_counts()[1] * 1.3) + 4096)
     st = train.TrainStep(arena, grads, m, v, groups, rast, poses, target, step_dev, pose_m=pm, pose_v=pv,
                          pose_steps=psteps, pose_lr=1e-4, loss_kind=0, status=status, image=img, dimage=dimg,
                          loss=loss, cams=[cam])
@@ -101,11 +103,11 @@ def test_graph_replayed_step_1m_720p(cuda_device):
                         cam.cy, W, H)
     rng = np.random.default_rng(11)
     rec = rast.splat_arrays()
-    samples = _disjoint_small_splats(rec, rng, 12)
+    samples = _disjoint_small_splats(rec, rng, 12, *rast.tile)
     assert len(samples) >= 8
     wins = [w for _, w in samples] + [(W - 40, H - 24, 40, 24)] + \
         [(int(rng.integers(0, W - 48)), int(rng.integers(0, H - 48)), 48, 48) for _ in range(2)]
-    ref = oracle.render(sc, [cam0] * len(wins), windows=wins)
+    ref = oracle.render(sc, [cam0] * len(wins), windows=wins, tile=rast.tile)
     full = rast.split(img.cpu(), 3)[0].numpy().astype(np.float64)
     flagged = total = 0
     for k, (x0, y0, w, h) in enumerate(wins):
@@ -136,7 +138,9 @@ def test_graph_replayed_step_1m_720p(cuda_device):
     assert np.all(np.abs(M1 - mm) <= 1e-6 * (0.9 * np.abs(M0[e]) + 0.1 * np.abs(G)) + 1e-30)
 
     # gradients: the step's backward kernels on its own tile lists, with the
-    # pre-step parameters and pose and the windowed, masked dL/dimage
+    # pre-step parameters and pose and the windowed, masked dL/dimage (the L1
+    # gradient of the step's image, which the fused pass formed internally)
+    loss(img, target, dimg, 0)
     arena.buf.copy_(torch.from_numpy(P0.astype(np.float32)))
     poses.copy_(torch.from_numpy(pose0.reshape(1, 12).astype(np.float32)))
     gwins = [w for _, w in samples]
@@ -152,7 +156,7 @@ def test_graph_replayed_step_1m_720p(cuda_device):
     rast.backward_pixels(dmask_dev, None, img)
     rast.backward_gaussians(arena, poses, grads, dpose)
     torch.cuda.synchronize()
-    g_ref = oracle.backward(sc, [cam0] * len(gwins), dwin, windows=gwins)
+    g_ref = oracle.backward(sc, [cam0] * len(gwins), dwin, windows=gwins, tile=rast.tile)
     g_gpu = grads.to_natural()
     for name in ("means", "log_scales", "quats", "opa_logits", "sh"):
         assert rel_err(g_gpu[name][ids_all], g_ref[name][ids_all]) <= GRAD_TOL, name
