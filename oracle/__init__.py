@@ -436,3 +436,112 @@ def keyframe_weights(kf, num_kf, min_keep=50, frac=0.05):
     w = np.where(kept, c, 0).astype(np.float64)
     p = w / w.sum() if w.sum() > 0 else w
     return c, p, kept
+
+
+# ---------------------------------------------------------------------------
+# Progressive hierarchy (gs_lod_oracle.cpp, orc_hier_*)
+# ---------------------------------------------------------------------------
+
+def _hier_lib():
+    L = _lod_lib()
+    if not hasattr(L, "_hier_ready"):
+        d = C.POINTER(C.c_double)
+        f = C.POINTER(C.c_float)
+        i32 = C.POINTER(C.c_int32)
+        u8 = C.POINTER(C.c_uint8)
+        i64 = C.POINTER(C.c_int64)
+        L.orc_hier_analyze.argtypes = [C.c_int64, C.c_int64, C.c_int, f, d, d, d, d, d, i32, i32, u8, d, d, i32,
+                                       C.c_double, C.c_double, d, u8, i64]
+        L.orc_hier_analyze.restype = C.c_int
+        L.orc_hier_refine.argtypes = [C.c_int64, d, d, i32, u8, d, d, i32, C.c_double, C.c_double, u8]
+        L.orc_hier_refine.restype = C.c_int64
+        L._hier_ready = True
+    return L
+
+
+class HierState:
+    """Node state of the progressive hierarchy in natural layouts, capacity
+    `cap` rows, the first n_nodes in use: means32 [cap,3] float32, means /
+    log_scales [cap,3], quats [cap,4], opa_logits [cap], sh [cap,3,nc]
+    (float64), parent [cap] int32 (-1: root), child [cap,4] int32 (-1: none),
+    active [cap] uint8."""
+
+    def __init__(self, scene, cap):
+        n = scene.n
+        self.nc = (scene.sh_degree + 1) ** 2
+        self.cap, self.n_nodes = int(cap), n
+        self.means32 = np.zeros((cap, 3), np.float32)
+        self.means32[:n] = scene.means
+        self.means = np.zeros((cap, 3))
+        self.means[:n] = scene.means
+        self.log_scales = np.zeros((cap, 3))
+        self.log_scales[:n] = scene.log_scales
+        self.quats = np.zeros((cap, 4))
+        self.quats[:, 0] = 1.0
+        self.quats[:n] = scene.quats
+        self.opa_logits = np.zeros(cap)
+        self.opa_logits[:n] = scene.opa_logits
+        self.sh = np.zeros((cap, 3, self.nc))
+        self.sh[:n] = scene.sh
+        self.parent = np.full(cap, -1, np.int32)
+        self.child = np.full((cap, 4), -1, np.int32)
+        self.active = np.zeros(cap, np.uint8)
+        self.active[:n] = 1
+
+    def copy(self):
+        c = HierState.__new__(HierState)
+        c.__dict__ = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in self.__dict__.items()}
+        return c
+
+
+def _cam_args(cam):
+    pose = _f64(cam.pose12())
+    intr = _f64([cam.fx, cam.fy, cam.cx, cam.cy])
+    wh = np.ascontiguousarray(np.array([cam.width, cam.height], np.int32))
+    return pose, intr, wh
+
+
+def hier_analyze(st: HierState, cam, znear=0.2, tau_l=0.5) -> Dict:
+    """One analysis of the progressive hierarchy from `cam` (updates st in
+    place).  Returns info (n_nodes, triggered, candidates, active, pulled,
+    groups, grouped), the screen sizes S and the ambiguity flags."""
+    L = _hier_lib()
+    nsh = 3 * st.nc
+    S = np.zeros(st.cap)
+    amb = np.zeros(st.cap, np.uint8)
+    info = np.zeros(8, np.int64)
+    pose, intr, wh = _cam_args(cam)
+    sh = np.ascontiguousarray(st.sh.reshape(st.cap, nsh))
+    rc = L.orc_hier_analyze(st.n_nodes, st.cap, nsh, st.means32.ctypes.data_as(C.POINTER(C.c_float)),
+                            _p(st.means), _p(st.log_scales), _p(st.quats), _p(st.opa_logits), _p(sh),
+                            st.parent.ctypes.data_as(C.POINTER(C.c_int32)),
+                            st.child.ctypes.data_as(C.POINTER(C.c_int32)),
+                            st.active.ctypes.data_as(C.POINTER(C.c_uint8)), _p(pose), _p(intr),
+                            wh.ctypes.data_as(C.POINTER(C.c_int32)), float(znear), float(tau_l), _p(S),
+                            amb.ctypes.data_as(C.POINTER(C.c_uint8)), info.ctypes.data_as(C.POINTER(C.c_int64)))
+    assert rc == 0, "hierarchy capacity exceeded"
+    st.sh[:] = sh.reshape(st.cap, 3, st.nc)
+    st.n_nodes = int(info[0])
+    names = ("n_nodes", "triggered", "candidates", "active", "pulled", "groups", "grouped")
+    return {"info": {k: int(v) for k, v in zip(names, info)}, "S": S, "amb": amb}
+
+
+def hier_refine(st: HierState, cam, znear=0.2, tau_h=1.0):
+    """Reload: refinement passes of st.active for `cam` (in place).  Returns
+    the number of nodes replaced by their children and the ambiguity flags."""
+    L = _hier_lib()
+    amb = np.zeros(max(1, st.n_nodes), np.uint8)
+    pose, intr, wh = _cam_args(cam)
+    k = L.orc_hier_refine(st.n_nodes, _p(st.means), _p(st.log_scales), st.child.ctypes.data_as(C.POINTER(C.c_int32)),
+                          st.active.ctypes.data_as(C.POINTER(C.c_uint8)), _p(pose), _p(intr),
+                          wh.ctypes.data_as(C.POINTER(C.c_int32)), float(znear), float(tau_h),
+                          amb.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return int(k), amb
+
+
+def hier_view_cut(st: HierState, cam, znear=0.2, tau_h=1.0) -> np.ndarray:
+    """The nodes a render from `cam` uses: the refinement of a copy of the
+    active set (the state is not changed)."""
+    c = st.copy()
+    hier_refine(c, cam, znear, tau_h)
+    return c.active[:st.n_nodes].copy()

@@ -314,3 +314,277 @@ void orc_lod_cut(int64_t N, int64_t n_leaf, const double* mu, const double* lsc,
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Progressive hierarchy (Sec. 6.1 "Adaptive Gaussian Merging and Retrieval",
+// Sec. 6.2): an active set of nodes (leaves and merged intermediate nodes)
+// that is a cut of the forest (every leaf has exactly one active node on its
+// path to its root), coarsened when a keyframe is analysed and refined where
+// a view needs it.  Nodes hold Gaussian parameters, a parent id (-1: root)
+// and up to 4 child ids (-1: none).
+//
+// Steps of one analysis from a keyframe's camera, in the paper's order:
+//   1. screen size S_i = f_x * 3 * max_k scale_k / t_z of every active node
+//      (+inf at or behind the near plane); candidates: active, S_i < tau_l
+//      (tau_l = 0.5 px);
+//   2. merging runs only when more than 20% of the active nodes are
+//      candidates (5 |C| > |A|);
+//   3. pull: an inactive parent all of whose children are candidates becomes
+//      active again and its children inactive (no new node);
+//   4. the remaining candidates without a parent are grouped with their 3
+//      nearest candidates (groups of up to 4): candidates in Morton order of
+//      their means (10 bits per axis over the candidates' bounding box,
+//      single precision, ties by index), cut into chunks of 64 consecutive
+//      candidates; within a chunk the 3 nearest by squared distance of the
+//      single-precision means (summed x, y, z in that order; ties by Morton
+//      position); then, in Morton order, a candidate not yet grouped takes
+//      those of its 3 nearest that are not yet grouped (a candidate left
+//      alone stays ungrouped and available to later ones);
+//   5. each group of 2-4 becomes a new parent node (moment-matching merge,
+//      as the static hierarchy), active, with the children inactive; new
+//      nodes are numbered after the existing ones in Morton order of their
+//      first child.
+// Readings: the paper's "4 closest" are the candidate and its 3 nearest; its
+// KL-divergence merge is read as the moment-matching merge; its fast KNN is
+// exact within chunks of 64 Morton-consecutive candidates.
+// Reload (Sec. 6.1, tau_h = 1): an active node with children that lies in
+// view (t_z > znear and its projected centre within the image widened by S)
+// and has S > tau_h is replaced in the active set by its children, repeated
+// until no node changes.  The view cut of a render is that refinement
+// applied to a copy of the active set.
+// ===========================================================================
+namespace {
+
+constexpr int kHierChunk = 64;
+
+struct HierView {
+  double R[9], t[3], fx, fy, cx, cy, znear;
+  int W, H;
+};
+
+HierView hier_view(const double* pose12, const double* intr, const int32_t* wh, double znear) {
+  HierView v;
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) v.R[3 * r + c] = pose12[4 * r + c];
+    v.t[r] = pose12[4 * r + 3];
+  }
+  v.fx = intr[0]; v.fy = intr[1]; v.cx = intr[2]; v.cy = intr[3];
+  v.W = wh[0]; v.H = wh[1];
+  v.znear = znear;
+  return v;
+}
+
+// Screen size and the in-view test of node i.
+void hier_screen(const HierView& v, const double* mu, const double* lsc, int64_t i, double* S, bool* inview) {
+  const double* m = mu + 3 * i;
+  double tc[3];
+  for (int r = 0; r < 3; ++r) tc[r] = v.R[3 * r] * m[0] + v.R[3 * r + 1] * m[1] + v.R[3 * r + 2] * m[2] + v.t[r];
+  if (!(tc[2] > v.znear)) {
+    *S = std::numeric_limits<double>::infinity();
+    *inview = false;
+    return;
+  }
+  const double smax = std::exp(std::max(lsc[3 * i], std::max(lsc[3 * i + 1], lsc[3 * i + 2])));
+  *S = v.fx * 3.0 * smax / tc[2];
+  const double u = v.fx * tc[0] / tc[2] + v.cx, w = v.fy * tc[1] / tc[2] + v.cy;
+  *inview = u >= -*S && u <= v.W + *S && w >= -*S && w <= v.H + *S;
+}
+
+bool near_rel(double a, double b, double rel) { return std::fabs(a - b) <= rel * std::fabs(b); }
+
+// Refinement passes (each pass: every expandable active node with children,
+// found on the state before the pass, is replaced by its children).
+int64_t hier_refine_passes(int64_t n_nodes, const double* mu, const double* lsc, const int32_t* child,
+                           uint8_t* active, const HierView& v, double tau_h, uint8_t* amb) {
+  int64_t changed = 0;
+  for (int pass = 0; pass < 64; ++pass) {
+    std::vector<int64_t> expand;
+    for (int64_t i = 0; i < n_nodes; ++i) {
+      if (!active[i] || child[4 * i] < 0) continue;
+      double S;
+      bool in;
+      hier_screen(v, mu, lsc, i, &S, &in);
+      if (amb && std::isfinite(S) && near_rel(S, tau_h, 1e-5)) amb[i] = 1;
+      if (in && S > tau_h) expand.push_back(i);
+    }
+    if (expand.empty()) break;
+    for (int64_t i : expand) {
+      active[i] = 0;
+      for (int k = 0; k < 4; ++k)
+        if (child[4 * i + k] >= 0) active[child[4 * i + k]] = 1;
+    }
+    changed += (int64_t)expand.size();
+  }
+  return changed;
+}
+
+}  // namespace
+
+extern "C" {
+
+// One analysis of the progressive hierarchy from a camera (steps 1-5 above).
+// Node state of capacity `cap` rows, n_nodes in use: means32 [cap][3]
+// (float; rewritten for new nodes), mu, lsc [cap][3], quat [cap][4], opl
+// [cap], sh [cap][nsh] (double, natural layouts; new nodes appended),
+// parent [cap], child [cap][4], active [cap] (updated).  pose12 [R | t],
+// intr (fx, fy, cx, cy), wh (W, H).  S_out [cap]: screen sizes of the nodes
+// active before the step (NaN elsewhere); amb [cap]: 1 where S lies within
+// 1e-5 of tau_l (a decision single precision may take either way).
+// info [8]: new n_nodes, triggered, candidates, active before, pulled parents,
+// groups, grouped candidates, 0.  Returns 0, or 1 if the capacity is too small.
+int orc_hier_analyze(int64_t n_nodes, int64_t cap, int nsh, float* means32, double* mu, double* lsc, double* quat,
+                     double* opl, double* sh, int32_t* parent, int32_t* child, uint8_t* active,
+                     const double* pose12, const double* intr, const int32_t* wh, double znear, double tau_l,
+                     double* S_out, uint8_t* amb, int64_t* info) {
+  const HierView v = hier_view(pose12, intr, wh, znear);
+  std::memset(info, 0, 8 * sizeof(int64_t));
+  info[0] = n_nodes;
+  // 1. screen sizes and candidates
+  std::vector<uint8_t> cand((size_t)n_nodes, 0);
+  int64_t nA = 0, nC = 0;
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    S_out[i] = std::numeric_limits<double>::quiet_NaN();
+    amb[i] = 0;
+    if (!active[i]) continue;
+    ++nA;
+    bool in;
+    hier_screen(v, mu, lsc, i, &S_out[i], &in);
+    if (std::isfinite(S_out[i]) && near_rel(S_out[i], tau_l, 1e-5)) amb[i] = 1;
+    if (S_out[i] < tau_l) {
+      cand[i] = 1;
+      ++nC;
+    }
+  }
+  info[2] = nC;
+  info[3] = nA;
+  // 2. the trigger: more than 20% of the active nodes
+  if (!(5 * nC > nA)) return 0;
+  info[1] = 1;
+  // 3. pull: inactive parents whose children are all candidates
+  std::vector<int64_t> pulled;
+  for (int64_t p = 0; p < n_nodes; ++p) {
+    if (active[p] || child[4 * p] < 0) continue;
+    bool all = true;
+    for (int k = 0; k < 4; ++k) {
+      const int32_t c = child[4 * p + k];
+      if (c >= 0 && !cand[c]) all = false;
+    }
+    if (all) pulled.push_back(p);
+  }
+  for (int64_t p : pulled) {
+    active[p] = 1;
+    for (int k = 0; k < 4; ++k) {
+      const int32_t c = child[4 * p + k];
+      if (c >= 0) {
+        active[c] = 0;
+        cand[c] = 0;
+      }
+    }
+  }
+  info[4] = (int64_t)pulled.size();
+  // 4. grouping of the remaining parentless candidates
+  std::vector<int64_t> G;
+  for (int64_t i = 0; i < n_nodes; ++i)
+    if (cand[i] && parent[i] < 0) G.push_back(i);
+  std::vector<float> gm(3 * G.size());
+  for (size_t j = 0; j < G.size(); ++j)
+    for (int a = 0; a < 3; ++a) gm[3 * j + a] = means32[3 * G[j] + a];
+  std::vector<uint32_t> code;
+  morton_codes((int64_t)G.size(), gm.data(), code);
+  std::vector<int64_t> ord(G.size());
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return code[a] < code[b]; });
+  std::vector<std::vector<int64_t>> groups;  // node ids, leader first
+  for (size_t c0 = 0; c0 < ord.size(); c0 += kHierChunk) {
+    const size_t len = std::min((size_t)kHierChunk, ord.size() - c0);
+    std::vector<int> knn(3 * len, -1);
+    for (size_t a = 0; a < len; ++a) {
+      const float* pa = &gm[3 * ord[c0 + a]];
+      float best[3] = {0, 0, 0};
+      int nb = 0;
+      for (size_t b = 0; b < len; ++b) {
+        if (b == a) continue;
+        const float* pb = &gm[3 * ord[c0 + b]];
+        const float dx = pb[0] - pa[0], dy = pb[1] - pa[1], dz = pb[2] - pa[2];
+        float d = dx * dx;
+        d = d + dy * dy;
+        d = d + dz * dz;
+        // insert (d, b) into the sorted top-3 (ties: smaller position first,
+        // as b increases)
+        int pos = nb;
+        while (pos > 0 && d < best[pos - 1]) --pos;
+        if (pos >= 3) continue;
+        for (int q = std::min(nb, 2); q > pos; --q) {
+          best[q] = best[q - 1];
+          knn[3 * a + q] = knn[3 * a + q - 1];
+        }
+        best[pos] = d;
+        knn[3 * a + pos] = (int)b;
+        nb = std::min(nb + 1, 3);
+      }
+    }
+    std::vector<uint8_t> taken(len, 0);
+    for (size_t a = 0; a < len; ++a) {
+      if (taken[a]) continue;
+      std::vector<int64_t> g = {G[ord[c0 + a]]};
+      taken[a] = 1;
+      for (int q = 0; q < 3; ++q) {
+        const int b = knn[3 * a + q];
+        if (b >= 0 && !taken[b]) {
+          taken[b] = 1;
+          g.push_back(G[ord[c0 + b]]);
+        }
+      }
+      if (g.size() >= 2) {
+        groups.push_back(g);
+      } else {
+        taken[a] = 0;  // alone: stays available to later candidates
+      }
+    }
+  }
+  // 5. merge each group into a new active parent
+  if (n_nodes + (int64_t)groups.size() > cap) return 1;
+  int64_t grouped = 0;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const std::vector<int64_t>& g = groups[gi];
+    const int k = (int)g.size();
+    const int64_t out = n_nodes + (int64_t)gi;
+    std::vector<double> m(3 * k), l(3 * k), q(4 * k), o(k), s((size_t)k * nsh);
+    for (int i = 0; i < k; ++i) {
+      const int64_t c = g[i];
+      for (int a = 0; a < 3; ++a) { m[3 * i + a] = mu[3 * c + a]; l[3 * i + a] = lsc[3 * c + a]; }
+      for (int a = 0; a < 4; ++a) q[4 * i + a] = quat[4 * c + a];
+      o[i] = opl[c];
+      for (int j = 0; j < nsh; ++j) s[(size_t)i * nsh + j] = sh[c * nsh + j];
+    }
+    double cov6[6];
+    merge(k, m.data(), l.data(), q.data(), o.data(), s.data(), nsh, mu + 3 * out, cov6, lsc + 3 * out,
+          quat + 4 * out, opl + out, sh + out * nsh);
+    for (int a = 0; a < 3; ++a) means32[3 * out + a] = (float)mu[3 * out + a];
+    parent[out] = -1;
+    active[out] = 1;
+    for (int i = 0; i < 4; ++i) child[4 * out + i] = i < k ? (int32_t)g[i] : -1;
+    for (int64_t c : g) {
+      parent[c] = (int32_t)out;
+      active[c] = 0;
+    }
+    grouped += k;
+  }
+  info[0] = n_nodes + (int64_t)groups.size();
+  info[5] = (int64_t)groups.size();
+  info[6] = grouped;
+  return 0;
+}
+
+// Reload (Sec. 6.1): refinement passes of the active set for one view.
+// Returns the number of nodes replaced by their children; amb [n_nodes]
+// marks nodes whose S lies within 1e-5 of tau_h.
+int64_t orc_hier_refine(int64_t n_nodes, const double* mu, const double* lsc, const int32_t* child,
+                        uint8_t* active, const double* pose12, const double* intr, const int32_t* wh, double znear,
+                        double tau_h, uint8_t* amb) {
+  const HierView v = hier_view(pose12, intr, wh, znear);
+  for (int64_t i = 0; i < n_nodes; ++i) amb[i] = 0;
+  return hier_refine_passes(n_nodes, mu, lsc, child, active, v, tau_h, amb);
+}
+
+}  // extern "C"

@@ -3,20 +3,22 @@
 // [start, end) range of each tile.
 //
 // A counting sort by tile followed by a sort of each tile's own list:
-//   1. an exclusive scan of the per-(view, Gaussian) tile counts gives every
-//      visible splat a contiguous block of pair slots (pair_off, emission
-//      order: what the backward indexes its per-pair gradients by);
-//   2. every pair takes a place in its tile with one shared-counter atomic
-//      (the counters live in the ranges array);
-//   3. a scan over the tiles turns the counts into list starts; every pair
-//      writes its (depth bits, Gaussian id) key at start + place;
-//   4. one CTA per tile sorts its list in shared memory (bitonic network, up
-//      to kShortList keys; longer lists take a CTA-wide stable radix sort
-//      through global memory) and writes the ids and the tile's range.
+//   1. a single-pass exclusive scan (decoupled look-back) of the
+//      per-(view, Gaussian) tile counts gives every visible splat a
+//      contiguous block of pair slots (pair_off, emission order: what the
+//      backward indexes its per-pair gradients by), and
+//   2. in the same launch every pair takes a place in its tile with one
+//      shared-counter atomic (the counters live in the ranges array);
+//   3. one CTA scans the tiles' counts into list starts (and, when asked,
+//      orders the tiles longest list first); every pair writes its
+//      (depth bits, Gaussian id) key at start + place;
+//   4. one CTA per tile sorts its list in shared memory (stable radix passes,
+//      up to kShortList keys; longer lists go through global memory) and
+//      writes the ids and the tile's range.
 // Within a tile every Gaussian appears once, so (depth bits, id) keys are
 // distinct and the sorted list is unique: the atomics' order never shows.
 // This is the order of one sort of 64-bit (tile, depth) keys with depth ties
-// in id order, with ~40 bytes moved per pair and a fixed dozen launches.
+// in id order, with ~40 bytes moved per pair in five launches.
 //
 // Every count (visible items, pairs) stays in device memory: kernels are
 // launched for the capacity and read the live count, so the whole stage runs
@@ -267,17 +269,11 @@ __global__ void k_init_counts(uint32_t* counts, uint32_t* scalars, uint32_t m, u
   counts[0] = 0; counts[1] = 0; counts[2] = 0; counts[3] = 0;
 }
 
-__global__ void k_pair_status(uint32_t* counts, int64_t cap) {
-  const uint32_t K = counts[1];
-  if ((int64_t)K > cap) counts[2] |= kStatusCapacity;
-  counts[3] = (int64_t)K > cap ? (uint32_t)cap : K;
-}
-
 struct PairArgs {
   const uint32_t* touched;
   const uint2* rect;
   const float* depth;
-  const uint32_t* pair_off;  // emission offset of every (view, Gaussian)
+  uint32_t* pair_off;        // emission offset of every (view, Gaussian)
   uint32_t* counts;
   int64_t n;
   int64_t cap;
@@ -287,30 +283,26 @@ struct PairArgs {
 };
 
 // Warp-cooperative walk over the pairs of 32 consecutive (view, Gaussian)
-// items: the warp scans the items' pair counts and its lanes take the pairs
-// 32 at a time, each finding its item by a binary search over the scan, so
-// the lanes stay busy whatever the mix of small and large splats and every
-// pair's memory operations of a round are in flight together.  Pairs of an
-// item are its rect's tiles in row-major order.
+// items starting at j0: the warp scans the items' pair counts and its lanes
+// take the pairs 32 at a time, each finding its item by a binary search over
+// the scan, so the lanes stay busy whatever the mix of small and large splats
+// and every pair's memory operations of a round are in flight together.
+// Pairs of an item are its rect's tiles in row-major order.  `off` is the
+// lane's item's first pair slot (its pair_off).  Returns the visible items of
+// the group (touched > 0).
 // PLACE: take each pair's place in its tile (count the tile, note the place);
 // otherwise write its key at the tile's start + place.
 template <bool PLACE>
-__global__ void __launch_bounds__(256) k_pairs(const PairArgs a, const ViewTable vt) {
+__device__ __forceinline__ uint32_t warp_pairs(const PairArgs& a, const ViewTable& vt, int64_t j0, uint32_t off) {
   const int64_t m = a.n * vt.views;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int64_t j0 = ((int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
-  if (j0 >= m) return;  // warp-uniform
   const int64_t j = j0 + lane;
   bool ok = j < m && a.touched[j] > 0u;
-  if (PLACE) {
-    const unsigned vis = __ballot_sync(full, ok);
-    if (lane == 0 && vis) atomicAdd(&a.counts[0], (uint32_t)__popc(vis));
-  }
-  uint32_t off = 0, x0y0 = 0, w = 1, cnt = 0, key_hi = 0, tb = 0, tx_n = 1, gid = 0;
+  const uint32_t vis = (uint32_t)__popc(__ballot_sync(full, ok));
+  uint32_t x0y0 = 0, w = 1, cnt = 0, key_hi = 0, tb = 0, tx_n = 1, gid = 0;
   if (ok) {
     const int v = (int)(j / a.n);
-    off = a.pair_off[j];
     const uint2 rc = a.rect[j];
     const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
     if (x1 >= vt.v[v].TX || y1 >= vt.v[v].TY || x0 > x1 || y0 > y1) {
@@ -364,6 +356,137 @@ __global__ void __launch_bounds__(256) k_pairs(const PairArgs a, const ViewTable
       }
     }
   }
+  return vis;
+}
+
+// One warp per 32 items (the key pass, and the place pass of the multi-kernel
+// path): offsets from pair_off.
+template <bool PLACE>
+__global__ void __launch_bounds__(256) k_pairs(const PairArgs a, const ViewTable vt) {
+  const int64_t m = a.n * vt.views;
+  const int64_t j0 = ((int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  if (j0 >= m) return;  // warp-uniform
+  const int64_t j = j0 + (threadIdx.x & 31);
+  const uint32_t off = j < m ? a.pair_off[j] : 0u;
+  const uint32_t vis = warp_pairs<PLACE>(a, vt, j0, off);
+  if (PLACE && (threadIdx.x & 31) == 0 && vis) atomicAdd(&a.counts[0], vis);
+}
+
+// ---------------------------------------------------------------------------
+// Single-pass scan of the items' tile counts with decoupled look-back, fused
+// with the place pass.  Each CTA takes the next partition of 2048 items from
+// a counter (so a CTA only ever waits for partitions taken before it, whose
+// CTAs are already running), scans its counts, publishes its total, finds
+// its prefix from the published words of the partitions before it (a warp
+// reads 32 of them at a time), publishes its inclusive prefix, writes the
+// pair offsets and then places its items' pairs in their tiles.  The waits
+// are bounded (kLookbackNs of %globaltimer): on expiry the CTA sets status
+// bit 4 in counts[2] and carries on with a wrong prefix (the result is then
+// flagged invalid, the launch still ends).
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kFlagAgg = 1ull << 32, kFlagInc = 2ull << 32;
+constexpr uint32_t kStatusTimeout = 16u;
+constexpr unsigned long long kLookbackNs = 2000000000ull;  // 2 s
+
+struct ScanPlaceArgs {
+  PairArgs p;
+  unsigned long long* state;  // [parts] look-back words (flag << 32 | value), zero at launch
+  uint32_t* ticket;           // partition counter, zero at launch
+  uint32_t parts;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_place(const ScanPlaceArgs a, const ViewTable vt) {
+  __shared__ uint32_t s_warp[kThreads / 32 + 1];
+  __shared__ uint32_t s_part, s_prefix, s_vis;
+  __shared__ uint32_t s_off[kItemsPerBlock];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t m = a.p.n * vt.views;
+  if (threadIdx.x == 0) {
+    s_part = atomicAdd(a.ticket, 1u);
+    s_vis = 0;
+  }
+  __syncthreads();
+  const uint32_t part = s_part;
+  const uint64_t pbase = (uint64_t)part * kItemsPerBlock;
+  // thread t owns the contiguous items [pbase + t*kIPT, pbase + (t+1)*kIPT)
+  const uint64_t base = pbase + (uint64_t)threadIdx.x * kIPT;
+  uint32_t x[kIPT];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int r = 0; r < kIPT; ++r) {
+    x[r] = (int64_t)(base + r) < m ? a.p.touched[base + r] : 0u;
+    sum += x[r];
+  }
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan(sum, s_warp, &total);
+  if (warp == 0) {
+    uint32_t prefix = 0;
+    if (part == 0) {
+      if (lane == 0) *(volatile unsigned long long*)&a.state[0] = kFlagInc | total;
+    } else {
+      if (lane == 0) *(volatile unsigned long long*)&a.state[part] = kFlagAgg | total;
+      int64_t p = (int64_t)part - 1;
+      const unsigned long long t0 = global_ns();
+      for (;;) {
+        const int64_t idx = p - lane;
+        const unsigned long long wd =
+            idx >= 0 ? *(volatile const unsigned long long*)&a.state[idx] : kFlagInc;  // none before the first
+        const uint32_t flag = (uint32_t)(wd >> 32);
+        const unsigned inc = __ballot_sync(0xffffffffu, flag == 2u);
+        const unsigned ready = __ballot_sync(0xffffffffu, flag != 0u);
+        const int first = inc ? __ffs(inc) - 1 : 31;            // the closest inclusive word, else all 32
+        const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+        if ((ready & need) != need) {  // a partition before this one has not published yet
+          if (global_ns() - t0 > kLookbackNs) {
+            if (lane == 0) atomicOr(&a.p.counts[2], kStatusTimeout);
+            break;
+          }
+          __nanosleep(64);
+          continue;
+        }
+        uint32_t v = lane <= first ? (uint32_t)wd : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        prefix += v;
+        if (inc) break;
+        p -= 32;
+      }
+      if (lane == 0) *(volatile unsigned long long*)&a.state[part] = kFlagInc | (prefix + total);
+    }
+    if (lane == 0) s_prefix = prefix;
+  }
+  __syncthreads();
+  uint32_t run = s_prefix + excl;
+#pragma unroll
+  for (int r = 0; r < kIPT; ++r) {
+    s_off[threadIdx.x * kIPT + r] = run;
+    if ((int64_t)(base + r) < m) a.p.pair_off[base + r] = run;
+    run += x[r];
+  }
+  if (part == a.parts - 1 && threadIdx.x == kThreads - 1) {
+    // the last partition knows the number of pairs
+    const uint32_t K = run;
+    a.p.counts[1] = K;
+    if ((int64_t)K > a.p.cap) atomicOr(&a.p.counts[2], kStatusCapacity);
+    a.p.counts[3] = (int64_t)K > a.p.cap ? (uint32_t)a.p.cap : K;
+  }
+  __syncthreads();
+  // place pass: warp w takes the partition's 32-item groups w, w + 8, ...
+  uint32_t vis = 0;
+  for (int g = warp; g < kItemsPerBlock / 32; g += kThreads / 32) {
+    const int64_t j0 = (int64_t)(pbase + (uint64_t)g * 32);
+    if (j0 >= m) break;
+    vis += warp_pairs<true>(a.p, vt, j0, s_off[g * 32 + lane]);
+  }
+  if (lane == 0 && vis) atomicAdd(&s_vis, vis);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_vis) atomicAdd(&a.p.counts[0], s_vis);
 }
 
 struct TileSortArgs {
@@ -514,15 +637,80 @@ __global__ void __launch_bounds__(kThreads) k_tile_sort(const TileSortArgs a) {
   if (threadIdx.x == 0) a.ranges[2 * (uint64_t)t + 1] = start + cnt;
 }
 
-// Tiles in decreasing order of list length, bucketed by powers of two:
-// bucket 0 holds lists of >= 2^15 pairs, bucket 15 single pairs, bucket 16
-// the empty tiles.  Counting pass, then placement; the order within a bucket
-// follows the atomics and does not matter (tiles are independent).
+// Exclusive scan of the tiles' pair counts into their list starts, one CTA of
+// 1024 threads (thread t takes a contiguous run of tiles); with `order`, also
+// the tiles in decreasing order of list length (power-of-two buckets, empty
+// tiles last; the order within a bucket follows the shared-memory atomics and
+// does not matter).  For up to kTileScanMax tiles; more go through the
+// multi-kernel scan.
+constexpr int kTileScanThreads = 1024;
+constexpr int64_t kTileScanMax = 1ll << 18;
 constexpr int kOrderBuckets = 17;
 
 __device__ __forceinline__ int order_bucket(uint32_t len) {
   return len == 0 ? kOrderBuckets - 1 : 15 - min(15, 31 - __clz(len));
 }
+
+__global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(uint32_t* __restrict__ ranges, uint32_t tiles,
+                                                                 uint32_t* __restrict__ order) {
+  constexpr int NW = kTileScanThreads / 32;
+  __shared__ uint32_t s_warp[NW + 1];
+  __shared__ uint32_t s_count[kOrderBuckets], s_base[kOrderBuckets];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t per = (tiles + kTileScanThreads - 1) / kTileScanThreads;
+  const uint32_t lo = min(tiles, threadIdx.x * per), hi = min(tiles, lo + per);
+  if (threadIdx.x < kOrderBuckets) s_count[threadIdx.x] = 0;
+  uint32_t sum = 0;
+  for (uint32_t t = lo; t < hi; ++t) sum += ranges[2 * (uint64_t)t + 1];
+  // block-wide exclusive scan of the per-thread sums
+  uint32_t inc = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < NW ? s_warp[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += y;
+    }
+    if (lane < NW) s_warp[lane] = wi - w;
+  }
+  __syncthreads();
+  uint32_t run = s_warp[warp] + inc - sum;
+  for (uint32_t t = lo; t < hi; ++t) {
+    const uint32_t c = ranges[2 * (uint64_t)t + 1];
+    ranges[2 * (uint64_t)t] = run;
+    run += c;
+    if (order) atomicAdd(&s_count[order_bucket(c)], 1u);
+  }
+  if (!order) return;  // uniform
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t b0 = 0;
+    for (int b = 0; b < kOrderBuckets; ++b) {
+      s_base[b] = b0;
+      b0 += s_count[b];
+      s_count[b] = 0;
+    }
+  }
+  __syncthreads();
+  for (uint32_t t = lo; t < hi; ++t) {
+    const int b = order_bucket(ranges[2 * (uint64_t)t + 1]);
+    order[s_base[b] + atomicAdd(&s_count[b], 1u)] = t;
+  }
+}
+
+// Tiles in decreasing order of list length, bucketed by powers of two:
+// bucket 0 holds lists of >= 2^15 pairs, bucket 15 single pairs, bucket 16
+// the empty tiles.  Counting pass, then placement; the order within a bucket
+// follows the atomics and does not matter (tiles are independent).  The
+// multi-kernel form, for more tiles than the single-CTA scan takes.
 
 __global__ void __launch_bounds__(kThreads) k_order_count(const uint32_t* __restrict__ ranges, uint32_t tiles,
                                                           uint32_t* __restrict__ bucket_count) {
@@ -616,12 +804,16 @@ gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b
 // ---------------------------------------------------------------------------
 struct BinWs {
   uint32_t* scalars;  // [0] = item count, [1] = tile count, [2] = scanned tile total,
+                      // [3] = partition counter of the item scan,
                       // [32, 49) tile-order bucket counts, [64, 81) their cursors
+  unsigned long long* state;  // look-back words of the item scan, one per 2048 items
   uint32_t* slot;
   uint64_t *keys_a, *keys_b;
   void* scan;
   size_t bytes;
 };
+
+static int64_t scan_parts(int64_t m) { return (m + kItemsPerBlock - 1) / kItemsPerBlock; }
 
 static BinWs bin_layout(char* base, int64_t m, int64_t cap) {
   BinWs w{};
@@ -633,10 +825,11 @@ static BinWs bin_layout(char* base, int64_t m, int64_t cap) {
   };
   const size_t c = (size_t)std::max<int64_t>(1, cap);
   w.scalars = (uint32_t*)take(128 * sizeof(uint32_t));
+  w.state = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)std::max<int64_t>(1, scan_parts(m)));
   w.slot = (uint32_t*)take(sizeof(uint32_t) * c);
   w.keys_a = (uint64_t*)take(sizeof(uint64_t) * c);
   w.keys_b = (uint64_t*)take(sizeof(uint64_t) * c);
-  w.scan = take(scan_workspace(std::max(m, kMaxScanTiles)));
+  w.scan = take(scan_workspace(kMaxScanTiles));
   w.bytes = off;
   return w;
 }
@@ -651,9 +844,10 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   const int64_t cap = bins.capacity;
   BinWs w = bin_layout(static_cast<char*>(ws), m, cap);
   uint32_t* counts = bins.counts;
+  const bool one_cta_tile_scan = vt.total_tiles <= kTileScanMax;
   // the tile order (when asked for) is written on every path, from the final ranges
   auto finish = [&]() {
-    if (bins.tile_order && vt.total_tiles > 0) {
+    if (bins.tile_order && vt.total_tiles > 0 && !one_cta_tile_scan) {
       const unsigned og = (unsigned)std::min<int64_t>(592, (vt.total_tiles + kThreads - 1) / kThreads);
       k_order_count<<<og, kThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, w.scalars + 32);
       k_order_place<<<og, kThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, w.scalars + 32,
@@ -665,19 +859,30 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   // the ranges array holds each tile's (start, count) until the tile is sorted
   if (cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)bins.num_tiles, s) != cudaSuccess)
     return check_launch("memset ranges");
-  if (m == 0) return finish();
-  // 1. pair slots per (view, Gaussian): exclusive scan of the tile counts
-  gs_status st = launch_scan(sp.touched, 1, bins.pair_off, 1, w.scalars, m, counts + 1, w.scan, s);
-  if (st != GS_OK) return st;
-  k_pair_status<<<1, 1, 0, s>>>(counts, cap);
-  if (cap == 0 || vt.total_tiles == 0) return finish();
+  if (m == 0) {
+    if (one_cta_tile_scan && bins.tile_order && vt.total_tiles > 0)
+      k_tile_scan<<<1, kTileScanThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, bins.tile_order);
+    return finish();
+  }
+  // 1. + 2. pair slots per (view, Gaussian) (single-pass scan of the tile
+  // counts) and a place in its tile for every pair, in one launch
+  const int64_t parts = scan_parts(m);
+  if (cudaMemsetAsync(w.state, 0, sizeof(unsigned long long) * (size_t)parts, s) != cudaSuccess)
+    return check_launch("memset scan state");
   PairArgs pa{sp.touched, reinterpret_cast<const uint2*>(sp.rect), sp.depth, bins.pair_off, counts, sp.n, cap,
               bins.ranges, w.slot, w.keys_a};
-  const unsigned pgrid = grid_for(m, 256);  // 8 warps of 32 items per block
-  // 2. a place in its tile for every pair; 3. list starts; keys at their places
-  k_pairs<true><<<pgrid, 256, 0, s>>>(pa, vt);
-  st = launch_scan(bins.ranges + 1, 2, bins.ranges, 2, w.scalars + 1, vt.total_tiles, w.scalars + 2, w.scan, s);
-  if (st != GS_OK) return st;
+  ScanPlaceArgs sa{pa, w.state, w.scalars + 3, (uint32_t)parts};
+  k_scan_place<<<(unsigned)parts, kThreads, 0, s>>>(sa, vt);
+  if (cap == 0 || vt.total_tiles == 0) return finish();
+  // 3. list starts (and the longest-first order); keys at their places
+  if (one_cta_tile_scan) {
+    k_tile_scan<<<1, kTileScanThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, bins.tile_order);
+  } else {
+    gs_status st = launch_scan(bins.ranges + 1, 2, bins.ranges, 2, w.scalars + 1, vt.total_tiles, w.scalars + 2,
+                               w.scan, s);
+    if (st != GS_OK) return st;
+  }
+  const unsigned pgrid = (unsigned)std::max<int64_t>(1, (m + 255) / 256);  // 8 warps of 32 items per block
   k_pairs<false><<<pgrid, 256, 0, s>>>(pa, vt);
   // 4. every tile's list by (depth bits, id)
   int id_bits = 1;

@@ -7,7 +7,7 @@ its autotuner picks, replayed from a captured CUDA graph.  Checked:
 - image windows of the replayed step, among them the ragged corner;
 - the replayed step's Adam update of sampled Gaussians' parameters and of
   random arena elements, given its gradient;
-- the gradients of sampled Gaussians and of the pose.  Each sampled Gaussian
+- the gradients of 40 sampled Gaussians and of the pose.  Each sampled Gaussian
   has a window covering its whole tile rect, and the windows are disjoint.
   The replayed step's parameters, pose and tile lists are kept, and its
   backward kernels run once more, with the step's own dL/dimage restricted
@@ -103,8 +103,11 @@ def test_graph_replayed_step_1m_720p(cuda_device):
                         cam.cy, W, H)
     rng = np.random.default_rng(11)
     rec = rast.splat_arrays()
-    samples = _disjoint_small_splats(rec, rng, 12, *rast.tile)
-    assert len(samples) >= 8
+    # 40 samples: many small splats are hidden (zero gradient on both sides)
+    # and a few barely visible ones have near-cancelling gradients, so the
+    # per-group normalisation needs a broad sample
+    samples = _disjoint_small_splats(rec, rng, 40, *rast.tile)
+    assert len(samples) >= 30
     wins = [w for _, w in samples] + [(W - 40, H - 24, 40, 24)] + \
         [(int(rng.integers(0, W - 48)), int(rng.integers(0, H - 48)), 48, 48) for _ in range(2)]
     ref = oracle.render(sc, [cam0] * len(wins), windows=wins, tile=rast.tile)
