@@ -384,6 +384,67 @@ GS_API gs_status gs_project_lod(const gs_params* nodes, int64_t n_leaf, const in
                                 const float* poses_dev, const gs_camera* cams, int32_t views,
                                 const gs_raster_cfg* cfg, gs_splats* out, gs_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Progressive hierarchy (Sec. 6.1 "Adaptive Gaussian Merging and Retrieval",
+ * Sec. 6.2): an active set of nodes (leaves and merged intermediate nodes)
+ * that is a cut of the forest; nodes live in the rows of the parameter arena
+ * (gs_grads layout, capacity rows), the first *n_nodes of them in use.
+ * Readings where the paper is silent or differs: groups are a candidate and
+ * its 3 nearest candidates (the paper's 4 closest), found exactly within
+ * chunks of 64 candidates consecutive in Morton order (its fast KNN); the
+ * KL-divergence merge is read as the moment-matching merge of
+ * gs_lod_build; a node is in view when t_z > znear and its projected centre
+ * lies within the image widened by its screen size.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+  int32_t* parent;    /* [capacity] parent node, -1 = root */
+  int32_t* child;     /* [capacity][4] child nodes, -1 = none */
+  uint8_t* active;    /* [capacity] 1 = in the active set */
+  uint32_t* n_nodes;  /* device word: arena rows in use (new nodes are appended) */
+  uint32_t* info;     /* optional device [8]: analyse: n_nodes, triggered, candidates, active,
+                         pulled parents, new groups, grouped candidates, status (1 = no room);
+                         refine: [0] = nodes replaced by their children */
+  int64_t capacity;   /* rows of the arena and of the arrays above */
+} gs_hier;
+
+/* Workspace bytes of gs_hier_analyze / gs_hier_refine. */
+GS_API size_t gs_hier_workspace(int64_t capacity);
+/* One analysis from a keyframe's camera (pose_dev: device float [12]
+ * world->camera, cam: host).  Screen size S = f_x 3 max scale / t_z of every
+ * active node (+inf at or behind znear); candidates S < tau_l (the paper's
+ * 0.5 px).  Only when more than 20% of the active nodes are candidates:
+ * inactive parents whose children are all candidates are pulled (active
+ * again, children inactive); the remaining candidates without a parent are
+ * grouped with their 3 nearest candidates (Morton order of their means, 10
+ * bits per axis over their bounding box, stable; chunks of 64; squared
+ * single-precision distances, ties by Morton position; greedy in Morton
+ * order, a candidate left alone stays ungrouped) and every group of 2-4
+ * becomes a new active node (moment-matching merge of its children, numbered
+ * after the existing nodes in Morton order of its first child) with its
+ * children inactive.  adam_m / adam_v (optional, gs_grads layout): the Adam
+ * moments of the arena, zeroed for every node whose active flag changes.  No
+ * host synchronisation; when the new nodes would not fit the capacity
+ * nothing is merged and info[7] bit 0 is set. */
+GS_API gs_status gs_hier_analyze(gs_grads* nodes, gs_hier* h, const gs_grads* adam_m, const gs_grads* adam_v,
+                                 const float* pose_dev, const gs_camera* cam, float znear, float tau_l, void* ws,
+                                 size_t ws_bytes, gs_stream stream);
+/* Reload (Sec. 6.1, tau_h = 1 px in the paper): up to `passes` passes; in each,
+ * every active node with children that is in view with S > tau_h (state
+ * before the pass) is replaced by its children.  Passes after one that
+ * changed nothing do nothing. */
+GS_API gs_status gs_hier_refine(gs_grads* nodes, gs_hier* h, const gs_grads* adam_m, const gs_grads* adam_v,
+                                const float* pose_dev, const gs_camera* cam, float znear, float tau_h,
+                                int32_t passes, void* ws, size_t ws_bytes, gs_stream stream);
+/* gs_project over the first nodes->n rows with each view's cut of the
+ * hierarchy: a node is projected iff it belongs to the active set refined for
+ * that view (the reload applied without changing the state): an active node
+ * that is not expandable (no children, not in view, or S <= tau_h), or an
+ * inactive one that is not expandable and whose path up to its first active
+ * ancestor consists of expandable nodes.  Other nodes are culled. */
+GS_API gs_status gs_project_hier(const gs_params* nodes, const gs_hier* h, float tau_h, const float* poses_dev,
+                                 const gs_camera* cams, int32_t views, const gs_raster_cfg* cfg, gs_splats* out,
+                                 gs_stream stream);
+
 /* Workspace bytes of gs_bin_sort. */
 GS_API size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity);
 

@@ -488,6 +488,25 @@ class HierState:
         self.active = np.zeros(cap, np.uint8)
         self.active[:n] = 1
 
+    @classmethod
+    def from_arrays(cls, nat, parent, child, active, n_nodes):
+        """A state from arrays of `cap` rows: nat = natural-layout parameters
+        (means, log_scales, quats, opa_logits, sh), the links and flags."""
+        st = cls.__new__(cls)
+        cap = len(parent)
+        st.nc = nat["sh"].shape[2]
+        st.cap, st.n_nodes = cap, int(n_nodes)
+        st.means = np.ascontiguousarray(nat["means"], np.float64)
+        st.means32 = np.ascontiguousarray(nat["means"], np.float32)
+        st.log_scales = np.ascontiguousarray(nat["log_scales"], np.float64)
+        st.quats = np.ascontiguousarray(nat["quats"], np.float64)
+        st.opa_logits = np.ascontiguousarray(nat["opa_logits"], np.float64)
+        st.sh = np.ascontiguousarray(nat["sh"], np.float64)
+        st.parent = np.ascontiguousarray(parent, np.int32)
+        st.child = np.ascontiguousarray(np.asarray(child).reshape(cap, 4), np.int32)
+        st.active = np.ascontiguousarray(active, np.uint8)
+        return st
+
     def copy(self):
         c = HierState.__new__(HierState)
         c.__dict__ = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in self.__dict__.items()}

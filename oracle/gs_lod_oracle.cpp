@@ -374,11 +374,15 @@ HierView hier_view(const double* pose12, const double* intr, const int32_t* wh, 
   return v;
 }
 
-// Screen size and the in-view test of node i.
-void hier_screen(const HierView& v, const double* mu, const double* lsc, int64_t i, double* S, bool* inview) {
+// Screen size and the in-view test of node i; *edge (optional) is set when
+// the in-view decision lies within 1e-4 px of an image edge (single
+// precision may take it either way).
+void hier_screen(const HierView& v, const double* mu, const double* lsc, int64_t i, double* S, bool* inview,
+                 bool* edge = nullptr) {
   const double* m = mu + 3 * i;
   double tc[3];
   for (int r = 0; r < 3; ++r) tc[r] = v.R[3 * r] * m[0] + v.R[3 * r + 1] * m[1] + v.R[3 * r + 2] * m[2] + v.t[r];
+  if (edge) *edge = std::fabs(tc[2] - v.znear) <= 1e-6 * v.znear;
   if (!(tc[2] > v.znear)) {
     *S = std::numeric_limits<double>::infinity();
     *inview = false;
@@ -388,6 +392,11 @@ void hier_screen(const HierView& v, const double* mu, const double* lsc, int64_t
   *S = v.fx * 3.0 * smax / tc[2];
   const double u = v.fx * tc[0] / tc[2] + v.cx, w = v.fy * tc[1] / tc[2] + v.cy;
   *inview = u >= -*S && u <= v.W + *S && w >= -*S && w <= v.H + *S;
+  if (edge) {
+    const double e = 1e-4 * (1.0 + *S);
+    *edge = *edge || std::fabs(u + *S) <= e || std::fabs(u - v.W - *S) <= e || std::fabs(w + *S) <= e ||
+            std::fabs(w - v.H - *S) <= e;
+  }
 }
 
 bool near_rel(double a, double b, double rel) { return std::fabs(a - b) <= rel * std::fabs(b); }
@@ -402,9 +411,9 @@ int64_t hier_refine_passes(int64_t n_nodes, const double* mu, const double* lsc,
     for (int64_t i = 0; i < n_nodes; ++i) {
       if (!active[i] || child[4 * i] < 0) continue;
       double S;
-      bool in;
-      hier_screen(v, mu, lsc, i, &S, &in);
-      if (amb && std::isfinite(S) && near_rel(S, tau_h, 1e-5)) amb[i] = 1;
+      bool in, edge;
+      hier_screen(v, mu, lsc, i, &S, &in, &edge);
+      if (amb && ((std::isfinite(S) && near_rel(S, tau_h, 1e-5)) || edge)) amb[i] = 1;
       if (in && S > tau_h) expand.push_back(i);
     }
     if (expand.empty()) break;

@@ -31,6 +31,7 @@ EXPORTED = (
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
     "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
     "gs_render_fused_workspace", "gs_render_fused", "gs_autotune_fused",
+    "gs_hier_workspace", "gs_hier_analyze", "gs_hier_refine", "gs_project_hier",
     "gs_ba_workspace_bytes", "gs_ba_solve",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
     "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_keyframe_weights", "gs_session_stats", "gs_session_read_params",
@@ -74,6 +75,11 @@ class GsBins(C.Structure):
     _fields_ = [("vals", C.c_void_p), ("ranges", C.c_void_p), ("pair_off", C.c_void_p),
                 ("keys", C.c_void_p), ("counts", C.c_void_p), ("capacity", C.c_int64),
                 ("num_tiles", C.c_int64), ("tile_order", C.c_void_p)]
+
+
+class GsHier(C.Structure):
+    _fields_ = [("parent", C.c_void_p), ("child", C.c_void_p), ("active", C.c_void_p), ("n_nodes", C.c_void_p),
+                ("info", C.c_void_p), ("capacity", C.c_int64)]
 
 
 class GsAdamGroup(C.Structure):
@@ -176,6 +182,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                   i64, vp, sz, vp]
     L.gs_autotune_fused.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsRasterCfg), P(GsSplats), P(GsBins), i64,
                                     vp, sz, vp, i32, vp, vp, vp, sz, i32, C.POINTER(C.c_float), vp]
+    L.gs_hier_workspace.argtypes = [i64]
+    L.gs_hier_workspace.restype = sz
+    L.gs_hier_analyze.argtypes = [P(GsGrads), P(GsHier), P(GsGrads), P(GsGrads), vp, P(GsCamera), C.c_float,
+                                  C.c_float, vp, sz, vp]
+    L.gs_hier_refine.argtypes = [P(GsGrads), P(GsHier), P(GsGrads), P(GsGrads), vp, P(GsCamera), C.c_float,
+                                 C.c_float, i32, vp, sz, vp]
+    L.gs_project_hier.argtypes = [P(GsParams), P(GsHier), C.c_float, vp, P(GsCamera), i32, P(GsRasterCfg),
+                                  P(GsSplats), vp]
     L.gs_sim3_update.argtypes = [P(GsGrads), vp, vp, i32, vp, vp]
     L.gs_keyframe_counts.argtypes = [vp, i64, i32, vp, vp]
     L.gs_lod_nodes.argtypes = [i64]
@@ -221,7 +235,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                  "gs_render_bwd",
                  "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
                  "gs_render_stats", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
-                 "gs_ba_solve", "gs_render_fused", "gs_autotune_fused"):
+                 "gs_ba_solve", "gs_render_fused", "gs_autotune_fused", "gs_hier_analyze", "gs_hier_refine",
+                 "gs_project_hier"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -295,6 +295,68 @@ gs_status gs_project_lod(const gs_params* nodes, int64_t n_leaf, const int32_t* 
   return launch_project(*nodes, poses_dev, vt, *cfg, *out, (cudaStream_t)stream, parent_dev, n_leaf, tau);
 }
 
+static gs_status check_hier(const gs_grads* nodes, const gs_hier* h) {
+  if (!nodes || !h) return fail(GS_ERR_INVALID, "NULL nodes or hierarchy");
+  gs_params view{nodes->means4, nodes->scale_opa, nodes->quat, nodes->sh, nodes->n, nodes->sh_degree,
+                 nodes->sh_stride};
+  gs_status st;
+  if ((st = check_params(&view)) != GS_OK) return st;
+  if (h->capacity < 1 || h->capacity > nodes->n || h->capacity >= (1ll << 31))
+    return fail(GS_ERR_INVALID, "hierarchy capacity must be 1..nodes->n");
+  if (!h->parent || !h->child || !h->active || !h->n_nodes)
+    return fail(GS_ERR_INVALID, "NULL hierarchy array");
+  return GS_OK;
+}
+
+size_t gs_hier_workspace(int64_t capacity) { return hier_workspace_bytes(std::max<int64_t>(1, capacity)); }
+
+gs_status gs_hier_analyze(gs_grads* nodes, gs_hier* h, const gs_grads* adam_m, const gs_grads* adam_v,
+                          const float* pose_dev, const gs_camera* cam, float znear, float tau_l, void* ws,
+                          size_t ws_bytes, gs_stream stream) {
+  GS_NVTX("gs_hier_analyze");
+  gs_status st;
+  if ((st = check_hier(nodes, h)) != GS_OK) return st;
+  if (!pose_dev || !cam) return fail(GS_ERR_INVALID, "NULL pose or camera");
+  if (!(znear > 0.f) || !(tau_l > 0.f)) return fail(GS_ERR_INVALID, "znear and tau_l must be > 0");
+  const size_t need = gs_hier_workspace(h->capacity);
+  if (!ws || ws_bytes < need) return fail(GS_ERR_OOM, "hier workspace: need %zu bytes, got %zu", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+  return launch_hier_analyze(*nodes, *h, adam_m, adam_v, pose_dev, *cam, znear, tau_l, ws, (cudaStream_t)stream);
+}
+
+gs_status gs_hier_refine(gs_grads* nodes, gs_hier* h, const gs_grads* adam_m, const gs_grads* adam_v,
+                         const float* pose_dev, const gs_camera* cam, float znear, float tau_h, int32_t passes,
+                         void* ws, size_t ws_bytes, gs_stream stream) {
+  GS_NVTX("gs_hier_refine");
+  gs_status st;
+  if ((st = check_hier(nodes, h)) != GS_OK) return st;
+  if (!pose_dev || !cam) return fail(GS_ERR_INVALID, "NULL pose or camera");
+  if (!(znear > 0.f) || !(tau_h > 0.f) || passes < 1 || passes > 64)
+    return fail(GS_ERR_INVALID, "znear, tau_h must be > 0 and passes 1..64");
+  const size_t need = gs_hier_workspace(h->capacity);
+  if (!ws || ws_bytes < need) return fail(GS_ERR_OOM, "hier workspace: need %zu bytes, got %zu", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+  return launch_hier_refine(*nodes, *h, adam_m, adam_v, pose_dev, *cam, znear, tau_h, passes, ws,
+                            (cudaStream_t)stream);
+}
+
+gs_status gs_project_hier(const gs_params* nodes, const gs_hier* h, float tau_h, const float* poses_dev,
+                          const gs_camera* cams, int32_t views, const gs_raster_cfg* cfg, gs_splats* out,
+                          gs_stream stream) {
+  GS_NVTX("gs_project_hier");
+  gs_status st;
+  if ((st = check_params(nodes)) != GS_OK) return st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
+  if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
+  if (!h || !h->parent || !h->child || !h->active || !h->n_nodes || h->capacity < nodes->n)
+    return fail(GS_ERR_INVALID, "hierarchy arrays must cover nodes->n rows");
+  if (!(tau_h > 0.f)) return fail(GS_ERR_INVALID, "tau_h must be > 0");
+  if ((st = check_splats(out, nodes->n, views)) != GS_OK) return st;
+  return launch_project(*nodes, poses_dev, vt, *cfg, *out, (cudaStream_t)stream, nullptr, 0, tau_h, h);
+}
+
 size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity) {
   return bin_sort_workspace_bytes(std::max<int64_t>(0, n) * std::max(0, views), std::max<int64_t>(0, capacity));
 }

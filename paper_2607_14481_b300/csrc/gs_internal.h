@@ -41,10 +41,21 @@ constexpr uint32_t kSchedKnown = 0x7u | (3u << 4) | (3u << 8) | (1u << 12);
 bool make_view_table(const gs_camera* cams, int views, ViewTable* vt, int tw = kTile, int th = kTile);
 
 // ---- kernels' host launchers (each enqueues on `s`, returns GS_OK or GS_ERR_CUDA)
-// parent != nullptr: level-of-detail cut (nodes [0, n_leaf) are leaves).
+// parent != nullptr: level-of-detail cut (nodes [0, n_leaf) are leaves);
+// hier != nullptr: the view cut of the progressive hierarchy at tau.
 gs_status launch_project(const gs_params& p, const float* poses, const ViewTable& vt,
                          const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s,
-                         const int32_t* parent = nullptr, int64_t n_leaf = 0, float tau = 0.f);
+                         const int32_t* parent = nullptr, int64_t n_leaf = 0, float tau = 0.f,
+                         const gs_hier* hier = nullptr);
+
+// Progressive hierarchy (gs_hier.cu).
+size_t hier_workspace_bytes(int64_t cap);
+gs_status launch_hier_analyze(const gs_grads& nodes, const gs_hier& h, const gs_grads* m, const gs_grads* v,
+                              const float* pose, const gs_camera& cam, float znear, float tau_l, void* ws,
+                              cudaStream_t s);
+gs_status launch_hier_refine(const gs_grads& nodes, const gs_hier& h, const gs_grads* m, const gs_grads* v,
+                             const float* pose, const gs_camera& cam, float znear, float tau_h, int passes, void* ws,
+                             cudaStream_t s);
 
 // Loop-closure update: Gaussian i moves with the Sim(3) of keyframe kf[i].
 gs_status launch_sim3_update(const gs_grads& p, const int32_t* kf, const float* sim3, int32_t num_kf,

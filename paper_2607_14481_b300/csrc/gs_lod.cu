@@ -24,15 +24,6 @@ namespace {
 
 constexpr int kLodThreads = 256;
 
-__device__ __forceinline__ uint32_t float_order(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-
-__device__ __forceinline__ float float_unorder(uint32_t u) {
-  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
-
 __global__ void k_lod_init(uint32_t* bbox, uint32_t* n_word, uint32_t n) {
   if (threadIdx.x < 3) {
     bbox[threadIdx.x] = 0xffffffffu;  // min (ordered)
@@ -72,22 +63,6 @@ __global__ void __launch_bounds__(kLodThreads) k_lod_bbox(const float4* __restri
   }
 }
 
-__device__ __forceinline__ uint32_t spread10(uint32_t v) {
-  v &= 0x3ffu;
-  v = (v | (v << 16)) & 0x030000ffu;
-  v = (v | (v << 8)) & 0x0300f00fu;
-  v = (v | (v << 4)) & 0x030c30c3u;
-  v = (v | (v << 2)) & 0x09249249u;
-  return v;
-}
-
-__device__ __forceinline__ uint32_t quantise10(float x, float lo, float scale) {
-  float f = floorf(__fmul_rn(__fsub_rn(x, lo), scale));
-  if (!(f >= 0.f)) f = 0.f;
-  if (f > 1023.f) f = 1023.f;
-  return (uint32_t)f;
-}
-
 // Morton code of every leaf (quantised in single precision) and its index.
 __global__ void __launch_bounds__(kLodThreads) k_lod_morton(const float4* __restrict__ means4, int64_t n,
                                                             const uint32_t* bbox, uint32_t* code, uint32_t* idx) {
@@ -118,70 +93,6 @@ struct MergeArgs {
   float* iws;             // [n1 + n2] 1 / sum of the weights
   int64_t n_leaf, n1, n2;
 };
-
-// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 (row-major A):
-// A = V diag(lam) V^T with the eigenvectors in the columns of V.
-__device__ void jacobi3(float* A, float* lam, float* V) {
-#pragma unroll
-  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.f : 0.f;
-  for (int sweep = 0; sweep < 8; ++sweep) {
-    const float off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
-    const float scale = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
-    if (!(off > 1e-14f * scale)) break;
-#pragma unroll
-    for (int pq = 0; pq < 3; ++pq) {
-      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
-      const float apq = A[3 * p + q];
-      if (apq == 0.f) continue;
-      const float theta = (A[3 * q + q] - A[3 * p + p]) / (2.f * apq);
-      const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-      const float c = 1.f / sqrtf(t * t + 1.f), s = t * c;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float akp = A[3 * k + p], akq = A[3 * k + q];
-        A[3 * k + p] = c * akp - s * akq;
-        A[3 * k + q] = s * akp + c * akq;
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float apk = A[3 * p + k], aqk = A[3 * q + k];
-        A[3 * p + k] = c * apk - s * aqk;
-        A[3 * q + k] = s * apk + c * aqk;
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float vkp = V[3 * k + p], vkq = V[3 * k + q];
-        V[3 * k + p] = c * vkp - s * vkq;
-        V[3 * k + q] = s * vkp + c * vkq;
-      }
-    }
-  }
-  lam[0] = A[0];
-  lam[1] = A[4];
-  lam[2] = A[8];
-}
-
-// Unit quaternion (w,x,y,z), w >= 0, of a rotation matrix (row-major).
-__device__ float4 rot_to_quat(const float* R) {
-  const float tr = R[0] + R[4] + R[8];
-  float w, x, y, z;
-  if (tr > 0.f) {
-    const float s = sqrtf(tr + 1.f) * 2.f;
-    w = 0.25f * s; x = (R[7] - R[5]) / s; y = (R[2] - R[6]) / s; z = (R[3] - R[1]) / s;
-  } else if (R[0] > R[4] && R[0] > R[8]) {
-    const float s = sqrtf(1.f + R[0] - R[4] - R[8]) * 2.f;
-    w = (R[7] - R[5]) / s; x = 0.25f * s; y = (R[1] + R[3]) / s; z = (R[2] + R[6]) / s;
-  } else if (R[4] > R[8]) {
-    const float s = sqrtf(1.f + R[4] - R[0] - R[8]) * 2.f;
-    w = (R[2] - R[6]) / s; x = (R[1] + R[3]) / s; y = 0.25f * s; z = (R[5] + R[7]) / s;
-  } else {
-    const float s = sqrtf(1.f + R[8] - R[0] - R[4]) * 2.f;
-    w = (R[3] - R[1]) / s; x = (R[2] + R[6]) / s; y = (R[5] + R[7]) / s; z = 0.25f * s;
-  }
-  if (w < 0.f) { w = -w; x = -x; y = -y; z = -z; }
-  const float inv = 1.f / sqrtf(w * w + x * x + y * y + z * z);
-  return make_float4(w * inv, x * inv, y * inv, z * inv);
-}
 
 // One thread per coarse node of the level: the moment-matching merge of its
 // (up to 8) children's geometry and opacity; the weights go to a.wts for the

@@ -29,6 +29,11 @@ struct ProjectArgs {
   const int32_t* parent;  // level-of-detail cut (nullptr: every Gaussian is a candidate)
   int64_t n_leaf;
   float tau;
+  // progressive hierarchy (h_active nullptr: none): the view cut at tau
+  const int32_t* h_parent;
+  const int32_t* h_child;
+  const uint8_t* h_active;
+  const uint32_t* h_n;
 };
 
 // Screen size of a node: f_x * 3 * max_k scale_k / t_z, infinite at or
@@ -72,6 +77,32 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
       const float tzp = R[6] * mp.x + R[7] * mp.y + R[8] * mp.z + tc[2];
       sel = screen_size(tzp, a.scale_opa[p], vi.fx, a.znear) >= a.tau;
       p = a.parent[p];
+    }
+    vis = sel;
+  }
+  if (vis && a.h_active) {
+    // the active set refined for this view: rendered iff not expandable, and
+    // either active or below an active ancestor through expandable nodes
+    auto expandable = [&](int64_t k) {
+      if (a.h_child[4 * k] < 0) return false;
+      bool in;
+      const float S = hier_node_screen(R, tc, vi.fx, vi.fy, vi.cx, vi.cy, vi.W, vi.H, a.znear, a.means4[k],
+                                       a.scale_opa[k], in);
+      return in && S > a.tau;
+    };
+    bool sel = i < (int64_t)*a.h_n && !expandable(i);
+    if (sel && !a.h_active[i]) {
+      int32_t p = a.h_parent[i];
+      int d = 0;
+      for (; p >= 0 && d < 64; ++d) {
+        if (!expandable(p)) {
+          sel = false;
+          break;
+        }
+        if (a.h_active[p]) break;
+        p = a.h_parent[p];
+      }
+      if (p < 0 || d >= 64) sel = false;
     }
     vis = sel;
   }
@@ -190,7 +221,7 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
 
 gs_status launch_project(const gs_params& p, const float* poses, const ViewTable& vt,
                          const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s, const int32_t* parent,
-                         int64_t n_leaf, float tau) {
+                         int64_t n_leaf, float tau, const gs_hier* hier) {
   ProjectArgs a;
   a.means4 = reinterpret_cast<const float4*>(p.means4);
   a.scale_opa = reinterpret_cast<const float4*>(p.scale_opa);
@@ -211,6 +242,10 @@ gs_status launch_project(const gs_params& p, const float* poses, const ViewTable
   a.parent = parent;
   a.n_leaf = n_leaf;
   a.tau = tau;
+  a.h_parent = hier ? hier->parent : nullptr;
+  a.h_child = hier ? hier->child : nullptr;
+  a.h_active = hier ? hier->active : nullptr;
+  a.h_n = hier ? hier->n_nodes : nullptr;
   if (p.n == 0) return GS_OK;
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)vt.views);
   switch (p.sh_degree) {

@@ -143,6 +143,61 @@ class LodHierarchy:
         return self.arena.struct(self.n_nodes)
 
 
+class Hierarchy:
+    """Progressive hierarchy (gs_hier_*) over the rows of a node arena: the
+    first n_leaf rows are the leaves, all active; analyses append merged
+    nodes after the rows in use (up to the arena's rows)."""
+
+    def __init__(self, arena: Arena, n_leaf: int):
+        self.L = _lib.load()
+        self.arena = arena
+        cap = arena.n
+        dev = arena.buf.device
+        self.capacity = cap
+        self.parent = torch.full((cap,), -1, dtype=torch.int32, device=dev)
+        self.child = torch.full((4 * cap,), -1, dtype=torch.int32, device=dev)
+        self.active = torch.zeros(cap, dtype=torch.uint8, device=dev)
+        self.active[:n_leaf] = 1
+        self.n_nodes = torch.tensor([n_leaf], dtype=torch.int32, device=dev)
+        self.info = torch.zeros(8, dtype=torch.int32, device=dev)
+        self.ws = torch.empty(max(1, self.L.gs_hier_workspace(cap)), dtype=torch.uint8, device=dev)
+        self.pose = torch.zeros(12, dtype=torch.float32, device=dev)
+
+    def struct(self):
+        return _lib.GsHier(self.parent.data_ptr(), self.child.data_ptr(), self.active.data_ptr(),
+                           self.n_nodes.data_ptr(), self.info.data_ptr(), self.capacity)
+
+    def _pose(self, cam: Camera):
+        self.pose.copy_(torch.from_numpy(np.asarray(cam.pose12(), np.float32).reshape(-1)))
+        return _p(self.pose)
+
+    def analyze(self, cam: Camera, znear=0.2, tau_l=0.5, m: Optional[Arena] = None, v: Optional[Arena] = None):
+        rw, h = self.arena.rw_struct(), self.struct()
+        ms = m.rw_struct() if m is not None else None
+        vs = v.rw_struct() if v is not None else None
+        c = cameras_struct([cam])
+        _lib.check(self.L.gs_hier_analyze(C.byref(rw), C.byref(h), C.byref(ms) if ms else None,
+                                          C.byref(vs) if vs else None, self._pose(cam), c, float(znear),
+                                          float(tau_l), _p(self.ws), self.ws.numel(), _stream()), "gs_hier_analyze")
+
+    def refine(self, cam: Camera, znear=0.2, tau_h=1.0, passes=16, m: Optional[Arena] = None,
+               v: Optional[Arena] = None):
+        rw, h = self.arena.rw_struct(), self.struct()
+        ms = m.rw_struct() if m is not None else None
+        vs = v.rw_struct() if v is not None else None
+        c = cameras_struct([cam])
+        _lib.check(self.L.gs_hier_refine(C.byref(rw), C.byref(h), C.byref(ms) if ms else None,
+                                         C.byref(vs) if vs else None, self._pose(cam), c, float(znear),
+                                         float(tau_h), int(passes), _p(self.ws), self.ws.numel(), _stream()),
+                   "gs_hier_refine")
+
+    def state(self) -> dict:
+        """Host copies (synchronises): n_nodes, info, parent, child [cap,4], active."""
+        n = int(self.n_nodes.item())
+        return {"n_nodes": n, "info": self.info.cpu().numpy().astype(np.int64), "parent": self.parent.cpu().numpy(),
+                "child": self.child.cpu().numpy().reshape(-1, 4), "active": self.active.cpu().numpy()}
+
+
 def cameras_struct(cams: Sequence[Camera]):
     arr = (_lib.GsCamera * len(cams))()
     for i, c in enumerate(cams):
@@ -269,6 +324,15 @@ class Rasterizer:
         _lib.check(self.L.gs_project_lod(C.byref(ps), lod.n_leaf, _p(lod.parent), float(tau), _p(poses),
                                          self.cam_struct, self.views, C.byref(self.cfg), C.byref(self.splats),
                                          _stream()), "gs_project_lod")
+
+    def project_hier(self, hier: "Hierarchy", poses: torch.Tensor, tau_h: float = 1.0) -> None:
+        """gs_project_hier: each view's cut of the progressive hierarchy over
+        this Rasterizer's n node rows."""
+        ps = hier.arena.struct(self.n)
+        h = hier.struct()
+        _lib.check(self.L.gs_project_hier(C.byref(ps), C.byref(h), float(tau_h), _p(poses), self.cam_struct,
+                                          self.views, C.byref(self.cfg), C.byref(self.splats), _stream()),
+                   "gs_project_hier")
 
     def bin_sort(self) -> None:
         b = self.bins_struct()
