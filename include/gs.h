@@ -688,8 +688,10 @@ typedef struct {
   float lr_means, lr_scale, lr_opacity, lr_quat, lr_sh_dc, lr_sh_rest;
   float beta1, beta2, eps;
   int32_t loss_kind;         /* 0 = L1, 1 = MSE */
-  int32_t lod;               /* 1: render requests go through a level-of-detail cut (gs_lod_build) */
-  float lod_tau;             /* cut threshold in pixels (> 0; the paper's tau = 1) */
+  int32_t lod;               /* 1: a progressive hierarchy (gs_session_analyze); renders and trains use
+                                each view's cut of its active set */
+  float lod_tau;             /* reload / cut threshold in pixels (> 0; the paper's tau_h = 1); merging
+                                takes nodes below lod_tau / 2 (the paper's tau_l = 0.5) */
 } gs_session_config;
 
 typedef struct {
@@ -706,7 +708,7 @@ typedef struct {
   int64_t iterations;        /* Adam steps taken (batches with train views) */
   int64_t batches;           /* batches issued, capacity retries included */
   int64_t retries;           /* batch parts issued again after a pair-capacity overflow */
-  int64_t lod_builds;        /* hierarchy builds (one before the first render after Gaussians were added) */
+  int64_t lod_builds;        /* hierarchy analyses swapped in (progressive hierarchy) */
   int64_t gaussians;         /* active Gaussians */
   double pixels;             /* pixels of completed requests */
   double p50_ms, p99_ms, mean_ms, max_ms;  /* arrival -> completion, completed requests */
@@ -768,7 +770,8 @@ GS_API gs_status gs_session_wait(gs_session* s, int64_t id, int32_t timeout_ms);
 /* Arrival and completion time (gs_session_now's clock, seconds) of a finished
  * request; GS_ERR_BUSY (no message) while it is pending. */
 GS_API gs_status gs_session_times(gs_session* s, int64_t id, double* arrival_s, double* done_s);
-/* Waits up to timeout_ms until nothing is queued or in flight. */
+/* Waits up to timeout_ms until nothing is queued or in flight (and a pending
+ * hierarchy analysis has completed and been swapped in). */
 GS_API gs_status gs_session_drain(gs_session* s, int32_t timeout_ms);
 /* on != 0 pauses admission: submitted requests queue up and no new batch is
  * formed (batches in flight complete); on == 0 resumes, and the queued
@@ -785,6 +788,30 @@ GS_API gs_status gs_session_read_params(gs_session* s, float* means4, float* sca
  * back; both drain first.  A resumed session continues bit-identically. */
 GS_API gs_status gs_session_save(gs_session* s, const char* path);
 GS_API gs_status gs_session_load(gs_session* s, const char* path);
+/* Analysis of the session's progressive hierarchy (lod = 1) from a new
+ * keyframe's camera (cam host, pose12 host [R | t]): gs_hier_analyze with
+ * tau_l = lod_tau / 2, then gs_hier_refine with tau_h = lod_tau, into the
+ * back buffer of the active set, enqueued on the session stream after
+ * everything issued so far.  Render parts keep using the front buffer while it
+ * runs (double buffering); once it has completed, the next batch formed swaps
+ * the buffers (the Adam moments of nodes whose flag changed are zeroed and
+ * every new merged node takes its children's most common keyframe tag).
+ * Leaves occupy rows [0, max_gaussians), merged nodes the rows after them;
+ * renders and trains use each view's cut of the front active set, so merged
+ * nodes are trained.  GS_ERR_BUSY (nothing issued) while the previous
+ * analysis has not completed; GS_ERR_INVALID without a hierarchy.
+ * Checkpoints (gs_session_save / load) are not supported with a hierarchy. */
+GS_API gs_status gs_session_analyze(gs_session* s, const gs_camera* cam, const float* pose12);
+/* The session's hierarchy (lod = 1) after draining (a pending analysis is
+ * waited for and swapped in): *rows = node rows in use (leaf slots
+ * [0, max_gaussians), merged nodes after them); with any array non-NULL,
+ * copies rows [0, *rows) in the library layout (as gs_session_read_params;
+ * sh [3*nc][*rows]), parent [rows], child [rows][4] and the front active
+ * flags [rows].  GS_ERR_INVALID: no hierarchy, or max_rows < *rows with an
+ * array given. */
+GS_API gs_status gs_session_read_hierarchy(gs_session* s, int64_t max_rows, int64_t* rows, float* means4,
+                                           float* scale_opa, float* quat, float* sh, int32_t* parent,
+                                           int32_t* child, uint8_t* active);
 /* Host-side fault injection for tests: the session's next `count` device
  * allocations fail as if the device were out of memory (no device fault is
  * made).  A batch whose pair buffers cannot grow finishes its requests with

@@ -35,7 +35,8 @@ EXPORTED = (
     "gs_ba_workspace_bytes", "gs_ba_solve",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
     "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_keyframe_weights", "gs_session_stats", "gs_session_read_params",
-    "gs_session_save", "gs_session_load", "gs_session_inject_alloc_failures", "gs_session_destroy",
+    "gs_session_save", "gs_session_load", "gs_session_inject_alloc_failures", "gs_session_analyze",
+    "gs_session_read_hierarchy", "gs_session_destroy",
 )
 
 GS_REQUEST_RENDER, GS_REQUEST_TRAIN = 0, 1
@@ -225,11 +226,13 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.gs_session_save.argtypes = [vp, C.c_char_p]
     L.gs_session_load.argtypes = [vp, C.c_char_p]
     L.gs_session_inject_alloc_failures.argtypes = [vp, i32]
+    L.gs_session_analyze.argtypes = [vp, P(GsCamera), C.POINTER(C.c_float)]
+    L.gs_session_read_hierarchy.argtypes = [vp, C.c_int64, C.POINTER(C.c_int64), vp, vp, vp, vp, vp, vp, vp]
     L.gs_session_destroy.argtypes = [vp]
     for name in ("gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
                  "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_keyframe_weights", "gs_session_stats",
                  "gs_session_read_params", "gs_session_save", "gs_session_load", "gs_session_inject_alloc_failures",
-                 "gs_session_destroy"):
+                 "gs_session_analyze", "gs_session_read_hierarchy", "gs_session_destroy"):
         getattr(L, name).restype = C.c_int
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
                  "gs_render_bwd",

@@ -61,7 +61,9 @@ gs_status launch_hier_refine(const gs_grads& nodes, const gs_hier& h, const gs_g
 gs_status launch_sim3_update(const gs_grads& p, const int32_t* kf, const float* sim3, int32_t num_kf,
                              uint32_t* status, cudaStream_t s);
 gs_status launch_fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s);
-gs_status launch_keyframe_counts(const int32_t* kf, int64_t n, int32_t num_kf, uint32_t* counts, cudaStream_t s);
+// active (optional): only rows with a nonzero flag are counted.
+gs_status launch_keyframe_counts(const int32_t* kf, int64_t n, int32_t num_kf, uint32_t* counts, cudaStream_t s,
+                                 const uint8_t* active = nullptr);
 
 // Local bundle adjustment (arguments validated by the caller).
 size_t ba_workspace_bytes(int num_cams, int num_points, int obs_per_point);

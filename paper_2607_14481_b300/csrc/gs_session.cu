@@ -104,15 +104,23 @@ struct gs_session {
   cudaStream_t stream = nullptr;
   gs::Dev arena[4];  // parameters, gradients, first and second moments (stride = capacity)
   gs::Dev status_word, step_dev;
-  gs::Dev lod_parent, lod_ws;  // level-of-detail hierarchy (cfg.lod)
-  gs::Dev kf_of;               // int32 [max_gaussians]: keyframe that added each Gaussian (-1: none)
+  // progressive hierarchy (cfg.lod): leaf rows [0, max_gaussians), merged
+  // nodes appended from row max_gaussians on; two active-set buffers: renders
+  // and trains read the front one while an analysis writes the other
+  gs::Dev h_parent, h_child, h_active[2], h_n, h_info, h_ws, h_pose;
+  int front = 0;
+  bool h_pending = false;       // an analysis was issued; its buffer becomes the front when it completes
+  cudaEvent_t h_done = nullptr;
+  uint32_t* h_read = nullptr;   // pinned [8]: summary words of the pending analysis (node rows first)
+  float* h_pose_host = nullptr; // pinned [12]
+  int64_t h_rows = 0;           // node rows in use after the last swap
+  gs::Dev kf_of;               // int32 [arena rows]: keyframe that added each Gaussian (-1: none)
   gs::Dev sim3, sim3_status;   // loop-closure corrections [num_kf][8], status word
   cudaEvent_t mut_done = nullptr;  // the last write of the parameters issued (session stream)
   int64_t fail_allocs = 0;     // host-side fault injection: device allocations still to fail
   int64_t train_beside_render = 0;  // train parts issued while a render part was in flight
   int32_t keyframe = -1;       // tag of the Gaussians added next
-  bool lod_dirty = true;       // leaves added since the last build
-  int64_t lod_builds = 0;
+  int64_t lod_builds = 0;      // hierarchy analyses completed (their buffers swapped in)
   int64_t capacity = 0;
   int64_t n_active = 0;
   int nc = 1;
@@ -177,14 +185,18 @@ size_t ctx_device_bytes(const gs_session_config& c, int64_t cap_n, int64_t pair_
 // Rows of the parameter arenas: the leaves, and with a hierarchy its coarse
 // nodes after them.
 int64_t arena_rows(const gs_session_config& c) {
-  return c.lod ? c.max_gaussians + lod_level1(c.max_gaussians) + lod_level2(c.max_gaussians) : c.max_gaussians;
+  return c.lod ? 2 * c.max_gaussians : c.max_gaussians;  // merged nodes: fewer than the leaves
 }
 
 size_t fixed_device_bytes(const gs_session_config& c) {
   const int nc = (c.sh_degree + 1) * (c.sh_degree + 1);
   size_t b = 4 * align_up(4 * arena_floats(arena_rows(c), nc), 256) + 2 * 256;
-  if (c.lod)
-    b += align_up(4 * (size_t)arena_rows(c), 256) + align_up(lod_build_workspace_bytes(c.max_gaussians), 256);
+  if (c.lod) {
+    const size_t r = (size_t)arena_rows(c);
+    b += align_up(4 * r, 256) + align_up(16 * r, 256) + 2 * align_up(r, 256) + align_up(hier_workspace_bytes(r), 256) +
+         3 * 256;
+  }
+  b += align_up(4 * (size_t)arena_rows(c), 256);  // keyframe tags
   return b;
 }
 
@@ -289,6 +301,18 @@ void free_ctx(gs_session* S, Ctx& c) {
   c = Ctx();
 }
 
+void free_hier(gs_session* S) {
+  for (Dev* d : {&S->h_parent, &S->h_child, &S->h_active[0], &S->h_active[1], &S->h_n, &S->h_info, &S->h_ws,
+                 &S->h_pose})
+    dfree(*d, S->in_use);
+  if (S->h_done) cudaEventDestroy(S->h_done);
+  if (S->h_read) cudaFreeHost(S->h_read);
+  if (S->h_pose_host) cudaFreeHost(S->h_pose_host);
+  S->h_done = nullptr;
+  S->h_read = nullptr;
+  S->h_pose_host = nullptr;
+}
+
 float* arena_ptr(gs_session* S, int k) { return static_cast<float*>(S->arena[k].p); }
 
 gs_params params_of(gs_session* S, int k) {
@@ -305,25 +329,109 @@ gs_params params_of(gs_session* S, int k) {
   return p;
 }
 
-// Adam groups over the active slots of the capacity-strided arena.
+void wait_renders(gs_session* S, cudaStream_t s);
+void mark_write(gs_session* S);
+
+// Adam groups over the rows in use of the capacity-strided arena: the active
+// leaf slots and, with a hierarchy, the merged nodes (rows from
+// max_gaussians on).
 int adam_groups(gs_session* S, gs_adam_group* g) {
   const auto& c = S->cfg;
-  const int64_t n = S->n_active, cap = S->capacity;
+  const int64_t cap = S->capacity;
   int k = 0;
   auto set = [&](int64_t b, int64_t e, float l0, float l1, float l2, float l3) {
     g[k].begin = b; g[k].end = e;
     g[k].lr[0] = l0; g[k].lr[1] = l1; g[k].lr[2] = l2; g[k].lr[3] = l3;
     ++k;
   };
-  set(0, 4 * n, c.lr_means, c.lr_means, c.lr_means, 0.f);
-  set(4 * cap, 4 * cap + 4 * n, c.lr_scale, c.lr_scale, c.lr_scale, c.lr_opacity);
-  set(8 * cap, 8 * cap + 4 * n, c.lr_quat, c.lr_quat, c.lr_quat, c.lr_quat);
-  for (int p = 0; p < 3 * S->nc; ++p) {
-    const float lr = (p % S->nc == 0) ? c.lr_sh_dc : c.lr_sh_rest;
-    const int64_t b = 12 * cap + (int64_t)p * cap;
-    set(b, b + n, lr, lr, lr, lr);
-  }
+  auto rows = [&](int64_t r0, int64_t r1) {
+    if (r1 <= r0) return;
+    set(4 * r0, 4 * r1, c.lr_means, c.lr_means, c.lr_means, 0.f);
+    set(4 * cap + 4 * r0, 4 * cap + 4 * r1, c.lr_scale, c.lr_scale, c.lr_scale, c.lr_opacity);
+    set(8 * cap + 4 * r0, 8 * cap + 4 * r1, c.lr_quat, c.lr_quat, c.lr_quat, c.lr_quat);
+    for (int p = 0; p < 3 * S->nc; ++p) {
+      const float lr = (p % S->nc == 0) ? c.lr_sh_dc : c.lr_sh_rest;
+      const int64_t b = 12 * cap + (int64_t)p * cap;
+      set(b + r0, b + r1, lr, lr, lr, lr);
+    }
+  };
+  // with a hierarchy, one range over the leaf slots and the merged nodes:
+  // the unused leaf slots between them have zero gradients and moments, so
+  // their update is zero (two ranges would need more groups than allowed)
+  rows(0, c.lod ? S->h_rows : S->n_active);
   return k;
+}
+
+gs_hier hier_of(gs_session* S, int buf) {
+  gs_hier h;
+  h.parent = static_cast<int32_t*>(S->h_parent.p);
+  h.child = static_cast<int32_t*>(S->h_child.p);
+  h.active = static_cast<uint8_t*>(S->h_active[buf].p);
+  h.n_nodes = static_cast<uint32_t*>(S->h_n.p);
+  h.info = static_cast<uint32_t*>(S->h_info.p);
+  h.capacity = S->capacity;
+  return h;
+}
+
+// At a swap: the Adam moments of the rows whose active flag changed are zeroed
+// (a node entering or leaving the active set starts afresh), and every new
+// merged node takes the keyframe tag most common among its children (ties:
+// the first child's), so a loop closure moves it with them.
+__global__ void k_hier_swap(const uint8_t* __restrict__ before, const uint8_t* __restrict__ after, int64_t rows,
+                            int64_t new_from, const int32_t* __restrict__ child, int32_t* __restrict__ kf, float* m,
+                            float* v, int64_t cap, int nc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  if (before[i] != after[i]) {
+    for (float* A : {m, v}) {
+      reinterpret_cast<float4*>(A)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      reinterpret_cast<float4*>(A + 4 * cap)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      reinterpret_cast<float4*>(A + 8 * cap)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int p = 0; p < 3 * nc; ++p) A[12 * cap + (int64_t)p * cap + i] = 0.f;
+    }
+  }
+  if (i >= new_from) {
+    int32_t best = -1;
+    int bc = 0;
+    for (int a = 0; a < 4; ++a) {
+      const int32_t ca = child[4 * i + a];
+      if (ca < 0) continue;
+      int cnt = 0;
+      for (int b = 0; b < 4; ++b)
+        if (child[4 * i + b] >= 0 && kf[child[4 * i + b]] == kf[ca]) ++cnt;
+      if (cnt > bc) {
+        bc = cnt;
+        best = kf[ca];
+      }
+    }
+    kf[i] = best;
+  }
+}
+
+// The pending analysis's buffer becomes the front one once it has completed
+// (S->mu held).  Its swap work is a write on the session stream.
+void try_swap(gs_session* S) {
+  if (!S->h_pending) return;
+  const cudaError_t e = cudaEventQuery(S->h_done);
+  if (e == cudaErrorNotReady) return;
+  S->h_pending = false;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    S->fatal = fail(GS_ERR_CUDA, "session: hierarchy analysis failed: %s", cudaGetErrorString(e));
+    return;
+  }
+  const int back = S->front ^ 1;
+  const int64_t rows = std::min<int64_t>(S->capacity, (int64_t)S->h_read[0]);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, (rows + 255) / 256);
+  k_hier_swap<<<grid, 256, 0, S->stream>>>(static_cast<const uint8_t*>(S->h_active[S->front].p),
+                                           static_cast<const uint8_t*>(S->h_active[back].p), rows, S->h_rows,
+                                           static_cast<const int32_t*>(S->h_child.p),
+                                           static_cast<int32_t*>(S->kf_of.p), arena_ptr(S, 2), arena_ptr(S, 3),
+                                           S->capacity, S->nc);
+  mark_write(S);
+  S->front = back;
+  S->h_rows = rows;
+  S->lod_builds++;
 }
 
 // The session stream waits, on the device, for every render part issued so
@@ -368,22 +476,11 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     if (cudaMemcpyAsync(poses, c.h_poses, 48 * R.size(), cudaMemcpyHostToDevice, rs) != cudaSuccess)
       return check_launch("session poses");
     gs_params PR = P;
-    const int32_t* parent = nullptr;
-    if (cf.lod && n > 0) {
-      if (S->lod_dirty) {
-        // the build writes the coarse nodes: after the render parts that read them
-        GS_NVTX("session hierarchy build");
-        wait_renders(S, s);
-        gs_grads rw{const_cast<float*>(P.means4), const_cast<float*>(P.scale_opa), const_cast<float*>(P.quat),
-                    const_cast<float*>(P.sh), S->capacity, P.sh_degree, P.sh_stride};
-        if ((st = launch_lod_build(rw, n, static_cast<int32_t*>(S->lod_parent.p), S->lod_ws.p, s)) != GS_OK)
-          return st;
-        mark_write(S);
-        S->lod_dirty = false;
-        S->lod_builds++;
-      }
-      PR.n = n + lod_level1(n) + lod_level2(n);
-      parent = static_cast<const int32_t*>(S->lod_parent.p);
+    gs_hier hf;
+    if (cf.lod) {
+      // the view cut of the front active set over every node row in use
+      PR.n = S->h_rows;
+      hf = hier_of(S, S->front);
     }
     // every write issued before this render part
     if (cudaStreamWaitEvent(rs, S->mut_done, 0) != cudaSuccess) return check_launch("session wait");
@@ -392,7 +489,9 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     gs_bins b{static_cast<uint32_t*>(c.vals.p), static_cast<uint32_t*>(c.ranges.p),
               static_cast<uint32_t*>(c.pair_off.p), nullptr, counts, c.pair_cap, vt.total_tiles,
               static_cast<uint32_t*>(c.order.p)};
-    if ((st = launch_project(PR, poses, vt, cf.raster, sp, rs, parent, n, cf.lod_tau)) != GS_OK) return st;
+    if ((st = launch_project(PR, poses, vt, cf.raster, sp, rs, nullptr, 0, cf.lod_tau, cf.lod ? &hf : nullptr)) !=
+        GS_OK)
+      return st;
     if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, rs)) != GS_OK) return st;
     if ((st = launch_render_fwd(sp, b, vt, cf.raster, img, nullptr, rs)) != GS_OK) return st;
     for (Req* r : R) off += 3 * (int64_t)r->cam.width * r->cam.height;
@@ -406,6 +505,9 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
   }
   if (!T.empty()) {
     GS_NVTX("session train part");
+    // the render part of this batch (on the context's stream) uses the same
+    // splat, pair and workspace buffers: the train part runs after it
+    if (!R.empty() && cudaStreamWaitEvent(s, c.rdone, 0) != cudaSuccess) return check_launch("session wait");
     for (auto& o : S->ctxs)
       if (o.get() != &c && o->busy && !o->reqs.empty() && o->reqs.front()->kind == GS_REQUEST_RENDER) {
         S->train_beside_render++;  // its forward and backward run beside that render part
@@ -425,19 +527,27 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     float* tposes = poses + 12 * V;
     if (cudaMemcpyAsync(tposes, c.h_poses + 12 * V, 48 * T.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return check_launch("session poses");
+    // with a hierarchy the train views render (and train) the cut of the
+    // front active set: merged nodes in it are optimised like leaves
+    const int64_t rows = cf.lod ? S->h_rows : n;
+    gs_params PT = P;
+    PT.n = rows;
+    gs_hier hf = cf.lod ? hier_of(S, S->front) : gs_hier{};
     gs_splats sp;
-    gs_splats_carve(c.splat_buf.p, n, (int32_t)T.size(), &sp);
+    gs_splats_carve(c.splat_buf.p, rows, (int32_t)T.size(), &sp);
     gs_bins b{static_cast<uint32_t*>(c.vals.p), static_cast<uint32_t*>(c.ranges.p),
               static_cast<uint32_t*>(c.pair_off.p), nullptr, counts + 4, c.pair_cap, vt.total_tiles,
               static_cast<uint32_t*>(c.order.p)};
     float* timg = img + off;
-    if ((st = launch_project(P, tposes, vt, cf.raster, sp, s)) != GS_OK) return st;
+    if ((st = launch_project(PT, tposes, vt, cf.raster, sp, s, nullptr, 0, cf.lod_tau, cf.lod ? &hf : nullptr)) !=
+        GS_OK)
+      return st;
     if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, s)) != GS_OK) return st;
     // composite, loss and per-pixel backward in one persistent launch
     float *partials, *pose_partials, *drgb;
-    render_bwd_ws_layout(n, (int32_t)T.size(), c.pair_cap, c.ws_bwd.p, &partials, &pose_partials, &drgb);
+    render_bwd_ws_layout(rows, (int32_t)T.size(), c.pair_cap, c.ws_bwd.p, &partials, &pose_partials, &drgb);
     char* wsb = static_cast<char*>(c.ws_bwd.p);
-    const size_t bwd_bytes = render_bwd_ws_bytes(n, (int32_t)T.size(), c.pair_cap);
+    const size_t bwd_bytes = render_bwd_ws_bytes(rows, (int32_t)T.size(), c.pair_cap);
     gs_raster_cfg rc = cf.raster;
     rc.schedule &= ~GS_SCHED_FUSED_LONGEST_FIRST;  // the session bins without a tile order
     if ((st = launch_render_fused(sp, b, vt, rc, tgt, cf.loss_kind, timg, nullptr, static_cast<float*>(c.loss.p),
@@ -446,8 +556,8 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
       return st;
     gs_params G = params_of(S, 1);
     gs_grads g{const_cast<float*>(G.means4), const_cast<float*>(G.scale_opa), const_cast<float*>(G.quat),
-               const_cast<float*>(G.sh), G.n, G.sh_degree, G.sh_stride};
-    if ((st = launch_project_bwd(P, tposes, vt, cf.raster, sp, b, partials, g, pose_partials, nullptr, drgb,
+               const_cast<float*>(G.sh), rows, G.sh_degree, G.sh_stride};
+    if ((st = launch_project_bwd(PT, tposes, vt, cf.raster, sp, b, partials, g, pose_partials, nullptr, drgb,
                                  s)) != GS_OK)
       return st;
     gs_adam_group groups[GS_MAX_ADAM_GROUPS];
@@ -531,6 +641,7 @@ void worker_main(gs_session* S) {
              (!S->queue.empty() && (!S->hold || S->stop) && free_ctx_of(S) != nullptr);
     });
     if (S->queue.empty()) break;  // stop requested and drained
+    try_swap(S);  // a completed hierarchy analysis becomes the front active set
     Ctx* c = free_ctx_of(S);
     c->busy = true;
     c->reqs.clear();
@@ -699,6 +810,20 @@ gs_status sync_stream(gs_session* S, double timeout_s) {
   return GS_OK;
 }
 
+// Waits (bounded) for a pending hierarchy analysis and swaps its buffer in
+// (S->mu held).
+gs_status finish_analysis(gs_session* S, double timeout_s) {
+  if (!S->h_pending) return GS_OK;
+  const double t0 = steady_now();
+  cudaError_t e;
+  while ((e = cudaEventQuery(S->h_done)) == cudaErrorNotReady) {
+    if (steady_now() - t0 > timeout_s) return fail(GS_ERR_TIMEOUT, "session: hierarchy analysis did not finish");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  try_swap(S);
+  return S->fatal;
+}
+
 }  // namespace
 }  // namespace gs
 
@@ -757,8 +882,7 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
     for (auto& a : S->arena) gs::dfree(a, S->in_use);
     gs::dfree(S->status_word, S->in_use);
     gs::dfree(S->step_dev, S->in_use);
-    gs::dfree(S->lod_parent, S->in_use);
-    gs::dfree(S->lod_ws, S->in_use);
+    gs::free_hier(S.get());
     gs::dfree(S->kf_of, S->in_use);
     gs::dfree(S->sim3_status, S->in_use);
     if (S->h_add) cudaFreeHost(S->h_add);
@@ -778,13 +902,36 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
   if ((st = gs::dalloc(S->step_dev, 16, S->in_use)) != GS_OK) return cleanup(st);
   cudaMemsetAsync(S->status_word.p, 0, 16, S->stream);
   cudaMemsetAsync(S->step_dev.p, 0, 16, S->stream);
-  if ((st = gs::dalloc(S->kf_of, 4 * (size_t)cfg->max_gaussians, S->in_use)) != GS_OK) return cleanup(st);
+  if ((st = gs::dalloc(S->kf_of, 4 * (size_t)S->capacity, S->in_use)) != GS_OK) return cleanup(st);
+  if ((st = gs::launch_fill_i32(static_cast<int32_t*>(S->kf_of.p), -1, S->capacity, S->stream)) != GS_OK)
+    return cleanup(st);
   if ((st = gs::dalloc(S->sim3_status, 16, S->in_use)) != GS_OK) return cleanup(st);
   cudaMemsetAsync(S->sim3_status.p, 0, 16, S->stream);
   if (cfg->lod) {
-    if ((st = gs::dalloc(S->lod_parent, 4 * (size_t)S->capacity, S->in_use)) != GS_OK) return cleanup(st);
-    if ((st = gs::dalloc(S->lod_ws, gs::lod_build_workspace_bytes(cfg->max_gaussians), S->in_use)) != GS_OK)
+    const size_t r = (size_t)S->capacity;
+    if ((st = gs::dalloc(S->h_parent, 4 * r, S->in_use)) != GS_OK) return cleanup(st);
+    if ((st = gs::dalloc(S->h_child, 16 * r, S->in_use)) != GS_OK) return cleanup(st);
+    for (auto& a : S->h_active) {
+      if ((st = gs::dalloc(a, r, S->in_use)) != GS_OK) return cleanup(st);
+      cudaMemsetAsync(a.p, 0, r, S->stream);
+    }
+    if ((st = gs::dalloc(S->h_n, 16, S->in_use)) != GS_OK) return cleanup(st);
+    if ((st = gs::dalloc(S->h_info, 32, S->in_use)) != GS_OK) return cleanup(st);
+    if ((st = gs::dalloc(S->h_pose, 48, S->in_use)) != GS_OK) return cleanup(st);
+    if ((st = gs::dalloc(S->h_ws, gs::hier_workspace_bytes(S->capacity), S->in_use)) != GS_OK) return cleanup(st);
+    if ((st = gs::launch_fill_i32(static_cast<int32_t*>(S->h_parent.p), -1, S->capacity, S->stream)) != GS_OK ||
+        (st = gs::launch_fill_i32(static_cast<int32_t*>(S->h_child.p), -1, 4 * S->capacity, S->stream)) != GS_OK)
       return cleanup(st);
+    // the leaf slots count as node rows (inactive until added); merged nodes follow
+    const uint32_t rows0 = (uint32_t)cfg->max_gaussians;
+    cudaMemcpyAsync(S->h_n.p, &rows0, 4, cudaMemcpyHostToDevice, S->stream);
+    S->h_rows = cfg->max_gaussians;
+    if (cudaEventCreateWithFlags(&S->h_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&S->h_read, 16 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&S->h_pose_host, 12 * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(gs::fail(GS_ERR_OOM, "session: hierarchy event or pinned buffers"));
+    }
   }
   for (int k = 0; k < plan.contexts; ++k) {
     S->ctxs.push_back(std::make_unique<Ctx>());
@@ -813,8 +960,7 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
   if (!means || !log_scales || !quats || !opa_logits || !sh) return gs::fail(GS_ERR_INVALID, "NULL array");
   // Adds are serialised; the host-side staging runs without the session lock,
   // the device copies are enqueued under it together with the new count (so
-  // a batch never sees rows that are being filled, and the hierarchy, whose
-  // coarse nodes the new rows overwrite, is marked for a rebuild).
+  // a batch never sees rows that are being filled).
   std::lock_guard<std::mutex> add_lk(S->add_mu);
   int64_t n0;
   {
@@ -862,7 +1008,7 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
   std::unique_lock<std::mutex> lk(S->mu);
   float* A = gs::arena_ptr(S, 0);
   cudaStream_t s = S->stream;
-  gs::wait_renders(S, s);  // the new rows overwrite coarse nodes that render parts may be reading
+  gs::wait_renders(S, s);  // the active flags change under render parts issued earlier
   cudaMemcpyAsync(A + 4 * n0, hm, 16 * k, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(A + 4 * cap + 4 * n0, hs, 16 * k, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(A + 8 * cap + 4 * n0, hq, 16 * k, cudaMemcpyHostToDevice, s);
@@ -876,12 +1022,13 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
   }
   gs_status st = gs::launch_fill_i32(static_cast<int32_t*>(S->kf_of.p) + n0, S->keyframe, k, s);
   if (st != GS_OK) return st;
+  if (S->cfg.lod)  // new leaves: active in both buffers (the pending analysis did not see them)
+    for (auto& a : S->h_active) cudaMemsetAsync(static_cast<uint8_t*>(a.p) + n0, 1, (size_t)k, s);
   cudaEventRecord(S->add_done, s);
   gs::mark_write(S);
   st = gs::check_launch("session add");
   if (st != GS_OK) return st;
   S->n_active += count;
-  S->lod_dirty = true;  // the new leaves overwrote coarse nodes
   return GS_OK;
 }
 
@@ -915,14 +1062,14 @@ gs_status gs_session_loop_closure(gs_session* S, int32_t num_kf, const float* si
   if (num_kf > 0 && cudaMemcpyAsync(S->sim3.p, sim3, 32 * (size_t)num_kf, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return gs::check_launch("session sim3");
   gs_params P = gs::params_of(S, 0);
+  // every row in use: leaves and merged nodes (tagged with their children's keyframe)
   gs_grads rw{const_cast<float*>(P.means4), const_cast<float*>(P.scale_opa), const_cast<float*>(P.quat),
-              const_cast<float*>(P.sh), S->n_active, P.sh_degree, P.sh_stride};
+              const_cast<float*>(P.sh), S->cfg.lod ? S->h_rows : S->n_active, P.sh_degree, P.sh_stride};
   gs_status st = gs::launch_sim3_update(rw, static_cast<const int32_t*>(S->kf_of.p),
                                         static_cast<const float*>(S->sim3.p), num_kf,
                                         static_cast<uint32_t*>(S->sim3_status.p), s);
   if (st != GS_OK) return st;
   gs::mark_write(S);
-  S->lod_dirty = true;  // coarse nodes follow the moved leaves at the next build
   return GS_OK;
 }
 
@@ -941,8 +1088,10 @@ gs_status gs_session_keyframe_weights(gs_session* S, int32_t num_kf, int32_t min
     gs_status st = gs::dalloc(counts, sizeof(uint32_t) * (size_t)num_kf, S->in_use);
     if (st != GS_OK) return st;
     // after everything enqueued so far (adds, closures), on the session stream
-    st = gs::launch_keyframe_counts(static_cast<const int32_t*>(S->kf_of.p), S->n_active, num_kf,
-                                    static_cast<uint32_t*>(counts.p), S->stream);
+    st = gs::launch_keyframe_counts(static_cast<const int32_t*>(S->kf_of.p), S->cfg.lod ? S->h_rows : S->n_active,
+                                    num_kf,
+                                    static_cast<uint32_t*>(counts.p), S->stream,
+                                    S->cfg.lod ? static_cast<const uint8_t*>(S->h_active[S->front].p) : nullptr);
     if (st == GS_OK &&
         cudaMemcpyAsync(c.data(), counts.p, sizeof(uint32_t) * (size_t)num_kf, cudaMemcpyDeviceToHost, S->stream) !=
             cudaSuccess)
@@ -1055,7 +1204,9 @@ gs_status gs_session_drain(gs_session* S, int32_t timeout_ms) {
   GS_NVTX("gs_session_drain");
   if (!S) return gs::fail(GS_ERR_INVALID, "session is NULL");
   std::unique_lock<std::mutex> lk(S->mu);
-  return gs::wait_idle(S, lk, timeout_ms);
+  gs_status st = gs::wait_idle(S, lk, timeout_ms);
+  if (st != GS_OK) return st;
+  return gs::finish_analysis(S, 1e-3 * timeout_ms);
 }
 
 gs_status gs_session_stats(gs_session* S, gs_stats* out) {
@@ -1104,6 +1255,7 @@ gs_status gs_session_stats(gs_session* S, gs_stats* out) {
 gs_status gs_session_save(gs_session* S, const char* path) {
   GS_NVTX("gs_session_save");
   if (!S || !path) return gs::fail(GS_ERR_INVALID, "NULL session or path");
+  if (S->cfg.lod) return gs::fail(GS_ERR_INVALID, "session: checkpoints of a session with a hierarchy are not supported");
   std::unique_lock<std::mutex> lk(S->mu);
   gs_status st = gs::wait_idle(S, lk, 60000);
   if (st != GS_OK) return st;
@@ -1140,6 +1292,7 @@ gs_status gs_session_save(gs_session* S, const char* path) {
 gs_status gs_session_load(gs_session* S, const char* path) {
   GS_NVTX("gs_session_load");
   if (!S || !path) return gs::fail(GS_ERR_INVALID, "NULL session or path");
+  if (S->cfg.lod) return gs::fail(GS_ERR_INVALID, "session: checkpoints of a session with a hierarchy are not supported");
   std::unique_lock<std::mutex> lk(S->mu);
   gs_status st = gs::wait_idle(S, lk, 60000);
   if (st != GS_OK) return st;
@@ -1178,7 +1331,6 @@ gs_status gs_session_load(gs_session* S, const char* path) {
   gs::mark_write(S);
   if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
   S->n_active = n;
-  S->lod_dirty = true;
   return gs::check_launch("session load");
 }
 
@@ -1198,6 +1350,73 @@ gs_status gs_session_read_params(gs_session* S, float* means4, float* scale_opa,
   if (sh) cudaMemcpy2DAsync(sh, 4 * n, A + 12 * cap, 4 * cap, 4 * n, 3 * S->nc, cudaMemcpyDeviceToHost, s);
   if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
   return gs::check_launch("session read");
+}
+
+gs_status gs_session_read_hierarchy(gs_session* S, int64_t max_rows, int64_t* rows, float* means4,
+                                    float* scale_opa, float* quat, float* sh, int32_t* parent, int32_t* child,
+                                    uint8_t* active) {
+  GS_NVTX("gs_session_read_hierarchy");
+  if (!S || !rows) return gs::fail(GS_ERR_INVALID, "NULL session or rows");
+  if (!S->cfg.lod) return gs::fail(GS_ERR_INVALID, "session: no hierarchy (lod = 0)");
+  std::unique_lock<std::mutex> lk(S->mu);
+  gs_status st = gs::wait_idle(S, lk, 60000);
+  if (st != GS_OK) return st;
+  if ((st = gs::finish_analysis(S, 30.0)) != GS_OK) return st;
+  if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
+  const int64_t n = S->h_rows, cap = S->capacity;
+  *rows = n;
+  const bool any = means4 || scale_opa || quat || sh || parent || child || active;
+  if (!any) return GS_OK;
+  if (max_rows < n) return gs::fail(GS_ERR_INVALID, "session: %lld node rows, arrays hold %lld", (long long)n,
+                                    (long long)max_rows);
+  const float* A = gs::arena_ptr(S, 0);
+  cudaStream_t s = S->stream;
+  if (means4) cudaMemcpyAsync(means4, A, 16 * n, cudaMemcpyDeviceToHost, s);
+  if (scale_opa) cudaMemcpyAsync(scale_opa, A + 4 * cap, 16 * n, cudaMemcpyDeviceToHost, s);
+  if (quat) cudaMemcpyAsync(quat, A + 8 * cap, 16 * n, cudaMemcpyDeviceToHost, s);
+  if (sh) cudaMemcpy2DAsync(sh, 4 * n, A + 12 * cap, 4 * cap, 4 * n, 3 * S->nc, cudaMemcpyDeviceToHost, s);
+  if (parent) cudaMemcpyAsync(parent, S->h_parent.p, 4 * n, cudaMemcpyDeviceToHost, s);
+  if (child) cudaMemcpyAsync(child, S->h_child.p, 16 * n, cudaMemcpyDeviceToHost, s);
+  if (active) cudaMemcpyAsync(active, S->h_active[S->front].p, (size_t)n, cudaMemcpyDeviceToHost, s);
+  if ((st = gs::sync_stream(S, 30.0)) != GS_OK) return st;
+  return gs::check_launch("session read hierarchy");
+}
+
+gs_status gs_session_analyze(gs_session* S, const gs_camera* cam, const float* pose12) {
+  GS_NVTX("gs_session_analyze");
+  if (!S || !cam || !pose12) return gs::fail(GS_ERR_INVALID, "NULL session, camera or pose");
+  if (!S->cfg.lod) return gs::fail(GS_ERR_INVALID, "session: no hierarchy (lod = 0)");
+  if (cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f))
+    return gs::fail(GS_ERR_INVALID, "session: bad camera");
+  std::lock_guard<std::mutex> add_lk(S->add_mu);
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->fatal != GS_OK) return gs::fail(S->fatal, "session failed earlier");
+  gs::try_swap(S);
+  if (S->h_pending) return gs::fail(GS_ERR_BUSY, "session: the previous analysis has not completed");
+  cudaStream_t s = S->stream;
+  const int back = S->front ^ 1;
+  // the back buffer may still be read by render parts issued before the last swap
+  gs::wait_renders(S, s);
+  cudaMemcpyAsync(S->h_active[back].p, S->h_active[S->front].p, (size_t)S->capacity, cudaMemcpyDeviceToDevice, s);
+  std::memcpy(S->h_pose_host, pose12, 48);
+  cudaMemcpyAsync(S->h_pose.p, S->h_pose_host, 48, cudaMemcpyHostToDevice, s);
+  gs_params P = gs::params_of(S, 0);
+  gs_grads rw{const_cast<float*>(P.means4), const_cast<float*>(P.scale_opa), const_cast<float*>(P.quat),
+              const_cast<float*>(P.sh), S->capacity, P.sh_degree, P.sh_stride};
+  gs_hier h = gs::hier_of(S, back);
+  const float tau_h = S->cfg.lod_tau, tau_l = 0.5f * S->cfg.lod_tau;
+  const float* pose = static_cast<const float*>(S->h_pose.p);
+  gs_status st = gs::launch_hier_analyze(rw, h, nullptr, nullptr, pose, *cam, S->cfg.raster.znear, tau_l, S->h_ws.p, s);
+  if (st == GS_OK) cudaMemcpyAsync(S->h_read + 1, S->h_info.p, 32, cudaMemcpyDeviceToHost, s);
+  // the reload for the same view: nodes too coarse for it go back to their children
+  if (st == GS_OK)
+    st = gs::launch_hier_refine(rw, h, nullptr, nullptr, pose, *cam, S->cfg.raster.znear, tau_h, 16, S->h_ws.p, s);
+  if (st != GS_OK) return st;
+  cudaMemcpyAsync(S->h_read, S->h_n.p, 4, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(S->h_read + 9, S->h_info.p, 4, cudaMemcpyDeviceToHost, s);
+  if (cudaEventRecord(S->h_done, s) != cudaSuccess) return gs::check_launch("session analysis event");
+  S->h_pending = true;
+  return gs::check_launch("session analyze");
 }
 
 gs_status gs_session_inject_alloc_failures(gs_session* S, int32_t count) {
@@ -1228,8 +1447,7 @@ gs_status gs_session_destroy(gs_session* S) {
   for (auto& a : S->arena) gs::dfree(a, S->in_use);
   gs::dfree(S->status_word, S->in_use);
   gs::dfree(S->step_dev, S->in_use);
-  gs::dfree(S->lod_parent, S->in_use);
-  gs::dfree(S->lod_ws, S->in_use);
+  gs::free_hier(S);
   gs::dfree(S->kf_of, S->in_use);
   gs::dfree(S->sim3, S->in_use);
   gs::dfree(S->sim3_status, S->in_use);

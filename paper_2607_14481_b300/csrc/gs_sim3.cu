@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(256) k_sim3_update(float4* __restrict__ means4
 // Leaf Gaussians per keyframe (integer counts: the order of the atomics does
 // not show); ids outside [0, num_kf) are not counted.
 __global__ void __launch_bounds__(256) k_keyframe_counts(const int32_t* __restrict__ kf, int64_t n, int32_t num_kf,
-                                                         uint32_t* __restrict__ counts) {
+                                                         uint32_t* __restrict__ counts,
+                                                         const uint8_t* __restrict__ active) {
   extern __shared__ uint32_t s_c[];
   const bool local = num_kf <= 8192;  // histogram in shared memory
   if (local)
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(256) k_keyframe_counts(const int32_t* __restri
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k = kf[i];
-    if (k < 0 || k >= num_kf) continue;
+    if (k < 0 || k >= num_kf || (active && !active[i])) continue;
     atomicAdd(local ? &s_c[k] : &counts[k], 1u);
   }
   __syncthreads();
@@ -68,14 +69,15 @@ __global__ void k_fill_i32(int32_t* p, int32_t v, int64_t n) {
 
 }  // namespace
 
-gs_status launch_keyframe_counts(const int32_t* kf, int64_t n, int32_t num_kf, uint32_t* counts, cudaStream_t s) {
+gs_status launch_keyframe_counts(const int32_t* kf, int64_t n, int32_t num_kf, uint32_t* counts, cudaStream_t s,
+                                 const uint8_t* active) {
   if (num_kf <= 0) return GS_OK;
   if (cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)num_kf, s) != cudaSuccess)
     return check_launch("keyframe counts");
   if (n <= 0) return GS_OK;
   const unsigned grid = (unsigned)std::min<int64_t>(592, (n + 255) / 256);
   const size_t smem = num_kf <= 8192 ? sizeof(uint32_t) * (size_t)num_kf : 0;
-  k_keyframe_counts<<<grid, 256, smem, s>>>(kf, n, num_kf, counts);
+  k_keyframe_counts<<<grid, 256, smem, s>>>(kf, n, num_kf, counts, active);
   return check_launch("k_keyframe_counts");
 }
 

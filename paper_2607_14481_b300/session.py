@@ -18,9 +18,9 @@ def default_config(max_gaussians: int, sh_degree: int = 3, max_batch_views: int 
                    lr_means=1.6e-4, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3, lr_sh_dc=2.5e-3,
                    lr_sh_rest=1.25e-4, lod: bool = False, lod_tau: float = 1.0,
                    tile=(16, 16)) -> _lib.GsSessionConfig:
-    """lod: render requests go through the three-level hierarchy's cut at
-    lod_tau pixels (rebuilt before the first render after Gaussians were
-    added); train requests always use the leaves.  tile: 16x16, 32x8 or 8x32."""
+    """lod: a progressive hierarchy (merge below lod_tau / 2 px, reload above
+    lod_tau px, analysed by Session.analyze); renders and trains use each
+    view's cut of its active set.  tile: 16x16, 32x8 or 8x32."""
     raster = _lib.GsRasterCfg(int(tile[0]), int(tile[1]), (C.c_float * 3)(*bg), float(znear), 1)
     return _lib.GsSessionConfig(int(max_gaussians), int(sh_degree), int(max_batch_views), int(max_width),
                                 int(max_height), int(max_inflight), int(hbm_budget_gb * (1 << 30)),
@@ -144,6 +144,34 @@ class Session:
 
     def drain(self, timeout_ms: int = 120000) -> None:
         _lib.check(self.L.gs_session_drain(self.h, timeout_ms), "gs_session_drain")
+
+    def analyze(self, cam: Camera) -> bool:
+        """gs_session_analyze from a new keyframe's camera: the hierarchy's
+        merge and reload run into the back buffer of the active set.  Returns
+        False when the previous analysis is still running (nothing issued)."""
+        c = _lib.GsCamera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+        pose = (C.c_float * 12)(*np.asarray(cam.pose12(), np.float32).tolist())
+        st = self.L.gs_session_analyze(self.h, C.byref(c), pose)
+        if st == _lib.GS_ERR_BUSY:
+            return False
+        _lib.check(st, "gs_session_analyze")
+        return True
+
+    def hierarchy(self) -> dict:
+        """gs_session_read_hierarchy: the node rows in use (leaf slots, then
+        merged nodes) with their parameters, links and front active flags."""
+        rows = C.c_int64(0)
+        _lib.check(self.L.gs_session_read_hierarchy(self.h, 0, C.byref(rows), None, None, None, None, None, None,
+                                                    None), "gs_session_read_hierarchy")
+        n = rows.value
+        out = {"means4": np.zeros((n, 4), np.float32), "scale_opa": np.zeros((n, 4), np.float32),
+               "quat": np.zeros((n, 4), np.float32), "sh": np.zeros((3 * self.nc, n), np.float32),
+               "parent": np.zeros(n, np.int32), "child": np.zeros((n, 4), np.int32),
+               "active": np.zeros(n, np.uint8)}
+        _lib.check(self.L.gs_session_read_hierarchy(self.h, n, C.byref(rows), *(out[k].ctypes.data for k in (
+            "means4", "scale_opa", "quat", "sh", "parent", "child", "active"))), "gs_session_read_hierarchy")
+        assert rows.value == n
+        return out
 
     def inject_alloc_failures(self, count: int) -> None:
         """The session's next `count` device allocations fail as if the

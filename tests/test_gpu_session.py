@@ -186,40 +186,89 @@ def test_empty_scene_renders_background(cuda_device):
         assert np.all(img[ch] == np.float32(b))
 
 
-def test_lod_render_equals_direct_hierarchy_and_rebuilds_on_add(cuda_device):
-    """Render requests through the session's level-of-detail cut give the
-    image of the direct pipeline (gs_lod_build + gs_project_lod); Gaussians
-    added later trigger a rebuild before the next render."""
+def _clustered_scene(clusters, per, seed):
+    """Tight clusters of `per` tiny Gaussians (a fraction of a pixel from a
+    camera at the origin looking down +z, focal 300): a merged cluster stays
+    below a pixel, so it stays in the active set after the reload."""
+    g = np.random.default_rng(seed)
+    z = g.uniform(10, 30, clusters)
+    centres = np.column_stack([g.uniform(-0.4, 0.4, clusters) * z, g.uniform(-0.3, 0.3, clusters) * z, z])
+    means = np.repeat(centres, per, axis=0) + g.normal(0, 0.002, (clusters * per, 3)) * np.repeat(z, per)[:, None] / 20
+    zz = means[:, 2]
+    S = g.uniform(0.05, 0.3, len(zz))
+    ls = np.log(S * zz / 900.0)[:, None] - np.abs(g.normal(0, 0.2, (len(zz), 3)))
+    base = synth.random_scene(len(zz), seed + 1, 1, (0, 0, 0), (1, 1, 1), 0.0, 1.0)
+    return synth.Scene(means.astype(np.float32), ls.astype(np.float32), base.quats, base.opa_logits, base.sh)
+
+
+def test_progressive_hierarchy_in_the_session(cuda_device):
+    """The session's progressive hierarchy (lod = 1).  Before any analysis
+    every added leaf is active and a render equals the plain render.  An
+    analysis from a keyframe's camera (merge below tau / 2, then reload above
+    tau) gives the node rows, links, active flags and merged parameters of
+    the direct gs_hier_analyze + gs_hier_refine, and renders through the
+    view cut equal the direct gs_project_hier path while blending fewer
+    splats.  A training request then updates merged nodes of the cut and
+    leaves the merged-away leaves alone; keyframe counts cover the active
+    nodes (merged nodes take their children's keyframe)."""
     ensure_built()
-    sc = synth.random_scene(6000, 12, 1, (-4, -1, -4), (4, 1, 4), -2.5, 0.5)
-    cam = synth.look_at((0.0, -0.5, -40.0), (0, 0, 0), 300.0, 300.0, 160, 120, 320, 240)
-    tau = 16.0
-    more = synth.random_scene(500, 13, 1, (-4, -1, -4), (4, 1, 4), -2.5, 0.5)
-    with session.Session(_cfg(sc.n + more.n, sh_degree=1, lod=True, lod_tau=tau)) as s:
+    n = 4000
+    sc = _clustered_scene(n // 4, 4, seed=3)
+    far = synth.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 300.0, 300.0, 320.0, 240.0, 640, 480)
+    dev = torch.device("cuda:0")
+    cfg = _cfg(n, sh_degree=1, lod=True, lod_tau=1.0, max_width=640, max_height=480, max_batch_views=2,
+               lr_means=1e-2, lr_sh_dc=1e-2)
+    with session.Session(cfg) as s:
+        s.set_keyframe(0)
         s.add(sc)
-        a = s.wait(s.submit(RENDER, cam, want_image=True))
-        st1 = s.stats()
-        s.add(more)
-        b = s.wait(s.submit(RENDER, cam, want_image=True))
+        img0 = s.wait(s.submit(RENDER, far, want_image=True))
+        assert s.analyze(far)
+        s.drain()
+        st = s.stats()
+        h = s.hierarchy()
+        img1 = s.wait(s.submit(RENDER, far, want_image=True))
+        kw = s.keyframe_weights(1, min_keep=0)
+        s.wait(s.submit(TRAIN, far, target=_targets([far], seed=5)[0]))
+        h2 = s.hierarchy()
         st2 = s.stats()
-    assert st1["lod_builds"] == 1 and st2["lod_builds"] == 2
-
-    def direct(scene):
-        dev = torch.device("cuda:0")
-        cap = int(_lib.load().gs_lod_nodes(scene.n))
-        arena = raster.Arena.from_scene(scene, dev, capacity=cap)
-        lod = raster.LodHierarchy(arena, scene.n)
-        lod.build()
-        r = raster.Rasterizer(lod.n_nodes, scene.sh_degree, [cam], device=dev)
-        img, _ = r.forward(arena, raster.poses_tensor([cam], dev), r.new_image(), None, lod=lod, tau=tau)
-        torch.cuda.synchronize()
-        return r.split(img.cpu(), 3)[0].numpy()
-
-    assert np.array_equal(a, direct(sc))
-    both = synth.Scene(*(np.concatenate([x, y]) for x, y in zip(
-        (sc.means, sc.log_scales, sc.quats, sc.opa_logits, sc.sh),
-        (more.means, more.log_scales, more.quats, more.opa_logits, more.sh))))
-    assert np.array_equal(b, direct(both))
+    assert np.array_equal(img0, _direct_render(sc, far))
+    assert st["lod_builds"] == 1 and st2["iterations"] == 1 and st2["failed"] == 0
+    # the direct path on an arena of the same rows
+    arena = raster.Arena.from_scene(sc, dev, capacity=2 * n)
+    hier = raster.Hierarchy(arena, n)
+    hier.analyze(far, tau_l=0.5)
+    hier.refine(far, tau_h=1.0, passes=16)
+    d = hier.state()
+    rows = d["n_nodes"]
+    assert rows > n and len(h["active"]) == rows
+    assert np.array_equal(h["parent"], d["parent"][:rows])
+    assert np.array_equal(h["child"], d["child"][:rows])
+    assert np.array_equal(h["active"], d["active"][:rows])
+    buf = arena.buf.cpu().numpy()
+    cap = 2 * n
+    assert np.array_equal(h["means4"], buf[0:4 * cap].reshape(cap, 4)[:rows])
+    assert np.array_equal(h["scale_opa"], buf[4 * cap:8 * cap].reshape(cap, 4)[:rows])
+    assert np.array_equal(h["quat"], buf[8 * cap:12 * cap].reshape(cap, 4)[:rows])
+    assert np.array_equal(h["sh"], buf[12 * cap:12 * cap + 12 * cap].reshape(12, cap)[:, :rows])
+    r = raster.Rasterizer(rows, 1, [far], device=dev)
+    r.project_hier(hier, raster.poses_tensor([far], dev), tau_h=1.0)
+    r.bin_sort()
+    img = r.new_image()
+    r.render_fwd(img, None)
+    torch.cuda.synchronize()
+    assert np.array_equal(img1, r.split(img.cpu(), 3)[0].numpy())
+    cut = int((r.splat_arrays()["touched"][0] > 0).sum())
+    plain = raster.Rasterizer(n, 1, [far], device=dev)
+    plain.project(raster.Arena.from_scene(sc, dev), raster.poses_tensor([far], dev))
+    assert cut < int((plain.splat_arrays()["touched"][0] > 0).sum())
+    assert int(kw["counts"][0]) == int(h["active"].sum())
+    # training: merged nodes of the cut move, merged-away leaves do not
+    merged = np.flatnonzero(h["active"][n:] == 1) + n
+    away = np.flatnonzero(h["active"][:n] == 0)
+    assert len(merged) > 0 and len(away) > 0
+    assert np.any(h2["means4"][merged] != h["means4"][merged])
+    assert np.array_equal(h2["means4"][away], h["means4"][away])
+    assert np.array_equal(h2["sh"][:, away], h["sh"][:, away])
 
 
 def test_loop_closure_moves_gaussians_with_their_keyframe(cuda_device):
