@@ -7,18 +7,21 @@
 //      per-(view, Gaussian) tile counts gives every visible splat a
 //      contiguous block of pair slots (pair_off, emission order: what the
 //      backward indexes its per-pair gradients by), and
-//   2. in the same launch every pair takes a place in its tile with one
-//      shared-counter atomic (the counters live in the ranges array);
-//   3. one CTA scans the tiles' counts into list starts (and, when asked,
-//      orders the tiles longest list first); every pair writes its
-//      (depth bits, Gaussian id) key at start + place;
-//   4. one CTA per tile sorts its list in shared memory (stable radix passes,
-//      up to kShortList keys; longer lists go through global memory) and
-//      writes the ids and the tile's range.
+//   2. in the same launch every pair is counted in its tile (a reduction
+//      into the ranges array, nothing waits for it);
+//   3. one CTA scans the tiles' counts into list starts, sets each tile's
+//      cursor to its start and groups the tiles by list length (and, when
+//      asked, orders them longest list first);
+//   4. every pair takes the next place of its tile's cursor and writes its
+//      (depth bits, Gaussian id) key there;
+//   5. each tile's list is sorted: lists of fewer than 256 keys by one warp
+//      in registers (eight tiles per CTA), longer ones by a CTA in shared
+//      memory (bitonic networks), the few beyond 4096 keys by stable radix
+//      passes through global memory; the sort writes the ids.
 // Within a tile every Gaussian appears once, so (depth bits, id) keys are
 // distinct and the sorted list is unique: the atomics' order never shows.
 // This is the order of one sort of 64-bit (tile, depth) keys with depth ties
-// in id order, with ~40 bytes moved per pair in five launches.
+// in id order, with ~30 bytes moved per pair in five launches.
 //
 // Every count (visible items, pairs) stays in device memory: kernels are
 // launched for the capacity and read the live count, so the whole stage runs
@@ -36,7 +39,6 @@ constexpr int kIPT = 8;                      // items per thread (scans)
 constexpr int kItemsPerBlock = kThreads * kIPT;
 constexpr int kRadixBits = 8;                // long-list fallback sort
 constexpr int kRadixDigits = 1 << kRadixBits;
-constexpr uint32_t kShortList = 2048;        // tile lists sorted in shared memory
 constexpr int64_t kMaxScanTiles = 1ll << 25; // bound of the tile scan's workspace
 
 __device__ __forceinline__ uint32_t num_blocks(uint32_t n) {
@@ -269,6 +271,11 @@ __global__ void k_init_counts(uint32_t* counts, uint32_t* scalars, uint32_t m, u
   counts[0] = 0; counts[1] = 0; counts[2] = 0; counts[3] = 0;
 }
 
+// Items with at least kWide pairs (splats covering many tiles) are keyed in
+// chunks of kWideChunk pairs, one warp per chunk, so that no warp walks a
+// long item alone.
+constexpr uint32_t kWide = 128, kWideChunk = 128;
+
 struct PairArgs {
   const uint32_t* touched;
   const uint2* rect;
@@ -277,33 +284,43 @@ struct PairArgs {
   uint32_t* counts;
   int64_t n;
   int64_t cap;
-  uint32_t* ranges;          // [tiles][2]: (start, count) while binning
-  uint32_t* slot;            // [cap] place of each pair within its tile
+  uint32_t* ranges;          // [tiles][2]: word 1 counts the tile's pairs, then (start, cursor), then (start, end)
   uint64_t* keys;            // [cap] (depth bits << 32 | id) at the pair's list position
+  unsigned long long* wide_count;  // (chunks << 32 | items) of the wide items, zero at launch
+  uint2* wide_chunks;        // [wide_cap] (item, first pair of the chunk)
+  uint32_t wide_cap;
 };
+
+// The next place in the tile's list (the tile's cursor).
+__device__ __forceinline__ uint32_t take_place(const PairArgs& a, uint32_t tile) {
+  return atomicAdd(&a.ranges[2 * (uint64_t)tile + 1], 1u);
+}
 
 // Warp-cooperative walk over the pairs of 32 consecutive (view, Gaussian)
 // items starting at j0: the warp scans the items' pair counts and its lanes
 // take the pairs 32 at a time, each finding its item by a binary search over
-// the scan, so the lanes stay busy whatever the mix of small and large splats
-// and every pair's memory operations of a round are in flight together.
-// Pairs of an item are its rect's tiles in row-major order.  `off` is the
-// lane's item's first pair slot (its pair_off).  Returns the visible items of
-// the group (touched > 0).
-// PLACE: take each pair's place in its tile (count the tile, note the place);
-// otherwise write its key at the tile's start + place.
-template <bool PLACE>
-__device__ __forceinline__ uint32_t warp_pairs(const PairArgs& a, const ViewTable& vt, int64_t j0, uint32_t off) {
+// the scan, so the lanes stay busy whatever the mix of small and large splats.
+// Pairs of an item are its rect's tiles in row-major order; `off` is the
+// lane's item's first pair slot (its pair_off), tch its tile count, rc its
+// rect and dep its depth (loaded by the caller).  Pairs at slots >= cap
+// (capacity overflow) are skipped by both passes.  Returns the visible items
+// of the group (touched > 0).
+// KEYS = false: count every pair in its tile (a reduction without return, no
+// wait); true: take the next place of the tile's cursor and write the pair's
+// key there.
+template <bool KEYS>
+__device__ __forceinline__ uint32_t warp_pairs(const PairArgs& a, const ViewTable& vt, int64_t j0, uint32_t off,
+                                               uint32_t tch, uint2 rc, float dep) {
   const int64_t m = a.n * vt.views;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t j = j0 + lane;
-  bool ok = j < m && a.touched[j] > 0u;
+  bool ok = j < m && tch > 0u;
   const uint32_t vis = (uint32_t)__popc(__ballot_sync(full, ok));
+  if (KEYS && tch >= kWide) ok = false;  // keyed by the wide pass, in balanced chunks
   uint32_t x0y0 = 0, w = 1, cnt = 0, key_hi = 0, tb = 0, tx_n = 1, gid = 0;
   if (ok) {
     const int v = (int)(j / a.n);
-    const uint2 rc = a.rect[j];
     const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
     if (x1 >= vt.v[v].TX || y1 >= vt.v[v].TY || x0 > x1 || y0 > y1) {
       atomicOr(&a.counts[2], kStatusIndex);
@@ -312,11 +329,11 @@ __device__ __forceinline__ uint32_t warp_pairs(const PairArgs& a, const ViewTabl
       x0y0 = rc.x;
       w = (uint32_t)(x1 - x0 + 1);
       // never beyond the item's own block of slots
-      cnt = min(w * (uint32_t)(y1 - y0 + 1), a.touched[j]);
+      cnt = min(w * (uint32_t)(y1 - y0 + 1), tch);
       tb = (uint32_t)vt.v[v].tile_base;
       tx_n = (uint32_t)vt.v[v].TX;
-      if (!PLACE) {
-        key_hi = __float_as_uint(a.depth[j]);  // positive floats order like their bits
+      if (KEYS) {
+        key_hi = __float_as_uint(dep);  // positive floats order like their bits
         gid = (uint32_t)(j - (int64_t)v * a.n);
       }
     }
@@ -329,57 +346,125 @@ __device__ __forceinline__ uint32_t warp_pairs(const PairArgs& a, const ViewTabl
   }
   const uint32_t total = __shfl_sync(full, incl, 31);
   const uint32_t excl = incl - cnt;
-  for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t q = base + lane;
-    // owner: the number of lanes whose inclusive count is <= q
-    int o = 0;
+  // rounds of 32 pairs, kRounds at a time: the key pass issues the rounds'
+  // cursor atomics together and only then waits for their places
+  constexpr int kRounds = KEYS ? 4 : 1;
+  for (uint32_t base = 0; base < total; base += 32 * kRounds) {
+    uint32_t pos[kRounds];
+    uint64_t key[kRounds];
 #pragma unroll
-    for (int step = 16; step > 0; step >>= 1)
-      if (__shfl_sync(full, incl, o + step - 1) <= q) o += step;
-    const uint32_t so = __shfl_sync(full, off, o), se = __shfl_sync(full, excl, o);
-    const uint32_t sxy = __shfl_sync(full, x0y0, o), sw = __shfl_sync(full, w, o);
-    const uint32_t stb = __shfl_sync(full, tb, o), stx = __shfl_sync(full, tx_n, o);
-    const uint32_t skey = __shfl_sync(full, key_hi, o), sg = __shfl_sync(full, gid, o);
-    if (q >= total) continue;
-    const uint32_t t = q - se;
-    const uint64_t p = (uint64_t)so + t;
-    if ((int64_t)p >= a.cap) continue;
-    const uint32_t tile = stb + ((sxy >> 16) + t / sw) * stx + (sxy & 0xffff) + t % sw;
-    if (PLACE) {
-      a.slot[p] = atomicAdd(&a.ranges[2 * (uint64_t)tile + 1], 1u);
-    } else {
-      const uint64_t pos = (uint64_t)a.ranges[2 * (uint64_t)tile] + a.slot[p];
-      if ((int64_t)pos < a.cap) {
-        a.keys[pos] = ((uint64_t)skey << 32) | sg;
+    for (int rr = 0; rr < kRounds; ++rr) {
+      pos[rr] = 0xffffffffu;
+      key[rr] = 0ull;
+    }
+#pragma unroll
+    for (int rr = 0; rr < kRounds; ++rr) {
+      const uint32_t q = base + 32 * rr + lane;
+      if (base + 32 * rr >= total) break;  // warp-uniform
+      // owner: the number of lanes whose inclusive count is <= q
+      int o = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(full, incl, o + step - 1) <= q) o += step;
+      const uint32_t so = __shfl_sync(full, off, o), se = __shfl_sync(full, excl, o);
+      const uint32_t sxy = __shfl_sync(full, x0y0, o), sw = __shfl_sync(full, w, o);
+      const uint32_t stb = __shfl_sync(full, tb, o), stx = __shfl_sync(full, tx_n, o);
+      const uint32_t skey = KEYS ? __shfl_sync(full, key_hi, o) : 0u;
+      const uint32_t sg = KEYS ? __shfl_sync(full, gid, o) : 0u;
+      if (q >= total) continue;
+      const uint32_t t = q - se;
+      if ((int64_t)so + t >= a.cap) continue;
+      const uint32_t tile = stb + ((sxy >> 16) + t / sw) * stx + (sxy & 0xffff) + t % sw;
+      if (!KEYS) {
+        atomicAdd(&a.ranges[2 * (uint64_t)tile + 1], 1u);  // result unused: a reduction
       } else {
-        atomicOr(&a.counts[2], kStatusIndex);
+        pos[rr] = take_place(a, tile);
+        key[rr] = ((uint64_t)skey << 32) | sg;
+      }
+    }
+    if (KEYS) {
+#pragma unroll
+      for (int rr = 0; rr < kRounds; ++rr) {
+        if (pos[rr] == 0xffffffffu) continue;
+        if ((int64_t)pos[rr] < a.cap) {
+          a.keys[pos[rr]] = key[rr];
+        } else {
+          atomicOr(&a.counts[2], kStatusIndex);
+        }
       }
     }
   }
   return vis;
 }
 
-// One warp per 32 items (the key pass, and the place pass of the multi-kernel
-// path): offsets from pair_off.
-template <bool PLACE>
-__global__ void __launch_bounds__(256) k_pairs(const PairArgs a, const ViewTable vt) {
+// The key pass: one warp per 32 items, offsets from pair_off.
+__global__ void __launch_bounds__(256) k_keys(const PairArgs a, const ViewTable vt) {
   const int64_t m = a.n * vt.views;
   const int64_t j0 = ((int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
   if (j0 >= m) return;  // warp-uniform
   const int64_t j = j0 + (threadIdx.x & 31);
-  const uint32_t off = j < m ? a.pair_off[j] : 0u;
-  const uint32_t vis = warp_pairs<PLACE>(a, vt, j0, off);
-  if (PLACE && (threadIdx.x & 31) == 0 && vis) atomicAdd(&a.counts[0], vis);
+  // every load of the item at once (not waiting for its count)
+  const bool in = j < m;
+  const uint32_t tch = in ? a.touched[j] : 0u;
+  const uint32_t off = in ? a.pair_off[j] : 0u;
+  const uint2 rc = in ? a.rect[j] : make_uint2(0u, 0u);
+  const float dep = in ? a.depth[j] : 0.f;
+  warp_pairs<true>(a, vt, j0, off, tch, rc, dep);
+}
+
+// The wide items' key pass: warps take chunks of kWideChunk pairs (grid
+// stride); the lanes of a round take 32 consecutive pairs of the chunk, with
+// the cursor atomics of the chunk's rounds issued together.
+__global__ void __launch_bounds__(256) k_keys_wide(const PairArgs a, const ViewTable vt) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nchunks = min((uint32_t)(*a.wide_count >> 32), a.wide_cap);
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    const uint2 wc = a.wide_chunks[c];
+    const int64_t j = wc.x;
+    const uint32_t tch = a.touched[j], off = a.pair_off[j];
+    const uint2 rc = a.rect[j];
+    const float dep = a.depth[j];
+    const int v = (int)(j / a.n);
+    const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
+    if (x1 >= vt.v[v].TX || y1 >= vt.v[v].TY || x0 > x1 || y0 > y1) {
+      if (lane == 0) atomicOr(&a.counts[2], kStatusIndex);
+      continue;
+    }
+    const uint32_t w = (uint32_t)(x1 - x0 + 1);
+    const uint32_t cnt = min(w * (uint32_t)(y1 - y0 + 1), tch);
+    const uint32_t tb = (uint32_t)vt.v[v].tile_base, tx_n = (uint32_t)vt.v[v].TX;
+    const uint64_t key = ((uint64_t)__float_as_uint(dep) << 32) | (uint32_t)(j - (int64_t)v * a.n);
+    constexpr int kR = kWideChunk / 32;
+    uint32_t pos[kR];
+#pragma unroll
+    for (int rr = 0; rr < kR; ++rr) {
+      pos[rr] = 0xffffffffu;
+      const uint32_t t = wc.y + 32 * rr + lane;
+      if (t >= cnt || (int64_t)off + t >= a.cap) continue;
+      const uint32_t tile = tb + ((uint32_t)y0 + t / w) * tx_n + (uint32_t)x0 + t % w;
+      pos[rr] = take_place(a, tile);
+    }
+#pragma unroll
+    for (int rr = 0; rr < kR; ++rr) {
+      if (pos[rr] == 0xffffffffu) continue;
+      if ((int64_t)pos[rr] < a.cap) {
+        a.keys[pos[rr]] = key;
+      } else {
+        atomicOr(&a.counts[2], kStatusIndex);
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Single-pass scan of the items' tile counts with decoupled look-back, fused
-// with the place pass.  Each CTA takes the next partition of 2048 items from
+// with the count pass.  Each CTA takes the next partition of 2048 items from
 // a counter (so a CTA only ever waits for partitions taken before it, whose
 // CTAs are already running), scans its counts, publishes its total, finds
 // its prefix from the published words of the partitions before it (a warp
 // reads 32 of them at a time), publishes its inclusive prefix, writes the
-// pair offsets and then places its items' pairs in their tiles.  The waits
+// pair offsets and then counts its items' pairs in their tiles.  The waits
 // are bounded (kLookbackNs of %globaltimer): on expiry the CTA sets status
 // bit 4 in counts[2] and carries on with a wrong prefix (the result is then
 // flagged invalid, the launch still ends).
@@ -388,7 +473,7 @@ constexpr unsigned long long kFlagAgg = 1ull << 32, kFlagInc = 2ull << 32;
 constexpr uint32_t kStatusTimeout = 16u;
 constexpr unsigned long long kLookbackNs = 2000000000ull;  // 2 s
 
-struct ScanPlaceArgs {
+struct ScanCountArgs {
   PairArgs p;
   unsigned long long* state;  // [parts] look-back words (flag << 32 | value), zero at launch
   uint32_t* ticket;           // partition counter, zero at launch
@@ -401,10 +486,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__global__ void __launch_bounds__(kThreads) k_scan_place(const ScanPlaceArgs a, const ViewTable vt) {
+__global__ void __launch_bounds__(kThreads) k_scan_count(const ScanCountArgs a, const ViewTable vt) {
   __shared__ uint32_t s_warp[kThreads / 32 + 1];
   __shared__ uint32_t s_part, s_prefix, s_vis;
-  __shared__ uint32_t s_off[kItemsPerBlock];
+  __shared__ uint32_t s_off[kItemsPerBlock], s_cnt[kItemsPerBlock];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t m = a.p.n * vt.views;
   if (threadIdx.x == 0) {
@@ -466,8 +551,19 @@ __global__ void __launch_bounds__(kThreads) k_scan_place(const ScanPlaceArgs a, 
 #pragma unroll
   for (int r = 0; r < kIPT; ++r) {
     s_off[threadIdx.x * kIPT + r] = run;
+    s_cnt[threadIdx.x * kIPT + r] = x[r];
     if ((int64_t)(base + r) < m) a.p.pair_off[base + r] = run;
     run += x[r];
+  }
+  // wide items: reserve their chunks (one atomic for the item and its chunks)
+#pragma unroll
+  for (int r = 0; r < kIPT; ++r) {
+    if (x[r] < kWide) continue;
+    const uint32_t nch = (x[r] + kWideChunk - 1) / kWideChunk;
+    const unsigned long long old = atomicAdd(a.p.wide_count, ((unsigned long long)nch << 32) | 1ull);
+    const uint32_t c0 = (uint32_t)(old >> 32);
+    for (uint32_t c = 0; c < nch; ++c)
+      if (c0 + c < a.p.wide_cap) a.p.wide_chunks[c0 + c] = make_uint2((uint32_t)(base + r), c * kWideChunk);
   }
   if (part == a.parts - 1 && threadIdx.x == kThreads - 1) {
     // the last partition knows the number of pairs
@@ -477,26 +573,152 @@ __global__ void __launch_bounds__(kThreads) k_scan_place(const ScanPlaceArgs a, 
     a.p.counts[3] = (int64_t)K > a.p.cap ? (uint32_t)a.p.cap : K;
   }
   __syncthreads();
-  // place pass: warp w takes the partition's 32-item groups w, w + 8, ...
+  // count pass: warp w takes the partition's 32-item groups w, w + 8, ...;
+  // the rects of all its visible items are loaded first
+  constexpr int kGroups = kItemsPerBlock / 32 / (kThreads / 32);
+  uint2 rc[kGroups];
+#pragma unroll
+  for (int i = 0; i < kGroups; ++i) {
+    const int g = warp + i * (kThreads / 32);
+    const uint64_t jj = pbase + (uint64_t)g * 32 + lane;
+    rc[i] = s_cnt[g * 32 + lane] ? a.p.rect[jj] : make_uint2(0u, 0u);
+  }
   uint32_t vis = 0;
-  for (int g = warp; g < kItemsPerBlock / 32; g += kThreads / 32) {
+#pragma unroll
+  for (int i = 0; i < kGroups; ++i) {
+    const int g = warp + i * (kThreads / 32);
     const int64_t j0 = (int64_t)(pbase + (uint64_t)g * 32);
     if (j0 >= m) break;
-    vis += warp_pairs<true>(a.p, vt, j0, s_off[g * 32 + lane]);
+    vis += warp_pairs<false>(a.p, vt, j0, s_off[g * 32 + lane], s_cnt[g * 32 + lane], rc[i], 0.f);
   }
   if (lane == 0 && vis) atomicAdd(&s_vis, vis);
   __syncthreads();
   if (threadIdx.x == 0 && s_vis) atomicAdd(&a.p.counts[0], s_vis);
 }
 
-struct TileSortArgs {
-  uint64_t* keys;       // [cap] tile lists, unsorted
-  uint64_t* keys_b;     // [cap] ping-pong buffer of lists too long for shared memory
-  uint32_t* ranges;     // [tiles][2]: (start, count) in, (start, end) out; (0, 0) when empty
-  uint32_t* vals;       // [cap] Gaussian ids in list order
-  uint64_t* full_keys;  // optional: (tile << 32 | depth bits) in list order
-  int id_bits;          // significant bits of the id (low word)
-};
+// ---------------------------------------------------------------------------
+// Tile scan: counts -> list starts, the cursors of the key pass, and the
+// tiles grouped by list length.  Tiles go into power-of-two buckets: bucket 0
+// holds lists of >= 2^15 pairs, bucket 15 single pairs, bucket 16 the empty
+// tiles.  The order within a bucket follows the atomics and does not matter.
+// Bucket counts go to bucket_count[17]; the non-empty tiles in bucket order
+// to `work` (what the tile sort takes its work from), and, when asked, all
+// tiles in bucket order (longest list first, empty tiles last) to `order`.
+// An empty tile's range becomes (0, 0).
+// ---------------------------------------------------------------------------
+constexpr int kTileScanThreads = 1024;
+constexpr int64_t kTileScanMax = 1ll << 18;
+constexpr int kOrderBuckets = 17;
+constexpr int kShortBucket = 8;  // buckets >= 8 (lists of < 256 pairs) are sorted by one warp
+
+__device__ __forceinline__ int order_bucket(uint32_t len) {
+  return len == 0 ? kOrderBuckets - 1 : 15 - min(15, 31 - __clz(len));
+}
+
+// One CTA of 1024 threads (thread t takes a contiguous run of tiles), for up
+// to kTileScanMax tiles; more go through the multi-kernel form below.
+__global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(uint32_t* __restrict__ ranges, uint32_t tiles,
+                                                                 uint32_t* __restrict__ bucket_count,
+                                                                 uint32_t* __restrict__ work,
+                                                                 uint32_t* __restrict__ order) {
+  constexpr int NW = kTileScanThreads / 32;
+  __shared__ uint32_t s_warp[NW + 1];
+  __shared__ uint32_t s_count[kOrderBuckets], s_base[kOrderBuckets];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t per = (tiles + kTileScanThreads - 1) / kTileScanThreads;
+  const uint32_t lo = min(tiles, threadIdx.x * per), hi = min(tiles, lo + per);
+  if (threadIdx.x < kOrderBuckets) s_count[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t sum = 0;
+  for (uint32_t t = lo; t < hi; ++t) {
+    const uint32_t c = ranges[2 * (uint64_t)t + 1];
+    sum += c;
+    atomicAdd(&s_count[order_bucket(c)], 1u);
+  }
+  // block-wide exclusive scan of the per-thread sums
+  uint32_t inc = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < NW ? s_warp[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += y;
+    }
+    if (lane < NW) s_warp[lane] = wi - w;
+  }
+  if (threadIdx.x == 0) {
+    uint32_t b0 = 0;
+    for (int b = 0; b < kOrderBuckets; ++b) {
+      bucket_count[b] = s_count[b];
+      s_base[b] = b0;
+      b0 += s_count[b];
+      s_count[b] = 0;
+    }
+  }
+  __syncthreads();
+  const uint32_t nonempty = s_base[kOrderBuckets - 1];
+  uint32_t run = s_warp[warp] + inc - sum;
+  for (uint32_t t = lo; t < hi; ++t) {
+    const uint32_t c = ranges[2 * (uint64_t)t + 1];
+    const int b = order_bucket(c);
+    const uint32_t pos = s_base[b] + atomicAdd(&s_count[b], 1u);
+    if (order) order[pos] = t;
+    if (pos < nonempty) work[pos] = t;
+    // the start, and the key pass's cursor; (0, 0) when empty
+    const uint32_t st = c ? run : 0u;
+    ranges[2 * (uint64_t)t] = st;
+    ranges[2 * (uint64_t)t + 1] = st;
+    run += c;
+  }
+}
+
+// The multi-kernel form, for more tiles (after a device-wide scan has put
+// the starts in ranges[2t], the counts still in ranges[2t + 1]): bucket
+// counts, then placement (which also sets the cursors and empty ranges).
+__global__ void __launch_bounds__(kThreads) k_order_count(const uint32_t* __restrict__ ranges, uint32_t tiles,
+                                                          uint32_t* __restrict__ bucket_count) {
+  __shared__ uint32_t s[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) s[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x)
+    atomicAdd(&s[order_bucket(ranges[2 * (uint64_t)t + 1])], 1u);
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets && s[threadIdx.x]) atomicAdd(&bucket_count[threadIdx.x], s[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_order_place(uint32_t* __restrict__ ranges, uint32_t tiles,
+                                                          const uint32_t* __restrict__ bucket_count,
+                                                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ work,
+                                                          uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_base[kOrderBuckets];
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < kOrderBuckets; ++b) {
+      s_base[b] = run;
+      run += bucket_count[b];
+    }
+  }
+  __syncthreads();
+  const uint32_t nonempty = s_base[kOrderBuckets - 1];
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
+    const uint32_t c = ranges[2 * (uint64_t)t + 1];
+    const int b = order_bucket(c);
+    const uint32_t pos = s_base[b] + atomicAdd(&cursor[b], 1u);
+    if (order && pos < tiles) order[pos] = t;
+    if (pos < nonempty) work[pos] = t;
+    const uint32_t st = c ? ranges[2 * (uint64_t)t] : 0u;
+    ranges[2 * (uint64_t)t] = st;
+    ranges[2 * (uint64_t)t + 1] = st;
+  }
+}
 
 // One stable CTA-wide LSD radix pass over src[0, cnt) on key bits
 // [lo, lo + 8), writing dst (shared or global memory).  A digit histogram of
@@ -590,157 +812,235 @@ __device__ uint64_t* cta_radix_sort(uint64_t* a, uint64_t* b, uint32_t cnt, int 
   return a;
 }
 
-// One CTA per tile: sort the tile's (depth bits << 32 | id) keys, write the
-// ids (and optionally the full keys) and the tile's [start, end) range.
-// Stable passes over the depth bits order the list by depth (a pass whose
-// digit is the same for every key is skipped); a tile in which two keys share
-// a depth is then sorted again over id and depth bits (stable LSD: id first),
-// which leaves equal depths in id order.  Lists of up to kShortList keys are
-// sorted in shared memory, longer ones through global memory.
-__global__ void __launch_bounds__(kThreads) k_tile_sort(const TileSortArgs a) {
-  __shared__ uint64_t s_a[kShortList], s_b[kShortList];
+struct TileSortArgs {
+  uint64_t* keys;       // [cap] tile lists, unsorted
+  uint64_t* keys_b;     // [cap] ping-pong buffer of lists too long for shared memory
+  const uint32_t* ranges;  // [tiles][2]: (start, end); (0, 0) when empty
+  uint32_t* vals;       // [cap] Gaussian ids in list order
+  uint64_t* full_keys;  // optional: (tile << 32 | depth bits) in list order
+  const uint32_t* work;          // non-empty tiles grouped by list length, longest first
+  const uint32_t* bucket_count;  // [17] tiles per length bucket
+  int id_bits;          // significant bits of the id (low word)
+};
+
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int j) {
+  const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, j);
+  const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), j);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// One exchange across lanes at distance J: the lane keeps the smaller key
+// when it is the lower of the pair in an ascending run (or the upper in a
+// descending one), else the larger.  Equal keys (padding) may go either way.
+template <int J>
+__device__ __forceinline__ void cx_lanes(uint64_t& x, bool up, int lane) {
+  const uint64_t o = shfl_xor64(x, J);
+  const bool keep_min = ((lane & J) == 0) == up;
+  x = (keep_min == (o < x)) ? o : x;
+}
+
+// One exchange of two keys held by the same thread (x at the lower index).
+__device__ __forceinline__ void cx_regs(uint64_t& x, uint64_t& y, bool up) {
+  const bool swap = (y < x) == up;
+  const uint64_t t = swap ? y : x;
+  y = swap ? x : y;
+  x = t;
+}
+
+// Stages J, J / 2, ..., 1 across lanes for one register (compile-time J).
+template <int J>
+__device__ __forceinline__ void lane_stages(uint64_t& x, bool up, int lane) {
+  cx_lanes<J>(x, up, lane);
+  if constexpr (J > 1) lane_stages<J / 2>(x, up, lane);
+}
+
+// Bitonic sorting network over 32 * E keys held by one warp in registers
+// (element r * 32 + lane in v[r]); ascending.  Exchanges across lanes take a
+// shuffle, the others stay in the thread.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&v)[E]) {
+  const int lane = threadIdx.x & 31;
+  // stage blocks k = 2 .. 32: within each register
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const uint32_t e = (uint32_t)(r * 32 + lane);
+    cx_lanes<1>(v[r], (e & 2) == 0, lane);
+    lane_stages<2>(v[r], (e & 4) == 0, lane);
+    lane_stages<4>(v[r], (e & 8) == 0, lane);
+    lane_stages<8>(v[r], (e & 16) == 0, lane);
+    lane_stages<16>(v[r], (e & 32) == 0, lane);
+  }
+  // stage blocks k = 64 .. 32 E: distances >= 32 in registers, then lanes
+#pragma unroll
+  for (int k = 64; k <= 32 * E; k <<= 1) {
+#pragma unroll
+    for (int jr = k / 64; jr >= 1; jr >>= 1) {
+#pragma unroll
+      for (int r = 0; r < E; ++r)
+        if (!(r & jr)) cx_regs(v[r], v[r | jr], ((r * 32) & k) == 0);
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) lane_stages<16>(v[r], ((r * 32) & k) == 0, lane);
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_list(const TileSortArgs& a, uint32_t t, uint32_t start, uint32_t cnt) {
+  const int lane = threadIdx.x & 31;
+  uint64_t v[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const uint32_t i = (uint32_t)(r * 32 + lane);
+    v[r] = i < cnt ? a.keys[start + i] : ~0ull;
+  }
+  warp_bitonic<E>(v);
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const uint32_t i = (uint32_t)(r * 32 + lane);
+    if (i < cnt) {
+      a.vals[start + i] = (uint32_t)v[r];
+      if (a.full_keys) a.full_keys[start + i] = ((uint64_t)t << 32) | (v[r] >> 32);
+    }
+  }
+}
+
+// Bitonic stages with partner distances 32, 16, ..., 1 of stage block k
+// (k >= 64) over one 64-key block held by a warp in registers: x0 is key
+// e0 = 64 b + lane, x1 key e0 + 32.  Distance 32 pairs a lane's own two keys,
+// smaller ones pair lanes (shuffles).  Both keys share the direction.
+__device__ __forceinline__ void block_run(uint64_t& x0, uint64_t& x1, uint32_t e0, uint32_t k) {
+  const int lane = threadIdx.x & 31;
+  const bool up = (e0 & k) == 0;
+  cx_regs(x0, x1, up);
+  lane_stages<16>(x0, up, lane);
+  lane_stages<16>(x1, up, lane);
+}
+
+// Bitonic sort of a tile's list of cnt keys (N = a power of two >= cnt, 256
+// .. kBitonicMax) by the CTA, ascending, writing the ids out.  Warp w owns
+// the 64-key blocks w, w + 8, ...: every stage with a partner distance of at
+// most 32 stays inside a block and runs in registers (stage blocks k <= 64
+// entirely, straight from the global list), the others go through shared
+// memory (contiguous, conflict-free pairs).
+__device__ void cta_bitonic(const TileSortArgs& a, uint32_t t, uint32_t start, uint32_t cnt, uint32_t N,
+                            uint64_t* s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t bb = (uint32_t)warp; bb < N / 64; bb += kThreads / 32) {
+    const uint32_t e0 = 64 * bb + (uint32_t)lane;
+    uint64_t x0 = e0 < cnt ? a.keys[start + e0] : ~0ull;
+    uint64_t x1 = e0 + 32 < cnt ? a.keys[start + e0 + 32] : ~0ull;
+    // stage blocks 2 .. 32 inside each 32-key half, then 64
+    cx_lanes<1>(x0, (e0 & 2) == 0, lane);
+    lane_stages<2>(x0, (e0 & 4) == 0, lane);
+    lane_stages<4>(x0, (e0 & 8) == 0, lane);
+    lane_stages<8>(x0, (e0 & 16) == 0, lane);
+    lane_stages<16>(x0, true, lane);
+    cx_lanes<1>(x1, (e0 & 2) == 0, lane);
+    lane_stages<2>(x1, (e0 & 4) == 0, lane);
+    lane_stages<4>(x1, (e0 & 8) == 0, lane);
+    lane_stages<8>(x1, (e0 & 16) == 0, lane);
+    lane_stages<16>(x1, false, lane);
+    block_run(x0, x1, e0, 64);
+    s[e0] = x0;
+    s[e0 + 32] = x1;
+  }
+  __syncthreads();
+  for (uint32_t k = 128; k <= N; k <<= 1) {
+    for (uint32_t j = k >> 1; j >= 64; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < N / 2; i += kThreads) {
+        const uint32_t x = 2 * i - (i & (j - 1)), y = x + j;
+        const bool up = (x & k) == 0;
+        const uint64_t p = s[x], q = s[y];
+        if ((p > q) == up) {
+          s[x] = q;
+          s[y] = p;
+        }
+      }
+      __syncthreads();
+    }
+    for (uint32_t bb = (uint32_t)warp; bb < N / 64; bb += kThreads / 32) {
+      const uint32_t e0 = 64 * bb + (uint32_t)lane;
+      uint64_t x0 = s[e0], x1 = s[e0 + 32];
+      block_run(x0, x1, e0, k);
+      if (k == N) {
+        if (e0 < cnt) {
+          a.vals[start + e0] = (uint32_t)x0;
+          if (a.full_keys) a.full_keys[start + e0] = ((uint64_t)t << 32) | (x0 >> 32);
+        }
+        if (e0 + 32 < cnt) {
+          a.vals[start + e0 + 32] = (uint32_t)x1;
+          if (a.full_keys) a.full_keys[start + e0 + 32] = ((uint64_t)t << 32) | (x1 >> 32);
+        }
+      } else {
+        s[e0] = x0;
+        s[e0 + 32] = x1;
+      }
+    }
+    if (k < N) __syncthreads();
+  }
+}
+
+constexpr uint32_t kBitonicMax = 4096;  // longest list sorted in shared memory
+
+// The tile sort.  Work unit u < L (L = tiles of >= 256 pairs) is the u-th
+// longest such tile, sorted by the whole CTA: a bitonic network in shared
+// memory up to kBitonicMax keys, stable LSD radix passes through global
+// memory beyond (a tile in which two keys share a depth is sorted again over
+// id and depth bits, which leaves equal depths in id order).  Later units
+// take eight shorter tiles, one per warp, each sorted in registers.  Keys
+// (depth bits, id) are distinct within a tile, so every network gives the
+// same list.  The CTA writes the ids (and optionally the full keys); the
+// ranges are already (start, end).
+__global__ void __launch_bounds__(kThreads, 4) k_tile_sort(const TileSortArgs a) {
+  __shared__ __align__(16) uint64_t s_keys[kBitonicMax];
   __shared__ uint32_t s_base[kRadixDigits];
   __shared__ uint32_t s_wh[kThreads / 32][kRadixDigits];
-  const uint32_t t = blockIdx.x;
-  const uint32_t start = a.ranges[2 * (uint64_t)t], cnt = a.ranges[2 * (uint64_t)t + 1];
-  if (cnt == 0) {
-    if (threadIdx.x == 0) a.ranges[2 * (uint64_t)t] = 0u;
+  uint32_t L = 0, S = 0;
+#pragma unroll
+  for (int b = 0; b < kOrderBuckets - 1; ++b) (b < kShortBucket ? L : S) += a.bucket_count[b];
+  const uint32_t u = blockIdx.x;
+  const int warp = threadIdx.x >> 5;
+  if (u >= L) {
+    const uint32_t k = (u - L) * (kThreads / 32) + (uint32_t)warp;
+    if (k >= S) return;
+    const uint32_t t = a.work[L + k];
+    const uint32_t start = a.ranges[2 * (uint64_t)t], cnt = a.ranges[2 * (uint64_t)t + 1] - start;
+    if (cnt <= 32) warp_sort_list<1>(a, t, start, cnt);
+    else if (cnt <= 64) warp_sort_list<2>(a, t, start, cnt);
+    else if (cnt <= 128) warp_sort_list<4>(a, t, start, cnt);
+    else warp_sort_list<8>(a, t, start, cnt);
     return;
   }
-  uint64_t *buf_a, *buf_b;
-  if (cnt <= kShortList) {
-    for (uint32_t i = threadIdx.x; i < cnt; i += kThreads) s_a[i] = a.keys[start + i];
-    buf_a = s_a;
-    buf_b = s_b;
-  } else {
-    buf_a = a.keys + start;
-    buf_b = a.keys_b + start;
+  const uint32_t t = a.work[u];
+  const uint32_t start = a.ranges[2 * (uint64_t)t], cnt = a.ranges[2 * (uint64_t)t + 1] - start;
+  if (cnt <= kBitonicMax) {
+    uint32_t N = 256;
+    while (N < cnt) N <<= 1;
+    cta_bitonic(a, t, start, cnt, N, s_keys);
+    return;
   }
-  __syncthreads();
-  uint64_t* sorted = cta_radix_sort(buf_a, buf_b, cnt, 32, 64, s_base, s_wh);
-  bool tie = false;
-  for (uint32_t i = threadIdx.x; i + 1 < cnt; i += kThreads)
-    tie |= (uint32_t)(sorted[i] >> 32) == (uint32_t)(sorted[i + 1] >> 32);
-  if (__syncthreads_or(tie)) {
-    uint64_t* other = sorted == buf_a ? buf_b : buf_a;
-    sorted = cta_radix_sort(sorted, other, cnt, 0, (a.id_bits + kRadixBits - 1) / kRadixBits * kRadixBits,
-                            s_base, s_wh);
-    other = sorted == buf_a ? buf_b : buf_a;
-    sorted = cta_radix_sort(sorted, other, cnt, 32, 64, s_base, s_wh);
+  const uint64_t* sorted;
+  {
+    uint64_t* buf_a = a.keys + start;
+    uint64_t* buf_b = a.keys_b + start;
+    uint64_t* out = cta_radix_sort(buf_a, buf_b, cnt, 32, 64, s_base, s_wh);
+    bool tie = false;
+    for (uint32_t i = threadIdx.x; i + 1 < cnt; i += kThreads)
+      tie |= (uint32_t)(out[i] >> 32) == (uint32_t)(out[i + 1] >> 32);
+    if (__syncthreads_or(tie)) {
+      uint64_t* other = out == buf_a ? buf_b : buf_a;
+      out = cta_radix_sort(out, other, cnt, 0, (a.id_bits + kRadixBits - 1) / kRadixBits * kRadixBits, s_base,
+                           s_wh);
+      other = out == buf_a ? buf_b : buf_a;
+      out = cta_radix_sort(out, other, cnt, 32, 64, s_base, s_wh);
+    }
+    __syncthreads();
+    sorted = out;
   }
-  __syncthreads();
   for (uint32_t i = threadIdx.x; i < cnt; i += kThreads) {
     const uint64_t k = sorted[i];
     a.vals[start + i] = (uint32_t)k;
     if (a.full_keys) a.full_keys[start + i] = ((uint64_t)t << 32) | (k >> 32);
-  }
-  if (threadIdx.x == 0) a.ranges[2 * (uint64_t)t + 1] = start + cnt;
-}
-
-// Exclusive scan of the tiles' pair counts into their list starts, one CTA of
-// 1024 threads (thread t takes a contiguous run of tiles); with `order`, also
-// the tiles in decreasing order of list length (power-of-two buckets, empty
-// tiles last; the order within a bucket follows the shared-memory atomics and
-// does not matter).  For up to kTileScanMax tiles; more go through the
-// multi-kernel scan.
-constexpr int kTileScanThreads = 1024;
-constexpr int64_t kTileScanMax = 1ll << 18;
-constexpr int kOrderBuckets = 17;
-
-__device__ __forceinline__ int order_bucket(uint32_t len) {
-  return len == 0 ? kOrderBuckets - 1 : 15 - min(15, 31 - __clz(len));
-}
-
-__global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(uint32_t* __restrict__ ranges, uint32_t tiles,
-                                                                 uint32_t* __restrict__ order) {
-  constexpr int NW = kTileScanThreads / 32;
-  __shared__ uint32_t s_warp[NW + 1];
-  __shared__ uint32_t s_count[kOrderBuckets], s_base[kOrderBuckets];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t per = (tiles + kTileScanThreads - 1) / kTileScanThreads;
-  const uint32_t lo = min(tiles, threadIdx.x * per), hi = min(tiles, lo + per);
-  if (threadIdx.x < kOrderBuckets) s_count[threadIdx.x] = 0;
-  uint32_t sum = 0;
-  for (uint32_t t = lo; t < hi; ++t) sum += ranges[2 * (uint64_t)t + 1];
-  // block-wide exclusive scan of the per-thread sums
-  uint32_t inc = sum;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-    if (lane >= d) inc += y;
-  }
-  if (lane == 31) s_warp[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t w = lane < NW ? s_warp[lane] : 0u;
-    uint32_t wi = w;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
-      if (lane >= d) wi += y;
-    }
-    if (lane < NW) s_warp[lane] = wi - w;
-  }
-  __syncthreads();
-  uint32_t run = s_warp[warp] + inc - sum;
-  for (uint32_t t = lo; t < hi; ++t) {
-    const uint32_t c = ranges[2 * (uint64_t)t + 1];
-    ranges[2 * (uint64_t)t] = run;
-    run += c;
-    if (order) atomicAdd(&s_count[order_bucket(c)], 1u);
-  }
-  if (!order) return;  // uniform
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t b0 = 0;
-    for (int b = 0; b < kOrderBuckets; ++b) {
-      s_base[b] = b0;
-      b0 += s_count[b];
-      s_count[b] = 0;
-    }
-  }
-  __syncthreads();
-  for (uint32_t t = lo; t < hi; ++t) {
-    const int b = order_bucket(ranges[2 * (uint64_t)t + 1]);
-    order[s_base[b] + atomicAdd(&s_count[b], 1u)] = t;
-  }
-}
-
-// Tiles in decreasing order of list length, bucketed by powers of two:
-// bucket 0 holds lists of >= 2^15 pairs, bucket 15 single pairs, bucket 16
-// the empty tiles.  Counting pass, then placement; the order within a bucket
-// follows the atomics and does not matter (tiles are independent).  The
-// multi-kernel form, for more tiles than the single-CTA scan takes.
-
-__global__ void __launch_bounds__(kThreads) k_order_count(const uint32_t* __restrict__ ranges, uint32_t tiles,
-                                                          uint32_t* __restrict__ bucket_count) {
-  __shared__ uint32_t s[kOrderBuckets];
-  if (threadIdx.x < kOrderBuckets) s[threadIdx.x] = 0;
-  __syncthreads();
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
-    const uint32_t len = ranges[2 * (uint64_t)t + 1] - ranges[2 * (uint64_t)t];
-    atomicAdd(&s[order_bucket(len)], 1u);
-  }
-  __syncthreads();
-  if (threadIdx.x < kOrderBuckets && s[threadIdx.x]) atomicAdd(&bucket_count[threadIdx.x], s[threadIdx.x]);
-}
-
-__global__ void __launch_bounds__(kThreads) k_order_place(const uint32_t* __restrict__ ranges, uint32_t tiles,
-                                                          const uint32_t* __restrict__ bucket_count,
-                                                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
-  __shared__ uint32_t s_base[kOrderBuckets];
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int b = 0; b < kOrderBuckets; ++b) {
-      s_base[b] = run;
-      run += bucket_count[b];
-    }
-  }
-  __syncthreads();
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
-    const int b = order_bucket(ranges[2 * (uint64_t)t + 1] - ranges[2 * (uint64_t)t]);
-    const uint32_t pos = s_base[b] + atomicAdd(&cursor[b], 1u);
-    if (pos < tiles) order[pos] = t;
   }
 }
 
@@ -804,10 +1104,11 @@ gs_status launch_radix_sort(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b
 // ---------------------------------------------------------------------------
 struct BinWs {
   uint32_t* scalars;  // [0] = item count, [1] = tile count, [2] = scanned tile total,
-                      // [3] = partition counter of the item scan,
-                      // [32, 49) tile-order bucket counts, [64, 81) their cursors
+                      // [3] = partition counter of the item scan, [4, 6) = the wide items'
+                      // (chunks << 32 | items) counter, [32, 49) tiles per length bucket,
+                      // [64, 81) their cursors
   unsigned long long* state;  // look-back words of the item scan, one per 2048 items
-  uint32_t* slot;
+  uint32_t* work;             // [cap] non-empty tiles grouped by list length (at most one per pair)
   uint64_t *keys_a, *keys_b;
   void* scan;
   size_t bytes;
@@ -826,7 +1127,7 @@ static BinWs bin_layout(char* base, int64_t m, int64_t cap) {
   const size_t c = (size_t)std::max<int64_t>(1, cap);
   w.scalars = (uint32_t*)take(128 * sizeof(uint32_t));
   w.state = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)std::max<int64_t>(1, scan_parts(m)));
-  w.slot = (uint32_t*)take(sizeof(uint32_t) * c);
+  w.work = (uint32_t*)take(sizeof(uint32_t) * c);
   w.keys_a = (uint64_t*)take(sizeof(uint64_t) * c);
   w.keys_b = (uint64_t*)take(sizeof(uint64_t) * c);
   w.scan = take(scan_workspace(kMaxScanTiles));
@@ -844,52 +1145,53 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   const int64_t cap = bins.capacity;
   BinWs w = bin_layout(static_cast<char*>(ws), m, cap);
   uint32_t* counts = bins.counts;
-  const bool one_cta_tile_scan = vt.total_tiles <= kTileScanMax;
-  // the tile order (when asked for) is written on every path, from the final ranges
-  auto finish = [&]() {
-    if (bins.tile_order && vt.total_tiles > 0 && !one_cta_tile_scan) {
-      const unsigned og = (unsigned)std::min<int64_t>(592, (vt.total_tiles + kThreads - 1) / kThreads);
-      k_order_count<<<og, kThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, w.scalars + 32);
-      k_order_place<<<og, kThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, w.scalars + 32,
-                                            w.scalars + 64, bins.tile_order);
-    }
-    return check_launch("bin_sort");
-  };
-  k_init_counts<<<1, 128, 0, s>>>(counts, w.scalars, (uint32_t)m, (uint32_t)vt.total_tiles);
-  // the ranges array holds each tile's (start, count) until the tile is sorted
+  const uint32_t tiles = (uint32_t)vt.total_tiles;
+  k_init_counts<<<1, 128, 0, s>>>(counts, w.scalars, (uint32_t)m, tiles);
+  // the ranges array counts each tile's pairs, then holds (start, cursor)
   if (cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)bins.num_tiles, s) != cudaSuccess)
     return check_launch("memset ranges");
-  if (m == 0) {
-    if (one_cta_tile_scan && bins.tile_order && vt.total_tiles > 0)
-      k_tile_scan<<<1, kTileScanThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, bins.tile_order);
-    return finish();
-  }
-  // 1. + 2. pair slots per (view, Gaussian) (single-pass scan of the tile
-  // counts) and a place in its tile for every pair, in one launch
-  const int64_t parts = scan_parts(m);
-  if (cudaMemsetAsync(w.state, 0, sizeof(unsigned long long) * (size_t)parts, s) != cudaSuccess)
-    return check_launch("memset scan state");
+  // the wide items' chunk table borrows keys_b (the sort's ping-pong buffer,
+  // not used before the key passes end): cap entries, more than the
+  // cap / 64 chunks that pairs within the capacity can need
+  const uint32_t wide_cap = (uint32_t)std::min<int64_t>((int64_t)UINT32_MAX, std::max<int64_t>(1, cap));
   PairArgs pa{sp.touched, reinterpret_cast<const uint2*>(sp.rect), sp.depth, bins.pair_off, counts, sp.n, cap,
-              bins.ranges, w.slot, w.keys_a};
-  ScanPlaceArgs sa{pa, w.state, w.scalars + 3, (uint32_t)parts};
-  k_scan_place<<<(unsigned)parts, kThreads, 0, s>>>(sa, vt);
-  if (cap == 0 || vt.total_tiles == 0) return finish();
-  // 3. list starts (and the longest-first order); keys at their places
-  if (one_cta_tile_scan) {
-    k_tile_scan<<<1, kTileScanThreads, 0, s>>>(bins.ranges, (uint32_t)vt.total_tiles, bins.tile_order);
+              bins.ranges, w.keys_a, reinterpret_cast<unsigned long long*>(w.scalars + 4),
+              reinterpret_cast<uint2*>(w.keys_b), wide_cap};
+  // 1. + 2. pair slots per (view, Gaussian) (single-pass scan of the tile
+  // counts) and every pair counted in its tile, in one launch
+  if (m > 0) {
+    const int64_t parts = scan_parts(m);
+    if (cudaMemsetAsync(w.state, 0, sizeof(unsigned long long) * (size_t)parts, s) != cudaSuccess)
+      return check_launch("memset scan state");
+    ScanCountArgs sa{pa, w.state, w.scalars + 3, (uint32_t)parts};
+    k_scan_count<<<(unsigned)parts, kThreads, 0, s>>>(sa, vt);
+  }
+  if (tiles == 0) return check_launch("bin_sort");
+  // 3. list starts, the key pass's cursors and the tiles grouped by length
+  if (vt.total_tiles <= kTileScanMax) {
+    k_tile_scan<<<1, kTileScanThreads, 0, s>>>(bins.ranges, tiles, w.scalars + 32, w.work, bins.tile_order);
   } else {
     gs_status st = launch_scan(bins.ranges + 1, 2, bins.ranges, 2, w.scalars + 1, vt.total_tiles, w.scalars + 2,
                                w.scan, s);
     if (st != GS_OK) return st;
+    const unsigned og = (unsigned)std::min<int64_t>(592, ((int64_t)tiles + kThreads - 1) / kThreads);
+    k_order_count<<<og, kThreads, 0, s>>>(bins.ranges, tiles, w.scalars + 32);
+    k_order_place<<<og, kThreads, 0, s>>>(bins.ranges, tiles, w.scalars + 32, w.scalars + 64, w.work,
+                                          bins.tile_order);
   }
+  if (m == 0 || cap == 0) return check_launch("bin_sort");
+  // 4. every key at its place in its tile's list
   const unsigned pgrid = (unsigned)std::max<int64_t>(1, (m + 255) / 256);  // 8 warps of 32 items per block
-  k_pairs<false><<<pgrid, 256, 0, s>>>(pa, vt);
-  // 4. every tile's list by (depth bits, id)
+  k_keys<<<pgrid, 256, 0, s>>>(pa, vt);
+  k_keys_wide<<<(unsigned)std::min<int64_t>(1184, pgrid), 256, 0, s>>>(pa, vt);
+  // 5. every tile's list by (depth bits, id)
   int id_bits = 1;
   while (id_bits < 32 && (1ll << id_bits) < sp.n) ++id_bits;
-  TileSortArgs ta{w.keys_a, w.keys_b, bins.ranges, bins.vals, reinterpret_cast<uint64_t*>(bins.keys), id_bits};
-  k_tile_sort<<<(unsigned)vt.total_tiles, kThreads, 0, s>>>(ta);
-  return finish();
+  TileSortArgs ta{w.keys_a, w.keys_b, bins.ranges, bins.vals, reinterpret_cast<uint64_t*>(bins.keys), w.work,
+                  w.scalars + 32, id_bits};
+  const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(vt.total_tiles, cap));
+  k_tile_sort<<<sgrid, kThreads, 0, s>>>(ta);
+  return check_launch("bin_sort");
 }
 
 }  // namespace gs
