@@ -108,12 +108,14 @@ def test_both_arms_report_the_same_config():
 
 
 def test_library_kernels_per_training_step():
-    # projection 1, binning 11, fused composite + loss + per-pixel backward 1,
-    # per-Gaussian backward 5, Adam 3; a longest-first schedule adds 2;
-    # unfused: composite 1, loss 2, per-pixel backward 1 instead of the fused 1
-    assert bench.launches_per_step(1, 3600) == 21
-    assert bench.launches_per_step(1, 3600, tile_order=True) == 23
-    assert bench.launches_per_step(1, 3600, fused=False) == 24
+    # projection 1, binning 6, fused composite + loss + per-pixel backward 1,
+    # per-Gaussian backward 5, Adam 3; a longest-first order costs no launch;
+    # unfused: composite 1, loss 2, per-pixel backward 1 instead of the fused 1;
+    # beyond 2^18 tiles the tile scan takes 5 launches instead of 1
+    assert bench.launches_per_step(1, 3600) == 16
+    assert bench.launches_per_step(1, 3600, tile_order=True) == 16
+    assert bench.launches_per_step(1, 3600, fused=False) == 19
+    assert bench.launches_per_step(64, 1 << 19) == 20
 
 
 def test_roofline_of_the_fused_step():
