@@ -248,7 +248,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-STAGES = ("project", "bin_sort", "render_fused", "render_bwd_gaussians", "adam")
+STAGES = ("project", "bin_sort", "render_fused", "bwd_gaussians_adam", "pose_adam")
 STAGES_UNFUSED = ("project", "bin_sort", "render_fwd", "loss", "render_bwd_pixels", "render_bwd_gaussians", "adam")
 
 
@@ -269,6 +269,8 @@ class Workload:
         self.arena = raster.Arena.from_scene(self.scene, device)
         self.grads, self.m, self.v = self.arena.like(), self.arena.like(), self.arena.like()
         self.groups = self.arena.adam_groups(lr_means=1.6e-4 * 10.0)
+        # the fused path also takes the parameters' Adam step inside the
+        # per-Gaussian backward (same rates as the groups)
         P = len(self.cams)
         self.poses = raster.poses_tensor(self.cams, device)
         self.pose_m = torch.zeros((P, 6), dtype=torch.float32, device=device)
@@ -276,6 +278,7 @@ class Workload:
         self.pose_steps = torch.zeros(P, dtype=torch.int32, device=device)
         self.step_dev = torch.zeros(1, dtype=torch.int32, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.adam = raster.adam_params(3, lr_means=1.6e-4 * 10.0, step_dev=self.step_dev, status=self.status)
         views = self.cams if batched else self.cams[:1]
         self.rast = raster.Rasterizer(n, 3, views, device=device)
         self.loss = raster.ImageLoss(device)
@@ -333,7 +336,7 @@ class Workload:
                 self.arena, self.grads, self.m, self.v, self.groups, self.rast, self.poses[sl], self.targets[k],
                 self.step_dev, pose_m=self.pose_m[sl], pose_v=self.pose_v[sl], pose_steps=self.pose_steps[sl],
                 pose_lr=1e-4, loss_kind=0, status=self.status, image=img[:3 * px], dimage=dimg[:3 * px],
-                loss=self.loss, cams=g, fused=fused))
+                loss=self.loss, cams=g, fused=fused, adam=self.adam if fused else None))
         if use_graphs:
             self.pool = torch.cuda.graph_pool_handle()
             for st in self.steps:
@@ -385,9 +388,14 @@ class Workload:
             next(e).record()
             r.backward_pixels(st.dimg, None, st.img)
             next(e).record()
-        r.backward_gaussians(st.arena, st.poses, st.grads, st.dpose)
+        if st.adam is not None:
+            r.backward_gaussians_adam(st.arena, st.poses, st.grads, st.m, st.v, st.adam, st.dpose)
+            groups = []
+        else:
+            r.backward_gaussians(st.arena, st.poses, st.grads, st.dpose)
+            groups = st.groups
         next(e).record()
-        self.raster.adam_step(st.arena, st.grads, st.m, st.v, 0, st.groups, status=st.status, pose=st.poses,
+        self.raster.adam_step(st.arena, st.grads, st.m, st.v, 0, groups, status=st.status, pose=st.poses,
                               dpose=st.dpose, pose_m=st.pose_m, pose_v=st.pose_v, pose_lr=st.pose_lr,
                               step_dev=st.step_dev, pose_steps_dev=st.pose_steps)
         next(e).record()
@@ -874,7 +882,7 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
                         "3-level LoD (8-child moment merge, tau = 1 px) for renders, 80 GB HBM budget"}
 
 
-def launches_per_step(views, num_tiles, tile_order=False, fused=True):
+def launches_per_step(views, num_tiles, tile_order=False, fused=True, fused_adam=None):
     """Kernels one training step launches (memsets excluded): projection 1;
     binning 6 (counts, pair-offset scan with the count pass, tile scan with
     the length grouping and any longest-first order, keys, keys of the wide
@@ -883,11 +891,14 @@ def launches_per_step(views, num_tiles, tile_order=False, fused=True):
     composite + loss + per-pixel backward 1 (or, unfused, composite 1, loss
     2, per-pixel backward 1); per-Gaussian backward 5 (pair sums,
     projection, SH, pose chunks and total); Adam 3 (parameters, poses, step
-    counter)."""
+    counter), 2 when the parameters' step runs inside the SH kernel
+    (fused_adam, by default with the fused pass)."""
+    if fused_adam is None:
+        fused_adam = fused
     tile_scan = 1 if num_tiles <= (1 << 18) else 3 + 2
     bin_sort = 1 + 1 + tile_scan + 1 + 1 + 1
     blend = 1 if fused else 1 + 2 + 1
-    return 1 + bin_sort + blend + 5 + 3
+    return 1 + bin_sort + blend + 5 + (2 if fused_adam else 3)
 
 
 def load_peaks():
@@ -981,11 +992,18 @@ def roofline(wl, stage_ms, work, peaks, sms, workload_key=None):
     E = work["evaluated"]
     clk = peaks["sm_max_mhz"]
     bs_bytes, passes = bin_sort_bytes(K, n * V, wl.rast.num_tiles)
+    F = wl.arena.padded / n  # floats per Gaussian (60 at SH degree 3)
     hbm = {
         "project": (240.0 + 48.0) * n * V,
         "bin_sort": bs_bytes,
         "render_bwd_gaussians": 36.0 * K + 480.0 * n,
         "adam": 28.0 * wl.arena.padded,
+        # fused: 36 B per pair summed; per Gaussian its parameters read once
+        # (4 B per float), the means / scale / rotation gradients written and
+        # read back (12 floats), and the moments read and parameters and
+        # moments written (20 B per float): the gradient round trip of the
+        # separate Adam is gone
+        "bwd_gaussians_adam": 36.0 * K + (24.0 * F + 96.0) * n,
         "loss": 36.0 * wl.pixels_per_iter,
     }
     table = {}

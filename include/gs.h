@@ -542,6 +542,44 @@ GS_API gs_status gs_render_bwd_gaussians(const gs_params* params, const float* p
                                          const gs_bins* bins, const gs_raster_cfg* cfg, gs_grads* grads,
                                          float* dL_dpose, void* ws, size_t ws_bytes, gs_stream stream);
 
+/* Adam settings of gs_render_bwd_gaussians_adam: one learning rate per lane
+ * of the float4 parameters and per SH plane (ch * nc + k), the betas and
+ * epsilon of gs_adam_cfg; the step: *step_dev + 1 when step_dev is not NULL
+ * (read, not incremented: a following gs_adam_step with the same step_dev
+ * increments it), else `step` (>= 1); skip_dev (optional): nonzero = no
+ * update; status (optional): bit 0 set when a gradient or a second moment is
+ * not finite.  update_mask: bit 0 means4, bit 1 scale_opa, bit 2 quat, bit 3
+ * the SH planes; parameters left out keep their values and moments. */
+typedef struct {
+  float lr_means4[4], lr_scale_opa[4], lr_quat[4];
+  float lr_sh[48];
+  float beta1, beta2, eps;
+  int32_t step;
+  uint32_t update_mask;
+  const int32_t* step_dev;
+  const uint32_t* skip_dev;
+  uint32_t* status;
+} gs_adam_params_cfg;
+
+/* gs_render_bwd_gaussians with the Adam update of the parameters fused in
+ * (the second half of a training step, Sec. 5.2): the kernel that turns each
+ * Gaussian's colour gradients into SH gradients finishes its gradient and
+ * applies to every parameter of that Gaussian the element update of
+ * gs_adam_step (same arithmetic, same bits), so the SH gradients never reach
+ * memory and the update takes no pass of its own.  params: read and
+ * written (gs_grads layout of the parameters); m, v: Adam moments, same
+ * shape (sh_stride may differ from params'); grads: receives the gradients
+ * of means4, scale_opa and quat (its sh planes are not written); dL_dpose as
+ * in gs_render_bwd_gaussians (the pose step stays with gs_adam_step, which
+ * takes num_groups = 0 for the poses alone).  Equal to
+ * gs_render_bwd_gaussians followed by gs_adam_step with one group per
+ * parameter kind covering rows [0, n) and the same rates. */
+GS_API gs_status gs_render_bwd_gaussians_adam(gs_grads* params, const float* poses_dev, const gs_camera* cams,
+                                              int32_t views, const gs_splats* splats, const gs_bins* bins,
+                                              const gs_raster_cfg* cfg, gs_grads* grads, gs_grads* adam_m,
+                                              gs_grads* adam_v, const gs_adam_params_cfg* adam,
+                                              float* dL_dpose, void* ws, size_t ws_bytes, gs_stream stream);
+
 /* Workspace bytes of gs_render_fused: the gs_render_bwd workspace (same
  * layout at its start, so the same buffer then serves
  * gs_render_bwd_gaussians) plus a work counter and one float per tile. */

@@ -28,6 +28,7 @@ EXPORTED = (
     "gs_last_error", "gs_version", "gs_built_arch", "gs_splats_bytes", "gs_splats_carve",
     "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
     "gs_render_bwd_workspace", "gs_render_bwd", "gs_render_bwd_pixels", "gs_render_bwd_gaussians",
+    "gs_render_bwd_gaussians_adam",
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
     "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
     "gs_render_fused_workspace", "gs_render_fused", "gs_autotune_fused",
@@ -93,6 +94,13 @@ class GsAdamCfg(C.Structure):
                 ("dpose", C.c_void_p), ("pose_m", C.c_void_p), ("pose_v", C.c_void_p),
                 ("views", C.c_int32), ("pose_lr", C.c_float), ("pose_step", C.c_int32),
                 ("step_dev", C.c_void_p), ("pose_steps_dev", C.c_void_p), ("skip_dev", C.c_void_p)]
+
+
+class GsAdamParamsCfg(C.Structure):
+    _fields_ = [("lr_means4", C.c_float * 4), ("lr_scale_opa", C.c_float * 4), ("lr_quat", C.c_float * 4),
+                ("lr_sh", C.c_float * 48), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int32), ("update_mask", C.c_uint32), ("step_dev", C.c_void_p),
+                ("skip_dev", C.c_void_p), ("status", C.c_void_p)]
 
 
 class GsBaProblem(C.Structure):
@@ -172,6 +180,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                 P(GsRasterCfg), vp, vp, vp, P(GsGrads), vp, vp, sz, vp]
     L.gs_render_bwd_pixels.argtypes = [P(GsSplats), P(GsBins), P(GsCamera), i32, P(GsRasterCfg), vp, vp, vp,
                                        i64, vp, sz, vp]
+    L.gs_render_bwd_gaussians_adam.argtypes = [P(GsGrads), vp, P(GsCamera), i32, P(GsSplats), P(GsBins),
+                                               P(GsRasterCfg), P(GsGrads), P(GsGrads), P(GsGrads),
+                                               P(GsAdamParamsCfg), vp, vp, sz, vp]
     L.gs_render_bwd_gaussians.argtypes = [P(GsParams), vp, P(GsCamera), i32, P(GsSplats), P(GsBins),
                                           P(GsRasterCfg), P(GsGrads), vp, vp, sz, vp]
     L.gs_adam_step.argtypes = [vp, vp, vp, vp, i64, P(GsAdamCfg), i32, vp]
@@ -236,7 +247,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         getattr(L, name).restype = C.c_int
     for name in ("gs_splats_carve", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd",
                  "gs_render_bwd",
-                 "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_adam_step", "gs_image_loss",
+                 "gs_render_bwd_pixels", "gs_render_bwd_gaussians", "gs_render_bwd_gaussians_adam", "gs_adam_step",
+                 "gs_image_loss",
                  "gs_render_stats", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
                  "gs_ba_solve", "gs_render_fused", "gs_autotune_fused", "gs_hier_analyze", "gs_hier_refine",
                  "gs_project_hier"):

@@ -28,26 +28,9 @@ struct AdamArgs {
   const uint32_t* skip_dev;  // optional: nonzero = skip the update
 };
 
-// 1 - beta^step: beta^step by exponentiation by squaring in double (only
-// multiplications, so host and device give the same bits), rounded once.
-__host__ __device__ __forceinline__ float bias_corr(float beta, int step) {
-  double r = 1.0, b = (double)beta;
-  for (unsigned e = (unsigned)step; e; e >>= 1) {
-    if (e & 1u) r *= b;
-    b *= b;
-  }
-  return (float)(1.0 - r);
-}
-
-// p -= lr * (m / bc1) / (sqrt(v / bc2) + eps), written as
-// p -= (lr / bc1) * m / (sqrt(v) * rsqrt_bc2 + eps) with the step constants
-// hoisted out of the element loop.
 __device__ __forceinline__ bool adam_elem(float& p, float g, float& m, float& v, float step_size,
                                           const AdamArgs& a, float rs_bc2) {
-  m = a.b1 * m + (1.f - a.b1) * g;
-  v = a.b2 * v + (1.f - a.b2) * g * g;
-  p -= step_size * __fdividef(m, sqrtf(v) * rs_bc2 + a.eps);
-  return isfinite(g) && isfinite(v);
+  return ::gs::adam_elem(p, g, m, v, step_size, a.b1, a.b2, a.eps, rs_bc2);
 }
 
 // Block b updates one chunk of one group: the group is found once per block

@@ -484,6 +484,52 @@ gs_status gs_render_bwd_gaussians(const gs_params* params, const float* poses_de
                             dL_dpose, drgb, (cudaStream_t)stream);
 }
 
+static gs_status check_like(const gs_grads* x, const gs_grads* params, const char* what) {
+  if (!x || x->n != params->n || x->sh_degree != params->sh_degree || (x->sh_stride != 0 && x->sh_stride < x->n))
+    return fail(GS_ERR_INVALID, "%s must match params", what);
+  if (params->n > 0 && (!x->means4 || !x->scale_opa || !x->quat || !x->sh))
+    return fail(GS_ERR_INVALID, "NULL %s array", what);
+  if (!aligned(x->means4, 16) || !aligned(x->scale_opa, 16) || !aligned(x->quat, 16))
+    return fail(GS_ERR_INVALID, "%s arrays must be 16-byte aligned", what);
+  return GS_OK;
+}
+
+gs_status gs_render_bwd_gaussians_adam(gs_grads* params, const float* poses_dev, const gs_camera* cams,
+                                       int32_t views, const gs_splats* splats, const gs_bins* bins,
+                                       const gs_raster_cfg* cfg, gs_grads* grads, gs_grads* adam_m,
+                                       gs_grads* adam_v, const gs_adam_params_cfg* adam, float* dL_dpose, void* ws,
+                                       size_t ws_bytes, gs_stream stream) {
+  GS_NVTX("gs_render_bwd_gaussians_adam");
+  if (!params || !adam) return fail(GS_ERR_INVALID, "NULL params or Adam settings");
+  const gs_params pv{params->means4, params->scale_opa, params->quat, params->sh, params->n, params->sh_degree,
+                     params->sh_stride};
+  gs_status st;
+  if ((st = check_params(&pv)) != GS_OK) return st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
+  if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
+  if ((st = check_splats(splats, params->n, views)) != GS_OK) return st;
+  if ((st = check_bins(bins, vt, params->n)) != GS_OK) return st;
+  if ((st = check_like(grads, params, "grads")) != GS_OK || (st = check_like(adam_m, params, "adam_m")) != GS_OK ||
+      (st = check_like(adam_v, params, "adam_v")) != GS_OK)
+    return st;
+  if ((adam_m->sh_stride > 0 ? adam_m->sh_stride : adam_m->n) != (adam_v->sh_stride > 0 ? adam_v->sh_stride : adam_v->n))
+    return fail(GS_ERR_INVALID, "adam_m and adam_v need the same sh_stride");
+  if (adam->step < 1 && !adam->step_dev) return fail(GS_ERR_INVALID, "step must be >= 1");
+  if (!(adam->beta1 >= 0.f && adam->beta1 < 1.f && adam->beta2 >= 0.f && adam->beta2 < 1.f && adam->eps >= 0.f))
+    return fail(GS_ERR_INVALID, "bad Adam hyper-parameters");
+  if (adam->update_mask & ~15u) return fail(GS_ERR_INVALID, "update_mask has bits beyond 0-3");
+  const size_t need = gs_render_bwd_workspace(params->n, views, bins->capacity);
+  if (!ws || ws_bytes < need)
+    return fail(GS_ERR_OOM, "render_bwd workspace: need %zu bytes, got %zu", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(GS_ERR_INVALID, "workspace must be 256-byte aligned");
+  float *partials, *pose_partials, *drgb;
+  bwd_layout(params->n, views, bins->capacity, static_cast<char*>(ws), &partials, &pose_partials, &drgb);
+  return launch_project_bwd_adam(pv, poses_dev, vt, *cfg, *splats, *bins, partials, *grads, pose_partials,
+                                 dL_dpose, drgb, *params, *adam_m, *adam_v, *adam, (cudaStream_t)stream);
+}
+
 static size_t fused_layout(int64_t n, int32_t views, int64_t capacity, int64_t num_tiles, char* base,
                            uint32_t** queue, float** tile_loss) {
   size_t off = bwd_layout(n, views, capacity, nullptr, nullptr, nullptr, nullptr);
@@ -568,8 +614,9 @@ gs_status gs_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
   if (n > 0 && (!p || !g || !m || !v)) return fail(GS_ERR_INVALID, "NULL arena");
   if (!aligned(p, 16) || !aligned(g, 16) || !aligned(m, 16) || !aligned(v, 16))
     return fail(GS_ERR_INVALID, "arenas must be 16-byte aligned");
-  if (cfg->num_groups < 1 || cfg->num_groups > GS_MAX_ADAM_GROUPS || !cfg->groups)
-    return fail(GS_ERR_INVALID, "num_groups must be 1..%d", GS_MAX_ADAM_GROUPS);
+  if (cfg->num_groups < 0 || cfg->num_groups > GS_MAX_ADAM_GROUPS || (cfg->num_groups > 0 && !cfg->groups))
+    return fail(GS_ERR_INVALID, "num_groups must be 0..%d", GS_MAX_ADAM_GROUPS);
+  if (cfg->num_groups == 0 && !cfg->pose) return fail(GS_ERR_INVALID, "no group and no pose step");
   for (int k = 0; k < cfg->num_groups; ++k) {
     const gs_adam_group& G = cfg->groups[k];
     if (G.begin < 0 || G.end < G.begin || G.end > n) return fail(GS_ERR_INVALID, "group %d out of range", k);

@@ -192,6 +192,35 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
 }
 
 // ---------------------------------------------------------------------------
+// The Adam update of one element (shared by the standalone step and the
+// per-Gaussian backward with the update fused in, so both give the same bits)
+// ---------------------------------------------------------------------------
+// 1 - beta^step: beta^step by exponentiation by squaring in double (only
+// multiplications, so host and device give the same bits), rounded once.
+__host__ __device__ __forceinline__ float bias_corr(float beta, int step) {
+  double r = 1.0, b = (double)beta;
+  for (unsigned e = (unsigned)step; e; e >>= 1) {
+    if (e & 1u) r *= b;
+    b *= b;
+  }
+  return (float)(1.0 - r);
+}
+
+// p -= lr * (m / bc1) / (sqrt(v / bc2) + eps), written as
+// p -= (lr / bc1) * m / (sqrt(v) * rsqrt_bc2 + eps) with the step constants
+// hoisted out of the element loop (step_size = lr / bc1).  Every operation is
+// an explicit rounding (no contraction left to the compiler), so the result
+// does not depend on the kernel it is inlined in.  False when the gradient
+// or the second moment is not finite.
+__device__ __forceinline__ bool adam_elem(float& p, float g, float& m, float& v, float step_size, float b1,
+                                          float b2, float eps, float rs_bc2) {
+  m = __fmaf_rn(b1, m, __fmul_rn(1.f - b1, g));
+  v = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(1.f - b2, g), g));
+  p = __fsub_rn(p, __fmul_rn(step_size, __fdividef(m, __fmaf_rn(sqrtf(v), rs_bc2, eps))));
+  return isfinite(g) && isfinite(v);
+}
+
+// ---------------------------------------------------------------------------
 // Helpers of the level-of-detail hierarchies: order-preserving float <-> u32
 // (for atomic min / max), 10-bit Morton quantisation in single precision, a
 // symmetric 3x3 eigen-decomposition and a rotation-to-quaternion conversion.

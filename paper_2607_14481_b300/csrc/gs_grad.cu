@@ -407,6 +407,164 @@ __global__ void __launch_bounds__(kGradBlock) k_sh_bwd(const GradArgs a, const V
   }
 }
 
+// Per-parameter Adam settings of the fused form: one learning rate per lane
+// of the float4 parameters and per SH plane (ch * nc + k); a parameter whose
+// rate entry is marked off keeps its value and moments.
+struct AdamFamilies {
+  float lr4[3][4];      // means4, scale_opa, quat
+  float lr_sh[48];
+  uint32_t on4;         // bit f: float4 family f updated
+  uint32_t on_sh;       // 1: the SH planes updated
+  float b1, b2, eps, bc1, bc2;
+  const int32_t* step_dev;
+  const uint32_t* skip_dev;
+  uint32_t* status;
+  float4* p_means4;     // parameters (read and written); the chain-rule reads go through GradArgs
+  float4* p_scale_opa;
+  float4* p_quat;
+  float* p_sh;
+  int64_t p_sh_stride;
+  float4 *m_means4, *m_scale_opa, *m_quat, *v_means4, *v_scale_opa, *v_quat;
+  float *m_sh, *v_sh;
+  int64_t mv_sh_stride;
+};
+
+__device__ __forceinline__ bool adam4(float4& p, const float4 g, float4& m, float4& v, const float (&lr)[4],
+                                      float ss, const AdamFamilies& f, float rs_bc2) {
+  bool ok = adam_elem(p.x, g.x, m.x, v.x, lr[0] * ss, f.b1, f.b2, f.eps, rs_bc2);
+  ok &= adam_elem(p.y, g.y, m.y, v.y, lr[1] * ss, f.b1, f.b2, f.eps, rs_bc2);
+  ok &= adam_elem(p.z, g.z, m.z, v.z, lr[2] * ss, f.b1, f.b2, f.eps, rs_bc2);
+  ok &= adam_elem(p.w, g.w, m.w, v.w, lr[3] * ss, f.b1, f.b2, f.eps, rs_bc2);
+  return ok;
+}
+
+// k_sh_bwd with the Adam update of the Gaussian fused in: once its SH
+// gradients (in registers) and its means gradient (k_project_bwd's plus the
+// view-direction term) are complete, every parameter of Gaussian i takes the
+// Adam step of gs_adam_step (same element update, same constants), so the SH
+// gradients never reach memory and the update needs no pass of its own.
+template <int DEG>
+__global__ void __launch_bounds__(kGradBlock) k_sh_bwd_adam(const GradArgs a, const ViewTable vt,
+                                                            const AdamFamilies f) {
+  constexpr int NC = (DEG + 1) * (DEG + 1);
+  const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
+  const bool valid = i < a.n;
+  const int64_t warp_id = i >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (kGradBlock / 32);
+  const float4 mu = valid ? a.means4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float gsh[3][NC];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
+  float gmu[3] = {0.f, 0.f, 0.f};
+  const uint32_t kpairs = a.counts[3];
+  for (int v = 0; v < vt.views; ++v) {
+    float pv[3] = {0.f, 0.f, 0.f};
+    const int64_t o = (int64_t)v * a.n + i;
+    uint32_t tch = 0;
+    if (valid && pair_range_ok(a, o, kpairs, tch)) {
+      const float4 g = a.drgb[o];
+      const uint32_t auxb = a.aux[o];
+      const float* P = a.poses + 12 * v;
+      const float oc0 = -(P[0] * P[3] + P[4] * P[7] + P[8] * P[11]);
+      const float oc1 = -(P[1] * P[3] + P[5] * P[7] + P[9] * P[11]);
+      const float oc2 = -(P[2] * P[3] + P[6] * P[7] + P[10] * P[11]);
+      const float wx = mu.x - oc0, wy = mu.y - oc1, wz = mu.z - oc2;
+      const float inv = 1.0f / sqrtf(wx * wx + wy * wy + wz * wz);
+      const float dx = wx * inv, dy = wy * inv, dz = wz * inv;
+      float Y[NC];
+      sh_basis<DEG>(dx, dy, dz, Y);
+      const float gc[3] = {(auxb & 1u) ? 0.f : g.x, (auxb & 2u) ? 0.f : g.y, (auxb & 4u) ? 0.f : g.z};
+      float dY[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) dY[k] = 0.f;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          gsh[ch][k] += gc[ch] * Y[k];
+          if (k > 0) dY[k] += gc[ch] * a.sh[(int64_t)(ch * NC + k) * a.sh_stride + i];
+        }
+      }
+      if (DEG > 0) {
+        float ddx, ddy, ddz;
+        sh_basis_grad<DEG>(dx, dy, dz, dY, ddx, ddy, ddz);
+        const float pr = dx * ddx + dy * ddy + dz * ddz;
+        const float dwx = (ddx - dx * pr) * inv, dwy = (ddy - dy * pr) * inv, dwz = (ddz - dz * pr) * inv;
+        gmu[0] += dwx; gmu[1] += dwy; gmu[2] += dwz;
+        pv[0] = P[0] * dwx + P[1] * dwy + P[2] * dwz;
+        pv[1] = P[4] * dwx + P[5] * dwy + P[6] * dwz;
+        pv[2] = P[8] * dwx + P[9] * dwy + P[10] * dwz;
+      }
+    }
+    warp_store_sum<3>(pv, a.pose_b + ((int64_t)v * warps + warp_id) * 3);
+  }
+  if (!valid || (f.skip_dev && *f.skip_dev)) return;
+  float bc1 = f.bc1, bc2 = f.bc2;
+  if (f.step_dev) {
+    const int st = *f.step_dev + 1;
+    bc1 = bias_corr(f.b1, st);
+    bc2 = bias_corr(f.b2, st);
+  }
+  const float rs_bc2 = rsqrtf(bc2), ss = 1.f / bc1;
+  bool ok = true;
+  // every load of a group of parameters is issued before its updates, so the
+  // memory round trips overlap (this kernel runs at a low occupancy)
+  {
+    float4 gm = a.g_means4[i];
+    if (DEG > 0) {
+      gm.x += gmu[0]; gm.y += gmu[1]; gm.z += gmu[2];
+    }
+    const float4 gso = a.g_scale_opa[i], gq = a.g_quat[i];
+    float4 p0 = f.p_means4[i], m0 = f.m_means4[i], v0 = f.v_means4[i];
+    float4 p1 = f.p_scale_opa[i], m1 = f.m_scale_opa[i], v1 = f.v_scale_opa[i];
+    float4 p2 = f.p_quat[i], m2 = f.m_quat[i], v2 = f.v_quat[i];
+    if (f.on4 & 1u) {
+      ok &= adam4(p0, gm, m0, v0, f.lr4[0], ss, f, rs_bc2);
+      f.p_means4[i] = p0; f.m_means4[i] = m0; f.v_means4[i] = v0;
+    }
+    if (f.on4 & 2u) {
+      ok &= adam4(p1, gso, m1, v1, f.lr4[1], ss, f, rs_bc2);
+      f.p_scale_opa[i] = p1; f.m_scale_opa[i] = m1; f.v_scale_opa[i] = v1;
+    }
+    if (f.on4 & 4u) {
+      ok &= adam4(p2, gq, m2, v2, f.lr4[2], ss, f, rs_bc2);
+      f.p_quat[i] = p2; f.m_quat[i] = m2; f.v_quat[i] = v2;
+    }
+  }
+  if (f.on_sh) {
+    constexpr int NP = 3 * NC, B = 8;
+#pragma unroll
+    for (int p0 = 0; p0 < NP; p0 += B) {
+      float P[B], M[B], V[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (p0 + b >= NP) break;
+        const int64_t ip = (int64_t)(p0 + b) * f.p_sh_stride + i, im = (int64_t)(p0 + b) * f.mv_sh_stride + i;
+        P[b] = f.p_sh[ip];
+        M[b] = f.m_sh[im];
+        V[b] = f.v_sh[im];
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (p0 + b >= NP) break;
+        const int pl = p0 + b;
+        ok &= adam_elem(P[b], gsh[pl / NC][pl % NC], M[b], V[b], f.lr_sh[pl] * ss, f.b1, f.b2, f.eps, rs_bc2);
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (p0 + b >= NP) break;
+        const int64_t ip = (int64_t)(p0 + b) * f.p_sh_stride + i, im = (int64_t)(p0 + b) * f.mv_sh_stride + i;
+        f.p_sh[ip] = P[b];
+        f.m_sh[im] = M[b];
+        f.v_sh[im] = V[b];
+      }
+    }
+  }
+  if (!ok && f.status) atomicOr(f.status, 1u);
+}
+
 constexpr int kPoseChunks = 64;
 
 // Stage 1 of the pose sum: block (chunk j, view v) sums the per-warp partials
@@ -523,6 +681,98 @@ gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewT
     k_pose_finalize<<<vt.views, kPoseChunks, 0, s>>>(a.pose_a, warps, chunk, dpose);
   }
   return check_launch("project_bwd");
+}
+
+gs_status launch_project_bwd_adam(const gs_params& p, const float* poses, const ViewTable& vt,
+                                  const gs_raster_cfg& cfg, const gs_splats& sp, const gs_bins& bins,
+                                  const float* partials, const gs_grads& g, float* pose_partials, float* dpose,
+                                  float* drgb, const gs_grads& prw, const gs_grads& m, const gs_grads& v,
+                                  const gs_adam_params_cfg& acfg, cudaStream_t s) {
+  GradArgs a;
+  a.means4 = reinterpret_cast<const float4*>(p.means4);
+  a.scale_opa = reinterpret_cast<const float4*>(p.scale_opa);
+  a.quat = reinterpret_cast<const float4*>(p.quat);
+  a.sh = p.sh;
+  a.n = p.n;
+  a.sh_stride = p.sh_stride > 0 ? p.sh_stride : p.n;
+  a.poses = poses;
+  a.clamp_j = cfg.clamp_jacobian;
+  a.touched = sp.touched;
+  a.aux = sp.aux;
+  a.pair_off = bins.pair_off;
+  a.counts = bins.counts;
+  a.partials = partials;
+  a.g_means4 = reinterpret_cast<float4*>(g.means4);
+  a.g_scale_opa = reinterpret_cast<float4*>(g.scale_opa);
+  a.g_quat = reinterpret_cast<float4*>(g.quat);
+  a.g_sh = g.sh;
+  a.g_sh_stride = g.sh_stride > 0 ? g.sh_stride : g.n;
+  const int64_t warps = pose_partial_warps(p.n);
+  a.pose_a = pose_partials;
+  a.pose_b = pose_partials + 6 * warps * vt.views;
+  a.gsum = reinterpret_cast<float4*>(drgb);
+  a.drgb = a.gsum + 2 * p.n * vt.views;
+  AdamFamilies f;
+  const int nc = (p.sh_degree + 1) * (p.sh_degree + 1);
+  for (int q = 0; q < 4; ++q) {
+    f.lr4[0][q] = acfg.lr_means4[q];
+    f.lr4[1][q] = acfg.lr_scale_opa[q];
+    f.lr4[2][q] = acfg.lr_quat[q];
+  }
+  f.on4 = acfg.update_mask & 7u;
+  f.on_sh = (acfg.update_mask & 8u) ? 1u : 0u;
+  for (int pl = 0; pl < 48; ++pl) f.lr_sh[pl] = pl < 3 * nc ? acfg.lr_sh[pl] : 0.f;
+  f.b1 = acfg.beta1; f.b2 = acfg.beta2; f.eps = acfg.eps;
+  f.bc1 = bias_corr(acfg.beta1, acfg.step);
+  f.bc2 = bias_corr(acfg.beta2, acfg.step);
+  f.step_dev = acfg.step_dev;
+  f.skip_dev = acfg.skip_dev;
+  f.status = acfg.status;
+  f.p_means4 = reinterpret_cast<float4*>(prw.means4);
+  f.p_scale_opa = reinterpret_cast<float4*>(prw.scale_opa);
+  f.p_quat = reinterpret_cast<float4*>(prw.quat);
+  f.p_sh = prw.sh;
+  f.p_sh_stride = prw.sh_stride > 0 ? prw.sh_stride : prw.n;
+  f.m_means4 = reinterpret_cast<float4*>(m.means4);
+  f.m_scale_opa = reinterpret_cast<float4*>(m.scale_opa);
+  f.m_quat = reinterpret_cast<float4*>(m.quat);
+  f.v_means4 = reinterpret_cast<float4*>(v.means4);
+  f.v_scale_opa = reinterpret_cast<float4*>(v.scale_opa);
+  f.v_quat = reinterpret_cast<float4*>(v.quat);
+  f.m_sh = m.sh;
+  f.v_sh = v.sh;
+  f.mv_sh_stride = m.sh_stride > 0 ? m.sh_stride : m.n;
+  if (p.n == 0) {
+    if (dpose) cudaMemsetAsync(dpose, 0, sizeof(float) * 6 * vt.views, s);
+    return check_launch("project_bwd_adam");
+  }
+  const unsigned grid = (unsigned)((p.n + kGradBlock - 1) / kGradBlock);
+  const int64_t mm = p.n * vt.views;
+  k_pair_sum<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(a, mm);
+  switch (p.sh_degree) {
+    case 0:
+      k_project_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt);
+      k_sh_bwd_adam<0><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      break;
+    case 1:
+      k_project_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt);
+      k_sh_bwd_adam<1><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      break;
+    case 2:
+      k_project_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt);
+      k_sh_bwd_adam<2><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      break;
+    default:
+      k_project_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt);
+      k_sh_bwd_adam<3><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      break;
+  }
+  if (dpose) {
+    const int64_t chunk = (warps + kPoseChunks - 1) / kPoseChunks;
+    k_pose_chunks<<<dim3(kPoseChunks, vt.views), 256, 0, s>>>(a.pose_a, a.pose_b, warps, chunk);
+    k_pose_finalize<<<vt.views, kPoseChunks, 0, s>>>(a.pose_a, warps, chunk, dpose);
+  }
+  return check_launch("project_bwd_adam");
 }
 
 }  // namespace gs

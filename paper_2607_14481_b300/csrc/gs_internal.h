@@ -48,6 +48,13 @@ gs_status launch_project(const gs_params& p, const float* poses, const ViewTable
                          const int32_t* parent = nullptr, int64_t n_leaf = 0, float tau = 0.f,
                          const gs_hier* hier = nullptr);
 
+// Per-Gaussian backward with the Adam update fused in (gs_grad.cu).
+gs_status launch_project_bwd_adam(const gs_params& p, const float* poses, const ViewTable& vt,
+                                  const gs_raster_cfg& cfg, const gs_splats& sp, const gs_bins& bins,
+                                  const float* partials, const gs_grads& g, float* pose_partials, float* dpose,
+                                  float* drgb, const gs_grads& prw, const gs_grads& m, const gs_grads& v,
+                                  const gs_adam_params_cfg& acfg, cudaStream_t s);
+
 // Progressive hierarchy (gs_hier.cu).
 size_t hier_workspace_bytes(int64_t cap);
 gs_status launch_hier_analyze(const gs_grads& nodes, const gs_hier& h, const gs_grads* m, const gs_grads* v,

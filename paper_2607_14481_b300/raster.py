@@ -104,6 +104,26 @@ class Arena:
         return groups
 
 
+def empty_adam_group() -> _lib.GsAdamGroup:
+    """An Adam group of no element (for a gs_adam_step that only advances the
+    device step counter)."""
+    return _lib.GsAdamGroup(0, 0, (C.c_float * 4)(0.0, 0.0, 0.0, 0.0))
+
+
+def adam_params(sh_degree: int, lr_means=1.6e-4, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3, lr_sh_dc=2.5e-3,
+                lr_sh_rest=1.25e-4, beta1=0.9, beta2=0.999, eps=1e-15, step: int = 0,
+                step_dev: Optional[torch.Tensor] = None, skip_dev: Optional[torch.Tensor] = None,
+                status: Optional[torch.Tensor] = None) -> _lib.GsAdamParamsCfg:
+    """gs_adam_params_cfg with the rates of Arena.adam_groups (the same update
+    as gs_adam_step over those groups)."""
+    nc = (sh_degree + 1) ** 2
+    f4 = C.c_float * 4
+    sh = (C.c_float * 48)(*[(lr_sh_dc if p % nc == 0 else lr_sh_rest) if p < 3 * nc else 0.0 for p in range(48)])
+    return _lib.GsAdamParamsCfg(f4(lr_means, lr_means, lr_means, 0.0), f4(lr_scale, lr_scale, lr_scale, lr_opacity),
+                                f4(lr_quat, lr_quat, lr_quat, lr_quat), sh, beta1, beta2, eps, int(step), 15,
+                                _p(step_dev), _p(skip_dev), _p(status))
+
+
 def sim3_update(arena: Arena, kf: torch.Tensor, sim3: torch.Tensor, status: Optional[torch.Tensor] = None):
     """gs_sim3_update: every Gaussian of the arena moves with the Sim(3)
     correction of its keyframe kf[i] (int32 [n], device; < 0: unchanged);
@@ -468,6 +488,19 @@ class Rasterizer:
                                                   _p(dpose), _p(self.ws_bwd), self.ws_bwd.numel(), _stream()),
                    "gs_render_bwd_gaussians")
 
+    def backward_gaussians_adam(self, params: Arena, poses: torch.Tensor, grads: Arena, m: Arena, v: Arena,
+                                adam: _lib.GsAdamParamsCfg, dpose: Optional[torch.Tensor]) -> None:
+        """gs_render_bwd_gaussians_adam: the per-Gaussian backward with the
+        Adam update of the parameters fused in (grads receives the means,
+        scale/opacity and rotation gradients only)."""
+        ps, gs_, ms, vs = params.rw_struct(), grads.rw_struct(), m.rw_struct(), v.rw_struct()
+        b = self.bins_struct()
+        _lib.check(self.L.gs_render_bwd_gaussians_adam(C.byref(ps), _p(poses), self.cam_struct, self.views,
+                                                       C.byref(self.splats), C.byref(b), C.byref(self.cfg),
+                                                       C.byref(gs_), C.byref(ms), C.byref(vs), C.byref(adam),
+                                                       _p(dpose), _p(self.ws_bwd), self.ws_bwd.numel(), _stream()),
+                   "gs_render_bwd_gaussians_adam")
+
     # -- splat records as tensors (tests, tools) -------------------------------
     def splat_views(self) -> dict:
         """Device tensor views of the splat arrays, shaped [V, n, ...]."""
@@ -508,7 +541,7 @@ def adam_step(params: Arena, grads: Arena, m: Arena, v: Arena, step: int, groups
     (a device int32 scalar) the step is read and incremented on the device, so
     the call can be captured in a CUDA graph."""
     L = _lib.load()
-    garr = (_lib.GsAdamGroup * len(groups))(*groups)
+    garr = (_lib.GsAdamGroup * max(1, len(groups)))(*groups)  # no group: the pose step alone
     cfg = _lib.GsAdamCfg(garr, len(groups), beta1, beta2, eps, _p(status), _p(pose), _p(dpose), _p(pose_m),
                          _p(pose_v), pose.shape[0] if pose is not None else 0, pose_lr, int(pose_step),
                          _p(step_dev), _p(pose_steps_dev), _p(skip_dev))

@@ -18,7 +18,9 @@ from .raster import Arena, ImageLoss, Rasterizer
 
 class TrainStep:
     """Forward, image loss (L1 or MSE), backward (parameters and pose twist),
-    fused Adam (parameters + poses) for the views of `rast`.  With fused=True
+    fused Adam (parameters + poses) for the views of `rast`; with `adam` (a
+    raster.adam_params config whose step_dev is this step's) the parameters'
+    Adam step runs inside the per-Gaussian backward.  With fused=True
     (the default) the composite, the loss and the per-pixel backward run as
     one persistent launch over all views' tiles (gs_render_fused); otherwise
     as three launches (gs_render_fwd, gs_image_loss, gs_render_bwd_pixels).
@@ -34,7 +36,7 @@ class TrainStep:
                  pose_steps: Optional[torch.Tensor] = None, pose_lr: float = 1e-4, loss_kind: int = 0,
                  status: Optional[torch.Tensor] = None, image: Optional[torch.Tensor] = None,
                  dimage: Optional[torch.Tensor] = None, loss: Optional[ImageLoss] = None,
-                 cams: Optional[Sequence] = None, fused: bool = True):
+                 cams: Optional[Sequence] = None, fused: bool = True, adam=None):
         self.arena, self.grads, self.m, self.v, self.groups = arena, grads, m, v, groups
         self.rast = rast
         self.cams = list(cams) if cams is not None else list(rast.cams)
@@ -52,6 +54,9 @@ class TrainStep:
         self.dimg = dimage if dimage is not None else rast.new_image()
         self.loss = loss if loss is not None else ImageLoss(dev)
         self.fused = fused
+        # gs_adam_params_cfg (raster.adam_params): the parameters' Adam step
+        # fused into the per-Gaussian backward; None: a separate gs_adam_step
+        self.adam = adam
         self.graph: Optional[torch.cuda.CUDAGraph] = None
 
     def body(self) -> None:
@@ -66,9 +71,16 @@ class TrainStep:
             r.render_fwd(self.img, None)
             self.loss(self.img, self.targets, self.dimg, self.kind)
             r.backward_pixels(self.dimg, None, self.img)
-        r.backward_gaussians(self.arena, self.poses, self.grads, self.dpose)
         with_pose = self.pose_m is not None
-        raster.adam_step(self.arena, self.grads, self.m, self.v, 0, self.groups, status=self.status,
+        groups = self.groups
+        if self.adam is not None:
+            r.backward_gaussians_adam(self.arena, self.poses, self.grads, self.m, self.v, self.adam, self.dpose)
+            # the parameters are updated; the poses and the step counter remain
+            # (an empty group when there is no pose step)
+            groups = [] if with_pose else [raster.empty_adam_group()]
+        else:
+            r.backward_gaussians(self.arena, self.poses, self.grads, self.dpose)
+        raster.adam_step(self.arena, self.grads, self.m, self.v, 0, groups, status=self.status,
                          pose=self.poses if with_pose else None, dpose=self.dpose if with_pose else None,
                          pose_m=self.pose_m, pose_v=self.pose_v, pose_lr=self.pose_lr,
                          step_dev=self.step_dev, pose_steps_dev=self.pose_steps)

@@ -109,21 +109,27 @@ def test_both_arms_report_the_same_config():
 
 def test_library_kernels_per_training_step():
     # projection 1, binning 6, fused composite + loss + per-pixel backward 1,
-    # per-Gaussian backward 5, Adam 3; a longest-first order costs no launch;
-    # unfused: composite 1, loss 2, per-pixel backward 1 instead of the fused 1;
+    # per-Gaussian backward 5 with the parameters' Adam inside, pose Adam and
+    # step counter 2; a longest-first order costs no launch; unfused:
+    # composite 1, loss 2, per-pixel backward 1 and a separate parameter Adam;
     # beyond 2^18 tiles the tile scan takes 5 launches instead of 1
-    assert bench.launches_per_step(1, 3600) == 16
-    assert bench.launches_per_step(1, 3600, tile_order=True) == 16
+    assert bench.launches_per_step(1, 3600) == 15
+    assert bench.launches_per_step(1, 3600, tile_order=True) == 15
     assert bench.launches_per_step(1, 3600, fused=False) == 19
-    assert bench.launches_per_step(64, 1 << 19) == 20
+    assert bench.launches_per_step(1, 3600, fused_adam=False) == 16
+    assert bench.launches_per_step(64, 1 << 19) == 19
 
 
 def test_roofline_of_the_fused_step():
     cam = synth.forward_trajectory(3, seed=1008)[0]
-    st = {"project": 0.08, "bin_sort": 0.21, "render_fused": 0.55, "render_bwd_gaussians": 0.2, "adam": 0.32}
+    st = {"project": 0.08, "bin_sort": 0.21, "render_fused": 0.55, "bwd_gaussians_adam": 0.3, "pose_adam": 0.01}
     r = bench.roofline(_workload(1_000_000, [cam]), st, WORK, PEAKS, sms=148)
     # both traversals per evaluated pair: 12 + 45 FP32, 1 + 2 MUFU
     assert r["kernel"] == "render_fused" and r["binding_unit"] == "fp32"
     assert r["algorithmic"] == pytest.approx(57 * 178e6)
     assert r["frac"] == pytest.approx(57 * 178e6 / 0.55e-3 / (148 * 128 * 2032e6))
     assert "loss" not in r["per_stage"] and "render_fwd" not in r["per_stage"]
+    # the per-Gaussian backward with Adam inside: 36 B per pair, 24 B per
+    # float + 96 B per Gaussian (60 floats)
+    ga = r["per_stage"]["bwd_gaussians_adam"]
+    assert ga["bound"] == "hbm" and ga["algorithmic"] == pytest.approx(1.81e6 * 36 + 1_000_000 * (24 * 60 + 96))

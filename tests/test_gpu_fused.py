@@ -209,3 +209,65 @@ def test_full_size_batched_2m_16_views_fused_every_tile_shape(cuda_device):
         compare_grads(g_f, g_ref)
         del r, arena, img, alpha
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("deg,nviews", [(0, 1), (1, 2), (2, 1), (3, 3)])
+def test_adam_fused_into_the_gaussian_backward_equals_separate_step(cuda_device, deg, nviews):
+    """gs_render_bwd_gaussians_adam (the Adam update applied by the SH kernel)
+    leaves parameters and moments bit-identical to gs_render_bwd_gaussians +
+    gs_adam_step with the matching groups, over two steps with the device step
+    counter; a set skip word leaves everything unchanged; parameters left out
+    of update_mask keep their values and moments."""
+    from paper_2607_14481_b300 import train
+    dev = torch.device("cuda:0")
+    sc = synth.random_scene(4000, 31 + deg, deg, (-1, -1, -1), (1, 1, 1), -3.2, 0.4)
+    eyes = [(0.0, 0.0, -3.0), (0.5, -0.2, -2.7), (-0.4, 0.3, -3.2)][:nviews]
+    sizes = [(96, 64), (80, 88), (70, 50)][:nviews]
+    cams = [synth.look_at(e, (0, 0, 0), 80.0, 80.0, w / 2, h / 2, w, h) for e, (w, h) in zip(eyes, sizes)]
+    lrs = dict(lr_means=1e-2, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4)
+    runs = []
+    for fused_adam in (False, True):
+        arena = raster.Arena.from_scene(sc, dev)
+        grads, m, v = arena.like(), arena.like(), arena.like()
+        r = raster.Rasterizer(sc.n, deg, cams, device=dev)
+        poses = raster.poses_tensor(cams, dev)
+        tgt = torch.rand(3 * r.pixels, generator=torch.Generator().manual_seed(5)).to(dev)
+        step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        ap = raster.adam_params(deg, step_dev=step_dev, status=status, **lrs) if fused_adam else None
+        st = train.TrainStep(arena, grads, m, v, arena.adam_groups(**lrs), r, poses, tgt, step_dev, status=status,
+                             adam=ap)
+        r.forward(arena, poses, r.new_image(), None, check=True)  # pair capacity for these views
+        for _ in range(2):
+            st.run()
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0 and int(step_dev.item()) == 2
+        runs.append((arena.buf.clone(), m.buf.clone(), v.buf.clone()))
+    for a, b in zip(runs[0], runs[1]):
+        assert torch.equal(a, b)
+    # skip word and update mask, straight through the entry point
+    arena = raster.Arena.from_scene(sc, dev)
+    grads, m, v = arena.like(), arena.like(), arena.like()
+    m.buf.fill_(0.5)
+    v.buf.fill_(0.25)
+    r = raster.Rasterizer(sc.n, deg, cams, device=dev)
+    poses = raster.poses_tensor(cams, dev)
+    img = r.new_image()
+    r.forward(arena, poses, img, None, check=True)
+    dimg = torch.full_like(img, 1e-3)
+    r.backward_pixels(dimg, None, img)
+    skip = torch.ones(1, dtype=torch.int32, device=dev)
+    before = (arena.buf.clone(), m.buf.clone(), v.buf.clone())
+    r.backward_gaussians_adam(arena, poses, grads, m, v, raster.adam_params(deg, step=1, skip_dev=skip, **lrs), None)
+    torch.cuda.synchronize()
+    assert all(torch.equal(x, y) for x, y in zip(before, (arena.buf, m.buf, v.buf)))
+    ap = raster.adam_params(deg, step=1, **lrs)
+    ap.update_mask = 1 | 8  # means and SH only
+    r.backward_gaussians_adam(arena, poses, grads, m, v, ap, None)
+    torch.cuda.synchronize()
+    n = sc.n
+    for lo, hi in ((4 * n, 8 * n), (8 * n, 12 * n)):  # scale_opa, quat untouched
+        assert torch.equal(arena.buf[lo:hi], before[0][lo:hi])
+        assert torch.equal(m.buf[lo:hi], before[1][lo:hi]) and torch.equal(v.buf[lo:hi], before[2][lo:hi])
+    assert not torch.equal(arena.buf[0:4 * n], before[0][0:4 * n])
+    assert not torch.equal(m.buf[12 * n:], before[1][12 * n:])
