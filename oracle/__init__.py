@@ -455,6 +455,8 @@ def _hier_lib():
         L.orc_hier_analyze.restype = C.c_int
         L.orc_hier_refine.argtypes = [C.c_int64, d, d, i32, u8, d, d, i32, C.c_double, C.c_double, u8]
         L.orc_hier_refine.restype = C.c_int64
+        L.orc_hier_render_cut.argtypes = [C.c_int64, d, d, i32, i32, d, d, i32, C.c_double, C.c_double, u8, u8]
+        L.orc_hier_render_cut.restype = C.c_int64
         L._hier_ready = True
     return L
 
@@ -556,6 +558,23 @@ def hier_refine(st: HierState, cam, znear=0.2, tau_h=1.0):
                           wh.ctypes.data_as(C.POINTER(C.c_int32)), float(znear), float(tau_h),
                           amb.ctypes.data_as(C.POINTER(C.c_uint8)))
     return int(k), amb
+
+
+def hier_render_cut(st: HierState, cam, znear=0.2, tau=1.0):
+    """Rendering a stored hierarchy (Sec. 6.2): descend from the roots while a
+    node is coarser than tau and has children.  Returns (selected [n_nodes]
+    uint8, amb [n_nodes] uint8: a decision within 1e-5 of tau on the node's
+    path); the state is not changed."""
+    L = _hier_lib()
+    n = st.n_nodes
+    sel = np.zeros(max(1, n), np.uint8)
+    amb = np.zeros(max(1, n), np.uint8)
+    pose, intr, wh = _cam_args(cam)
+    L.orc_hier_render_cut(n, _p(st.means), _p(st.log_scales), st.parent.ctypes.data_as(C.POINTER(C.c_int32)),
+                          st.child.ctypes.data_as(C.POINTER(C.c_int32)), _p(pose), _p(intr),
+                          wh.ctypes.data_as(C.POINTER(C.c_int32)), float(znear), float(tau),
+                          sel.ctypes.data_as(C.POINTER(C.c_uint8)), amb.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return sel[:n].copy(), amb[:n].copy()
 
 
 def hier_view_cut(st: HierState, cam, znear=0.2, tau_h=1.0) -> np.ndarray:

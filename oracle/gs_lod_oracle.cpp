@@ -585,6 +585,38 @@ int orc_hier_analyze(int64_t n_nodes, int64_t cap, int nsh, float* means32, doub
   return 0;
 }
 
+// Render cut (Sec. 6.2, rendering a stored hierarchy): start at the roots
+// (nodes without a parent) and descend while a node is coarser than tau
+// (S > tau, +inf at or behind the near plane) and has children; the nodes
+// where the descent stops are rendered.  selected[i] = 1 iff node i does not
+// descend and every ancestor does (independent of the active set).  amb[i] =
+// 1 when S of the node or of an ancestor lies within 1e-5 of tau.  Returns
+// the number of selected nodes.
+int64_t orc_hier_render_cut(int64_t n_nodes, const double* mu, const double* lsc, const int32_t* parent,
+                            const int32_t* child, const double* pose12, const double* intr, const int32_t* wh,
+                            double znear, double tau, uint8_t* selected, uint8_t* amb) {
+  const HierView v = hier_view(pose12, intr, wh, znear);
+  std::vector<double> S((size_t)n_nodes);
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    bool in;
+    hier_screen(v, mu, lsc, i, &S[(size_t)i], &in);
+  }
+  auto descends = [&](int64_t k) { return child[4 * k] >= 0 && S[(size_t)k] > tau; };
+  int64_t cnt = 0;
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    bool ok = !descends(i);
+    bool a = near_rel(S[(size_t)i], tau, 1e-5);
+    for (int32_t p = parent[i]; p >= 0; p = parent[p]) {
+      ok = ok && descends(p);
+      a = a || near_rel(S[(size_t)p], tau, 1e-5);
+    }
+    selected[i] = ok ? 1 : 0;
+    amb[i] = a ? 1 : 0;
+    cnt += ok ? 1 : 0;
+  }
+  return cnt;
+}
+
 // Reload (Sec. 6.1): refinement passes of the active set for one view.
 // Returns the number of nodes replaced by their children; amb [n_nodes]
 // marks nodes whose S lies within 1e-5 of tau_h.

@@ -255,3 +255,79 @@ def test_active_set_stays_a_cut_over_random_analyses_and_reloads():
             c = st.parent[c]
             depth[i] += 1
     assert depth.max() >= 1
+
+
+def test_render_cut_worked_example():
+    # node 4 (parent of leaves 0-3) at depth 50 with scale 0.5: S = 3 F 0.5 /
+    # 50 = 3 px > 1, so the descent goes on to its children; node 5 is a
+    # root leaf.  With scale 1e-3 (S = 0.006 px) the parent itself is drawn.
+    sel, amb = oracle.hier_render_cut(_tree(big_parent=True), _cam())
+    assert list(sel) == [1, 1, 1, 1, 0, 1] and not amb.any()
+    sel, _ = oracle.hier_render_cut(_tree(big_parent=False), _cam())
+    assert list(sel) == [0, 0, 0, 0, 1, 1]
+    # the active set does not matter
+    st = _tree(big_parent=False)
+    st.active[:] = 0
+    st.active[:4] = 1
+    assert list(oracle.hier_render_cut(st, _cam())[0]) == [0, 0, 0, 0, 1, 1]
+    # behind the camera S is infinite: the descent reaches every leaf
+    back = synth.Camera(np.diag([-1.0, 1.0, -1.0]).astype(np.float32), np.zeros(3, np.float32), F, F, 100, 100,
+                        200, 200)
+    assert list(oracle.hier_render_cut(_tree(big_parent=False), back)[0]) == [1, 1, 1, 1, 0, 1]
+
+
+def _brute_render_cut(st, cam, znear=0.2, tau=1.0):
+    """Recursive descent from the roots with the screen size written out
+    independently: t_z = R[2] . m + t[2], S = f_x 3 max exp(log-scale) / t_z,
+    +inf at or behind the near plane."""
+    R = np.asarray(cam.R, np.float64)
+    t = np.asarray(cam.t, np.float64)
+    n = st.n_nodes
+    S = np.empty(n)
+    for i in range(n):
+        tz = float(R[2] @ st.means[i] + t[2])
+        S[i] = np.inf if tz <= znear else float(cam.fx) * 3.0 * np.exp(st.log_scales[i].max()) / tz
+    sel = np.zeros(n, np.uint8)
+
+    def visit(k):
+        kids = [int(c) for c in st.child[k] if c >= 0]
+        if kids and S[k] > tau:
+            for c in kids:
+                visit(c)
+        else:
+            sel[k] = 1
+
+    for r in range(n):
+        if st.parent[r] < 0:
+            visit(r)
+    return sel
+
+
+def test_render_cut_against_brute_force_descent():
+    g = np.random.default_rng(17)
+    n = 500
+    means = np.column_stack([g.uniform(-2, 2, n), g.uniform(-1, 1, n), g.uniform(4, 30, n)])
+    st = oracle.HierState(_scene(means, g.normal(-5.5, 0.6, n)), 4 * n)
+    cams = [synth.look_at((g.uniform(-1, 1), g.uniform(-0.5, 0.5), g.uniform(-15, 2)), (0, 0, 15), F, F, 100, 100,
+                          200, 200) for _ in range(8)]
+    for c in cams[:6]:
+        oracle.hier_analyze(st, c)
+    assert st.n_nodes > n
+    coarser = 0
+    for c in cams:
+        for tau in (0.5, 1.0, 4.0):
+            sel, amb = oracle.hier_render_cut(st, c, tau=tau)
+            want = _brute_render_cut(st, c, tau=tau)
+            ok = amb == 0
+            assert np.array_equal(sel[ok], want[ok])
+            # a cut: every leaf has exactly one selected node on its path
+            for i in range(st.n_nodes):
+                if st.child[i, 0] >= 0:
+                    continue
+                k, p = 0, i
+                while p >= 0:
+                    k += int(sel[p])
+                    p = st.parent[p]
+                assert k == 1
+            coarser += int(sel[n:st.n_nodes].sum())
+    assert coarser > 0  # merged nodes are drawn somewhere
