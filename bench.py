@@ -746,29 +746,33 @@ def run_local_ba(device, iters=10, reps=30, cpu=True, seed=SEED_BA):
     return out
 
 
-def run_lod(device, n_frames=100, per_frame=50_000, reps=10, taus=(1.0, 4.0, 16.0), seed=SEED_STREAM):
-    """The level-of-detail hierarchy on a streamed scene: n_frames x per_frame
-    Gaussians spawned in the frustums of a camera walking the 200 m loop (the
-    streaming workload's generator), SH3.  Times, with CUDA events over `reps`
-    launches each: gs_lod_build (Morton grouping, sort, two merge levels) and,
-    for frame 0's 1080p view, the projection of all leaves against the cut
-    projection at each tau (pixels), then binning + composite of each.  HBM figure of
-    the build: 340 B per leaf (means for the codes 16 B, three 8-bit sort
-    passes over (code, index) 48 B, leaf parameters read by the first merge
-    240 B, a level-1 node written per 8 leaves 30 B, parent ids 4 B)."""
+def run_lod(device, n_frames=100, per_frame=50_000, reps=5, keyframe_every=10, loop_m=1000.0, seed=SEED_STREAM):
+    """The progressive hierarchy (Sec. 6.1 merging and retrieval, Sec. 6.2
+    rendering) on a large streamed scene: n_frames x per_frame Gaussians
+    spawned in the frustums of a camera walking a loop_m loop (10 m between
+    frames; about 1.5 px on screen when spawned, so most of the scene is
+    sub-pixel from any one camera), in overlapping groups of four as on a
+    reconstructed surface (synth.frustum_clusters), SH3, node rows for twice
+    the leaves.  An analysis
+    (merge below tau_l = 0.5 px when more than 20% qualify, then reload above
+    tau_h = 1 px) runs from every keyframe_every-th camera, in loop order,
+    each timed with CUDA events.  Then, for the 1080p views of frames 0, 25,
+    50 and 75: the splats the projection keeps and the tile pairs with all
+    leaves, with the final active set refined for the view (what a training
+    view optimises) and with the render cut from the roots at tau = 1 px
+    (what a render draws, Sec. 6.2), and the time of projection + binning +
+    composite of each (mean of `reps`)."""
     import torch
     from paper_2607_14481_b300 import raster, synth
-    cams = [synth.stream_camera(k, n_frames) for k in range(n_frames)]
-    parts = [synth.frustum_gaussians(cams[k], per_frame, seed * 7919 + k) for k in range(n_frames)]
+    cams = [synth.stream_camera(k, n_frames, loop_m=loop_m) for k in range(n_frames)]
+    parts = [synth.frustum_clusters(cams[k], per_frame, seed * 7919 + k) for k in range(n_frames)]
     sc = synth.Scene(*(np.concatenate([getattr(p, f) for p in parts]) for f in
                        ("means", "log_scales", "quats", "opa_logits", "sh")))
     del parts
     n = sc.n
-    from paper_2607_14481_b300 import _lib
-    n_nodes = int(_lib.load().gs_lod_nodes(n))
-    arena = raster.Arena.from_scene(sc, device, capacity=n_nodes)
+    arena = raster.Arena.from_scene(sc, device, capacity=2 * n)
     del sc
-    lod = raster.LodHierarchy(arena, n)
+    hier = raster.Hierarchy(arena, n)
 
     def timed(fn, k):
         fn()
@@ -781,40 +785,67 @@ def run_lod(device, n_frames=100, per_frame=50_000, reps=10, taus=(1.0, 4.0, 16.
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
 
-    build_ms = timed(lod.build, reps)
-    cam = [cams[0]]
-    poses = raster.poses_tensor(cam, device)
-    out = {"leaves": n, "nodes": n_nodes, "view": [cam[0].width, cam[0].height], "build_ms": build_ms}
+    analyses = []
+    for k in range(0, n_frames, keyframe_every):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        hier.analyze(cams[k])
+        e1.record()
+        hier.refine(cams[k])
+        e2.record()
+        torch.cuda.synchronize()
+        st = hier.state()
+        info = st["info"]
+        analyses.append({"frame": k, "analyze_ms": e0.elapsed_time(e1), "reload_ms": e1.elapsed_time(e2),
+                         "nodes": st["n_nodes"], "active": int(st["active"][:st["n_nodes"]].sum()),
+                         "candidates": int(info[2]), "triggered": int(info[1]), "groups": int(info[5]),
+                         "pulled": int(info[4])})
+    st = hier.state()
+    rows = st["n_nodes"]
+    out = {"leaves": n, "loop_m": loop_m, "node_rows": rows, "active": int(st["active"][:rows].sum()),
+           "merged_nodes": rows - n, "analyses": analyses,
+           "analysis_ms_mean": float(np.mean([a["analyze_ms"] + a["reload_ms"] for a in analyses])),
+           "tau_l": 0.5, "tau_h": 1.0, "views": {}}
+
     class _Leaves:  # the first n rows of the node arena (its SH stride), as projection parameters
         def struct(self):
             return arena.struct(n)
-    leaves_arena = _Leaves()
-    for name, r_n, proj in [("leaves", n, None)] + [(f"cut_tau{t:g}", n_nodes, t) for t in taus]:
-        r = raster.Rasterizer(r_n, 3, cam, device=device)
-        img = r.new_image()
-        if proj is None:
-            r.forward(leaves_arena, poses, img, None, check=True)
-            pj = lambda: r.project(leaves_arena, poses)
-        else:
-            r.forward(arena, poses, img, None, check=True, lod=lod, tau=proj)
-            pj = lambda: r.project_lod(lod, poses, proj)
-        cnt = r.read_counts()
-        proj_ms = timed(pj, reps)
 
-        def fwd():
+    leaves = _Leaves()
+    for k in (0, n_frames // 4, n_frames // 2, 3 * n_frames // 4):
+        poses = raster.poses_tensor([cams[k]], device)
+        res = {}
+        for name in ("leaves", "active_cut", "render_cut"):
+            r = raster.Rasterizer(n if name == "leaves" else rows, 3, [cams[k]], device=device)
+            img = r.new_image()
+            if name == "leaves":
+                pj = lambda: r.project(leaves, poses)
+            else:
+                pj = lambda: r.project_hier(hier, poses, tau_h=1.0, from_roots=name == "render_cut")
+            pj()
+            r.set_capacity(max(4096, r.capacity))
+            r.bin_sort()
+            torch.cuda.synchronize()
+            c = r.read_counts()
+            if c[2] & 1:
+                r.set_capacity(int(c[1] * 1.25) + 4096)
             pj()
             r.bin_sort()
-            r.render_fwd(img, None)
-        out[name] = {"project_ms": proj_ms, "project_bin_render_ms": timed(fwd, reps),
-                     "rendered_splats": int(cnt[0]), "pairs": int(cnt[1])}
-        del r, img
-        torch.cuda.empty_cache()
-    peaks = load_peaks()
-    gbs = 340.0 * n / (build_ms / 1e3) / 1e9
-    out["build_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                             "frac": gbs / peaks["hbm_gbs"], "bytes_per_leaf": 340}
+            torch.cuda.synchronize()
+            c = r.read_counts()
+
+            def fwd():
+                pj()
+                r.bin_sort()
+                r.render_fwd(img, None)
+            res[name] = {"rendered_splats": int(c[0]), "pairs": int(c[1]), "project_bin_render_ms": timed(fwd, reps)}
+            del r, img
+            torch.cuda.empty_cache()
+        res["splat_ratio"] = res["render_cut"]["rendered_splats"] / max(1, res["leaves"]["rendered_splats"])
+        res["speedup"] = res["leaves"]["project_bin_render_ms"] / res["render_cut"]["project_bin_render_ms"]
+        out["views"][f"frame{k}"] = res
     out["paper_traversal_ms"] = "5-30 (the paper's hierarchy traversal per frame; another GPU; context)"
-    del lod, arena, leaves_arena
+    del hier, arena, leaves
     torch.cuda.empty_cache()
     return out
 

@@ -444,6 +444,16 @@ GS_API gs_status gs_hier_refine(gs_grads* nodes, gs_hier* h, const gs_grads* ada
 GS_API gs_status gs_project_hier(const gs_params* nodes, const gs_hier* h, float tau_h, const float* poses_dev,
                                  const gs_camera* cams, int32_t views, const gs_raster_cfg* cfg, gs_splats* out,
                                  gs_stream stream);
+/* gs_project over the first nodes->n rows with each view's render cut of the
+ * stored hierarchy (Sec. 6.2): starting at the roots (parent -1), the descent
+ * goes on through every node that has children and is coarser than tau
+ * (S > tau; S = +inf at or behind the near plane), and stops at the others,
+ * which are projected: node i is projected iff it does not descend and every
+ * ancestor does.  The active set is not read (h->active may be NULL); rows
+ * >= *h->n_nodes are culled. */
+GS_API gs_status gs_project_hier_render(const gs_params* nodes, const gs_hier* h, float tau,
+                                        const float* poses_dev, const gs_camera* cams, int32_t views,
+                                        const gs_raster_cfg* cfg, gs_splats* out, gs_stream stream);
 
 /* Workspace bytes of gs_bin_sort. */
 GS_API size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity);
@@ -726,9 +736,9 @@ typedef struct {
   float lr_means, lr_scale, lr_opacity, lr_quat, lr_sh_dc, lr_sh_rest;
   float beta1, beta2, eps;
   int32_t loss_kind;         /* 0 = L1, 1 = MSE */
-  int32_t lod;               /* 1: a progressive hierarchy (gs_session_analyze); renders and trains use
-                                each view's cut of its active set */
-  float lod_tau;             /* reload / cut threshold in pixels (> 0; the paper's tau_h = 1); merging
+  int32_t lod;               /* 1: a progressive hierarchy (gs_session_analyze); renders draw its render
+                                cut (descent from the roots), trains each view's cut of the active set */
+  float lod_tau;             /* reload / cut threshold in pixels (> 0; the paper's tau_h = tau = 1); merging
                                 takes nodes below lod_tau / 2 (the paper's tau_l = 0.5) */
 } gs_session_config;
 
@@ -835,8 +845,9 @@ GS_API gs_status gs_session_load(gs_session* s, const char* path);
  * the buffers (the Adam moments of nodes whose flag changed are zeroed and
  * every new merged node takes its children's most common keyframe tag).
  * Leaves occupy rows [0, max_gaussians), merged nodes the rows after them;
- * renders and trains use each view's cut of the front active set, so merged
- * nodes are trained.  GS_ERR_BUSY (nothing issued) while the previous
+ * trains use each view's cut of the front active set, so merged nodes are
+ * trained; renders draw the render cut of the hierarchy (gs_project_hier_render
+ * at lod_tau: descent from the roots while a node is coarser than lod_tau).  GS_ERR_BUSY (nothing issued) while the previous
  * analysis has not completed; GS_ERR_INVALID without a hierarchy.
  * Checkpoints (gs_session_save / load) are not supported with a hierarchy. */
 GS_API gs_status gs_session_analyze(gs_session* s, const gs_camera* cam, const float* pose12);

@@ -32,7 +32,7 @@ EXPORTED = (
     "gs_adam_step", "gs_image_loss_workspace", "gs_image_loss", "gs_render_stats",
     "gs_lod_nodes", "gs_lod_build_workspace", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
     "gs_render_fused_workspace", "gs_render_fused", "gs_autotune_fused",
-    "gs_hier_workspace", "gs_hier_analyze", "gs_hier_refine", "gs_project_hier",
+    "gs_hier_workspace", "gs_hier_analyze", "gs_hier_refine", "gs_project_hier", "gs_project_hier_render",
     "gs_ba_workspace_bytes", "gs_ba_solve",
     "gs_session_now", "gs_session_plan", "gs_session_create", "gs_session_add_gaussians", "gs_session_submit",
     "gs_session_poll", "gs_session_wait", "gs_session_drain", "gs_session_hold", "gs_session_times", "gs_session_set_keyframe", "gs_session_loop_closure", "gs_session_keyframe_weights", "gs_session_stats", "gs_session_read_params",
@@ -202,6 +202,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                  C.c_float, i32, vp, sz, vp]
     L.gs_project_hier.argtypes = [P(GsParams), P(GsHier), C.c_float, vp, P(GsCamera), i32, P(GsRasterCfg),
                                   P(GsSplats), vp]
+    L.gs_project_hier_render.argtypes = [P(GsParams), P(GsHier), C.c_float, vp, P(GsCamera), i32,
+                                         P(GsRasterCfg), P(GsSplats), vp]
     L.gs_sim3_update.argtypes = [P(GsGrads), vp, vp, i32, vp, vp]
     L.gs_keyframe_counts.argtypes = [vp, i64, i32, vp, vp]
     L.gs_lod_nodes.argtypes = [i64]
@@ -251,7 +253,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                  "gs_image_loss",
                  "gs_render_stats", "gs_lod_build", "gs_project_lod", "gs_sim3_update", "gs_keyframe_counts", "gs_autotune_blend",
                  "gs_ba_solve", "gs_render_fused", "gs_autotune_fused", "gs_hier_analyze", "gs_hier_refine",
-                 "gs_project_hier"):
+                 "gs_project_hier", "gs_project_hier_render"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

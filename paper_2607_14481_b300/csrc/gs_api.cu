@@ -357,6 +357,23 @@ gs_status gs_project_hier(const gs_params* nodes, const gs_hier* h, float tau_h,
   return launch_project(*nodes, poses_dev, vt, *cfg, *out, (cudaStream_t)stream, nullptr, 0, tau_h, h);
 }
 
+gs_status gs_project_hier_render(const gs_params* nodes, const gs_hier* h, float tau, const float* poses_dev,
+                                 const gs_camera* cams, int32_t views, const gs_raster_cfg* cfg, gs_splats* out,
+                                 gs_stream stream) {
+  GS_NVTX("gs_project_hier_render");
+  gs_status st;
+  if ((st = check_params(nodes)) != GS_OK) return st;
+  if ((st = check_cfg(cfg)) != GS_OK) return st;
+  ViewTable vt;
+  if (!make_view_table(cams, views, &vt, cfg->tile_w, cfg->tile_h)) return GS_ERR_INVALID;
+  if (!poses_dev) return fail(GS_ERR_INVALID, "poses is NULL");
+  if (!h || !h->parent || !h->child || !h->n_nodes || h->capacity < nodes->n)
+    return fail(GS_ERR_INVALID, "hierarchy arrays must cover nodes->n rows");
+  if (!(tau > 0.f)) return fail(GS_ERR_INVALID, "tau must be > 0");
+  if ((st = check_splats(out, nodes->n, views)) != GS_OK) return st;
+  return launch_project(*nodes, poses_dev, vt, *cfg, *out, (cudaStream_t)stream, nullptr, 0, tau, h, true);
+}
+
 size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity) {
   return bin_sort_workspace_bytes(std::max<int64_t>(0, n) * std::max(0, views), std::max<int64_t>(0, capacity));
 }

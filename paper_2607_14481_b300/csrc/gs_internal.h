@@ -42,11 +42,13 @@ bool make_view_table(const gs_camera* cams, int views, ViewTable* vt, int tw = k
 
 // ---- kernels' host launchers (each enqueues on `s`, returns GS_OK or GS_ERR_CUDA)
 // parent != nullptr: level-of-detail cut (nodes [0, n_leaf) are leaves);
-// hier != nullptr: the view cut of the progressive hierarchy at tau.
+// hier != nullptr: the view cut of the progressive hierarchy at tau (the
+// active set refined for the view), or with hier_roots its render cut from
+// the roots.
 gs_status launch_project(const gs_params& p, const float* poses, const ViewTable& vt,
                          const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s,
                          const int32_t* parent = nullptr, int64_t n_leaf = 0, float tau = 0.f,
-                         const gs_hier* hier = nullptr);
+                         const gs_hier* hier = nullptr, bool hier_roots = false);
 
 // Per-Gaussian backward with the Adam update fused in (gs_grad.cu).
 gs_status launch_project_bwd_adam(const gs_params& p, const float* poses, const ViewTable& vt,

@@ -34,6 +34,7 @@ struct ProjectArgs {
   const int32_t* h_child;
   const uint8_t* h_active;
   const uint32_t* h_n;
+  int h_roots;            // 1: the render cut from the roots (h_active unused)
 };
 
 // Screen size of a node: f_x * 3 * max_k scale_k / t_z, infinite at or
@@ -80,7 +81,27 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
     }
     vis = sel;
   }
-  if (vis && a.h_active) {
+  if (vis && a.h_roots) {
+    // the render cut: descend from the roots while a node has children and
+    // is coarser than tau; the nodes where the descent stops are drawn
+    auto descends = [&](int64_t k) {
+      if (a.h_child[4 * k] < 0) return false;
+      bool in;
+      const float S = hier_node_screen(R, tc, vi.fx, vi.fy, vi.cx, vi.cy, vi.W, vi.H, a.znear, a.means4[k],
+                                       a.scale_opa[k], in);
+      return S > a.tau;
+    };
+    bool sel = i < (int64_t)*a.h_n && !descends(i);
+    int32_t p = sel ? a.h_parent[i] : -1;
+    for (int d = 0; p >= 0; ++d) {
+      if (d >= 64 || !descends(p)) {
+        sel = false;
+        break;
+      }
+      p = a.h_parent[p];
+    }
+    vis = sel;
+  } else if (vis && a.h_active) {
     // the active set refined for this view: rendered iff not expandable, and
     // either active or below an active ancestor through expandable nodes
     auto expandable = [&](int64_t k) {
@@ -221,7 +242,7 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
 
 gs_status launch_project(const gs_params& p, const float* poses, const ViewTable& vt,
                          const gs_raster_cfg& cfg, const gs_splats& out, cudaStream_t s, const int32_t* parent,
-                         int64_t n_leaf, float tau, const gs_hier* hier) {
+                         int64_t n_leaf, float tau, const gs_hier* hier, bool hier_roots) {
   ProjectArgs a;
   a.means4 = reinterpret_cast<const float4*>(p.means4);
   a.scale_opa = reinterpret_cast<const float4*>(p.scale_opa);
@@ -246,6 +267,7 @@ gs_status launch_project(const gs_params& p, const float* poses, const ViewTable
   a.h_child = hier ? hier->child : nullptr;
   a.h_active = hier ? hier->active : nullptr;
   a.h_n = hier ? hier->n_nodes : nullptr;
+  a.h_roots = hier && hier_roots ? 1 : 0;
   if (p.n == 0) return GS_OK;
   dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)vt.views);
   switch (p.sh_degree) {

@@ -478,7 +478,7 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     gs_params PR = P;
     gs_hier hf;
     if (cf.lod) {
-      // the view cut of the front active set over every node row in use
+      // every node row in use (the render cut does not read the active set)
       PR.n = S->h_rows;
       hf = hier_of(S, S->front);
     }
@@ -489,8 +489,9 @@ gs_status issue_batch(gs_session* S, Ctx& c) {
     gs_bins b{static_cast<uint32_t*>(c.vals.p), static_cast<uint32_t*>(c.ranges.p),
               static_cast<uint32_t*>(c.pair_off.p), nullptr, counts, c.pair_cap, vt.total_tiles,
               static_cast<uint32_t*>(c.order.p)};
-    if ((st = launch_project(PR, poses, vt, cf.raster, sp, rs, nullptr, 0, cf.lod_tau, cf.lod ? &hf : nullptr)) !=
-        GS_OK)
+    // renders draw the hierarchy's render cut (descent from the roots, Sec. 6.2)
+    if ((st = launch_project(PR, poses, vt, cf.raster, sp, rs, nullptr, 0, cf.lod_tau, cf.lod ? &hf : nullptr,
+                             true)) != GS_OK)
       return st;
     if ((st = launch_bin_sort(sp, vt, b, c.ws_bin.p, rs)) != GS_OK) return st;
     if ((st = launch_render_fwd(sp, b, vt, cf.raster, img, nullptr, rs)) != GS_OK) return st;

@@ -345,14 +345,16 @@ class Rasterizer:
                                          self.cam_struct, self.views, C.byref(self.cfg), C.byref(self.splats),
                                          _stream()), "gs_project_lod")
 
-    def project_hier(self, hier: "Hierarchy", poses: torch.Tensor, tau_h: float = 1.0) -> None:
+    def project_hier(self, hier: "Hierarchy", poses: torch.Tensor, tau_h: float = 1.0, from_roots=False) -> None:
         """gs_project_hier: each view's cut of the progressive hierarchy over
-        this Rasterizer's n node rows."""
+        this Rasterizer's n node rows (the active set refined for the view),
+        or, from_roots, gs_project_hier_render (the render cut descending from
+        the roots)."""
         ps = hier.arena.struct(self.n)
         h = hier.struct()
-        _lib.check(self.L.gs_project_hier(C.byref(ps), C.byref(h), float(tau_h), _p(poses), self.cam_struct,
-                                          self.views, C.byref(self.cfg), C.byref(self.splats), _stream()),
-                   "gs_project_hier")
+        fn = self.L.gs_project_hier_render if from_roots else self.L.gs_project_hier
+        _lib.check(fn(C.byref(ps), C.byref(h), float(tau_h), _p(poses), self.cam_struct, self.views,
+                      C.byref(self.cfg), C.byref(self.splats), _stream()), "gs_project_hier")
 
     def bin_sort(self) -> None:
         b = self.bins_struct()

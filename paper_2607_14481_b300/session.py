@@ -19,8 +19,9 @@ def default_config(max_gaussians: int, sh_degree: int = 3, max_batch_views: int 
                    lr_sh_rest=1.25e-4, lod: bool = False, lod_tau: float = 1.0,
                    tile=(16, 16)) -> _lib.GsSessionConfig:
     """lod: a progressive hierarchy (merge below lod_tau / 2 px, reload above
-    lod_tau px, analysed by Session.analyze); renders and trains use each
-    view's cut of its active set.  tile: 16x16, 32x8 or 8x32."""
+    lod_tau px, analysed by Session.analyze); renders draw its render cut
+    (descent from the roots), trains each view's cut of the active set.
+    tile: 16x16, 32x8 or 8x32."""
     raster = _lib.GsRasterCfg(int(tile[0]), int(tile[1]), (C.c_float * 3)(*bg), float(znear), 1)
     return _lib.GsSessionConfig(int(max_gaussians), int(sh_degree), int(max_batch_views), int(max_width),
                                 int(max_height), int(max_inflight), int(hbm_budget_gb * (1 << 30)),

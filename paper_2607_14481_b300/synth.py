@@ -279,6 +279,24 @@ def frustum_gaussians(cam: Camera, n: int, seed: int, sh_degree: int = 3, depth=
     return Scene(means, log_scales, quats, opa, sh)
 
 
+def frustum_clusters(cam: Camera, n: int, seed: int, per_cluster: int = 4, sh_degree: int = 3,
+                     depth=(1.0, 8.0)) -> Scene:
+    """n Gaussians in groups of per_cluster that overlap one another, as
+    neighbouring Gaussians on a reconstructed surface do: the group centres
+    and every Gaussian's size, rotation, opacity and colour as
+    frustum_gaussians; members offset from their centre by N(0, s^2) per axis,
+    s = exp(the member's mean log-scale)."""
+    k = n // per_cluster
+    base = frustum_gaussians(cam, k, seed, sh_degree, depth)
+    g = _rng(seed + 104729)
+    members = frustum_gaussians(cam, k * per_cluster, seed + 1, sh_degree, depth)
+    centres = np.repeat(base.means, per_cluster, axis=0)
+    ls = np.repeat(base.log_scales, per_cluster, axis=0) + g.normal(0, 0.1, (k * per_cluster, 3)).astype(np.float32)
+    s = np.exp(ls.mean(axis=1))[:, None]
+    means = (centres + g.normal(0, 1.0, (k * per_cluster, 3)) * s).astype(np.float32)
+    return Scene(means, ls.astype(np.float32), members.quats, members.opa_logits, members.sh)
+
+
 def stream_frame(k: int, n_frames: int, seed: int):
     """Frame k of the stream: (camera at 1080p, U{10k..50k} new Gaussians in
     its frustum, requests [(kind, width, height)] with U{1..8} requests, each

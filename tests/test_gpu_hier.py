@@ -208,3 +208,51 @@ def test_no_merge_below_the_trigger_and_capacity_guard(cuda_device):
     assert s3["info"][1] == 1 and s3["info"][7] & 1 and s3["n_nodes"] == sc.n
     st3, _ = _gpu_state(arena3, h3)
     assert _is_cut(st3)
+
+
+def test_render_cut_from_the_roots_matches_oracle(cuda_device):
+    """gs_project_hier_render: the nodes the projection keeps are the oracle's
+    render cut (Sec. 6.2, descent from the roots while coarser than tau) up to
+    the projection's own culling and decisions within rounding of tau; the
+    image equals the oracle's render of the cut, and far views draw merged
+    nodes whatever the active set holds."""
+    sc, arena, hier = _setup(seed=5)
+    hier.analyze(_cam(0.0))
+    hier.analyze(_cam(-12.0))
+    hier.refine(_cam(8.0))  # the active set back to fine nodes near that camera
+    st, s = _gpu_state(arena, hier)
+    assert st.n_nodes > sc.n
+    merged_drawn = 0
+    dev = torch.device("cuda:0")
+    for cam, tau in ((_cam(6.0), 1.0), (_cam(0.0), 1.0), (_cam(-25.0), 1.0), (_cam(-25.0), 4.0)):
+        want, amb = oracle.hier_render_cut(st, cam, tau=tau)
+        r = raster.Rasterizer(st.n_nodes, sc.sh_degree, [cam], device=dev)
+        r.project_hier(hier, raster.poses_tensor([cam], dev), tau_h=tau, from_roots=True)
+        got = (r.splat_arrays()["touched"][0] > 0).astype(np.uint8)
+        ok = amb == 0
+        assert np.all(got[ok] <= want[ok])
+        missing = np.flatnonzero(ok & (want == 1) & (got == 0))
+        if len(missing):
+            proj = oracle.render(synth.Scene(st.means32[missing], st.log_scales[missing].astype(np.float32),
+                                             st.quats[missing].astype(np.float32),
+                                             st.opa_logits[missing].astype(np.float32),
+                                             st.sh[missing].astype(np.float32)), [cam], want_proj=True,
+                                 windows=[(0, 0, 8, 8)])["proj"][0]
+            vis_col = oracle.PROJ_FIELDS.index("vis")
+            amb_col = oracle.PROJ_FIELDS.index("bin_amb")
+            assert np.all((proj[:, vis_col] == 0) | (proj[:, amb_col] == 1))
+        merged_drawn += int(got[sc.n:].sum())
+        if amb.any():
+            continue
+        ref_img = oracle.render(synth.Scene(st.means32[:st.n_nodes][want == 1],
+                                            st.log_scales[:st.n_nodes][want == 1].astype(np.float32),
+                                            st.quats[:st.n_nodes][want == 1].astype(np.float32),
+                                            st.opa_logits[:st.n_nodes][want == 1].astype(np.float32),
+                                            st.sh[:st.n_nodes][want == 1].astype(np.float32)), [cam])
+        r.bin_sort()
+        img = r.new_image()
+        r.render_fwd(img, None)
+        g_img = r.split(img.cpu(), 3)[0].numpy().astype(np.float64)
+        okp = (ref_img["flags"][0] & 1) == 0
+        assert np.abs(g_img - ref_img["image"][0])[:, okp].max(initial=0.0) <= IMG_TOL
+    assert merged_drawn > 0

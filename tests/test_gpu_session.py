@@ -207,8 +207,8 @@ def test_progressive_hierarchy_in_the_session(cuda_device):
     analysis from a keyframe's camera (merge below tau / 2, then reload above
     tau) gives the node rows, links, active flags and merged parameters of
     the direct gs_hier_analyze + gs_hier_refine, and renders through the
-    view cut equal the direct gs_project_hier path while blending fewer
-    splats.  A training request then updates merged nodes of the cut and
+    render cut (descent from the roots) equal the direct
+    gs_project_hier_render path while blending fewer splats.  A training request then updates merged nodes of the cut and
     leaves the merged-away leaves alone; keyframe counts cover the active
     nodes (merged nodes take their children's keyframe)."""
     ensure_built()
@@ -251,7 +251,7 @@ def test_progressive_hierarchy_in_the_session(cuda_device):
     assert np.array_equal(h["quat"], buf[8 * cap:12 * cap].reshape(cap, 4)[:rows])
     assert np.array_equal(h["sh"], buf[12 * cap:12 * cap + 12 * cap].reshape(12, cap)[:, :rows])
     r = raster.Rasterizer(rows, 1, [far], device=dev)
-    r.project_hier(hier, raster.poses_tensor([far], dev), tau_h=1.0)
+    r.project_hier(hier, raster.poses_tensor([far], dev), tau_h=1.0, from_roots=True)
     r.bin_sort()
     img = r.new_image()
     r.render_fwd(img, None)
