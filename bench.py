@@ -854,9 +854,10 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
     """The streaming session loop: the scene grows from n0 to n_max Gaussians
     while frames arrive in real time at rate_hz; every frame adds its new
     Gaussians (U{10k..50k}, in the frame camera's frustum) and submits
-    U{1..8} render / train requests at 540p-1080p as one group; a
-    three-level hierarchy serves the render requests (tau = 1 px); admission
-    by an 80 GB HBM budget.  Frame-update latency = a train request's
+    U{1..8} render / train requests at 540p-1080p as one group; every 10th
+    frame is a keyframe whose camera analyses the progressive hierarchy
+    (renders draw its render cut, trains the active set's cut; tau = 1 px);
+    admission by an 80 GB HBM budget.  Frame-update latency = a train request's
     arrival (its frame's arrival) to the completion of the Adam step that
     used it."""
     import time
@@ -870,6 +871,7 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
                for wh in synth.STREAM_RESOLUTIONS}
     frames = [synth.stream_frame(k, n_frames, seed) for k in range(n_frames)]
     ids = []
+    analyses = 0
     with session.Session(cfg) as s:
         s.add(synth.frustum_gaussians(synth.stream_camera(0, n_frames), n0, seed + 1))
         n = n0
@@ -881,6 +883,8 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
             if n + new.n <= n_max + 60_000:
                 s.add(new)
                 n += new.n
+            if k % 10 == 9:  # a keyframe: analyse the hierarchy (skipped while the last one runs)
+                analyses += int(s.analyze(cam))
             s.hold(True)
             for i, (kind, w, h) in enumerate(reqs):
                 c = synth.with_resolution(cam, w, h)
@@ -905,12 +909,14 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
             "frame_update_p50_ms": pct(lat[1], 50), "frame_update_p99_ms": pct(lat[1], 99),
             "render_p50_ms": pct(lat[0], 50), "render_p99_ms": pct(lat[0], 99),
             "iterations": int(st["iterations"]), "iters_per_s": st["iterations"] / wall, "wall_s": wall,
-            "batches": int(st["batches"]), "retries": int(st["retries"]), "lod_builds": int(st["lod_builds"]),
+            "batches": int(st["batches"]), "retries": int(st["retries"]), "analyses_issued": analyses,
+            "analyses_swapped_in": int(st["lod_builds"]),
             "hbm_in_use_gb": st["hbm_in_use"] / 2 ** 30, "hbm_budget_gb": st["hbm_budget"] / 2 ** 30,
             "contexts": int(st["contexts"]),
             "workload": "camera on a 200 m loop, frames at 30 Hz, U{10k..50k} new Gaussians per frame in the "
                         "frame camera's frustum, U{1..8} requests per frame (render/train p = 0.5, 540p-1080p), "
-                        "3-level LoD (8-child moment merge, tau = 1 px) for renders, 80 GB HBM budget"}
+                        "progressive hierarchy analysed every 10th frame (renders: render cut, trains: the active "
+                        "set's cut, tau = 1 px), 80 GB HBM budget"}
 
 
 def launches_per_step(views, num_tiles, tile_order=False, fused=True, fused_adam=None):

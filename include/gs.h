@@ -397,7 +397,8 @@ GS_API gs_status gs_project_lod(const gs_params* nodes, int64_t n_leaf, const in
  * lies within the image widened by its screen size.
  * --------------------------------------------------------------------------- */
 typedef struct {
-  int32_t* parent;    /* [capacity] parent node, -1 = root */
+  int32_t* parent;    /* [capacity] parent node, -1 = root; -2 marks a row that holds no node yet
+                         (an unused slot below n_nodes: never drawn, never merged) */
   int32_t* child;     /* [capacity][4] child nodes, -1 = none */
   uint8_t* active;    /* [capacity] 1 = in the active set */
   uint32_t* n_nodes;  /* device word: arena rows in use (new nodes are appended) */

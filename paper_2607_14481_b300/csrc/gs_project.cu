@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
                                        a.scale_opa[k], in);
       return S > a.tau;
     };
-    bool sel = i < (int64_t)*a.h_n && !descends(i);
+    bool sel = i < (int64_t)*a.h_n && a.h_parent[i] >= -1 && !descends(i);
     int32_t p = sel ? a.h_parent[i] : -1;
     for (int d = 0; p >= 0; ++d) {
       if (d >= 64 || !descends(p)) {

@@ -920,7 +920,11 @@ gs_status gs_session_create(const gs_session_config* cfg, gs_session** out) {
     if ((st = gs::dalloc(S->h_info, 32, S->in_use)) != GS_OK) return cleanup(st);
     if ((st = gs::dalloc(S->h_pose, 48, S->in_use)) != GS_OK) return cleanup(st);
     if ((st = gs::dalloc(S->h_ws, gs::hier_workspace_bytes(S->capacity), S->in_use)) != GS_OK) return cleanup(st);
-    if ((st = gs::launch_fill_i32(static_cast<int32_t*>(S->h_parent.p), -1, S->capacity, S->stream)) != GS_OK ||
+    // leaf slots hold no node until Gaussians are added to them (-2)
+    if ((st = gs::launch_fill_i32(static_cast<int32_t*>(S->h_parent.p), -2, cfg->max_gaussians, S->stream)) !=
+            GS_OK ||
+        (st = gs::launch_fill_i32(static_cast<int32_t*>(S->h_parent.p) + cfg->max_gaussians, -1,
+                                  S->capacity - cfg->max_gaussians, S->stream)) != GS_OK ||
         (st = gs::launch_fill_i32(static_cast<int32_t*>(S->h_child.p), -1, 4 * S->capacity, S->stream)) != GS_OK)
       return cleanup(st);
     // the leaf slots count as node rows (inactive until added); merged nodes follow
@@ -1023,8 +1027,11 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
   }
   gs_status st = gs::launch_fill_i32(static_cast<int32_t*>(S->kf_of.p) + n0, S->keyframe, k, s);
   if (st != GS_OK) return st;
-  if (S->cfg.lod)  // new leaves: active in both buffers (the pending analysis did not see them)
+  if (S->cfg.lod) {  // new leaves: roots, active in both buffers (the pending analysis did not see them)
+    st = gs::launch_fill_i32(static_cast<int32_t*>(S->h_parent.p) + n0, -1, k, s);
+    if (st != GS_OK) return st;
     for (auto& a : S->h_active) cudaMemsetAsync(static_cast<uint8_t*>(a.p) + n0, 1, (size_t)k, s);
+  }
   cudaEventRecord(S->add_done, s);
   gs::mark_write(S);
   st = gs::check_launch("session add");

@@ -418,3 +418,22 @@ def test_session_with_other_tile_shapes(cuda_device, tile):
     ref = oracle.render(sc, cams[:1], tile=tile)
     ok = (ref["flags"][0] & 1) == 0
     assert np.abs(img.astype(np.float64) - ref["image"][0])[:, ok].max() <= IMG_TOL
+
+
+def test_hierarchy_session_never_draws_unused_slots(cuda_device):
+    """With a hierarchy, leaf slots not yet filled (rows past the added
+    Gaussians) hold no node: renders and trains skip them, so a render equals
+    the direct render of the Gaussians added (a zeroed slot would be a unit
+    Gaussian at the origin, in front of this camera)."""
+    ensure_built()
+    sc = _clustered_scene(500, 4, seed=9)
+    cam = synth.Camera(np.eye(3, dtype=np.float32), np.array([0.0, 0.0, 5.0], np.float32), 300.0, 300.0, 160.0,
+                       120.0, 320, 240)  # the world origin 5 m ahead
+    cfg = _cfg(sc.n + 1000, sh_degree=1, lod=True, lod_tau=1.0, max_width=320, max_height=240)
+    with session.Session(cfg) as s:
+        s.add(sc)
+        img = s.wait(s.submit(RENDER, cam, want_image=True))
+        s.wait(s.submit(TRAIN, cam, target=_targets([cam], seed=2)[0]))
+        st = s.stats()
+    assert st["failed"] == 0 and st["iterations"] == 1
+    assert np.array_equal(img, _direct_render(sc, cam))
