@@ -793,12 +793,13 @@ GS_API gs_status gs_session_add_gaussians(gs_session* s, int64_t count, const fl
 /* Gaussians added after this call are tagged with keyframe kf (< 0: none;
  * the default): the keyframe whose correction moves them at a loop closure. */
 GS_API gs_status gs_session_set_keyframe(gs_session* s, int32_t kf);
-/* Loop closure (Sec. 5.5): every active Gaussian tagged with keyframe k <
- * num_kf moves with the correction sim3[k] = (qw, qx, qy, qz, tx, ty, tz, s)
- * (host [num_kf][8], s > 0) as gs_sim3_update does; untagged Gaussians and
- * tags >= num_kf stay.  Enqueued on the session stream after the batches
- * already issued (it never waits for them), before any later one; the
- * hierarchy is rebuilt before the next render. */
+/* Loop closure (Sec. 5.5): every Gaussian tagged with keyframe k < num_kf
+ * moves with the correction sim3[k] = (qw, qx, qy, qz, tx, ty, tz, s) (host
+ * [num_kf][8], s > 0) as gs_sim3_update does; untagged Gaussians and tags >=
+ * num_kf stay.  With a hierarchy every node moves, merged nodes with the
+ * keyframe most common among their children (Sec. 6.1).  Enqueued on the
+ * session stream after the batches already issued (it never waits for them),
+ * before any later one. */
 GS_API gs_status gs_session_loop_closure(gs_session* s, int32_t num_kf, const float* sim3);
 /* Keyframe sampling weights (Sec. 6.2): keyframe k < num_kf is drawn for
  * optimisation with probability proportional to the active leaf Gaussians it

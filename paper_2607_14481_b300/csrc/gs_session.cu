@@ -1096,8 +1096,9 @@ gs_status gs_session_keyframe_weights(gs_session* S, int32_t num_kf, int32_t min
     gs_status st = gs::dalloc(counts, sizeof(uint32_t) * (size_t)num_kf, S->in_use);
     if (st != GS_OK) return st;
     // after everything enqueued so far (adds, closures), on the session stream
-    st = gs::launch_keyframe_counts(static_cast<const int32_t*>(S->kf_of.p), S->cfg.lod ? S->h_rows : S->n_active,
-                                    num_kf,
+    // the leaf Gaussians (rows [0, n_active)) each keyframe generated that
+    // are still in the active set (all of them without a hierarchy)
+    st = gs::launch_keyframe_counts(static_cast<const int32_t*>(S->kf_of.p), S->n_active, num_kf,
                                     static_cast<uint32_t*>(counts.p), S->stream,
                                     S->cfg.lod ? static_cast<const uint8_t*>(S->h_active[S->front].p) : nullptr);
     if (st == GS_OK &&
