@@ -504,6 +504,20 @@ def run_batched(n, device, cams16, K, warmup, ws, rank):
            "roofline": roofline(wb, sb, wkb, load_peaks(), sm_count(device))}
     del wb
     torch.cuda.empty_cache()
+    # the same 16 views trained one per Adam step (the plain mode on this view
+    # mix): what batching them into one step buys
+    wp = Workload(n, device, cams16, batched=False, rank=rank)
+    for _ in range(max(3, warmup)):
+        wp.step()
+    torch.cuda.synchronize()
+    Kp = 16 * max(2, Kb // 2)
+    ep = timed_loop(wp, Kp, ws)
+    wp.check_device_status()
+    out["plain_same_views"] = {"view_iters_per_s": ws * Kp / ep, "ms_per_view_iter": 1e3 * ep / Kp, "steps": Kp,
+                               "blend_schedule": wp.tuning}
+    out["vs_plain_same_views"] = out["view_iters_per_s"] / out["plain_same_views"]["view_iters_per_s"]
+    del wp
+    torch.cuda.empty_cache()
     return out
 
 

@@ -551,6 +551,49 @@ __device__ __forceinline__ void splat_grad_front(const Eval& e, const float4 col
   alpha_grad(e, gc * T - R * rom, d);
 }
 
+// One pixel's step of the single-pass backward without branches: the splat
+// test (as splat_alpha), the stop test, and the gradient contribution with
+// alpha, exp(power) and the weight masked to zero when the pixel does not
+// blend the splat, so that a contribution is exactly zero then and the
+// transmittance and g . rem stay.  ACC = false writes the contribution into
+// d (the first pixel), true adds it (the second), so the partials need no
+// zeroing per splat.  Returns whether the pixel blended the splat; *done is
+// set when it stops there.
+template <bool ACC>
+__device__ __forceinline__ bool pixel_step_front(const XTerms& x, const float4 g, const float4 g2, float ly,
+                                                 const float4 col, float g0, float g1, float g2c, float& T,
+                                                 float& R, bool& done, float (&d)[kPartialValues]) {
+  const float dx = x.dx, dy = __fsub_rn(g.y, ly);
+  const float p = __fmaf_rn(dy, __fmaf_rn(g2.x, dy, x.b2dx), x.a2dx2);
+  const bool hit = !done && fabsf(dx) <= g2.w && fabsf(dy) <= g2.w && p <= 0.f && p >= g2.y;
+  const float ex0 = ex2_approx(fminf(p, 0.f));
+  const float raw0 = __fmul_rn(g2.z, ex0);
+  const float alpha0 = fminf(kAlphaMax, raw0);
+  const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha0));
+  const bool stop = hit && Tn < kTransMin;
+  const bool blend = hit && !stop;
+  done = done || stop;
+  const float alpha = blend ? alpha0 : 0.f, ex = blend ? ex0 : 0.f;
+  const float w = alpha * T;
+  const float gc = g0 * col.x + g1 * col.y + g2c * col.z;
+  R -= gc * w;
+  const float rom = __fdividef(1.f, 1.f - alpha);
+  const float dal = gc * T - R * rom;
+  // no opacity / power gradient while alpha is clamped at its maximum
+  const float dex = raw0 <= kAlphaMax ? dal * ex : 0.f;
+  const float dp = raw0 <= kAlphaMax ? dal * alpha : 0.f;
+  const float xp = dx * dp, yp = dy * dp;
+  if (ACC) {
+    d[0] += xp; d[1] += yp; d[2] += dx * xp; d[3] += dy * xp; d[4] += dy * yp;
+    d[5] += dex; d[6] += g0 * w; d[7] += g1 * w; d[8] += g2c * w;
+  } else {
+    d[0] = xp; d[1] = yp; d[2] = dx * xp; d[3] = dy * xp; d[4] = dy * yp;
+    d[5] = dex; d[6] = g0 * w; d[7] = g1 * w; d[8] = g2c * w;
+  }
+  T = blend ? Tn : T;
+  return blend;
+}
+
 template <int TW>
 __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const ViewTable vt) {
   constexpr int kBatch = kThreads;
@@ -734,32 +777,10 @@ __device__ __forceinline__ void bwd_front_tile(const BwdArgs& a, const TileCoord
       }
       const int k = q * 32 + __ffs(bits) - 1;
       float d[kPartialValues];
-#pragma unroll
-      for (int c = 0; c < kPartialValues; ++c) d[c] = 0.f;
-      bool contrib = false;
-      const float4 g = sm.geo[k], g2 = sm.geo2[k];
+      const float4 g = sm.geo[k], g2 = sm.geo2[k], col = sm.rgb[k];
       const XTerms x = splat_x(g, tc.lx);
-      Eval e;
-      if (!d0 && splat_alpha(x, g, g2, tc.ly0, e)) {
-        const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
-        if (Tn < kTransMin) {
-          d0 = true;
-        } else {
-          splat_grad_front(e, sm.rgb[k], g00, g01, g02, T0, R0, d);
-          T0 = Tn;
-          contrib = true;
-        }
-      }
-      if (!d1 && splat_alpha(x, g, g2, tc.ly1, e)) {
-        const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
-        if (Tn < kTransMin) {
-          d1 = true;
-        } else {
-          splat_grad_front(e, sm.rgb[k], g10, g11, g12, T1, R1, d);
-          T1 = Tn;
-          contrib = true;
-        }
-      }
+      bool contrib = pixel_step_front<false>(x, g, g2, tc.ly0, col, g00, g01, g02, T0, R0, d0, d);
+      contrib |= pixel_step_front<true>(x, g, g2, tc.ly1, col, g10, g11, g12, T1, R1, d1, d);
       if (__any_sync(0xffffffffu, contrib)) {
         float s8, t8;
         int idx;
