@@ -246,6 +246,30 @@ struct CountState {
   int last = -1;                                       // last blended list position
 };
 
+// One pixel's composite step without branches: the splat test (as
+// splat_alpha), the stop test, and the blend with the weight masked to zero
+// when the pixel does not blend the splat (so its colour and transmittance
+// keep their exact values).  Returns whether it blended; *stopped is set
+// when the splat stops the pixel (and then done).
+__device__ __forceinline__ bool pixel_step_fwd(const XTerms& x, const float4 g, const float4 g2, float ly,
+                                               const float4 col, float& T, float& c0, float& c1, float& c2,
+                                               bool& done, bool& stopped) {
+  const float dy = __fsub_rn(g.y, ly);
+  const float p = __fmaf_rn(dy, __fmaf_rn(g2.x, dy, x.b2dx), x.a2dx2);
+  const bool hit = !done && fabsf(x.dx) <= g2.w && fabsf(dy) <= g2.w && p <= 0.f && p >= g2.y;
+  const float alpha = fminf(kAlphaMax, __fmul_rn(g2.z, ex2_approx(fminf(p, 0.f))));
+  const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+  stopped = hit && Tn < kTransMin;
+  const bool blend = hit && !stopped;
+  done = done || stopped;
+  const float w = blend ? alpha * T : 0.f;
+  c0 += col.x * w;
+  c1 += col.y * w;
+  c2 += col.z * w;
+  T = blend ? Tn : T;
+  return blend;
+}
+
 // Front-to-back composite of one tile's list for the thread's two pixels:
 // on return T0/T1 hold the final transmittance and c0/c1 the colour
 // composited (background not added).  Shared arrays: the staging slots of
@@ -273,40 +297,17 @@ __device__ __forceinline__ void composite_tile(const FwdArgs& a, const TileCoord
     for (int q = 0; q * 32 < cnt && !(d0 && d1); ++q) {
      for (uint32_t bits = s_wbw[q]; bits && !(d0 && d1); bits &= bits - 1) {
       const int k = q * 32 + __ffs(bits) - 1;
-      const float4 g = s_geo[k], g2 = s_geo2[k];
+      const float4 g = s_geo[k], g2 = s_geo2[k], col = s_rgb[k];
       const XTerms x = splat_x(g, tc.lx);
-      Eval e;
-      if (!d0) {
-        if (COUNT) ++cs.n_tested;
-        if (splat_alpha(x, g, g2, tc.ly0, e)) {
-          const float Tn = __fmul_rn(T0, __fsub_rn(1.f, e.alpha));
-          if (Tn < kTransMin) {
-            d0 = true;
-            if (COUNT) cs.stop0 = start + k;
-          } else {
-            const float4 col = s_rgb[k];
-            const float w = e.alpha * T0;
-            c00 += col.x * w; c01 += col.y * w; c02 += col.z * w;
-            T0 = Tn;
-            if (COUNT) { ++cs.n_blended; cs.last = max(cs.last, (int)(start + k)); }
-          }
-        }
-      }
-      if (!d1) {
-        if (COUNT) ++cs.n_tested;
-        if (splat_alpha(x, g, g2, tc.ly1, e)) {
-          const float Tn = __fmul_rn(T1, __fsub_rn(1.f, e.alpha));
-          if (Tn < kTransMin) {
-            d1 = true;
-            if (COUNT) cs.stop1 = start + k;
-          } else {
-            const float4 col = s_rgb[k];
-            const float w = e.alpha * T1;
-            c10 += col.x * w; c11 += col.y * w; c12 += col.z * w;
-            T1 = Tn;
-            if (COUNT) { ++cs.n_blended; cs.last = max(cs.last, (int)(start + k)); }
-          }
-        }
+      if (COUNT) cs.n_tested += (d0 ? 0u : 1u) + (d1 ? 0u : 1u);
+      bool st0, st1;
+      const bool b0 = pixel_step_fwd(x, g, g2, tc.ly0, col, T0, c00, c01, c02, d0, st0);
+      const bool b1 = pixel_step_fwd(x, g, g2, tc.ly1, col, T1, c10, c11, c12, d1, st1);
+      if (COUNT) {
+        if (st0) cs.stop0 = start + k;
+        if (st1) cs.stop1 = start + k;
+        cs.n_blended += (b0 ? 1u : 0u) + (b1 ? 1u : 0u);
+        if (b0 || b1) cs.last = max(cs.last, (int)(start + k));
       }
      }
     }
