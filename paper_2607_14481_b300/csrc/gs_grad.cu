@@ -443,8 +443,11 @@ __device__ __forceinline__ bool adam4(float4& p, const float4 g, float4& m, floa
 // view-direction term) are complete, every parameter of Gaussian i takes the
 // Adam step of gs_adam_step (same element update, same constants), so the SH
 // gradients never reach memory and the update needs no pass of its own.
-template <int DEG>
-__global__ void __launch_bounds__(kGradBlock) k_sh_bwd_adam(const GradArgs a, const ViewTable vt,
+// ONE (a single view): the SH gradient g_c Y_k is formed in the update from
+// the view's colour gradient and basis instead of 48 accumulators (0 + g_c Y_k,
+// the accumulated value's bits), which frees registers for occupancy.
+template <int DEG, bool ONE>
+__global__ void __launch_bounds__(kGradBlock, ONE ? 3 : 2) k_sh_bwd_adam(const GradArgs a, const ViewTable vt,
                                                             const AdamFamilies f) {
   constexpr int NC = (DEG + 1) * (DEG + 1);
   const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
@@ -452,11 +455,17 @@ __global__ void __launch_bounds__(kGradBlock) k_sh_bwd_adam(const GradArgs a, co
   const int64_t warp_id = i >> 5;
   const int64_t warps = (int64_t)gridDim.x * (kGradBlock / 32);
   const float4 mu = valid ? a.means4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float gsh[3][NC];
+  float gsh[ONE ? 1 : 3][ONE ? 1 : NC];
+  float Ys[ONE ? NC : 1], gcs[3] = {0.f, 0.f, 0.f};
+  if constexpr (ONE) {
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch)
+    for (int k = 0; k < NC; ++k) Ys[k] = 0.f;
+  } else {
 #pragma unroll
-    for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
+    for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
+  }
   float gmu[3] = {0.f, 0.f, 0.f};
   const uint32_t kpairs = a.counts[3];
   for (int v = 0; v < vt.views; ++v) {
@@ -483,9 +492,14 @@ __global__ void __launch_bounds__(kGradBlock) k_sh_bwd_adam(const GradArgs a, co
       for (int ch = 0; ch < 3; ++ch) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-          gsh[ch][k] += gc[ch] * Y[k];
+          if constexpr (!ONE) gsh[ch][k] += gc[ch] * Y[k];
           if (k > 0) dY[k] += gc[ch] * a.sh[(int64_t)(ch * NC + k) * a.sh_stride + i];
         }
+      }
+      if constexpr (ONE) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) Ys[k] = Y[k];
+        gcs[0] = gc[0]; gcs[1] = gc[1]; gcs[2] = gc[2];
       }
       if (DEG > 0) {
         float ddx, ddy, ddz;
@@ -550,7 +564,10 @@ __global__ void __launch_bounds__(kGradBlock) k_sh_bwd_adam(const GradArgs a, co
       for (int b = 0; b < B; ++b) {
         if (p0 + b >= NP) break;
         const int pl = p0 + b;
-        ok &= adam_elem(P[b], gsh[pl / NC][pl % NC], M[b], V[b], f.lr_sh[pl] * ss, f.b1, f.b2, f.eps, rs_bc2);
+        float gp;
+        if constexpr (ONE) gp = __fadd_rn(0.f, __fmul_rn(gcs[pl / NC], Ys[pl % NC]));
+        else gp = gsh[pl / NC][pl % NC];
+        ok &= adam_elem(P[b], gp, M[b], V[b], f.lr_sh[pl] * ss, f.b1, f.b2, f.eps, rs_bc2);
       }
 #pragma unroll
       for (int b = 0; b < B; ++b) {
@@ -752,19 +769,23 @@ gs_status launch_project_bwd_adam(const gs_params& p, const float* poses, const 
   switch (p.sh_degree) {
     case 0:
       k_project_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd_adam<0><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      if (vt.views == 1) k_sh_bwd_adam<0, true><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      else k_sh_bwd_adam<0, false><<<grid, kGradBlock, 0, s>>>(a, vt, f);
       break;
     case 1:
       k_project_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd_adam<1><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      if (vt.views == 1) k_sh_bwd_adam<1, true><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      else k_sh_bwd_adam<1, false><<<grid, kGradBlock, 0, s>>>(a, vt, f);
       break;
     case 2:
       k_project_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd_adam<2><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      if (vt.views == 1) k_sh_bwd_adam<2, true><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      else k_sh_bwd_adam<2, false><<<grid, kGradBlock, 0, s>>>(a, vt, f);
       break;
     default:
       k_project_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd_adam<3><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      if (vt.views == 1) k_sh_bwd_adam<3, true><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      else k_sh_bwd_adam<3, false><<<grid, kGradBlock, 0, s>>>(a, vt, f);
       break;
   }
   if (dpose) {
