@@ -447,7 +447,7 @@ __device__ __forceinline__ bool adam4(float4& p, const float4 g, float4& m, floa
 // the view's colour gradient and basis instead of 48 accumulators (0 + g_c Y_k,
 // the accumulated value's bits), which frees registers for occupancy.
 template <int DEG, bool ONE>
-__global__ void __launch_bounds__(kGradBlock, ONE ? 3 : 2) k_sh_bwd_adam(const GradArgs a, const ViewTable vt,
+__global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 2) k_sh_bwd_adam(const GradArgs a, const ViewTable vt,
                                                             const AdamFamilies f) {
   constexpr int NC = (DEG + 1) * (DEG + 1);
   const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
