@@ -279,7 +279,8 @@ class Workload:
         self.step_dev = torch.zeros(1, dtype=torch.int32, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.adam = raster.adam_params(3, lr_means=1.6e-4 * 10.0, step_dev=self.step_dev, status=self.status)
-        views = self.cams if batched else self.cams[:1]
+        # plain: one view per step, buffers sized for the largest view
+        views = self.cams if batched else [max(self.cams, key=lambda c: c.width * c.height)]
         self.rast = raster.Rasterizer(n, 3, views, device=device)
         self.loss = raster.ImageLoss(device)
         # targets: renders of a perturbed copy of the scene

@@ -270,6 +270,8 @@ class Rasterizer:
         self.max_tiles = max(self.tiles_for(t) for t in _lib.TILE_SHAPES)
         self.pixels = sum(c.width * c.height for c in cams)
         if hasattr(self, "ranges") and self.ranges.numel() >= 2 * self.max_tiles:
+            if hasattr(self, "ws_bwd") and self.max_tiles > self._ws_tiles:
+                self._alloc_pairs()  # the fused pass's per-tile terms for more tiles
             return
         self.ranges = torch.zeros(max(2, 2 * self.max_tiles), dtype=torch.int32, device=self.device)
         self.tile_order = torch.zeros(max(1, self.max_tiles), dtype=torch.int32, device=self.device)
@@ -299,8 +301,10 @@ class Rasterizer:
         cap = self.capacity
         self.ws_bin = torch.empty(self.L.gs_bin_sort_workspace(self.n, self.views, cap), dtype=torch.uint8,
                                   device=self.device)
-        # the fused pass's workspace: the backward's layout plus its counter and per-tile loss terms
-        self.ws_bwd = torch.empty(self.L.gs_render_fused_workspace(self.n, self.views, cap, self.max_tiles),
+        # the fused pass's workspace: the backward's layout plus its counter and
+        # per-tile loss terms, for the most tiles any camera set so far had
+        self._ws_tiles = max(self.max_tiles, getattr(self, "_ws_tiles", 0))
+        self.ws_bwd = torch.empty(self.L.gs_render_fused_workspace(self.n, self.views, cap, self._ws_tiles),
                                   dtype=torch.uint8, device=self.device)
 
     def bins_struct(self, with_order: Optional[bool] = None):
