@@ -55,7 +55,9 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
   const float R[9] = {P[0], P[1], P[2], P[4], P[5], P[6], P[8], P[9], P[10]};
   const float tc[3] = {P[3], P[7], P[11]};
 
-  const float4 mu = a.means4[i];
+  // the rotation and scale are loaded with the mean, so that the thread
+  // waits for one memory round trip before the covariance, not two
+  const float4 mu = a.means4[i], q = a.quat[i], so = a.scale_opa[i];
   // camera-space centre in double-single
   const df tz = df_dot3_add(R[6], mu.x, R[7], mu.y, R[8], mu.z, tc[2]);
   bool vis = !df_le(tz, a.znear);
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
   if (vis && a.parent) {
     // level-of-detail cut: rendered iff (a leaf or S < tau) and every
     // ancestor has S >= tau
-    bool sel = i < a.n_leaf || screen_size(tz.hi, a.scale_opa[i], vi.fx, a.znear) < a.tau;
+    bool sel = i < a.n_leaf || screen_size(tz.hi, so, vi.fx, a.znear) < a.tau;
     int32_t p = a.parent[i];
     for (int d = 0; d < 8 && sel && p >= 0 && p < a.n; ++d) {
       const float4 mp = a.means4[p];
@@ -140,11 +142,9 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
     mfy = (my.hi - miy) + my.lo;
     if (mfy < 0.f) { miy -= 1.f; mfy += 1.f; } else if (mfy >= 1.f) { miy += 1.f; mfy -= 1.f; }
 
-    const float4 q = a.quat[i];
     const float qi = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     float Rq[9];
     quat_rot(q.x * qi, q.y * qi, q.z * qi, q.w * qi, Rq);
-    const float4 so = a.scale_opa[i];
     const float s[3] = {expf(so.x), expf(so.y), expf(so.z)};
 
     // perspective Jacobian with the frustum guard
