@@ -257,7 +257,8 @@ __device__ __forceinline__ bool pixel_step_fwd(const XTerms& x, const float4 g, 
   const float dy = __fsub_rn(g.y, ly);
   const float p = __fmaf_rn(dy, __fmaf_rn(g2.x, dy, x.b2dx), x.a2dx2);
   const bool hit = !done && fabsf(x.dx) <= g2.w && fabsf(dy) <= g2.w && p <= 0.f && p >= g2.y;
-  const float alpha = fminf(kAlphaMax, __fmul_rn(g2.z, ex2_approx(fminf(p, 0.f))));
+  // a power above zero fails the test; its exponential (up to +inf) is masked
+  const float alpha = fminf(kAlphaMax, __fmul_rn(g2.z, ex2_approx(p)));
   const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
   stopped = hit && Tn < kTransMin;
   const bool blend = hit && !stopped;
@@ -567,22 +568,26 @@ __device__ __forceinline__ bool pixel_step_front(const XTerms& x, const float4 g
   const float dx = x.dx, dy = __fsub_rn(g.y, ly);
   const float p = __fmaf_rn(dy, __fmaf_rn(g2.x, dy, x.b2dx), x.a2dx2);
   const bool hit = !done && fabsf(dx) <= g2.w && fabsf(dy) <= g2.w && p <= 0.f && p >= g2.y;
-  const float ex0 = ex2_approx(fminf(p, 0.f));
+  // a power above zero fails the test; its exponential (up to +inf) is masked
+  const float ex0 = ex2_approx(p);
   const float raw0 = __fmul_rn(g2.z, ex0);
   const float alpha0 = fminf(kAlphaMax, raw0);
   const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha0));
   const bool stop = hit && Tn < kTransMin;
   const bool blend = hit && !stop;
   done = done || stop;
-  const float alpha = blend ? alpha0 : 0.f, ex = blend ? ex0 : 0.f;
+  const float alpha = blend ? alpha0 : 0.f;
+  // no opacity / power gradient while alpha is clamped at its maximum;
+  // unclamped, d alpha / d power = alpha = opacity * exp(power), the same
+  // product as raw0
+  const float exg = blend && raw0 <= kAlphaMax ? ex0 : 0.f;
   const float w = alpha * T;
   const float gc = g0 * col.x + g1 * col.y + g2c * col.z;
   R -= gc * w;
   const float rom = __fdividef(1.f, 1.f - alpha);
   const float dal = gc * T - R * rom;
-  // no opacity / power gradient while alpha is clamped at its maximum
-  const float dex = raw0 <= kAlphaMax ? dal * ex : 0.f;
-  const float dp = raw0 <= kAlphaMax ? dal * alpha : 0.f;
+  const float dex = dal * exg;
+  const float dp = dal * __fmul_rn(g2.z, exg);
   const float xp = dx * dp, yp = dy * dp;
   if (ACC) {
     d[0] += xp; d[1] += yp; d[2] += dx * xp; d[3] += dy * xp; d[4] += dy * yp;
