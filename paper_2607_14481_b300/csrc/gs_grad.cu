@@ -69,6 +69,23 @@ __device__ __forceinline__ bool pair_range_ok(const GradArgs& a, int64_t o, uint
   return tch > 0;
 }
 
+// The views (bit v) in which Gaussian i has rendered pairs (as
+// pair_range_ok), with every view's count and offset loaded before any
+// view's work: a per-view loop then waits for memory only in the views that
+// see the Gaussian (a few of a batch's views), not twice per view.
+__device__ __forceinline__ uint64_t visible_views(const GradArgs& a, int64_t i, bool valid, int views,
+                                                  uint32_t kpairs) {
+  uint64_t m = 0;
+  if (!valid) return m;
+#pragma unroll 8
+  for (int v = 0; v < views; ++v) {
+    const int64_t o = (int64_t)v * a.n + i;
+    const uint32_t tch = a.touched[o], off = a.pair_off[o];
+    if (tch > 0 && (uint64_t)off + tch <= kpairs) m |= 1ull << v;
+  }
+  return m;
+}
+
 // Sum of each visible (view, Gaussian)'s per-tile partials, in a fixed
 // order.  A (view, Gaussian) with at most kWideSegment pairs is summed by its
 // own thread in list order, four pairs per step so that their twelve loads
@@ -186,12 +203,11 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
   for (int k = 0; k < 9; ++k) gRq[k] = 0.f;
   float gsc[3] = {0.f, 0.f, 0.f};
 
-  const uint32_t kpairs = a.counts[3];
+  const uint64_t vmask = visible_views(a, i, valid, vt.views, a.counts[3]);
   for (int v = 0; v < vt.views; ++v) {
     float pv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int64_t o = (int64_t)v * a.n + i;
-    uint32_t tch = 0;
-    if (valid && pair_range_ok(a, o, kpairs, tch)) {
+    if ((vmask >> v) & 1ull) {
       const ViewInfo vi = vt.v[v];
       const uint32_t auxb = a.aux[o];
       // ---- this (view, Gaussian)'s summed pixel-space gradients
@@ -353,12 +369,11 @@ __global__ void __launch_bounds__(kGradBlock) k_sh_bwd(const GradArgs a, const V
 #pragma unroll
     for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
   float gmu[3] = {0.f, 0.f, 0.f};
-  const uint32_t kpairs = a.counts[3];
+  const uint64_t vmask = visible_views(a, i, valid, vt.views, a.counts[3]);
   for (int v = 0; v < vt.views; ++v) {
     float pv[3] = {0.f, 0.f, 0.f};
     const int64_t o = (int64_t)v * a.n + i;
-    uint32_t tch = 0;
-    if (valid && pair_range_ok(a, o, kpairs, tch)) {
+    if ((vmask >> v) & 1ull) {
       const float4 g = a.drgb[o];
       const uint32_t auxb = a.aux[o];
       const float* P = a.poses + 12 * v;
@@ -467,12 +482,11 @@ __global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 2) k_sh_bwd_adam(const G
       for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
   }
   float gmu[3] = {0.f, 0.f, 0.f};
-  const uint32_t kpairs = a.counts[3];
+  const uint64_t vmask = visible_views(a, i, valid, vt.views, a.counts[3]);
   for (int v = 0; v < vt.views; ++v) {
     float pv[3] = {0.f, 0.f, 0.f};
     const int64_t o = (int64_t)v * a.n + i;
-    uint32_t tch = 0;
-    if (valid && pair_range_ok(a, o, kpairs, tch)) {
+    if ((vmask >> v) & 1ull) {
       const float4 g = a.drgb[o];
       const uint32_t auxb = a.aux[o];
       const float* P = a.poses + 12 * v;
