@@ -69,6 +69,12 @@ __device__ __forceinline__ bool pair_range_ok(const GradArgs& a, int64_t o, uint
   return tch > 0;
 }
 
+// Hint that the line holding p will be read soon by this SM (no register,
+// no wait; p must point into an allocation).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 // The views (bit v) in which Gaussian i has rendered pairs (as
 // pair_range_ok), with every view's count and offset loaded before any
 // view's work: a per-view loop then waits for memory only in the views that
@@ -204,6 +210,16 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
   float gsc[3] = {0.f, 0.f, 0.f};
 
   const uint64_t vmask = visible_views(a, i, valid, vt.views, a.counts[3]);
+  // the summed gradients of the views that see the Gaussian, fetched into L1
+  // while the first views are worked on
+  if (vt.views > 1) {
+    for (uint64_t mm = vmask; mm; mm &= mm - 1) {
+      const int64_t o = (int64_t)(__ffsll((long long)mm) - 1) * a.n + i;
+      prefetch_l1(a.gsum + o);
+      prefetch_l1(a.gsum + (int64_t)vt.views * a.n + o);
+      prefetch_l1(a.aux + o);
+    }
+  }
   for (int v = 0; v < vt.views; ++v) {
     float pv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int64_t o = (int64_t)v * a.n + i;
@@ -483,6 +499,20 @@ __global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 2) k_sh_bwd_adam(const G
   }
   float gmu[3] = {0.f, 0.f, 0.f};
   const uint64_t vmask = visible_views(a, i, valid, vt.views, a.counts[3]);
+  if constexpr (!ONE) {
+    // the colour gradients of the views that see the Gaussian and its SH
+    // planes, fetched into L1 ahead of the view loop
+    for (uint64_t mm = vmask; mm; mm &= mm - 1) {
+      const int64_t o = (int64_t)(__ffsll((long long)mm) - 1) * a.n + i;
+      prefetch_l1(a.drgb + o);
+      prefetch_l1(a.aux + o);
+    }
+    if (vmask) {
+#pragma unroll
+      for (int pl = 1; pl < 3 * NC; ++pl)
+        if (pl % NC) prefetch_l1(a.sh + (int64_t)pl * a.sh_stride + i);
+    }
+  }
   for (int v = 0; v < vt.views; ++v) {
     float pv[3] = {0.f, 0.f, 0.f};
     const int64_t o = (int64_t)v * a.n + i;
