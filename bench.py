@@ -938,7 +938,7 @@ def launches_per_step(views, num_tiles, tile_order=False, fused=True, fused_adam
     """Kernels one training step launches (memsets excluded): projection 1;
     binning 6 (counts, pair-offset scan with the count pass, tile scan with
     the length grouping and any longest-first order, keys, keys of the wide
-    splats, tile sort; more than 2^18 tiles take a three-kernel device scan
+    splats, tile sort; more than 2^13 tiles take a three-kernel device scan
     and two ordering kernels instead of the one-CTA tile scan); the fused
     composite + loss + per-pixel backward 1 (or, unfused, composite 1, loss
     2, per-pixel backward 1); per-Gaussian backward 5 (pair sums,
@@ -947,7 +947,7 @@ def launches_per_step(views, num_tiles, tile_order=False, fused=True, fused_adam
     (fused_adam, by default with the fused pass)."""
     if fused_adam is None:
         fused_adam = fused
-    tile_scan = 1 if num_tiles <= (1 << 18) else 3 + 2
+    tile_scan = 1 if num_tiles <= (1 << 13) else 3 + 2
     bin_sort = 1 + 1 + tile_scan + 1 + 1 + 1
     blend = 1 if fused else 1 + 2 + 1
     return 1 + bin_sort + blend + 5 + (2 if fused_adam else 3)
