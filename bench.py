@@ -935,11 +935,12 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
 
 
 def launches_per_step(views, num_tiles, tile_order=False, fused=True, fused_adam=None):
-    """Kernels one training step launches (memsets excluded): projection 1;
-    binning 6 (counts, pair-offset scan with the count pass, tile scan with
-    the length grouping and any longest-first order, keys, keys of the wide
-    splats, tile sort; more than 2^13 tiles take a three-kernel device scan
-    and two ordering kernels instead of the one-CTA tile scan); the fused
+    """Kernels one training step launches: projection 1; binning 5 (zeroing
+    of counters and ranges, pair-offset scan with the count pass, tile scan
+    with the length grouping and any longest-first order, keys (the wide
+    splats' chunks in the same launch), tile sort; more than 2^13 tiles take
+    a three-kernel device scan and two ordering kernels instead of the
+    one-CTA tile scan); the fused
     composite + loss + per-pixel backward 1 (or, unfused, composite 1, loss
     2, per-pixel backward 1); per-Gaussian backward 5 (pair sums,
     projection, SH, pose chunks and total); Adam 3 (parameters, poses, step
@@ -948,7 +949,7 @@ def launches_per_step(views, num_tiles, tile_order=False, fused=True, fused_adam
     if fused_adam is None:
         fused_adam = fused
     tile_scan = 1 if num_tiles <= (1 << 13) else 3 + 2
-    bin_sort = 1 + 1 + tile_scan + 1 + 1 + 1
+    bin_sort = 1 + 1 + tile_scan + 1 + 1
     blend = 1 if fused else 1 + 2 + 1
     return 1 + bin_sort + blend + 5 + (2 if fused_adam else 3)
 

@@ -262,13 +262,23 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
 // read from an earlier stage was out of range (the access was skipped).
 constexpr uint32_t kStatusCapacity = 1u, kStatusIndex = 2u;
 
-__global__ void k_init_counts(uint32_t* counts, uint32_t* scalars, uint32_t m, uint32_t tiles) {
-  for (int i = threadIdx.x; i < 128; i += blockDim.x) scalars[i] = 0;
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  scalars[0] = m;      // live length of the item scan
-  scalars[1] = tiles;  // live length of the tile scan
-  counts[0] = 0; counts[1] = 0; counts[2] = 0; counts[3] = 0;
+// Zeroes what a binning accumulates into, in one launch: the scalars and
+// counters (block 0), the tiles' range words and the look-back words of the
+// item scan (grid-stride).
+__global__ void k_init_bins(uint32_t* counts, uint32_t* scalars, uint32_t m, uint32_t tiles, uint32_t* ranges,
+                            int64_t range_words, unsigned long long* state, int64_t parts) {
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) scalars[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      scalars[0] = m;      // live length of the item scan
+      scalars[1] = tiles;  // live length of the tile scan
+      counts[0] = 0; counts[1] = 0; counts[2] = 0; counts[3] = 0;
+    }
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < range_words; i += stride) ranges[i] = 0u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < parts; i += stride) state[i] = 0ull;
 }
 
 // Items with at least kWide pairs (splats covering many tiles) are keyed in
@@ -397,29 +407,13 @@ __device__ __forceinline__ uint32_t warp_pairs(const PairArgs& a, const ViewTabl
   return vis;
 }
 
-// The key pass: one warp per 32 items, offsets from pair_off.
-__global__ void __launch_bounds__(256) k_keys(const PairArgs a, const ViewTable vt) {
-  const int64_t m = a.n * vt.views;
-  const int64_t j0 = ((int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
-  if (j0 >= m) return;  // warp-uniform
-  const int64_t j = j0 + (threadIdx.x & 31);
-  // every load of the item at once (not waiting for its count)
-  const bool in = j < m;
-  const uint32_t tch = in ? a.touched[j] : 0u;
-  const uint32_t off = in ? a.pair_off[j] : 0u;
-  const uint2 rc = in ? a.rect[j] : make_uint2(0u, 0u);
-  const float dep = in ? a.depth[j] : 0.f;
-  warp_pairs<true>(a, vt, j0, off, tch, rc, dep);
-}
-
-// The wide items' key pass: warps take chunks of kWideChunk pairs (grid
-// stride); the lanes of a round take 32 consecutive pairs of the chunk, with
+// The wide items' keys: warps w, w + warps, ... take chunks of kWideChunk
+// pairs; the lanes of a round take 32 consecutive pairs of the chunk, with
 // the cursor atomics of the chunk's rounds issued together.
-__global__ void __launch_bounds__(256) k_keys_wide(const PairArgs a, const ViewTable vt) {
+__device__ __forceinline__ void keys_wide(const PairArgs& a, const ViewTable& vt, uint32_t w, uint32_t warps) {
   const int lane = threadIdx.x & 31;
   const uint32_t nchunks = min((uint32_t)(*a.wide_count >> 32), a.wide_cap);
-  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-  for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+  for (uint32_t c = w; c < nchunks; c += warps) {
     const uint2 wc = a.wide_chunks[c];
     const int64_t j = wc.x;
     const uint32_t tch = a.touched[j], off = a.pair_off[j];
@@ -431,8 +425,8 @@ __global__ void __launch_bounds__(256) k_keys_wide(const PairArgs a, const ViewT
       if (lane == 0) atomicOr(&a.counts[2], kStatusIndex);
       continue;
     }
-    const uint32_t w = (uint32_t)(x1 - x0 + 1);
-    const uint32_t cnt = min(w * (uint32_t)(y1 - y0 + 1), tch);
+    const uint32_t wd = (uint32_t)(x1 - x0 + 1);
+    const uint32_t cnt = min(wd * (uint32_t)(y1 - y0 + 1), tch);
     const uint32_t tb = (uint32_t)vt.v[v].tile_base, tx_n = (uint32_t)vt.v[v].TX;
     const uint64_t key = ((uint64_t)__float_as_uint(dep) << 32) | (uint32_t)(j - (int64_t)v * a.n);
     constexpr int kR = kWideChunk / 32;
@@ -442,7 +436,7 @@ __global__ void __launch_bounds__(256) k_keys_wide(const PairArgs a, const ViewT
       pos[rr] = 0xffffffffu;
       const uint32_t t = wc.y + 32 * rr + lane;
       if (t >= cnt || (int64_t)off + t >= a.cap) continue;
-      const uint32_t tile = tb + ((uint32_t)y0 + t / w) * tx_n + (uint32_t)x0 + t % w;
+      const uint32_t tile = tb + ((uint32_t)y0 + t / wd) * tx_n + (uint32_t)x0 + t % wd;
       pos[rr] = take_place(a, tile);
     }
 #pragma unroll
@@ -455,6 +449,28 @@ __global__ void __launch_bounds__(256) k_keys_wide(const PairArgs a, const ViewT
       }
     }
   }
+}
+
+// The key pass: blocks below item_blocks take 32 items per warp (offsets
+// from pair_off); the blocks after them key the wide items' chunks, so that
+// one launch covers both and the chunks fill the item blocks' tail.
+__global__ void __launch_bounds__(256) k_keys(const PairArgs a, const ViewTable vt, uint32_t item_blocks) {
+  if (blockIdx.x >= item_blocks) {
+    const uint32_t wb = blockIdx.x - item_blocks, nwb = gridDim.x - item_blocks;
+    keys_wide(a, vt, wb * (blockDim.x >> 5) + (threadIdx.x >> 5), nwb * (blockDim.x >> 5));
+    return;
+  }
+  const int64_t m = a.n * vt.views;
+  const int64_t j0 = ((int64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  if (j0 >= m) return;  // warp-uniform
+  const int64_t j = j0 + (threadIdx.x & 31);
+  // every load of the item at once (not waiting for its count)
+  const bool in = j < m;
+  const uint32_t tch = in ? a.touched[j] : 0u;
+  const uint32_t off = in ? a.pair_off[j] : 0u;
+  const uint2 rc = in ? a.rect[j] : make_uint2(0u, 0u);
+  const float dep = in ? a.depth[j] : 0.f;
+  warp_pairs<true>(a, vt, j0, off, tch, rc, dep);
 }
 
 // ---------------------------------------------------------------------------
@@ -1149,10 +1165,13 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   BinWs w = bin_layout(static_cast<char*>(ws), m, cap);
   uint32_t* counts = bins.counts;
   const uint32_t tiles = (uint32_t)vt.total_tiles;
-  k_init_counts<<<1, 128, 0, s>>>(counts, w.scalars, (uint32_t)m, tiles);
-  // the ranges array counts each tile's pairs, then holds (start, cursor)
-  if (cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)bins.num_tiles, s) != cudaSuccess)
-    return check_launch("memset ranges");
+  // counters, scalars, the ranges (each tile's pair count, then (start,
+  // cursor)) and the scan's look-back words, zeroed by one launch
+  const int64_t parts = m > 0 ? scan_parts(m) : 0;
+  const int64_t range_words = 2 * (int64_t)bins.num_tiles;
+  const unsigned igrid =
+      (unsigned)std::min<int64_t>(592, std::max<int64_t>(1, (std::max(range_words, parts) + 255) / 256));
+  k_init_bins<<<igrid, 256, 0, s>>>(counts, w.scalars, (uint32_t)m, tiles, bins.ranges, range_words, w.state, parts);
   // the wide items' chunk table borrows keys_b (the sort's ping-pong buffer,
   // not used before the key passes end): cap entries, more than the
   // cap / 64 chunks that pairs within the capacity can need
@@ -1163,9 +1182,6 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   // 1. + 2. pair slots per (view, Gaussian) (single-pass scan of the tile
   // counts) and every pair counted in its tile, in one launch
   if (m > 0) {
-    const int64_t parts = scan_parts(m);
-    if (cudaMemsetAsync(w.state, 0, sizeof(unsigned long long) * (size_t)parts, s) != cudaSuccess)
-      return check_launch("memset scan state");
     ScanCountArgs sa{pa, w.state, w.scalars + 3, (uint32_t)parts};
     k_scan_count<<<(unsigned)parts, kThreads, 0, s>>>(sa, vt);
   }
@@ -1185,8 +1201,8 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   if (m == 0 || cap == 0) return check_launch("bin_sort");
   // 4. every key at its place in its tile's list
   const unsigned pgrid = (unsigned)std::max<int64_t>(1, (m + 255) / 256);  // 8 warps of 32 items per block
-  k_keys<<<pgrid, 256, 0, s>>>(pa, vt);
-  k_keys_wide<<<(unsigned)std::min<int64_t>(1184, pgrid), 256, 0, s>>>(pa, vt);
+  const unsigned wgrid = (unsigned)std::min<int64_t>(1184, pgrid);         // the wide items' chunks
+  k_keys<<<pgrid + wgrid, 256, 0, s>>>(pa, vt, pgrid);
   // 5. every tile's list by (depth bits, id)
   int id_bits = 1;
   while (id_bits < 32 && (1ll << id_bits) < sp.n) ++id_bits;

@@ -108,17 +108,17 @@ def test_both_arms_report_the_same_config():
 
 
 def test_library_kernels_per_training_step():
-    # projection 1, binning 6, fused composite + loss + per-pixel backward 1,
+    # projection 1, binning 5, fused composite + loss + per-pixel backward 1,
     # per-Gaussian backward 5 with the parameters' Adam inside, pose Adam and
     # step counter 2; a longest-first order costs no launch; unfused:
     # composite 1, loss 2, per-pixel backward 1 and a separate parameter Adam;
     # beyond 2^13 tiles the tile scan takes 5 launches instead of 1
-    assert bench.launches_per_step(1, 3600) == 15
-    assert bench.launches_per_step(1, 3600, tile_order=True) == 15
-    assert bench.launches_per_step(1, 3600, fused=False) == 19
-    assert bench.launches_per_step(1, 3600, fused_adam=False) == 16
-    assert bench.launches_per_step(64, 1 << 19) == 19
-    assert bench.launches_per_step(16, 80_000) == 19 and bench.launches_per_step(1, 8192) == 15
+    assert bench.launches_per_step(1, 3600) == 14
+    assert bench.launches_per_step(1, 3600, tile_order=True) == 14
+    assert bench.launches_per_step(1, 3600, fused=False) == 18
+    assert bench.launches_per_step(1, 3600, fused_adam=False) == 15
+    assert bench.launches_per_step(64, 1 << 19) == 18
+    assert bench.launches_per_step(16, 80_000) == 18 and bench.launches_per_step(1, 8192) == 14
 
 
 def test_roofline_of_the_fused_step():
