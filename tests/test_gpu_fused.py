@@ -211,7 +211,7 @@ def test_full_size_batched_2m_16_views_fused_every_tile_shape(cuda_device):
         torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("deg,nviews", [(0, 1), (1, 2), (2, 1), (3, 3)])
+@pytest.mark.parametrize("deg,nviews", [(0, 1), (1, 2), (2, 1), (3, 3), (3, 40)])
 def test_adam_fused_into_the_gaussian_backward_equals_separate_step(cuda_device, deg, nviews):
     """gs_render_bwd_gaussians_adam (the Adam update applied by the SH kernel)
     leaves parameters and moments bit-identical to gs_render_bwd_gaussians +
@@ -221,8 +221,13 @@ def test_adam_fused_into_the_gaussian_backward_equals_separate_step(cuda_device,
     from paper_2607_14481_b300 import train
     dev = torch.device("cuda:0")
     sc = synth.random_scene(4000, 31 + deg, deg, (-1, -1, -1), (1, 1, 1), -3.2, 0.4)
-    eyes = [(0.0, 0.0, -3.0), (0.5, -0.2, -2.7), (-0.4, 0.3, -3.2)][:nviews]
-    sizes = [(96, 64), (80, 88), (70, 50)][:nviews]
+    if nviews <= 3:
+        eyes = [(0.0, 0.0, -3.0), (0.5, -0.2, -2.7), (-0.4, 0.3, -3.2)][:nviews]
+        sizes = [(96, 64), (80, 88), (70, 50)][:nviews]
+    else:  # a circle of small views: more than 32 views per launch
+        eyes = [(3.0 * np.sin(2 * np.pi * k / nviews), 0.2, -3.0 * np.cos(2 * np.pi * k / nviews))
+                for k in range(nviews)]
+        sizes = [(40 + 8 * (k % 3), 32) for k in range(nviews)]
     cams = [synth.look_at(e, (0, 0, 0), 80.0, 80.0, w / 2, h / 2, w, h) for e, (w, h) in zip(eyes, sizes)]
     lrs = dict(lr_means=1e-2, lr_scale=5e-3, lr_opacity=5e-2, lr_quat=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4)
     runs = []

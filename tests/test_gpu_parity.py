@@ -276,6 +276,28 @@ def test_gradients_diffcheck_mse_with_alpha_and_background(cuda_device):
     compare_grads(g_gpu, g_ref)
 
 
+def test_gradients_forty_views_in_one_launch(cuda_device):
+    """40 views of the diffcheck scene on a full circle in one launch (more
+    than 32, so the per-Gaussian backward's bit set of the views that see a
+    Gaussian uses both of its words; views from behind see the scene's other
+    side): gradients, the 40 pose gradients included, against the oracle."""
+    sc, _, _ = synth.diffcheck()
+    cams = []
+    for k in range(40):
+        a = 2.0 * np.pi * k / 40
+        eye = (2.5 * np.sin(a), 0.4 * np.sin(3.0 * a), -2.5 * np.cos(a))
+        cams.append(synth.look_at(eye, (0, 0, 0), 40.0, 40.0, 16.0, 12.0, 32, 24))
+    g = np.random.default_rng(11)
+    targets = [g.random((3, 24, 32)).astype(np.float32) for _ in cams]
+    ref = oracle.render(sc, cams)
+    _, dimg = oracle.l1_loss(ref["image"], targets)
+    dimg = _masked(dimg, ref["flags"])
+    r, arena, poses, img, alpha = gpu_forward(sc, cams)
+    g_gpu = gpu_backward(r, arena, poses, dimg, image=img)
+    g_ref = oracle.backward(sc, cams, dimg)
+    compare_grads(g_gpu, g_ref)
+
+
 @pytest.mark.parametrize("single_pass", [False, True])
 def test_backward_deterministic(cuda_device, single_pass):
     sc, cams, targets = synth.diffcheck()
