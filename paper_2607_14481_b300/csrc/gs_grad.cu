@@ -209,6 +209,13 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
   for (int k = 0; k < 9; ++k) gRq[k] = 0.f;
   float gsc[3] = {0.f, 0.f, 0.f};
 
+  if (vt.views == 1 && valid) {
+    // one view: its summed gradients requested with the pair count, not
+    // after it
+    prefetch_l1(a.gsum + i);
+    prefetch_l1(a.gsum + a.n + i);
+    prefetch_l1(a.aux + i);
+  }
   const uint64_t vmask = visible_views(a, i, valid, vt.views, a.counts[3]);
   // the summed gradients of the views that see the Gaussian, fetched into L1
   // while the first views are worked on
