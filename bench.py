@@ -882,7 +882,10 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
     cfg = session.default_config(n_max + 60_000, sh_degree=3, max_batch_views=8, max_width=1920, max_height=1080,
                                  max_inflight=2, hbm_budget_gb=80.0, pair_factor=8.0, lod=True, lod_tau=1.0)
     g = np.random.default_rng(seed)
-    targets = {wh: [g.random((3, wh[1], wh[0]), dtype=np.float32) for _ in range(2)]
+    # train targets in pinned host memory, as frames a capture pipeline has
+    # written there: the session reads them in place (borrowed), no copy at submit
+    import torch
+    targets = {wh: [torch.from_numpy(g.random((3, wh[1], wh[0]), dtype=np.float32)).pin_memory() for _ in range(2)]
                for wh in synth.STREAM_RESOLUTIONS}
     frames = [synth.stream_frame(k, n_frames, seed) for k in range(n_frames)]
     ids = []
@@ -904,7 +907,7 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
             for i, (kind, w, h) in enumerate(reqs):
                 c = synth.with_resolution(cam, w, h)
                 tgt = targets[(w, h)][(k + i) % 2] if kind == 1 else None
-                ids.append((kind, s.submit(kind, c, target=tgt, arrival=t_arr)))
+                ids.append((kind, s.submit(kind, c, target=tgt, arrival=t_arr, borrow_target=tgt is not None)))
             s.hold(False)
         s.drain(timeout_ms=600_000)
         st = s.stats()
@@ -929,7 +932,8 @@ def run_streaming(n_max, seed=SEED_STREAM, rate_hz=30.0, n0=100_000):
             "hbm_in_use_gb": st["hbm_in_use"] / 2 ** 30, "hbm_budget_gb": st["hbm_budget"] / 2 ** 30,
             "contexts": int(st["contexts"]),
             "workload": "camera on a 200 m loop, frames at 30 Hz, U{10k..50k} new Gaussians per frame in the "
-                        "frame camera's frustum, U{1..8} requests per frame (render/train p = 0.5, 540p-1080p), "
+                        "frame camera's frustum, U{1..8} requests per frame (render/train p = 0.5, 540p-1080p; train "
+                        "targets in pinned host memory, borrowed by the session), "
                         "progressive hierarchy analysed every 10th frame (renders: render cut, trains: the active "
                         "set's cut, tau = 1 px), 80 GB HBM budget"}
 

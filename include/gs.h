@@ -724,6 +724,13 @@ typedef struct gs_session gs_session;
 
 #define GS_REQUEST_RENDER 0
 #define GS_REQUEST_TRAIN 1
+/* gs_request.flags: the train target is page-locked host memory (cudaHostAlloc
+   or cudaHostRegister) that the caller leaves allocated and unchanged until
+   the request has completed (gs_session_wait, or gs_session_times returning
+   GS_OK); the session copies it to the device from there instead of taking a
+   copy during submit (a camera frame already written to pinned memory is not
+   copied twice) */
+#define GS_REQUEST_BORROW_TARGET 1
 
 typedef struct {
   int64_t max_gaussians;     /* device capacity (fixed for the session) */
@@ -747,9 +754,10 @@ typedef struct {
   int32_t kind;              /* GS_REQUEST_RENDER or GS_REQUEST_TRAIN */
   gs_camera cam;             /* within the session's maximum resolution */
   float pose[12];            /* world->camera [R | t], row-major 3x4 */
-  const float* target;       /* train: host [3][H][W], copied during submit */
+  const float* target;       /* train: host [3][H][W], copied during submit (unless borrowed, flags) */
   float* image_out;          /* render: host [3][H][W], filled before the request completes (may be NULL) */
   double arrival_s;          /* arrival time on gs_session_now()'s clock; 0 = submit time */
+  int32_t flags;             /* 0 or GS_REQUEST_BORROW_TARGET */
 } gs_request;
 
 typedef struct {

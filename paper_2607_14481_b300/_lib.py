@@ -119,9 +119,12 @@ class GsSessionConfig(C.Structure):
                 ("lod", C.c_int32), ("lod_tau", C.c_float)]
 
 
+GS_REQUEST_BORROW_TARGET = 1
+
+
 class GsRequest(C.Structure):
     _fields_ = [("kind", C.c_int32), ("cam", GsCamera), ("pose", C.c_float * 12), ("target", C.c_void_p),
-                ("image_out", C.c_void_p), ("arrival_s", C.c_double)]
+                ("image_out", C.c_void_p), ("arrival_s", C.c_double), ("flags", C.c_int32)]
 
 
 class GsStats(C.Structure):

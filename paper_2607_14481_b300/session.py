@@ -50,12 +50,14 @@ class Session:
         _lib.check(self.L.gs_session_create(C.byref(cfg), C.byref(h)), "gs_session_create")
         self.h = h
         self._keep = {}  # host buffers referenced by queued requests
+        self._borrowed = {}  # pinned targets the session reads until their requests complete
 
     def close(self):
         if self.h:
             _lib.check(self.L.gs_session_destroy(self.h), "gs_session_destroy")
             self.h = None
             self._keep.clear()
+            self._borrowed.clear()
 
     def __enter__(self):
         return self
@@ -73,14 +75,27 @@ class Session:
         ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs]
         _lib.check(self.L.gs_session_add_gaussians(self.h, sc.n, *ptrs), "gs_session_add_gaussians")
 
-    def submit(self, kind: int, cam: Camera, target: Optional[np.ndarray] = None, want_image: bool = False,
-               arrival: float = 0.0) -> int:
+    def submit(self, kind: int, cam: Camera, target=None, want_image: bool = False,
+               arrival: float = 0.0, borrow_target: bool = False) -> int:
+        """target: [3][H][W] float32, copied during the call; with
+        borrow_target a pinned CPU torch tensor that the session reads until
+        the request completes (GS_REQUEST_BORROW_TARGET; this object keeps a
+        reference until wait() or times() has seen it complete)."""
         req = _lib.GsRequest()
         req.kind = kind
         req.cam = _lib.GsCamera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
         req.pose = (C.c_float * 12)(*np.asarray(cam.pose12(), np.float32).tolist())
         tgt = None
-        if target is not None:
+        if target is not None and borrow_target:
+            import torch
+            if not (isinstance(target, torch.Tensor) and target.device.type == "cpu" and target.is_pinned()
+                    and target.dtype == torch.float32 and target.is_contiguous()
+                    and tuple(target.shape) == (3, cam.height, cam.width)):
+                raise ValueError("a borrowed target is a contiguous pinned float32 CPU tensor [3][H][W]")
+            tgt = target
+            req.target = target.data_ptr()
+            req.flags = _lib.GS_REQUEST_BORROW_TARGET
+        elif target is not None:
             tgt = np.ascontiguousarray(target, np.float32)
             req.target = tgt.ctypes.data
         img = None
@@ -91,10 +106,13 @@ class Session:
         rid = C.c_int64()
         _lib.check(self.L.gs_session_submit(self.h, C.byref(req), C.byref(rid)), "gs_session_submit")
         self._keep[rid.value] = img
+        if borrow_target and tgt is not None:
+            self._borrowed[rid.value] = tgt
         return rid.value
 
     def wait(self, rid: int, timeout_ms: int = 60000) -> Optional[np.ndarray]:
         _lib.check(self.L.gs_session_wait(self.h, rid, timeout_ms), "gs_session_wait")
+        self._borrowed.pop(rid, None)
         return self._keep.pop(rid, None)
 
     def times(self, rid: int) -> Optional[tuple]:
@@ -103,6 +121,7 @@ class Session:
         st = self.L.gs_session_times(self.h, rid, C.byref(a), C.byref(d))
         if st == _lib.GS_ERR_BUSY:
             return None
+        self._borrowed.pop(rid, None)
         _lib.check(st, "gs_session_times")
         return a.value, d.value
 

@@ -9,6 +9,7 @@
   * save / load resumes bit-identically;
   * a batch that overflows its pair capacity grows it and runs again.
 """
+import ctypes as C
 import os
 
 import numpy as np
@@ -136,6 +137,45 @@ def test_train_alone_equals_with_renders_mixed_and_direct(cuda_device):
     assert np.array_equal(results[0]["scale_opa"], nat[4 * n:8 * n].reshape(n, 4))
     assert np.array_equal(results[0]["quat"], nat[8 * n:12 * n].reshape(n, 4))
     assert np.array_equal(results[0]["sh"], nat[12 * n:12 * n + 48 * n].reshape(48, n))
+
+
+def test_borrowed_pinned_targets_train_like_copied_ones(cuda_device):
+    """GS_REQUEST_BORROW_TARGET: train requests whose targets stay in the
+    caller's pinned memory (several in flight at once, two sharing one
+    buffer) leave the parameters bit-identical to the same requests with
+    targets copied during submit; a pageable array is refused as a borrowed
+    target and unknown flags are rejected by the library."""
+    ensure_built()
+    sc = _scene(n=12000, seed=12)
+    cams = _cams(5, seed=13)
+    targets = _targets(cams, seed=5)
+    pinned = [torch.from_numpy(np.ascontiguousarray(t, np.float32)).pin_memory() for t in targets]
+    results = []
+    for borrow in (False, True):
+        with session.Session(_cfg(sc.n)) as s:
+            s.add(sc)
+            s.hold(True)
+            ids = [s.submit(TRAIN, c, target=(p if borrow else t), borrow_target=borrow)
+                   for c, t, p in zip(cams, targets, pinned)]
+            ids.append(s.submit(TRAIN, cams[0], target=(pinned[0] if borrow else targets[0]), borrow_target=borrow))
+            s.hold(False)
+            for rid in ids:
+                s.wait(rid)
+            assert s.stats()["failed"] == 0
+            results.append(s.params())
+    for k in results[0]:
+        assert np.array_equal(results[0][k], results[1][k]), k
+    with session.Session(_cfg(sc.n)) as s:
+        s.add(sc)
+        with pytest.raises(ValueError):
+            s.submit(TRAIN, cams[0], target=targets[0], borrow_target=True)
+        req = _lib.GsRequest()
+        req.kind = TRAIN
+        req.cam = _lib.GsCamera(cams[0].fx, cams[0].fy, cams[0].cx, cams[0].cy, cams[0].width, cams[0].height)
+        req.target = pinned[0].data_ptr()
+        req.flags = 2
+        rid = C.c_int64()
+        assert s.L.gs_session_submit(s.h, C.byref(req), C.byref(rid)) == _lib.GS_ERR_INVALID
 
 
 def test_save_load_resumes_bit_identically(cuda_device, tmp_path):
