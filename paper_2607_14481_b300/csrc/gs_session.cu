@@ -1042,7 +1042,7 @@ gs_status gs_session_add_gaussians(gs_session* S, int64_t count, const float* me
   // Gaussian by Gaussian (the source read in order; a plane-by-plane sweep
   // re-read it once per plane, 3x slower at 50k Gaussians), in ranges of
   // Gaussians on several threads
-  gs::host_parallel(k, 8192, [&](int64_t lo, int64_t hi) {
+  gs::host_parallel(k, 2048, [&](int64_t lo, int64_t hi) {
     for (int64_t i = lo; i < hi; ++i) {
       hm[4 * i] = means[3 * i]; hm[4 * i + 1] = means[3 * i + 1]; hm[4 * i + 2] = means[3 * i + 2];
       hm[4 * i + 3] = 0.f;
