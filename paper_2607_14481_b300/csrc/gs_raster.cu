@@ -1,16 +1,18 @@
-// Front-to-back alpha compositing per 16x16 tile and its backward (the
-// per-pixel stages of the splat renderer of §5.2).
+// Front-to-back alpha compositing per tile and its backward (the per-pixel
+// stages of the splat renderer of §5.2), for tiles of 16x16, 32x8 or 8x32
+// pixels.
 //
 // One CTA of 128 threads per (view, tile); each thread owns two vertically
-// adjacent pixels, so a warp covers 4 tile rows and every splat fetched from
-// shared memory serves two pixels.  Each batch of the tile's sorted splat list
-// is staged in shared memory by the CTA's threads with coalesced float4 loads,
-// together with a mask of the warps whose strip of 4 rows the splat can reach
-// at alpha >= 1/255 (the exponent's maximum over the strip, a conservative
-// test, so a warp never skips a splat the exact per-pixel test would accept).
-// Each warp turns its bits of the masks into a bit set with one ballot per 32
-// staged splats and visits only the set bits, in list order.  The CTA leaves
-// the list as soon as every pixel has saturated (__syncthreads_count).
+// adjacent pixels, so a warp covers a strip of 64 pixels (16x4, 32x2 or 8x8)
+// and every splat read from shared memory serves two pixels.  Each batch of
+// the tile's sorted splat list is staged in shared memory by the CTA's
+// threads with coalesced float4 loads, together with a mask of the warps
+// whose strip the splat can reach at alpha >= 1/255 (the exponent's maximum
+// over the strip, a conservative test, so a warp never skips a splat the
+// exact per-pixel test would accept).  Each warp turns its bits of the masks
+// into a bit set with one ballot per 32 staged splats and visits only the set
+// bits, in list order.  The CTA leaves the list as soon as every pixel has
+// saturated (__syncthreads_count).
 //
 // The backward accumulates per pixel only the moments of dL/dpower (dx dp,
 // dy dp, dx^2 dp, dx dy dp, dy^2 dp) for the splat's mean and conic; the conic
@@ -19,11 +21,12 @@
 //
 // Each staged splat carries its centre relative to the tile origin, its conic
 // scaled to base-2 exponent units and the exponent threshold below which its
-// alpha would fall under 1/255, so a pixel test is a few FMAs and two
-// compares, and the exponential is evaluated only for splats that pass.  The
-// test is written once (splat_x + splat_alpha) with explicit round-to-nearest
-// intrinsics so that the forward and every backward form take bit-identical
-// decisions.
+// alpha would fall under 1/255, so a pixel test is a few FMAs and compares.
+// A pixel's step over a visited splat has no branch: the test, the stop and
+// the contribution are computed and masked to zero where the pixel does not
+// blend.  The test is written once (splat_x with the pixel steps, and
+// splat_alpha for the replay form) with explicit round-to-nearest intrinsics,
+// so that the forward and every backward form take bit-identical decisions.
 #include <algorithm>
 #include <mutex>
 #include <type_traits>
