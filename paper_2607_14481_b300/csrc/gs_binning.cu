@@ -727,10 +727,23 @@ __global__ void __launch_bounds__(kThreads) k_order_place(uint32_t* __restrict__
   }
   __syncthreads();
   const uint32_t nonempty = s_base[kOrderBuckets - 1];
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
-    const uint32_t c = ranges[2 * (uint64_t)t + 1];
-    const int b = order_bucket(c);
-    const uint32_t pos = s_base[b] + atomicAdd(&cursor[b], 1u);
+  const int lane = threadIdx.x & 31;
+  // grid-stride rounds are uniform per warp (the stride is a multiple of 32),
+  // so the whole warp takes each round together: the lanes of one bucket
+  // take their places with one atomic (most rounds hold a few buckets)
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < tiles; t0 += stride) {
+    const uint32_t t = t0 + (uint32_t)lane;
+    const bool in = t < tiles;
+    const uint32_t c = in ? ranges[2 * (uint64_t)t + 1] : 0u;
+    const int b = in ? order_bucket(c) : kOrderBuckets;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t first = 0;
+    if (in && lane == leader) first = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    if (!in) continue;
+    const uint32_t pos = s_base[b] + first + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     if (order && pos < tiles) order[pos] = t;
     if (pos < nonempty) work[pos] = t;
     const uint32_t st = c ? ranges[2 * (uint64_t)t] : 0u;
