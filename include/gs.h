@@ -133,7 +133,8 @@ typedef struct {
  *   GS_SCHED_FUSED_LONGEST_FIRST: gs_render_fused hands out its (view, tile)
  *     items in gs_bins.tile_order (longest lists of all views first) instead
  *     of view-major order;
- *   GS_SCHED_FUSED_BATCH(b): splats per batch of gs_render_fused, 0: 128, 1: 64. */
+ *   GS_SCHED_FUSED_BATCH(b): splats per batch of gs_render_fused, 0: 128, 1: 64,
+ *     2: 32. */
 #define GS_SCHED_FWD_LONGEST_FIRST 0x1u
 #define GS_SCHED_BWD_LONGEST_FIRST 0x2u
 #define GS_SCHED_FUSED_LONGEST_FIRST 0x4u
@@ -641,7 +642,7 @@ GS_API gs_status gs_autotune_blend(const gs_splats* splats, const gs_bins* bins,
 /* Autotuner of the fused pass (the batched iteration's knobs: tile shape,
  * splats per shared-memory batch, work order).  For each tile shape (16x16,
  * 32x8, 8x32) the caller's Gaussians are projected and binned again; each
- * candidate shape x batch (128, 64) x order (view-major, longest lists first
+ * candidate shape x batch (128, 64, 32) x order (view-major, longest lists first
  * when bins->tile_order is given) is timed over `reps` runs of gs_project +
  * gs_bin_sort + gs_render_fused after one warm-up, with CUDA events.  A shape
  * whose lists exceed bins->capacity, whose tiles exceed ranges_tiles (the
@@ -649,8 +650,8 @@ GS_API gs_status gs_autotune_blend(const gs_splats* splats, const gs_bins* bins,
  * ws_bytes is skipped.  On return cfg holds the fastest tile shape and fused
  * schedule (other schedule bits unchanged), bins->num_tiles that shape's tile
  * count, and splats / bins / image / loss the results of that configuration.
- * times_ms (optional, host, 12 floats): mean time of each candidate in the
- * order shape (16x16, 32x8, 8x32) x batch (128, 64) x order (view-major,
+ * times_ms (optional, host, 18 floats): mean time of each candidate in the
+ * order shape (16x16, 32x8, 8x32) x batch (128, 64, 32) x order (view-major,
  * longest first); NaN where skipped.  bin_ws: the gs_bin_sort workspace; ws:
  * the gs_render_fused workspace.  Synchronises (bounded waits,
  * GS_ERR_TIMEOUT): not for use under stream capture.  The image does not

@@ -80,6 +80,7 @@ static gs_status check_cfg(const gs_raster_cfg* cfg) {
     return fail(GS_ERR_INVALID, "tile must be 16x16, 32x8 or 8x32 (got %dx%d)", cfg->tile_w, cfg->tile_h);
   if (!(cfg->znear > 0.f)) return fail(GS_ERR_INVALID, "znear must be > 0");
   if ((cfg->schedule & ~kSchedKnown) || ((cfg->schedule >> kSchedFwdBatchShift) & 3u) == 3u ||
+      ((cfg->schedule >> kSchedFusedBatchShift) & 3u) == 3u ||
       ((cfg->schedule >> kSchedBwdBatchShift) & 3u) > 1u)
     return fail(GS_ERR_INVALID, "unknown schedule 0x%x", cfg->schedule);
 

@@ -137,7 +137,7 @@ extern "C" gs_status gs_autotune_fused(const gs_params* params, const float* pos
     cudaEventDestroy(e0);
     return gs::check_launch("autotune event");
   }
-  const uint32_t fused_mask = GS_SCHED_FUSED_LONGEST_FIRST | GS_SCHED_FUSED_BATCH(1);
+  const uint32_t fused_mask = GS_SCHED_FUSED_LONGEST_FIRST | GS_SCHED_FUSED_BATCH(3);
   const uint32_t base = cfg->schedule & ~fused_mask;
   gs_raster_cfg best = *cfg;
   float t_best = INFINITY;
@@ -174,7 +174,7 @@ extern "C" gs_status gs_autotune_fused(const gs_params* params, const float* pos
       }
       ok = st == GS_OK && cnt[2] == 0;
     }
-    for (int bt = 0; bt < 2; ++bt)
+    for (int bt = 0; bt < 3; ++bt)
       for (int order = 0; order < 2; ++order, ++slot) {
         float ms = NAN;
         if (ok && st == GS_OK && (order == 0 || b.tile_order)) {

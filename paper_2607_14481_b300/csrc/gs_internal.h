@@ -34,7 +34,7 @@ constexpr uint32_t kSchedBwdLongestFirst = GS_SCHED_BWD_LONGEST_FIRST;
 constexpr int kSchedFwdBatchShift = 4;
 constexpr int kSchedBwdBatchShift = 8;
 constexpr int kSchedFusedBatchShift = 12;
-constexpr uint32_t kSchedKnown = 0x7u | (3u << 4) | (3u << 8) | (1u << 12);
+constexpr uint32_t kSchedKnown = 0x7u | (3u << 4) | (3u << 8) | (3u << 12);
 
 // Fills a ViewTable from host cameras for tiles of tw x th pixels; returns
 // false (with a message) on invalid cameras or an unsupported tile shape.

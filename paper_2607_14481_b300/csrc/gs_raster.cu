@@ -1127,7 +1127,7 @@ gs_status launch_render_fused(const gs_splats& sp, const gs_bins& bins, const Vi
     if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return check_launch("fused loss");
     return GS_OK;
   }
-  const bool b64 = ((cfg.schedule >> kSchedFusedBatchShift) & 1u) != 0;
+  const uint32_t bsel = (cfg.schedule >> kSchedFusedBatchShift) & 3u;  // 0: 128, 1: 64, 2: 32
   bool ok = true;
   with_tile_width(vt, [&](auto tw) {
     constexpr int TW = decltype(tw)::value;
@@ -1136,11 +1136,15 @@ gs_status launch_render_fused(const gs_splats& sp, const gs_bins& bins, const Vi
       if (g <= 0) { ok = false; return; }
       kernel<<<g, kThreads, 0, s>>>(a, vt);
     };
-    const size_t base = (TW == 8 ? 0 : TW == 16 ? 4 : 8);
+    const size_t base = (TW == 8 ? 0 : TW == 16 ? 6 : 12);
     if (loss_kind == 0) {
-      if (b64) go(k_render_fused<64, TW, 0>, base + 0); else go(k_render_fused<128, TW, 0>, base + 1);
+      if (bsel == 1) go(k_render_fused<64, TW, 0>, base + 0);
+      else if (bsel == 2) go(k_render_fused<32, TW, 0>, base + 1);
+      else go(k_render_fused<128, TW, 0>, base + 2);
     } else {
-      if (b64) go(k_render_fused<64, TW, 1>, base + 2); else go(k_render_fused<128, TW, 1>, base + 3);
+      if (bsel == 1) go(k_render_fused<64, TW, 1>, base + 3);
+      else if (bsel == 2) go(k_render_fused<32, TW, 1>, base + 4);
+      else go(k_render_fused<128, TW, 1>, base + 5);
     }
   });
   if (!ok) return fail(GS_ERR_CUDA, "k_render_fused: occupancy query failed");

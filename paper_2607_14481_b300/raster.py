@@ -413,7 +413,7 @@ class Rasterizer:
         the candidates' times and the choice."""
         ps = params.struct()
         b = self.bins_struct(with_order=True)
-        t = (C.c_float * 12)()
+        t = (C.c_float * 18)()
         _lib.check(self.L.gs_autotune_fused(C.byref(ps), _p(poses), self.cam_struct, self.views, C.byref(self.cfg),
                                             C.byref(self.splats), C.byref(b), self.max_tiles, _p(self.ws_bin),
                                             self.ws_bin.numel(), _p(target), int(loss_kind), _p(image), _p(loss),
@@ -421,7 +421,7 @@ class Rasterizer:
                    "gs_autotune_fused")
         self.tile = (int(self.cfg.tile_w), int(self.cfg.tile_h))
         self.num_tiles = self.tiles_for(self.tile)
-        names = [f"{tw}x{th}_b{bt}_{o}" for tw, th in _lib.TILE_SHAPES for bt in (128, 64)
+        names = [f"{tw}x{th}_b{bt}_{o}" for tw, th in _lib.TILE_SHAPES for bt in (128, 64, 32)
                  for o in ("viewmajor", "longest")]
         return {"tile": list(self.tile), "schedule": int(self.cfg.schedule),
                 "ms": {k: float(v) for k, v in zip(names, t)}}

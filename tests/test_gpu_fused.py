@@ -74,16 +74,16 @@ def test_fused_pass_matches_separate_kernels_and_oracle(cuda_device, tile, case,
 
 @pytest.mark.parametrize("tile", SHAPES)
 def test_fused_schedules_change_no_result(cuda_device, tile):
-    """Splats per batch (128, 64) and work order (view-major, longest lists
-    first) change no bit of the image, loss or gradients; repeated runs are
-    bit-identical."""
+    """Splats per batch (128, 64, 32) and work order (view-major, longest
+    lists first) change no bit of the image, loss or gradients; repeated runs
+    are bit-identical."""
     sc, cams, _ = synth.diffcheck()
     r, arena, poses, img, alpha = gpu_forward(sc, cams, tile=tile)
     ref = oracle.render(sc, cams, tile=tile)
     _, tgt = _target(r, img, ref, np.random.default_rng(5))
     base = None
     for order in (0, 1):
-        for b in (0, 1):
+        for b in (0, 1, 2):
             r.cfg.schedule = (_lib.GS_SCHED_FUSED_LONGEST_FIRST if order else 0) | _lib.GS_SCHED_FUSED_BATCH(b)
             r.bin_sort()  # the longest-first order is written by the binning
             for _ in range(2):
