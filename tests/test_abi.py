@@ -67,7 +67,7 @@ def test_unknown_schedule_rejected_on_host(lib):
     cam = (_lib.GsCamera * 1)(_lib.GsCamera(100.0, 100.0, 32.0, 32.0, 64, 64))
     sp = _lib.GsSplats(256, 256, 256, 256, 256, 256, 256, 10, 1)
     bins = _lib.GsBins(16, 16, 16, None, 16, 100, 16)
-    for sched in (3 << 4, 2 << 8, 2 << 12, 1 << 16):
+    for sched in (3 << 4, 2 << 8, 3 << 12, 1 << 16):
         cfg = _lib.GsRasterCfg(16, 16, (C.c_float * 3)(0, 0, 0), 0.2, 1, sched)
         st = lib.gs_render_fwd(C.byref(sp), C.byref(bins), cam, 1, C.byref(cfg), C.c_void_p(256), None, None)
         assert st == _lib.GS_ERR_INVALID and "schedule" in _lib.last_error()
