@@ -107,6 +107,7 @@ struct PoseArgs {
 // Pose step per view: Adam on xi (zero-based tangent), then the SE(3)
 // exponential (Rodrigues rotation, V-matrix translation) applied on the left.
 __global__ void k_pose_adam(const PoseArgs a) {
+  chain_enter();
   const int vw = blockIdx.x * blockDim.x + threadIdx.x;
   if (vw >= a.views || (a.skip_dev && *a.skip_dev)) return;
   float bc1 = a.bc1, bc2 = a.bc2;
@@ -172,6 +173,7 @@ __global__ void k_pose_adam(const PoseArgs a) {
 }
 
 __global__ void k_step_increment(int32_t* step, const uint32_t* skip) {
+  chain_enter();
   if (!(skip && *skip)) *step += 1;
 }
 
@@ -207,9 +209,9 @@ gs_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
     pa.step_dev = cfg.step_dev;
     pa.pose_steps = cfg.pose_steps_dev;
     pa.skip_dev = cfg.skip_dev;
-    k_pose_adam<<<(cfg.views + 63) / 64, 64, 0, s>>>(pa);
+    launch_dependent(k_pose_adam, (cfg.views + 63) / 64, 64, s, pa);
   }
-  if (cfg.step_dev) k_step_increment<<<1, 1, 0, s>>>(cfg.step_dev, cfg.skip_dev);
+  if (cfg.step_dev) launch_dependent(k_step_increment, 1, 1, s, cfg.step_dev, cfg.skip_dev);
   return check_launch("adam");
 }
 

@@ -267,6 +267,7 @@ constexpr uint32_t kStatusCapacity = 1u, kStatusIndex = 2u;
 // item scan (grid-stride).
 __global__ void k_init_bins(uint32_t* counts, uint32_t* scalars, uint32_t m, uint32_t tiles, uint32_t* ranges,
                             int64_t range_words, unsigned long long* state, int64_t parts) {
+  chain_enter();
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < 128; i += blockDim.x) scalars[i] = 0;
     __syncthreads();
@@ -455,6 +456,7 @@ __device__ __forceinline__ void keys_wide(const PairArgs& a, const ViewTable& vt
 // from pair_off); the blocks after them key the wide items' chunks, so that
 // one launch covers both and the chunks fill the item blocks' tail.
 __global__ void __launch_bounds__(256) k_keys(const PairArgs a, const ViewTable vt, uint32_t item_blocks) {
+  chain_enter();
   if (blockIdx.x >= item_blocks) {
     const uint32_t wb = blockIdx.x - item_blocks, nwb = gridDim.x - item_blocks;
     keys_wide(a, vt, wb * (blockDim.x >> 5) + (threadIdx.x >> 5), nwb * (blockDim.x >> 5));
@@ -503,6 +505,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 __global__ void __launch_bounds__(kThreads) k_scan_count(const ScanCountArgs a, const ViewTable vt) {
+  chain_enter();
   __shared__ uint32_t s_warp[kThreads / 32 + 1];
   __shared__ uint32_t s_part, s_prefix, s_vis;
   __shared__ uint32_t s_off[kItemsPerBlock], s_cnt[kItemsPerBlock];
@@ -640,6 +643,7 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(uint32_t* __rest
                                                                  uint32_t* __restrict__ bucket_count,
                                                                  uint32_t* __restrict__ work,
                                                                  uint32_t* __restrict__ order) {
+  chain_enter();
   constexpr int NW = kTileScanThreads / 32;
   __shared__ uint32_t s_warp[NW + 1];
   __shared__ uint32_t s_count[kOrderBuckets], s_base[kOrderBuckets];
@@ -1024,6 +1028,7 @@ constexpr uint32_t kBitonicMax = 4096;  // longest list sorted in shared memory
 // same list.  The CTA writes the ids (and optionally the full keys); the
 // ranges are already (start, end).
 __global__ void __launch_bounds__(kThreads, 4) k_tile_sort(const TileSortArgs a) {
+  chain_enter();
   __shared__ __align__(16) uint64_t s_keys[kBitonicMax];
   __shared__ uint32_t s_base[kRadixDigits];
   __shared__ uint32_t s_wh[kThreads / 32][kRadixDigits];
@@ -1184,7 +1189,8 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   const int64_t range_words = 2 * (int64_t)bins.num_tiles;
   const unsigned igrid =
       (unsigned)std::min<int64_t>(592, std::max<int64_t>(1, (std::max(range_words, parts) + 255) / 256));
-  k_init_bins<<<igrid, 256, 0, s>>>(counts, w.scalars, (uint32_t)m, tiles, bins.ranges, range_words, w.state, parts);
+  launch_dependent(k_init_bins, igrid, 256, s, counts, w.scalars, (uint32_t)m, tiles, bins.ranges, range_words,
+                   w.state, parts);
   // the wide items' chunk table borrows keys_b (the sort's ping-pong buffer,
   // not used before the key passes end): cap entries, more than the
   // cap / 64 chunks that pairs within the capacity can need
@@ -1196,12 +1202,13 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   // counts) and every pair counted in its tile, in one launch
   if (m > 0) {
     ScanCountArgs sa{pa, w.state, w.scalars + 3, (uint32_t)parts};
-    k_scan_count<<<(unsigned)parts, kThreads, 0, s>>>(sa, vt);
+    launch_dependent(k_scan_count, (unsigned)parts, kThreads, s, sa, vt);
   }
   if (tiles == 0) return check_launch("bin_sort");
   // 3. list starts, the key pass's cursors and the tiles grouped by length
   if (vt.total_tiles <= kTileScanMax) {
-    k_tile_scan<<<1, kTileScanThreads, 0, s>>>(bins.ranges, tiles, w.scalars + 32, w.work, bins.tile_order);
+    launch_dependent(k_tile_scan, 1, kTileScanThreads, s, bins.ranges, tiles, w.scalars + 32, w.work,
+                     bins.tile_order);
   } else {
     gs_status st = launch_scan(bins.ranges + 1, 2, bins.ranges, 2, w.scalars + 1, vt.total_tiles, w.scalars + 2,
                                w.scan, s);
@@ -1215,14 +1222,14 @@ gs_status launch_bin_sort(const gs_splats& sp, const ViewTable& vt, const gs_bin
   // 4. every key at its place in its tile's list
   const unsigned pgrid = (unsigned)std::max<int64_t>(1, (m + 255) / 256);  // 8 warps of 32 items per block
   const unsigned wgrid = (unsigned)std::min<int64_t>(1184, pgrid);         // the wide items' chunks
-  k_keys<<<pgrid + wgrid, 256, 0, s>>>(pa, vt, pgrid);
+  launch_dependent(k_keys, pgrid + wgrid, 256, s, pa, vt, pgrid);
   // 5. every tile's list by (depth bits, id)
   int id_bits = 1;
   while (id_bits < 32 && (1ll << id_bits) < sp.n) ++id_bits;
   TileSortArgs ta{w.keys_a, w.keys_b, bins.ranges, bins.vals, reinterpret_cast<uint64_t*>(bins.keys), w.work,
                   w.scalars + 32, id_bits};
   const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(vt.total_tiles, cap));
-  k_tile_sort<<<sgrid, kThreads, 0, s>>>(ta);
+  launch_dependent(k_tile_sort, sgrid, kThreads, s, ta);
   return check_launch("bin_sort");
 }
 

@@ -42,6 +42,17 @@ inline bool tile_shape_ok(int tw, int th) {
 }
 
 // View owning global tile gt (binary search over tile_base).
+// First statement of a kernel in a chain of programmatic dependent launches
+// (launch_dependent): waits until the grid before it on the stream has
+// completed and its writes are visible (a no-op for a kernel launched the
+// ordinary way), then lets the next kernel of the chain be scheduled as this
+// grid's blocks retire; that kernel's own chain_enter holds it until this
+// grid has completed, so no read moves ahead of a write it depends on.
+__device__ __forceinline__ void chain_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ int view_of_tile(const ViewTable& vt, int gt) {
   int lo = 0, hi = vt.views - 1;
   while (lo < hi) {

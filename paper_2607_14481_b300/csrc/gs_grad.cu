@@ -102,6 +102,7 @@ __device__ __forceinline__ uint64_t visible_views(const GradArgs& a, int64_t i, 
 constexpr uint32_t kWideSegment = 16;
 
 __global__ void __launch_bounds__(256) k_pair_sum(const GradArgs a, int64_t m) {
+  chain_enter();
   const int64_t o = (int64_t)blockIdx.x * 256 + threadIdx.x;
   const int lane = threadIdx.x & 31;
   uint32_t tch = 0;
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(256) k_pair_sum(const GradArgs a, int64_t m) {
 
 template <int DEG>
 __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, const ViewTable vt) {
+  chain_enter();
   const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
   const bool valid = i < a.n;
   const int64_t warp_id = i >> 5;
@@ -380,6 +382,7 @@ __global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, co
 // translation (mu - centre moves by R^T v).
 template <int DEG>
 __global__ void __launch_bounds__(kGradBlock) k_sh_bwd(const GradArgs a, const ViewTable vt) {
+  chain_enter();
   constexpr int NC = (DEG + 1) * (DEG + 1);
   const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
   const bool valid = i < a.n;
@@ -487,6 +490,7 @@ __device__ __forceinline__ bool adam4(float4& p, const float4 g, float4& m, floa
 template <int DEG, bool ONE>
 __global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 2) k_sh_bwd_adam(const GradArgs a, const ViewTable vt,
                                                             const AdamFamilies f) {
+  chain_enter();
   constexpr int NC = (DEG + 1) * (DEG + 1);
   const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
   const bool valid = i < a.n;
@@ -640,6 +644,7 @@ constexpr int kPoseChunks = 64;
 // of the chunk's first warp (no other block reads that chunk).
 __global__ void __launch_bounds__(256) k_pose_chunks(float* __restrict__ pa, const float* __restrict__ pb,
                                                      int64_t warps, int64_t chunk) {
+  chain_enter();
   __shared__ float s[256][6];
   const int v = blockIdx.y;
   const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(warps, b0 + chunk);
@@ -670,6 +675,7 @@ __global__ void __launch_bounds__(256) k_pose_chunks(float* __restrict__ pa, con
 // that the loads are issued together).
 __global__ void __launch_bounds__(kPoseChunks) k_pose_finalize(const float* __restrict__ pa, int64_t warps,
                                                              int64_t chunk, float* __restrict__ dpose) {
+  chain_enter();
   __shared__ float s[kPoseChunks][6];
   const int v = blockIdx.x, t = threadIdx.x;
   const int64_t b0 = (int64_t)t * chunk;
@@ -724,29 +730,29 @@ gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewT
   }
   const unsigned grid = (unsigned)((p.n + kGradBlock - 1) / kGradBlock);
   const int64_t m = p.n * vt.views;
-  k_pair_sum<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(a, m);
+  launch_dependent(k_pair_sum, (unsigned)((m + 255) / 256), 256, s, a, m);
   switch (p.sh_degree) {
     case 0:
-      k_project_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt);
+      launch_dependent(k_project_bwd<0>, grid, kGradBlock, s, a, vt);
+      launch_dependent(k_sh_bwd<0>, grid, kGradBlock, s, a, vt);
       break;
     case 1:
-      k_project_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt);
+      launch_dependent(k_project_bwd<1>, grid, kGradBlock, s, a, vt);
+      launch_dependent(k_sh_bwd<1>, grid, kGradBlock, s, a, vt);
       break;
     case 2:
-      k_project_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt);
+      launch_dependent(k_project_bwd<2>, grid, kGradBlock, s, a, vt);
+      launch_dependent(k_sh_bwd<2>, grid, kGradBlock, s, a, vt);
       break;
     default:
-      k_project_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt);
-      k_sh_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt);
+      launch_dependent(k_project_bwd<3>, grid, kGradBlock, s, a, vt);
+      launch_dependent(k_sh_bwd<3>, grid, kGradBlock, s, a, vt);
       break;
   }
   if (dpose) {
     const int64_t chunk = (warps + kPoseChunks - 1) / kPoseChunks;
-    k_pose_chunks<<<dim3(kPoseChunks, vt.views), 256, 0, s>>>(a.pose_a, a.pose_b, warps, chunk);
-    k_pose_finalize<<<vt.views, kPoseChunks, 0, s>>>(a.pose_a, warps, chunk, dpose);
+    launch_dependent(k_pose_chunks, dim3(kPoseChunks, vt.views), 256, s, a.pose_a, a.pose_b, warps, chunk);
+    launch_dependent(k_pose_finalize, vt.views, kPoseChunks, s, a.pose_a, warps, chunk, dpose);
   }
   return check_launch("project_bwd");
 }
@@ -816,33 +822,33 @@ gs_status launch_project_bwd_adam(const gs_params& p, const float* poses, const 
   }
   const unsigned grid = (unsigned)((p.n + kGradBlock - 1) / kGradBlock);
   const int64_t mm = p.n * vt.views;
-  k_pair_sum<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(a, mm);
+  launch_dependent(k_pair_sum, (unsigned)((mm + 255) / 256), 256, s, a, mm);
   switch (p.sh_degree) {
     case 0:
-      k_project_bwd<0><<<grid, kGradBlock, 0, s>>>(a, vt);
-      if (vt.views == 1) k_sh_bwd_adam<0, true><<<grid, kGradBlock, 0, s>>>(a, vt, f);
-      else k_sh_bwd_adam<0, false><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      launch_dependent(k_project_bwd<0>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_sh_bwd_adam<0, true>, grid, kGradBlock, s, a, vt, f);
+      else launch_dependent(k_sh_bwd_adam<0, false>, grid, kGradBlock, s, a, vt, f);
       break;
     case 1:
-      k_project_bwd<1><<<grid, kGradBlock, 0, s>>>(a, vt);
-      if (vt.views == 1) k_sh_bwd_adam<1, true><<<grid, kGradBlock, 0, s>>>(a, vt, f);
-      else k_sh_bwd_adam<1, false><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      launch_dependent(k_project_bwd<1>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_sh_bwd_adam<1, true>, grid, kGradBlock, s, a, vt, f);
+      else launch_dependent(k_sh_bwd_adam<1, false>, grid, kGradBlock, s, a, vt, f);
       break;
     case 2:
-      k_project_bwd<2><<<grid, kGradBlock, 0, s>>>(a, vt);
-      if (vt.views == 1) k_sh_bwd_adam<2, true><<<grid, kGradBlock, 0, s>>>(a, vt, f);
-      else k_sh_bwd_adam<2, false><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      launch_dependent(k_project_bwd<2>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_sh_bwd_adam<2, true>, grid, kGradBlock, s, a, vt, f);
+      else launch_dependent(k_sh_bwd_adam<2, false>, grid, kGradBlock, s, a, vt, f);
       break;
     default:
-      k_project_bwd<3><<<grid, kGradBlock, 0, s>>>(a, vt);
-      if (vt.views == 1) k_sh_bwd_adam<3, true><<<grid, kGradBlock, 0, s>>>(a, vt, f);
-      else k_sh_bwd_adam<3, false><<<grid, kGradBlock, 0, s>>>(a, vt, f);
+      launch_dependent(k_project_bwd<3>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_sh_bwd_adam<3, true>, grid, kGradBlock, s, a, vt, f);
+      else launch_dependent(k_sh_bwd_adam<3, false>, grid, kGradBlock, s, a, vt, f);
       break;
   }
   if (dpose) {
     const int64_t chunk = (warps + kPoseChunks - 1) / kPoseChunks;
-    k_pose_chunks<<<dim3(kPoseChunks, vt.views), 256, 0, s>>>(a.pose_a, a.pose_b, warps, chunk);
-    k_pose_finalize<<<vt.views, kPoseChunks, 0, s>>>(a.pose_a, warps, chunk, dpose);
+    launch_dependent(k_pose_chunks, dim3(kPoseChunks, vt.views), 256, s, a.pose_a, a.pose_b, warps, chunk);
+    launch_dependent(k_pose_finalize, vt.views, kPoseChunks, s, a.pose_a, warps, chunk, dpose);
   }
   return check_launch("project_bwd_adam");
 }

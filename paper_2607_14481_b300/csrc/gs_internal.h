@@ -28,6 +28,25 @@ struct NvtxRange {
 };
 #define GS_NVTX(name) ::gs::NvtxRange gs_nvtx_scope_(name)
 
+// Launches `kernel` so that it may start while the kernel before it on the
+// stream finishes (programmatic dependent launch, kept in a captured graph):
+// the kernel's first statement is chain_enter(), so only the launch and the
+// start of its blocks overlap the predecessor's tail, not any of its reads.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Schedule bits of gs_raster_cfg (see gs.h).
 constexpr uint32_t kSchedFwdLongestFirst = GS_SCHED_FWD_LONGEST_FIRST;
 constexpr uint32_t kSchedBwdLongestFirst = GS_SCHED_BWD_LONGEST_FIRST;
