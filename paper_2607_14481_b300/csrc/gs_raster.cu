@@ -539,23 +539,14 @@ __device__ __forceinline__ void splat_grad(const Eval& e, const float4 col, floa
   T = Tb;
 }
 
-// Single-pass form, walking front to back: T is the transmittance in front
-// of the splat (unchanged here).  rem, the colour still to come behind the
-// splat (background included, the forward image minus the colour composited
-// so far), enters the gradient only through g . rem, so the pixel carries
-// that one number, R = g . rem; on return it no longer holds this splat's
-// share.  dL/dalpha = T (g . c) - (g . rem) / (1 - alpha): the colour behind
-// the splat seen through it is T S = rem / (1 - alpha).
-__device__ __forceinline__ void splat_grad_front(const Eval& e, const float4 col, float g0, float g1,
-                                                 float g2, float T, float& R, float (&d)[kPartialValues]) {
-  const float w = e.alpha * T;
-  d[6] += g0 * w; d[7] += g1 * w; d[8] += g2 * w;
-  const float gc = g0 * col.x + g1 * col.y + g2 * col.z;
-  R -= gc * w;
-  const float rom = __fdividef(1.f, 1.f - e.alpha);
-  alpha_grad(e, gc * T - R * rom, d);
-}
-
+// The single-pass form walks front to back with T, the transmittance in
+// front of the splat.  rem, the colour still to come behind the splat
+// (background included, the forward image minus the colour composited so
+// far), enters the gradient only through g . rem, so the pixel carries that
+// one number, R = g . rem, and drops each blended splat's share from it.
+// dL/dalpha = T (g . c) - (g . rem) / (1 - alpha): the colour behind the
+// splat seen through it is T S = rem / (1 - alpha).
+//
 // One pixel's step of the single-pass backward without branches: the splat
 // test (as splat_alpha), the stop test, and the gradient contribution with
 // alpha, exp(power) and the weight masked to zero when the pixel does not

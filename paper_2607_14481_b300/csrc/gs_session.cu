@@ -853,12 +853,11 @@ gs_status sync_stream(gs_session* S, double timeout_s) {
 gs_status finish_analysis(gs_session* S, double timeout_s) {
   if (!S->h_pending) return GS_OK;
   const double t0 = steady_now();
-  cudaError_t e;
-  while ((e = cudaEventQuery(S->h_done)) == cudaErrorNotReady) {
+  while (cudaEventQuery(S->h_done) == cudaErrorNotReady) {
     if (steady_now() - t0 > timeout_s) return fail(GS_ERR_TIMEOUT, "session: hierarchy analysis did not finish");
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
-  try_swap(S);
+  try_swap(S);  // reads the event's status (an error is fatal)
   return S->fatal;
 }
 
