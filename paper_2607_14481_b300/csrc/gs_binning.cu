@@ -1018,6 +1018,73 @@ __device__ void cta_bitonic(const TileSortArgs& a, uint32_t t, uint32_t start, u
 
 constexpr uint32_t kBitonicMax = 4096;  // longest list sorted in shared memory
 
+constexpr uint32_t kMergeMax = 2048;     // longest list sorted by runs and merges (two buffers of s_keys)
+
+// Sort of a tile's list of 256 < cnt <= kMergeMax keys by the CTA: warp w
+// sorts runs w, w + 8, ... of 256 keys in registers (the warp's bitonic
+// network; the last run padded with ~0 keys, which sort last), then passes of
+// merges double the sorted runs up to the whole list, ping-ponging between
+// the two halves of s (each thread finds where its share of a merged run
+// starts by a binary search along the merge path, then merges its share in
+// order).  Keys of a tile are distinct, so the result is the one order; the
+// ids (and optionally the full keys) are written out.
+__device__ void cta_merge_sort(const TileSortArgs& a, uint32_t t, uint32_t start, uint32_t cnt, uint64_t* s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t npad = (cnt + 255u) & ~255u;  // whole runs of 256
+  uint64_t* src = s;
+  uint64_t* dst = s + kMergeMax;
+  for (uint32_t r = (uint32_t)warp; r * 256u < npad; r += kThreads / 32) {
+    uint64_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const uint32_t i = r * 256u + (uint32_t)(e * 32 + lane);
+      v[e] = i < cnt ? a.keys[start + i] : ~0ull;
+    }
+    warp_bitonic<8>(v);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) src[r * 256u + (uint32_t)(e * 32 + lane)] = v[e];
+  }
+  __syncthreads();
+  // each merged run is cut into chunks of kChunk outputs (kChunk divides
+  // every run length 2 * width, so no chunk straddles two runs)
+  constexpr uint32_t kChunk = 4;
+  for (uint32_t width = 256; width < npad; width <<= 1) {
+    for (uint32_t o = threadIdx.x * kChunk; o < npad; o += kThreads * kChunk) {
+      const uint32_t seg = o / (2 * width) * (2 * width);
+      const uint32_t la = min(width, npad - seg);       // run A = [seg, seg + la)
+      const uint32_t lb = min(width, npad - seg - la);  // run B follows it (may be empty)
+      const uint64_t* A = src + seg;
+      const uint64_t* B = A + la;
+      const uint32_t k = o - seg;  // position within the merged run
+      // merge path: i keys of A and k - i of B precede output k
+      uint32_t lo = k > lb ? k - lb : 0u, hi = min(k, la);
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (A[mid] <= B[k - mid - 1]) lo = mid + 1; else hi = mid;
+      }
+      uint32_t i = lo, j = k - lo;
+#pragma unroll
+      for (uint32_t q = 0; q < kChunk; ++q) {
+        const bool take_a = j >= lb || (i < la && A[i] <= B[j]);
+        dst[o + q] = take_a ? A[i] : B[j];
+        i += take_a ? 1u : 0u;
+        j += take_a ? 0u : 1u;
+      }
+    }
+    __syncthreads();
+    uint64_t* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  for (uint32_t i = threadIdx.x; i < cnt; i += kThreads) {
+    const uint64_t key = src[i];
+    a.vals[start + i] = (uint32_t)key;
+    if (a.full_keys) a.full_keys[start + i] = ((uint64_t)t << 32) | (key >> 32);
+  }
+}
+
+
+
 // The tile sort.  Work unit u < L (L = tiles of >= 256 pairs) is the u-th
 // longest such tile, sorted by the whole CTA: a bitonic network in shared
 // memory up to kBitonicMax keys, stable LSD radix passes through global
@@ -1050,6 +1117,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_tile_sort(const TileSortArgs a)
   }
   const uint32_t t = a.work[u];
   const uint32_t start = a.ranges[2 * (uint64_t)t], cnt = a.ranges[2 * (uint64_t)t + 1] - start;
+  if (cnt <= kMergeMax) {
+    cta_merge_sort(a, t, start, cnt, s_keys);
+    return;
+  }
   if (cnt <= kBitonicMax) {
     uint32_t N = 256;
     while (N < cnt) N <<= 1;
