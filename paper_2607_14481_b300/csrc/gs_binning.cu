@@ -11,17 +11,22 @@
 //      into the ranges array, nothing waits for it);
 //   3. one CTA scans the tiles' counts into list starts, sets each tile's
 //      cursor to its start and groups the tiles by list length (and, when
-//      asked, orders them longest list first);
+//      asked, orders them longest list first); beyond 8192 tiles a
+//      device-wide scan and two ordering kernels do it;
 //   4. every pair takes the next place of its tile's cursor and writes its
-//      (depth bits, Gaussian id) key there;
+//      (depth bits, Gaussian id) key there (splats of >= 128 tiles in
+//      128-pair chunks by extra blocks of the same launch);
 //   5. each tile's list is sorted: lists of fewer than 256 keys by one warp
-//      in registers (eight tiles per CTA), longer ones by a CTA in shared
-//      memory (bitonic networks), the few beyond 4096 keys by stable radix
-//      passes through global memory; the sort writes the ids.
+//      in registers (eight tiles per CTA), up to 2048 by a CTA merging warp-
+//      sorted runs of 256 in shared memory, up to 4096 by a CTA bitonic
+//      network, the few beyond by stable radix passes through global
+//      memory; the sort writes the ids.
+// A first launch zeroes the counters, the ranges and the scan's look-back
+// words; the five launches are chained as programmatic dependent launches.
 // Within a tile every Gaussian appears once, so (depth bits, id) keys are
 // distinct and the sorted list is unique: the atomics' order never shows.
 // This is the order of one sort of 64-bit (tile, depth) keys with depth ties
-// in id order, with ~30 bytes moved per pair in five launches.
+// in id order, with ~30 bytes moved per pair.
 //
 // Every count (visible items, pairs) stays in device memory: kernels are
 // launched for the capacity and read the live count, so the whole stage runs

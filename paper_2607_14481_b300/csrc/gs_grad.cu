@@ -10,11 +10,17 @@
 //   k_project_bwd  pixel-space mean, conic, opacity -> means, log-scales,
 //                  quaternion, opacity logit, pose (t and rotation terms);
 //   k_sh_bwd       colour -> SH coefficients and, through the view
-//                  direction, the means and the pose translation.
-// Pose gradients are reduced per warp (shuffles, fixed tree), then over
-// fixed chunks of warps and the chunks in a fixed order: deterministic, no
-// atomics.  The pair sum is its own kernel so that its scattered loads run at
-// full occupancy: the chain-rule kernels hold ~120 registers per thread.
+//                  direction, the means and the pose translation;
+//   k_sh_bwd_adam  the same, with the Adam step of every parameter of the
+//                  Gaussian applied once its gradients are complete (the
+//                  training step's form).
+// A thread first loads every view's pair count and offset (a bit set of the
+// views that see its Gaussian), so a view loop waits on memory only in those
+// views.  Pose gradients are reduced per warp (shuffles, fixed tree), then
+// over fixed chunks of warps and the chunks in a fixed order: deterministic,
+// no atomics.  The pair sum is its own kernel so that its scattered loads run
+// at full occupancy: the chain-rule kernels hold ~120 registers per thread.
+// The kernels of a backward are chained as programmatic dependent launches.
 #include <algorithm>
 
 #include "gs_internal.h"
