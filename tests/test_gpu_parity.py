@@ -181,6 +181,49 @@ def test_bins_bit_exact_long_tile_lists(cuda_device):
         assert np.array_equal(r.ranges[:2 * r.num_tiles].cpu().numpy().view(np.uint32).reshape(-1, 2), ranges_o)
 
 
+def test_bins_bit_exact_at_every_sort_size_boundary(cuda_device):
+    """One list per tile at the lengths where the per-tile sort changes form
+    or shape (warp networks of 32..256 keys, merged warp runs of 256 up to
+    2048, the CTA network up to 4096, radix passes beyond, and the padding
+    of each), single-tile footprints with a few depth levels so that equal
+    depths must come out in id order: keys, ids and ranges equal the oracle's
+    bit for bit."""
+    lens = [0, 1, 31, 32, 33, 255, 256, 257, 383, 511, 512, 513, 767, 768, 1024, 1025, 1500, 2047, 2048, 2049,
+            3000, 4096, 4097, 5000]
+    tiles = [(6, 4)]
+    n = int(sum(lens))
+    g = np.random.default_rng(91)
+    depth = np.zeros((1, n), np.float32)
+    rect = np.zeros((1, n, 4), np.int32)
+    tile_of = np.repeat(np.arange(len(lens)), lens)
+    g.shuffle(tile_of)  # the lists' members interleaved in id order
+    depth[0] = np.where(g.random(n) < 0.3, np.float32(3.5), (0.2 + 20.0 * g.random(n)).astype(np.float32))
+    rect[0, :, 0] = rect[0, :, 2] = tile_of % 6
+    rect[0, :, 1] = rect[0, :, 3] = tile_of // 6
+    keys_o, vals_o, ranges_o = oracle.bin_records(depth, rect, tiles)
+    assert np.array_equal(ranges_o[:, 1] - ranges_o[:, 0], lens)
+    cams = [synth.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 100.0, 100.0, 0.0, 0.0, 96, 64)]
+    from paper_2607_14481_b300 import raster
+    from gpu_util import ensure_built
+    ensure_built()
+    r = raster.Rasterizer(n, 0, cams, capacity=len(keys_o) + 9, device=cuda_device, keep_keys=True)
+    sv = r.splat_views()
+    sv["depth"].copy_(torch.from_numpy(depth))
+    packed = np.zeros((1, n, 2), np.uint32)
+    packed[..., 0] = rect[..., 0].astype(np.uint32) | (rect[..., 1].astype(np.uint32) << 16)
+    packed[..., 1] = rect[..., 2].astype(np.uint32) | (rect[..., 3].astype(np.uint32) << 16)
+    sv["rect"].copy_(torch.from_numpy(packed.view(np.int32)))
+    sv["touched"].copy_(torch.ones((1, n), dtype=torch.int32))
+    r.bin_sort()
+    torch.cuda.synchronize()
+    K = len(keys_o)
+    cnt = r.read_counts()
+    assert cnt[1] == K and cnt[2] == 0 and cnt[3] == K
+    assert np.array_equal(r.keys[:K].cpu().numpy().view(np.uint64), keys_o)
+    assert np.array_equal(r.vals[:K].cpu().numpy().view(np.uint32), vals_o)
+    assert np.array_equal(r.ranges[:2 * r.num_tiles].cpu().numpy().view(np.uint32).reshape(-1, 2), ranges_o)
+
+
 def test_bins_capacity_overflow_is_flagged_and_recovered(cuda_device):
     sc, cams, _ = synth.plain_small()
     r, arena, poses, img, alpha = gpu_forward(sc, cams, capacity=64)
