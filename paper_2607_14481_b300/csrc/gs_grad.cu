@@ -494,7 +494,7 @@ __device__ __forceinline__ bool adam4(float4& p, const float4 g, float4& m, floa
 // the view's colour gradient and basis instead of 48 accumulators (0 + g_c Y_k,
 // the accumulated value's bits), which frees registers for occupancy.
 template <int DEG, bool ONE>
-__global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 2) k_sh_bwd_adam(const GradArgs a, const ViewTable vt,
+__global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 3) k_sh_bwd_adam(const GradArgs a, const ViewTable vt,
                                                             const AdamFamilies f) {
   chain_enter();
   constexpr int NC = (DEG + 1) * (DEG + 1);
@@ -503,16 +503,16 @@ __global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 2) k_sh_bwd_adam(const G
   const int64_t warp_id = i >> 5;
   const int64_t warps = (int64_t)gridDim.x * (kGradBlock / 32);
   const float4 mu = valid ? a.means4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float gsh[ONE ? 1 : 3][ONE ? 1 : NC];
+  // several views: the 3 NC SH gradient sums live in shared memory (plane
+  // pl of thread t at s_gsh[pl][t], conflict-free), not in registers
+  __shared__ float s_gsh[ONE ? 1 : 3 * NC][ONE ? 1 : kGradBlock];
   float Ys[ONE ? NC : 1], gcs[3] = {0.f, 0.f, 0.f};
   if constexpr (ONE) {
 #pragma unroll
     for (int k = 0; k < NC; ++k) Ys[k] = 0.f;
   } else {
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
-#pragma unroll
-      for (int k = 0; k < NC; ++k) gsh[ch][k] = 0.f;
+    for (int pl = 0; pl < 3 * NC; ++pl) s_gsh[pl][threadIdx.x] = 0.f;
   }
   float gmu[3] = {0.f, 0.f, 0.f};
   const uint64_t vmask = visible_views(a, i, valid, vt.views, a.counts[3]);
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 2) k_sh_bwd_adam(const G
       for (int ch = 0; ch < 3; ++ch) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-          if constexpr (!ONE) gsh[ch][k] += gc[ch] * Y[k];
+          if constexpr (!ONE) s_gsh[ch * NC + k][threadIdx.x] += gc[ch] * Y[k];
           if (k > 0) dY[k] += gc[ch] * a.sh[(int64_t)(ch * NC + k) * a.sh_stride + i];
         }
       }
@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 2) k_sh_bwd_adam(const G
         const int pl = p0 + b;
         float gp;
         if constexpr (ONE) gp = __fadd_rn(0.f, __fmul_rn(gcs[pl / NC], Ys[pl % NC]));
-        else gp = gsh[pl / NC][pl % NC];
+        else gp = s_gsh[pl][threadIdx.x];
         ok &= adam_elem(P[b], gp, M[b], V[b], f.lr_sh[pl] * ss, f.b1, f.b2, f.eps, rs_bc2);
       }
 #pragma unroll
