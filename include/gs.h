@@ -465,8 +465,9 @@ GS_API size_t gs_bin_sort_workspace(int64_t n, int32_t views, int64_t capacity);
  * Gaussian-id order, and each tile's [start, end) range is written.  The sort
  * is a counting sort by tile (each pair takes a place in its tile list with
  * one atomic; a scan over the tiles gives the list starts) followed by a sort
- * of every tile's own (depth bits, id) keys by one CTA (in shared memory up
- * to 4096 pairs, else by a CTA-wide stable radix sort); the keys of one tile
+ * of every tile's own (depth bits, id) keys by one warp (in registers, below
+ * 256 pairs) or CTA (in shared memory up to 4096 pairs, else by a CTA-wide
+ * stable radix sort); the keys of one tile
  * are distinct, so the result does not depend on the atomics' order.  At most
  * 2^25 tiles over all views.  No host synchronisation: K stays on the device
  * (counts).  ws: device, >= gs_bin_sort_workspace bytes, 256-byte aligned. */
