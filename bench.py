@@ -58,6 +58,8 @@ def parse_args():
                     help="run only the level-of-detail measurement (one JSON line)")
     ap.add_argument("--ba-only", action="store_true",
                     help="run only the local bundle adjustment measurement (one JSON line)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched measurement at --gaussians (one JSON line)")
     return ap.parse_args()
 
 
@@ -1214,6 +1216,15 @@ def main():
         import torch
         out = run_local_ba(torch.device("cuda", 0), cpu=not args.no_cpu_baseline)
         print(json.dumps({"local_ba": out}), flush=True)
+        return
+    if args.batched_only:
+        import torch
+        from paper_2607_14481_b300 import build, synth
+        build.build()
+        torch.cuda.set_device(0)
+        out = run_batched(args.n, torch.device("cuda", 0), synth.loop_views(16, SEED_TRAJ + 1), args.steps,
+                          args.warmup, 1, 0)
+        print(json.dumps({"batched": out}), flush=True)
         return
     ws, rank, local = dist_setup(args.gpus)
     out, rank = run_ours(args, ws, rank, local)
