@@ -58,14 +58,17 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const View
   // the rotation and scale are loaded with the mean, so that the thread
   // waits for one memory round trip before the covariance, not two
   const float4 mu = a.means4[i], q = a.quat[i], so = a.scale_opa[i];
-  // the SH planes are read only once the splat is known to be visible, a
-  // second dependent round trip: start bringing them to L2 now
-#pragma unroll
-  for (int k = 0; k < 3 * NC; ++k)
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(a.sh + (int64_t)k * a.sh_stride + i)));
   // camera-space centre in double-single
   const df tz = df_dot3_add(R[6], mu.x, R[7], mu.y, R[8], mu.z, tc[2]);
   bool vis = !df_le(tz, a.znear);
+  // the SH planes are read only once the splat is known to be visible, a
+  // second dependent round trip: for a centre in front of the camera start
+  // bringing them to L2 now
+  if (vis) {
+#pragma unroll
+    for (int k = 0; k < 3 * NC; ++k)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(a.sh + (int64_t)k * a.sh_stride + i)));
+  }
   df tx = {0.f, 0.f}, ty = {0.f, 0.f}, mx = {0.f, 0.f}, my = {0.f, 0.f};
   if (vis) {
     tx = df_dot3_add(R[0], mu.x, R[1], mu.y, R[2], mu.z, tc[0]);
