@@ -515,6 +515,16 @@ __global__ void __launch_bounds__(kGradBlock, ONE ? 4 : 3) k_sh_bwd_adam(const G
     for (int pl = 0; pl < 3 * NC; ++pl) s_gsh[pl][threadIdx.x] = 0.f;
   }
   float gmu[3] = {0.f, 0.f, 0.f};
+  if constexpr (ONE) {
+    // one view: the chain rule reads 45 SH planes once the view is known to
+    // see the Gaussian, and the update reads all 48 of every Gaussian: ask
+    // for their lines in L2 at once
+    if (valid) {
+#pragma unroll
+      for (int pl = 0; pl < 3 * NC; ++pl)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(a.sh + (int64_t)pl * a.sh_stride + i)));
+    }
+  }
   const uint64_t vmask = visible_views(a, i, valid, vt.views, a.counts[3]);
   if constexpr (!ONE) {
     // the colour gradients of the views that see the Gaussian and its SH
