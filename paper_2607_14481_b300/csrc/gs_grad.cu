@@ -186,8 +186,10 @@ __global__ void __launch_bounds__(256) k_pair_sum(const GradArgs a, int64_t m) {
   }
 }
 
-template <int DEG>
-__global__ void __launch_bounds__(kGradBlock) k_project_bwd(const GradArgs a, const ViewTable vt) {
+// ONE (a single view): the same code bounded to 3 CTAs per SM (85
+// registers) instead of 2 (its per-view loop runs once).
+template <int DEG, bool ONE>
+__global__ void __launch_bounds__(kGradBlock, ONE ? 3 : 2) k_project_bwd(const GradArgs a, const ViewTable vt) {
   chain_enter();
   const int64_t i = (int64_t)blockIdx.x * kGradBlock + threadIdx.x;
   const bool valid = i < a.n;
@@ -749,19 +751,23 @@ gs_status launch_project_bwd(const gs_params& p, const float* poses, const ViewT
   launch_dependent(k_pair_sum, (unsigned)((m + 255) / 256), 256, s, a, m);
   switch (p.sh_degree) {
     case 0:
-      launch_dependent(k_project_bwd<0>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_project_bwd<0, true>, grid, kGradBlock, s, a, vt);
+      else launch_dependent(k_project_bwd<0, false>, grid, kGradBlock, s, a, vt);
       launch_dependent(k_sh_bwd<0>, grid, kGradBlock, s, a, vt);
       break;
     case 1:
-      launch_dependent(k_project_bwd<1>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_project_bwd<1, true>, grid, kGradBlock, s, a, vt);
+      else launch_dependent(k_project_bwd<1, false>, grid, kGradBlock, s, a, vt);
       launch_dependent(k_sh_bwd<1>, grid, kGradBlock, s, a, vt);
       break;
     case 2:
-      launch_dependent(k_project_bwd<2>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_project_bwd<2, true>, grid, kGradBlock, s, a, vt);
+      else launch_dependent(k_project_bwd<2, false>, grid, kGradBlock, s, a, vt);
       launch_dependent(k_sh_bwd<2>, grid, kGradBlock, s, a, vt);
       break;
     default:
-      launch_dependent(k_project_bwd<3>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_project_bwd<3, true>, grid, kGradBlock, s, a, vt);
+      else launch_dependent(k_project_bwd<3, false>, grid, kGradBlock, s, a, vt);
       launch_dependent(k_sh_bwd<3>, grid, kGradBlock, s, a, vt);
       break;
   }
@@ -841,22 +847,26 @@ gs_status launch_project_bwd_adam(const gs_params& p, const float* poses, const 
   launch_dependent(k_pair_sum, (unsigned)((mm + 255) / 256), 256, s, a, mm);
   switch (p.sh_degree) {
     case 0:
-      launch_dependent(k_project_bwd<0>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_project_bwd<0, true>, grid, kGradBlock, s, a, vt);
+      else launch_dependent(k_project_bwd<0, false>, grid, kGradBlock, s, a, vt);
       if (vt.views == 1) launch_dependent(k_sh_bwd_adam<0, true>, grid, kGradBlock, s, a, vt, f);
       else launch_dependent(k_sh_bwd_adam<0, false>, grid, kGradBlock, s, a, vt, f);
       break;
     case 1:
-      launch_dependent(k_project_bwd<1>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_project_bwd<1, true>, grid, kGradBlock, s, a, vt);
+      else launch_dependent(k_project_bwd<1, false>, grid, kGradBlock, s, a, vt);
       if (vt.views == 1) launch_dependent(k_sh_bwd_adam<1, true>, grid, kGradBlock, s, a, vt, f);
       else launch_dependent(k_sh_bwd_adam<1, false>, grid, kGradBlock, s, a, vt, f);
       break;
     case 2:
-      launch_dependent(k_project_bwd<2>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_project_bwd<2, true>, grid, kGradBlock, s, a, vt);
+      else launch_dependent(k_project_bwd<2, false>, grid, kGradBlock, s, a, vt);
       if (vt.views == 1) launch_dependent(k_sh_bwd_adam<2, true>, grid, kGradBlock, s, a, vt, f);
       else launch_dependent(k_sh_bwd_adam<2, false>, grid, kGradBlock, s, a, vt, f);
       break;
     default:
-      launch_dependent(k_project_bwd<3>, grid, kGradBlock, s, a, vt);
+      if (vt.views == 1) launch_dependent(k_project_bwd<3, true>, grid, kGradBlock, s, a, vt);
+      else launch_dependent(k_project_bwd<3, false>, grid, kGradBlock, s, a, vt);
       if (vt.views == 1) launch_dependent(k_sh_bwd_adam<3, true>, grid, kGradBlock, s, a, vt, f);
       else launch_dependent(k_sh_bwd_adam<3, false>, grid, kGradBlock, s, a, vt, f);
       break;
