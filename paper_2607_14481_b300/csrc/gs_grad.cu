@@ -107,7 +107,7 @@ __device__ __forceinline__ uint64_t visible_views(const GradArgs& a, int64_t i, 
 // lanes, so the warp's time is not set by one thread walking a long segment.
 constexpr uint32_t kWideSegment = 16;
 
-__global__ void __launch_bounds__(256) k_pair_sum(const GradArgs a, int64_t m) {
+__global__ void __launch_bounds__(256, 6) k_pair_sum(const GradArgs a, int64_t m) {
   chain_enter();
   const int64_t o = (int64_t)blockIdx.x * 256 + threadIdx.x;
   const int lane = threadIdx.x & 31;
