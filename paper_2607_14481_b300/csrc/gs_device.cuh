@@ -53,6 +53,12 @@ __device__ __forceinline__ void chain_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Hint that the line holding p will be read soon by this SM (no register,
+// no wait; p must point into an allocation).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 __device__ __forceinline__ int view_of_tile(const ViewTable& vt, int gt) {
   int lo = 0, hi = vt.views - 1;
   while (lo < hi) {

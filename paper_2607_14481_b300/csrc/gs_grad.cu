@@ -75,12 +75,6 @@ __device__ __forceinline__ bool pair_range_ok(const GradArgs& a, int64_t o, uint
   return tch > 0;
 }
 
-// Hint that the line holding p will be read soon by this SM (no register,
-// no wait; p must point into an allocation).
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));
-}
-
 // The views (bit v) in which Gaussian i has rendered pairs (as
 // pair_range_ok), with every view's count and offset loaded before any
 // view's work: a per-view loop then waits for memory only in the views that

@@ -226,6 +226,26 @@ __device__ __forceinline__ void stage_splat(const float4* xy, const float4* coni
                                              __fmul_rn(-0.5f * kLog2e, co.z), -log2f(255.f * co.w), col.w);
 }
 
+// Asks this SM's L1 for the records of list position j (and, with pair_off,
+// the inputs of its pair slot) one batch before they are staged: the
+// staging's two dependent loads (list id, then records) then find their
+// lines in L1 instead of waiting on L2 with every warp of the CTA at the
+// barrier behind them.
+__device__ __forceinline__ void prefetch_splat(const float4* xy, const float4* conic, const float4* rgb,
+                                               const uint32_t* vals, int64_t n, int64_t vbase, uint32_t j,
+                                               const uint32_t* pair_off, const uint2* rect) {
+  const uint32_t g = vals[j];
+  if (g >= n) return;
+  const int64_t gi = vbase + g;
+  prefetch_l1(xy + gi);
+  prefetch_l1(conic + gi);
+  prefetch_l1(rgb + gi);
+  if (pair_off) {
+    prefetch_l1(pair_off + gi);
+    prefetch_l1(rect + gi);
+  }
+}
+
 // Bit set of the staged splats [0, cnt) that warp `warp` can reach (its bit
 // of s_mask), 32 per word, written to s_wb[0 .. ceil(cnt/32)): the warp's
 // loop visits only these, in ascending order (front to back), instead of
@@ -293,6 +313,8 @@ __device__ __forceinline__ void composite_tile(const FwdArgs& a, const TileCoord
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
     if (__syncthreads_count(d0 && d1) == kThreads) break;
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
+    for (int t = threadIdx.x; t < kBatch && start + kBatch + t < rg.y; t += kThreads)
+      prefetch_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + kBatch + t, nullptr, nullptr);
     for (int t = threadIdx.x; t < cnt; t += kThreads)
       stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + t, t, tc.ox, tc.oy, s_geo, s_geo2,
                       s_rgb, s_mask, nullptr, COUNT ? nullptr : a.counts);
@@ -724,18 +746,40 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(const BwdArgs a, const 
   }
 }
 
-// Shared arrays of the per-pixel backward: the staged splats (with the
-// unscaled conic), the bit sets, and per staged splat its pair slot and the
-// warps' reduced partials.
+// Shared arrays of the single-pass backward: the staged splats, the bit
+// sets, and per staged splat the warps' reduced partials and which warps
+// wrote them (cleared by the thread that stores the pair, so every slot is
+// zero again when the next batch is staged).
 template <int kBatch>
 struct BwdSmem {
-  float4 geo[kBatch], geo2[kBatch], rgb[kBatch], co[kBatch];
+  float4 geo[kBatch], geo2[kBatch], rgb[kBatch];
   uint8_t mask[kBatch];
   uint32_t wb[kWarps][kBatch / 32];
-  uint32_t pidx[kBatch];
   float red[kBatch][kWarps][kPartialValues];
   uint8_t hit[kBatch][kWarps];
 };
+
+// Zeroes the hit flags once, before a CTA's first tile.
+template <int kBatch>
+__device__ __forceinline__ void clear_hits(BwdSmem<kBatch>& sm) {
+  for (int i = threadIdx.x; i < kBatch * kWarps; i += kThreads) (&sm.hit[0][0])[i] = 0;
+}
+
+// Stores the pair of list position j from staged slot k's partials: its
+// pair slot and unscaled conic are read again from memory (lines the
+// staging brought into L1), so no shared slot carries them from the staging
+// to the store, and clears the slot's hit flags.
+__device__ __forceinline__ void store_staged(const BwdArgs& a, int64_t vbase, uint32_t j, const TileCoords& tc,
+                                             const float (&red)[kWarps][kPartialValues], uint8_t (&hit)[kWarps]) {
+  const uint32_t g = a.vals[j];
+  if (g < a.n) {
+    const int64_t gi = vbase + g;
+    const uint32_t pidx = a.pair_off[gi] + rect_index(a.rect[gi], tc.tx, tc.ty);
+    store_pair(a, pidx, red, hit, a.conic[gi]);
+  }
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) hit[w] = 0;
+}
 
 // Single front-to-back backward pass over one tile's list for the thread's
 // two pixels, with upstream colour gradients g0/g1 and R0/R1 = g . (forward
@@ -744,7 +788,10 @@ struct BwdSmem {
 // order, with the forward's own decisions (same splat test, same
 // transmittance products, same stop), yields every gradient without a replay
 // and without recovering T by division.  Stores every pair's partials (zeros
-// for pairs no pixel reached).
+// for pairs no pixel reached).  Two barriers per batch: after the batch's
+// pixel steps, the pairs of the batch are stored by the threads from kBatch
+// on (modulo the CTA) while threads [0, kBatch) stage the next batch, which
+// touch different shared arrays.  The hit flags must be zero on entry.
 template <int kBatch, int TW>
 __device__ __forceinline__ void bwd_front_tile(const BwdArgs& a, const TileCoords& tc, const uint2 rg,
                                                const int64_t vbase, const float (&gp0)[3], const float (&gp1)[3],
@@ -752,49 +799,56 @@ __device__ __forceinline__ void bwd_front_tile(const BwdArgs& a, const TileCoord
   static_assert(kBatch <= kThreads, "one staged splat per thread");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float g00 = gp0[0], g01 = gp0[1], g02 = gp0[2], g10 = gp1[0], g11 = gp1[1], g12 = gp1[2];
+  const int ss = (int)((threadIdx.x + kThreads - kBatch) % kThreads);  // the slot this thread stores
   float T0 = 1.f, T1 = 1.f;
   bool d0 = !tc.in0, d1 = !tc.in1;
   uint32_t start = rg.x;
-  for (; start < rg.y; start += kBatch) {
-    if (__syncthreads_count(d0 && d1) == kThreads) break;
-    const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
-    if (threadIdx.x < cnt) {
-      const uint32_t j = start + threadIdx.x;
-      stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, sm.geo, sm.geo2,
-                      sm.rgb, sm.mask, sm.co, nullptr);
-      sm.pidx[threadIdx.x] = pair_slot(a, vbase, j, tc);
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) sm.hit[threadIdx.x][w] = 0;
-    }
-    __syncthreads();
-    warp_bits<kBatch>(sm.mask, cnt, warp, lane, sm.wb[warp]);
-    bool live = true;
-    for (int q = 0; q * 32 < cnt && live; ++q) {
-     for (uint32_t bits = sm.wb[warp][q]; bits; bits &= bits - 1) {  // warp-uniform
-      if (__all_sync(0xffffffffu, d0 && d1)) {  // the warp's pixels are done
-        live = false;
-        break;
+  // the first barrier also ends the previous phase's reads of the staging slots
+  if (__syncthreads_count(d0 && d1) < kThreads && start < rg.y) {
+    int cnt = (int)min((uint32_t)kBatch, rg.y - start);
+    for (;;) {
+      if (threadIdx.x < cnt) {
+        if (start + kBatch + threadIdx.x < rg.y)
+          prefetch_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + kBatch + threadIdx.x, a.pair_off,
+                         a.rect);
+        stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + threadIdx.x, threadIdx.x, tc.ox, tc.oy,
+                        sm.geo, sm.geo2, sm.rgb, sm.mask, nullptr, nullptr);
       }
-      const int k = q * 32 + __ffs(bits) - 1;
-      float d[kPartialValues];
-      const float4 g = sm.geo[k], g2 = sm.geo2[k], col = sm.rgb[k];
-      const XTerms x = splat_x(g, tc.lx);
-      bool contrib = pixel_step_front<false>(x, g, g2, tc.ly0, col, g00, g01, g02, T0, R0, d0, d);
-      contrib |= pixel_step_front<true>(x, g, g2, tc.ly1, col, g10, g11, g12, T1, R1, d1, d);
-      if (__any_sync(0xffffffffu, contrib)) {
-        float s8, t8;
-        int idx;
-        warp_sum9(d, lane, s8, idx, t8);
-        if ((lane & 3) == 0) sm.red[k][warp][idx] = s8;
-        if (lane == 0) {
-          sm.red[k][warp][8] = t8;
-          sm.hit[k][warp] = 1;
+      __syncthreads();
+      warp_bits<kBatch>(sm.mask, cnt, warp, lane, sm.wb[warp]);
+      bool live = true;
+      for (int q = 0; q * 32 < cnt && live; ++q) {
+       for (uint32_t bits = sm.wb[warp][q]; bits; bits &= bits - 1) {  // warp-uniform
+        if (__all_sync(0xffffffffu, d0 && d1)) {  // the warp's pixels are done
+          live = false;
+          break;
         }
+        const int k = q * 32 + __ffs(bits) - 1;
+        float d[kPartialValues];
+        const float4 g = sm.geo[k], g2 = sm.geo2[k], col = sm.rgb[k];
+        const XTerms x = splat_x(g, tc.lx);
+        bool contrib = pixel_step_front<false>(x, g, g2, tc.ly0, col, g00, g01, g02, T0, R0, d0, d);
+        contrib |= pixel_step_front<true>(x, g, g2, tc.ly1, col, g10, g11, g12, T1, R1, d1, d);
+        if (__any_sync(0xffffffffu, contrib)) {
+          float s8, t8;
+          int idx;
+          warp_sum9(d, lane, s8, idx, t8);
+          if ((lane & 3) == 0) sm.red[k][warp][idx] = s8;
+          if (lane == 0) {
+            sm.red[k][warp][8] = t8;
+            sm.hit[k][warp] = 1;
+          }
+        }
+       }
       }
-     }
+      // every warp is past this batch's pixel steps: its partials are
+      // complete and the staging slots are free
+      const bool all_done = __syncthreads_count(d0 && d1) == kThreads;
+      if (ss < cnt) store_staged(a, vbase, start + ss, tc, sm.red[ss], sm.hit[ss]);
+      start += kBatch;
+      if (all_done || start >= rg.y) break;
+      cnt = (int)min((uint32_t)kBatch, rg.y - start);
     }
-    __syncthreads();
-    if (threadIdx.x < cnt) store_pair(a, sm.pidx[threadIdx.x], sm.red[threadIdx.x], sm.hit[threadIdx.x], sm.co[threadIdx.x]);
   }
   // pairs past the batch where every pixel of the tile had stopped
   for (uint32_t p = start + threadIdx.x; p < rg.y; p += kThreads) zero_pair(a, vbase, p, tc);
@@ -805,6 +859,7 @@ __device__ __forceinline__ void bwd_front_tile(const BwdArgs& a, const TileCoord
 template <int kBatch, int TW>
 __global__ void __launch_bounds__(kThreads) k_render_bwd_front(const BwdArgs a, const ViewTable vt) {
   __shared__ BwdSmem<kBatch> sm;
+  clear_hits(sm);  // ordered before their first use by the backward's first barrier
   const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;  // longest lists first
   const TileCoords tc = tile_coords<TW>(vt, gt);
   const ViewInfo& vi = vt.v[tc.v];
@@ -861,6 +916,7 @@ __global__ void __launch_bounds__(kThreads) k_render_fused(const FusedArgs a, co
   __shared__ float s_red[kWarps];
   __shared__ bool s_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  clear_hits(sm);  // ordered before their first use by the barrier below
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(&a.queue[0], 1u);
     __syncthreads();
