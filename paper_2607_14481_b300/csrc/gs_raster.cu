@@ -226,24 +226,19 @@ __device__ __forceinline__ void stage_splat(const float4* xy, const float4* coni
                                              __fmul_rn(-0.5f * kLog2e, co.z), -log2f(255.f * co.w), col.w);
 }
 
-// Asks this SM's L1 for the records of list position j (and, with pair_off,
-// the inputs of its pair slot) one batch before they are staged: the
-// staging's two dependent loads (list id, then records) then find their
-// lines in L1 instead of waiting on L2 with every warp of the CTA at the
-// barrier behind them.
+// Asks this SM's L1 for the records of list position j one batch before
+// they are staged: the staging's two dependent loads (list id, then
+// records) then find their lines in L1 instead of waiting on L2 with every
+// warp of the CTA at the barrier behind them.  Callers skip it once half of
+// the tile's threads have stopped (the next batch may never be staged).
 __device__ __forceinline__ void prefetch_splat(const float4* xy, const float4* conic, const float4* rgb,
-                                               const uint32_t* vals, int64_t n, int64_t vbase, uint32_t j,
-                                               const uint32_t* pair_off, const uint2* rect) {
+                                               const uint32_t* vals, int64_t n, int64_t vbase, uint32_t j) {
   const uint32_t g = vals[j];
   if (g >= n) return;
   const int64_t gi = vbase + g;
   prefetch_l1(xy + gi);
   prefetch_l1(conic + gi);
   prefetch_l1(rgb + gi);
-  if (pair_off) {
-    prefetch_l1(pair_off + gi);
-    prefetch_l1(rect + gi);
-  }
 }
 
 // Bit set of the staged splats [0, cnt) that warp `warp` can reach (its bit
@@ -311,10 +306,12 @@ __device__ __forceinline__ void composite_tile(const FwdArgs& a, const TileCoord
   float c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
   bool d0 = !tc.in0, d1 = !tc.in1;
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
-    if (__syncthreads_count(d0 && d1) == kThreads) break;
+    const int ndone = __syncthreads_count(d0 && d1);
+    if (ndone == kThreads) break;
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
-    for (int t = threadIdx.x; t < kBatch && start + kBatch + t < rg.y; t += kThreads)
-      prefetch_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + kBatch + t, nullptr, nullptr);
+    if (2 * ndone < kThreads)
+      for (int t = threadIdx.x; t < kBatch && start + kBatch + t < rg.y; t += kThreads)
+        prefetch_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + kBatch + t);
     for (int t = threadIdx.x; t < cnt; t += kThreads)
       stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + t, t, tc.ox, tc.oy, s_geo, s_geo2,
                       s_rgb, s_mask, nullptr, COUNT ? nullptr : a.counts);
@@ -804,15 +801,22 @@ __device__ __forceinline__ void bwd_front_tile(const BwdArgs& a, const TileCoord
   bool d0 = !tc.in0, d1 = !tc.in1;
   uint32_t start = rg.x;
   // the first barrier also ends the previous phase's reads of the staging slots
-  if (__syncthreads_count(d0 && d1) < kThreads && start < rg.y) {
+  int ndone = __syncthreads_count(d0 && d1);
+  if (ndone < kThreads && start < rg.y) {
     int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     for (;;) {
       if (threadIdx.x < cnt) {
-        if (start + kBatch + threadIdx.x < rg.y)
-          prefetch_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + kBatch + threadIdx.x, a.pair_off,
-                         a.rect);
-        stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, start + threadIdx.x, threadIdx.x, tc.ox, tc.oy,
-                        sm.geo, sm.geo2, sm.rgb, sm.mask, nullptr, nullptr);
+        const uint32_t j = start + threadIdx.x;
+        if (2 * ndone < kThreads && j + kBatch < rg.y)
+          prefetch_splat(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j + kBatch);
+        stage_splat<TW>(a.xy, a.conic, a.rgb, a.vals, a.n, vbase, j, threadIdx.x, tc.ox, tc.oy, sm.geo, sm.geo2,
+                        sm.rgb, sm.mask, nullptr, nullptr);
+        // the pair slot's inputs, read by the store after this batch
+        const uint32_t g = a.vals[j];
+        if (g < a.n) {
+          prefetch_l1(a.pair_off + vbase + g);
+          prefetch_l1(a.rect + vbase + g);
+        }
       }
       __syncthreads();
       warp_bits<kBatch>(sm.mask, cnt, warp, lane, sm.wb[warp]);
@@ -843,10 +847,10 @@ __device__ __forceinline__ void bwd_front_tile(const BwdArgs& a, const TileCoord
       }
       // every warp is past this batch's pixel steps: its partials are
       // complete and the staging slots are free
-      const bool all_done = __syncthreads_count(d0 && d1) == kThreads;
+      ndone = __syncthreads_count(d0 && d1);
       if (ss < cnt) store_staged(a, vbase, start + ss, tc, sm.red[ss], sm.hit[ss]);
       start += kBatch;
-      if (all_done || start >= rg.y) break;
+      if (ndone == kThreads || start >= rg.y) break;
       cnt = (int)min((uint32_t)kBatch, rg.y - start);
     }
   }
