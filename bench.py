@@ -58,6 +58,9 @@ def parse_args():
                     help="run only the level-of-detail measurement (one JSON line)")
     ap.add_argument("--ba-only", action="store_true",
                     help="run only the local bundle adjustment measurement (one JSON line)")
+    ap.add_argument("--fused-schedule", default=None,
+                    help="pin the fused pass's schedule (an autotune candidate name, e.g. 8x32_b64_viewmajor) "
+                         "instead of autotuning it; for profiling runs")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched measurement at --gaussians (one JSON line)")
     return ap.parse_args()
@@ -261,7 +264,7 @@ class Workload:
     one captured CUDA graph per pose.  batched: all views of `cams` in every
     iteration (one Adam step), one captured graph."""
 
-    def __init__(self, n, device, cams, batched, rank=0, use_graphs=True, fused=True):
+    def __init__(self, n, device, cams, batched, rank=0, use_graphs=True, fused=True, fused_schedule=None):
         import torch
         from paper_2607_14481_b300 import raster, synth, train
         self.torch, self.raster = torch, raster
@@ -308,8 +311,15 @@ class Workload:
             # the middle view group; then the pair capacity for that tile shape
             self.rast.set_capacity(int(kmax * 1.5) + 4096)
             self.rast.set_cameras(groups[k])
-            self.tuning = self.rast.autotune_fused(self.arena, self.poses[sl], self.targets[k], 0,
-                                                   timg[:3 * self.view_pixels[k]], self.loss.loss, reps=3)
+            if fused_schedule:
+                # pinned (profiling runs: the autotuner's timings are not
+                # comparable under a profiler)
+                self.rast.set_fused_schedule(fused_schedule)
+                self.tuning = {"tile": list(self.rast.tile), "schedule": int(self.rast.cfg.schedule),
+                               "pinned": fused_schedule}
+            else:
+                self.tuning = self.rast.autotune_fused(self.arena, self.poses[sl], self.targets[k], 0,
+                                                       timg[:3 * self.view_pixels[k]], self.loss.loss, reps=3)
             kmax = 0
             for j, g in enumerate(groups):
                 self.rast.set_cameras(g)
@@ -486,10 +496,10 @@ def stage_times(wl, K):
     return ms, work
 
 
-def run_batched(n, device, cams16, K, warmup, ws, rank):
+def run_batched(n, device, cams16, K, warmup, ws, rank, fused_schedule=None):
     """16 views of uneven size per iteration (one Adam step), one CUDA graph."""
     import torch
-    wb = Workload(n, device, cams16, batched=True, rank=rank)
+    wb = Workload(n, device, cams16, batched=True, rank=rank, fused_schedule=fused_schedule)
     for _ in range(max(3, warmup)):
         wb.step()
     torch.cuda.synchronize()
@@ -534,7 +544,8 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(device)
     K = args.steps
     # ---- plain single-view training (the headline)
-    wl = Workload(args.n, device, synth.forward_trajectory(N_POSES, SEED_TRAJ), batched=False, rank=rank)
+    wl = Workload(args.n, device, synth.forward_trajectory(N_POSES, SEED_TRAJ), batched=False, rank=rank,
+                  fused_schedule=args.fused_schedule)
     for _ in range(max(3, args.warmup)):
         wl.step()
     torch.cuda.synchronize()
@@ -1223,7 +1234,7 @@ def main():
         build.build()
         torch.cuda.set_device(0)
         out = run_batched(args.n, torch.device("cuda", 0), synth.loop_views(16, SEED_TRAJ + 1), args.steps,
-                          args.warmup, 1, 0)
+                          args.warmup, 1, 0, fused_schedule=args.fused_schedule)
         print(json.dumps({"batched": out}), flush=True)
         return
     ws, rank, local = dist_setup(args.gpus)

@@ -229,6 +229,23 @@ def poses_tensor(cams: Sequence[Camera], device="cuda") -> torch.Tensor:
     return torch.from_numpy(np.stack([c.pose12() for c in cams]).astype(np.float32)).to(device).contiguous()
 
 
+def parse_fused_schedule(name: str):
+    """(tile, schedule bits) of a fused-pass schedule name as autotune_fused
+    reports them: "<tw>x<th>_b<128|64|32>_<viewmajor|longest>"."""
+    parts = name.split("_")
+    if len(parts) != 3 or not parts[1].startswith("b"):
+        raise ValueError(f"fused schedule {name!r}: expected <tw>x<th>_b<n>_<viewmajor|longest>")
+    tile = tuple(int(x) for x in parts[0].split("x"))
+    if tile not in _lib.TILE_SHAPES:
+        raise ValueError(f"fused schedule {name!r}: tile shape not one of {_lib.TILE_SHAPES}")
+    batches = {128: 0, 64: 1, 32: 2}
+    bt = int(parts[1][1:])
+    if bt not in batches or parts[2] not in ("viewmajor", "longest"):
+        raise ValueError(f"fused schedule {name!r}: splats per batch 128, 64 or 32; order viewmajor or longest")
+    bits = _lib.GS_SCHED_FUSED_BATCH(batches[bt]) | (_lib.GS_SCHED_FUSED_LONGEST_FIRST if parts[2] == "longest" else 0)
+    return tile, bits
+
+
 class Rasterizer:
     """Splat records, tile lists and workspaces for a fixed set of views.
 
@@ -287,6 +304,15 @@ class Rasterizer:
         self.tile = (int(tile[0]), int(tile[1]))
         self.cfg.tile_w, self.cfg.tile_h = self.tile
         self.num_tiles = self.tiles_for(self.tile)
+
+    def set_fused_schedule(self, name: str) -> None:
+        """Pins the fused pass's schedule instead of autotuning it: `name` is
+        one of autotune_fused's candidates, "<tw>x<th>_b<splats per
+        batch>_<viewmajor|longest>" (e.g. "8x32_b64_viewmajor")."""
+        tile, bits = parse_fused_schedule(name)
+        self.set_tile(tile)
+        keep = self.cfg.schedule & ~(_lib.GS_SCHED_FUSED_BATCH(3) | _lib.GS_SCHED_FUSED_LONGEST_FIRST)
+        self.cfg.schedule = keep | bits
 
     def set_capacity(self, cap: int) -> None:
         cap = int(cap)

@@ -134,3 +134,15 @@ def test_roofline_of_the_fused_step():
     # float + 96 B per Gaussian (60 floats)
     ga = r["per_stage"]["bwd_gaussians_adam"]
     assert ga["bound"] == "hbm" and ga["algorithmic"] == pytest.approx(1.81e6 * 36 + 1_000_000 * (24 * 60 + 96))
+
+
+def test_fused_schedule_names():
+    from paper_2607_14481_b300 import _lib, raster
+    tile, bits = raster.parse_fused_schedule("8x32_b64_viewmajor")
+    assert tile == (8, 32) and bits == _lib.GS_SCHED_FUSED_BATCH(1)
+    tile, bits = raster.parse_fused_schedule("16x16_b32_longest")
+    assert tile == (16, 16) and bits == _lib.GS_SCHED_FUSED_BATCH(2) | _lib.GS_SCHED_FUSED_LONGEST_FIRST
+    assert raster.parse_fused_schedule("32x8_b128_viewmajor") == ((32, 8), 0)
+    for bad in ("8x32_b48_viewmajor", "8x16_b64_viewmajor", "8x32_b64", "8x32_64_longest", "8x32_b64_random"):
+        with pytest.raises(ValueError):
+            raster.parse_fused_schedule(bad)
