@@ -145,6 +145,53 @@ def test_fused_empty_scene_and_all_culled(cuda_device):
         assert np.all(g_f[k] == 0.0), k
 
 
+def _occluded_scene():
+    """Six large, nearly opaque Gaussians in front of 2,000 small ones: every
+    pixel stops within the first few list entries while each tile's list runs
+    on for several batches of staged splats."""
+    back = synth.random_scene(2000, 41, 1, (-0.5, -0.4, 1.5), (0.5, 0.4, 3.0), -3.5, 0.3)
+    front = synth.random_scene(6, 42, 1, (-0.05, -0.05, 0.5), (0.05, 0.05, 0.8), 0.5, 0.1)
+    front.opa_logits[:] = 3.0  # opacity 0.953: below the alpha clamp, no decision near a threshold
+    return synth.Scene(*(np.concatenate([getattr(front, f), getattr(back, f)])
+                         for f in ("means", "log_scales", "quats", "opa_logits", "sh")))
+
+
+@pytest.mark.parametrize("tile", SHAPES)
+def test_fused_every_pixel_stops_in_the_first_batch(cuda_device, tile):
+    """Lists several batches long where every pixel stops in the first: the
+    pairs past the stop get zero gradients and the result matches the
+    separate kernels and the oracle at every splats-per-batch setting."""
+    sc = _occluded_scene()
+    cams = [synth.look_at((0, 0, 0), (0, 0, 1), 60.0, 60.0, 24.0, 20.0, 48, 40)]
+    r, arena, poses, img, alpha = gpu_forward(sc, cams, tile=tile)
+    ref = oracle.render(sc, cams, tile=tile)
+    pairs = int(r.read_counts()[1])
+    assert pairs > 2 * 128 * r.num_tiles // 3  # long lists: a few batches per tile on average
+    assert not np.any(np.asarray(ref["flags"][0]))  # no decision within single-precision reach
+    assert np.all(alpha.cpu().numpy() > 1.0 - 1e-3)  # every pixel saturated by the front splats
+    # (the oracle's image without the back splats is the same image)
+    assert np.array_equal(np.asarray(oracle.render(sc.subset(np.arange(6)), cams, tile=tile)["image"][0]),
+                          np.asarray(ref["image"][0]))
+    _, tgt = _target(r, img, ref, np.random.default_rng(9))
+    iv = [x.numpy().astype(np.float64) for x in r.split(img.cpu(), 3)]
+    tv = [x.numpy().astype(np.float64) for x in r.split(tgt.cpu(), 3)]
+    dimg = loss_grad(iv, tv, 0, 3 * r.pixels)
+    g_ref = oracle.backward(sc, cams, dimg, tile=tile)
+    g_sep = gpu_backward(r, arena, poses, dimg, image=img)
+    for b in (0, 1, 2):
+        r.cfg.schedule = _lib.GS_SCHED_FUSED_BATCH(b)
+        img_f, loss_f, g_f = fused_step(r, arena, poses, tgt, 0)
+        assert torch.equal(img_f, img)
+        for k in g_sep:
+            if k == "means_pad":
+                continue
+            scale = max(np.abs(g_sep[k]).max(), 1e-30)
+            assert np.abs(g_f[k] - g_sep[k]).max() <= 1e-5 * scale, (b, k)
+        compare_grads(g_f, g_ref)
+        # the hidden splats receive nothing
+        assert np.all(g_f["opa_logits"][6:] == 0.0) and np.all(g_f["sh"][6:] == 0.0), b
+
+
 def test_autotune_fused_picks_a_shape_and_leaves_its_results(cuda_device):
     ensure_built()
     sc, cams, _ = synth.diffcheck()
