@@ -349,7 +349,7 @@ class Workload:
                 self.arena, self.grads, self.m, self.v, self.groups, self.rast, self.poses[sl], self.targets[k],
                 self.step_dev, pose_m=self.pose_m[sl], pose_v=self.pose_v[sl], pose_steps=self.pose_steps[sl],
                 pose_lr=1e-4, loss_kind=0, status=self.status, image=img[:3 * px], dimage=dimg[:3 * px],
-                loss=self.loss, cams=g, fused=fused, adam=self.adam if fused else None))
+                loss=raster.ImageLoss(device), cams=g, fused=fused, adam=self.adam if fused else None))
         if use_graphs:
             self.pool = torch.cuda.graph_pool_handle()
             for st in self.steps:
@@ -431,13 +431,19 @@ def timed_loop(wl, K, ws, e2e=False):
     (on a copy stream, one iteration ahead, so the copy of iteration i + 1
     overlaps the compute of iteration i; iteration i waits for its own copy,
     and a copy into a target buffer waits for the last iteration that read
-    it) and reads its loss back to pinned host memory."""
+    it) and reads its loss back to pinned host memory: on a third stream
+    once the iteration's kernels are done, so the next iteration does not
+    wait behind the copy (each trajectory position has its own loss word, and
+    an iteration waits for the read of its word's previous value; the end
+    event waits for the last read)."""
     import torch
     seq = wl.sequence(K)
     loss_host = torch.zeros(max(K, 1), dtype=torch.float32).pin_memory() if e2e else None
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream() if e2e else None
+    readback = torch.cuda.Stream() if e2e else None
     done_ev = [None] * len(wl.steps)  # last iteration that read each target buffer
+    read_ev = [None] * len(wl.steps)  # last read of each position's loss word
 
     def issue_copy(k):
         ev = torch.cuda.Event()
@@ -460,16 +466,26 @@ def timed_loop(wl, K, ws, e2e=False):
         st = wl.steps[k]
         if e2e:
             comp.wait_event(ready)
+            if read_ev[k] is not None:
+                comp.wait_event(read_ev[k])
         st.run()
         if e2e:
-            loss_host[i:i + 1].copy_(st.loss.loss, non_blocking=True)
             done_ev[k] = torch.cuda.Event()
             done_ev[k].record(comp)
+            with torch.cuda.stream(readback):
+                readback.wait_event(done_ev[k])
+                loss_host[i:i + 1].copy_(st.loss.loss, non_blocking=True)
+                read_ev[k] = torch.cuda.Event()
+                read_ev[k].record(readback)
             if i + 1 < K:
                 ready = issue_copy(seq[i + 1])
+    if e2e:
+        comp.wait_stream(readback)
     t1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
+    if e2e and not bool(torch.isfinite(loss_host[:K]).all()):
+        raise RuntimeError("a loss read back in the end-to-end loop is not finite")
     barrier(ws)
     wl.i += K
     return allreduce_max(t0.elapsed_time(t1) / 1e3, ws)
