@@ -17,7 +17,9 @@
 // The backward accumulates per pixel only the moments of dL/dpower (dx dp,
 // dy dp, dx^2 dp, dx dy dp, dy^2 dp) for the splat's mean and conic; the conic
 // is applied once per (tile, splat) when the pair's reduced gradient is
-// stored.
+// stored.  In the single-pass backward the stores of one batch's pairs and
+// the staging of the next run side by side on different threads, and the
+// staging asks L1 for the next batch's records one batch ahead.
 //
 // Each staged splat carries its centre relative to the tile origin, its conic
 // scaled to base-2 exponent units and the exponent threshold below which its
