@@ -46,8 +46,11 @@ __device__ __forceinline__ float screen_size(float tz, float4 so, float fx, floa
 template <int DEG>
 __global__ void __launch_bounds__(256) k_project(const ProjectArgs a, const ViewTable vt) {
   constexpr int NC = (DEG + 1) * (DEG + 1);
-  const int v = blockIdx.y;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // the blocks of one chunk of Gaussians for every view are adjacent, so the
+  // views of a chunk run close together and share its parameter and SH
+  // lines in L2 (one DRAM read of them per step, not one per view)
+  const int v = (int)(blockIdx.x % (unsigned)vt.views);
+  const int64_t i = (int64_t)(blockIdx.x / (unsigned)vt.views) * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const int64_t o = (int64_t)v * a.n + i;
   const ViewInfo vi = vt.v[v];
@@ -277,7 +280,7 @@ gs_status launch_project(const gs_params& p, const float* poses, const ViewTable
   a.h_n = hier ? hier->n_nodes : nullptr;
   a.h_roots = hier && hier_roots ? 1 : 0;
   if (p.n == 0) return GS_OK;
-  dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)vt.views);
+  const unsigned grid = (unsigned)((p.n + 255) / 256) * (unsigned)vt.views;
   switch (p.sh_degree) {
     case 0: k_project<0><<<grid, 256, 0, s>>>(a, vt); break;
     case 1: k_project<1><<<grid, 256, 0, s>>>(a, vt); break;
