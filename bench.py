@@ -494,17 +494,21 @@ def timed_loop(wl, K, ws, e2e=False):
 def stage_times(wl, K):
     """Per-stage device times (CUDA events on the launching stream) of K eager
     iterations over poses spread along the trajectory, and the blend work
-    counts of each iteration's tile lists (their means)."""
+    counts of each iteration's tile lists (their means).  Each iteration is
+    queued behind a 2 ms spin of the device, so that the host has issued its
+    launches before the device reaches them and no stage time includes the
+    host's launch latency (the work counts synchronise every iteration)."""
     import torch
     names = wl.stages()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(K)]
     counts = []
     seq = wl.sequence(K)
-    torch.cuda.nvtx.range_push("eager")
     for i in range(K):
+        torch.cuda._sleep(4_000_000)  # outside the range that profiles select
+        torch.cuda.nvtx.range_push("eager")
         wl.instrumented_step(evs[i], seq[i])
         counts.append(wl.rast.render_stats())
-    torch.cuda.nvtx.range_pop()
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = {s: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K)]))
           for j, s in enumerate(names)}
